@@ -1,0 +1,260 @@
+"""Seeded synthetic workloads for manifold tracing and certification.
+
+This module only builds inputs: RBF decision-function parameters (support
+vectors, weights, gamma, b), seeds, the lattice scale and offset, the C-space
+box, and the robot/obstacle geometry.  It holds none of the tracing or
+certification arithmetic, and both the CUDA path and the CPU oracle receive
+exactly the arrays it returns.
+
+The paper's scenes (Packbot, UR5, Schunk; Sec. VI) and its learned SVMs are not
+available, so each workload is a stand-in with the paper's shapes: a d-DoF
+serial arm with capsule links among box/sphere obstacles and an RBF-kernel SVM
+decision function (Sec. IV-A) over [-pi, pi]^d.
+
+Seeds stand in for the paper's manifold sampler (SLSQP minimising |M(q)|,
+Sec. IV-A), which is not part of the traced path: they are placed by plain
+numpy bisection between a point with f < 0 and one with f >= 0.  The traced
+set depends only on the n-simplex each seed falls in.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+BOX, SPHERE = 0, 1
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    d: int
+    sv: np.ndarray          # [N, d] support vectors
+    alpha: np.ndarray       # [N] dual weights (signed)
+    gamma: float
+    b: float
+    lam: float              # lattice scale lambda_T
+    offset: np.ndarray      # [d] lattice offset o
+    lo: np.ndarray          # [d] C-space box
+    hi: np.ndarray
+    seeds: np.ndarray       # [S, d]
+    dh: np.ndarray          # [d, 4] theta0, d, a, alpha (DH) per link
+    radius: np.ndarray      # [d] capsule radius per link
+    obs_type: np.ndarray    # [M] BOX / SPHERE
+    obs_pose: np.ndarray    # [M, 12] R (row-major, local->world) then t
+    obs_dims: np.ndarray    # [M, 3] box side lengths / sphere radius in [0]
+    batch_cap: int = 1 << 24
+    precision: str = "fp64"
+    recheck_band: float = 1e-3
+    meta: dict = dataclasses.field(default_factory=dict)
+
+
+def lattice_offset(d: int, lam: float) -> np.ndarray:
+    """A fixed, generic lattice offset so that seeds and constructed zeros do
+    not sit on lattice vertices."""
+    i = np.arange(d, dtype=np.float64)
+    return lam * np.modf(i * 0.6180339887498949 + 0.5)[0] / 7.0
+
+
+def _rbf_numpy(sv, alpha, gamma, b, q):
+    # Used only to place seeds (stand-in for the out-of-scope manifold sampler).
+    q = np.atleast_2d(q)
+    d2 = ((q[:, None, :] - sv[None, :, :]) ** 2).sum(-1)
+    return np.exp(-gamma * d2) @ alpha + b
+
+
+def place_seeds(rng, sv, alpha, gamma, b, lo, hi, n_seeds, inner=None, step=0.05, max_steps=200):
+    """Seeds on f = 0: march from an inner point (f < 0) along a random
+    direction until f >= 0, then bisect 60 times."""
+    d = sv.shape[1]
+    if inner is None:
+        cand = np.concatenate([sv, rng.uniform(lo, hi, size=(4096, d))])
+        fc = _rbf_numpy(sv, alpha, gamma, b, cand)
+        inner = cand[fc < 0]
+    if inner.shape[0] == 0:
+        raise ValueError("no point with f < 0 to start from")
+    seeds = []
+    tries = 0
+    while len(seeds) < n_seeds and tries < 100 * n_seeds:
+        tries += 1
+        a = inner[rng.integers(inner.shape[0])]
+        u = rng.normal(size=d)
+        u /= np.linalg.norm(u)
+        fa = _rbf_numpy(sv, alpha, gamma, b, a)[0]
+        if fa >= 0:
+            continue
+        bpt = None
+        for k in range(1, max_steps + 1):
+            p = a + k * step * u
+            if np.any(p < lo) or np.any(p > hi):
+                break
+            if _rbf_numpy(sv, alpha, gamma, b, p)[0] >= 0:
+                bpt = p
+                break
+        if bpt is None:
+            continue
+        x0, x1 = a.copy(), bpt.copy()
+        for _ in range(60):
+            m = 0.5 * (x0 + x1)
+            if _rbf_numpy(sv, alpha, gamma, b, m)[0] >= 0:
+                x1 = m
+            else:
+                x0 = m
+        seeds.append(0.5 * (x0 + x1))
+    if len(seeds) < n_seeds:
+        raise ValueError("could not place %d seeds" % n_seeds)
+    return np.array(seeds)
+
+
+def _aabb_pose(center):
+    pose = np.zeros(12)
+    pose[[0, 4, 8]] = 1.0
+    pose[9:12] = center
+    return pose
+
+
+def _ball(rng, n, radius):
+    u = rng.normal(size=(n, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    r = radius * rng.uniform(size=(n, 1)) ** (1.0 / 3.0)
+    return u * r
+
+
+def _dh_arm(rng, d, radius):
+    dh = np.zeros((d, 4))
+    dh[:, 1] = rng.uniform(0.0, 0.2, size=d)
+    dh[:, 2] = rng.uniform(0.2, 0.5, size=d)
+    dh[:, 3] = rng.choice([-math.pi / 2, 0.0, math.pi / 2], size=d)
+    return dh, np.full(d, radius)
+
+
+def _svm_stand_in(rng, d, n_sv, p_neg, b):
+    """Support vectors uniform in the C-space box; alpha = label * |N(0,1)|
+    with a share p_neg of free-space (negative) labels; fixed bias b > 0, so
+    the zero set is a family of closed shells around free-space vectors."""
+    sv = rng.uniform(-math.pi, math.pi, size=(n_sv, d))
+    lab = np.where(rng.uniform(size=n_sv) < p_neg, -1.0, 1.0)
+    alpha = lab * np.abs(rng.normal(size=n_sv))
+    return sv, alpha, float(b)
+
+
+def config_d3(seed: int = 1000, lam: float = 0.1) -> Workload:
+    """d=3 plain FP64: 64 SVs uniform in [-pi,pi]^3, alpha ~ N(0,1), gamma=2,
+    b so that f(0) = 0, one seed at the origin (a zero of f by construction),
+    lambda=0.1, planar 3-link arm (unit links, capsule r=0.05) among 4 random
+    axis-aligned boxes."""
+    rng = np.random.default_rng(seed)
+    d = 3
+    sv = rng.uniform(-math.pi, math.pi, size=(64, d))
+    alpha = rng.normal(size=64)
+    gamma = 2.0
+    b = -float(np.sum(alpha * np.exp(-gamma * np.sum(sv * sv, axis=1))))
+    dh = np.zeros((3, 4))
+    dh[:, 2] = 1.0
+    radius = np.full(3, 0.05)
+    centers = np.zeros((4, 3))
+    centers[:, :2] = rng.uniform(-2.5, 2.5, size=(4, 2))
+    half = rng.uniform(0.1, 0.5, size=(4, 3))
+    lo, hi = np.full(d, -math.pi), np.full(d, math.pi)
+    return Workload("d3_fp64_64sv", d, sv, alpha, gamma, b, lam, lattice_offset(d, lam), lo, hi,
+                    np.zeros((1, d)), dh, radius, np.zeros(4, np.int32),
+                    np.stack([_aabb_pose(c) for c in centers]), 2.0 * half,
+                    batch_cap=1 << 24, precision="fp64")
+
+
+def config_d5(seed: int = 1001, lam: float = 0.05, n_sv: int = 2048, n_seeds: int = 16,
+              b: float = 0.6, p_neg: float = 0.3) -> Workload:
+    """d=5 plain FP64: 5-DoF DH arm (a in [0.2,0.5], d in [0,0.2], link twist
+    in {-pi/2, 0, pi/2}, capsules r=0.04) among 12 random boxes; RBF with 2048
+    SVs from seeded C-space samples, gamma=4; lambda=0.05; 16 seeds; batch cap
+    2^24 edges."""
+    rng = np.random.default_rng(seed)
+    d = 5
+    dh, radius = _dh_arm(rng, d, 0.04)
+    reach = float(dh[:, 2].sum())
+    centers = _ball(rng, 12, reach)
+    half = rng.uniform(0.05, 0.3, size=(12, 3))
+    sv, alpha, b = _svm_stand_in(rng, d, n_sv, p_neg, b)
+    gamma = 4.0
+    lo, hi = np.full(d, -math.pi), np.full(d, math.pi)
+    seeds = place_seeds(rng, sv, alpha, gamma, b, lo, hi, n_seeds)
+    return Workload("d5_fp64_%dsv" % n_sv, d, sv, alpha, gamma, b, lam, lattice_offset(d, lam),
+                    lo, hi, seeds, dh, radius, np.zeros(12, np.int32),
+                    np.stack([_aabb_pose(c) for c in centers]), 2.0 * half,
+                    batch_cap=1 << 24, precision="fp64")
+
+
+def config_d6(seed: int = 1002, lam: float = 0.04, n_sv: int = 8192, n_seeds: int = 64,
+              b: float = 0.6, p_neg: float = 0.3) -> Workload:
+    """d=6 mixed precision: 6-DoF arm among 10 boxes + 10 spheres; RBF with
+    8192 SVs, gamma=6; distance GEMM in BF16 with FP32 accumulation, FP64
+    recheck band |f| < 1e-3; lambda=0.04; 64 seeds."""
+    rng = np.random.default_rng(seed)
+    d = 6
+    dh, radius = _dh_arm(rng, d, 0.04)
+    reach = float(dh[:, 2].sum())
+    cb = _ball(rng, 10, reach)
+    cs = _ball(rng, 10, reach)
+    half = rng.uniform(0.05, 0.3, size=(10, 3))
+    rs = rng.uniform(0.05, 0.25, size=10)
+    sv, alpha, b = _svm_stand_in(rng, d, n_sv, p_neg, b)
+    gamma = 6.0
+    lo, hi = np.full(d, -math.pi), np.full(d, math.pi)
+    seeds = place_seeds(rng, sv, alpha, gamma, b, lo, hi, n_seeds)
+    types = np.array([BOX] * 10 + [SPHERE] * 10, np.int32)
+    poses = np.stack([_aabb_pose(c) for c in np.concatenate([cb, cs])])
+    dims = np.concatenate([2.0 * half, np.stack([rs, np.zeros(10), np.zeros(10)], 1)])
+    return Workload("d6_mixed_%dsv" % n_sv, d, sv, alpha, gamma, b, lam, lattice_offset(d, lam),
+                    lo, hi, seeds, dh, radius, types, poses, dims,
+                    batch_cap=1 << 24, precision="mixed", recheck_band=1e-3)
+
+
+def sphere_workload(d: int, r: float = 1.0, gamma: float = 1.0, lam: float = 0.2,
+                    center=None) -> Workload:
+    """One-SV RBF whose zero set is exactly the sphere |q - c| = r:
+    f = -exp(-gamma |q - c|^2) + exp(-gamma r^2)."""
+    c = np.zeros(d) if center is None else np.asarray(center, np.float64)
+    sv = c[None, :].copy()
+    alpha = np.array([-1.0])
+    b = math.exp(-gamma * r * r)
+    seed = c.copy()
+    seed[0] += r
+    lo, hi = np.full(d, -math.pi), np.full(d, math.pi)
+    dh = np.zeros((d, 4))
+    dh[:, 2] = 1.0
+    return Workload("sphere_d%d" % d, d, sv, alpha, gamma, b, lam, lattice_offset(d, lam), lo, hi,
+                    seed[None, :], dh, np.full(d, 0.05), np.zeros(0, np.int32),
+                    np.zeros((0, 12)), np.zeros((0, 3)))
+
+
+def plane_workload(d: int, lam: float = 0.2, gamma: float = 0.5, rng_seed: int = 7) -> Workload:
+    """Two SVs with alpha = (+1, -1), b = 0: the zero set is the bisector
+    hyperplane of the two support vectors."""
+    rng = np.random.default_rng(rng_seed)
+    s1 = rng.uniform(-1, 1, size=d)
+    s2 = rng.uniform(-1, 1, size=d)
+    sv = np.stack([s1, s2])
+    alpha = np.array([1.0, -1.0])
+    seed = 0.5 * (s1 + s2)
+    lo, hi = np.full(d, -1.0), np.full(d, 1.0)
+    dh = np.zeros((d, 4))
+    dh[:, 2] = 1.0
+    return Workload("plane_d%d" % d, d, sv, alpha, gamma, 0.0, lam, lattice_offset(d, lam), lo, hi,
+                    seed[None, :], dh, np.full(d, 0.05), np.zeros(0, np.int32),
+                    np.zeros((0, 12)), np.zeros((0, 3)))
+
+
+def random_small(d: int, n_sv: int, seed: int, lam: float, gamma: float = 2.0, n_seeds: int = 4,
+                 box: float = 1.5, b: float = 0.3, p_neg: float = 0.5) -> Workload:
+    """Small random RBF problems for brute-force and parity tests."""
+    rng = np.random.default_rng(seed)
+    sv = rng.uniform(-box, box, size=(n_sv, d))
+    lab = np.where(rng.uniform(size=n_sv) < p_neg, -1.0, 1.0)
+    alpha = lab * (0.5 + np.abs(rng.normal(size=n_sv)))
+    lo, hi = np.full(d, -box), np.full(d, box)
+    seeds = place_seeds(rng, sv, alpha, gamma, b, lo, hi, n_seeds)
+    dh, radius = _dh_arm(rng, d, 0.04)
+    return Workload("rand_d%d_%d" % (d, seed), d, sv, alpha, gamma, b, lam,
+                    lattice_offset(d, lam), lo, hi, seeds, dh, radius,
+                    np.zeros(0, np.int32), np.zeros((0, 12)), np.zeros((0, 3)))
