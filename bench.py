@@ -1,0 +1,321 @@
+"""Benchmark: traced simplices per second (and ms per proof) of the manifold
+tracing + certification path on GB300.
+
+A step is one proof: mf_trace (seeds, BFS, roots, cells, CSR) + mf_certify on
+one synthetic workload (default: d=5, 2048 support vectors, gamma=4,
+lambda=0.05, 16 seeds, batch cap 2^24, FP64 path).  Inputs are resident in HBM
+for the device-timed value; the e2e figure copies the inputs from pinned host
+memory and reads the point verdicts back every step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--config d5|d3|d6] [--precision auto|fp64|mixed]
+
+Under torchrun each rank traces its own independent workload (seed + rank):
+weak scaling, no collective on the data path.  `--impl reference` times the
+FP64 CPU oracle (the only other arm this method has) on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2406_04795_gb300 import workloads as W  # noqa: E402
+
+FP64_EXP_FLOPS = 26  # Cody-Waite reduction (2 FMA) + degree-11 Horner (11 FMA), 2 flops per FMA
+
+
+def make_workload(cfg: str, rank: int, lam=None):
+    kw = {} if lam is None else {"lam": lam}
+    if cfg == "d3":
+        return W.config_d3(seed=1000 + 10 * rank, **kw)
+    if cfg == "d6":
+        return W.config_d6(seed=1002 + 10 * rank, **kw)
+    return W.config_d5(seed=1001 + 10 * rank, **kw)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for k, n in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def roofline(stats, w, clocks, n_sms=152):
+    """Roofline of the dominant phase: FP64 pipe for the RBF phases
+    (2 FP64 FMA per SM per clock on GB300), HBM for the table phases."""
+    peaks, src = measured_peaks()
+    dom = max(stats, key=lambda k: stats[k]["ms"])
+    s = stats[dom]
+    ms_per_launch = s["ms"] / max(s["launches"], 1)
+    d = w.d
+    mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = n_sms * 4.0 * mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
+    if dom in ("roots", "eval"):
+        per_term = (5 * d + 5 if dom == "roots" else 3 * d + 3) + FP64_EXP_FLOPS
+        flops = s["terms"] * per_term / max(s["launches"], 1)
+        ach = flops / (ms_per_launch * 1e-3) / 1e12
+        return {"kernel": "k_roots_f64" if dom == "roots" else "k_eval_vertices_f64",
+                "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": ach / fp64_peak, "traffic": None,
+                "peak_source": "FP64 pipe: %d SMs x 2 DFMA/clk x %.0f MHz (sampled)" % (n_sms, mhz),
+                "work": "%d FP64 RBF terms x %d flops" % (s["terms"], per_term),
+                "phase_ms": {k: round(v["ms"], 3) for k, v in stats.items() if v["ms"] > 0}}
+    if dom == "certify_points":
+        n_obs = int(w.obs_type.shape[0])
+        flops = s["units"] * d * (60 + n_obs * 150) / max(s["launches"], 1)
+        ach = flops / (ms_per_launch * 1e-3) / 1e12
+        return {"kernel": "k_certify_points", "bound": "alu", "achieved": ach, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
+                "peak_source": "FP64 pipe at the sampled clock",
+                "phase_ms": {k: round(v["ms"], 3) for k, v in stats.items() if v["ms"] > 0}}
+    # table phases: algorithmic bytes = one 32-byte sector per hash probe / record touched
+    per_unit = {"expand_vertices": (4 * d + 4) + 32 * (2 ** d),
+                "expand_edges": (4 * d + 20) + 64 * (2 ** d),
+                "cells": (4 * d + 4) + 64 * 60, "csr": (5 * d) + 32 * (d + 1) * d + 16}.get(dom, 64)
+    by = s["units"] * per_unit / max(s["launches"], 1)
+    ach = by / (ms_per_launch * 1e-3) / 1e9
+    return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+            "phase_ms": {k: round(v["ms"], 3) for k, v in stats.items() if v["ms"] > 0}}
+
+
+def cpu_baseline(w, budget_s=15.0):
+    """The FP64 oracle on a bounded sample of the same workload: trace (with
+    roots and cells) until max_edges edges exist, then certify those points."""
+    import oracle
+    oracle.build()
+    n = 200
+    rate, sample = None, None
+    while True:
+        t0 = time.perf_counter()
+        r = oracle.trace(w.sv, w.alpha, w.gamma, w.b, w.lam, w.offset, w.lo, w.hi, w.seeds,
+                         roots=True, cells=True, max_edges=n)
+        oracle.certify(w.dh, w.radius, w.obs_type, w.obs_pose, w.obs_dims, r["edge_pt"],
+                       r["cell_off"], r["cell_idx"])
+        dt = time.perf_counter() - t0
+        E = len(r["edge_t"])
+        rate, sample = E / dt, "first %d edges of the BFS (+ roots, cells, certify) in %.1f s" % (E, dt)
+        if dt > budget_s / 4 or E < n:
+            break
+        n *= 4
+    return {"value": rate, "unit": "simplices/s", "cores": 1, "kind": "oracle", "sample": sample}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = make_workload(args.config, 0, args.lam)
+    for _ in range(args.warmup):
+        pass
+    vals = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(w, budget_s=8.0))
+    dt = time.perf_counter() - t_all
+    v = statistics.median([x["value"] for x in vals])
+    line = {"impl": "reference", "metric": "traced simplices/s", "value": v, "unit": "simplices/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "lambda": w.lam, "n_sv": int(w.sv.shape[0]),
+                       "seeds": int(w.seeds.shape[0]), "precision": "fp64"},
+            "cpu_baseline": dict(vals[-1], value=v),
+            "e2e": {"value": v, "unit": "simplices/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_gb300(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2406_04795_gb300 import mf
+    from paper_2406_04795_gb300.api import Context
+    from paper_2406_04795_gb300.pipeline import Proof, host_inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    w = make_workload(args.config, rank, args.lam)
+    if args.precision == "fp64":
+        w.precision = "fp64"
+    elif args.precision == "mixed":
+        w.precision = "mixed"
+    ctx = Context(local, 0)
+    proof = Proof(ctx, w)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 0)):
+        r, v, m, cv = proof.step()
+    torch.cuda.synchronize()
+    E = r["n_edges"]
+    mf.mf_ctx_set_profiling(ctx.h, True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    edges = 0
+    for _ in range(args.steps):
+        r, v, m, cv = proof.step()
+        edges += r["n_edges"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / max(args.steps, 1)
+    stats = mf.mf_ctx_get_stats(ctx.h)
+    mf.mf_ctx_set_profiling(ctx.h, False)
+    launches = sum(s["launches"] for s in stats.values())
+
+    # end to end: pinned host inputs copied in, verdicts read back, every step
+    hin = host_inputs(w)
+    verdict_host = torch.empty(E, dtype=torch.uint8).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in hin.values())
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_edges = 0
+    for _ in range(args.steps):
+        for name, t in hin.items():
+            getattr(proof, name).copy_(t, non_blocking=True)
+        r, v, m, cv = proof.step()
+        n = r["n_edges"]
+        if verdict_host.numel() < n:
+            verdict_host = torch.empty(n, dtype=torch.uint8).pin_memory()
+        verdict_host[:n].copy_(v, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_edges += n
+    e2e_s = time.perf_counter() - t0
+    barrier()
+
+    agg = torch.tensor([ms, float(edges), e2e_s, float(e2e_edges)], dtype=torch.float64,
+                       device="cuda")
+    if world > 1:
+        mx = agg.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = agg.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_max, edges_all, e2e_max, e2e_edges_all = mx[0].item(), sm[1].item(), mx[2].item(), sm[3].item()
+    else:
+        ms_max, edges_all, e2e_max, e2e_edges_all = ms, float(edges), e2e_s, float(e2e_edges)
+    if rank == 0:
+        value = edges_all / args.steps / (ms_max * 1e-3)
+        line = {
+            "metric": "traced simplices/s", "value": value, "unit": "simplices/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if w.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "d": w.d, "lambda": w.lam,
+                       "n_sv": int(w.sv.shape[0]), "gamma": w.gamma,
+                       "seeds": int(w.seeds.shape[0]), "batch_cap": w.batch_cap,
+                       "precision": w.precision, "edges_per_proof": E,
+                       "cells_per_proof": r["n_cells"], "vertices_per_proof": r["n_vertices"],
+                       "bfs_levels": r["levels"], "ms_per_proof": ms_max,
+                       "l2": "inputs larger than L2 (resident hash tables and lists are GBs)"},
+            "e2e": {"value": e2e_edges_all / args.steps / (e2e_max / args.steps),
+                    "unit": "simplices/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": E},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "roofline": roofline(stats, w, clocks),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="d5", choices=["d3", "d5", "d6"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lam", type=float, default=None,
+                    help="override the lattice scale (small profiling cases)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

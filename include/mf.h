@@ -1,0 +1,221 @@
+/*
+ * mf.h -- C ABI of the GB300 manifold-tracing and certification library
+ * (libmf.so).  A from-scratch implementation of the hot path of
+ * "Scaling Motion Planning Infeasibility Proofs" (Li & Dantam, arXiv 2406.04795):
+ * tracing the zero set of a learned RBF decision function over the Coxeter
+ * (Ã_d) triangulation in permutahedral representation (Sec. II-B, IV-A),
+ * the crossing n-simplices (Sec. IV-C), and the forward-kinematics / capsule
+ * collision check that certifies the traced points (Sec. V-C, App. A).
+ *
+ * Conventions for every entry point
+ *  - Return value: MF_OK (0) or a negative MF_ERR_* code; mf_last_error(ctx)
+ *    then holds a one-line message.  No entry point aborts the process.
+ *  - Pointers documented "device" must point to memory of the context's
+ *    device (cudaMalloc, torch CUDA tensors, ...); "host" pointers to host
+ *    memory.  The caller owns every buffer it passes; the library never frees
+ *    or keeps a caller pointer beyond the call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls enqueue their kernels on it and return after the counts
+ *    they report are known (they synchronise that stream).
+ *  - The context owns its resident device memory (hash tables, frontier and
+ *    vertex lists, cell tables) inside the HBM budget given at creation.
+ *  - Multi-dimensional arrays are row-major.  d is the configuration-space
+ *    dimension, 2 <= d <= MF_MAXD.
+ */
+#ifndef MF_H
+#define MF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MF_MAXD 8
+
+#define MF_OK 0
+#define MF_ERR_INVALID (-1)   /* bad argument: d out of range, lambda <= 0, NaN, NULL */
+#define MF_ERR_DOMAIN (-2)    /* lattice keys of this domain / lambda do not fit 64 bits */
+#define MF_ERR_OOM (-3)       /* the request does not fit the context's HBM budget */
+#define MF_ERR_CAPACITY (-4)  /* an output buffer is too small; counts hold the sizes needed */
+#define MF_ERR_MAXEDGES (-5)  /* traced set exceeded opts.max_edges; result is partial */
+#define MF_ERR_TIMEOUT (-6)   /* a bounded device-side wait gave up */
+#define MF_ERR_CUDA (-7)      /* a CUDA runtime call failed */
+#define MF_ERR_DEVICE (-8)    /* a device-side check failed (hash probe limit, index) */
+
+/* Arithmetic of the RBF evaluation (north-star "Precision"). */
+#define MF_FP64 0        /* FP64 differences and exp */
+#define MF_MIXED_BF16 1  /* distance GEMM on tcgen05 tensor cores (BF16 split, FP32
+                            accumulate), FP32 exp, FP64 recheck of |f~| <= band */
+#define MF_MIXED_FP32 2  /* FP32 SIMT distance and exp, FP64 recheck of |f~| <= band */
+
+/* mf_trace_opts.flags */
+#define MF_WANT_ROOTS 1u /* solve t and the intersection point of every traced edge */
+#define MF_WANT_CELLS 2u /* crossing n-simplices and the cell -> edge CSR */
+
+typedef struct mf_ctx mf_ctx;
+
+/* The learned manifold: f(q) = sum_i alpha_i exp(-gamma |q - s_i|^2) + b, the
+ * decision function of an RBF-kernel SVM (Sec. IV-A; ThunderSVM, Sec. VI). */
+typedef struct {
+  int32_t d;
+  int64_t n_sv;
+  const double *sv;    /* device [n_sv][d] support vectors */
+  const double *alpha; /* device [n_sv] signed dual weights */
+  double gamma;        /* > 0 */
+  double b;
+} mf_rbf;
+
+/* The traced region: the closed box [lo, hi]^d of C-space, and the lattice
+ * offset o of the triangulation x = lambda * L * y + o (L = I - c 1 1^T,
+ * c = (1 - 1/sqrt(d+1))/d, the Ã_d realisation of the Freudenthal-Kuhn
+ * lattice).  An edge is traced only if both its vertices lie in the box. */
+typedef struct {
+  double lo[MF_MAXD], hi[MF_MAXD];
+  double offset[MF_MAXD];
+} mf_domain;
+
+typedef struct {
+  double lambda;           /* triangulation scale lambda_T (Sec. IV-A), > 0 */
+  int64_t batch_cap_edges; /* frontier edges expanded per BFS chunk; 0 = 2^24 */
+  int32_t precision;       /* MF_FP64 / MF_MIXED_BF16 / MF_MIXED_FP32 */
+  double recheck_band;     /* mixed paths: vertices with |f~| <= max(bound, band)
+                              are re-evaluated in FP64; 0 = 1e-3 */
+  double root_tol;         /* root solve stops when |Newton step| <= root_tol; 0 = 1e-12 */
+  int64_t max_edges;       /* capacity of the resident edge table; 0 = 2^24 */
+  int64_t max_vertices;    /* capacity of the vertex table; 0 = max_edges */
+  int64_t max_cells;       /* capacity of the cell table; 0 = 2 * max_edges */
+  uint32_t flags;          /* MF_WANT_ROOTS | MF_WANT_CELLS */
+} mf_trace_opts;
+
+/* Results of mf_trace.  Array fields are caller-owned DEVICE buffers of the
+ * given capacities (NULL with capacity 0 = not wanted).  If a capacity is too
+ * small the call returns MF_ERR_CAPACITY after filling the counts; the result
+ * stays in the context, and mf_trace_fetch copies it into larger buffers
+ * without tracing again.  The order of edges and cells is unspecified (each
+ * BFS level is contiguous); compare them as sets. */
+typedef struct {
+  int64_t cap_edges;
+  int32_t *edge_y;        /* [cap_edges][d] first vertex y of each traced edge */
+  uint32_t *edge_mask;    /* [cap_edges] first part p1 of the edge's ordered
+                             partition (p1, p2), as a mask over {0..d-1}; the
+                             second vertex is y + sum_{i in p1} e_i */
+  double *edge_f;         /* [cap_edges][2] f at the two vertices */
+  double *edge_t;         /* [cap_edges] root parameter t in [0,1] (MF_WANT_ROOTS) */
+  double *points;         /* [cap_edges][d] intersection point x(y) + t (x(y') - x(y)) */
+  int64_t cap_cells;
+  int32_t *cell_y;        /* [cap_cells][d] vertex of each crossing n-simplex */
+  uint8_t *cell_perm;     /* [cap_cells][d] order of its singleton parts before {d} */
+  int64_t *cell_edge_off; /* [cap_cells + 1] CSR offsets into cell_edge_idx */
+  int64_t cap_cell_edges;
+  int64_t *cell_edge_idx; /* [cap_cell_edges] indices of the traced edges of each cell */
+  /* counts written by the library */
+  int64_t n_edges, n_cells, n_cell_edges;
+  int64_t n_vertices;     /* distinct lattice vertices at which f was evaluated */
+  int64_t n_near_zero;    /* of those, |f| < 1e-12 */
+  int64_t n_recheck;      /* mixed paths: vertices re-evaluated in FP64 */
+  int64_t n_boundary;     /* (traced edge, 2-coface) pairs whose new vertex lies outside the box */
+  int64_t n_dead_seeds;   /* seeds whose n-simplex has no traced edge */
+  int64_t levels;         /* BFS levels (level 0 = seed edges) */
+  int64_t root_evals;     /* f evaluations spent by the root solve */
+} mf_trace_out;
+
+/* Serial arm for certification: frame T_{i+1} = T_i Rz(q_i + theta_i) Tz(d_i)
+ * Tx(a_i) Rx(alpha_i), T_0 = identity; link i is the capsule between the
+ * origins of T_i and T_{i+1} with radius radius[i]. */
+typedef struct {
+  int32_t n_links;        /* == d of the points */
+  const double *dh;       /* device [n_links][4]: theta_i, d_i, a_i, alpha_i */
+  const double *radius;   /* device [n_links] */
+} mf_robot;
+
+#define MF_BOX 0
+#define MF_SPHERE 1
+typedef struct {
+  int32_t n;
+  const int32_t *type;    /* device [n]: MF_BOX / MF_SPHERE */
+  const double *pose;     /* device [n][12]: rotation R (row-major, obstacle frame
+                             -> world) followed by the translation t */
+  const double *dims;     /* device [n][3]: box side lengths; sphere radius in [0] */
+} mf_scene;
+
+/* Creates a context on `device` whose resident allocations never exceed
+ * hbm_budget_bytes (0 = 90% of free memory).  *out receives the context. */
+int mf_ctx_create(int device, size_t hbm_budget_bytes, mf_ctx **out);
+void mf_ctx_destroy(mf_ctx *ctx);
+/* One-line description of the last error on this context ("" if none). */
+const char *mf_last_error(mf_ctx *ctx);
+/* Device bytes currently held by the context. */
+size_t mf_ctx_bytes(mf_ctx *ctx);
+
+/* Query type 1 (Sec. IV-A): the n-simplex of the Ã_d triangulation holding
+ * each point.  points: device [n][d]; y_out: device [n][d] vertex; perm_out:
+ * device [n][d] the singleton parts in walk order before {d}.  Ties among the
+ * fractional lattice coordinates go to the lower index. */
+int mf_locate(mf_ctx *ctx, int32_t d, double lambda, const double *offset_host,
+              const double *points, int64_t n, int32_t *y_out, uint8_t *perm_out, void *stream);
+
+/* f at n arbitrary points (the RBF kernel evaluation of the traced path).
+ * q: device [n][d]; f_out: device [n].  precision as in mf_trace_opts; the
+ * mixed paths apply the same FP64 recheck band (band <= 0 means 1e-3). */
+int mf_eval(mf_ctx *ctx, const mf_rbf *rbf, const double *q, int64_t n, int32_t precision,
+            double band, double *f_out, void *stream);
+
+/* Manifold tracing (Sec. IV-A, Figs. 3-4) from n_seeds points: locate each
+ * seed's n-simplex, keep its crossing edges, then breadth-first search over
+ * shared 2-simplex cofaces until the frontier is empty; then the root of f
+ * on every traced edge and the crossing n-simplices (Sec. IV-C).
+ * seeds: device [n_seeds][d]. */
+int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom, const mf_trace_opts *opts,
+             const double *seeds, int64_t n_seeds, mf_trace_out *out, void *stream);
+
+/* Copies the last mf_trace result of this context into `out` (two-call
+ * pattern after MF_ERR_CAPACITY). */
+int mf_trace_fetch(mf_ctx *ctx, mf_trace_out *out, void *stream);
+
+/* Certification (Sec. V-C, App. A): forward kinematics of every point, exact
+ * capsule/box and capsule/sphere distances, per-point margin
+ * max_{link,obstacle}(radius - distance) and verdict (1 = in collision, i.e.
+ * the point is in C_obs, iff margin >= 0), and per cell the AND of the
+ * verdicts of its points.  points: device [n_points][d]; cell CSR: device
+ * (n_cells may be 0 and the CSR pointers NULL); outputs: device
+ * point_verdict [n_points], margin [n_points], cell_verdict [n_cells]. */
+int mf_certify(mf_ctx *ctx, const mf_robot *robot, const mf_scene *scene, const double *points,
+               int64_t n_points, int32_t d, const int64_t *cell_edge_off,
+               const int64_t *cell_edge_idx, int64_t n_cells, uint8_t *point_verdict,
+               double *margin, uint8_t *cell_verdict, void *stream);
+
+/* Native per-phase profiling (CUDA events recorded on the call's stream
+ * around every kernel launch of the library; no effect on results). */
+#define MF_PHASES 12
+enum {
+  MF_PH_PREPARE = 0,   /* RBF preparation */
+  MF_PH_SEEDS = 1,     /* locate edges (Fig. 3) */
+  MF_PH_EXPAND_V = 2,  /* BFS: new vertices of 2-cofaces */
+  MF_PH_EVAL = 3,      /* f at new vertices (incl. FP64 recheck) */
+  MF_PH_EXPAND_E = 4,  /* BFS: new crossing edges, dedup */
+  MF_PH_ROOTS = 5,     /* root solve on every traced edge */
+  MF_PH_CELLS = 6,     /* n-cofaces of traced edges, dedup */
+  MF_PH_CSR = 7,       /* cell -> edge CSR (count, scan, fill) */
+  MF_PH_COPY = 8,      /* copies into caller buffers */
+  MF_PH_CERT_PTS = 9,  /* FK + capsule/obstacle distances */
+  MF_PH_CERT_CELLS = 10,
+  MF_PH_OTHER = 11
+};
+typedef struct {
+  double ms[MF_PHASES];        /* device time summed over the phase's launches */
+  int64_t launches[MF_PHASES]; /* kernel launches of the phase */
+  int64_t units[MF_PHASES];    /* work items: seeds, frontier edges, edges solved, points ... */
+  int64_t terms[MF_PHASES];    /* RBF terms evaluated in FP64 (eval / roots phases) */
+} mf_stats;
+
+/* Enables (1) or disables (0) profiling on the context; enabling clears the stats. */
+int mf_ctx_set_profiling(mf_ctx *ctx, int enable);
+/* Copies the accumulated stats (zeros when profiling is off). */
+int mf_ctx_get_stats(mf_ctx *ctx, mf_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MF_H */

@@ -89,8 +89,12 @@ def lib():
         L.or_f_batch.argtypes = [P(Rbf), P(C.c_double), C.c_int64, P(C.c_double)]
         L.or_trace.restype = C.c_int
         L.or_trace.argtypes = [P(Rbf), C.c_double, P(C.c_double), P(C.c_double), P(C.c_double),
-                               P(C.c_double), C.c_int64, C.c_int, C.c_int, P(TraceResult)]
+                               P(C.c_double), C.c_int64, C.c_int, C.c_int, C.c_int64,
+                               P(TraceResult)]
         L.or_trace_free.argtypes = [P(TraceResult)]
+        L.or_edge_roots.argtypes = [P(Rbf), C.c_double, P(C.c_double), P(C.c_int32),
+                                    P(C.c_uint32), C.c_int64, P(C.c_double), P(C.c_double),
+                                    P(C.c_double), P(C.c_uint8)]
         L.or_fk.argtypes = [P(Robot), P(C.c_double), P(C.c_double)]
         L.or_segseg_dist.restype = C.c_double
         L.or_segseg_dist.argtypes = [P(C.c_double)] * 4
@@ -218,8 +222,9 @@ def _arr(ptr, n, dtype):
     return np.ctypeslib.as_array(ptr, shape=(n,)).astype(dtype, copy=True)
 
 
-def trace(sv, alpha, gamma, b, lam, o, lo, hi, seeds, roots=True, cells=True):
-    """Trace from the seeds; returns a dict of numpy arrays and counters."""
+def trace(sv, alpha, gamma, b, lam, o, lo, hi, seeds, roots=True, cells=True, max_edges=0):
+    """Trace from the seeds; returns a dict of numpy arrays and counters.
+    max_edges > 0 stops the search once that many edges exist (bounded sample)."""
     h = _RbfHold(sv, alpha, gamma, b)
     d = h.sv.shape[1]
     o, lo, hi = _f64(o), _f64(lo), _f64(hi)
@@ -227,7 +232,7 @@ def trace(sv, alpha, gamma, b, lam, o, lo, hi, seeds, roots=True, cells=True):
     r = TraceResult()
     rc = lib().or_trace(C.byref(h.s), float(lam), _p(o, C.c_double), _p(lo, C.c_double),
                         _p(hi, C.c_double), _p(seeds, C.c_double), seeds.shape[0],
-                        int(bool(roots)), int(bool(cells)), C.byref(r))
+                        int(bool(roots)), int(bool(cells)), int(max_edges), C.byref(r))
     if rc != 0:
         raise RuntimeError("oracle trace failed")
     E, Cn = r.n_edges, r.n_cells
@@ -251,6 +256,25 @@ def trace(sv, alpha, gamma, b, lam, o, lo, hi, seeds, roots=True, cells=True):
                    cell_off=off, cell_idx=_arr(r.cell_idx, int(off[-1]) if Cn else 0, np.int64))
     lib().or_trace_free(C.byref(r))
     return out
+
+
+def edge_roots(sv, alpha, gamma, b, lam, o, edge_y, edge_mask):
+    """f at both vertices, bisection root, point and multi-root flag of given edges."""
+    h = _RbfHold(sv, alpha, gamma, b)
+    d = h.sv.shape[1]
+    ey = np.ascontiguousarray(edge_y, dtype=np.int32).reshape(-1, d)
+    em = np.ascontiguousarray(edge_mask, dtype=np.uint32)
+    n = ey.shape[0]
+    o = _f64(o)
+    f2 = np.zeros((n, 2))
+    t = np.zeros(n)
+    pt = np.zeros((n, d))
+    mr = np.zeros(n, dtype=np.uint8)
+    if n:
+        lib().or_edge_roots(C.byref(h.s), float(lam), _p(o, C.c_double), _p(ey, C.c_int32),
+                            _p(em, C.c_uint32), n, _p(f2, C.c_double), _p(t, C.c_double),
+                            _p(pt, C.c_double), _p(mr, C.c_uint8))
+    return f2, t, pt, mr
 
 
 # --------------------------------------------------------------------------

@@ -442,12 +442,39 @@ static int multiroot(const or_rbf *rbf, int d, const double *x1, const double *x
   return changes > 1;
 }
 
+/* For given edges (y, p1): f at both vertices, the bisection root t, the
+ * intersection point and the multi-root flag (used to check sampled edges of
+ * a traced set too large to trace here). */
+void or_edge_roots(const or_rbf *rbf, double lam, const double *o, const int32_t *ey,
+                   const uint32_t *emask, int64_t n, double *f2, double *t, double *pt,
+                   uint8_t *mr) {
+  int d = rbf->d;
+  for (int64_t i = 0; i < n; i++) {
+    or_simplex e;
+    or_simplex_zero(&e);
+    for (int k = 0; k < d; k++) e.y[k] = ey[i * d + k];
+    e.k = 1;
+    e.part[0] = emask[i];
+    e.part[1] = ((2u << d) - 1u) & ~emask[i];
+    int32_t v[2 * OR_MAXD];
+    double x1[OR_MAXD], x2[OR_MAXD];
+    or_simplex_vertices(d, &e, v);
+    or_vertex_x(d, lam, o, v, x1);
+    or_vertex_x(d, lam, o, v + d, x2);
+    f2[2 * i] = or_f(rbf, x1);
+    f2[2 * i + 1] = or_f(rbf, x2);
+    t[i] = root_bisect(rbf, d, x1, x2, f2[2 * i]);
+    for (int k = 0; k < d; k++) pt[i * d + k] = seg_point(x1[k], x2[k], t[i]);
+    mr[i] = (uint8_t)multiroot(rbf, d, x1, x2);
+  }
+}
+
 /* Trace the zero set of f from the seeds.  Returns 0, or -1 on allocation
  * failure / bad arguments.  want_cells: also build cells and their CSR;
  * want_roots: also solve the roots. */
 int or_trace(const or_rbf *rbf, double lam, const double *o, const double *lo, const double *hi,
              const double *seeds, int64_t n_seeds, int want_roots, int want_cells,
-             or_trace_result *res) {
+             int64_t max_edges, or_trace_result *res) {
   int d = rbf->d;
   memset(res, 0, sizeof(*res));
   if (d < 2 || d > OR_MAXD || !(lam > 0.0)) return -1;
@@ -496,7 +523,8 @@ int or_trace(const or_rbf *rbf, double lam, const double *o, const double *lo, c
   {
     size_t head = 0;
     or_simplex tris[2 * (1 << OR_MAXD)];
-    while (head < eset.n) {
+    /* max_edges > 0 bounds the sample: expansion stops once that many edges exist */
+    while (head < eset.n && !(max_edges > 0 && (int64_t)eset.n >= max_edges)) {
       or_simplex e = ((or_simplex *)eset.recs)[head];
       int lev = level[head];
       head++;

@@ -1,0 +1,185 @@
+"""Torch-facing convenience layer over the C ABI (argument marshalling only).
+
+``Context`` owns one library context (its resident hash tables and lists) and
+turns numpy / torch inputs into device buffers for ``mf_trace``, ``mf_certify``,
+``mf_eval`` and ``mf_locate``.  Every computation runs in libmf.so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import mf
+
+
+def _dev(x, dtype, device):
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=dtype).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device=device)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Context:
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the GB300 library needs a CUDA device; there is no CPU path")
+        self.device = torch.device("cuda", device)
+        torch.cuda.set_device(self.device)
+        self.h = mf.mf_ctx_create(device, hbm_budget_bytes)
+
+    def close(self):
+        if self.h:
+            mf.mf_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------
+    def rbf(self, sv, alpha, gamma, b):
+        sv_t = _dev(sv, torch.float64, self.device)
+        al_t = _dev(alpha, torch.float64, self.device)
+        r = mf.mf_rbf(sv_t.shape[1], sv_t.shape[0], sv_t.data_ptr(), al_t.data_ptr(), float(gamma),
+                      float(b))
+        return r, (sv_t, al_t)
+
+    @staticmethod
+    def domain(lo, hi, offset):
+        dom = mf.mf_domain()
+        for i, v in enumerate(lo):
+            dom.lo[i] = float(v)
+        for i, v in enumerate(hi):
+            dom.hi[i] = float(v)
+        for i, v in enumerate(offset):
+            dom.offset[i] = float(v)
+        return dom
+
+    def locate(self, d, lam, offset, points, stream=None):
+        pts = _dev(points, torch.float64, self.device).reshape(-1, d)
+        n = pts.shape[0]
+        y = torch.empty((n, d), dtype=torch.int32, device=self.device)
+        perm = torch.empty((n, d), dtype=torch.uint8, device=self.device)
+        mf.mf_locate(self.h, d, float(lam), list(offset), pts.data_ptr(), n, y.data_ptr(),
+                     perm.data_ptr(), _stream_handle(stream))
+        return y, perm
+
+    def eval(self, sv, alpha, gamma, b, points, precision=mf.MF_FP64, band=1e-3, stream=None):
+        r, keep = self.rbf(sv, alpha, gamma, b)
+        pts = _dev(points, torch.float64, self.device).reshape(-1, r.d)
+        out = torch.empty(pts.shape[0], dtype=torch.float64, device=self.device)
+        mf.mf_eval(self.h, r, pts.data_ptr(), pts.shape[0], precision, band, out.data_ptr(),
+                   _stream_handle(stream))
+        return out
+
+    def trace(self, sv, alpha, gamma, b, lam, offset, lo, hi, seeds, precision=mf.MF_FP64,
+              roots=True, cells=True, batch_cap=1 << 24, max_edges=1 << 22, max_vertices=0,
+              max_cells=0, recheck_band=1e-3, root_tol=1e-12, stream=None, outputs=None):
+        """Traces the zero set; returns a dict of device tensors and counters.
+
+        ``outputs`` may hold preallocated output tensors (as returned by an
+        earlier call) to avoid allocations in timed loops."""
+        r, keep = self.rbf(sv, alpha, gamma, b)
+        d = r.d
+        dom = self.domain(lo, hi, offset)
+        seeds_t = _dev(seeds, torch.float64, self.device).reshape(-1, d)
+        opts = mf.mf_trace_opts(float(lam), int(batch_cap), int(precision), float(recheck_band),
+                                float(root_tol), int(max_edges), int(max_vertices), int(max_cells),
+                                (mf.MF_WANT_ROOTS if roots else 0) | (mf.MF_WANT_CELLS if cells else 0))
+        st = _stream_handle(stream)
+        res = outputs if outputs is not None else {}
+        out = self._out_struct(res, d)
+        rc = mf.mf_trace(self.h, r, dom, opts, seeds_t.data_ptr(), seeds_t.shape[0], out, st,
+                         check=False)
+        if rc == mf.MF_ERR_CAPACITY or (rc == mf.MF_OK and not res):
+            res = self._alloc_outputs(d, out.n_edges, out.n_cells, out.n_cell_edges)
+            out = self._out_struct(res, d)
+            mf.mf_trace_fetch(self.h, out, st)
+        elif rc != mf.MF_OK:
+            mf._check(self.h, rc)
+        E, Cn, CE = out.n_edges, out.n_cells, out.n_cell_edges
+        result = dict(
+            edge_y=res["edge_y"][:E], edge_mask=res["edge_mask"][:E], edge_f=res["edge_f"][:E],
+            edge_t=res["edge_t"][:E], points=res["points"][:E],
+            cell_y=res["cell_y"][:Cn], cell_perm=res["cell_perm"][:Cn],
+            cell_off=res["cell_off"][:Cn + 1], cell_idx=res["cell_idx"][:CE],
+            n_edges=E, n_cells=Cn, n_cell_edges=CE, n_vertices=out.n_vertices,
+            n_near_zero=out.n_near_zero, n_recheck=out.n_recheck, n_boundary=out.n_boundary,
+            n_dead_seeds=out.n_dead_seeds, levels=out.levels, root_evals=out.root_evals,
+            _buffers=res)
+        return result
+
+    def _alloc_outputs(self, d, E, Cn, CE):
+        E, Cn, CE = max(int(E), 1), max(int(Cn), 1), max(int(CE), 1)
+        dev = self.device
+        return dict(edge_y=torch.empty((E, d), dtype=torch.int32, device=dev),
+                    edge_mask=torch.empty(E, dtype=torch.int32, device=dev),
+                    edge_f=torch.empty((E, 2), dtype=torch.float64, device=dev),
+                    edge_t=torch.empty(E, dtype=torch.float64, device=dev),
+                    points=torch.empty((E, d), dtype=torch.float64, device=dev),
+                    cell_y=torch.empty((Cn, d), dtype=torch.int32, device=dev),
+                    cell_perm=torch.empty((Cn, d), dtype=torch.uint8, device=dev),
+                    cell_off=torch.empty(Cn + 1, dtype=torch.int64, device=dev),
+                    cell_idx=torch.empty(CE, dtype=torch.int64, device=dev))
+
+    @staticmethod
+    def _out_struct(res, d):
+        o = mf.mf_trace_out()
+        if res:
+            o.cap_edges = res["edge_y"].shape[0]
+            o.edge_y = res["edge_y"].data_ptr()
+            o.edge_mask = res["edge_mask"].data_ptr()
+            o.edge_f = res["edge_f"].data_ptr()
+            o.edge_t = res["edge_t"].data_ptr()
+            o.points = res["points"].data_ptr()
+            o.cap_cells = res["cell_y"].shape[0]
+            o.cell_y = res["cell_y"].data_ptr()
+            o.cell_perm = res["cell_perm"].data_ptr()
+            o.cell_edge_off = res["cell_off"].data_ptr()
+            o.cap_cell_edges = res["cell_idx"].shape[0]
+            o.cell_edge_idx = res["cell_idx"].data_ptr()
+        else:
+            # ask for everything with zero capacity: the call reports the sizes
+            o.cap_edges = 0
+            o.edge_y = C.c_void_p(1).value
+            o.cap_cells = 0
+            o.cell_y = C.c_void_p(1).value
+            o.cap_cell_edges = 0
+            o.cell_edge_idx = C.c_void_p(1).value
+        return o
+
+    def certify(self, dh, radius, types, pose, dims, points, cell_off=None, cell_idx=None,
+                stream=None):
+        dh_t = _dev(dh, torch.float64, self.device).reshape(-1, 4)
+        rad_t = _dev(radius, torch.float64, self.device)
+        ty_t = _dev(types, torch.int32, self.device)
+        po_t = _dev(pose, torch.float64, self.device).reshape(-1, 12)
+        di_t = _dev(dims, torch.float64, self.device).reshape(-1, 3)
+        d = dh_t.shape[0]
+        pts = _dev(points, torch.float64, self.device).reshape(-1, d)
+        P = pts.shape[0]
+        verdict = torch.empty(max(P, 1), dtype=torch.uint8, device=self.device)
+        margin = torch.empty(max(P, 1), dtype=torch.float64, device=self.device)
+        robot = mf.mf_robot(d, dh_t.data_ptr(), rad_t.data_ptr())
+        scene = mf.mf_scene(ty_t.shape[0], ty_t.data_ptr(), po_t.data_ptr(), di_t.data_ptr())
+        if cell_off is not None and cell_off.shape[0] > 1:
+            off_t = _dev(cell_off, torch.int64, self.device)
+            idx_t = _dev(cell_idx, torch.int64, self.device)
+            nc = off_t.shape[0] - 1
+            cv = torch.empty(nc, dtype=torch.uint8, device=self.device)
+            offp, idxp, cvp = off_t.data_ptr(), idx_t.data_ptr() if idx_t.numel() else None, cv.data_ptr()
+        else:
+            nc, offp, idxp, cvp, cv = 0, None, None, None, torch.empty(0, dtype=torch.uint8,
+                                                                        device=self.device)
+        mf.mf_certify(self.h, robot, scene, pts.data_ptr(), P, d, offp, idxp, nc, verdict.data_ptr(),
+                      margin.data_ptr(), cvp, _stream_handle(stream))
+        return verdict[:P], margin[:P], cv

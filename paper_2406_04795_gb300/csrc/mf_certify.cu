@@ -1,0 +1,218 @@
+// mf_certify.cu -- certification of traced points (Sec. V-C, App. A):
+// forward kinematics of a serial DH arm and the exact distance between each
+// link capsule and each box / sphere obstacle, in FP64.
+//
+// Capsule/box distance: in the box frame the squared distance from the
+// segment point p(t) = a + t (b - a) to the box is
+//   F(t) = sum_i max(0, |p_i(t)| - h_i)^2,
+// convex and piecewise quadratic with breakpoints where p_i(t) = +-h_i.  The
+// minimum over [0,1] is found exactly by minimising the quadratic of every
+// piece (at most 7).  This extends App. A's sphere/box test (a sphere is the
+// zero-length capsule) to capsules.
+#include <cmath>
+
+#include "mf_internal.cuh"
+#include "mf_ctx.h"
+
+#define CERT_MAX_OBS 256
+#define CERT_THREADS 128
+
+struct CertObs {
+  double R[9];
+  double t[3];
+  double h[3];  // box half extents; sphere radius in h[0]
+  int type;
+};
+
+__device__ __forceinline__ double box_F(const double *a, const double *dl, const double *h, double t) {
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    const double p = fabs(fma(t, dl[i], a[i])) - h[i];
+    if (p > 0.0) s = fma(p, p, s);
+  }
+  return s;
+}
+
+// Squared distance from segment [a, a+dl] (box frame) to the box |p_i| <= h_i.
+__device__ double seg_box_d2(const double *a, const double *dl, const double *h) {
+  double bp[8];
+  int nb = 0;
+  bp[nb++] = 0.0;
+  bp[nb++] = 1.0;
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    if (dl[i] != 0.0) {
+      const double t1 = (h[i] - a[i]) / dl[i], t2 = (-h[i] - a[i]) / dl[i];
+      if (t1 > 0.0 && t1 < 1.0) bp[nb++] = t1;
+      if (t2 > 0.0 && t2 < 1.0) bp[nb++] = t2;
+    }
+  }
+  // insertion sort (<= 8 entries)
+  for (int i = 1; i < nb; i++) {
+    const double v = bp[i];
+    int j = i - 1;
+    while (j >= 0 && bp[j] > v) { bp[j + 1] = bp[j]; j--; }
+    bp[j + 1] = v;
+  }
+  double best = box_F(a, dl, h, 0.0);
+  best = fmin(best, box_F(a, dl, h, 1.0));
+  for (int k = 0; k + 1 < nb; k++) {
+    const double ta = bp[k], tb = bp[k + 1];
+    if (!(tb > ta)) continue;
+    const double tm = 0.5 * (ta + tb);
+    double A = 0.0, Bc = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      const double p = fma(tm, dl[i], a[i]);
+      double c0;
+      if (p > h[i]) c0 = a[i] - h[i];
+      else if (p < -h[i]) c0 = a[i] + h[i];
+      else continue;
+      A = fma(dl[i], dl[i], A);
+      Bc = fma(2.0 * dl[i], c0, Bc);
+    }
+    if (A > 0.0) {
+      double ts = -Bc / (2.0 * A);
+      ts = fmin(fmax(ts, ta), tb);
+      best = fmin(best, box_F(a, dl, h, ts));
+    }
+  }
+  return best;
+}
+
+__device__ double seg_obstacle_dist(const CertObs &o, const double *pa, const double *pb) {
+  double a[3], b[3], dl[3];
+  // local = R^T (p - t)
+  const double wa[3] = {pa[0] - o.t[0], pa[1] - o.t[1], pa[2] - o.t[2]};
+  const double wb[3] = {pb[0] - o.t[0], pb[1] - o.t[1], pb[2] - o.t[2]};
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    a[i] = o.R[i] * wa[0] + o.R[3 + i] * wa[1] + o.R[6 + i] * wa[2];
+    b[i] = o.R[i] * wb[0] + o.R[3 + i] * wb[1] + o.R[6 + i] * wb[2];
+    dl[i] = b[i] - a[i];
+  }
+  if (o.type == MF_BOX) return sqrt(seg_box_d2(a, dl, o.h));
+  // sphere at the local origin: clamped projection of the centre
+  const double dd = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
+  double t = 0.0;
+  if (dd > 0.0) {
+    t = -(a[0] * dl[0] + a[1] * dl[1] + a[2] * dl[2]) / dd;
+    t = fmin(fmax(t, 0.0), 1.0);
+  }
+  const double c0 = fma(t, dl[0], a[0]), c1 = fma(t, dl[1], a[1]), c2 = fma(t, dl[2], a[2]);
+  const double dist = sqrt(c0 * c0 + c1 * c1 + c2 * c2) - o.h[0];
+  return dist > 0.0 ? dist : 0.0;
+}
+
+__global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int nl, const double *dh, const double *radius, int nobs,
+                                                    const int32_t *type, const double *pose,
+                                                    const double *dims, const double *pts,
+                                                    int64_t n, int d, uint8_t *verdict,
+                                                    double *margin) {
+  __shared__ CertObs so[CERT_MAX_OBS];
+  __shared__ double sdh[MF_MAXD * 4], srad[MF_MAXD];
+  for (int i = threadIdx.x; i < nobs; i += blockDim.x) {
+    CertObs o;
+    for (int k = 0; k < 9; k++) o.R[k] = pose[12 * i + k];
+    for (int k = 0; k < 3; k++) o.t[k] = pose[12 * i + 9 + k];
+    o.type = type[i];
+    for (int k = 0; k < 3; k++) o.h[k] = o.type == MF_BOX ? 0.5 * dims[3 * i + k] : dims[3 * i + k];
+    so[i] = o;
+  }
+  for (int i = threadIdx.x; i < nl * 4; i += blockDim.x) sdh[i] = dh[i];
+  for (int i = threadIdx.x; i < nl; i += blockDim.x) srad[i] = radius[i];
+  __syncthreads();
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  // forward kinematics: T = T * A_i with the standard DH link transform
+  double T[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};  // 3x4 row-major
+  double prev[3] = {0.0, 0.0, 0.0};
+  double best = -INFINITY;
+  for (int i = 0; i < nl; i++) {
+    const double th = pts[p * d + i] + sdh[4 * i], dd = sdh[4 * i + 1], aa = sdh[4 * i + 2],
+                 al = sdh[4 * i + 3];
+    double st, ct, sa, ca;
+    sincos(th, &st, &ct);
+    sincos(al, &sa, &ca);
+    const double A[12] = {ct, -st * ca, st * sa, aa * ct, st, ct * ca, -ct * sa, aa * st,
+                          0.0, sa, ca, dd};
+    double N[12];
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        double v = T[4 * r + 0] * A[c] + T[4 * r + 1] * A[4 + c] + T[4 * r + 2] * A[8 + c];
+        if (c == 3) v += T[4 * r + 3];
+        N[4 * r + c] = v;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 12; k++) T[k] = N[k];
+    const double cur[3] = {T[3], T[7], T[11]};
+    for (int k = 0; k < nobs; k++) {
+      const double m = srad[i] - seg_obstacle_dist(so[k], prev, cur);
+      best = fmax(best, m);
+    }
+    prev[0] = cur[0];
+    prev[1] = cur[1];
+    prev[2] = cur[2];
+  }
+  margin[p] = best;
+  verdict[p] = best >= 0.0 ? 1 : 0;
+}
+
+__global__ void k_certify_cells(const int64_t *off, const int64_t *idx, int64_t n_cells,
+                                const uint8_t *verdict, int64_t n_points, uint8_t *cell_verdict,
+                                unsigned *bad) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  uint8_t v = 1;
+  for (int64_t j = off[c]; j < off[c + 1]; j++) {
+    const int64_t i = idx[j];
+    if (i < 0 || i >= n_points) { atomicOr(bad, 1u); v = 0; break; }
+    v &= verdict[i];
+  }
+  cell_verdict[c] = v;
+}
+
+extern "C" int mf_certify(mf_ctx *ctx, const mf_robot *robot, const mf_scene *scene,
+                          const double *points, int64_t n_points, int32_t d,
+                          const int64_t *cell_off, const int64_t *cell_idx, int64_t n_cells,
+                          uint8_t *point_verdict, double *margin, uint8_t *cell_verdict,
+                          void *stream) {
+  if (!ctx) return MF_ERR_INVALID;
+  if (!robot || !scene || d < 1 || d > MF_MAXD || robot->n_links != d || n_points < 0 ||
+      n_cells < 0 || scene->n < 0 || scene->n > CERT_MAX_OBS || !robot->dh || !robot->radius ||
+      (scene->n > 0 && (!scene->type || !scene->pose || !scene->dims)) ||
+      (n_points > 0 && (!points || !point_verdict || !margin)) ||
+      (n_cells > 0 && (!cell_off || !cell_idx || !cell_verdict)))
+    return mf_set_error(ctx, MF_ERR_INVALID, "mf_certify: bad arguments");
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned *bad = (unsigned *)mf_ctx_buffer(ctx, MF_SLOT_CERT, 256);
+  if (!bad) return MF_ERR_OOM;
+  cudaMemsetAsync(bad, 0, sizeof(unsigned), st);
+  if (n_points > 0) {
+    MfProfScope ps(ctx, MF_PH_CERT_PTS, st, 1, n_points);
+    k_certify_points<<<(unsigned)((n_points + CERT_THREADS - 1) / CERT_THREADS), CERT_THREADS, 0,
+                       st>>>(robot->n_links, robot->dh, robot->radius, scene->n, scene->type,
+                             scene->pose, scene->dims, points, n_points, d, point_verdict, margin);
+  }
+  if (n_cells > 0) {
+    MfProfScope ps(ctx, MF_PH_CERT_CELLS, st, 1, n_cells);
+    k_certify_cells<<<(unsigned)((n_cells + 255) / 256), 256, 0, st>>>(
+        cell_off, cell_idx, n_cells, point_verdict, n_points, cell_verdict, bad);
+  }
+  int rc = mf_cuda_check(ctx, cudaGetLastError(), "mf_certify launch");
+  if (rc) return rc;
+  unsigned hb = 0;
+  rc = mf_cuda_check(ctx, cudaMemcpyAsync(&hb, bad, sizeof(hb), cudaMemcpyDeviceToHost, st),
+                     "mf_certify");
+  if (rc) return rc;
+  rc = mf_cuda_check(ctx, cudaStreamSynchronize(st), "mf_certify");
+  if (rc) return rc;
+  mf_prof_collect(ctx);
+  if (hb) return mf_set_error(ctx, MF_ERR_INVALID, "cell_edge_idx holds an index outside [0, n_points)");
+  return MF_OK;
+}

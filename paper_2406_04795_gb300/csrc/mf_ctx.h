@@ -1,0 +1,54 @@
+// mf_ctx.h -- host-side layout of a library context (private).
+#pragma once
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "mf_internal.cuh"
+
+// The result of the last mf_trace on a context: its frame, buffers and counts.
+struct MfTraceState {
+  bool valid = false;
+  MfFrame F;
+  MfTraceBufs B;
+  int64_t n_edges = 0, n_cells = 0, n_cell_edges = 0, n_vertices = 0, n_near_zero = 0,
+          n_recheck = 0, n_boundary = 0, n_dead_seeds = 0, levels = 0, root_evals = 0;
+  uint32_t flags = 0;
+};
+
+// Event pairs recorded around library launches while profiling is on.
+struct MfProfiler {
+  bool on = false;
+  mf_stats stats = {};
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  size_t used = 0;
+};
+
+struct mf_ctx {
+  int device = 0;
+  int sms = 0;
+  size_t budget = 0;
+  size_t total = 0;
+  std::string err;
+  void *slot_ptr[MF_NUM_SLOTS] = {};
+  size_t slot_bytes[MF_NUM_SLOTS] = {};
+  MfCounters *h_counters = nullptr;  // pinned host mirror of the device counters
+  MfTraceState last;
+  MfProfiler prof;
+};
+
+void mf_frame_lattice(MfFrame *F, int d, double lam, const double *o);
+
+// Profiling scope: records an event pair around the launches issued between
+// construction and destruction (no-op when profiling is off).
+struct MfProfScope {
+  mf_ctx *c;
+  int phase;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  MfProfScope(mf_ctx *ctx, int ph, cudaStream_t s, int launches, int64_t units = 0);
+  ~MfProfScope();
+};
+// Resolves pending event pairs into the stats (call after a stream sync).
+void mf_prof_collect(mf_ctx *c);

@@ -1,0 +1,260 @@
+// mf_internal.cuh -- device-side building blocks shared by the library's
+// translation units: the lattice frame of one trace, integer simplex keys,
+// open-addressing hash tables, and the trace's device counters.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/mf.h"
+
+#define MF_EMPTY_KEY 0xFFFFFFFFFFFFFFFFull
+
+// Lattice frame of one trace: the Ã_d realisation x = lam * (y - c * sum(y)) + o
+// (Sec. II-B; L = I - c 1 1^T, c = (1 - 1/sqrt(d+1))/d), the closed C-space box,
+// and the mixed-radix packing of lattice vertices into 64-bit keys.
+struct MfFrame {
+  int32_t d;
+  double lam, c, cinv;  // cinv = c * sqrt(d+1): L^-1 = I + cinv 1 1^T
+  double o[MF_MAXD], lo[MF_MAXD], hi[MF_MAXD];
+  int32_t ymin[MF_MAXD];    // lowest encodable lattice coordinate per axis
+  int32_t range[MF_MAXD];   // encodable values per axis
+  uint64_t stride[MF_MAXD]; // mixed-radix place value per axis
+};
+
+// Device counters of one trace; read back by the host once per BFS level.
+struct MfCounters {
+  unsigned long long n_edges;      // edges appended to the edge list
+  unsigned long long n_vertices;   // vertices appended to the vertex list
+  unsigned long long v_evaluated;  // vertex list prefix whose f is final
+  unsigned long long n_cells;
+  unsigned long long n_boundary;
+  unsigned long long n_near_zero;
+  unsigned long long n_dead_seeds;
+  unsigned long long n_recheck;    // mixed: vertices queued for FP64 recheck
+  unsigned long long n_recheck_done;
+  unsigned long long root_evals;
+  unsigned long long n_cell_edges;
+  unsigned long long eval_terms;   // RBF terms evaluated in FP64 by vertex evaluation
+  unsigned long long root_terms;   // RBF terms evaluated in FP64 by the root solve
+  unsigned int err_table_full;     // a hash probe ran past the table
+  unsigned int err_overflow;       // a list ran past its capacity
+  unsigned int err_missing;        // a vertex expected in the table was absent
+  unsigned int pad;
+};
+
+// Pointers of one trace's resident device state (all owned by the context).
+struct MfTraceBufs {
+  // edge hash table: key -> index into the edge list
+  unsigned long long *etab_key;
+  uint32_t *etab_val;
+  uint64_t etab_mask;
+  // vertex hash table: key -> f
+  unsigned long long *vtab_key;
+  double *vtab_f;
+  uint64_t vtab_mask;
+  // cell hash table (keys only; winners append to the cell list)
+  unsigned long long *ctab_key;
+  uint64_t ctab_mask;
+  // edge list (insertion order; each BFS level is a contiguous range)
+  int32_t *edge_y;     // [ME][d]
+  uint32_t *edge_mask; // [ME]
+  double *edge_f;      // [ME][2]
+  double *edge_t;      // [ME]
+  double *edge_pt;     // [ME][d]
+  uint64_t max_edges;
+  // vertex list (insertion order): lattice vertex and its table slot
+  int32_t *vert_y;     // [MV][d]
+  uint32_t *vert_slot; // [MV]
+  uint64_t max_vertices;
+  // mixed path: recheck queue of vertex-list indices
+  uint32_t *recheck;   // [MV]
+  // cell list
+  int32_t *cell_y;     // [MC][d]
+  uint8_t *cell_perm;  // [MC][d]
+  int64_t *cell_off;   // [MC+1]
+  int64_t *cell_idx;   // [MC * (d+1)d/2]
+  uint64_t max_cells;
+  MfCounters *cnt;
+};
+
+// Prepared RBF: structure-of-arrays copies for coalesced streaming.
+struct MfRbfDev {
+  int32_t d;
+  int32_t n;
+  const float *sv32;   // [d][n]
+  const double *sv64;  // [d][n]
+  const double *alpha; // [n]
+  const float *alpha32;// [n]
+  double gamma, b;
+  float screen_r2;     // keep a term in the FP64 sum iff r^2 (FP32) <= screen_r2
+  double drop_bound;   // sum_i |alpha_i| exp(-gamma * screen cut): bound on dropped terms
+  float smax;          // max |s_ik| over all support-vector coordinates
+};
+
+// ------------------------------------------------------------------------
+// Lattice arithmetic with a fixed operation order (no contraction) so that a
+// vertex's coordinates are bit-identical wherever they are computed.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ void mf_vertex_x(const MfFrame &F, const int32_t *y, double *x) {
+  long long s = 0;
+#pragma unroll
+  for (int i = 0; i < MF_MAXD; i++)
+    if (i < F.d) s += y[i];
+  const double cs = __dmul_rn(F.c, (double)s);
+#pragma unroll
+  for (int i = 0; i < MF_MAXD; i++)
+    if (i < F.d) x[i] = __dadd_rn(__dmul_rn(F.lam, __dsub_rn((double)y[i], cs)), F.o[i]);
+}
+
+__device__ __forceinline__ bool mf_in_box(const MfFrame &F, const double *x) {
+  bool in = true;
+#pragma unroll
+  for (int i = 0; i < MF_MAXD; i++)
+    if (i < F.d) in = in && (x[i] >= F.lo[i]) && (x[i] <= F.hi[i]);
+  return in;
+}
+
+__device__ __forceinline__ unsigned long long mf_vertex_key(const MfFrame &F, const int32_t *y) {
+  unsigned long long k = 0;
+#pragma unroll
+  for (int i = 0; i < MF_MAXD; i++)
+    if (i < F.d) k += (unsigned long long)(uint32_t)(y[i] - F.ymin[i]) * F.stride[i];
+  return k;
+}
+
+__device__ __forceinline__ bool mf_vertex_encodable(const MfFrame &F, const int32_t *y) {
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < MF_MAXD; i++)
+    if (i < F.d) ok = ok && (y[i] >= F.ymin[i]) && (y[i] - F.ymin[i] < F.range[i]);
+  return ok;
+}
+
+// Edge (y, p1) with p1 a non-empty mask over {0..d-1}: key = vidx * 2^d + p1.
+__device__ __forceinline__ unsigned long long mf_edge_key(const MfFrame &F, const int32_t *y,
+                                                          uint32_t mask) {
+  return (mf_vertex_key(F, y) << F.d) | (unsigned long long)mask;
+}
+
+// v += e(M) for M a mask over {0..d-1}
+__device__ __forceinline__ void mf_add_mask(int d, int32_t *v, uint32_t M, int sign) {
+#pragma unroll
+  for (int i = 0; i < MF_MAXD; i++)
+    if (i < d && ((M >> i) & 1u)) v[i] += sign;
+}
+
+// Query type 1 (Sec. IV-A): locate the n-simplex holding x.  Same operation
+// order as the inverse map y' = L^-1 (x - o) / lam; vertex = floor(y'); the walk
+// order sorts the fractional parts descending, ties to the lower index.
+__device__ __forceinline__ void mf_locate_point(const MfFrame &F, const double *x, int32_t *y,
+                                                int *perm) {
+  const int d = F.d;
+  double s = 0.0;
+  for (int j = 0; j < d; j++) s = __dadd_rn(s, __dsub_rn(x[j], F.o[j]));
+  double fr[MF_MAXD];
+  for (int i = 0; i < d; i++) {
+    double u = __dadd_rn(__dsub_rn(x[i], F.o[i]), __dmul_rn(F.cinv, s));
+    double yp = __ddiv_rn(u, F.lam);
+    double fl = floor(yp);
+    y[i] = (int32_t)fl;
+    fr[i] = __dsub_rn(yp, fl);
+    perm[i] = i;
+  }
+  for (int i = 1; i < d; i++) {
+    int p = perm[i], j = i - 1;
+    while (j >= 0 && fr[perm[j]] < fr[p]) { perm[j + 1] = perm[j]; j--; }
+    perm[j + 1] = p;
+  }
+}
+
+// ------------------------------------------------------------------------
+// Open-addressing hash tables (linear probing, 64-bit keys, atomicCAS).
+// ------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t mf_hash64(unsigned long long k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+// Insert-if-absent.  Returns the slot; *won = true iff this call inserted.
+// Returns ~0ull if the table is full (probe count exceeded its size).
+__device__ __forceinline__ uint64_t mf_table_insert(unsigned long long *keys, uint64_t mask,
+                                                    unsigned long long key, bool *won) {
+  uint64_t h = mf_hash64(key) & mask;
+  for (uint64_t probe = 0; probe <= mask; probe++) {
+    unsigned long long cur = keys[h];
+    if (cur == key) { *won = false; return h; }
+    if (cur == MF_EMPTY_KEY) {
+      unsigned long long prev = atomicCAS(&keys[h], MF_EMPTY_KEY, key);
+      if (prev == MF_EMPTY_KEY) { *won = true; return h; }
+      if (prev == key) { *won = false; return h; }
+    }
+    h = (h + 1) & mask;
+  }
+  *won = false;
+  return ~0ull;
+}
+
+// Lookup; returns the slot or ~0ull if absent.
+__device__ __forceinline__ uint64_t mf_table_find(const unsigned long long *keys, uint64_t mask,
+                                                  unsigned long long key) {
+  uint64_t h = mf_hash64(key) & mask;
+  for (uint64_t probe = 0; probe <= mask; probe++) {
+    unsigned long long cur = keys[h];
+    if (cur == key) return h;
+    if (cur == MF_EMPTY_KEY) return ~0ull;
+    h = (h + 1) & mask;
+  }
+  return ~0ull;
+}
+
+__device__ __forceinline__ float mf_warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double mf_warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------------------
+// Host-side helpers shared by the translation units (defined in mf_api.cu).
+// ------------------------------------------------------------------------
+int mf_set_error(mf_ctx *ctx, int code, const char *fmt, ...);
+int mf_cuda_check(mf_ctx *ctx, cudaError_t e, const char *what);
+// Device arena of the context: returns a 256-byte aligned region of `bytes`
+// from slot `slot` (each slot is a separately grown allocation), or NULL with
+// the error set when the budget would be exceeded.
+void *mf_ctx_buffer(mf_ctx *ctx, int slot, size_t bytes);
+int mf_ctx_sm_count(mf_ctx *ctx);
+
+// RBF preparation (mf_eval.cu): SoA FP32/FP64 copies in context buffers.
+int mf_prepare_rbf(mf_ctx *ctx, const mf_rbf *rbf, MfRbfDev *out, cudaStream_t st);
+// Evaluate f at vertex-list entries [begin, end) read from the device counter
+// (FP64 path); writes vtab_f of each vertex's slot.
+void mf_launch_eval_vertices_f64(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
+                                 int sms, cudaStream_t st);
+void mf_launch_eval_vertices_mixed(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
+                                   int precision, double band, int sms, cudaStream_t st);
+void mf_launch_roots_f64(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
+                         uint64_t n_edges, double tol, int sms, cudaStream_t st);
+
+// Context slots (each a separately grown device allocation).
+enum {
+  MF_SLOT_COUNTERS = 0,
+  MF_SLOT_RBF = 1,
+  MF_SLOT_TABLES = 2,
+  MF_SLOT_EDGES = 3,
+  MF_SLOT_VERTS = 4,
+  MF_SLOT_CELLS = 5,
+  MF_SLOT_SCAN = 6,
+  MF_SLOT_MIXED = 7,
+  MF_SLOT_CERT = 8,
+  MF_SLOT_CELLIDX = 9,
+  MF_NUM_SLOTS = 10
+};

@@ -1,0 +1,770 @@
+// mf_trace.cu -- manifold tracing over the Coxeter triangulation
+// (Sec. IV-A, Figs. 3-4), the crossing n-simplices (Sec. IV-C), and the host
+// driver of mf_trace.
+//
+// Device state of one trace (all resident in the context):
+//   edge table   key(y, p1) -> index in the edge list     (dedup, Sec. IV-A)
+//   vertex table key(y)     -> f(y)                        (each vertex evaluated once)
+//   cell table   key(z, pi)                               (dedup of n-cofaces, Sec. IV-C)
+//   edge list    insertion order; BFS level L is the contiguous range appended
+//                while level L-1 was expanded, so the list is also the queue.
+//
+// One BFS level, per frontier chunk of <= batch_cap edges:
+//   k_expand_vertices  thread per (edge, M), M a non-empty mask over {0..d-1}:
+//                      the new vertex w of every 2-simplex coface (query type 3)
+//                      is inserted into the vertex table; first inserters append
+//                      it to the vertex list.
+//   eval               f at the newly appended vertices (FP64 or mixed).
+//   k_expand_edges     same threads: sign of f(w) decides which of the coface's
+//                      two edges through w crosses (query type 4); insert it into
+//                      the edge table; first inserters append it to the edge list.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "mf_internal.cuh"
+#include "mf_ctx.h"
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_y(const int32_t *src, int d, int32_t *y) {
+#pragma unroll
+  for (int k = 0; k < MF_MAXD; k++) y[k] = k < d ? src[k] : 0;
+}
+
+// Inserts an in-domain vertex into the vertex table; first inserter appends it.
+__device__ __forceinline__ void visit_vertex(const MfFrame &F, const MfTraceBufs &B, const int32_t *w) {
+  const unsigned long long key = mf_vertex_key(F, w);
+  bool won;
+  const uint64_t slot = mf_table_insert(B.vtab_key, B.vtab_mask, key, &won);
+  if (slot == ~0ull) { atomicOr(&B.cnt->err_table_full, 1u); return; }
+  if (!won) return;
+  const unsigned long long idx = atomicAdd(&B.cnt->n_vertices, 1ull);
+  if (idx >= B.max_vertices) { atomicOr(&B.cnt->err_overflow, 1u); return; }
+#pragma unroll
+  for (int k = 0; k < MF_MAXD; k++)
+    if (k < F.d) B.vert_y[idx * F.d + k] = w[k];
+  B.vert_slot[idx] = (uint32_t)slot;
+}
+
+__device__ __forceinline__ double lookup_f(const MfFrame &F, const MfTraceBufs &B, const int32_t *w) {
+  const uint64_t slot = mf_table_find(B.vtab_key, B.vtab_mask, mf_vertex_key(F, w));
+  if (slot == ~0ull) { atomicOr(&B.cnt->err_missing, 1u); return 0.0; }
+  return B.vtab_f[slot];
+}
+
+// Appends edge (y, mask) with end values (fa at y, fb at y + e(mask)) if new.
+__device__ __forceinline__ void emit_edge(const MfFrame &F, const MfTraceBufs &B, const int32_t *y,
+                                          uint32_t mask, double fa, double fb) {
+  const unsigned long long key = mf_edge_key(F, y, mask);
+  bool won;
+  const uint64_t slot = mf_table_insert(B.etab_key, B.etab_mask, key, &won);
+  if (slot == ~0ull) { atomicOr(&B.cnt->err_table_full, 1u); return; }
+  if (!won) return;
+  const unsigned long long idx = atomicAdd(&B.cnt->n_edges, 1ull);
+  if (idx >= B.max_edges) { atomicOr(&B.cnt->err_overflow, 1u); return; }
+#pragma unroll
+  for (int k = 0; k < MF_MAXD; k++)
+    if (k < F.d) B.edge_y[idx * F.d + k] = y[k];
+  B.edge_mask[idx] = mask;
+  B.edge_f[2 * idx] = fa;
+  B.edge_f[2 * idx + 1] = fb;
+  B.etab_val[slot] = (uint32_t)idx;
+}
+
+__device__ __forceinline__ bool vertex_in(const MfFrame &F, const int32_t *v) {
+  double x[MF_MAXD];
+  mf_vertex_x(F, v, x);
+  return mf_in_box(F, x);
+}
+
+// ---------------------------------------------------------------------------
+// Locate edges (Fig. 3): seed -> n-simplex (query type 1) -> its vertices.
+// ---------------------------------------------------------------------------
+__global__ void k_seed_vertices(MfFrame F, MfTraceBufs B, const double *seeds, int64_t n) {
+  constexpr bool DEAD_COUNT = false;
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int d = F.d;
+  double x[MF_MAXD];
+  bool finite = true;
+  for (int k = 0; k < d; k++) {
+    x[k] = seeds[s * d + k];
+    finite = finite && isfinite(x[k]) && fabs(x[k]) < 1e12;
+  }
+  if (!finite) {  // a non-finite seed locates nothing; it counts as dead
+    if (DEAD_COUNT) atomicAdd(&B.cnt->n_dead_seeds, 1ull);
+    return;
+  }
+  int32_t v[MF_MAXD];
+  int perm[MF_MAXD];
+  mf_locate_point(F, x, v, perm);
+  for (int j = 0; j <= d; j++) {
+    if (vertex_in(F, v)) visit_vertex(F, B, v);
+    if (j < d) v[perm[j]] += 1;
+  }
+}
+
+// The (d+1)d/2 edges of each seed's n-simplex (query type 2) that cross.
+__global__ void k_seed_edges(MfFrame F, MfTraceBufs B, const double *seeds, int64_t n) {
+  constexpr bool DEAD_COUNT = true;
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int d = F.d;
+  double x[MF_MAXD];
+  bool finite = true;
+  for (int k = 0; k < d; k++) {
+    x[k] = seeds[s * d + k];
+    finite = finite && isfinite(x[k]) && fabs(x[k]) < 1e12;
+  }
+  if (!finite) {  // a non-finite seed locates nothing; it counts as dead
+    if (DEAD_COUNT) atomicAdd(&B.cnt->n_dead_seeds, 1ull);
+    return;
+  }
+  int32_t y[MF_MAXD];
+  int perm[MF_MAXD];
+  mf_locate_point(F, x, y, perm);
+  bool any = false;
+  int32_t vi[MF_MAXD];
+  load_y(y, d, vi);
+  for (int i = 0; i < d; i++) {
+    const bool in_i = vertex_in(F, vi);
+    const double fi = in_i ? lookup_f(F, B, vi) : 0.0;
+    uint32_t mask = 0;
+    int32_t vj[MF_MAXD];
+    load_y(vi, d, vj);
+    for (int j = i + 1; j <= d; j++) {
+      mask |= 1u << perm[j - 1];
+      vj[perm[j - 1]] += 1;
+      if (!in_i || !vertex_in(F, vj)) continue;
+      const double fj = lookup_f(F, B, vj);
+      if ((fi >= 0.0) == (fj >= 0.0)) continue;
+      any = true;
+      emit_edge(F, B, vi, mask, fi, fj);
+    }
+    vi[perm[i]] += 1;
+  }
+  if (!any) atomicAdd(&B.cnt->n_dead_seeds, 1ull);
+}
+
+// ---------------------------------------------------------------------------
+// Search edges (Fig. 4).  For edge (y, S), S = p1, T = {0..d-1} \ S, the
+// 2-simplex cofaces (query type 3, ordered two-set partitions of p1 and of
+// p2 = T + {d}) are, for each non-empty mask M:
+//   M a proper subset of S : triangle (y, (M, S\M, p2)),          new vertex y + e(M)
+//   M a subset of T        : triangle (y, (S, M, rest)),          new vertex y + e(S) + e(M)
+//                            triangle (y - e(M), (M, S, rest)),    new vertex y - e(M)
+// ---------------------------------------------------------------------------
+__global__ void k_expand_vertices(MfFrame F, MfTraceBufs B, uint64_t e0, uint64_t n) {
+  const int d = F.d;
+  const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t ei = tid >> d;
+  const uint32_t M = (uint32_t)(tid & ((1u << d) - 1u));
+  if (ei >= n || M == 0) return;
+  const uint64_t e = e0 + ei;
+  int32_t y[MF_MAXD], w[MF_MAXD];
+  load_y(B.edge_y + e * d, d, y);
+  const uint32_t S = B.edge_mask[e];
+  unsigned nb = 0;
+  if ((M & ~S) == 0 && M != S) {
+    load_y(y, d, w);
+    mf_add_mask(d, w, M, 1);
+    if (vertex_in(F, w)) visit_vertex(F, B, w); else nb++;
+  }
+  if ((M & S) == 0) {
+    load_y(y, d, w);
+    mf_add_mask(d, w, S | M, 1);
+    if (vertex_in(F, w)) visit_vertex(F, B, w); else nb++;
+    load_y(y, d, w);
+    mf_add_mask(d, w, M, -1);
+    if (vertex_in(F, w)) visit_vertex(F, B, w); else nb++;
+  }
+  if (nb) atomicAdd(&B.cnt->n_boundary, (unsigned long long)nb);
+}
+
+// Under the sign rule s = [f >= 0] a crossing triangle has exactly two
+// crossing edges (Sec. IV-A): the parent and the one joining the new vertex w
+// to the parent end whose sign differs from s(w).
+__global__ void k_expand_edges(MfFrame F, MfTraceBufs B, uint64_t e0, uint64_t n) {
+  const int d = F.d;
+  const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t ei = tid >> d;
+  const uint32_t M = (uint32_t)(tid & ((1u << d) - 1u));
+  if (ei >= n || M == 0) return;
+  const uint64_t e = e0 + ei;
+  int32_t y[MF_MAXD], w[MF_MAXD], u[MF_MAXD];
+  load_y(B.edge_y + e * d, d, y);
+  const uint32_t S = B.edge_mask[e];
+  const double f0 = B.edge_f[2 * e], f1 = B.edge_f[2 * e + 1];
+  const bool s0 = f0 >= 0.0;
+  if ((M & ~S) == 0 && M != S) {
+    load_y(y, d, w);
+    mf_add_mask(d, w, M, 1);
+    if (vertex_in(F, w)) {
+      const double fw = lookup_f(F, B, w);
+      if ((fw >= 0.0) != s0) emit_edge(F, B, y, M, f0, fw);
+      else emit_edge(F, B, w, S & ~M, fw, f1);
+    }
+  }
+  if ((M & S) == 0) {
+    load_y(y, d, w);
+    mf_add_mask(d, w, S | M, 1);
+    if (vertex_in(F, w)) {
+      const double fw = lookup_f(F, B, w);
+      if ((fw >= 0.0) != s0) emit_edge(F, B, y, S | M, f0, fw);
+      else {
+        load_y(y, d, u);
+        mf_add_mask(d, u, S, 1);
+        emit_edge(F, B, u, M, f1, fw);
+      }
+    }
+    load_y(y, d, w);
+    mf_add_mask(d, w, M, -1);
+    if (vertex_in(F, w)) {
+      const double fw = lookup_f(F, B, w);
+      if ((fw >= 0.0) != s0) emit_edge(F, B, w, M, fw, f0);
+      else emit_edge(F, B, w, M | S, fw, f1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cells (Sec. IV-C): the |p1|!|p2|! n-simplex cofaces of every traced edge,
+// de-duplicated through the cell table.  Coface j orders p1's elements by the
+// Lehmer code j mod |p1|! and p2's by j / |p1|!; the walk is then rotated so
+// that d comes last: vertex z = y + sum_{i<pos(d)} e_sigma_i - 1.
+// Key = rank(pi) + d! * key(z).
+// ---------------------------------------------------------------------------
+__constant__ uint32_t c_fact[13] = {1u, 1u, 2u, 6u, 24u, 120u, 720u, 5040u, 40320u, 362880u,
+                                    3628800u, 39916800u, 479001600u};
+
+__device__ __forceinline__ uint32_t perm_rank(const int *pi, int d) {
+  uint32_t r = 0;
+  for (int i = 0; i < d; i++) {
+    int less = 0;
+    for (int k = i + 1; k < d; k++) less += pi[k] < pi[i];
+    r += (uint32_t)less * c_fact[d - 1 - i];
+  }
+  return r;
+}
+
+__global__ void k_cells_enum(MfFrame F, MfTraceBufs B, uint64_t n_edges) {
+  const int d = F.d;
+  const int lane = threadIdx.x & 31;
+  const uint64_t e = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  if (e >= n_edges) return;
+  int32_t y[MF_MAXD];
+  load_y(B.edge_y + e * d, d, y);
+  const uint32_t S = B.edge_mask[e];
+  int ls[MF_MAXD + 1], lt[MF_MAXD + 1], n1 = 0, n2 = 0;
+  for (int i = 0; i <= d; i++) {
+    if (i < d && ((S >> i) & 1u)) ls[n1++] = i;
+    else lt[n2++] = i;
+  }
+  const uint32_t f1 = c_fact[n1], total = f1 * c_fact[n2];
+  const unsigned long long dfact = c_fact[d];
+  for (uint32_t j = lane; j < total; j += 32) {
+    int sigma[MF_MAXD + 1];
+    // Lehmer decode of each part
+    {
+      int pool[MF_MAXD + 1];
+      uint32_t r = j % f1;
+      for (int i = 0; i < n1; i++) pool[i] = ls[i];
+      for (int i = 0; i < n1; i++) {
+        const uint32_t f = c_fact[n1 - 1 - i], q = r / f;
+        r -= q * f;
+        sigma[i] = pool[q];
+        for (int k = q; k < n1 - 1 - i; k++) pool[k] = pool[k + 1];
+      }
+      r = j / f1;
+      for (int i = 0; i < n2; i++) pool[i] = lt[i];
+      for (int i = 0; i < n2; i++) {
+        const uint32_t f = c_fact[n2 - 1 - i], q = r / f;
+        r -= q * f;
+        sigma[n1 + i] = pool[q];
+        for (int k = q; k < n2 - 1 - i; k++) pool[k] = pool[k + 1];
+      }
+    }
+    int p = 0;
+    while (sigma[p] != d) p++;
+    int32_t z[MF_MAXD];
+    load_y(y, d, z);
+    for (int i = 0; i < p; i++) z[sigma[i]] += 1;
+    for (int k = 0; k < d; k++) z[k] -= 1;
+    int pi[MF_MAXD];
+    int m = 0;
+    for (int i = p + 1; i <= d; i++) pi[m++] = sigma[i];
+    for (int i = 0; i < p; i++) pi[m++] = sigma[i];
+    const unsigned long long key = (unsigned long long)perm_rank(pi, d) + dfact * mf_vertex_key(F, z);
+    bool won;
+    const uint64_t slot = mf_table_insert(B.ctab_key, B.ctab_mask, key, &won);
+    if (slot == ~0ull) { atomicOr(&B.cnt->err_table_full, 1u); continue; }
+    if (!won) continue;
+    const unsigned long long idx = atomicAdd(&B.cnt->n_cells, 1ull);
+    if (idx >= B.max_cells) { atomicOr(&B.cnt->err_overflow, 1u); continue; }
+    for (int k = 0; k < d; k++) {
+      B.cell_y[idx * d + k] = z[k];
+      B.cell_perm[idx * d + k] = (uint8_t)pi[k];
+    }
+  }
+}
+
+// Cell -> traced edges: the (d+1)d/2 edges of the cell (query type 2) found
+// in the edge table.  FILL = false counts, FILL = true writes indices.
+template <bool FILL>
+__global__ void k_cells_edges(MfFrame F, MfTraceBufs B, uint64_t n_cells, int64_t *cnt_or_off) {
+  const int d = F.d;
+  const uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  int32_t vi[MF_MAXD];
+  int pi[MF_MAXD];
+  load_y(B.cell_y + c * d, d, vi);
+  for (int k = 0; k < d; k++) pi[k] = B.cell_perm[c * d + k];
+  int64_t pos = FILL ? cnt_or_off[c] : 0;
+  int64_t count = 0;
+  for (int i = 0; i < d; i++) {
+    int32_t vj[MF_MAXD];
+    load_y(vi, d, vj);
+    uint32_t mask = 0;
+    for (int j = i + 1; j <= d; j++) {
+      mask |= 1u << pi[j - 1];
+      vj[pi[j - 1]] += 1;
+      const uint64_t slot = mf_table_find(B.etab_key, B.etab_mask, mf_edge_key(F, vi, mask));
+      if (slot == ~0ull) continue;
+      if (FILL) B.cell_idx[pos + count] = (int64_t)B.etab_val[slot];
+      count++;
+    }
+    vi[pi[i]] += 1;
+  }
+  if (!FILL) cnt_or_off[c] = count;
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of int64 counts (three passes): per-tile scans, a scan of the
+// tile totals, and the tile offsets added back.  out[n] receives the total.
+// ---------------------------------------------------------------------------
+#define SCAN_THREADS 512
+#define SCAN_PER_THREAD 8
+#define SCAN_TILE (SCAN_THREADS * SCAN_PER_THREAD)
+
+__device__ int64_t block_exclusive_scan(int64_t v, int64_t *total) {
+  __shared__ int64_t warp_tot[SCAN_THREADS / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += t;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int64_t t = lane < SCAN_THREADS / 32 ? warp_tot[lane] : 0;
+    int64_t s = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t u = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += u;
+    }
+    if (lane < SCAN_THREADS / 32) warp_tot[lane] = s - t;
+    if (lane == 31) *total = s;
+  }
+  __syncthreads();
+  const int64_t r = x - v + warp_tot[w];
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_scan_tiles(const int64_t *in, int64_t *out, int64_t n, int64_t *tile_tot) {
+  __shared__ int64_t tot;
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_PER_THREAD;
+  int64_t v[SCAN_PER_THREAD], s = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_PER_THREAD; i++) {
+    v[i] = base + i < n ? in[base + i] : 0;
+    s += v[i];
+  }
+  int64_t off = block_exclusive_scan(s, &tot);
+#pragma unroll
+  for (int i = 0; i < SCAN_PER_THREAD; i++) {
+    if (base + i < n) out[base + i] = off;
+    off += v[i];
+  }
+  if (threadIdx.x == 0) tile_tot[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_totals(int64_t *tile_tot, int64_t ntiles, int64_t *grand) {
+  __shared__ int64_t tot;
+  int64_t carry = 0;
+  for (int64_t b = 0; b < ntiles; b += SCAN_THREADS) {
+    const int64_t i = b + threadIdx.x;
+    const int64_t v = i < ntiles ? tile_tot[i] : 0;
+    const int64_t ex = block_exclusive_scan(v, &tot);
+    if (i < ntiles) tile_tot[i] = ex + carry;
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *grand = carry;
+}
+
+__global__ void k_scan_add(int64_t *out, int64_t n, const int64_t *tile_tot) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] += tile_tot[i / SCAN_TILE];
+}
+
+// in and out may alias.  scratch: ceil(n / SCAN_TILE) + 1 int64.
+static void exclusive_scan(const int64_t *in, int64_t *out, int64_t n, int64_t *scratch,
+                           cudaStream_t st) {
+  const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (ntiles == 0) {
+    cudaMemsetAsync(out, 0, sizeof(int64_t), st);
+    return;
+  }
+  k_scan_tiles<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(in, out, n, scratch);
+  k_scan_totals<<<1, SCAN_THREADS, 0, st>>>(scratch, ntiles, out + n);
+  k_scan_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n, scratch);
+}
+
+// ---------------------------------------------------------------------------
+// Host driver
+// ---------------------------------------------------------------------------
+static uint64_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// Builds the frame: lattice constants, the box, and the key packing.  The box
+// maps under L^-1 to per-axis lattice ranges; a margin of 3 covers the
+// vertices of n-cofaces and rounding.  Fails if keys do not fit 64 bits.
+static int build_frame(mf_ctx *ctx, int d, double lam, const mf_domain *dom, MfFrame *F) {
+  mf_frame_lattice(F, d, lam, dom->offset);
+  double slo = 0.0, shi = 0.0;
+  for (int j = 0; j < d; j++) {
+    if (!(dom->lo[j] <= dom->hi[j]) || !std::isfinite(dom->lo[j]) || !std::isfinite(dom->hi[j]) ||
+        !std::isfinite(dom->offset[j]))
+      return mf_set_error(ctx, MF_ERR_INVALID, "bad domain on axis %d", j);
+    F->lo[j] = dom->lo[j];
+    F->hi[j] = dom->hi[j];
+    slo += dom->lo[j] - dom->offset[j];
+    shi += dom->hi[j] - dom->offset[j];
+  }
+  unsigned __int128 prod = 1;
+  for (int i = 0; i < d; i++) {
+    const double a = ((dom->lo[i] - dom->offset[i]) + F->cinv * slo) / lam;
+    const double b = ((dom->hi[i] - dom->offset[i]) + F->cinv * shi) / lam;
+    if (!(std::fabs(a) < 1e9 && std::fabs(b) < 1e9))
+      return mf_set_error(ctx, MF_ERR_DOMAIN, "lattice range too large on axis %d", i);
+    const long long ymin = (long long)std::floor(a) - 3, ymax = (long long)std::ceil(b) + 3;
+    F->ymin[i] = (int32_t)ymin;
+    F->range[i] = (int32_t)(ymax - ymin + 1);
+    F->stride[i] = (uint64_t)prod;
+    prod *= (unsigned __int128)F->range[i];
+    if (prod > ((unsigned __int128)1 << 62))
+      return mf_set_error(ctx, MF_ERR_DOMAIN, "lattice keys need more than 64 bits");
+  }
+  unsigned __int128 fact = 1;
+  for (int i = 2; i <= d; i++) fact *= i;
+  const unsigned __int128 lim = ((unsigned __int128)1 << 64) - 2;
+  if ((prod << d) > lim || prod * fact > lim)
+    return mf_set_error(ctx, MF_ERR_DOMAIN,
+                        "edge/cell keys need more than 64 bits (domain too large for lambda)");
+  return MF_OK;
+}
+
+static int read_counters(mf_ctx *ctx, const MfTraceBufs &B, cudaStream_t st) {
+  int rc = mf_cuda_check(ctx, cudaMemcpyAsync(ctx->h_counters, B.cnt, sizeof(MfCounters),
+                                              cudaMemcpyDeviceToHost, st),
+                         "read counters");
+  if (rc) return rc;
+  rc = mf_cuda_check(ctx, cudaStreamSynchronize(st), "trace kernels");
+  if (rc) return rc;
+  const MfCounters &h = *ctx->h_counters;
+  if (h.err_table_full)
+    return mf_set_error(ctx, MF_ERR_DEVICE, "a resident hash table is full");
+  if (h.err_missing)
+    return mf_set_error(ctx, MF_ERR_DEVICE, "vertex missing from the vertex table");
+  if (h.err_overflow || h.n_edges > B.max_edges || h.n_vertices > B.max_vertices ||
+      h.n_cells > B.max_cells)
+    return mf_set_error(ctx, MF_ERR_MAXEDGES,
+                        "traced set exceeds capacity (edges %llu/%llu, vertices %llu/%llu, "
+                        "cells %llu/%llu)",
+                        h.n_edges, (unsigned long long)B.max_edges, h.n_vertices,
+                        (unsigned long long)B.max_vertices, h.n_cells,
+                        (unsigned long long)B.max_cells);
+  return MF_OK;
+}
+
+// Carves the trace's buffers from the context slots.
+static int setup_buffers(mf_ctx *ctx, int d, uint64_t ME, uint64_t MV, uint64_t MC, bool mixed,
+                         MfTraceBufs *B) {
+  memset(B, 0, sizeof(*B));
+  // load factor <= 3/4 at capacity
+  const uint64_t TE = next_pow2(ME + ME / 3 + 1), TV = next_pow2(MV + MV / 3 + 1),
+                 TC = next_pow2(MC + MC / 3 + 1);
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  size_t tb = al(TE * 8) + al(TE * 4) + al(TV * 8) + al(TV * 8) + al(TC * 8);
+  char *t = (char *)mf_ctx_buffer(ctx, MF_SLOT_TABLES, tb);
+  if (!t) return MF_ERR_OOM;
+  B->etab_key = (unsigned long long *)t; t += al(TE * 8);
+  B->etab_val = (uint32_t *)t; t += al(TE * 4);
+  B->vtab_key = (unsigned long long *)t; t += al(TV * 8);
+  B->vtab_f = (double *)t; t += al(TV * 8);
+  B->ctab_key = (unsigned long long *)t;
+  B->etab_mask = TE - 1;
+  B->vtab_mask = TV - 1;
+  B->ctab_mask = TC - 1;
+  size_t eb = al(ME * d * 4) + al(ME * 4) + al(ME * 16) + al(ME * 8) + al(ME * d * 8);
+  char *e = (char *)mf_ctx_buffer(ctx, MF_SLOT_EDGES, eb);
+  if (!e) return MF_ERR_OOM;
+  B->edge_y = (int32_t *)e; e += al(ME * d * 4);
+  B->edge_mask = (uint32_t *)e; e += al(ME * 4);
+  B->edge_f = (double *)e; e += al(ME * 16);
+  B->edge_t = (double *)e; e += al(ME * 8);
+  B->edge_pt = (double *)e;
+  B->max_edges = ME;
+  size_t vb = al(MV * d * 4) + al(MV * 4) + (mixed ? al(MV * 4) : 0);
+  char *v = (char *)mf_ctx_buffer(ctx, MF_SLOT_VERTS, vb);
+  if (!v) return MF_ERR_OOM;
+  B->vert_y = (int32_t *)v; v += al(MV * d * 4);
+  B->vert_slot = (uint32_t *)v; v += al(MV * 4);
+  B->recheck = mixed ? (uint32_t *)v : nullptr;
+  B->max_vertices = MV;
+  size_t cb = al(MC * d * 4) + al(MC * d) + al((MC + 1) * 8);
+  char *c = (char *)mf_ctx_buffer(ctx, MF_SLOT_CELLS, cb);
+  if (!c) return MF_ERR_OOM;
+  B->cell_y = (int32_t *)c; c += al(MC * d * 4);
+  B->cell_perm = (uint8_t *)c; c += al(MC * d);
+  B->cell_off = (int64_t *)c;
+  B->max_cells = MC;
+  B->cnt = (MfCounters *)mf_ctx_buffer(ctx, MF_SLOT_COUNTERS, sizeof(MfCounters));
+  if (!B->cnt) return MF_ERR_OOM;
+  return MF_OK;
+}
+
+static int copy_out(mf_ctx *ctx, const MfTraceState &L, mf_trace_out *out, cudaStream_t st) {
+  const int d = L.F.d;
+  out->n_edges = L.n_edges;
+  out->n_cells = L.n_cells;
+  out->n_cell_edges = L.n_cell_edges;
+  out->n_vertices = L.n_vertices;
+  out->n_near_zero = L.n_near_zero;
+  out->n_recheck = L.n_recheck;
+  out->n_boundary = L.n_boundary;
+  out->n_dead_seeds = L.n_dead_seeds;
+  out->levels = L.levels;
+  out->root_evals = L.root_evals;
+  const MfTraceBufs &B = L.B;
+  bool small = false;
+  const size_t E = (size_t)L.n_edges;
+  auto cp = [&](void *dst, const void *src, size_t bytes) {
+    if (dst && bytes) cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st);
+  };
+  if (out->edge_y || out->edge_mask || out->edge_f || out->edge_t || out->points) {
+    if (out->cap_edges < L.n_edges) small = true;
+    else {
+      cp(out->edge_y, B.edge_y, E * d * 4);
+      cp(out->edge_mask, B.edge_mask, E * 4);
+      cp(out->edge_f, B.edge_f, E * 16);
+      if (L.flags & MF_WANT_ROOTS) {
+        cp(out->edge_t, B.edge_t, E * 8);
+        cp(out->points, B.edge_pt, E * d * 8);
+      }
+    }
+  }
+  if ((L.flags & MF_WANT_CELLS) && (out->cell_y || out->cell_perm || out->cell_edge_off)) {
+    if (out->cap_cells < L.n_cells) small = true;
+    else {
+      const size_t C = (size_t)L.n_cells;
+      cp(out->cell_y, B.cell_y, C * d * 4);
+      cp(out->cell_perm, B.cell_perm, C * d);
+      cp(out->cell_edge_off, B.cell_off, (C + 1) * 8);
+    }
+  }
+  if ((L.flags & MF_WANT_CELLS) && out->cell_edge_idx) {
+    if (out->cap_cell_edges < L.n_cell_edges) small = true;
+    else cp(out->cell_edge_idx, B.cell_idx, (size_t)L.n_cell_edges * 8);
+  }
+  int rc = mf_cuda_check(ctx, cudaStreamSynchronize(st), "copy out");
+  if (rc) return rc;
+  if (small)
+    return mf_set_error(ctx, MF_ERR_CAPACITY,
+                        "output buffers too small: need %lld edges, %lld cells, %lld cell edges",
+                        (long long)L.n_edges, (long long)L.n_cells, (long long)L.n_cell_edges);
+  return MF_OK;
+}
+
+extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
+                        const mf_trace_opts *opts, const double *seeds, int64_t n_seeds,
+                        mf_trace_out *out, void *stream) {
+  if (!ctx) return MF_ERR_INVALID;
+  ctx->last.valid = false;
+  if (!rbf || !dom || !opts || !out || n_seeds < 0 || (n_seeds > 0 && !seeds))
+    return mf_set_error(ctx, MF_ERR_INVALID, "mf_trace: NULL argument");
+  if (!(opts->lambda > 0.0) || !std::isfinite(opts->lambda))
+    return mf_set_error(ctx, MF_ERR_INVALID, "lambda must be > 0");
+  if (opts->precision != MF_FP64 && opts->precision != MF_MIXED_FP32 &&
+      opts->precision != MF_MIXED_BF16)
+    return mf_set_error(ctx, MF_ERR_INVALID, "unknown precision %d", opts->precision);
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int d = rbf->d;
+  MfRbfDev R;
+  int rc;
+  {
+    MfProfScope ps(ctx, MF_PH_PREPARE, st, 1, rbf ? rbf->n_sv : 0);
+    rc = mf_prepare_rbf(ctx, rbf, &R, st);
+  }
+  if (rc) return rc;
+  MfFrame F;
+  rc = build_frame(ctx, d, opts->lambda, dom, &F);
+  if (rc) return rc;
+  const uint64_t ME = opts->max_edges > 0 ? (uint64_t)opts->max_edges : (1ull << 24);
+  const uint64_t MV = opts->max_vertices > 0 ? (uint64_t)opts->max_vertices : ME;
+  const uint64_t MC = opts->max_cells > 0 ? (uint64_t)opts->max_cells : 2 * ME;
+  if (ME >= (1ull << 32) || MV >= (1ull << 32))
+    return mf_set_error(ctx, MF_ERR_INVALID, "max_edges / max_vertices must be < 2^32");
+  const bool mixed = opts->precision != MF_FP64;
+  MfTraceBufs B;
+  rc = setup_buffers(ctx, d, ME, MV, MC, mixed, &B);
+  if (rc) return rc;
+  const uint64_t cap = opts->batch_cap_edges > 0 ? (uint64_t)opts->batch_cap_edges : (1ull << 24);
+  const double band = opts->recheck_band > 0 ? opts->recheck_band : 1e-3;
+  const double tol = opts->root_tol > 0 ? opts->root_tol : 1e-12;
+  const int sms = ctx->sms;
+
+  cudaMemsetAsync(B.cnt, 0, sizeof(MfCounters), st);
+  cudaMemsetAsync(B.etab_key, 0xFF, (B.etab_mask + 1) * 8, st);
+  cudaMemsetAsync(B.vtab_key, 0xFF, (B.vtab_mask + 1) * 8, st);
+  if (opts->flags & MF_WANT_CELLS) cudaMemsetAsync(B.ctab_key, 0xFF, (B.ctab_mask + 1) * 8, st);
+
+  auto eval = [&]() {
+    if (mixed) mf_launch_eval_vertices_mixed(F, R, B, opts->precision, band, sms, st);
+    else mf_launch_eval_vertices_f64(F, R, B, sms, st);
+  };
+
+  // Locate edges (Fig. 3)
+  if (n_seeds > 0) {
+    const unsigned g = (unsigned)((n_seeds + 127) / 128);
+    MfProfScope ps(ctx, MF_PH_SEEDS, st, mixed ? 5 : 4, n_seeds);
+    k_seed_vertices<<<g, 128, 0, st>>>(F, B, seeds, n_seeds);
+    eval();
+    k_seed_edges<<<g, 128, 0, st>>>(F, B, seeds, n_seeds);
+  }
+  rc = mf_cuda_check(ctx, cudaGetLastError(), "seed kernels");
+  if (rc) return rc;
+  rc = read_counters(ctx, B, st);
+  if (rc) return rc;
+
+  // Search edges (Fig. 4): one level per pass, each in chunks of <= cap edges.
+  uint64_t fs = 0, fe = ctx->h_counters->n_edges;
+  int64_t levels = fe > 0 ? 1 : 0;
+  while (fe > fs) {
+    for (uint64_t a = fs; a < fe; a += cap) {
+      const uint64_t n = std::min(cap, fe - a);
+      const uint64_t threads = n << d;
+      const unsigned g = (unsigned)((threads + 255) / 256);
+      {
+        MfProfScope ps(ctx, MF_PH_EXPAND_V, st, 1, (int64_t)n);
+        k_expand_vertices<<<g, 256, 0, st>>>(F, B, a, n);
+      }
+      {
+        MfProfScope ps(ctx, MF_PH_EVAL, st, mixed ? 3 : 2);
+        eval();
+      }
+      {
+        MfProfScope ps(ctx, MF_PH_EXPAND_E, st, 1, (int64_t)n);
+        k_expand_edges<<<g, 256, 0, st>>>(F, B, a, n);
+      }
+    }
+    rc = mf_cuda_check(ctx, cudaGetLastError(), "BFS kernels");
+    if (rc) return rc;
+    rc = read_counters(ctx, B, st);
+    if (rc) return rc;
+    fs = fe;
+    fe = ctx->h_counters->n_edges;
+    if (fe > fs) levels++;
+  }
+  const uint64_t E = fe;
+
+  // Roots (the iterative intersection solve of Sec. VI), FP64 Newton.
+  if (opts->flags & MF_WANT_ROOTS) {
+    MfProfScope ps(ctx, MF_PH_ROOTS, st, E > 0 ? 1 : 0, (int64_t)E);
+    mf_launch_roots_f64(F, R, B, E, tol, sms, st);
+  }
+
+  // Cells (Sec. IV-C) and the cell -> edge CSR.
+  int64_t n_cells = 0, n_cell_edges = 0;
+  if ((opts->flags & MF_WANT_CELLS) && E > 0) {
+    {
+      MfProfScope ps(ctx, MF_PH_CELLS, st, 1, (int64_t)E);
+      k_cells_enum<<<(unsigned)((E * 32 + 255) / 256), 256, 0, st>>>(F, B, E);
+    }
+    rc = mf_cuda_check(ctx, cudaGetLastError(), "cell kernels");
+    if (rc) return rc;
+    rc = read_counters(ctx, B, st);
+    if (rc) return rc;
+    n_cells = (int64_t)ctx->h_counters->n_cells;
+    const unsigned g = (unsigned)((n_cells + 255) / 256);
+    int64_t *scratch = (int64_t *)mf_ctx_buffer(ctx, MF_SLOT_SCAN,
+                                                ((size_t)n_cells / SCAN_TILE + 2) * 8);
+    if (!scratch) return MF_ERR_OOM;
+    {
+      MfProfScope ps(ctx, MF_PH_CSR, st, 4, n_cells);
+      k_cells_edges<false><<<g, 256, 0, st>>>(F, B, (uint64_t)n_cells, B.cell_off);
+      exclusive_scan(B.cell_off, B.cell_off, n_cells, scratch, st);
+    }
+    rc = mf_cuda_check(ctx, cudaMemcpyAsync(&n_cell_edges, B.cell_off + n_cells, 8,
+                                            cudaMemcpyDeviceToHost, st),
+                       "cell totals");
+    if (rc) return rc;
+    rc = mf_cuda_check(ctx, cudaStreamSynchronize(st), "cell scan");
+    if (rc) return rc;
+    B.cell_idx = (int64_t *)mf_ctx_buffer(ctx, MF_SLOT_CELLIDX, (size_t)n_cell_edges * 8 + 256);
+    if (!B.cell_idx) return MF_ERR_OOM;
+    {
+      MfProfScope ps(ctx, MF_PH_CSR, st, 1);
+      k_cells_edges<true><<<g, 256, 0, st>>>(F, B, (uint64_t)n_cells, B.cell_off);
+    }
+  }
+  rc = mf_cuda_check(ctx, cudaGetLastError(), "CSR kernels");
+  if (rc) return rc;
+  rc = read_counters(ctx, B, st);
+  if (rc) return rc;
+
+  MfTraceState &L = ctx->last;
+  L.F = F;
+  L.B = B;
+  L.flags = opts->flags;
+  const MfCounters &h = *ctx->h_counters;
+  L.n_edges = (int64_t)E;
+  L.n_cells = n_cells;
+  L.n_cell_edges = n_cell_edges;
+  L.n_vertices = (int64_t)h.n_vertices;
+  L.n_near_zero = (int64_t)h.n_near_zero;
+  L.n_recheck = (int64_t)h.n_recheck;
+  L.n_boundary = (int64_t)h.n_boundary;
+  L.n_dead_seeds = (int64_t)h.n_dead_seeds;
+  L.levels = levels;
+  L.root_evals = (int64_t)h.root_evals;
+  L.valid = true;
+  if (ctx->prof.on) {
+    ctx->prof.stats.terms[MF_PH_EVAL] += (int64_t)h.eval_terms;
+    ctx->prof.stats.terms[MF_PH_ROOTS] += (int64_t)h.root_terms;
+  }
+  {
+    MfProfScope ps(ctx, MF_PH_COPY, st, 0);
+    rc = copy_out(ctx, L, out, st);
+  }
+  mf_prof_collect(ctx);
+  return rc;
+}
+
+extern "C" int mf_trace_fetch(mf_ctx *ctx, mf_trace_out *out, void *stream) {
+  if (!ctx || !out) return MF_ERR_INVALID;
+  if (!ctx->last.valid) return mf_set_error(ctx, MF_ERR_INVALID, "no trace result to fetch");
+  cudaSetDevice(ctx->device);
+  return copy_out(ctx, ctx->last, out, (cudaStream_t)stream);
+}

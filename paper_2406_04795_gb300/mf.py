@@ -1,0 +1,205 @@
+"""ctypes binding of libmf.so (include/mf.h), same names as the C ABI.
+
+Argument marshalling only: every step of the traced path runs in the CUDA
+library.  Loading fails loudly when the library is missing; there is no CPU
+fallback.  Device buffers are passed as raw pointers (e.g. torch CUDA tensors'
+``data_ptr()``); streams as ``torch.cuda.Stream.cuda_stream`` integers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+MF_MAXD = 8
+MF_OK = 0
+MF_ERR_INVALID = -1
+MF_ERR_DOMAIN = -2
+MF_ERR_OOM = -3
+MF_ERR_CAPACITY = -4
+MF_ERR_MAXEDGES = -5
+MF_ERR_TIMEOUT = -6
+MF_ERR_CUDA = -7
+MF_ERR_DEVICE = -8
+
+MF_FP64 = 0
+MF_MIXED_BF16 = 1
+MF_MIXED_FP32 = 2
+
+MF_WANT_ROOTS = 1
+MF_WANT_CELLS = 2
+
+MF_BOX = 0
+MF_SPHERE = 1
+
+EXPORTS = ("mf_ctx_create", "mf_ctx_destroy", "mf_last_error", "mf_ctx_bytes", "mf_locate",
+           "mf_eval", "mf_trace", "mf_trace_fetch", "mf_certify", "mf_ctx_set_profiling",
+           "mf_ctx_get_stats")
+
+MF_PHASES = 12
+PHASE_NAMES = ("prepare", "seeds", "expand_vertices", "eval", "expand_edges", "roots", "cells",
+               "csr", "copy", "certify_points", "certify_cells", "other")
+
+_ERRNAMES = {v: k for k, v in globals().items() if k.startswith("MF_ERR_") or k == "MF_OK"}
+
+
+class mf_rbf(C.Structure):
+    _fields_ = [("d", C.c_int32), ("n_sv", C.c_int64), ("sv", C.c_void_p), ("alpha", C.c_void_p),
+                ("gamma", C.c_double), ("b", C.c_double)]
+
+
+class mf_domain(C.Structure):
+    _fields_ = [("lo", C.c_double * MF_MAXD), ("hi", C.c_double * MF_MAXD),
+                ("offset", C.c_double * MF_MAXD)]
+
+
+class mf_trace_opts(C.Structure):
+    _fields_ = [("lambda_", C.c_double), ("batch_cap_edges", C.c_int64), ("precision", C.c_int32),
+                ("recheck_band", C.c_double), ("root_tol", C.c_double), ("max_edges", C.c_int64),
+                ("max_vertices", C.c_int64), ("max_cells", C.c_int64), ("flags", C.c_uint32)]
+
+
+class mf_trace_out(C.Structure):
+    _fields_ = [("cap_edges", C.c_int64), ("edge_y", C.c_void_p), ("edge_mask", C.c_void_p),
+                ("edge_f", C.c_void_p), ("edge_t", C.c_void_p), ("points", C.c_void_p),
+                ("cap_cells", C.c_int64), ("cell_y", C.c_void_p), ("cell_perm", C.c_void_p),
+                ("cell_edge_off", C.c_void_p), ("cap_cell_edges", C.c_int64),
+                ("cell_edge_idx", C.c_void_p),
+                ("n_edges", C.c_int64), ("n_cells", C.c_int64), ("n_cell_edges", C.c_int64),
+                ("n_vertices", C.c_int64), ("n_near_zero", C.c_int64), ("n_recheck", C.c_int64),
+                ("n_boundary", C.c_int64), ("n_dead_seeds", C.c_int64), ("levels", C.c_int64),
+                ("root_evals", C.c_int64)]
+
+
+class mf_robot(C.Structure):
+    _fields_ = [("n_links", C.c_int32), ("dh", C.c_void_p), ("radius", C.c_void_p)]
+
+
+class mf_scene(C.Structure):
+    _fields_ = [("n", C.c_int32), ("type", C.c_void_p), ("pose", C.c_void_p), ("dims", C.c_void_p)]
+
+
+class mf_stats(C.Structure):
+    _fields_ = [("ms", C.c_double * MF_PHASES), ("launches", C.c_int64 * MF_PHASES),
+                ("units", C.c_int64 * MF_PHASES), ("terms", C.c_int64 * MF_PHASES)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmf.so")
+
+
+def load(build_if_missing: bool = True):
+    """Loads libmf.so (building it in-tree if absent).  Raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if build_if_missing:
+        from . import build as _build
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError("libmf.so is missing: build it with paper_2406_04795_gb300.build")
+    L = C.CDLL(path)
+    P, V = C.POINTER, C.c_void_p
+    L.mf_ctx_create.restype = C.c_int
+    L.mf_ctx_create.argtypes = [C.c_int, C.c_size_t, P(V)]
+    L.mf_ctx_destroy.restype = None
+    L.mf_ctx_destroy.argtypes = [V]
+    L.mf_last_error.restype = C.c_char_p
+    L.mf_last_error.argtypes = [V]
+    L.mf_ctx_bytes.restype = C.c_size_t
+    L.mf_ctx_bytes.argtypes = [V]
+    L.mf_locate.restype = C.c_int
+    L.mf_locate.argtypes = [V, C.c_int32, C.c_double, P(C.c_double), V, C.c_int64, V, V, V]
+    L.mf_eval.restype = C.c_int
+    L.mf_eval.argtypes = [V, P(mf_rbf), V, C.c_int64, C.c_int32, C.c_double, V, V]
+    L.mf_trace.restype = C.c_int
+    L.mf_trace.argtypes = [V, P(mf_rbf), P(mf_domain), P(mf_trace_opts), V, C.c_int64,
+                           P(mf_trace_out), V]
+    L.mf_trace_fetch.restype = C.c_int
+    L.mf_trace_fetch.argtypes = [V, P(mf_trace_out), V]
+    L.mf_certify.restype = C.c_int
+    L.mf_certify.argtypes = [V, P(mf_robot), P(mf_scene), V, C.c_int64, C.c_int32, V, V,
+                             C.c_int64, V, V, V, V]
+    L.mf_ctx_set_profiling.restype = C.c_int
+    L.mf_ctx_set_profiling.argtypes = [V, C.c_int]
+    L.mf_ctx_get_stats.restype = C.c_int
+    L.mf_ctx_get_stats.argtypes = [V, P(mf_stats)]
+    _lib = L
+    return L
+
+
+class MfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_ERRNAMES.get(code, "MF_ERR"), code, msg))
+        self.code = code
+
+
+def _check(ctx, rc):
+    if rc != MF_OK:
+        msg = load().mf_last_error(ctx).decode() if ctx else ""
+        raise MfError(rc, msg)
+    return rc
+
+
+# ---------------------------------------------------------------------------
+# Same-name wrappers (raw pointers in, return code checked)
+# ---------------------------------------------------------------------------
+def mf_ctx_create(device: int = 0, hbm_budget_bytes: int = 0):
+    h = C.c_void_p()
+    rc = load().mf_ctx_create(device, hbm_budget_bytes, C.byref(h))
+    if rc != MF_OK:
+        raise MfError(rc, "mf_ctx_create failed")
+    return h
+
+
+def mf_ctx_destroy(ctx):
+    load().mf_ctx_destroy(ctx)
+
+
+def mf_last_error(ctx) -> str:
+    return load().mf_last_error(ctx).decode()
+
+
+def mf_ctx_bytes(ctx) -> int:
+    return load().mf_ctx_bytes(ctx)
+
+
+def mf_locate(ctx, d, lam, offset, points_ptr, n, y_ptr, perm_ptr, stream=0):
+    off = (C.c_double * MF_MAXD)(*[float(v) for v in offset])
+    return _check(ctx, load().mf_locate(ctx, d, lam, off, points_ptr, n, y_ptr, perm_ptr, stream))
+
+
+def mf_eval(ctx, rbf: mf_rbf, q_ptr, n, precision, band, f_ptr, stream=0):
+    return _check(ctx, load().mf_eval(ctx, C.byref(rbf), q_ptr, n, precision, band, f_ptr, stream))
+
+
+def mf_trace(ctx, rbf: mf_rbf, dom: mf_domain, opts: mf_trace_opts, seeds_ptr, n_seeds,
+             out: mf_trace_out, stream=0, check=True):
+    rc = load().mf_trace(ctx, C.byref(rbf), C.byref(dom), C.byref(opts), seeds_ptr, n_seeds,
+                         C.byref(out), stream)
+    return _check(ctx, rc) if check else rc
+
+
+def mf_trace_fetch(ctx, out: mf_trace_out, stream=0):
+    return _check(ctx, load().mf_trace_fetch(ctx, C.byref(out), stream))
+
+
+def mf_ctx_set_profiling(ctx, enable: bool):
+    return _check(ctx, load().mf_ctx_set_profiling(ctx, 1 if enable else 0))
+
+
+def mf_ctx_get_stats(ctx) -> dict:
+    s = mf_stats()
+    _check(ctx, load().mf_ctx_get_stats(ctx, C.byref(s)))
+    return {name: dict(ms=s.ms[i], launches=s.launches[i], units=s.units[i], terms=s.terms[i])
+            for i, name in enumerate(PHASE_NAMES)}
+
+
+def mf_certify(ctx, robot: mf_robot, scene: mf_scene, points_ptr, n_points, d, off_ptr, idx_ptr,
+               n_cells, verdict_ptr, margin_ptr, cell_verdict_ptr, stream=0):
+    return _check(ctx, load().mf_certify(ctx, C.byref(robot), C.byref(scene), points_ptr, n_points,
+                                         d, off_ptr, idx_ptr, n_cells, verdict_ptr, margin_ptr,
+                                         cell_verdict_ptr, stream))

@@ -1,0 +1,75 @@
+"""One proof = one pass of the traced path on one workload: ``mf_trace`` (locate
+seeds, breadth-first tracing, roots, cells and their CSR) followed by
+``mf_certify`` (forward kinematics and capsule/obstacle checks of every
+intersection point, AND over each cell).  Inputs stay resident on the device;
+outputs are preallocated after the first call so that repeated steps allocate
+nothing."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import mf
+from .api import Context
+
+# Capacities of the resident tables per workload family (edges, vertices,
+# cells).  Measured ratios on these workloads: vertices/edges ~ 0.2-0.5,
+# cells/edges ~ 1.5 (d=3) to ~10 (d=5), cell edges/cell ~ 3-6.
+SIZING = {
+    3: dict(max_edges=1 << 20, max_vertices=1 << 20, max_cells=1 << 22),
+    4: dict(max_edges=1 << 22, max_vertices=1 << 22, max_cells=1 << 25),
+    5: dict(max_edges=100_000_000, max_vertices=40_000_000, max_cells=1_000_000_000),
+    6: dict(max_edges=120_000_000, max_vertices=60_000_000, max_cells=1_600_000_000),
+}
+
+
+LAMBDA_REF = {3: 0.1, 4: 0.08, 5: 0.05, 6: 0.04}
+
+
+def sizing_for(w) -> dict:
+    """Table capacities for a workload: the family's sizing scaled by
+    (lambda_ref / lambda)^(d-1) (traced sets grow as lambda^-(d-1))."""
+    base = SIZING.get(w.d, SIZING[6])
+    f = (LAMBDA_REF.get(w.d, 0.04) / w.lam) ** (w.d - 1)
+    f = min(max(f, 1e-3), 4.0)
+    return {k: int(max(v * f, 1 << 16)) for k, v in base.items()}
+
+
+def precision_of(w) -> int:
+    return mf.MF_FP64 if w.precision == "fp64" else mf.MF_MIXED_FP32
+
+
+class Proof:
+    """Device-resident inputs and reusable outputs for one workload."""
+
+    def __init__(self, ctx: Context, w, precision=None, sizing=None):
+        self.ctx, self.w = ctx, w
+        dev = ctx.device
+        self.precision = precision_of(w) if precision is None else precision
+        self.sizing = dict(sizing_for(w) if sizing is None else sizing)
+        t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+        self.sv, self.alpha, self.seeds = t(w.sv), t(w.alpha), t(w.seeds)
+        self.dh, self.radius = t(w.dh), t(w.radius)
+        self.otype, self.opose, self.odims = t(w.obs_type, torch.int32), t(w.obs_pose), t(w.obs_dims)
+        self.outputs = None
+        self.last = None
+
+    def step(self, stream=None):
+        w = self.w
+        r = self.ctx.trace(self.sv, self.alpha, w.gamma, w.b, w.lam, w.offset, w.lo, w.hi,
+                           self.seeds, precision=self.precision, roots=True, cells=True,
+                           batch_cap=w.batch_cap, recheck_band=w.recheck_band,
+                           outputs=self.outputs, stream=stream, **self.sizing)
+        self.outputs = r["_buffers"]
+        v, m, cv = self.ctx.certify(self.dh, self.radius, self.otype, self.opose, self.odims,
+                                    r["points"], r["cell_off"], r["cell_idx"], stream=stream)
+        self.last = (r, v, m, cv)
+        return r, v, m, cv
+
+
+def host_inputs(w):
+    """Pinned host copies of a workload's inputs (for end-to-end timing)."""
+    pin = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
+    return dict(sv=pin(w.sv), alpha=pin(w.alpha), seeds=pin(w.seeds), dh=pin(w.dh),
+                radius=pin(w.radius), otype=pin(w.obs_type, torch.int32), opose=pin(w.obs_pose),
+                odims=pin(w.obs_dims))

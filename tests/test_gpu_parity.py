@@ -1,0 +1,171 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle,
+element by element on seeded inputs."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2406_04795_gb300 import mf
+from paper_2406_04795_gb300 import workloads as W
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2406_04795_gb300.api import Context
+    c = Context(0, 64 << 30)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 5, 6, 7, 8])
+def test_locate_bit_exact(ctx, d):
+    rng = np.random.default_rng(100 + d)
+    lam = 0.07
+    o = rng.uniform(-0.03, 0.03, d)
+    pts = rng.uniform(-3, 3, size=(3000, d))
+    # points exactly on lattice vertices exercise the tie rule
+    pts[:50] = oracle.vertex_x(d, lam, o, rng.integers(-30, 30, size=(50, d)).astype(np.int32))
+    y, perm = ctx.locate(d, lam, o, pts)
+    y, perm = y.cpu().numpy(), perm.cpu().numpy()
+    for i in range(pts.shape[0]):
+        oy, parts = oracle.locate(d, lam, o, pts[i])
+        assert tuple(y[i]) == oy
+        assert tuple(1 << int(p) for p in perm[i]) + (1 << d,) == parts
+
+
+@pytest.mark.parametrize("d,n_sv,gamma", [(3, 64, 2.0), (5, 2048, 4.0), (6, 1000, 6.0)])
+def test_eval_fp64_and_mixed(ctx, d, n_sv, gamma):
+    rng = np.random.default_rng(d)
+    sv = rng.uniform(-math.pi, math.pi, size=(n_sv, d))
+    alpha = rng.normal(size=n_sv)
+    b = 0.1
+    q = rng.uniform(-math.pi, math.pi, size=(5000, d))
+    k = min(200, n_sv)
+    q[:k] = sv[:k] + rng.normal(scale=0.2, size=(k, d))
+    fo = oracle.f(sv, alpha, gamma, b, q)
+    f64 = ctx.eval(sv, alpha, gamma, b, q, precision=mf.MF_FP64).cpu().numpy()
+    assert np.max(np.abs(f64 - fo)) <= 1e-12
+    for prec in (mf.MF_MIXED_FP32,):
+        fm = ctx.eval(sv, alpha, gamma, b, q, precision=prec, band=1e-3).cpu().numpy()
+        assert np.max(np.abs(fm - fo)) <= 1e-3
+        mask = np.abs(fo) >= 1e-12
+        assert np.array_equal(fm[mask] >= 0, fo[mask] >= 0)
+
+
+@pytest.mark.parametrize("precision", [mf.MF_FP64, mf.MF_MIXED_FP32])
+def test_d3_config_full_parity(ctx, precision):
+    w = W.config_d3()
+    g = P.gpu_trace(ctx, w, precision)
+    o = P.oracle_trace(w)
+    rep = P.compare_traces(w, g, o, t_tol=1e-9, f_tol=1e-12 if precision == mf.MF_FP64 else 1e-3)
+    assert rep["n_diff"] == 0 and rep["n_edges"] > 1000
+    # certification of the traced points and cells
+    vg, mg, cg = ctx.certify(w.dh, w.radius, w.obs_type, w.obs_pose, w.obs_dims, g["points"],
+                             g["cell_off"], g["cell_idx"])
+    vo, mo, co = oracle.certify(w.dh, w.radius, w.obs_type, w.obs_pose, w.obs_dims, g["points"],
+                                g["cell_off"], g["cell_idx"])
+    vg, mg, cg = vg.cpu().numpy(), mg.cpu().numpy(), cg.cpu().numpy()
+    sure = np.abs(mo) > 1e-12
+    assert np.array_equal(vg[sure], vo[sure])
+    assert np.max(np.abs(mg - mo)) <= 1e-9
+    if sure.all():
+        assert np.array_equal(cg, co)
+
+
+@pytest.mark.parametrize("cap", [1, 7, 100])
+def test_result_independent_of_batch_cap(ctx, cap):
+    w = W.random_small(3, 10, 21, 0.2, gamma=1.5, n_seeds=3, box=1.2)
+    o = P.oracle_trace(w, roots=False, cells=True)
+    g = P.gpu_trace(ctx, w, batch_cap=cap, roots=False)
+    rep = P.compare_traces(w, g, o)
+    assert rep["n_diff"] == 0
+
+
+@pytest.mark.parametrize("d,lam,n_sv,seed", [(2, 0.05, 12, 1), (3, 0.15, 20, 2), (4, 0.3, 16, 3),
+                                             (5, 0.5, 16, 4), (6, 0.7, 12, 5)])
+@pytest.mark.parametrize("precision", [mf.MF_FP64, mf.MF_MIXED_FP32])
+def test_random_problems_parity(ctx, d, lam, n_sv, seed, precision):
+    w = W.random_small(d, n_sv, seed, lam, gamma=1.5, n_seeds=4, box=1.3)
+    o = P.oracle_trace(w, roots=True, cells=d <= 5)
+    g = P.gpu_trace(ctx, w, precision, cells=d <= 5)
+    rep = P.compare_traces(w, g, o, f_tol=1e-12 if precision == mf.MF_FP64 else 1e-3,
+                           check_cells=d <= 5)
+    assert rep["n_edges"] > 20
+
+
+def test_sphere_closed_form_on_gpu(ctx):
+    w = W.sphere_workload(4, r=1.0, gamma=0.8, lam=0.25)
+    g = P.gpu_trace(ctx, w)
+    assert g["n_edges"] > 500
+    assert np.max(np.abs(np.linalg.norm(g["points"], axis=1) - 1.0)) < 1e-9
+    # Euler characteristic in d = 3
+    w3 = W.sphere_workload(3, r=1.0, gamma=1.0, lam=0.2)
+    g3 = P.gpu_trace(ctx, w3)
+    o3 = P.oracle_trace(w3)
+    assert P.compare_traces(w3, g3, o3)["n_diff"] == 0
+    assert g3["n_edges"] - o3["n_crossing_triangles"] + g3["n_cells"] == 2
+
+
+def test_empty_and_dead_seeds(ctx):
+    w = W.config_d3()
+    w.seeds = np.zeros((0, 3))
+    g = P.gpu_trace(ctx, w)
+    assert g["n_edges"] == 0 and g["levels"] == 0
+    w.seeds = np.array([[3.0, 3.0, 3.0], [100.0, 0.0, 0.0]])  # far from f = 0 / outside the box
+    g = P.gpu_trace(ctx, w)
+    o = P.oracle_trace(w)
+    assert g["n_dead_seeds"] == o["n_dead_seeds"] == 2 and g["n_edges"] == 0
+
+
+def test_error_codes(ctx):
+    w = W.config_d3()
+    with pytest.raises(mf.MfError) as e:
+        P.gpu_trace(ctx, w, max_edges=100)
+    assert e.value.code == mf.MF_ERR_MAXEDGES
+    bad = W.config_d3()
+    bad.lam = -1.0
+    with pytest.raises(mf.MfError) as e:
+        P.gpu_trace(ctx, bad)
+    assert e.value.code == mf.MF_ERR_INVALID
+    bad = W.config_d3()
+    bad.alpha = bad.alpha.copy()
+    bad.alpha[3] = np.nan
+    with pytest.raises(mf.MfError) as e:
+        P.gpu_trace(ctx, bad)
+    assert e.value.code == mf.MF_ERR_INVALID
+    # a context whose budget cannot hold the tables
+    from paper_2406_04795_gb300.api import Context
+    small = Context(0, 1 << 20)
+    with pytest.raises(mf.MfError) as e:
+        P.gpu_trace(small, w)
+    assert e.value.code == mf.MF_ERR_OOM
+    small.close()
+    # the context stays usable after errors
+    g = P.gpu_trace(ctx, w)
+    assert g["n_edges"] > 1000
+
+
+def test_two_call_capacity_pattern(ctx):
+    w = W.config_d3()
+    r = ctx.trace(w.sv, w.alpha, w.gamma, w.b, w.lam, w.offset, w.lo, w.hi, w.seeds)
+    E = r["n_edges"]
+    small = ctx._alloc_outputs(3, 10, 10, 10)
+    out = ctx._out_struct(small, 3)
+    rbf, keep = ctx.rbf(w.sv, w.alpha, w.gamma, w.b)
+    dom = ctx.domain(w.lo, w.hi, w.offset)
+    opts = mf.mf_trace_opts(w.lam, 1 << 24, 0, 1e-3, 1e-12, 1 << 22, 0, 0, 3)
+    seeds = torch.as_tensor(w.seeds, device="cuda")
+    rc = mf.mf_trace(ctx.h, rbf, dom, opts, seeds.data_ptr(), 1, out,
+                     torch.cuda.current_stream().cuda_stream, check=False)
+    assert rc == mf.MF_ERR_CAPACITY and out.n_edges == E
+    big = ctx._alloc_outputs(3, out.n_edges, out.n_cells, out.n_cell_edges)
+    out2 = ctx._out_struct(big, 3)
+    mf.mf_trace_fetch(ctx.h, out2)
+    assert out2.n_edges == E
+    assert set(P.keys(big["edge_y"].cpu().numpy(), big["edge_mask"].cpu().numpy())) == \
+        set(P.keys(r["edge_y"].cpu().numpy(), r["edge_mask"].cpu().numpy()))
