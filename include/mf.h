@@ -207,7 +207,8 @@ typedef struct {
   double ms[MF_PHASES];        /* device time summed over the phase's launches */
   int64_t launches[MF_PHASES]; /* kernel launches of the phase */
   int64_t units[MF_PHASES];    /* work items: seeds, frontier edges, edges solved, points ... */
-  int64_t terms[MF_PHASES];    /* RBF terms evaluated in FP64 (eval / roots phases) */
+  int64_t terms[MF_PHASES];    /* RBF terms with the FP64 exp (eval / roots phases) */
+  int64_t terms_weak[MF_PHASES]; /* RBF terms with the reduced-cost exp (|term| <= 1e-9) */
 } mf_stats;
 
 /* Enables (1) or disables (0) profiling on the context; enabling clears the stats. */

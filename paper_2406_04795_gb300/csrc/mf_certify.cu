@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int nl, const d
                                                     int64_t n, int d, uint8_t *verdict,
                                                     double *margin) {
   __shared__ CertObs so[CERT_MAX_OBS];
-  __shared__ double sdh[MF_MAXD * 4], srad[MF_MAXD];
+  __shared__ float4 sbound[CERT_MAX_OBS];  // obstacle centre and bounding-sphere radius
+  __shared__ double sdh[MF_MAXD * 4], srad[MF_MAXD], ssa[MF_MAXD], sca[MF_MAXD];
   for (int i = threadIdx.x; i < nobs; i += blockDim.x) {
     CertObs o;
     for (int k = 0; k < 9; k++) o.R[k] = pose[12 * i + k];
@@ -119,22 +120,28 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int nl, const d
     o.type = type[i];
     for (int k = 0; k < 3; k++) o.h[k] = o.type == MF_BOX ? 0.5 * dims[3 * i + k] : dims[3 * i + k];
     so[i] = o;
+    const double rb = o.type == MF_BOX ? sqrt(o.h[0] * o.h[0] + o.h[1] * o.h[1] + o.h[2] * o.h[2])
+                                       : o.h[0];
+    sbound[i] = make_float4((float)o.t[0], (float)o.t[1], (float)o.t[2], (float)rb);
   }
   for (int i = threadIdx.x; i < nl * 4; i += blockDim.x) sdh[i] = dh[i];
-  for (int i = threadIdx.x; i < nl; i += blockDim.x) srad[i] = radius[i];
+  for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+    srad[i] = radius[i];
+    sincos(dh[4 * i + 3], &ssa[i], &sca[i]);
+  }
   __syncthreads();
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
-  // forward kinematics: T = T * A_i with the standard DH link transform
+  // forward kinematics: T = T * A_i with the standard DH link transform; keep
+  // every frame origin (link i runs from origin i to origin i+1)
   double T[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};  // 3x4 row-major
-  double prev[3] = {0.0, 0.0, 0.0};
-  double best = -INFINITY;
+  double org[3 * (MF_MAXD + 1)];
+  org[0] = org[1] = org[2] = 0.0;
   for (int i = 0; i < nl; i++) {
-    const double th = pts[p * d + i] + sdh[4 * i], dd = sdh[4 * i + 1], aa = sdh[4 * i + 2],
-                 al = sdh[4 * i + 3];
-    double st, ct, sa, ca;
+    const double th = pts[p * d + i] + sdh[4 * i], dd = sdh[4 * i + 1], aa = sdh[4 * i + 2];
+    double st, ct;
     sincos(th, &st, &ct);
-    sincos(al, &sa, &ca);
+    const double sa = ssa[i], ca = sca[i];
     const double A[12] = {ct, -st * ca, st * sa, aa * ct, st, ct * ca, -ct * sa, aa * st,
                           0.0, sa, ca, dd};
     double N[12];
@@ -149,15 +156,41 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int nl, const d
     }
 #pragma unroll
     for (int k = 0; k < 12; k++) T[k] = N[k];
-    const double cur[3] = {T[3], T[7], T[11]};
-    for (int k = 0; k < nobs; k++) {
-      const double m = srad[i] - seg_obstacle_dist(so[k], prev, cur);
-      best = fmax(best, m);
-    }
-    prev[0] = cur[0];
-    prev[1] = cur[1];
-    prev[2] = cur[2];
+    org[3 * (i + 1) + 0] = T[3];
+    org[3 * (i + 1) + 1] = T[7];
+    org[3 * (i + 1) + 2] = T[11];
   }
+  // margin = max over (link, obstacle) of radius - distance.  A pair whose
+  // bounding-sphere lower bound lb on the distance gives radius - lb <= the
+  // best exact margin so far cannot change the maximum and is skipped; the
+  // pair with the largest radius - lb is evaluated first.  lb is computed in
+  // FP32 with a relative slack of 1e-5, so it never exceeds the true distance.
+  auto lower_bound = [&](int i, int k) -> float {
+    const float ax = (float)org[3 * i], ay = (float)org[3 * i + 1], az = (float)org[3 * i + 2];
+    const float bx = (float)org[3 * i + 3], by = (float)org[3 * i + 4], bz = (float)org[3 * i + 5];
+    const float mx = 0.5f * (ax + bx), my = 0.5f * (ay + by), mz = 0.5f * (az + bz);
+    const float hl = 0.5f * sqrtf((bx - ax) * (bx - ax) + (by - ay) * (by - ay) + (bz - az) * (bz - az));
+    const float4 c = sbound[k];
+    const float dc = sqrtf((mx - c.x) * (mx - c.x) + (my - c.y) * (my - c.y) + (mz - c.z) * (mz - c.z));
+    const float scale = fabsf(mx) + fabsf(my) + fabsf(mz) + fabsf(c.x) + fabsf(c.y) + fabsf(c.z) +
+                        hl + c.w;
+    return dc - hl - c.w - 1e-5f * scale - 1e-6f;
+  };
+  double best = -INFINITY;
+  int bi = -1, bk = -1;
+  float bub = -INFINITY;
+  for (int i = 0; i < nl; i++)
+    for (int k = 0; k < nobs; k++) {
+      const float ub = (float)srad[i] - lower_bound(i, k);
+      if (ub > bub) { bub = ub; bi = i; bk = k; }
+    }
+  if (bi >= 0) best = srad[bi] - seg_obstacle_dist(so[bk], &org[3 * bi], &org[3 * bi + 3]);
+  for (int i = 0; i < nl; i++)
+    for (int k = 0; k < nobs; k++) {
+      if (i == bi && k == bk) continue;
+      if ((double)((float)srad[i] - lower_bound(i, k)) <= best) continue;
+      best = fmax(best, srad[i] - seg_obstacle_dist(so[k], &org[3 * i], &org[3 * i + 3]));
+    }
   margin[p] = best;
   verdict[p] = best >= 0.0 ? 1 : 0;
 }

@@ -2,12 +2,20 @@
 // exp(-gamma |q - s_i|^2) + b (RBF-SVM decision function, Sec. IV-A), and the
 // root solve along traced edges (the "iterative algorithm" of Sec. VI).
 //
-// FP64 path: one warp per point.  Each lane screens one support vector per
-// step in FP32; the survivors (gamma r^2 <= T, T chosen on the host so that
-// the dropped terms sum to <= 1e-13) are compacted into a per-warp queue and
-// evaluated in FP64 by all 32 lanes at once, so FP64 work is spent only on
-// terms that can change f above 1e-13.  GB300 issues few FP64 operations per
-// clock, so this compaction is what bounds the FP64 path.
+// FP64 path (GB300 issues two FP64 FMAs per SM per clock, so FP64 work is what
+// the path must save).  One warp per point.  Each lane screens one support
+// vector per step in FP32 and sorts it into one of three classes:
+//   dropped  gamma r^2 > T, T chosen so that all dropped terms sum to <= 1e-13;
+//   strong   |alpha| e^{-gamma r^2} may exceed tau = 1e-9: FP64 distance and
+//            the FP64 exp of the CUDA math library;
+//   weak     the rest: FP64 distance, and e^a by a Cody-Waite reduction
+//            a = k ln2 + r with 2^(r/ln2) from the hardware ex2 (relative error
+//            below 2^-20) scaled exactly by 2^k.
+// Strong and weak terms are compacted into two per-warp queues, so FP64 lanes
+// never idle on skipped terms and each batch of 32 runs one code path.  The
+// weak terms' error is bounded on the fly (6e-7 x sum of their magnitudes);
+// if the bound would push the total error above 2.5e-13 the point is
+// evaluated again with every kept term strong.
 //
 // Mixed FP32 SIMT path: one thread per two points, support vectors broadcast
 // from shared memory, FP32 differences and ex2, and a per-point rigorous bound
@@ -19,6 +27,26 @@
 #include "mf_ctx.h"
 
 #define FULL 0xffffffffu
+#define WEAK_REL_ERR 6e-7  // relative error bound of exp_cheap (2^-20 plus rounding)
+#define STRONG_TAU 1e-9
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// e^a for a <= 0: Cody-Waite reduction a = k ln2 + r (|r| <= ln2/2), e^r as
+// 2^(r log2 e) by the hardware ex2 in FP32, exact scaling by 2^k through the
+// exponent field.  Relative error < 2^-20 + 2^-24.
+__device__ __forceinline__ double exp_cheap(double a) {
+  const double kd = rint(a * 1.4426950408889634);
+  const double r = fma(-kd, 0.6931471805599453, a);
+  const float e = ex2_approx((float)r * 1.44269504f);
+  const int k = (int)kd;
+  if (k < -1020) return 0.0;
+  return (double)e * __longlong_as_double((long long)(k + 1023) << 52);
+}
 
 // ---------------------------------------------------------------------------
 // RBF preparation
@@ -30,7 +58,8 @@ struct MfRbfStats {
 };
 
 __global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alpha, float *sv32,
-                              double *sv64, float *alpha32, MfRbfStats *st) {
+                              float *svlo32, double *sv64, float *alpha32, float *strong32,
+                              MfRbfStats *st) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   double a = 0.0;
   float m = 0.f;
@@ -40,13 +69,17 @@ __global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alph
       double s = sv[(int64_t)j * d + k];
       if (!isfinite(s)) bad = 1;
       sv64[(int64_t)k * n + j] = s;
-      sv32[(int64_t)k * n + j] = (float)s;
-      m = fmaxf(m, fabsf((float)s));
+      const float hi = (float)s;
+      sv32[(int64_t)k * n + j] = hi;
+      svlo32[(int64_t)k * n + j] = (float)(s - (double)hi);
+      m = fmaxf(m, fabsf(hi));
     }
     double al = alpha[j];
     if (!isfinite(al)) bad = 1;
     alpha32[j] = (float)al;
     a = fabs(al);
+    // strong iff gamma r^2 < ln(|alpha| / tau)
+    strong32[j] = a > STRONG_TAU ? (float)log(a / STRONG_TAU) : -1.0f;
   }
   a = mf_warp_sum_d(a);
 #pragma unroll
@@ -67,16 +100,21 @@ int mf_prepare_rbf(mf_ctx *ctx, const mf_rbf *rbf, MfRbfDev *out, cudaStream_t s
       !std::isfinite(rbf->b))
     return mf_set_error(ctx, MF_ERR_INVALID, "bad RBF parameters");
   const int d = rbf->d, n = (int)rbf->n_sv;
-  size_t nb = (size_t)n;
-  size_t bytes = nb * d * 4 + nb * d * 8 + nb * 4 + 1024;
+  const size_t nb = (size_t)n;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t bytes = 256 + al(nb * d * 8) + 2 * al(nb * d * 4) + 2 * al(nb * 4);
   char *base = (char *)mf_ctx_buffer(ctx, MF_SLOT_RBF, bytes);
   if (!base) return MF_ERR_OOM;
   MfRbfStats *dst = (MfRbfStats *)base;
-  double *sv64 = (double *)(base + 256);
-  float *sv32 = (float *)(sv64 + nb * d);
-  float *alpha32 = sv32 + nb * d;
+  char *p = base + 256;
+  double *sv64 = (double *)p; p += al(nb * d * 8);
+  float *sv32 = (float *)p; p += al(nb * d * 4);
+  float *svlo32 = (float *)p; p += al(nb * d * 4);
+  float *alpha32 = (float *)p; p += al(nb * 4);
+  float *strong32 = (float *)p;
   cudaMemsetAsync(dst, 0, sizeof(MfRbfStats), st);
-  k_prepare_rbf<<<(n + 255) / 256, 256, 0, st>>>(d, n, rbf->sv, rbf->alpha, sv32, sv64, alpha32, dst);
+  k_prepare_rbf<<<(n + 255) / 256, 256, 0, st>>>(d, n, rbf->sv, rbf->alpha, sv32, svlo32, sv64,
+                                                  alpha32, strong32, dst);
   MfRbfStats h;
   int rc = mf_cuda_check(ctx, cudaMemcpyAsync(&h, dst, sizeof(h), cudaMemcpyDeviceToHost, st),
                          "prepare rbf");
@@ -87,9 +125,11 @@ int mf_prepare_rbf(mf_ctx *ctx, const mf_rbf *rbf, MfRbfDev *out, cudaStream_t s
   out->d = d;
   out->n = n;
   out->sv32 = sv32;
+  out->svlo32 = svlo32;
   out->sv64 = sv64;
   out->alpha = rbf->alpha;
   out->alpha32 = alpha32;
+  out->strong32 = strong32;
   out->gamma = rbf->gamma;
   out->b = rbf->b;
   // Screen: drop terms with gamma r^2 > T where sum|alpha| e^-T <= 1e-13.
@@ -99,19 +139,20 @@ int mf_prepare_rbf(mf_ctx *ctx, const mf_rbf *rbf, MfRbfDev *out, cudaStream_t s
   if (T > 740.0) T = 740.0;
   out->screen_r2 = (float)((T + 0.5) / rbf->gamma);
   out->drop_bound = sa * std::exp(-T);
+  out->weak_limit = 2.5e-13 - out->drop_bound;
   out->smax = h.max_abs_s;
   return MF_OK;
 }
 
 // ---------------------------------------------------------------------------
-// FP64 warp evaluator with FP32 screening and lane compaction.
+// FP64 warp evaluator: FP32 screening into strong / weak queues.
 // ---------------------------------------------------------------------------
 struct F64Acc {
-  double f, g;
+  double f, g;  // f (with b) and, with GRAD, grad f . dir
+  float weak;   // sum of |term| over weak terms (error bound input)
 };
 
-// One compacted batch: lane processes support vector `j` (or nothing if j<0).
-template <bool GRAD>
+template <bool GRAD, bool STRONG>
 __device__ __forceinline__ void f64_term(const MfRbfDev &R, const double *x, const double *dir,
                                          int j, F64Acc &acc) {
   if (j < 0) return;
@@ -124,26 +165,41 @@ __device__ __forceinline__ void f64_term(const MfRbfDev &R, const double *x, con
       if (GRAD) proj = fma(t, dir[k], proj);
     }
   }
-  double e = R.alpha[j] * exp(-R.gamma * r2);
+  const double a = -R.gamma * r2;
+  const double e = R.alpha[j] * (STRONG ? exp(a) : exp_cheap(a));
   acc.f += e;
+  if (!STRONG) acc.weak += (float)fabs(e);
   if (GRAD) acc.g = fma(e, proj, acc.g);
 }
 
+// Pops 32 entries of a queue of length n (>= 32) into lane `j`.
+__device__ __forceinline__ int pop32(int *q, int &n, int lane) {
+  __syncwarp();
+  const int j = q[lane];
+  __syncwarp();
+  if (lane < n - 32) q[lane] = q[32 + lane];
+  __syncwarp();
+  n -= 32;
+  return j;
+}
+
 // All lanes pass the same x (FP64) and get f (and, with GRAD, g = grad f . dir).
-// `terms` accumulates the number of terms evaluated in FP64.
-template <bool GRAD>
-__device__ F64Acc warp_f64(const MfRbfDev &R, const double *x, const double *dir, int *buf,
-                           unsigned long long &terms) {
+// qs, qw: two 64-entry per-warp queues.  ALL_STRONG puts every kept term in
+// the strong queue.  terms[0/1] count strong / weak terms.
+template <bool GRAD, bool ALL_STRONG>
+__device__ F64Acc warp_f64_pass(const MfRbfDev &R, const double *x, const double *dir, int *qs,
+                                int *qw, unsigned long long *terms) {
   const int lane = threadIdx.x & 31;
   float x32[MF_MAXD];
 #pragma unroll
   for (int k = 0; k < MF_MAXD; k++) x32[k] = k < R.d ? (float)x[k] : 0.f;
-  F64Acc acc = {0.0, 0.0};
-  int nbuf = 0;
+  const float g32 = (float)R.gamma;
+  F64Acc acc = {0.0, 0.0, 0.f};
+  int ns = 0, nw = 0;
   const unsigned lt = (1u << lane) - 1u;
   for (int base = 0; base < R.n; base += 32) {
     const int j = base + lane;
-    bool near = false;
+    bool keep = false, strong = false;
     if (j < R.n) {
       float r2 = 0.f;
 #pragma unroll
@@ -152,80 +208,103 @@ __device__ F64Acc warp_f64(const MfRbfDev &R, const double *x, const double *dir
           float t = x32[k] - R.sv32[(int64_t)k * R.n + j];
           r2 = fmaf(t, t, r2);
         }
-      near = r2 <= R.screen_r2;
+      keep = r2 <= R.screen_r2;
+      strong = ALL_STRONG || (g32 * r2 < R.strong32[j] + 0.5f);
     }
-    const unsigned m = __ballot_sync(FULL, near);
-    if (near) buf[nbuf + __popc(m & lt)] = j;
-    nbuf += __popc(m);
-    terms += __popc(m);
-    if (nbuf >= 32) {
-      __syncwarp();
-      const int jj = buf[lane];
-      __syncwarp();
-      if (lane < nbuf - 32) buf[lane] = buf[32 + lane];
-      __syncwarp();
-      nbuf -= 32;
-      f64_term<GRAD>(R, x, dir, jj, acc);
+    const unsigned ms = __ballot_sync(FULL, keep && strong);
+    const unsigned mw = __ballot_sync(FULL, keep && !strong);
+    if (keep && strong) qs[ns + __popc(ms & lt)] = j;
+    if (keep && !strong) qw[nw + __popc(mw & lt)] = j;
+    ns += __popc(ms);
+    nw += __popc(mw);
+    terms[0] += __popc(ms);
+    terms[1] += __popc(mw);
+    if (ns >= 32) {
+      const int jj = pop32(qs, ns, lane);
+      f64_term<GRAD, true>(R, x, dir, jj, acc);
+    }
+    if (nw >= 32) {
+      const int jj = pop32(qw, nw, lane);
+      f64_term<GRAD, false>(R, x, dir, jj, acc);
     }
   }
   __syncwarp();
-  const int jj = lane < nbuf ? buf[lane] : -1;
+  const int js = lane < ns ? qs[lane] : -1;
+  const int jw = lane < nw ? qw[lane] : -1;
   __syncwarp();
-  f64_term<GRAD>(R, x, dir, jj, acc);
+  f64_term<GRAD, true>(R, x, dir, js, acc);
+  f64_term<GRAD, false>(R, x, dir, jw, acc);
   acc.f = mf_warp_sum_d(acc.f) + R.b;
+  acc.weak = mf_warp_sum_f(acc.weak);
   if (GRAD) acc.g = -2.0 * R.gamma * mf_warp_sum_d(acc.g);
   return acc;
+}
+
+// f with total error <= 2.5e-13 (dropped + weak terms), all lanes.
+template <bool GRAD>
+__device__ __forceinline__ F64Acc warp_f64(const MfRbfDev &R, const double *x, const double *dir,
+                                           int *qs, int *qw, unsigned long long *terms) {
+  F64Acc a = warp_f64_pass<GRAD, false>(R, x, dir, qs, qw, terms);
+  if ((double)a.weak * 1.01 * WEAK_REL_ERR > R.weak_limit)
+    a = warp_f64_pass<GRAD, true>(R, x, dir, qs, qw, terms);
+  return a;
 }
 
 #define EVAL_WARPS 8
 
 // f at vertex-list entries [v_evaluated, n_vertices) (FP64).
 __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_vertices_f64(MfFrame F, MfRbfDev R, MfTraceBufs B) {
-  __shared__ int sbuf[EVAL_WARPS][64];
+  __shared__ int sq[EVAL_WARPS][2][64];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint64_t begin = B.cnt->v_evaluated;
   uint64_t end = B.cnt->n_vertices;
   if (end > B.max_vertices) end = B.max_vertices;
-  const uint64_t nw = (uint64_t)gridDim.x * EVAL_WARPS;
-  unsigned long long terms = 0;
-  for (uint64_t i = begin + (uint64_t)blockIdx.x * EVAL_WARPS + w; i < end; i += nw) {
+  const uint64_t nwarps = (uint64_t)gridDim.x * EVAL_WARPS;
+  unsigned long long terms[2] = {0, 0};
+  for (uint64_t i = begin + (uint64_t)blockIdx.x * EVAL_WARPS + w; i < end; i += nwarps) {
     int32_t y[MF_MAXD];
     double x[MF_MAXD];
 #pragma unroll
     for (int k = 0; k < MF_MAXD; k++) y[k] = k < F.d ? B.vert_y[i * F.d + k] : 0;
     mf_vertex_x(F, y, x);
-    F64Acc a = warp_f64<false>(R, x, nullptr, sbuf[w], terms);
+    F64Acc a = warp_f64<false>(R, x, nullptr, sq[w][0], sq[w][1], terms);
     if (lane == 0) {
       B.vtab_f[B.vert_slot[i]] = a.f;
       if (fabs(a.f) < 1e-12) atomicAdd(&B.cnt->n_near_zero, 1ull);
     }
   }
-  if (lane == 0 && terms) atomicAdd(&B.cnt->eval_terms, terms);
+  if (lane == 0 && (terms[0] | terms[1])) {
+    atomicAdd(&B.cnt->eval_terms, terms[0]);
+    atomicAdd(&B.cnt->eval_terms_weak, terms[1]);
+  }
 }
 
 // FP64 re-evaluation of the recheck queue [n_recheck_done, n_recheck).
 __global__ void __launch_bounds__(EVAL_WARPS * 32) k_recheck_vertices_f64(MfFrame F, MfRbfDev R, MfTraceBufs B) {
-  __shared__ int sbuf[EVAL_WARPS][64];
+  __shared__ int sq[EVAL_WARPS][2][64];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint64_t begin = B.cnt->n_recheck_done;
   uint64_t end = B.cnt->n_recheck;
   if (end > B.max_vertices) end = B.max_vertices;
-  const uint64_t nw = (uint64_t)gridDim.x * EVAL_WARPS;
-  unsigned long long terms = 0;
-  for (uint64_t q = begin + (uint64_t)blockIdx.x * EVAL_WARPS + w; q < end; q += nw) {
+  const uint64_t nwarps = (uint64_t)gridDim.x * EVAL_WARPS;
+  unsigned long long terms[2] = {0, 0};
+  for (uint64_t q = begin + (uint64_t)blockIdx.x * EVAL_WARPS + w; q < end; q += nwarps) {
     const uint32_t i = B.recheck[q];
     int32_t y[MF_MAXD];
     double x[MF_MAXD];
 #pragma unroll
     for (int k = 0; k < MF_MAXD; k++) y[k] = k < F.d ? B.vert_y[(uint64_t)i * F.d + k] : 0;
     mf_vertex_x(F, y, x);
-    F64Acc a = warp_f64<false>(R, x, nullptr, sbuf[w], terms);
+    F64Acc a = warp_f64<false>(R, x, nullptr, sq[w][0], sq[w][1], terms);
     if (lane == 0) {
       B.vtab_f[B.vert_slot[i]] = a.f;
       if (fabs(a.f) < 1e-12) atomicAdd(&B.cnt->n_near_zero, 1ull);
     }
   }
-  if (lane == 0 && terms) atomicAdd(&B.cnt->eval_terms, terms);
+  if (lane == 0 && (terms[0] | terms[1])) {
+    atomicAdd(&B.cnt->eval_terms, terms[0]);
+    atomicAdd(&B.cnt->eval_terms_weak, terms[1]);
+  }
 }
 
 __global__ void k_advance_eval(MfCounters *c) {
@@ -237,18 +316,14 @@ __global__ void k_advance_eval(MfCounters *c) {
 // Mixed FP32 SIMT evaluator: thread per MIX_VPT points, support vectors in
 // shared memory tiles.  Per point it accumulates
 //   acc = sum alpha_j e_j,  A = sum |alpha_j| e_j,  Q = sum |alpha_j| e_j r_j^2
-// and bounds |f~ - f| <= A (gamma rho0 + eps_exp + (n/1 + 2) u) + Q gamma (d+2) u,
-// where rho0 = d (2 D eta + eta^2) bounds the error of r^2 from rounding the
-// coordinates to FP32 (eta = 2.01 u (|x|max + |s|max), D = |x|max + |s|max).
+// and bounds |f~ - f| by the coordinate rounding (eta = 2.01 u (|x|max +
+// |s|max) per coordinate, |r~^2 - r^2| <= 2 eta sqrt(d) r + d eta^2, and
+// sum |alpha| e r <= sqrt(A Q)), the ex2 error (2^-20), the exponent rounding
+// ((d+2) u gamma r^2) and the blocked FP32 summation.
 // ---------------------------------------------------------------------------
 #define MIX_THREADS 128
 #define MIX_VPT 2
 #define MIX_TILE 256
-
-struct MixOut {
-  double f;
-  double bound;
-};
 
 __device__ __forceinline__ void mix_tile_loop(const MfRbfDev &R, const float (*xs)[MF_MAXD],
                                               float *acc, float *A, float *Q, const float *s_sv,
@@ -268,7 +343,7 @@ __device__ __forceinline__ void mix_tile_loop(const MfRbfDev &R, const float (*x
           float t = xs[v][k] - s[k];
           r2 = fmaf(t, t, r2);
         }
-      const float e = exp2f(-g2 * r2);
+      const float e = ex2_approx(-g2 * r2);
       acc[v] = fmaf(al, e, acc[v]);
       const float ae = aa * e;
       A[v] += ae;
@@ -282,7 +357,7 @@ template <bool VERTS>
 __global__ void __launch_bounds__(MIX_THREADS) k_eval_mixed_f32(MfFrame F, MfRbfDev R, MfTraceBufs B,
                                                                 const double *pts, int64_t npts,
                                                                 double *fout, uint8_t *flag,
-                                                                double band, float smax) {
+                                                                double band) {
   __shared__ float s_sv[MF_MAXD * MIX_TILE];
   __shared__ float s_al[MIX_TILE];
   const int d = R.d;
@@ -299,7 +374,6 @@ __global__ void __launch_bounds__(MIX_THREADS) k_eval_mixed_f32(MfFrame F, MfRbf
        base += (uint64_t)gridDim.x * per_block) {
     float xs[MIX_VPT][MF_MAXD];
     double xmax[MIX_VPT];
-    double fx[MIX_VPT];
     uint64_t idx[MIX_VPT];
 #pragma unroll
     for (int v = 0; v < MIX_VPT; v++) {
@@ -324,7 +398,6 @@ __global__ void __launch_bounds__(MIX_THREADS) k_eval_mixed_f32(MfFrame F, MfRbf
         xs[v][k] = (float)x[k];
         xmax[v] = fmax(xmax[v], fabs(x[k]));
       }
-      fx[v] = 0.0;
     }
     float acc[MIX_VPT], A[MIX_VPT], Q[MIX_VPT];
 #pragma unroll
@@ -347,9 +420,7 @@ __global__ void __launch_bounds__(MIX_THREADS) k_eval_mixed_f32(MfFrame F, MfRbf
 #pragma unroll
     for (int v = 0; v < MIX_VPT; v++) {
       if (idx[v] >= end) continue;
-      // |r~^2 - r^2| <= sum_k eta (2 |t_k| + eta) <= 2 eta sqrt(d) r + d eta^2 per term, and
-      // sum |alpha| e r <= sqrt(A Q) (Cauchy-Schwarz).
-      const double D = xmax[v] + (double)smax;
+      const double D = xmax[v] + (double)R.smax;
       const double eta = 2.01 * u * D;
       const double Av = (double)A[v], Qv = (double)Q[v];
       const double coord = R.gamma * (2.0 * eta * sqrt((double)d) * sqrt(Av * Qv) + d * eta * eta * Av);
@@ -357,18 +428,18 @@ __global__ void __launch_bounds__(MIX_THREADS) k_eval_mixed_f32(MfFrame F, MfRbf
       const double nsum = (double)MIX_TILE + (double)R.n / MIX_TILE + 2.0;  // blocked FP32 sums
       const double bound = (coord + Av * (eps_exp + (nsum + 2.0) * u) +
                             Qv * R.gamma * (d + 2) * u) * 1.02 + 1e-30;
-      fx[v] = (double)acc[v] + R.b;
-      const bool recheck = fabs(fx[v]) <= fmax(bound, band);
+      const double fx = (double)acc[v] + R.b;
+      const bool recheck = fabs(fx) <= fmax(bound, band);
       if (VERTS) {
         const uint32_t slot = B.vert_slot[idx[v]];
-        B.vtab_f[slot] = fx[v];
+        B.vtab_f[slot] = fx;
         if (recheck) {
           unsigned long long q = atomicAdd(&B.cnt->n_recheck, 1ull);
           if (q < B.max_vertices) B.recheck[q] = (uint32_t)idx[v];
           else atomicOr(&B.cnt->err_overflow, 1u);
         }
       } else {
-        fout[idx[v]] = fx[v];
+        fout[idx[v]] = fx;
         flag[idx[v]] = recheck ? 1 : 0;
       }
     }
@@ -378,39 +449,113 @@ __global__ void __launch_bounds__(MIX_THREADS) k_eval_mixed_f32(MfFrame F, MfRbf
 // FP64 evaluation of flagged plain points (mf_eval mixed recheck), or of all
 // points when flag == NULL.
 __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_points_f64(MfRbfDev R, const double *pts, int64_t n,
-                                                        double *fout, const uint8_t *flag,
-                                                        unsigned long long *nre) {
-  __shared__ int sbuf[EVAL_WARPS][64];
+                                                        double *fout, const uint8_t *flag) {
+  __shared__ int sq[EVAL_WARPS][2][64];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t)gridDim.x * EVAL_WARPS;
-  for (int64_t i = (int64_t)blockIdx.x * EVAL_WARPS + w; i < n; i += nw) {
+  const int64_t nwarps = (int64_t)gridDim.x * EVAL_WARPS;
+  unsigned long long terms[2] = {0, 0};
+  for (int64_t i = (int64_t)blockIdx.x * EVAL_WARPS + w; i < n; i += nwarps) {
     if (flag && !flag[i]) continue;
     double x[MF_MAXD];
 #pragma unroll
     for (int k = 0; k < MF_MAXD; k++) x[k] = k < R.d ? pts[i * R.d + k] : 0.0;
-    unsigned long long terms = 0;
-    F64Acc a = warp_f64<false>(R, x, nullptr, sbuf[w], terms);
-    if (lane == 0) {
-      fout[i] = a.f;
-      if (nre) atomicAdd(nre, 1ull);
-    }
+    F64Acc a = warp_f64<false>(R, x, nullptr, sq[w][0], sq[w][1], terms);
+    if (lane == 0) fout[i] = a.f;
   }
 }
 
 // ---------------------------------------------------------------------------
-// Root solve (FP64): safeguarded Newton on g(t) = f(x1 + t (x2 - x1)) with the
-// analytic derivative g'(t) = -2 gamma sum alpha_i e_i (x - s_i).(x2 - x1),
-// bracket [lo, hi] kept under the sign rule s = [f >= 0]; start from the
-// linear interpolant of the end values.
+// Root solve along each traced edge: g(t) = f(x1 + t (x2 - x1)), t in [0,1],
+// g(0) and g(1) of opposite sign (Sec. VI's "iterative algorithm").
+//
+// 1. Segment screen (FP32): the support vectors within the FP64 screen
+//    distance of the whole segment are compacted into a per-warp list in
+//    shared memory, strong ones from the front, weak ones from the back.
+// 2. FP32 Newton from the linear interpolant of the end values, over that
+//    list, with hi/lo-split coordinates (x = x_hi + x_lo) so that differences
+//    keep FP32 relative accuracy; it also yields g''.
+// 3. FP64 Newton with a kept bracket [lo, hi] under the sign rule
+//    s = [f >= 0], over the same list (strong: FP64 exp; weak: exp_cheap).  A
+//    step is final when |step| <= 1e-7, or on the first FP64 step when
+//    |g''| step^2 <= 5e-11 |g'| (the remaining Newton error is then below
+//    ~3e-11 in t).  Lists that overflow fall back to full per-point screening.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(EVAL_WARPS * 32) k_roots_f64(MfFrame F, MfRbfDev R, MfTraceBufs B, uint64_t n_edges,
-                                                  double tol) {
-  __shared__ int sbuf[EVAL_WARPS][64];
+#define ROOT_WARPS 8
+#define NEAR_CAP 1024
+
+struct Root32 {
+  double g, gp, gpp;
+};
+
+// FP32 evaluation of g, g', g'' at t over the near list (all lanes).
+__device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const int *near, int ns, int nw,
+                                              const float *x1hi, const float *x1lo,
+                                              const float *dir32, float dd32, float t) {
+  const int lane = threadIdx.x & 31;
+  const float g2 = (float)(R.gamma * 1.4426950408889634);
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  const int total = ns + nw;
+  for (int i = lane; i < total; i += 32) {
+    const int j = i < ns ? near[i] : near[NEAR_CAP - 1 - (i - ns)];
+    float r2 = 0.f, proj = 0.f;
+#pragma unroll
+    for (int k = 0; k < MF_MAXD; k++) {
+      if (k < R.d) {
+        const float a = x1hi[k] - R.sv32[(int64_t)k * R.n + j];
+        const float b = fmaf(t, dir32[k], x1lo[k] - R.svlo32[(int64_t)k * R.n + j]);
+        const float df = a + b;
+        r2 = fmaf(df, df, r2);
+        proj = fmaf(df, dir32[k], proj);
+      }
+    }
+    const float e = R.alpha32[j] * ex2_approx(-g2 * r2);
+    s0 += e;
+    s1 = fmaf(e, proj, s1);
+    s2 = fmaf(e * proj, proj, s2);
+  }
+  s0 = mf_warp_sum_f(s0);
+  s1 = mf_warp_sum_f(s1);
+  s2 = mf_warp_sum_f(s2);
+  const double gm = R.gamma;
+  Root32 r;
+  r.g = (double)s0 + R.b;
+  r.gp = -2.0 * gm * (double)s1;
+  r.gpp = 4.0 * gm * gm * (double)s2 - 2.0 * gm * (double)dd32 * (double)s0;
+  return r;
+}
+
+// FP64 evaluation of g and g' at x over the near list (all lanes).
+template <bool ALL_STRONG>
+__device__ __forceinline__ F64Acc root_eval64(const MfRbfDev &R, const int *near, int ns, int nw,
+                                              const double *x, const double *dir,
+                                              unsigned long long *terms) {
+  const int lane = threadIdx.x & 31;
+  F64Acc acc = {0.0, 0.0, 0.f};
+  for (int i = lane; i < ns; i += 32) f64_term<true, true>(R, x, dir, near[i], acc);
+  for (int i = lane; i < nw; i += 32) {
+    if (ALL_STRONG) f64_term<true, true>(R, x, dir, near[NEAR_CAP - 1 - i], acc);
+    else f64_term<true, false>(R, x, dir, near[NEAR_CAP - 1 - i], acc);
+  }
+  terms[0] += ns + (ALL_STRONG ? nw : 0);
+  terms[1] += ALL_STRONG ? 0 : nw;
+  acc.f = mf_warp_sum_d(acc.f) + R.b;
+  acc.weak = mf_warp_sum_f(acc.weak);
+  acc.g = -2.0 * R.gamma * mf_warp_sum_d(acc.g);
+  return acc;
+}
+
+__global__ void __launch_bounds__(ROOT_WARPS * 32) k_roots_f64(MfFrame F, MfRbfDev R, MfTraceBufs B,
+                                                               uint64_t n_edges, double tol) {
+  __shared__ int snear[ROOT_WARPS][NEAR_CAP];
+  __shared__ int sq[ROOT_WARPS][2][64];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int d = F.d;
-  const uint64_t nw = (uint64_t)gridDim.x * EVAL_WARPS;
-  unsigned long long evals = 0, terms = 0;
-  for (uint64_t e = (uint64_t)blockIdx.x * EVAL_WARPS + w; e < n_edges; e += nw) {
+  const uint64_t nwarps = (uint64_t)gridDim.x * ROOT_WARPS;
+  const unsigned lt = (1u << lane) - 1u;
+  const float g32 = (float)R.gamma;
+  int *near = snear[w];
+  unsigned long long evals = 0, terms[2] = {0, 0};
+  for (uint64_t e = (uint64_t)blockIdx.x * ROOT_WARPS + w; e < n_edges; e += nwarps) {
     int32_t y[MF_MAXD], y2[MF_MAXD];
 #pragma unroll
     for (int k = 0; k < MF_MAXD; k++) y[k] = y2[k] = k < d ? B.edge_y[e * d + k] : 0;
@@ -418,17 +563,80 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_roots_f64(MfFrame F, MfRbfD
     double x1[MF_MAXD], x2[MF_MAXD], dir[MF_MAXD], x[MF_MAXD];
     mf_vertex_x(F, y, x1);
     mf_vertex_x(F, y2, x2);
+    float x1hi[MF_MAXD], x1lo[MF_MAXD], dir32[MF_MAXD];
+    float dd32 = 0.f;
 #pragma unroll
-    for (int k = 0; k < MF_MAXD; k++) dir[k] = k < d ? __dsub_rn(x2[k], x1[k]) : 0.0;
+    for (int k = 0; k < MF_MAXD; k++) {
+      dir[k] = k < d ? __dsub_rn(x2[k], x1[k]) : 0.0;
+      x1hi[k] = (float)x1[k];
+      x1lo[k] = (float)(x1[k] - (double)x1hi[k]);
+      dir32[k] = (float)dir[k];
+      dd32 = fmaf(dir32[k], dir32[k], dd32);
+    }
+    // 1. segment screen
+    int ns = 0, nw = 0;
+    for (int base = 0; base < R.n; base += 32) {
+      const int j = base + lane;
+      bool keep = false, strong = false;
+      if (j < R.n) {
+        float p[MF_MAXD], pd = 0.f;
+#pragma unroll
+        for (int k = 0; k < MF_MAXD; k++) {
+          p[k] = k < d ? (R.sv32[(int64_t)k * R.n + j] - x1hi[k]) : 0.f;
+          pd = fmaf(p[k], dir32[k], pd);
+        }
+        const float tt = fminf(fmaxf(pd / dd32, 0.f), 1.f);
+        float r2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < MF_MAXD; k++) {
+          const float q = fmaf(-tt, dir32[k], p[k]);
+          r2 = fmaf(q, q, r2);
+        }
+        keep = r2 <= R.screen_r2;
+        strong = g32 * r2 < R.strong32[j] + 0.5f;
+      }
+      const unsigned ms = __ballot_sync(FULL, keep && strong);
+      const unsigned mw = __ballot_sync(FULL, keep && !strong);
+      const int cs = ns + __popc(ms & lt), cw = nw + __popc(mw & lt);
+      if (keep && strong && cs + nw < NEAR_CAP) near[cs] = j;
+      if (keep && !strong && ns + cw < NEAR_CAP) near[NEAR_CAP - 1 - cw] = j;
+      ns += __popc(ms);
+      nw += __popc(mw);
+    }
+    __syncwarp();
+    const bool overflow = ns + nw > NEAR_CAP;
     const double f0 = B.edge_f[2 * e], f1 = B.edge_f[2 * e + 1];
     const bool s1 = f0 >= 0.0;
-    double lo = 0.0, hi = 1.0;
     double t = f0 / (f0 - f1);
     if (!(t > 0.0 && t < 1.0)) t = 0.5;
+    // 2. FP32 Newton
+    double gpp = INFINITY;
+    if (!overflow) {
+      double lo = 0.0, hi = 1.0;
+      for (int it = 0; it < 12; it++) {
+        const Root32 r = root_eval32(R, near, ns, nw, x1hi, x1lo, dir32, dd32, (float)t);
+        gpp = r.gpp;
+        if ((r.g >= 0.0) == s1) lo = t; else hi = t;
+        double tn = t - r.g / r.gp;
+        if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+        const double step = fabs(tn - t);
+        t = tn;
+        if (step <= 2e-6) break;
+      }
+    }
+    // 3. FP64 Newton with a kept bracket
+    double lo = 0.0, hi = 1.0;
     for (int it = 0; it < 64; it++) {
 #pragma unroll
       for (int k = 0; k < MF_MAXD; k++) x[k] = k < d ? __dadd_rn(x1[k], __dmul_rn(t, dir[k])) : 0.0;
-      F64Acc a = warp_f64<true>(R, x, dir, sbuf[w], terms);
+      F64Acc a;
+      if (overflow) {
+        a = warp_f64<true>(R, x, dir, sq[w][0], sq[w][1], terms);
+      } else {
+        a = root_eval64<false>(R, near, ns, nw, x, dir, terms);
+        if ((double)a.weak * 1.01 * WEAK_REL_ERR > R.weak_limit)
+          a = root_eval64<true>(R, near, ns, nw, x, dir, terms);
+      }
       evals++;
       if (a.f == 0.0) break;
       if ((a.f >= 0.0) == s1) lo = t; else hi = t;
@@ -436,7 +644,9 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_roots_f64(MfFrame F, MfRbfD
       if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
       const double step = fabs(tn - t);
       t = tn;
-      if (step <= tol || hi - lo <= 9.094947017729282e-13) break;
+      if (step <= tol || step <= 1e-7 || hi - lo <= 9.094947017729282e-13 ||
+          (it == 0 && fabs(gpp) * step * step <= 5e-11 * fabs(a.g)))
+        break;
     }
     if (lane == 0) {
       B.edge_t[e] = t;
@@ -445,7 +655,8 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_roots_f64(MfFrame F, MfRbfD
   }
   if (lane == 0 && evals) {
     atomicAdd(&B.cnt->root_evals, evals);
-    atomicAdd(&B.cnt->root_terms, terms);
+    atomicAdd(&B.cnt->root_terms, terms[0]);
+    atomicAdd(&B.cnt->root_terms_weak, terms[1]);
   }
 }
 
@@ -461,8 +672,7 @@ void mf_launch_eval_vertices_f64(const MfFrame &F, const MfRbfDev &R, const MfTr
 void mf_launch_eval_vertices_mixed(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
                                    int precision, double band, int sms, cudaStream_t st) {
   (void)precision;
-  k_eval_mixed_f32<true><<<sms * 4, MIX_THREADS, 0, st>>>(F, R, B, nullptr, 0, nullptr, nullptr,
-                                                          band, R.smax);
+  k_eval_mixed_f32<true><<<sms * 4, MIX_THREADS, 0, st>>>(F, R, B, nullptr, 0, nullptr, nullptr, band);
   k_recheck_vertices_f64<<<sms * 8, EVAL_WARPS * 32, 0, st>>>(F, R, B);
   k_advance_eval<<<1, 1, 0, st>>>(B.cnt);
 }
@@ -470,7 +680,7 @@ void mf_launch_eval_vertices_mixed(const MfFrame &F, const MfRbfDev &R, const Mf
 void mf_launch_roots_f64(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, uint64_t n_edges,
                          double tol, int sms, cudaStream_t st) {
   if (n_edges == 0) return;
-  k_roots_f64<<<sms * 8, EVAL_WARPS * 32, 0, st>>>(F, R, B, n_edges, tol);
+  k_roots_f64<<<sms * 4, ROOT_WARPS * 32, 0, st>>>(F, R, B, n_edges, tol);
 }
 
 extern "C" int mf_eval(mf_ctx *ctx, const mf_rbf *rbf, const double *q, int64_t n, int32_t precision,
@@ -487,7 +697,7 @@ extern "C" int mf_eval(mf_ctx *ctx, const mf_rbf *rbf, const double *q, int64_t 
   if (n == 0) return MF_OK;
   const int sms = ctx->sms;
   if (precision == MF_FP64) {
-    k_eval_points_f64<<<sms * 8, EVAL_WARPS * 32, 0, st>>>(R, q, n, f_out, nullptr, nullptr);
+    k_eval_points_f64<<<sms * 8, EVAL_WARPS * 32, 0, st>>>(R, q, n, f_out, nullptr);
   } else {
     uint8_t *flag = (uint8_t *)mf_ctx_buffer(ctx, MF_SLOT_SCAN, (size_t)n + 256);
     if (!flag) return MF_ERR_OOM;
@@ -495,8 +705,8 @@ extern "C" int mf_eval(mf_ctx *ctx, const mf_rbf *rbf, const double *q, int64_t 
     mf_frame_lattice(&F, R.d, 1.0, nullptr);
     MfTraceBufs B = {};
     k_eval_mixed_f32<false><<<sms * 4, MIX_THREADS, 0, st>>>(F, R, B, q, n, f_out, flag,
-                                                             band > 0 ? band : 1e-3, R.smax);
-    k_eval_points_f64<<<sms * 8, EVAL_WARPS * 32, 0, st>>>(R, q, n, f_out, flag, nullptr);
+                                                             band > 0 ? band : 1e-3);
+    k_eval_points_f64<<<sms * 8, EVAL_WARPS * 32, 0, st>>>(R, q, n, f_out, flag);
   }
   rc = mf_cuda_check(ctx, cudaGetLastError(), "mf_eval launch");
   if (rc) return rc;

@@ -34,8 +34,10 @@ struct MfCounters {
   unsigned long long n_recheck_done;
   unsigned long long root_evals;
   unsigned long long n_cell_edges;
-  unsigned long long eval_terms;   // RBF terms evaluated in FP64 by vertex evaluation
-  unsigned long long root_terms;   // RBF terms evaluated in FP64 by the root solve
+  unsigned long long eval_terms;   // RBF terms with FP64 exp, vertex evaluation
+  unsigned long long root_terms;   // RBF terms with FP64 exp, root solve
+  unsigned long long eval_terms_weak;  // RBF terms with the reduced-cost exp, vertex evaluation
+  unsigned long long root_terms_weak;  // RBF terms with the reduced-cost exp, root solve
   unsigned int err_table_full;     // a hash probe ran past the table
   unsigned int err_overflow;       // a list ran past its capacity
   unsigned int err_missing;        // a vertex expected in the table was absent
@@ -81,13 +83,16 @@ struct MfTraceBufs {
 struct MfRbfDev {
   int32_t d;
   int32_t n;
-  const float *sv32;   // [d][n]
+  const float *sv32;   // [d][n] FP32 rounding of the coordinates
+  const float *svlo32; // [d][n] s - (double)sv32: the low part of a hi/lo split
   const double *sv64;  // [d][n]
   const double *alpha; // [n]
   const float *alpha32;// [n]
+  const float *strong32; // [n] ln(|alpha| / 1e-9): term needs the FP64 exp iff gamma r^2 below
   double gamma, b;
   float screen_r2;     // keep a term in the FP64 sum iff r^2 (FP32) <= screen_r2
   double drop_bound;   // sum_i |alpha_i| exp(-gamma * screen cut): bound on dropped terms
+  double weak_limit;   // allowed error of the reduced-cost exp terms (2.5e-13 - drop_bound)
   float smax;          // max |s_ik| over all support-vector coordinates
 };
 

@@ -753,6 +753,8 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
   if (ctx->prof.on) {
     ctx->prof.stats.terms[MF_PH_EVAL] += (int64_t)h.eval_terms;
     ctx->prof.stats.terms[MF_PH_ROOTS] += (int64_t)h.root_terms;
+    ctx->prof.stats.terms_weak[MF_PH_EVAL] += (int64_t)h.eval_terms_weak;
+    ctx->prof.stats.terms_weak[MF_PH_ROOTS] += (int64_t)h.root_terms_weak;
   }
   {
     MfProfScope ps(ctx, MF_PH_COPY, st, 0);

@@ -80,7 +80,8 @@ class mf_scene(C.Structure):
 
 class mf_stats(C.Structure):
     _fields_ = [("ms", C.c_double * MF_PHASES), ("launches", C.c_int64 * MF_PHASES),
-                ("units", C.c_int64 * MF_PHASES), ("terms", C.c_int64 * MF_PHASES)]
+                ("units", C.c_int64 * MF_PHASES), ("terms", C.c_int64 * MF_PHASES),
+                ("terms_weak", C.c_int64 * MF_PHASES)]
 
 
 _lib = None
@@ -194,7 +195,8 @@ def mf_ctx_set_profiling(ctx, enable: bool):
 def mf_ctx_get_stats(ctx) -> dict:
     s = mf_stats()
     _check(ctx, load().mf_ctx_get_stats(ctx, C.byref(s)))
-    return {name: dict(ms=s.ms[i], launches=s.launches[i], units=s.units[i], terms=s.terms[i])
+    return {name: dict(ms=s.ms[i], launches=s.launches[i], units=s.units[i], terms=s.terms[i],
+                       terms_weak=s.terms_weak[i])
             for i, name in enumerate(PHASE_NAMES)}
 
 

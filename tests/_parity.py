@@ -46,7 +46,8 @@ def near_zero_edge(w, key):
     return bool(np.any(np.abs(f) < NEAR_ZERO))
 
 
-def compare_traces(w, g, o, t_tol=1e-9, f_tol=1e-12, check_f=True, check_cells=True):
+def compare_traces(w, g, o, t_tol=1e-9, f_tol=1e-12, check_f=True, check_cells=True,
+                   check_t=True):
     """Element-by-element comparison of a GPU trace with the oracle's."""
     gk = keys(g["edge_y"], g["edge_mask"])
     ok = keys(o["edge_y"], o["edge_mask"])
@@ -67,11 +68,11 @@ def compare_traces(w, g, o, t_tol=1e-9, f_tol=1e-12, check_f=True, check_cells=T
     gidx = np.array([gi[k] for k in common], dtype=np.int64)
     if check_f and len(common):
         assert np.max(np.abs(g["edge_f"][gidx] - o["edge_f"][oi])) <= f_tol
-    if "edge_t" in o and len(common) and g["edge_t"].shape[0]:
+    if check_t and len(common) and g["edge_t"].shape[0]:
         mr = o["edge_multiroot"][oi] == 0
         dt = np.abs(g["edge_t"][gidx] - o["edge_t"][oi])[mr]
         report["max_dt"] = float(dt.max()) if dt.size else 0.0
-        assert report["max_dt"] <= t_tol
+        assert report["max_dt"] <= t_tol, report
         dp = np.abs(g["points"][gidx] - o["edge_pt"][oi])[mr]
         assert (dp.max() if dp.size else 0.0) <= t_tol
     if check_cells and "cell_y" in o:
