@@ -186,6 +186,32 @@ int mf_certify(mf_ctx *ctx, const mf_robot *robot, const mf_scene *scene, const 
                const int64_t *cell_edge_idx, int64_t n_cells, uint8_t *point_verdict,
                double *margin, uint8_t *cell_verdict, void *stream);
 
+/* Size of the fixed device array used by mf_trace_noalloc (64 MiB). */
+#define MF_NOALLOC_SCRATCH_BYTES (64ull << 20)
+
+/* mf_trace without any allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- code running
+ * under another framework's memory pool, real-time loops that forbid
+ * allocation after start-up, processes whose device memory is reserved by
+ * someone else.  It computes what mf_trace computes (same arguments and
+ * outputs, no context) with all scratch (hash tables, lists, counters,
+ * prepared support vectors) carved from one file-scope device array of
+ * MF_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * exit.  It calls no cudaMalloc/cudaFree and no allocating library routine.
+ *  - Runs on the current device.  Its first call on a device looks up the
+ *    array's address (cudaGetSymbolAddress); make that call before any stream
+ *    capture.
+ *  - Capacities: opts->max_edges / max_vertices / max_cells, or (when 0) the
+ *    largest default that fits.  Requests whose tables and lists exceed the
+ *    array return MF_ERR_OOM; output buffers that are too small return
+ *    MF_ERR_CAPACITY with the counts filled (call again with larger ones).
+ *  - All calls on a device share the array: each clears what must start
+ *    empty, and calls that overlap on the GPU race and must not be issued.
+ *  - No context means no mf_last_error message: the return code is the
+ *    whole diagnosis. */
+int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const mf_trace_opts *opts,
+                     const double *seeds, int64_t n_seeds, mf_trace_out *out, void *stream);
+
 /* Native per-phase profiling (CUDA events recorded on the call's stream
  * around every kernel launch of the library; no effect on results). */
 #define MF_PHASES 12

@@ -33,7 +33,7 @@ MF_SPHERE = 1
 
 EXPORTS = ("mf_ctx_create", "mf_ctx_destroy", "mf_last_error", "mf_ctx_bytes", "mf_locate",
            "mf_eval", "mf_trace", "mf_trace_fetch", "mf_certify", "mf_ctx_set_profiling",
-           "mf_ctx_get_stats")
+           "mf_ctx_get_stats", "mf_trace_noalloc")
 
 MF_PHASES = 12
 PHASE_NAMES = ("prepare", "seeds", "expand_vertices", "eval", "expand_edges", "roots", "cells",
@@ -128,6 +128,9 @@ def load(build_if_missing: bool = True):
     L.mf_ctx_set_profiling.argtypes = [V, C.c_int]
     L.mf_ctx_get_stats.restype = C.c_int
     L.mf_ctx_get_stats.argtypes = [V, P(mf_stats)]
+    L.mf_trace_noalloc.restype = C.c_int
+    L.mf_trace_noalloc.argtypes = [P(mf_rbf), P(mf_domain), P(mf_trace_opts), V, C.c_int64,
+                                   P(mf_trace_out), V]
     _lib = L
     return L
 
@@ -186,6 +189,14 @@ def mf_trace(ctx, rbf: mf_rbf, dom: mf_domain, opts: mf_trace_opts, seeds_ptr, n
 
 def mf_trace_fetch(ctx, out: mf_trace_out, stream=0):
     return _check(ctx, load().mf_trace_fetch(ctx, C.byref(out), stream))
+
+
+def mf_trace_noalloc(rbf: mf_rbf, dom: mf_domain, opts: mf_trace_opts, seeds_ptr, n_seeds,
+                     out: mf_trace_out, stream=0) -> int:
+    """The allocation-free trace (for callers that cannot allocate device
+    memory); returns the MF_* code (there is no context to hold a message)."""
+    return load().mf_trace_noalloc(C.byref(rbf), C.byref(dom), C.byref(opts), seeds_ptr, n_seeds,
+                                   C.byref(out), stream)
 
 
 def mf_ctx_set_profiling(ctx, enable: bool):
