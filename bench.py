@@ -167,6 +167,53 @@ def cpu_baseline(w, budget_s=15.0):
     return {"value": rate, "unit": "simplices/s", "cores": 1, "kind": "oracle", "sample": sample}
 
 
+def run_served(ctx, n_requests, rate_hz, max_slots=48, hbm_bytes=120 << 30, seed=1005):
+    """Poisson stream of proof requests through the continuous-batching
+    server: p50 / p99 latency (arrival -> results fetched) and simplices/s."""
+    import torch
+    from paper_2406_04795_gb300 import mf
+    arrivals, reqs = W.served_requests(seed=seed, n_requests=n_requests, rate_hz=rate_hz)
+    free, _ = torch.cuda.mem_get_info()
+    hbm_bytes = int(min(hbm_bytes, free - (8 << 30)))  # what the proofs before left free
+    server = ctx.server(max_slots=max_slots, hbm_bytes=hbm_bytes)
+    lat, edges, nxt = [], 0, 0
+    live = {}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while nxt < n_requests or live:
+        now = time.perf_counter() - t0
+        if now > 600.0:
+            raise RuntimeError("served run exceeded 600 s")
+        while nxt < n_requests and arrivals[nxt] <= now:
+            w = reqs[nxt]
+            rid = server.submit(w, precision=mf.MF_MIXED_FP32, **W.shell_capacity(w))
+            live[rid] = arrivals[nxt]
+            nxt += 1
+        if not live:
+            time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+            continue
+        server.step()
+        for rid in list(live):
+            state = server.status(rid)[0]
+            if state == 2 or state < 0:
+                if state == 2:
+                    edges += server.fetch(rid)["n_edges"]
+                else:
+                    try:
+                        server.fetch(rid)
+                    except mf.MfError:
+                        pass
+                lat.append(time.perf_counter() - t0 - live.pop(rid))
+    wall = time.perf_counter() - t0
+    server.close()
+    lat_ms = np.array(lat) * 1e3
+    return {"requests": n_requests, "rate_hz": rate_hz, "slots": max_slots,
+            "arena_gib": round(hbm_bytes / 2**30, 1),
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "simplices_per_s": edges / wall, "wall_s": wall, "precision": "mixed",
+            "workload": "d in {4,5,6}, 512-8192 SVs, lambda in [0.03,0.08], 1-16 seeds"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -297,6 +344,26 @@ def run_gb300(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
+        if world == 1 and not args.no_extras:
+            # the same proof on the mixed-precision path
+            wm = make_workload(args.config, rank, args.lam)
+            wm.precision = "mixed" if w.precision == "fp64" else "fp64"
+            pm = Proof(ctx, wm)
+            pm.step()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(2):
+                rm, _, _, _ = pm.step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            msm = e0.elapsed_time(e1) / 2
+            line["other_precision"] = {"precision": wm.precision, "ms_per_proof": msm,
+                                       "value": rm["n_edges"] / (msm * 1e-3),
+                                       "edges_per_proof": rm["n_edges"],
+                                       "rechecked_vertices": rm["n_recheck"]}
+            del pm
+            line["served"] = run_served(ctx, args.served_requests, args.served_rate)
         print(json.dumps(line))
     ctx.close()
     if world > 1:
@@ -314,6 +381,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lam", type=float, default=None,
                     help="override the lattice scale (small profiling cases)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other-precision proof and the served run")
+    ap.add_argument("--served-requests", type=int, default=2000)
+    ap.add_argument("--served-rate", type=float, default=50.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

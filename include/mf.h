@@ -156,6 +156,17 @@ size_t mf_ctx_bytes(mf_ctx *ctx);
 int mf_locate(mf_ctx *ctx, int32_t d, double lambda, const double *offset_host,
               const double *points, int64_t n, int32_t *y_out, uint8_t *perm_out, void *stream);
 
+/* The exact domain test the tracing kernels use, as a table (host only, no
+ * GPU needed).  For s = sum(y) in [*smin, *smin + *span) and axis i, entries
+ * tab[(s - *smin) * d * 2 + 2i] and [... + 1] are the lowest and highest y_i
+ * whose coordinate x_i = lambda * (y_i - c s) + o_i (Ã_d map, rounded as the
+ * kernels round it) lies in [lo_i, hi_i]; an empty range has low > high.  A
+ * lattice vertex is in the box iff every y_i is in its range for s = sum(y).
+ * tab may be NULL to query the size (span * d * 2 int32); cap is tab's length.
+ * MF_ERR_DOMAIN if the table would exceed 2^22 rows. */
+int mf_domain_table(int32_t d, double lambda, const mf_domain *dom, int32_t *smin, int32_t *span,
+                    int32_t *tab, int64_t cap);
+
 /* f at n arbitrary points (the RBF kernel evaluation of the traced path).
  * q: device [n][d]; f_out: device [n].  precision as in mf_trace_opts; the
  * mixed paths apply the same FP64 recheck band (band <= 0 means 1e-3). */
@@ -173,6 +184,50 @@ int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom, const mf_trac
 /* Copies the last mf_trace result of this context into `out` (two-call
  * pattern after MF_ERR_CAPACITY). */
 int mf_trace_fetch(mf_ctx *ctx, mf_trace_out *out, void *stream);
+
+/* Many independent traces (Sec. IV-A tracing, Sec. IV-C cells) in one launch:
+ * trace t has its own RBF rbfs[t] (any d, support-vector count, gamma), domain
+ * doms[t], options opts[t] (lambda, precision, capacities, flags) and seeds
+ * seeds[t] (a host array of n device pointers to [n_seeds[t]][d_t]).  All
+ * traces advance together: one CUDA-graph launch (a conditional WHILE loop
+ * over breadth-first steps) runs every level of every trace, with the work
+ * items of all traces sharing each kernel.  Results go to outs[t] exactly as
+ * mf_trace writes them; a trace whose buffers are too small gets its counts
+ * and the call returns MF_ERR_CAPACITY (call again with larger buffers).
+ * 1 <= n <= 1024.  Capacities default to 2^20 edges per trace. */
+int mf_trace_batch(mf_ctx *ctx, int32_t n, const mf_rbf *rbfs, const mf_domain *doms,
+                   const mf_trace_opts *opts, const double *const *seeds, const int64_t *n_seeds,
+                   mf_trace_out *outs, void *stream);
+
+/* Proof server (continuous batching of tracing requests; the paper's
+ * planner-side loop is out of scope, this is the serving runtime around the
+ * traced path).  The server holds up to max_slots concurrent traces in an HBM
+ * arena of hbm_bytes (one server per context).  Requests queue FIFO; each
+ * mf_server_step admits queued requests while a slot is free and the
+ * request's buffers (sized from its opts capacities, defaults 2^20 edges) fit
+ * the arena, runs one breadth-first step of every running trace (a CUDA
+ * graph captured at creation), and finishes traces whose search ended
+ * (roots, cells, CSR over just those slots).  A trace gives its slot back
+ * when it finishes or fails; its results stay in the arena until fetched, so
+ * a caller that never fetches eventually blocks admission by memory.  The
+ * caller keeps each request's inputs (support vectors, alpha, seeds) alive
+ * until the request is done, and passes the same stream to every step and
+ * fetch of one server (memory handed back is reused in stream order). */
+typedef struct mf_server mf_server;
+int mf_server_create(mf_ctx *ctx, int32_t max_slots, size_t hbm_bytes, mf_server **out);
+void mf_server_destroy(mf_server *s);
+/* Queues a request; *id receives its handle. */
+int mf_server_submit(mf_server *s, const mf_rbf *rbf, const mf_domain *dom,
+                     const mf_trace_opts *opts, const double *seeds, int64_t n_seeds, int64_t *id);
+/* One scheduling round (see above); reports running and queued requests. */
+int mf_server_step(mf_server *s, void *stream, int32_t *n_running, int32_t *n_queued);
+/* state: 0 queued, 1 running, 2 done, < 0 the request's error code; times are
+ * host steady-clock seconds at submission, admission and completion. */
+int mf_server_status(mf_server *s, int64_t id, int32_t *state, double *t_submit, double *t_admit,
+                     double *t_done);
+/* Copies a done request's results (as mf_trace does) and releases its
+ * memory; a failed request returns its error code and is forgotten. */
+int mf_server_fetch(mf_server *s, int64_t id, mf_trace_out *out, void *stream);
 
 /* Certification (Sec. V-C, App. A): forward kinematics of every point, exact
  * capsule/box and capsule/sphere distances, per-point margin

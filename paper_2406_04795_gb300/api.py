@@ -118,6 +118,61 @@ class Context:
             _buffers=res)
         return result
 
+    def trace_batch(self, workloads, precisions=None, roots=True, cells=True, capacities=None,
+                    batch_cap=1 << 24, recheck_band=1e-3, root_tol=1e-12, stream=None):
+        """Traces many workloads in one batched call (mf_trace_batch).
+
+        workloads: objects with sv, alpha, gamma, b, lam, offset, lo, hi, seeds.
+        capacities: per-trace dicts (max_edges, max_vertices, max_cells); the
+        output buffers are allocated at those capacities."""
+        n = len(workloads)
+        precisions = precisions or [mf.MF_FP64] * n
+        capacities = capacities or [dict(max_edges=1 << 18)] * n
+        rbfs = (mf.mf_rbf * n)()
+        doms = (mf.mf_domain * n)()
+        opts = (mf.mf_trace_opts * n)()
+        outs = (mf.mf_trace_out * n)()
+        seeds = (C.c_void_p * n)()
+        nseeds = (C.c_int64 * n)()
+        keep, bufs = [], []
+        flags = (mf.MF_WANT_ROOTS if roots else 0) | (mf.MF_WANT_CELLS if cells else 0)
+        for t, w in enumerate(workloads):
+            r, k = self.rbf(w.sv, w.alpha, w.gamma, w.b)
+            keep.append(k)
+            rbfs[t] = r
+            doms[t] = self.domain(w.lo, w.hi, w.offset)
+            cap = capacities[t]
+            me = int(cap.get("max_edges", 1 << 18))
+            mv = int(cap.get("max_vertices", me))
+            mc = int(cap.get("max_cells", 2 * me))
+            opts[t] = mf.mf_trace_opts(float(w.lam), int(batch_cap), int(precisions[t]),
+                                       float(recheck_band), float(root_tol), me, mv, mc, flags)
+            sd = _dev(w.seeds, torch.float64, self.device).reshape(-1, r.d)
+            keep.append(sd)
+            seeds[t] = sd.data_ptr() if sd.numel() else None
+            nseeds[t] = sd.shape[0]
+            ce = mc * (r.d + 1) * r.d // 2
+            b = self._alloc_outputs(r.d, me, mc, ce)
+            bufs.append(b)
+            outs[t] = self._out_struct(b, r.d)
+        mf.mf_trace_batch(self.h, rbfs, doms, opts, seeds, nseeds, outs, _stream_handle(stream))
+        results = []
+        for t in range(n):
+            o, b = outs[t], bufs[t]
+            E, Cn, CE = o.n_edges, o.n_cells, o.n_cell_edges
+            results.append(dict(
+                edge_y=b["edge_y"][:E], edge_mask=b["edge_mask"][:E], edge_f=b["edge_f"][:E],
+                edge_t=b["edge_t"][:E], points=b["points"][:E], cell_y=b["cell_y"][:Cn],
+                cell_perm=b["cell_perm"][:Cn], cell_off=b["cell_off"][:Cn + 1],
+                cell_idx=b["cell_idx"][:CE], n_edges=E, n_cells=Cn, n_cell_edges=CE,
+                n_vertices=o.n_vertices, n_near_zero=o.n_near_zero, n_recheck=o.n_recheck,
+                n_boundary=o.n_boundary, n_dead_seeds=o.n_dead_seeds, levels=o.levels,
+                root_evals=o.root_evals))
+        return results
+
+    def server(self, max_slots=64, hbm_bytes=16 << 30):
+        return Server(self, max_slots, hbm_bytes)
+
     def _alloc_outputs(self, d, E, Cn, CE):
         E, Cn, CE = max(int(E), 1), max(int(Cn), 1), max(int(CE), 1)
         dev = self.device
@@ -183,3 +238,68 @@ class Context:
         mf.mf_certify(self.h, robot, scene, pts.data_ptr(), P, d, offp, idxp, nc, verdict.data_ptr(),
                       margin.data_ptr(), cvp, _stream_handle(stream))
         return verdict[:P], margin[:P], cv
+
+
+class Server:
+    """Continuous-batching proof server (mf_server_*): submit requests at any
+    time, call step() to admit, advance and finish traces, fetch() results."""
+
+    def __init__(self, ctx: Context, max_slots=64, hbm_bytes=16 << 30):
+        self.ctx = ctx
+        self.h = mf.mf_server_create(ctx.h, max_slots, hbm_bytes)
+        self._keep = {}
+
+    def close(self):
+        if self.h:
+            mf.mf_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, w, precision=mf.MF_MIXED_FP32, roots=True, cells=True, max_edges=1 << 20,
+               max_vertices=0, max_cells=0, batch_cap=1 << 24, recheck_band=1e-3, root_tol=1e-12):
+        r, keep = self.ctx.rbf(w.sv, w.alpha, w.gamma, w.b)
+        dom = self.ctx.domain(w.lo, w.hi, w.offset)
+        sd = _dev(w.seeds, torch.float64, self.ctx.device).reshape(-1, r.d)
+        opts = mf.mf_trace_opts(float(w.lam), int(batch_cap), int(precision), float(recheck_band),
+                                float(root_tol), int(max_edges), int(max_vertices), int(max_cells),
+                                (mf.MF_WANT_ROOTS if roots else 0) | (mf.MF_WANT_CELLS if cells else 0))
+        rid = mf.mf_server_submit(self.ctx.h, self.h, r, dom, opts, sd.data_ptr(), sd.shape[0])
+        self._keep[rid] = (keep, sd, r.d, max_edges, max_cells or 2 * max_edges)
+        return rid
+
+    def step(self, stream=None):
+        return mf.mf_server_step(self.ctx.h, self.h, _stream_handle(stream))
+
+    def status(self, rid):
+        return mf.mf_server_status(self.ctx.h, self.h, rid)
+
+    def fetch(self, rid, stream=None):
+        keep, sd, d, me, mc = self._keep[rid]
+        # two-call pattern: the counts first (capacity error, request kept),
+        # then buffers of exactly that size
+        probe = mf.mf_trace_out()
+        rc = mf.mf_server_fetch(self.ctx.h, self.h, rid, probe, _stream_handle(stream), check=False)
+        if rc not in (mf.MF_OK, mf.MF_ERR_CAPACITY):
+            self._keep.pop(rid, None)
+            mf._check(self.ctx.h, rc)
+        bufs = self.ctx._alloc_outputs(d, probe.n_edges, probe.n_cells, probe.n_cell_edges)
+        out = probe  # an empty result fits zero capacities and is already fetched
+        if rc == mf.MF_ERR_CAPACITY:
+            out = self.ctx._out_struct(bufs, d)
+            mf.mf_server_fetch(self.ctx.h, self.h, rid, out, _stream_handle(stream))
+        del self._keep[rid]
+        E, Cn, CE = out.n_edges, out.n_cells, out.n_cell_edges
+        return dict(edge_y=bufs["edge_y"][:E], edge_mask=bufs["edge_mask"][:E],
+                    edge_f=bufs["edge_f"][:E], edge_t=bufs["edge_t"][:E], points=bufs["points"][:E],
+                    cell_y=bufs["cell_y"][:Cn], cell_perm=bufs["cell_perm"][:Cn],
+                    cell_off=bufs["cell_off"][:Cn + 1], cell_idx=bufs["cell_idx"][:CE],
+                    n_edges=E, n_cells=Cn, n_cell_edges=CE, n_vertices=out.n_vertices,
+                    n_near_zero=out.n_near_zero, n_recheck=out.n_recheck,
+                    n_boundary=out.n_boundary, n_dead_seeds=out.n_dead_seeds, levels=out.levels,
+                    root_evals=out.root_evals)

@@ -14,95 +14,100 @@
 #include "mf_internal.cuh"
 #include "mf_ctx.h"
 
-#define CERT_MAX_OBS 256
+#define CERT_MAX_OBS 128
 #define CERT_THREADS 128
 
-struct CertObs {
-  double R[9];
-  double t[3];
-  double h[3];  // box half extents; sphere radius in h[0]
+template <typename T>
+struct CertObsT {
+  T R[9];
+  T t[3];
+  T h[3];  // box half extents; sphere radius in h[0]
   int type;
 };
+typedef CertObsT<double> CertObs;
 
-__device__ __forceinline__ double box_F(const double *a, const double *dl, const double *h, double t) {
-  double s = 0.0;
+template <typename T>
+__device__ __forceinline__ T box_F(const T *a, const T *dl, const T *h, T t) {
+  T s = 0;
 #pragma unroll
   for (int i = 0; i < 3; i++) {
-    const double p = fabs(fma(t, dl[i], a[i])) - h[i];
-    if (p > 0.0) s = fma(p, p, s);
+    const T p = fabs(fma(t, dl[i], a[i])) - h[i];
+    if (p > (T)0) s = fma(p, p, s);
   }
   return s;
 }
 
 // Squared distance from segment [a, a+dl] (box frame) to the box |p_i| <= h_i.
-__device__ double seg_box_d2(const double *a, const double *dl, const double *h) {
-  double bp[8];
+template <typename T>
+__device__ T seg_box_d2(const T *a, const T *dl, const T *h) {
+  T bp[8];
   int nb = 0;
-  bp[nb++] = 0.0;
-  bp[nb++] = 1.0;
+  bp[nb++] = 0;
+  bp[nb++] = 1;
 #pragma unroll
   for (int i = 0; i < 3; i++) {
-    if (dl[i] != 0.0) {
-      const double t1 = (h[i] - a[i]) / dl[i], t2 = (-h[i] - a[i]) / dl[i];
-      if (t1 > 0.0 && t1 < 1.0) bp[nb++] = t1;
-      if (t2 > 0.0 && t2 < 1.0) bp[nb++] = t2;
+    if (dl[i] != (T)0) {
+      const T t1 = (h[i] - a[i]) / dl[i], t2 = (-h[i] - a[i]) / dl[i];
+      if (t1 > (T)0 && t1 < (T)1) bp[nb++] = t1;
+      if (t2 > (T)0 && t2 < (T)1) bp[nb++] = t2;
     }
   }
   // insertion sort (<= 8 entries)
   for (int i = 1; i < nb; i++) {
-    const double v = bp[i];
+    const T v = bp[i];
     int j = i - 1;
     while (j >= 0 && bp[j] > v) { bp[j + 1] = bp[j]; j--; }
     bp[j + 1] = v;
   }
-  double best = box_F(a, dl, h, 0.0);
-  best = fmin(best, box_F(a, dl, h, 1.0));
+  T best = box_F<T>(a, dl, h, (T)0);
+  best = fmin(best, box_F<T>(a, dl, h, (T)1));
   for (int k = 0; k + 1 < nb; k++) {
-    const double ta = bp[k], tb = bp[k + 1];
+    const T ta = bp[k], tb = bp[k + 1];
     if (!(tb > ta)) continue;
-    const double tm = 0.5 * (ta + tb);
-    double A = 0.0, Bc = 0.0;
+    const T tm = (T)0.5 * (ta + tb);
+    T A = 0, Bc = 0;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
-      const double p = fma(tm, dl[i], a[i]);
-      double c0;
+      const T p = fma(tm, dl[i], a[i]);
+      T c0;
       if (p > h[i]) c0 = a[i] - h[i];
       else if (p < -h[i]) c0 = a[i] + h[i];
       else continue;
       A = fma(dl[i], dl[i], A);
-      Bc = fma(2.0 * dl[i], c0, Bc);
+      Bc = fma((T)2 * dl[i], c0, Bc);
     }
-    if (A > 0.0) {
-      double ts = -Bc / (2.0 * A);
+    if (A > (T)0) {
+      T ts = -Bc / ((T)2 * A);
       ts = fmin(fmax(ts, ta), tb);
-      best = fmin(best, box_F(a, dl, h, ts));
+      best = fmin(best, box_F<T>(a, dl, h, ts));
     }
   }
   return best;
 }
 
-__device__ double seg_obstacle_dist(const CertObs &o, const double *pa, const double *pb) {
-  double a[3], b[3], dl[3];
+template <typename T>
+__device__ T seg_obstacle_dist(const CertObsT<T> &o, const T *pa, const T *pb) {
+  T a[3], b[3], dl[3];
   // local = R^T (p - t)
-  const double wa[3] = {pa[0] - o.t[0], pa[1] - o.t[1], pa[2] - o.t[2]};
-  const double wb[3] = {pb[0] - o.t[0], pb[1] - o.t[1], pb[2] - o.t[2]};
+  const T wa[3] = {pa[0] - o.t[0], pa[1] - o.t[1], pa[2] - o.t[2]};
+  const T wb[3] = {pb[0] - o.t[0], pb[1] - o.t[1], pb[2] - o.t[2]};
 #pragma unroll
   for (int i = 0; i < 3; i++) {
     a[i] = o.R[i] * wa[0] + o.R[3 + i] * wa[1] + o.R[6 + i] * wa[2];
     b[i] = o.R[i] * wb[0] + o.R[3 + i] * wb[1] + o.R[6 + i] * wb[2];
     dl[i] = b[i] - a[i];
   }
-  if (o.type == MF_BOX) return sqrt(seg_box_d2(a, dl, o.h));
+  if (o.type == MF_BOX) return sqrt(seg_box_d2<T>(a, dl, o.h));
   // sphere at the local origin: clamped projection of the centre
-  const double dd = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
-  double t = 0.0;
-  if (dd > 0.0) {
+  const T dd = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
+  T t = 0;
+  if (dd > (T)0) {
     t = -(a[0] * dl[0] + a[1] * dl[1] + a[2] * dl[2]) / dd;
-    t = fmin(fmax(t, 0.0), 1.0);
+    t = fmin(fmax(t, (T)0), (T)1);
   }
-  const double c0 = fma(t, dl[0], a[0]), c1 = fma(t, dl[1], a[1]), c2 = fma(t, dl[2], a[2]);
-  const double dist = sqrt(c0 * c0 + c1 * c1 + c2 * c2) - o.h[0];
-  return dist > 0.0 ? dist : 0.0;
+  const T c0 = fma(t, dl[0], a[0]), c1 = fma(t, dl[1], a[1]), c2 = fma(t, dl[2], a[2]);
+  const T dist = sqrt(c0 * c0 + c1 * c1 + c2 * c2) - o.h[0];
+  return dist > (T)0 ? dist : (T)0;
 }
 
 __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int nl, const double *dh, const double *radius, int nobs,
@@ -111,18 +116,18 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int nl, const d
                                                     int64_t n, int d, uint8_t *verdict,
                                                     double *margin) {
   __shared__ CertObs so[CERT_MAX_OBS];
-  __shared__ float4 sbound[CERT_MAX_OBS];  // obstacle centre and bounding-sphere radius
+  __shared__ CertObsT<float> sof[CERT_MAX_OBS];  // FP32 copy for the lower bounds
   __shared__ double sdh[MF_MAXD * 4], srad[MF_MAXD], ssa[MF_MAXD], sca[MF_MAXD];
   for (int i = threadIdx.x; i < nobs; i += blockDim.x) {
     CertObs o;
-    for (int k = 0; k < 9; k++) o.R[k] = pose[12 * i + k];
-    for (int k = 0; k < 3; k++) o.t[k] = pose[12 * i + 9 + k];
-    o.type = type[i];
-    for (int k = 0; k < 3; k++) o.h[k] = o.type == MF_BOX ? 0.5 * dims[3 * i + k] : dims[3 * i + k];
+    CertObsT<float> of;
+    for (int k = 0; k < 9; k++) of.R[k] = (float)(o.R[k] = pose[12 * i + k]);
+    for (int k = 0; k < 3; k++) of.t[k] = (float)(o.t[k] = pose[12 * i + 9 + k]);
+    of.type = o.type = type[i];
+    for (int k = 0; k < 3; k++)
+      of.h[k] = (float)(o.h[k] = o.type == MF_BOX ? 0.5 * dims[3 * i + k] : dims[3 * i + k]);
     so[i] = o;
-    const double rb = o.type == MF_BOX ? sqrt(o.h[0] * o.h[0] + o.h[1] * o.h[1] + o.h[2] * o.h[2])
-                                       : o.h[0];
-    sbound[i] = make_float4((float)o.t[0], (float)o.t[1], (float)o.t[2], (float)rb);
+    sof[i] = of;
   }
   for (int i = threadIdx.x; i < nl * 4; i += blockDim.x) sdh[i] = dh[i];
   for (int i = threadIdx.x; i < nl; i += blockDim.x) {
@@ -160,21 +165,23 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int nl, const d
     org[3 * (i + 1) + 1] = T[7];
     org[3 * (i + 1) + 2] = T[11];
   }
-  // margin = max over (link, obstacle) of radius - distance.  A pair whose
-  // bounding-sphere lower bound lb on the distance gives radius - lb <= the
-  // best exact margin so far cannot change the maximum and is skipped; the
-  // pair with the largest radius - lb is evaluated first.  lb is computed in
-  // FP32 with a relative slack of 1e-5, so it never exceeds the true distance.
+  // margin = max over (link, obstacle) of radius - distance.  Every pair first
+  // gets the same distance computed in FP32; minus a slack of 1e-4 (1 + the
+  // largest coordinate), far above the FP32 rounding of the computation
+  // (about 1e-6 of that scale), it is a lower bound lb on the true distance.
+  // A pair with radius - lb <= the best exact margin so far cannot change the
+  // maximum and is skipped; the pair with the largest radius - lb is
+  // evaluated first, so typically only it is evaluated in FP64.
+  float org32[3 * (MF_MAXD + 1)];
+  for (int k = 0; k < 3 * (nl + 1); k++) org32[k] = (float)org[k];
   auto lower_bound = [&](int i, int k) -> float {
-    const float ax = (float)org[3 * i], ay = (float)org[3 * i + 1], az = (float)org[3 * i + 2];
-    const float bx = (float)org[3 * i + 3], by = (float)org[3 * i + 4], bz = (float)org[3 * i + 5];
-    const float mx = 0.5f * (ax + bx), my = 0.5f * (ay + by), mz = 0.5f * (az + bz);
-    const float hl = 0.5f * sqrtf((bx - ax) * (bx - ax) + (by - ay) * (by - ay) + (bz - az) * (bz - az));
-    const float4 c = sbound[k];
-    const float dc = sqrtf((mx - c.x) * (mx - c.x) + (my - c.y) * (my - c.y) + (mz - c.z) * (mz - c.z));
-    const float scale = fabsf(mx) + fabsf(my) + fabsf(mz) + fabsf(c.x) + fabsf(c.y) + fabsf(c.z) +
-                        hl + c.w;
-    return dc - hl - c.w - 1e-5f * scale - 1e-6f;
+    const float *a = &org32[3 * i], *b = &org32[3 * i + 3];
+    const float dist = seg_obstacle_dist<float>(sof[k], a, b);
+    float scale = 1.f;
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+      scale = fmaxf(scale, fmaxf(fmaxf(fabsf(a[c]), fabsf(b[c])), fabsf(sof[k].t[c]) + sof[k].h[c]));
+    return dist - 1e-4f * (1.f + scale);
   };
   double best = -INFINITY;
   int bi = -1, bk = -1;

@@ -6,16 +6,16 @@
 // the path must save).  One warp per point.  Each lane screens one support
 // vector per step in FP32 and sorts it into one of three classes:
 //   dropped  gamma r^2 > T, T chosen so that all dropped terms sum to <= 1e-13;
-//   strong   |alpha| e^{-gamma r^2} may exceed tau = 1e-9: FP64 distance and
+//   strong   |alpha| e^{-gamma r^2} may exceed tau = 3e-10: FP64 distance and
 //            the FP64 exp of the CUDA math library;
-//   weak     the rest: FP64 distance, and e^a by a Cody-Waite reduction
-//            a = k ln2 + r with 2^(r/ln2) from the hardware ex2 (relative error
-//            below 2^-20) scaled exactly by 2^k.
-// Strong and weak terms are compacted into two per-warp queues, so FP64 lanes
-// never idle on skipped terms and each batch of 32 runs one code path.  The
-// weak terms' error is bounded on the fly (6e-7 x sum of their magnitudes);
-// if the bound would push the total error above 2.5e-13 the point is
-// evaluated again with every kept term strong.
+//   weak     the rest: evaluated entirely in FP32 with hi/lo-split
+//            coordinates (x = x_hi + x_lo, s = s_hi + s_lo, so differences keep
+//            FP32 relative accuracy) and the hardware ex2; no FP64 instruction.
+// Strong and weak terms are compacted into two per-warp queues, so lanes never
+// idle on skipped terms and each batch of 32 runs one code path.  The weak
+// terms' error is bounded on the fly (their summed magnitude times a relative
+// bound computed on the host); if the bound would push the total error above
+// 2.5e-13 the point is evaluated again with every kept term strong.
 //
 // Mixed FP32 SIMT path: one thread per two points, support vectors broadcast
 // from shared memory, FP32 differences and ex2, and a per-point rigorous bound
@@ -27,25 +27,12 @@
 #include "mf_ctx.h"
 
 #define FULL 0xffffffffu
-#define WEAK_REL_ERR 6e-7  // relative error bound of exp_cheap (2^-20 plus rounding)
-#define STRONG_TAU 1e-9
+#define STRONG_TAU 3e-10  // terms above this magnitude use the FP64 exp
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
-}
-
-// e^a for a <= 0: Cody-Waite reduction a = k ln2 + r (|r| <= ln2/2), e^r as
-// 2^(r log2 e) by the hardware ex2 in FP32, exact scaling by 2^k through the
-// exponent field.  Relative error < 2^-20 + 2^-24.
-__device__ __forceinline__ double exp_cheap(double a) {
-  const double kd = rint(a * 1.4426950408889634);
-  const double r = fma(-kd, 0.6931471805599453, a);
-  const float e = ex2_approx((float)r * 1.44269504f);
-  const int k = (int)kd;
-  if (k < -1020) return 0.0;
-  return (double)e * __longlong_as_double((long long)(k + 1023) << 52);
 }
 
 // ---------------------------------------------------------------------------
@@ -94,7 +81,22 @@ __global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alph
   }
 }
 
+size_t mf_rbf_prep_bytes(int d, int64_t n) {
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t nb = (size_t)n;
+  return 256 + al(nb * d * 8) + 2 * al(nb * d * 4) + 2 * al(nb * 4);
+}
+
 int mf_prepare_rbf(mf_ctx *ctx, const mf_rbf *rbf, MfRbfDev *out, cudaStream_t st) {
+  if (!rbf || rbf->d < 2 || rbf->d > MF_MAXD || rbf->n_sv < 1 || rbf->n_sv > (1ll << 30))
+    return mf_set_error(ctx, MF_ERR_INVALID, "bad RBF parameters");
+  char *base = (char *)mf_ctx_buffer(ctx, MF_SLOT_RBF, mf_rbf_prep_bytes(rbf->d, rbf->n_sv));
+  if (!base) return MF_ERR_OOM;
+  return mf_prepare_rbf_at(ctx, rbf, base, out, st);
+}
+
+// As mf_prepare_rbf, into `base` (mf_rbf_prep_bytes bytes of device memory).
+int mf_prepare_rbf_at(mf_ctx *ctx, const mf_rbf *rbf, char *base, MfRbfDev *out, cudaStream_t st) {
   if (!rbf || rbf->d < 2 || rbf->d > MF_MAXD || rbf->n_sv < 1 || rbf->n_sv > (1ll << 30) ||
       !rbf->sv || !rbf->alpha || !(rbf->gamma > 0.0) || !std::isfinite(rbf->gamma) ||
       !std::isfinite(rbf->b))
@@ -102,9 +104,6 @@ int mf_prepare_rbf(mf_ctx *ctx, const mf_rbf *rbf, MfRbfDev *out, cudaStream_t s
   const int d = rbf->d, n = (int)rbf->n_sv;
   const size_t nb = (size_t)n;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  const size_t bytes = 256 + al(nb * d * 8) + 2 * al(nb * d * 4) + 2 * al(nb * 4);
-  char *base = (char *)mf_ctx_buffer(ctx, MF_SLOT_RBF, bytes);
-  if (!base) return MF_ERR_OOM;
   MfRbfStats *dst = (MfRbfStats *)base;
   char *p = base + 256;
   double *sv64 = (double *)p; p += al(nb * d * 8);
@@ -140,6 +139,9 @@ int mf_prepare_rbf(mf_ctx *ctx, const mf_rbf *rbf, MfRbfDev *out, cudaStream_t s
   out->screen_r2 = (float)((T + 0.5) / rbf->gamma);
   out->drop_bound = sa * std::exp(-T);
   out->weak_limit = 2.5e-13 - out->drop_bound;
+  // relative error of a weak FP32 term on the kept range gamma r^2 <= T + 1/2
+  out->weak_rel = 1.1 * ((d + 2) * 5.9604644775390625e-08 * (T + 0.5)) + 9.5367431640625e-07 +
+                  2.0 * 5.9604644775390625e-08;
   out->smax = h.max_abs_s;
   return MF_OK;
 }
@@ -150,9 +152,28 @@ int mf_prepare_rbf(mf_ctx *ctx, const mf_rbf *rbf, MfRbfDev *out, cudaStream_t s
 struct F64Acc {
   double f, g;  // f (with b) and, with GRAD, grad f . dir
   float weak;   // sum of |term| over weak terms (error bound input)
+  float wf, wg; // FP32 partial sums of the weak terms
 };
 
-template <bool GRAD, bool STRONG>
+// x split as x_hi + x_lo (both FP32) so that FP32 differences to a support
+// vector split the same way keep FP32 relative accuracy.
+struct Split32 {
+  float hi[MF_MAXD], lo[MF_MAXD], dir[MF_MAXD];
+};
+
+__device__ __forceinline__ Split32 split32(int d, const double *x, const double *dir) {
+  Split32 s;
+#pragma unroll
+  for (int k = 0; k < MF_MAXD; k++) {
+    s.hi[k] = k < d ? (float)x[k] : 0.f;
+    s.lo[k] = k < d ? (float)(x[k] - (double)s.hi[k]) : 0.f;
+    s.dir[k] = (k < d && dir) ? (float)dir[k] : 0.f;
+  }
+  return s;
+}
+
+// Strong term: FP64 difference, FP64 exp of the CUDA math library.
+template <bool GRAD>
 __device__ __forceinline__ void f64_term(const MfRbfDev &R, const double *x, const double *dir,
                                          int j, F64Acc &acc) {
   if (j < 0) return;
@@ -165,11 +186,34 @@ __device__ __forceinline__ void f64_term(const MfRbfDev &R, const double *x, con
       if (GRAD) proj = fma(t, dir[k], proj);
     }
   }
-  const double a = -R.gamma * r2;
-  const double e = R.alpha[j] * (STRONG ? exp(a) : exp_cheap(a));
+  const double e = R.alpha[j] * exp(-R.gamma * r2);
   acc.f += e;
-  if (!STRONG) acc.weak += (float)fabs(e);
   if (GRAD) acc.g = fma(e, proj, acc.g);
+}
+
+// Weak term (|alpha| e <= tau): FP32 throughout with hi/lo-split coordinates.
+// Its relative error is at most (d+2) u gamma r^2 (differences, squares and
+// the exponent's rounding, u = 2^-24) + 2^-20 (ex2) + 2u (alpha, product); on
+// the kept range gamma r^2 <= T + 1/2 the host bounds this by R.weak_rel.
+template <bool GRAD>
+__device__ __forceinline__ void f32_weak_term(const MfRbfDev &R, const Split32 &x, int j,
+                                              F64Acc &acc) {
+  if (j < 0) return;
+  const float g2 = (float)(R.gamma * 1.4426950408889634);
+  float r2 = 0.f, proj = 0.f;
+#pragma unroll
+  for (int k = 0; k < MF_MAXD; k++) {
+    if (k < R.d) {
+      const float t = (x.hi[k] - R.sv32[(int64_t)k * R.n + j]) +
+                      (x.lo[k] - R.svlo32[(int64_t)k * R.n + j]);
+      r2 = fmaf(t, t, r2);
+      if (GRAD) proj = fmaf(t, x.dir[k], proj);
+    }
+  }
+  const float e = R.alpha32[j] * ex2_approx(-g2 * r2);
+  acc.wf += e;
+  acc.weak += fabsf(e);
+  if (GRAD) acc.wg = fmaf(e, proj, acc.wg);
 }
 
 // Pops 32 entries of a queue of length n (>= 32) into lane `j`.
@@ -194,7 +238,8 @@ __device__ F64Acc warp_f64_pass(const MfRbfDev &R, const double *x, const double
 #pragma unroll
   for (int k = 0; k < MF_MAXD; k++) x32[k] = k < R.d ? (float)x[k] : 0.f;
   const float g32 = (float)R.gamma;
-  F64Acc acc = {0.0, 0.0, 0.f};
+  F64Acc acc = {0.0, 0.0, 0.f, 0.f, 0.f};
+  const Split32 xs = split32(R.d, x, dir);
   int ns = 0, nw = 0;
   const unsigned lt = (1u << lane) - 1u;
   for (int base = 0; base < R.n; base += 32) {
@@ -221,22 +266,22 @@ __device__ F64Acc warp_f64_pass(const MfRbfDev &R, const double *x, const double
     terms[1] += __popc(mw);
     if (ns >= 32) {
       const int jj = pop32(qs, ns, lane);
-      f64_term<GRAD, true>(R, x, dir, jj, acc);
+      f64_term<GRAD>(R, x, dir, jj, acc);
     }
     if (nw >= 32) {
       const int jj = pop32(qw, nw, lane);
-      f64_term<GRAD, false>(R, x, dir, jj, acc);
+      f32_weak_term<GRAD>(R, xs, jj, acc);
     }
   }
   __syncwarp();
   const int js = lane < ns ? qs[lane] : -1;
   const int jw = lane < nw ? qw[lane] : -1;
   __syncwarp();
-  f64_term<GRAD, true>(R, x, dir, js, acc);
-  f64_term<GRAD, false>(R, x, dir, jw, acc);
-  acc.f = mf_warp_sum_d(acc.f) + R.b;
+  f64_term<GRAD>(R, x, dir, js, acc);
+  f32_weak_term<GRAD>(R, xs, jw, acc);
+  acc.f = mf_warp_sum_d(acc.f) + (double)mf_warp_sum_f(acc.wf) + R.b;
   acc.weak = mf_warp_sum_f(acc.weak);
-  if (GRAD) acc.g = -2.0 * R.gamma * mf_warp_sum_d(acc.g);
+  if (GRAD) acc.g = -2.0 * R.gamma * (mf_warp_sum_d(acc.g) + (double)mf_warp_sum_f(acc.wg));
   return acc;
 }
 
@@ -245,7 +290,7 @@ template <bool GRAD>
 __device__ __forceinline__ F64Acc warp_f64(const MfRbfDev &R, const double *x, const double *dir,
                                            int *qs, int *qw, unsigned long long *terms) {
   F64Acc a = warp_f64_pass<GRAD, false>(R, x, dir, qs, qw, terms);
-  if ((double)a.weak * 1.01 * WEAK_REL_ERR > R.weak_limit)
+  if ((double)a.weak * 1.01 * R.weak_rel > R.weak_limit)
     a = warp_f64_pass<GRAD, true>(R, x, dir, qs, qw, terms);
   return a;
 }
@@ -475,7 +520,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_points_f64(MfRbfDev R,
 //    list, with hi/lo-split coordinates (x = x_hi + x_lo) so that differences
 //    keep FP32 relative accuracy; it also yields g''.
 // 3. FP64 Newton with a kept bracket [lo, hi] under the sign rule
-//    s = [f >= 0], over the same list (strong: FP64 exp; weak: exp_cheap).  A
+//    s = [f >= 0], over the same list (strong: FP64 exp; weak: FP32).  A
 //    step is final when |step| <= 1e-7, or on the first FP64 step when
 //    |g''| step^2 <= 5e-11 |g'| (the remaining Newton error is then below
 //    ~3e-11 in t).  Lists that overflow fall back to full per-point screening.
@@ -530,32 +575,32 @@ __device__ __forceinline__ F64Acc root_eval64(const MfRbfDev &R, const int *near
                                               const double *x, const double *dir,
                                               unsigned long long *terms) {
   const int lane = threadIdx.x & 31;
-  F64Acc acc = {0.0, 0.0, 0.f};
-  for (int i = lane; i < ns; i += 32) f64_term<true, true>(R, x, dir, near[i], acc);
-  for (int i = lane; i < nw; i += 32) {
-    if (ALL_STRONG) f64_term<true, true>(R, x, dir, near[NEAR_CAP - 1 - i], acc);
-    else f64_term<true, false>(R, x, dir, near[NEAR_CAP - 1 - i], acc);
+  F64Acc acc = {0.0, 0.0, 0.f, 0.f, 0.f};
+  for (int i = lane; i < ns; i += 32) f64_term<true>(R, x, dir, near[i], acc);
+  if (ALL_STRONG) {
+    for (int i = lane; i < nw; i += 32) f64_term<true>(R, x, dir, near[NEAR_CAP - 1 - i], acc);
+  } else {
+    const Split32 xs = split32(R.d, x, dir);
+    for (int i = lane; i < nw; i += 32) f32_weak_term<true>(R, xs, near[NEAR_CAP - 1 - i], acc);
   }
   terms[0] += ns + (ALL_STRONG ? nw : 0);
   terms[1] += ALL_STRONG ? 0 : nw;
-  acc.f = mf_warp_sum_d(acc.f) + R.b;
+  acc.f = mf_warp_sum_d(acc.f) + (double)mf_warp_sum_f(acc.wf) + R.b;
   acc.weak = mf_warp_sum_f(acc.weak);
-  acc.g = -2.0 * R.gamma * mf_warp_sum_d(acc.g);
+  acc.g = -2.0 * R.gamma * (mf_warp_sum_d(acc.g) + (double)mf_warp_sum_f(acc.wg));
   return acc;
 }
 
-__global__ void __launch_bounds__(ROOT_WARPS * 32) k_roots_f64(MfFrame F, MfRbfDev R, MfTraceBufs B,
-                                                               uint64_t n_edges, double tol) {
-  __shared__ int snear[ROOT_WARPS][NEAR_CAP];
-  __shared__ int sq[ROOT_WARPS][2][64];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// Solves the root of edge e (all lanes of the warp); near: NEAR_CAP ints,
+// qs / qw: 64-entry queues, all in this warp's shared memory.
+__device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, uint64_t e,
+                          double tol, int *near, int *qs, int *qw, unsigned long long &evals,
+                          unsigned long long *terms) {
+  const int lane = threadIdx.x & 31;
   const int d = F.d;
-  const uint64_t nwarps = (uint64_t)gridDim.x * ROOT_WARPS;
   const unsigned lt = (1u << lane) - 1u;
   const float g32 = (float)R.gamma;
-  int *near = snear[w];
-  unsigned long long evals = 0, terms[2] = {0, 0};
-  for (uint64_t e = (uint64_t)blockIdx.x * ROOT_WARPS + w; e < n_edges; e += nwarps) {
+  {
     int32_t y[MF_MAXD], y2[MF_MAXD];
 #pragma unroll
     for (int k = 0; k < MF_MAXD; k++) y[k] = y2[k] = k < d ? B.edge_y[e * d + k] : 0;
@@ -631,10 +676,10 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32) k_roots_f64(MfFrame F, MfRbfD
       for (int k = 0; k < MF_MAXD; k++) x[k] = k < d ? __dadd_rn(x1[k], __dmul_rn(t, dir[k])) : 0.0;
       F64Acc a;
       if (overflow) {
-        a = warp_f64<true>(R, x, dir, sq[w][0], sq[w][1], terms);
+        a = warp_f64<true>(R, x, dir, qs, qw, terms);
       } else {
         a = root_eval64<false>(R, near, ns, nw, x, dir, terms);
-        if ((double)a.weak * 1.01 * WEAK_REL_ERR > R.weak_limit)
+        if ((double)a.weak * 1.01 * R.weak_rel > R.weak_limit)
           a = root_eval64<true>(R, near, ns, nw, x, dir, terms);
       }
       evals++;
@@ -653,11 +698,156 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32) k_roots_f64(MfFrame F, MfRbfD
       for (int k = 0; k < d; k++) B.edge_pt[e * d + k] = __dadd_rn(x1[k], __dmul_rn(t, dir[k]));
     }
   }
-  if (lane == 0 && evals) {
+}
+
+__device__ __forceinline__ void root_flush(const MfTraceBufs &B, unsigned long long evals,
+                                           const unsigned long long *terms) {
+  if ((threadIdx.x & 31) == 0 && evals) {
     atomicAdd(&B.cnt->root_evals, evals);
     atomicAdd(&B.cnt->root_terms, terms[0]);
     atomicAdd(&B.cnt->root_terms_weak, terms[1]);
   }
+}
+
+__global__ void __launch_bounds__(ROOT_WARPS * 32) k_roots_f64(MfFrame F, MfRbfDev R, MfTraceBufs B,
+                                                               uint64_t n_edges, double tol) {
+  __shared__ int snear[ROOT_WARPS][NEAR_CAP];
+  __shared__ int sq[ROOT_WARPS][2][64];
+  const int w = threadIdx.x >> 5;
+  const uint64_t nwarps = (uint64_t)gridDim.x * ROOT_WARPS;
+  unsigned long long evals = 0, terms[2] = {0, 0};
+  for (uint64_t e = (uint64_t)blockIdx.x * ROOT_WARPS + w; e < n_edges; e += nwarps)
+    root_edge(F, R, B, e, tol, snear[w], sq[w][0], sq[w][1], evals, terms);
+  root_flush(B, evals, terms);
+}
+
+// ---------------------------------------------------------------------------
+// Batched evaluation and roots: one warp per work item, the item's trace found
+// through the plan's prefix array; every slot has its own support vectors,
+// precision and tables.
+// ---------------------------------------------------------------------------
+
+// Warp-level FP32 evaluation of f at x with the rigorous bound of the mixed
+// path (lane-strided sums: each lane adds about n/32 terms, then a 5-level
+// tree), all lanes get (f~, bound).
+__device__ void warp_f32_bound(const MfRbfDev &R, const double *x, double &f, double &bound) {
+  const int lane = threadIdx.x & 31;
+  const int d = R.d;
+  const float g2 = (float)(R.gamma * 1.4426950408889634);
+  float xs[MF_MAXD];
+  double xmax = 0.0;
+#pragma unroll
+  for (int k = 0; k < MF_MAXD; k++) {
+    xs[k] = k < d ? (float)x[k] : 0.f;
+    if (k < d) xmax = fmax(xmax, fabs(x[k]));
+  }
+  float acc = 0.f, A = 0.f, Q = 0.f;
+  for (int j = lane; j < R.n; j += 32) {
+    float r2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < MF_MAXD; k++)
+      if (k < d) {
+        const float t = xs[k] - R.sv32[(int64_t)k * R.n + j];
+        r2 = fmaf(t, t, r2);
+      }
+    const float al = R.alpha32[j];
+    const float e = ex2_approx(-g2 * r2);
+    acc = fmaf(al, e, acc);
+    const float ae = fabsf(al) * e;
+    A += ae;
+    Q = fmaf(ae, r2, Q);
+  }
+  acc = mf_warp_sum_f(acc);
+  A = mf_warp_sum_f(A);
+  Q = mf_warp_sum_f(Q);
+  const double u = 5.9604644775390625e-08;
+  const double D = xmax + (double)R.smax;
+  const double eta = 2.01 * u * D;
+  const double Av = (double)A, Qv = (double)Q;
+  const double coord = R.gamma * (2.0 * eta * sqrt((double)d) * sqrt(Av * Qv) + d * eta * eta * Av);
+  const double nsum = (double)R.n / 32.0 + 6.0;
+  bound = (coord + Av * (9.5367431640625e-07 + (nsum + 2.0) * u) + Qv * R.gamma * (d + 2) * u) * 1.02 +
+          1e-30;
+  f = (double)acc + R.b;
+}
+
+__global__ void __launch_bounds__(EVAL_WARPS * 32) k_b_eval(const MfSlot *slots, const MfBatchPlan *P,
+                                                           int n, int recheck) {
+  __shared__ int sq[EVAL_WARPS][2][64];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned long long *pfx = recheck ? P->pr : P->pv;
+  const unsigned long long total = pfx[n];
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * EVAL_WARPS;
+  for (unsigned long long item = (unsigned long long)blockIdx.x * EVAL_WARPS + w; item < total;
+       item += nwarps) {
+    const int t = mf_slot_of(pfx, n, item);
+    const MfSlot &S = slots[t];
+    const int d = S.F.d;
+    const unsigned long long local = item - pfx[t];
+    const uint64_t i = recheck ? (uint64_t)S.B.recheck[P->r0[t] + local] : P->v0[t] + local;
+    int32_t y[MF_MAXD];
+    double x[MF_MAXD];
+#pragma unroll
+    for (int k = 0; k < MF_MAXD; k++) y[k] = k < d ? S.B.vert_y[i * d + k] : 0;
+    mf_vertex_x(S.F, y, x);
+    const uint32_t slot = S.B.vert_slot[i];
+    if (recheck || S.precision == MF_FP64) {
+      unsigned long long terms[2] = {0, 0};
+      const F64Acc a = warp_f64<false>(S.R, x, nullptr, sq[w][0], sq[w][1], terms);
+      if (lane == 0) {
+        S.B.vtab_f[slot] = a.f;
+        if (fabs(a.f) < 1e-12) atomicAdd(&S.B.cnt->n_near_zero, 1ull);
+        atomicAdd(&S.B.cnt->eval_terms, terms[0]);
+        atomicAdd(&S.B.cnt->eval_terms_weak, terms[1]);
+      }
+    } else {
+      double f, bound;
+      warp_f32_bound(S.R, x, f, bound);
+      if (lane == 0) {
+        S.B.vtab_f[slot] = f;
+        if (fabs(f) <= fmax(bound, S.band)) {
+          const unsigned long long q = atomicAdd(&S.B.cnt->n_recheck, 1ull);
+          if (q < S.B.max_vertices) S.B.recheck[q] = (uint32_t)i;
+          else atomicOr(&S.B.cnt->err_overflow, 1u);
+        }
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(ROOT_WARPS * 32) k_b_roots(const MfSlot *slots, const MfBatchPlan *P,
+                                                            int n) {
+  __shared__ int snear[ROOT_WARPS][NEAR_CAP];
+  __shared__ int sq[ROOT_WARPS][2][64];
+  const int w = threadIdx.x >> 5;
+  const unsigned long long total = P->pe[n];
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * ROOT_WARPS;
+  for (unsigned long long item = (unsigned long long)blockIdx.x * ROOT_WARPS + w; item < total;
+       item += nwarps) {
+    const int t = mf_slot_of(P->pe, n, item);
+    const MfSlot &S = slots[t];
+    unsigned long long evals = 0, terms[2] = {0, 0};
+    root_edge(S.F, S.R, S.B, item - P->pe[t], S.root_tol, snear[w], sq[w][0], sq[w][1], evals,
+              terms);
+    root_flush(S.B, evals, terms);
+  }
+}
+
+void mf_b_launch_eval(const MfSlot *slots, MfBatchPlan *P, int n, bool any_mixed, int sms,
+                      cudaStream_t s) {
+  mf_b_launch_plan_eval(slots, P, n, false, s);
+  k_b_eval<<<sms * 8, EVAL_WARPS * 32, 0, s>>>(slots, P, n, 0);
+  if (any_mixed) {
+    mf_b_launch_plan_eval(slots, P, n, true, s);
+    k_b_eval<<<sms * 8, EVAL_WARPS * 32, 0, s>>>(slots, P, n, 1);
+  }
+  mf_b_launch_advance(slots, n, s);
+}
+
+void mf_b_launch_roots(const MfSlot *slots, MfBatchPlan *P, int n, const int32_t *only, int sms,
+                       cudaStream_t s) {
+  mf_b_launch_plan_edges(slots, P, n, 0, only, s);
+  k_b_roots<<<sms * 4, ROOT_WARPS * 32, 0, s>>>(slots, P, n);
 }
 
 // ---------------------------------------------------------------------------

@@ -19,6 +19,11 @@ struct MfFrame {
   int32_t ymin[MF_MAXD];    // lowest encodable lattice coordinate per axis
   int32_t range[MF_MAXD];   // encodable values per axis
   uint64_t stride[MF_MAXD]; // mixed-radix place value per axis
+  // Optional exact domain table: for s = sum(y) in [smin, smin + sspan) and
+  // each axis i, the interval of y_i whose x_i (computed as mf_vertex_x does)
+  // lies in [lo_i, hi_i].  NULL: the domain test evaluates x in FP64.
+  const int2 *dom_tab;      // [sspan][d]
+  int32_t smin, sspan;
 };
 
 // Device counters of one trace; read back by the host once per BFS level.
@@ -92,9 +97,82 @@ struct MfRbfDev {
   double gamma, b;
   float screen_r2;     // keep a term in the FP64 sum iff r^2 (FP32) <= screen_r2
   double drop_bound;   // sum_i |alpha_i| exp(-gamma * screen cut): bound on dropped terms
-  double weak_limit;   // allowed error of the reduced-cost exp terms (2.5e-13 - drop_bound)
+  double weak_limit;   // allowed error of the FP32 weak terms (2.5e-13 - drop_bound)
+  double weak_rel;     // relative error bound of one FP32 weak term
   float smax;          // max |s_ik| over all support-vector coordinates
 };
+
+// ------------------------------------------------------------------------
+// Batches: many independent traces advanced together by the same kernels.
+// Every work item (frontier edge x mask, vertex, edge, cell) carries its
+// trace through a prefix array over the slots.
+// ------------------------------------------------------------------------
+#define MF_MAX_SLOTS 1024
+
+struct MfSlot {  // one trace of a batch (device-resident descriptor)
+  MfFrame F;
+  MfRbfDev R;
+  MfTraceBufs B;
+  int32_t precision;
+  double band;             // mixed precision: FP64 recheck band
+  double root_tol;
+  unsigned long long cap;  // frontier edges expanded per step
+  uint32_t flags;          // MF_WANT_ROOTS | MF_WANT_CELLS
+};
+
+struct MfSlotState;
+struct MfBatchPlan;
+
+// Host launchers of the batched kernels.
+void mf_b_launch_init(const MfSlot *slots, MfSlotState *st, int n, cudaStream_t s);
+void mf_b_launch_expand(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, int n, bool edges,
+                        int sms, cudaStream_t s);
+void mf_b_launch_plan_eval(const MfSlot *slots, MfBatchPlan *P, int n, bool recheck, cudaStream_t s);
+void mf_b_launch_advance(const MfSlot *slots, int n, cudaStream_t s);
+void mf_b_launch_update(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, int n,
+                        cudaGraphConditionalHandle h, int use_handle, cudaStream_t s);
+// `only` (device, n int32, may be NULL): restrict roots / cells / CSR to the
+// slots with a non-zero entry.
+void mf_b_launch_plan_edges(const MfSlot *slots, MfBatchPlan *P, int n, int cells,
+                            const int32_t *only, cudaStream_t s);
+void mf_b_launch_cells(const MfSlot *slots, MfBatchPlan *P, int n, const int32_t *only, int sms,
+                       cudaStream_t s);
+void mf_b_launch_cell_edges(const MfSlot *slots, MfBatchPlan *P, int n, bool fill,
+                            const int32_t *only, int sms, cudaStream_t s);
+void mf_b_launch_eval(const MfSlot *slots, MfBatchPlan *P, int n, bool any_mixed, int sms,
+                      cudaStream_t s);
+void mf_b_launch_roots(const MfSlot *slots, MfBatchPlan *P, int n, const int32_t *only, int sms,
+                       cudaStream_t s);
+
+struct MfSlotState {  // breadth-first progress of one trace
+  unsigned long long cursor;     // next frontier edge to expand
+  unsigned long long level_end;  // end of the current level in the edge list
+  unsigned long long chunk_n;    // edges expanded by the current step
+  int32_t active, levels, err, pad;
+};
+
+struct MfBatchPlan {  // per-step work prefixes over the slots
+  unsigned long long px[MF_MAX_SLOTS + 1];  // expansion items (edges << d)
+  unsigned long long pv[MF_MAX_SLOTS + 1];  // vertices to evaluate
+  unsigned long long pr[MF_MAX_SLOTS + 1];  // vertices to re-check in FP64
+  unsigned long long pe[MF_MAX_SLOTS + 1];  // traced edges (roots, cells)
+  unsigned long long pc[MF_MAX_SLOTS + 1];  // cells (CSR)
+  unsigned long long v0[MF_MAX_SLOTS], r0[MF_MAX_SLOTS];
+  unsigned long long steps;  // steps run since the plan was cleared
+  int32_t overrun;           // the step limit stopped the search
+};
+#define MF_MAX_STEPS (1ull << 22)  // bound on breadth-first steps of one batch
+
+// Largest t in [0, n) with p[t] <= item (p non-decreasing, p[0] = 0).
+__device__ __forceinline__ int mf_slot_of(const unsigned long long *p, int n,
+                                          unsigned long long item) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
 
 // ------------------------------------------------------------------------
 // Lattice arithmetic with a fixed operation order (no contraction) so that a
@@ -117,6 +195,31 @@ __device__ __forceinline__ bool mf_in_box(const MfFrame &F, const double *x) {
   for (int i = 0; i < MF_MAXD; i++)
     if (i < F.d) in = in && (x[i] >= F.lo[i]) && (x[i] <= F.hi[i]);
   return in;
+}
+
+// Is lattice vertex y inside the box?  Exactly the decision mf_in_box makes on
+// mf_vertex_x(y): by integer table lookups when the frame has a table.
+__device__ __forceinline__ bool mf_vertex_in(const MfFrame &F, const int32_t *y) {
+  if (F.dom_tab) {
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < MF_MAXD; i++)
+      if (i < F.d) s += y[i];
+    const unsigned row = (unsigned)(s - F.smin);
+    if (row >= (unsigned)F.sspan) return false;
+    const int2 *r = F.dom_tab + (size_t)row * F.d;
+    bool in = true;
+#pragma unroll
+    for (int i = 0; i < MF_MAXD; i++)
+      if (i < F.d) {
+        const int2 b = r[i];
+        in = in && y[i] >= b.x && y[i] <= b.y;
+      }
+    return in;
+  }
+  double x[MF_MAXD];
+  mf_vertex_x(F, y, x);
+  return mf_in_box(F, x);
 }
 
 __device__ __forceinline__ unsigned long long mf_vertex_key(const MfFrame &F, const int32_t *y) {
@@ -240,6 +343,14 @@ int mf_ctx_sm_count(mf_ctx *ctx);
 
 // RBF preparation (mf_eval.cu): SoA FP32/FP64 copies in context buffers.
 int mf_prepare_rbf(mf_ctx *ctx, const mf_rbf *rbf, MfRbfDev *out, cudaStream_t st);
+size_t mf_rbf_prep_bytes(int d, int64_t n);
+int mf_prepare_rbf_at(mf_ctx *ctx, const mf_rbf *rbf, char *base, MfRbfDev *out, cudaStream_t st);
+// Trace host helpers (mf_trace.cu).
+int mf_build_frame(mf_ctx *ctx, int d, double lam, const mf_domain *dom, MfFrame *F);
+void mf_exclusive_scan(const int64_t *in, int64_t *out, int64_t n, int64_t *scratch, cudaStream_t st);
+uint64_t mf_next_pow2(uint64_t x);
+void mf_launch_seeds(const MfFrame &F, const MfTraceBufs &B, const double *seeds, int64_t n,
+                     bool vertices, cudaStream_t s);
 // Evaluate f at vertex-list entries [begin, end) read from the device counter
 // (FP64 path); writes vtab_f of each vertex's slot.
 void mf_launch_eval_vertices_f64(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
@@ -261,5 +372,8 @@ enum {
   MF_SLOT_MIXED = 7,
   MF_SLOT_CERT = 8,
   MF_SLOT_CELLIDX = 9,
-  MF_NUM_SLOTS = 10
+  MF_SLOT_DOMTAB = 10,
+  MF_SLOT_BATCH = 11,
+  MF_SLOT_SERVER = 12,
+  MF_NUM_SLOTS = 13
 };

@@ -262,6 +262,8 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   R.screen_r2 = (float)((T + 0.5) / rbf->gamma);
   R.drop_bound = sa * std::exp(-T);
   R.weak_limit = 2.5e-13 - R.drop_bound;
+  R.weak_rel = 1.1 * ((d + 2) * 5.9604644775390625e-08 * (T + 0.5)) + 9.5367431640625e-07 +
+               2.0 * 5.9604644775390625e-08;
   R.smax = hs.max_abs_s;
 
   // Everything that must start empty.

@@ -20,6 +20,7 @@
 //                      the edge table; first inserters append it to the edge list.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 
@@ -75,9 +76,7 @@ __device__ __forceinline__ void emit_edge(const MfFrame &F, const MfTraceBufs &B
 }
 
 __device__ __forceinline__ bool vertex_in(const MfFrame &F, const int32_t *v) {
-  double x[MF_MAXD];
-  mf_vertex_x(F, v, x);
-  return mf_in_box(F, x);
+  return mf_vertex_in(F, v);
 }
 
 // ---------------------------------------------------------------------------
@@ -157,13 +156,11 @@ __global__ void k_seed_edges(MfFrame F, MfTraceBufs B, const double *seeds, int6
 //   M a subset of T        : triangle (y, (S, M, rest)),          new vertex y + e(S) + e(M)
 //                            triangle (y - e(M), (M, S, rest)),    new vertex y - e(M)
 // ---------------------------------------------------------------------------
-__global__ void k_expand_vertices(MfFrame F, MfTraceBufs B, uint64_t e0, uint64_t n) {
+// Visits the new vertices of the cofaces of edge e selected by mask M;
+// returns how many of them lie outside the box.
+__device__ __forceinline__ unsigned expand_vertices_item(const MfFrame &F, const MfTraceBufs &B,
+                                                         uint64_t e, uint32_t M) {
   const int d = F.d;
-  const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  const uint64_t ei = tid >> d;
-  const uint32_t M = (uint32_t)(tid & ((1u << d) - 1u));
-  if (ei >= n || M == 0) return;
-  const uint64_t e = e0 + ei;
   int32_t y[MF_MAXD], w[MF_MAXD];
   load_y(B.edge_y + e * d, d, y);
   const uint32_t S = B.edge_mask[e];
@@ -181,19 +178,37 @@ __global__ void k_expand_vertices(MfFrame F, MfTraceBufs B, uint64_t e0, uint64_
     mf_add_mask(d, w, M, -1);
     if (vertex_in(F, w)) visit_vertex(F, B, w); else nb++;
   }
+  return nb;
+}
+
+__global__ void k_expand_vertices(MfFrame F, MfTraceBufs B, uint64_t e0, uint64_t n) {
+  const int d = F.d;
+  const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t ei = tid >> d;
+  const uint32_t M = (uint32_t)(tid & ((1u << d) - 1u));
+  if (ei >= n || M == 0) return;
+  const unsigned nb = expand_vertices_item(F, B, e0 + ei, M);
   if (nb) atomicAdd(&B.cnt->n_boundary, (unsigned long long)nb);
 }
 
 // Under the sign rule s = [f >= 0] a crossing triangle has exactly two
 // crossing edges (Sec. IV-A): the parent and the one joining the new vertex w
 // to the parent end whose sign differs from s(w).
+__device__ __forceinline__ void expand_edges_item(const MfFrame &F, const MfTraceBufs &B,
+                                                  uint64_t e, uint32_t M);
+
 __global__ void k_expand_edges(MfFrame F, MfTraceBufs B, uint64_t e0, uint64_t n) {
   const int d = F.d;
   const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   const uint64_t ei = tid >> d;
   const uint32_t M = (uint32_t)(tid & ((1u << d) - 1u));
   if (ei >= n || M == 0) return;
-  const uint64_t e = e0 + ei;
+  expand_edges_item(F, B, e0 + ei, M);
+}
+
+__device__ __forceinline__ void expand_edges_item(const MfFrame &F, const MfTraceBufs &B,
+                                                  uint64_t e, uint32_t M) {
+  const int d = F.d;
   int32_t y[MF_MAXD], w[MF_MAXD], u[MF_MAXD];
   load_y(B.edge_y + e * d, d, y);
   const uint32_t S = B.edge_mask[e];
@@ -250,11 +265,20 @@ __device__ __forceinline__ uint32_t perm_rank(const int *pi, int d) {
   return r;
 }
 
+__device__ __forceinline__ void cells_enum_edge(const MfFrame &F, const MfTraceBufs &B, uint64_t e,
+                                                int lane);
+
 __global__ void k_cells_enum(MfFrame F, MfTraceBufs B, uint64_t n_edges) {
-  const int d = F.d;
   const int lane = threadIdx.x & 31;
   const uint64_t e = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   if (e >= n_edges) return;
+  cells_enum_edge(F, B, e, lane);
+}
+
+// The n-cofaces j = lane, lane + 32, ... of edge e.
+__device__ __forceinline__ void cells_enum_edge(const MfFrame &F, const MfTraceBufs &B, uint64_t e,
+                                                int lane) {
+  const int d = F.d;
   int32_t y[MF_MAXD];
   load_y(B.edge_y + e * d, d, y);
   const uint32_t S = B.edge_mask[e];
@@ -314,10 +338,20 @@ __global__ void k_cells_enum(MfFrame F, MfTraceBufs B, uint64_t n_edges) {
 // Cell -> traced edges: the (d+1)d/2 edges of the cell (query type 2) found
 // in the edge table.  FILL = false counts, FILL = true writes indices.
 template <bool FILL>
+__device__ __forceinline__ void cell_edges_item(const MfFrame &F, const MfTraceBufs &B, uint64_t c,
+                                                int64_t *cnt_or_off);
+
+template <bool FILL>
 __global__ void k_cells_edges(MfFrame F, MfTraceBufs B, uint64_t n_cells, int64_t *cnt_or_off) {
-  const int d = F.d;
   const uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (c >= n_cells) return;
+  cell_edges_item<FILL>(F, B, c, cnt_or_off);
+}
+
+template <bool FILL>
+__device__ __forceinline__ void cell_edges_item(const MfFrame &F, const MfTraceBufs &B, uint64_t c,
+                                                int64_t *cnt_or_off) {
+  const int d = F.d;
   int32_t vi[MF_MAXD];
   int pi[MF_MAXD];
   load_y(B.cell_y + c * d, d, vi);
@@ -339,6 +373,269 @@ __global__ void k_cells_edges(MfFrame F, MfTraceBufs B, uint64_t n_cells, int64_
     vi[pi[i]] += 1;
   }
   if (!FILL) cnt_or_off[c] = count;
+}
+
+// ---------------------------------------------------------------------------
+// Batched kernels: all traces of a batch advance together.  Plan kernels run
+// as one block of MF_MAX_SLOTS threads (thread t = slot t) and write work
+// prefixes; work kernels are grid-stride loops over the prefix total, so a
+// step can be captured once in a CUDA graph and replayed for any mix of
+// active traces.
+// ---------------------------------------------------------------------------
+__device__ unsigned long long block_scan_u64(unsigned long long v, unsigned long long *total) {
+  __shared__ unsigned long long wsum[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  unsigned long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    const unsigned long long t = lane < nw ? wsum[lane] : 0ull;
+    unsigned long long s = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) wsum[lane] = s - t;
+    if (lane == 31) *total = s;
+  }
+  __syncthreads();
+  const unsigned long long r = x - v + wsum[w];
+  __syncthreads();
+  return r;
+}
+
+// After the seeds: every slot's first level is its seed edges.
+__global__ void k_b_init(const MfSlot *slots, MfSlotState *st, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const MfCounters *c = slots[t].B.cnt;
+  MfSlotState s;
+  s.cursor = 0;
+  s.level_end = c->n_edges < slots[t].B.max_edges ? c->n_edges : slots[t].B.max_edges;
+  s.chunk_n = 0;
+  s.err = (c->err_table_full || c->err_missing || c->err_overflow) ? 1 : 0;
+  s.active = (s.level_end > 0 && !s.err) ? 1 : 0;
+  s.levels = s.level_end > 0 ? 1 : 0;
+  s.pad = 0;
+  st[t] = s;
+}
+
+__global__ void k_b_plan_expand(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, int n) {
+  __shared__ unsigned long long total;
+  const int t = threadIdx.x;
+  unsigned long long cnt = 0;
+  if (t < n) {
+    unsigned long long chunk = 0;
+    if (st[t].active) {
+      const unsigned long long left = st[t].level_end - st[t].cursor;
+      chunk = left < slots[t].cap ? left : slots[t].cap;
+    }
+    st[t].chunk_n = chunk;
+    cnt = chunk << slots[t].F.d;
+  }
+  const unsigned long long ex = block_scan_u64(cnt, &total);
+  if (t < n) P->px[t] = ex;
+  if (t == 0) P->px[n] = total;
+}
+
+template <bool EDGES>
+__global__ void k_b_expand(const MfSlot *slots, const MfSlotState *st, const MfBatchPlan *P, int n) {
+  const unsigned long long total = P->px[n];
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long item = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+       item < total; item += stride) {
+    const int t = mf_slot_of(P->px, n, item);
+    const MfSlot &S = slots[t];
+    const int d = S.F.d;
+    const unsigned long long local = item - P->px[t];
+    const uint32_t M = (uint32_t)(local & ((1u << d) - 1u));
+    if (M == 0) continue;
+    const uint64_t e = st[t].cursor + (local >> d);
+    if (EDGES) {
+      expand_edges_item(S.F, S.B, e, M);
+    } else {
+      const unsigned nb = expand_vertices_item(S.F, S.B, e, M);
+      if (nb) atomicAdd(&S.B.cnt->n_boundary, (unsigned long long)nb);
+    }
+  }
+}
+
+// Vertex-evaluation and FP64-recheck ranges of every slot.
+__global__ void k_b_plan_eval(const MfSlot *slots, MfBatchPlan *P, int n) {
+  __shared__ unsigned long long total;
+  const int t = threadIdx.x;
+  unsigned long long cv = 0;
+  if (t < n && slots[t].B.cnt) {  // empty (zeroed) descriptors hold no trace
+    const MfTraceBufs &B = slots[t].B;
+    const unsigned long long v0 = B.cnt->v_evaluated;
+    unsigned long long v1 = B.cnt->n_vertices;
+    if (v1 > B.max_vertices) v1 = B.max_vertices;
+    cv = v1 > v0 ? v1 - v0 : 0;
+    P->v0[t] = v0;
+  }
+  unsigned long long ex = block_scan_u64(cv, &total);
+  if (t < n) P->pv[t] = ex;
+  if (t == 0) P->pv[n] = total;
+}
+
+__global__ void k_b_plan_recheck(const MfSlot *slots, MfBatchPlan *P, int n) {
+  __shared__ unsigned long long total;
+  const int t = threadIdx.x;
+  unsigned long long cr = 0;
+  if (t < n && slots[t].B.cnt) {
+    const MfTraceBufs &B = slots[t].B;
+    const unsigned long long r0 = B.cnt->n_recheck_done;
+    unsigned long long r1 = B.cnt->n_recheck;
+    if (r1 > B.max_vertices) r1 = B.max_vertices;
+    cr = r1 > r0 ? r1 - r0 : 0;
+    P->r0[t] = r0;
+  }
+  const unsigned long long ex = block_scan_u64(cr, &total);
+  if (t < n) P->pr[t] = ex;
+  if (t == 0) P->pr[n] = total;
+}
+
+__global__ void k_b_advance(const MfSlot *slots, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n || !slots[t].B.cnt) return;
+  MfCounters *c = slots[t].B.cnt;
+  c->v_evaluated = c->n_vertices;
+  c->n_recheck_done = c->n_recheck;
+}
+
+// End of a step: advance each slot's cursor; a finished level opens the next
+// one if it appended edges, otherwise the slot is done.  Any slot still active
+// keeps the enclosing graph loop running.
+__global__ void k_b_update(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, int n,
+                           cudaGraphConditionalHandle handle, int use_handle) {
+  __shared__ int any, stop;
+  if (threadIdx.x == 0) {
+    any = 0;
+    // a hard bound on the number of steps: the loop ends even if a slot
+    // never finished (reported as an overrun error)
+    stop = ++P->steps > MF_MAX_STEPS;
+    if (stop) P->overrun = 1;
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t < n && st[t].active && stop) {
+    st[t].active = 0;
+    st[t].err = 1;
+  } else if (t < n && st[t].active) {
+    MfSlotState s = st[t];
+    s.cursor += s.chunk_n;
+    s.chunk_n = 0;
+    if (s.cursor >= s.level_end) {
+      const MfCounters *c = slots[t].B.cnt;
+      const unsigned long long ne = c->n_edges;
+      if (c->err_table_full || c->err_missing || c->err_overflow || ne > slots[t].B.max_edges) {
+        s.err = 1;
+        s.active = 0;
+      } else if (ne > s.level_end) {
+        s.level_end = ne;
+        s.levels++;
+      } else {
+        s.active = 0;
+      }
+    }
+    st[t] = s;
+    if (s.active) atomicOr(&any, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && use_handle) cudaGraphSetConditional(handle, any ? 1u : 0u);
+}
+
+// Traced-edge and cell prefixes.  mode 0: edges of slots that want roots;
+// mode 1: cells of slots that want cells (into pc); mode 2: edges of slots
+// that want cells.
+__global__ void k_b_plan_edges(const MfSlot *slots, MfBatchPlan *P, int n, int mode,
+                               const int32_t *only) {
+  __shared__ unsigned long long total;
+  const int t = threadIdx.x;
+  unsigned long long c = 0;
+  if (t < n && (!only || only[t]) && slots[t].B.cnt) {
+    const MfTraceBufs &B = slots[t].B;
+    const uint32_t want = mode == 0 ? MF_WANT_ROOTS : MF_WANT_CELLS;
+    if (slots[t].flags & want) {
+      if (mode == 1) c = B.cnt->n_cells < B.max_cells ? B.cnt->n_cells : B.max_cells;
+      else c = B.cnt->n_edges < B.max_edges ? B.cnt->n_edges : B.max_edges;
+    }
+  }
+  const unsigned long long ex = block_scan_u64(c, &total);
+  unsigned long long *p = mode == 1 ? P->pc : P->pe;
+  if (t < n) p[t] = ex;
+  if (t == 0) p[n] = total;
+}
+
+__global__ void k_b_cells_enum(const MfSlot *slots, const MfBatchPlan *P, int n) {
+  const unsigned long long total = P->pe[n];
+  const int lane = threadIdx.x & 31;
+  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  for (unsigned long long item = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+       item < total; item += nwarps) {
+    const int t = mf_slot_of(P->pe, n, item);
+    cells_enum_edge(slots[t].F, slots[t].B, item - P->pe[t], lane);
+  }
+}
+
+template <bool FILL>
+__global__ void k_b_cell_edges(const MfSlot *slots, const MfBatchPlan *P, int n) {
+  const unsigned long long total = P->pc[n];
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long item = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+       item < total; item += stride) {
+    const int t = mf_slot_of(P->pc, n, item);
+    cell_edges_item<FILL>(slots[t].F, slots[t].B, item - P->pc[t], slots[t].B.cell_off);
+  }
+}
+
+// Host launchers of the batched kernels (used by the batch driver).
+void mf_b_launch_init(const MfSlot *slots, MfSlotState *st, int n, cudaStream_t s) {
+  k_b_init<<<(n + 255) / 256, 256, 0, s>>>(slots, st, n);
+}
+void mf_b_launch_expand(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, int n, bool edges,
+                        int sms, cudaStream_t s) {
+  if (!edges) {
+    k_b_plan_expand<<<1, MF_MAX_SLOTS, 0, s>>>(slots, st, P, n);
+    k_b_expand<false><<<sms * 8, 256, 0, s>>>(slots, st, P, n);
+  } else {
+    k_b_expand<true><<<sms * 8, 256, 0, s>>>(slots, st, P, n);
+  }
+}
+void mf_b_launch_plan_eval(const MfSlot *slots, MfBatchPlan *P, int n, bool recheck, cudaStream_t s) {
+  if (recheck) k_b_plan_recheck<<<1, MF_MAX_SLOTS, 0, s>>>(slots, P, n);
+  else k_b_plan_eval<<<1, MF_MAX_SLOTS, 0, s>>>(slots, P, n);
+}
+void mf_b_launch_advance(const MfSlot *slots, int n, cudaStream_t s) {
+  k_b_advance<<<(n + 255) / 256, 256, 0, s>>>(slots, n);
+}
+void mf_b_launch_update(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, int n,
+                        cudaGraphConditionalHandle h, int use_handle, cudaStream_t s) {
+  k_b_update<<<1, MF_MAX_SLOTS, 0, s>>>(slots, st, P, n, h, use_handle);
+}
+void mf_b_launch_plan_edges(const MfSlot *slots, MfBatchPlan *P, int n, int cells,
+                            const int32_t *only, cudaStream_t s) {
+  k_b_plan_edges<<<1, MF_MAX_SLOTS, 0, s>>>(slots, P, n, cells, only);
+}
+void mf_b_launch_cells(const MfSlot *slots, MfBatchPlan *P, int n, const int32_t *only, int sms,
+                       cudaStream_t s) {
+  k_b_plan_edges<<<1, MF_MAX_SLOTS, 0, s>>>(slots, P, n, 2, only);
+  k_b_cells_enum<<<sms * 8, 256, 0, s>>>(slots, P, n);
+}
+void mf_b_launch_cell_edges(const MfSlot *slots, MfBatchPlan *P, int n, bool fill,
+                            const int32_t *only, int sms, cudaStream_t s) {
+  if (!fill) {
+    k_b_plan_edges<<<1, MF_MAX_SLOTS, 0, s>>>(slots, P, n, 1, only);
+    k_b_cell_edges<false><<<sms * 8, 256, 0, s>>>(slots, P, n);
+  } else {
+    k_b_cell_edges<true><<<sms * 8, 256, 0, s>>>(slots, P, n);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -472,6 +769,108 @@ static int build_frame(mf_ctx *ctx, int d, double lam, const mf_domain *dom, MfF
     return mf_set_error(ctx, MF_ERR_DOMAIN,
                         "edge/cell keys need more than 64 bits (domain too large for lambda)");
   return MF_OK;
+}
+
+// The exact domain table of the frame (see MfFrame::dom_tab): x_i(y, s) =
+// lam * ((double)y_i - c * s) + o_i rises with y_i, so the in-box y_i form one
+// interval per (s, i), found by binary search with the device's operation
+// order (this translation unit's host code is compiled without contraction).
+// Fills `tab` and sets F->smin / F->sspan; false if the table would be too
+// large (the kernels then test the domain in FP64).
+bool mf_domain_table_host(MfFrame *F, std::vector<int2> &tab) {
+  const int d = F->d;
+  long long smin = 0, smax = 0;
+  for (int i = 0; i < d; i++) {
+    smin += F->ymin[i];
+    smax += (long long)F->ymin[i] + F->range[i] - 1;
+  }
+  const long long span = smax - smin + 1;
+  F->dom_tab = nullptr;
+  if (span <= 0 || span > (1ll << 22)) return false;
+  tab.assign((size_t)span * d, int2());
+  for (long long s = smin; s <= smax; s++) {
+    const double cs = F->c * (double)s;
+    for (int i = 0; i < d; i++) {
+      auto xof = [&](long long y) {
+        const volatile double u = (double)y - cs;
+        const volatile double w = F->lam * u;
+        return w + F->o[i];
+      };
+      const long long y0 = F->ymin[i], y1 = (long long)F->ymin[i] + F->range[i] - 1;
+      // midpoints from a + (b - a) / 2 with b > a: never truncated onto an end,
+      // so each search halves a non-empty interval (coordinates may be negative)
+      long long a = y0, b = y1 + 1;  // first y with x >= lo
+      while (a < b) {
+        const long long m = a + (b - a) / 2;
+        if (xof(m) >= F->lo[i]) b = m; else a = m + 1;
+      }
+      const long long first = a;
+      a = y0 - 1;
+      b = y1;  // last y with x <= hi
+      while (a < b) {
+        const long long m = a + (b - a + 1) / 2;
+        if (xof(m) <= F->hi[i]) a = m; else b = m - 1;
+      }
+      const long long last = a;
+      int2 v;
+      if (first <= last) { v.x = (int)first; v.y = (int)last; }
+      else { v.x = 1 << 30; v.y = -(1 << 30); }
+      tab[(size_t)(s - smin) * d + i] = v;
+    }
+  }
+  F->smin = (int32_t)smin;
+  F->sspan = (int32_t)span;
+  return true;
+}
+
+static int build_domain_table(mf_ctx *ctx, MfFrame *F, cudaStream_t st) {
+  std::vector<int2> tab;
+  if (!mf_domain_table_host(F, tab)) return MF_OK;  // FP64 test instead
+  int2 *dev = (int2 *)mf_ctx_buffer(ctx, MF_SLOT_DOMTAB, tab.size() * sizeof(int2));
+  if (!dev) return MF_ERR_OOM;
+  int rc = mf_cuda_check(ctx, cudaMemcpyAsync(dev, tab.data(), tab.size() * sizeof(int2),
+                                              cudaMemcpyHostToDevice, st),
+                         "domain table");
+  if (rc) return rc;
+  rc = mf_cuda_check(ctx, cudaStreamSynchronize(st), "domain table");
+  if (rc) return rc;
+  F->dom_tab = dev;
+  return MF_OK;
+}
+
+extern "C" int mf_domain_table(int32_t d, double lambda, const mf_domain *dom, int32_t *smin,
+                               int32_t *span, int32_t *tab, int64_t cap) {
+  if (d < 2 || d > MF_MAXD || !(lambda > 0.0) || !dom || !smin || !span) return MF_ERR_INVALID;
+  MfFrame F;
+  const int rc = build_frame(nullptr, d, lambda, dom, &F);
+  if (rc) return rc;
+  std::vector<int2> t;
+  if (!mf_domain_table_host(&F, t)) return MF_ERR_DOMAIN;
+  *smin = F.smin;
+  *span = F.sspan;
+  if (!tab) return MF_OK;
+  if (cap < (int64_t)t.size() * 2) return MF_ERR_CAPACITY;
+  for (size_t i = 0; i < t.size(); i++) {
+    tab[2 * i] = t[i].x;
+    tab[2 * i + 1] = t[i].y;
+  }
+  return MF_OK;
+}
+
+// Entry points for the batch driver (mf_batch.cu).
+int mf_build_frame(mf_ctx *ctx, int d, double lam, const mf_domain *dom, MfFrame *F) {
+  return build_frame(ctx, d, lam, dom, F);
+}
+void mf_exclusive_scan(const int64_t *in, int64_t *out, int64_t n, int64_t *scratch,
+                       cudaStream_t st) {
+  exclusive_scan(in, out, n, scratch, st);
+}
+uint64_t mf_next_pow2(uint64_t x) { return next_pow2(x); }
+void mf_launch_seeds(const MfFrame &F, const MfTraceBufs &B, const double *seeds, int64_t n,
+                     bool vertices, cudaStream_t s) {
+  const unsigned g = (unsigned)((n + 127) / 128);
+  if (vertices) k_seed_vertices<<<g, 128, 0, s>>>(F, B, seeds, n);
+  else k_seed_edges<<<g, 128, 0, s>>>(F, B, seeds, n);
 }
 
 static int read_counters(mf_ctx *ctx, const MfTraceBufs &B, cudaStream_t st) {
@@ -620,6 +1019,8 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
   if (rc) return rc;
   MfFrame F;
   rc = build_frame(ctx, d, opts->lambda, dom, &F);
+  if (rc) return rc;
+  rc = build_domain_table(ctx, &F, st);
   if (rc) return rc;
   const uint64_t ME = opts->max_edges > 0 ? (uint64_t)opts->max_edges : (1ull << 24);
   const uint64_t MV = opts->max_vertices > 0 ? (uint64_t)opts->max_vertices : ME;

@@ -33,7 +33,9 @@ MF_SPHERE = 1
 
 EXPORTS = ("mf_ctx_create", "mf_ctx_destroy", "mf_last_error", "mf_ctx_bytes", "mf_locate",
            "mf_eval", "mf_trace", "mf_trace_fetch", "mf_certify", "mf_ctx_set_profiling",
-           "mf_ctx_get_stats", "mf_trace_noalloc")
+           "mf_ctx_get_stats", "mf_trace_noalloc", "mf_trace_batch", "mf_domain_table",
+           "mf_server_create", "mf_server_destroy", "mf_server_submit", "mf_server_step",
+           "mf_server_status", "mf_server_fetch")
 
 MF_PHASES = 12
 PHASE_NAMES = ("prepare", "seeds", "expand_vertices", "eval", "expand_edges", "roots", "cells",
@@ -128,6 +130,26 @@ def load(build_if_missing: bool = True):
     L.mf_ctx_set_profiling.argtypes = [V, C.c_int]
     L.mf_ctx_get_stats.restype = C.c_int
     L.mf_ctx_get_stats.argtypes = [V, P(mf_stats)]
+    L.mf_server_create.restype = C.c_int
+    L.mf_server_create.argtypes = [V, C.c_int32, C.c_size_t, P(V)]
+    L.mf_server_destroy.restype = None
+    L.mf_server_destroy.argtypes = [V]
+    L.mf_server_submit.restype = C.c_int
+    L.mf_server_submit.argtypes = [V, P(mf_rbf), P(mf_domain), P(mf_trace_opts), V, C.c_int64,
+                                   P(C.c_int64)]
+    L.mf_server_step.restype = C.c_int
+    L.mf_server_step.argtypes = [V, V, P(C.c_int32), P(C.c_int32)]
+    L.mf_server_status.restype = C.c_int
+    L.mf_server_status.argtypes = [V, C.c_int64, P(C.c_int32), P(C.c_double), P(C.c_double),
+                                   P(C.c_double)]
+    L.mf_server_fetch.restype = C.c_int
+    L.mf_server_fetch.argtypes = [V, C.c_int64, P(mf_trace_out), V]
+    L.mf_domain_table.restype = C.c_int
+    L.mf_domain_table.argtypes = [C.c_int32, C.c_double, P(mf_domain), P(C.c_int32), P(C.c_int32),
+                                  V, C.c_int64]
+    L.mf_trace_batch.restype = C.c_int
+    L.mf_trace_batch.argtypes = [V, C.c_int32, P(mf_rbf), P(mf_domain), P(mf_trace_opts),
+                                 P(C.c_void_p), P(C.c_int64), P(mf_trace_out), V]
     L.mf_trace_noalloc.restype = C.c_int
     L.mf_trace_noalloc.argtypes = [P(mf_rbf), P(mf_domain), P(mf_trace_opts), V, C.c_int64,
                                    P(mf_trace_out), V]
@@ -189,6 +211,63 @@ def mf_trace(ctx, rbf: mf_rbf, dom: mf_domain, opts: mf_trace_opts, seeds_ptr, n
 
 def mf_trace_fetch(ctx, out: mf_trace_out, stream=0):
     return _check(ctx, load().mf_trace_fetch(ctx, C.byref(out), stream))
+
+
+def mf_server_create(ctx, max_slots, hbm_bytes):
+    h = C.c_void_p()
+    _check(ctx, load().mf_server_create(ctx, max_slots, hbm_bytes, C.byref(h)))
+    return h
+
+
+def mf_server_destroy(server):
+    load().mf_server_destroy(server)
+
+
+def mf_server_submit(ctx, server, rbf, dom, opts, seeds_ptr, n_seeds):
+    rid = C.c_int64()
+    _check(ctx, load().mf_server_submit(server, C.byref(rbf), C.byref(dom), C.byref(opts),
+                                        seeds_ptr, n_seeds, C.byref(rid)))
+    return rid.value
+
+
+def mf_server_step(ctx, server, stream=0):
+    nr, nq = C.c_int32(), C.c_int32()
+    _check(ctx, load().mf_server_step(server, stream, C.byref(nr), C.byref(nq)))
+    return nr.value, nq.value
+
+
+def mf_server_status(ctx, server, rid):
+    st = C.c_int32()
+    t = [C.c_double(), C.c_double(), C.c_double()]
+    _check(ctx, load().mf_server_status(server, rid, C.byref(st), *[C.byref(x) for x in t]))
+    return st.value, t[0].value, t[1].value, t[2].value
+
+
+def mf_server_fetch(ctx, server, rid, out: mf_trace_out, stream=0, check=True):
+    rc = load().mf_server_fetch(server, rid, C.byref(out), stream)
+    return _check(ctx, rc) if check else rc
+
+
+def mf_domain_table(d, lam, dom: mf_domain):
+    """(smin, table[span][d][2]) of the exact lattice domain test (host only)."""
+    import numpy as np
+    smin, span = C.c_int32(), C.c_int32()
+    rc = load().mf_domain_table(d, lam, C.byref(dom), C.byref(smin), C.byref(span), None, 0)
+    if rc != MF_OK:
+        raise MfError(rc, "mf_domain_table")
+    tab = np.zeros((span.value, d, 2), dtype=np.int32)
+    rc = load().mf_domain_table(d, lam, C.byref(dom), C.byref(smin), C.byref(span),
+                                tab.ctypes.data_as(C.c_void_p), tab.size)
+    if rc != MF_OK:
+        raise MfError(rc, "mf_domain_table")
+    return smin.value, tab
+
+
+def mf_trace_batch(ctx, rbfs, doms, opts, seed_ptrs, n_seeds, outs, stream=0, check=True):
+    """rbfs / doms / opts / outs: ctypes arrays of the structs; seed_ptrs: a
+    ctypes array of device pointers; n_seeds: a ctypes int64 array."""
+    rc = load().mf_trace_batch(ctx, len(rbfs), rbfs, doms, opts, seed_ptrs, n_seeds, outs, stream)
+    return _check(ctx, rc) if check else rc
 
 
 def mf_trace_noalloc(rbf: mf_rbf, dom: mf_domain, opts: mf_trace_opts, seeds_ptr, n_seeds,

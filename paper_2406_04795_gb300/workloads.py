@@ -72,6 +72,13 @@ def place_seeds(rng, sv, alpha, gamma, b, lo, hi, n_seeds, inner=None, step=0.05
         cand = np.concatenate([sv, rng.uniform(lo, hi, size=(4096, d))])
         fc = _rbf_numpy(sv, alpha, gamma, b, cand)
         inner = cand[fc < 0]
+    else:
+        # the march stays within max_steps * step of the inner points: support
+        # vectors farther than that plus sqrt(30 / gamma) add < e^-30 each
+        reach = max_steps * step + math.sqrt(30.0 / gamma)
+        dist = np.min(np.linalg.norm(sv[:, None, :] - inner[None, :, :], axis=2), axis=1)
+        keep = dist <= reach
+        sv, alpha = sv[keep], alpha[keep]
     if inner.shape[0] == 0:
         raise ValueError("no point with f < 0 to start from")
     seeds = []
@@ -208,6 +215,78 @@ def config_d6(seed: int = 1002, lam: float = 0.04, n_sv: int = 8192, n_seeds: in
     return Workload("d6_mixed_%dsv" % n_sv, d, sv, alpha, gamma, b, lam, lattice_offset(d, lam),
                     lo, hi, seeds, dh, radius, types, poses, dims,
                     batch_cap=1 << 24, precision="mixed", recheck_band=1e-3)
+
+
+# shell radius in lattice units per dimension: bounds the traced set of a
+# batched / served trace to about 1e5 - 3e6 edges
+SHELL_LATTICE_RADIUS = {2: 12.0, 3: 10.0, 4: 8.0, 5: 5.0, 6: 3.0, 7: 2.5, 8: 2.0}
+
+
+def shell_trace(rng, d: int, n_sv: int, lam: float, n_seeds: int, n_free: int = 1,
+                b: float = 0.5, name: str = "shell") -> Workload:
+    """One trace of the batched and served workloads: n_sv support vectors
+    uniform in [-pi, pi]^d, obstacle-class weights alpha = +|N(0,1)|/2 and
+    n_free free-space vectors with alpha = -2; gamma is chosen so that a free
+    vector's shell 2 exp(-gamma r^2) = b has radius SHELL_LATTICE_RADIUS[d] *
+    lambda; all seeds lie on the free vectors' shells."""
+    sv = rng.uniform(-math.pi, math.pi, size=(n_sv, d))
+    alpha = 0.5 * np.abs(rng.normal(size=n_sv))
+    free = rng.choice(n_sv, size=n_free, replace=False)
+    alpha[free] = -2.0
+    r_shell = min(SHELL_LATTICE_RADIUS.get(d, 2.0) * lam, 0.8)
+    gamma = math.log(2.0 / b) / (r_shell * r_shell)
+    lo, hi = np.full(d, -math.pi), np.full(d, math.pi)
+    seeds = place_seeds(rng, sv, alpha, gamma, b, lo, hi, n_seeds, inner=sv[free],
+                        step=0.25 * r_shell, max_steps=16)
+    dh, radius = _dh_arm(rng, d, 0.04)
+    reach = float(dh[:, 2].sum())
+    centers = _ball(rng, 8, reach)
+    half = rng.uniform(0.05, 0.3, size=(8, 3))
+    return Workload(name, d, sv, alpha, gamma, b, lam, lattice_offset(d, lam), lo, hi, seeds, dh,
+                    radius, np.zeros(8, np.int32), np.stack([_aabb_pose(c) for c in centers]),
+                    2.0 * half, precision="mixed")
+
+
+def shell_capacity(w) -> dict:
+    """Table capacities for one shell trace: its shells hold a fixed number of
+    lattice radii, so edges depend on d only (measured: d=4 ~1e5, d=5 ~5e5,
+    d=6 ~1e6 per two shells); cells per edge grow with d."""
+    me = {2: 1 << 16, 3: 1 << 17, 4: 1 << 19, 5: 1 << 21, 6: 1 << 22}.get(w.d, 1 << 22)
+    cells_per_edge = {2: 2, 3: 3, 4: 6, 5: 12, 6: 20}.get(w.d, 24)
+    return dict(max_edges=me, max_vertices=me, max_cells=me * cells_per_edge)
+
+
+def config_batched(seed: int = 1003, n_traces: int = 64, lam_scale: float = 1.0):
+    """Batched: 64 independent traces, d in {4,5,6}, 256-8192 support vectors
+    log-uniform, lambda in [0.03, 0.1], 1-64 seeds each (lam_scale > 1 makes
+    every lattice coarser for quick tests)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for t in range(n_traces):
+        d = int(rng.integers(4, 7))
+        n_sv = int(round(math.exp(rng.uniform(math.log(256), math.log(8192)))))
+        lam = float(rng.uniform(0.03, 0.1)) * lam_scale
+        n_seeds = int(rng.integers(1, 65))
+        out.append(shell_trace(rng, d, n_sv, lam, n_seeds, n_free=int(rng.integers(1, 3)),
+                               name="batch%d_d%d_%dsv" % (t, d, n_sv)))
+    return out
+
+
+def served_requests(seed: int = 1005, n_requests: int = 2000, rate_hz: float = 50.0,
+                    lam_scale: float = 1.0):
+    """Served: a Poisson stream (exponential inter-arrival times, mean
+    1/rate) of proof requests, d in {4,5,6}, 512-8192 support vectors
+    log-uniform, lambda in [0.03, 0.08].  Returns (arrival_s, workloads)."""
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate_hz, size=n_requests))
+    reqs = []
+    for i in range(n_requests):
+        d = int(rng.integers(4, 7))
+        n_sv = int(round(math.exp(rng.uniform(math.log(512), math.log(8192)))))
+        lam = float(rng.uniform(0.03, 0.08)) * lam_scale
+        n_seeds = int(rng.integers(1, 17))
+        reqs.append(shell_trace(rng, d, n_sv, lam, n_seeds, name="req%d_d%d_%dsv" % (i, d, n_sv)))
+    return arrivals, reqs
 
 
 def sphere_workload(d: int, r: float = 1.0, gamma: float = 1.0, lam: float = 0.2,
