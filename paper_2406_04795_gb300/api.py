@@ -284,9 +284,11 @@ class Server:
         # two-call pattern: the counts first (capacity error, request kept),
         # then buffers of exactly that size
         probe = mf.mf_trace_out()
+        state = self.status(rid)[0]
         rc = mf.mf_server_fetch(self.ctx.h, self.h, rid, probe, _stream_handle(stream), check=False)
         if rc not in (mf.MF_OK, mf.MF_ERR_CAPACITY):
-            self._keep.pop(rid, None)
+            if state < 0:  # a failed request is forgotten by the server
+                self._keep.pop(rid, None)
             mf._check(self.ctx.h, rc)
         bufs = self.ctx._alloc_outputs(d, probe.n_edges, probe.n_cells, probe.n_cell_edges)
         out = probe  # an empty result fits zero capacities and is already fetched

@@ -7,7 +7,7 @@
 // vector per step in FP32 and sorts it into one of three classes:
 //   dropped  gamma r^2 > T, T chosen so that all dropped terms sum to <= 1e-13;
 //   strong   |alpha| e^{-gamma r^2} may exceed tau = 3e-10: FP64 distance and
-//            the FP64 exp of the CUDA math library;
+//            an FP64 table-driven exp (mf_exp_neg);
 //   weak     the rest: evaluated entirely in FP32 with hi/lo-split
 //            coordinates (x = x_hi + x_lo, s = s_hi + s_lo, so differences keep
 //            FP32 relative accuracy) and the hardware ex2; no FP64 instruction.
@@ -46,8 +46,9 @@ struct MfRbfStats {
 
 __global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alpha, float *sv32,
                               float *svlo32, double *sv64, float *alpha32, float *strong32,
-                              MfRbfStats *st) {
+                              double *exp_tab, MfRbfStats *st) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < 64) exp_tab[j] = exp2((double)j / 64.0);
   double a = 0.0;
   float m = 0.f;
   int bad = 0;
@@ -84,7 +85,7 @@ __global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alph
 size_t mf_rbf_prep_bytes(int d, int64_t n) {
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t nb = (size_t)n;
-  return 256 + al(nb * d * 8) + 2 * al(nb * d * 4) + 2 * al(nb * 4);
+  return 256 + al(nb * d * 8) + 2 * al(nb * d * 4) + 2 * al(nb * 4) + al(64 * 8);
 }
 
 int mf_prepare_rbf(mf_ctx *ctx, const mf_rbf *rbf, MfRbfDev *out, cudaStream_t st) {
@@ -110,10 +111,11 @@ int mf_prepare_rbf_at(mf_ctx *ctx, const mf_rbf *rbf, char *base, MfRbfDev *out,
   float *sv32 = (float *)p; p += al(nb * d * 4);
   float *svlo32 = (float *)p; p += al(nb * d * 4);
   float *alpha32 = (float *)p; p += al(nb * 4);
-  float *strong32 = (float *)p;
+  float *strong32 = (float *)p; p += al(nb * 4);
+  double *exp_tab = (double *)p;
   cudaMemsetAsync(dst, 0, sizeof(MfRbfStats), st);
   k_prepare_rbf<<<(n + 255) / 256, 256, 0, st>>>(d, n, rbf->sv, rbf->alpha, sv32, svlo32, sv64,
-                                                  alpha32, strong32, dst);
+                                                  alpha32, strong32, exp_tab, dst);
   MfRbfStats h;
   int rc = mf_cuda_check(ctx, cudaMemcpyAsync(&h, dst, sizeof(h), cudaMemcpyDeviceToHost, st),
                          "prepare rbf");
@@ -129,6 +131,7 @@ int mf_prepare_rbf_at(mf_ctx *ctx, const mf_rbf *rbf, char *base, MfRbfDev *out,
   out->alpha = rbf->alpha;
   out->alpha32 = alpha32;
   out->strong32 = strong32;
+  out->exp_tab = exp_tab;
   out->gamma = rbf->gamma;
   out->b = rbf->b;
   // Screen: drop terms with gamma r^2 > T where sum|alpha| e^-T <= 1e-13.
@@ -157,14 +160,24 @@ struct F64Acc {
 
 // x split as x_hi + x_lo (both FP32) so that FP32 differences to a support
 // vector split the same way keep FP32 relative accuracy.
+template <int D>
 struct Split32 {
-  float hi[MF_MAXD], lo[MF_MAXD], dir[MF_MAXD];
+  float hi[D], lo[D], dir[D];
 };
 
-__device__ __forceinline__ Split32 split32(int d, const double *x, const double *dir) {
-  Split32 s;
+// Dimension of the work: a compile-time D below MF_MAXD is exact; D ==
+// MF_MAXD serves every d <= MF_MAXD at run time.
+template <int D>
+__device__ __forceinline__ int dim_of(int rt) {
+  return D < MF_MAXD ? D : rt;
+}
+
+template <int D>
+__device__ __forceinline__ Split32<D> split32(int d, const double *x, const double *dir) {
+  Split32<D> s;
+  d = dim_of<D>(d);
 #pragma unroll
-  for (int k = 0; k < MF_MAXD; k++) {
+  for (int k = 0; k < D; k++) {
     s.hi[k] = k < d ? (float)x[k] : 0.f;
     s.lo[k] = k < d ? (float)(x[k] - (double)s.hi[k]) : 0.f;
     s.dir[k] = (k < d && dir) ? (float)dir[k] : 0.f;
@@ -172,21 +185,50 @@ __device__ __forceinline__ Split32 split32(int d, const double *x, const double 
   return s;
 }
 
-// Strong term: FP64 difference, FP64 exp of the CUDA math library.
-template <bool GRAD>
+// e^x for x <= 0 in FP64 by the table-driven method of P. T. P. Tang
+// ("Table-driven implementation of the exponential function in IEEE
+// floating-point arithmetic", ACM TOMS 15(2), 1989): x = (64 m + j) ln2/64 + r
+// with |r| <= ln2/128 (about), e^x = 2^m 2^(j/64) e^r, and e^r - 1 by its
+// Taylor polynomial of degree 5 (truncation below 4e-17 relative).  ln2/64 is
+// split into L1 (29 significant bits, so k L1 is exact for |k| < 2^17) and
+// L2.  Arguments below -708 return e^-708 (absolute error < 4e-308).  Relative
+// error a few ulp; 12 FP64-pipe instructions and one table load.
+__device__ __forceinline__ double mf_exp_neg(double x, const double *tab) {
+  const double inv_l = 0x1.71547652b82fep+6;   // 64 / ln2
+  const double l1 = 0x1.62e42ff000000p-7;      // ln2/64, leading bits
+  const double l2 = -0x1.718432a1b0e26p-41;    // ln2/64 - l1
+  const double shift = 0x1.8p52;               // rounds to an integer in the low word
+  x = fmax(x, -708.0);
+  const double ks = fma(x, inv_l, shift);
+  const int k = __double2loint(ks);
+  const double kd = ks - shift;
+  const double r = fma(-kd, l2, fma(-kd, l1, x));
+  const double r2 = r * r;
+  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  q = fma(q, r, 1.0 / 6.0);
+  q = fma(q, r, 0.5);
+  const double p = fma(r2, q, r);  // e^r - 1
+  const double t = __ldg(tab + (k & 63));
+  const double scale = __hiloint2double(((k >> 6) + 1023) << 20, 0);  // 2^m, m >= -1022
+  return fma(t, p, t) * scale;
+}
+
+// Strong term: FP64 difference and the FP64 exp above.
+template <bool GRAD, int D>
 __device__ __forceinline__ void f64_term(const MfRbfDev &R, const double *x, const double *dir,
                                          int j, F64Acc &acc) {
   if (j < 0) return;
+  const int d = dim_of<D>(R.d);
   double r2 = 0.0, proj = 0.0;
 #pragma unroll
-  for (int k = 0; k < MF_MAXD; k++) {
-    if (k < R.d) {
+  for (int k = 0; k < D; k++) {
+    if (k < d) {
       double t = x[k] - R.sv64[(int64_t)k * R.n + j];
       r2 = fma(t, t, r2);
       if (GRAD) proj = fma(t, dir[k], proj);
     }
   }
-  const double e = R.alpha[j] * exp(-R.gamma * r2);
+  const double e = R.alpha[j] * mf_exp_neg(-R.gamma * r2, R.exp_tab);
   acc.f += e;
   if (GRAD) acc.g = fma(e, proj, acc.g);
 }
@@ -195,15 +237,16 @@ __device__ __forceinline__ void f64_term(const MfRbfDev &R, const double *x, con
 // Its relative error is at most (d+2) u gamma r^2 (differences, squares and
 // the exponent's rounding, u = 2^-24) + 2^-20 (ex2) + 2u (alpha, product); on
 // the kept range gamma r^2 <= T + 1/2 the host bounds this by R.weak_rel.
-template <bool GRAD>
-__device__ __forceinline__ void f32_weak_term(const MfRbfDev &R, const Split32 &x, int j,
+template <bool GRAD, int D>
+__device__ __forceinline__ void f32_weak_term(const MfRbfDev &R, const Split32<D> &x, int j,
                                               F64Acc &acc) {
   if (j < 0) return;
+  const int d = dim_of<D>(R.d);
   const float g2 = (float)(R.gamma * 1.4426950408889634);
   float r2 = 0.f, proj = 0.f;
 #pragma unroll
-  for (int k = 0; k < MF_MAXD; k++) {
-    if (k < R.d) {
+  for (int k = 0; k < D; k++) {
+    if (k < d) {
       const float t = (x.hi[k] - R.sv32[(int64_t)k * R.n + j]) +
                       (x.lo[k] - R.svlo32[(int64_t)k * R.n + j]);
       r2 = fmaf(t, t, r2);
@@ -230,16 +273,14 @@ __device__ __forceinline__ int pop32(int *q, int &n, int lane) {
 // All lanes pass the same x (FP64) and get f (and, with GRAD, g = grad f . dir).
 // qs, qw: two 64-entry per-warp queues.  ALL_STRONG puts every kept term in
 // the strong queue.  terms[0/1] count strong / weak terms.
-template <bool GRAD, bool ALL_STRONG>
+template <bool GRAD, bool ALL_STRONG, int D>
 __device__ F64Acc warp_f64_pass(const MfRbfDev &R, const double *x, const double *dir, int *qs,
                                 int *qw, unsigned long long *terms) {
   const int lane = threadIdx.x & 31;
-  float x32[MF_MAXD];
-#pragma unroll
-  for (int k = 0; k < MF_MAXD; k++) x32[k] = k < R.d ? (float)x[k] : 0.f;
+  const int d = dim_of<D>(R.d);
   const float g32 = (float)R.gamma;
   F64Acc acc = {0.0, 0.0, 0.f, 0.f, 0.f};
-  const Split32 xs = split32(R.d, x, dir);
+  const Split32<D> xs = split32<D>(d, x, dir);
   int ns = 0, nw = 0;
   const unsigned lt = (1u << lane) - 1u;
   for (int base = 0; base < R.n; base += 32) {
@@ -248,9 +289,9 @@ __device__ F64Acc warp_f64_pass(const MfRbfDev &R, const double *x, const double
     if (j < R.n) {
       float r2 = 0.f;
 #pragma unroll
-      for (int k = 0; k < MF_MAXD; k++)
-        if (k < R.d) {
-          float t = x32[k] - R.sv32[(int64_t)k * R.n + j];
+      for (int k = 0; k < D; k++)
+        if (k < d) {
+          float t = xs.hi[k] - R.sv32[(int64_t)k * R.n + j];
           r2 = fmaf(t, t, r2);
         }
       keep = r2 <= R.screen_r2;
@@ -266,19 +307,19 @@ __device__ F64Acc warp_f64_pass(const MfRbfDev &R, const double *x, const double
     terms[1] += __popc(mw);
     if (ns >= 32) {
       const int jj = pop32(qs, ns, lane);
-      f64_term<GRAD>(R, x, dir, jj, acc);
+      f64_term<GRAD, D>(R, x, dir, jj, acc);
     }
     if (nw >= 32) {
       const int jj = pop32(qw, nw, lane);
-      f32_weak_term<GRAD>(R, xs, jj, acc);
+      f32_weak_term<GRAD, D>(R, xs, jj, acc);
     }
   }
   __syncwarp();
   const int js = lane < ns ? qs[lane] : -1;
   const int jw = lane < nw ? qw[lane] : -1;
   __syncwarp();
-  f64_term<GRAD>(R, x, dir, js, acc);
-  f32_weak_term<GRAD>(R, xs, jw, acc);
+  f64_term<GRAD, D>(R, x, dir, js, acc);
+  f32_weak_term<GRAD, D>(R, xs, jw, acc);
   acc.f = mf_warp_sum_d(acc.f) + (double)mf_warp_sum_f(acc.wf) + R.b;
   acc.weak = mf_warp_sum_f(acc.weak);
   if (GRAD) acc.g = -2.0 * R.gamma * (mf_warp_sum_d(acc.g) + (double)mf_warp_sum_f(acc.wg));
@@ -286,18 +327,19 @@ __device__ F64Acc warp_f64_pass(const MfRbfDev &R, const double *x, const double
 }
 
 // f with total error <= 2.5e-13 (dropped + weak terms), all lanes.
-template <bool GRAD>
+template <bool GRAD, int D>
 __device__ __forceinline__ F64Acc warp_f64(const MfRbfDev &R, const double *x, const double *dir,
                                            int *qs, int *qw, unsigned long long *terms) {
-  F64Acc a = warp_f64_pass<GRAD, false>(R, x, dir, qs, qw, terms);
+  F64Acc a = warp_f64_pass<GRAD, false, D>(R, x, dir, qs, qw, terms);
   if ((double)a.weak * 1.01 * R.weak_rel > R.weak_limit)
-    a = warp_f64_pass<GRAD, true>(R, x, dir, qs, qw, terms);
+    a = warp_f64_pass<GRAD, true, D>(R, x, dir, qs, qw, terms);
   return a;
 }
 
 #define EVAL_WARPS 8
 
 // f at vertex-list entries [v_evaluated, n_vertices) (FP64).
+template <int D>
 __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_vertices_f64(MfFrame F, MfRbfDev R, MfTraceBufs B) {
   __shared__ int sq[EVAL_WARPS][2][64];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -308,11 +350,13 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_vertices_f64(MfFrame F
   unsigned long long terms[2] = {0, 0};
   for (uint64_t i = begin + (uint64_t)blockIdx.x * EVAL_WARPS + w; i < end; i += nwarps) {
     int32_t y[MF_MAXD];
-    double x[MF_MAXD];
+    double xm[MF_MAXD], x[D];
 #pragma unroll
     for (int k = 0; k < MF_MAXD; k++) y[k] = k < F.d ? B.vert_y[i * F.d + k] : 0;
-    mf_vertex_x(F, y, x);
-    F64Acc a = warp_f64<false>(R, x, nullptr, sq[w][0], sq[w][1], terms);
+    mf_vertex_x(F, y, xm);
+#pragma unroll
+    for (int k = 0; k < D; k++) x[k] = xm[k];
+    F64Acc a = warp_f64<false, D>(R, x, nullptr, sq[w][0], sq[w][1], terms);
     if (lane == 0) {
       B.vtab_f[B.vert_slot[i]] = a.f;
       if (fabs(a.f) < 1e-12) atomicAdd(&B.cnt->n_near_zero, 1ull);
@@ -325,6 +369,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_vertices_f64(MfFrame F
 }
 
 // FP64 re-evaluation of the recheck queue [n_recheck_done, n_recheck).
+template <int D>
 __global__ void __launch_bounds__(EVAL_WARPS * 32) k_recheck_vertices_f64(MfFrame F, MfRbfDev R, MfTraceBufs B) {
   __shared__ int sq[EVAL_WARPS][2][64];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -336,11 +381,13 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_recheck_vertices_f64(MfFram
   for (uint64_t q = begin + (uint64_t)blockIdx.x * EVAL_WARPS + w; q < end; q += nwarps) {
     const uint32_t i = B.recheck[q];
     int32_t y[MF_MAXD];
-    double x[MF_MAXD];
+    double xm[MF_MAXD], x[D];
 #pragma unroll
     for (int k = 0; k < MF_MAXD; k++) y[k] = k < F.d ? B.vert_y[(uint64_t)i * F.d + k] : 0;
-    mf_vertex_x(F, y, x);
-    F64Acc a = warp_f64<false>(R, x, nullptr, sq[w][0], sq[w][1], terms);
+    mf_vertex_x(F, y, xm);
+#pragma unroll
+    for (int k = 0; k < D; k++) x[k] = xm[k];
+    F64Acc a = warp_f64<false, D>(R, x, nullptr, sq[w][0], sq[w][1], terms);
     if (lane == 0) {
       B.vtab_f[B.vert_slot[i]] = a.f;
       if (fabs(a.f) < 1e-12) atomicAdd(&B.cnt->n_near_zero, 1ull);
@@ -504,7 +551,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_points_f64(MfRbfDev R,
     double x[MF_MAXD];
 #pragma unroll
     for (int k = 0; k < MF_MAXD; k++) x[k] = k < R.d ? pts[i * R.d + k] : 0.0;
-    F64Acc a = warp_f64<false>(R, x, nullptr, sq[w][0], sq[w][1], terms);
+    F64Acc a = warp_f64<false, MF_MAXD>(R, x, nullptr, sq[w][0], sq[w][1], terms);
     if (lane == 0) fout[i] = a.f;
   }
 }
@@ -529,14 +576,16 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_points_f64(MfRbfDev R,
 #define NEAR_CAP 1024
 
 struct Root32 {
-  double g, gp, gpp;
+  float g, gp, gpp;
 };
 
 // FP32 evaluation of g, g', g'' at t over the near list (all lanes).
+template <int D>
 __device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const int *near, int ns, int nw,
                                               const float *x1hi, const float *x1lo,
-                                              const float *dir32, float dd32, float t) {
+                                              const float *dir32, float dd32, float b32, float t) {
   const int lane = threadIdx.x & 31;
+  const int d = dim_of<D>(R.d);
   const float g2 = (float)(R.gamma * 1.4426950408889634);
   float s0 = 0.f, s1 = 0.f, s2 = 0.f;
   const int total = ns + nw;
@@ -544,8 +593,8 @@ __device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const int *near
     const int j = i < ns ? near[i] : near[NEAR_CAP - 1 - (i - ns)];
     float r2 = 0.f, proj = 0.f;
 #pragma unroll
-    for (int k = 0; k < MF_MAXD; k++) {
-      if (k < R.d) {
+    for (int k = 0; k < D; k++) {
+      if (k < d) {
         const float a = x1hi[k] - R.sv32[(int64_t)k * R.n + j];
         const float b = fmaf(t, dir32[k], x1lo[k] - R.svlo32[(int64_t)k * R.n + j]);
         const float df = a + b;
@@ -561,27 +610,27 @@ __device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const int *near
   s0 = mf_warp_sum_f(s0);
   s1 = mf_warp_sum_f(s1);
   s2 = mf_warp_sum_f(s2);
-  const double gm = R.gamma;
+  const float gm = (float)R.gamma;
   Root32 r;
-  r.g = (double)s0 + R.b;
-  r.gp = -2.0 * gm * (double)s1;
-  r.gpp = 4.0 * gm * gm * (double)s2 - 2.0 * gm * (double)dd32 * (double)s0;
+  r.g = s0 + b32;
+  r.gp = -2.f * gm * s1;
+  r.gpp = 4.f * gm * gm * s2 - 2.f * gm * dd32 * s0;
   return r;
 }
 
-// FP64 evaluation of g and g' at x over the near list (all lanes).
-template <bool ALL_STRONG>
+// FP64 evaluation of g and g' at x over the near list (all lanes); xs is x
+// split into FP32 hi/lo parts for the weak terms.
+template <bool ALL_STRONG, int D>
 __device__ __forceinline__ F64Acc root_eval64(const MfRbfDev &R, const int *near, int ns, int nw,
-                                              const double *x, const double *dir,
+                                              const double *x, const double *dir, const Split32<D> &xs,
                                               unsigned long long *terms) {
   const int lane = threadIdx.x & 31;
   F64Acc acc = {0.0, 0.0, 0.f, 0.f, 0.f};
-  for (int i = lane; i < ns; i += 32) f64_term<true>(R, x, dir, near[i], acc);
+  for (int i = lane; i < ns; i += 32) f64_term<true, D>(R, x, dir, near[i], acc);
   if (ALL_STRONG) {
-    for (int i = lane; i < nw; i += 32) f64_term<true>(R, x, dir, near[NEAR_CAP - 1 - i], acc);
+    for (int i = lane; i < nw; i += 32) f64_term<true, D>(R, x, dir, near[NEAR_CAP - 1 - i], acc);
   } else {
-    const Split32 xs = split32(R.d, x, dir);
-    for (int i = lane; i < nw; i += 32) f32_weak_term<true>(R, xs, near[NEAR_CAP - 1 - i], acc);
+    for (int i = lane; i < nw; i += 32) f32_weak_term<true, D>(R, xs, near[NEAR_CAP - 1 - i], acc);
   }
   terms[0] += ns + (ALL_STRONG ? nw : 0);
   terms[1] += ALL_STRONG ? 0 : nw;
@@ -592,112 +641,137 @@ __device__ __forceinline__ F64Acc root_eval64(const MfRbfDev &R, const int *near
 }
 
 // Solves the root of edge e (all lanes of the warp); near: NEAR_CAP ints,
-// qs / qw: 64-entry queues, all in this warp's shared memory.
+// qs / qw: 64-entry queues, all in this warp's shared memory.  FP64 work that
+// is the same for every lane (coordinates, their splits) runs once per axis:
+// lane k < d computes axis k and shuffles broadcast it.
+template <int D>
 __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, uint64_t e,
                           double tol, int *near, int *qs, int *qw, unsigned long long &evals,
                           unsigned long long *terms) {
   const int lane = threadIdx.x & 31;
-  const int d = F.d;
+  const int d = dim_of<D>(F.d);
   const unsigned lt = (1u << lane) - 1u;
   const float g32 = (float)R.gamma;
-  {
-    int32_t y[MF_MAXD], y2[MF_MAXD];
+  const int ko = lane < d ? lane : 0;  // this lane's axis
+  // endpoints: x1 = x(y), x2 = x(y + e(mask)) in mf_vertex_x's operation order
+  long long sy = 0;
+  int32_t yo = 0;
 #pragma unroll
-    for (int k = 0; k < MF_MAXD; k++) y[k] = y2[k] = k < d ? B.edge_y[e * d + k] : 0;
-    mf_add_mask(d, y2, B.edge_mask[e], 1);
-    double x1[MF_MAXD], x2[MF_MAXD], dir[MF_MAXD], x[MF_MAXD];
-    mf_vertex_x(F, y, x1);
-    mf_vertex_x(F, y2, x2);
-    float x1hi[MF_MAXD], x1lo[MF_MAXD], dir32[MF_MAXD];
-    float dd32 = 0.f;
-#pragma unroll
-    for (int k = 0; k < MF_MAXD; k++) {
-      dir[k] = k < d ? __dsub_rn(x2[k], x1[k]) : 0.0;
-      x1hi[k] = (float)x1[k];
-      x1lo[k] = (float)(x1[k] - (double)x1hi[k]);
-      dir32[k] = (float)dir[k];
-      dd32 = fmaf(dir32[k], dir32[k], dd32);
-    }
-    // 1. segment screen
-    int ns = 0, nw = 0;
-    for (int base = 0; base < R.n; base += 32) {
-      const int j = base + lane;
-      bool keep = false, strong = false;
-      if (j < R.n) {
-        float p[MF_MAXD], pd = 0.f;
-#pragma unroll
-        for (int k = 0; k < MF_MAXD; k++) {
-          p[k] = k < d ? (R.sv32[(int64_t)k * R.n + j] - x1hi[k]) : 0.f;
-          pd = fmaf(p[k], dir32[k], pd);
-        }
-        const float tt = fminf(fmaxf(pd / dd32, 0.f), 1.f);
-        float r2 = 0.f;
-#pragma unroll
-        for (int k = 0; k < MF_MAXD; k++) {
-          const float q = fmaf(-tt, dir32[k], p[k]);
-          r2 = fmaf(q, q, r2);
-        }
-        keep = r2 <= R.screen_r2;
-        strong = g32 * r2 < R.strong32[j] + 0.5f;
-      }
-      const unsigned ms = __ballot_sync(FULL, keep && strong);
-      const unsigned mw = __ballot_sync(FULL, keep && !strong);
-      const int cs = ns + __popc(ms & lt), cw = nw + __popc(mw & lt);
-      if (keep && strong && cs + nw < NEAR_CAP) near[cs] = j;
-      if (keep && !strong && ns + cw < NEAR_CAP) near[NEAR_CAP - 1 - cw] = j;
-      ns += __popc(ms);
-      nw += __popc(mw);
-    }
-    __syncwarp();
-    const bool overflow = ns + nw > NEAR_CAP;
-    const double f0 = B.edge_f[2 * e], f1 = B.edge_f[2 * e + 1];
-    const bool s1 = f0 >= 0.0;
-    double t = f0 / (f0 - f1);
-    if (!(t > 0.0 && t < 1.0)) t = 0.5;
-    // 2. FP32 Newton
-    double gpp = INFINITY;
-    if (!overflow) {
-      double lo = 0.0, hi = 1.0;
-      for (int it = 0; it < 12; it++) {
-        const Root32 r = root_eval32(R, near, ns, nw, x1hi, x1lo, dir32, dd32, (float)t);
-        gpp = r.gpp;
-        if ((r.g >= 0.0) == s1) lo = t; else hi = t;
-        double tn = t - r.g / r.gp;
-        if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
-        const double step = fabs(tn - t);
-        t = tn;
-        if (step <= 2e-6) break;
-      }
-    }
-    // 3. FP64 Newton with a kept bracket
-    double lo = 0.0, hi = 1.0;
-    for (int it = 0; it < 64; it++) {
-#pragma unroll
-      for (int k = 0; k < MF_MAXD; k++) x[k] = k < d ? __dadd_rn(x1[k], __dmul_rn(t, dir[k])) : 0.0;
-      F64Acc a;
-      if (overflow) {
-        a = warp_f64<true>(R, x, dir, qs, qw, terms);
-      } else {
-        a = root_eval64<false>(R, near, ns, nw, x, dir, terms);
-        if ((double)a.weak * 1.01 * R.weak_rel > R.weak_limit)
-          a = root_eval64<true>(R, near, ns, nw, x, dir, terms);
-      }
-      evals++;
-      if (a.f == 0.0) break;
-      if ((a.f >= 0.0) == s1) lo = t; else hi = t;
-      double tn = t - a.f / a.g;
-      if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
-      const double step = fabs(tn - t);
-      t = tn;
-      if (step <= tol || step <= 1e-7 || hi - lo <= 9.094947017729282e-13 ||
-          (it == 0 && fabs(gpp) * step * step <= 5e-11 * fabs(a.g)))
-        break;
-    }
-    if (lane == 0) {
-      B.edge_t[e] = t;
-      for (int k = 0; k < d; k++) B.edge_pt[e * d + k] = __dadd_rn(x1[k], __dmul_rn(t, dir[k]));
+  for (int k = 0; k < D; k++) {
+    if (k < d) {
+      const int32_t v = B.edge_y[e * d + k];
+      sy += v;
+      if (k == ko) yo = v;
     }
   }
+  const uint32_t mask = B.edge_mask[e] & ((1u << d) - 1u);
+  const double cs1 = __dmul_rn(F.c, (double)sy);
+  const double cs2 = __dmul_rn(F.c, (double)(sy + __popc(mask)));
+  const double x1o = __dadd_rn(__dmul_rn(F.lam, __dsub_rn((double)yo, cs1)), F.o[ko]);
+  const double x2o =
+      __dadd_rn(__dmul_rn(F.lam, __dsub_rn((double)(yo + (int32_t)((mask >> ko) & 1u)), cs2)), F.o[ko]);
+  const double diro = __dsub_rn(x2o, x1o);
+  const float hio = (float)x1o, loo = (float)(x1o - (double)hio), d32o = (float)diro;
+  double dir[D], x[D];
+  float x1hi[D], x1lo[D], dir32[D];
+  float dd32 = 0.f;
+#pragma unroll
+  for (int k = 0; k < D; k++) {
+    dir[k] = k < d ? __shfl_sync(FULL, diro, k) : 0.0;
+    x1hi[k] = k < d ? __shfl_sync(FULL, hio, k) : 0.f;
+    x1lo[k] = k < d ? __shfl_sync(FULL, loo, k) : 0.f;
+    dir32[k] = k < d ? __shfl_sync(FULL, d32o, k) : 0.f;
+    dd32 = fmaf(dir32[k], dir32[k], dd32);
+  }
+  // 1. segment screen
+  int ns = 0, nw = 0;
+  for (int base = 0; base < R.n; base += 32) {
+    const int j = base + lane;
+    bool keep = false, strong = false;
+    if (j < R.n) {
+      float p[D], pd = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; k++) {
+        p[k] = k < d ? (R.sv32[(int64_t)k * R.n + j] - x1hi[k]) : 0.f;
+        pd = fmaf(p[k], dir32[k], pd);
+      }
+      const float tt = fminf(fmaxf(pd / dd32, 0.f), 1.f);
+      float r2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; k++) {
+        const float q = fmaf(-tt, dir32[k], p[k]);
+        r2 = fmaf(q, q, r2);
+      }
+      keep = r2 <= R.screen_r2;
+      strong = g32 * r2 < R.strong32[j] + 0.5f;
+    }
+    const unsigned ms = __ballot_sync(FULL, keep && strong);
+    const unsigned mw = __ballot_sync(FULL, keep && !strong);
+    const int cs = ns + __popc(ms & lt), cw = nw + __popc(mw & lt);
+    if (keep && strong && cs + nw < NEAR_CAP) near[cs] = j;
+    if (keep && !strong && ns + cw < NEAR_CAP) near[NEAR_CAP - 1 - cw] = j;
+    ns += __popc(ms);
+    nw += __popc(mw);
+  }
+  __syncwarp();
+  const bool overflow = ns + nw > NEAR_CAP;
+  const double f0 = B.edge_f[2 * e], f1 = B.edge_f[2 * e + 1];
+  const bool s1 = f0 >= 0.0;
+  // 2. FP32 Newton (bracketed) from the linear interpolant of the end values
+  float t32 = (float)f0 / ((float)f0 - (float)f1);
+  if (!(t32 > 0.f && t32 < 1.f)) t32 = 0.5f;
+  float gpp = INFINITY;
+  if (!overflow) {
+    const float b32 = (float)R.b;
+    float lo = 0.f, hi = 1.f;
+    for (int it = 0; it < 12; it++) {
+      const Root32 r = root_eval32<D>(R, near, ns, nw, x1hi, x1lo, dir32, dd32, b32, t32);
+      gpp = r.gpp;
+      if ((r.g >= 0.f) == s1) lo = t32; else hi = t32;
+      float tn = t32 - r.g / r.gp;
+      if (!(tn > lo && tn < hi)) tn = 0.5f * (lo + hi);
+      const float step = fabsf(tn - t32);
+      t32 = tn;
+      if (step <= 2e-6f) break;
+    }
+  }
+  // 3. FP64 Newton with a kept bracket
+  double t = (double)t32, xo = 0.0;
+  const double gpp64 = fabs((double)gpp);
+  double lo = 0.0, hi = 1.0;
+  for (int it = 0; it < 64; it++) {
+    xo = __dadd_rn(x1o, __dmul_rn(t, diro));
+    const float xho = (float)xo, xlo = (float)(xo - (double)xho);
+    Split32<D> xs;
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+      x[k] = k < d ? __shfl_sync(FULL, xo, k) : 0.0;
+      xs.hi[k] = k < d ? __shfl_sync(FULL, xho, k) : 0.f;
+      xs.lo[k] = k < d ? __shfl_sync(FULL, xlo, k) : 0.f;
+      xs.dir[k] = dir32[k];
+    }
+    F64Acc a;
+    if (overflow) {
+      a = warp_f64<true, D>(R, x, dir, qs, qw, terms);
+    } else {
+      a = root_eval64<false, D>(R, near, ns, nw, x, dir, xs, terms);
+      if ((double)a.weak * 1.01 * R.weak_rel > R.weak_limit)
+        a = root_eval64<true, D>(R, near, ns, nw, x, dir, xs, terms);
+    }
+    evals++;
+    if (a.f == 0.0) break;
+    if ((a.f >= 0.0) == s1) lo = t; else hi = t;
+    // the derivative only steers the step: its reciprocal in FP32 suffices
+    double tn = t - a.f * (double)(1.0f / (float)a.g);
+    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    const double step = fabs(tn - t);
+    t = tn;
+    if (step <= tol || step <= 1e-7 || hi - lo <= 9.094947017729282e-13 ||
+        (it == 0 && gpp64 * step * step <= 5e-11 * fabs(a.g)))
+      break;
+  }
+  if (lane == 0) B.edge_t[e] = t;
+  if (lane < d) B.edge_pt[e * d + lane] = __dadd_rn(x1o, __dmul_rn(t, diro));
 }
 
 __device__ __forceinline__ void root_flush(const MfTraceBufs &B, unsigned long long evals,
@@ -709,6 +783,7 @@ __device__ __forceinline__ void root_flush(const MfTraceBufs &B, unsigned long l
   }
 }
 
+template <int D>
 __global__ void __launch_bounds__(ROOT_WARPS * 32) k_roots_f64(MfFrame F, MfRbfDev R, MfTraceBufs B,
                                                                uint64_t n_edges, double tol) {
   __shared__ int snear[ROOT_WARPS][NEAR_CAP];
@@ -717,7 +792,7 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32) k_roots_f64(MfFrame F, MfRbfD
   const uint64_t nwarps = (uint64_t)gridDim.x * ROOT_WARPS;
   unsigned long long evals = 0, terms[2] = {0, 0};
   for (uint64_t e = (uint64_t)blockIdx.x * ROOT_WARPS + w; e < n_edges; e += nwarps)
-    root_edge(F, R, B, e, tol, snear[w], sq[w][0], sq[w][1], evals, terms);
+    root_edge<D>(F, R, B, e, tol, snear[w], sq[w][0], sq[w][1], evals, terms);
   root_flush(B, evals, terms);
 }
 
@@ -793,7 +868,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_b_eval(const MfSlot *slots,
     const uint32_t slot = S.B.vert_slot[i];
     if (recheck || S.precision == MF_FP64) {
       unsigned long long terms[2] = {0, 0};
-      const F64Acc a = warp_f64<false>(S.R, x, nullptr, sq[w][0], sq[w][1], terms);
+      const F64Acc a = warp_f64<false, MF_MAXD>(S.R, x, nullptr, sq[w][0], sq[w][1], terms);
       if (lane == 0) {
         S.B.vtab_f[slot] = a.f;
         if (fabs(a.f) < 1e-12) atomicAdd(&S.B.cnt->n_near_zero, 1ull);
@@ -827,7 +902,7 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32) k_b_roots(const MfSlot *slots
     const int t = mf_slot_of(P->pe, n, item);
     const MfSlot &S = slots[t];
     unsigned long long evals = 0, terms[2] = {0, 0};
-    root_edge(S.F, S.R, S.B, item - P->pe[t], S.root_tol, snear[w], sq[w][0], sq[w][1], evals,
+    root_edge<MF_MAXD>(S.F, S.R, S.B, item - P->pe[t], S.root_tol, snear[w], sq[w][0], sq[w][1], evals,
               terms);
     root_flush(S.B, evals, terms);
   }
@@ -855,7 +930,13 @@ void mf_b_launch_roots(const MfSlot *slots, MfBatchPlan *P, int n, const int32_t
 // ---------------------------------------------------------------------------
 void mf_launch_eval_vertices_f64(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, int sms,
                                  cudaStream_t st) {
-  k_eval_vertices_f64<<<sms * 8, EVAL_WARPS * 32, 0, st>>>(F, R, B);
+  switch (F.d) {
+#define MF_CASE(DD) \
+  case DD: k_eval_vertices_f64<DD><<<sms * 8, EVAL_WARPS * 32, 0, st>>>(F, R, B); break;
+    MF_CASE(2) MF_CASE(3) MF_CASE(4) MF_CASE(5) MF_CASE(6) MF_CASE(7)
+#undef MF_CASE
+    default: k_eval_vertices_f64<MF_MAXD><<<sms * 8, EVAL_WARPS * 32, 0, st>>>(F, R, B);
+  }
   k_advance_eval<<<1, 1, 0, st>>>(B.cnt);
 }
 
@@ -863,14 +944,26 @@ void mf_launch_eval_vertices_mixed(const MfFrame &F, const MfRbfDev &R, const Mf
                                    int precision, double band, int sms, cudaStream_t st) {
   (void)precision;
   k_eval_mixed_f32<true><<<sms * 4, MIX_THREADS, 0, st>>>(F, R, B, nullptr, 0, nullptr, nullptr, band);
-  k_recheck_vertices_f64<<<sms * 8, EVAL_WARPS * 32, 0, st>>>(F, R, B);
+  switch (F.d) {
+#define MF_CASE(DD) \
+  case DD: k_recheck_vertices_f64<DD><<<sms * 8, EVAL_WARPS * 32, 0, st>>>(F, R, B); break;
+    MF_CASE(2) MF_CASE(3) MF_CASE(4) MF_CASE(5) MF_CASE(6) MF_CASE(7)
+#undef MF_CASE
+    default: k_recheck_vertices_f64<MF_MAXD><<<sms * 8, EVAL_WARPS * 32, 0, st>>>(F, R, B);
+  }
   k_advance_eval<<<1, 1, 0, st>>>(B.cnt);
 }
 
 void mf_launch_roots_f64(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, uint64_t n_edges,
                          double tol, int sms, cudaStream_t st) {
   if (n_edges == 0) return;
-  k_roots_f64<<<sms * 4, ROOT_WARPS * 32, 0, st>>>(F, R, B, n_edges, tol);
+  switch (F.d) {
+#define MF_CASE(DD) \
+  case DD: k_roots_f64<DD><<<sms * 4, ROOT_WARPS * 32, 0, st>>>(F, R, B, n_edges, tol); break;
+    MF_CASE(2) MF_CASE(3) MF_CASE(4) MF_CASE(5) MF_CASE(6) MF_CASE(7)
+#undef MF_CASE
+    default: k_roots_f64<MF_MAXD><<<sms * 4, ROOT_WARPS * 32, 0, st>>>(F, R, B, n_edges, tol);
+  }
 }
 
 extern "C" int mf_eval(mf_ctx *ctx, const mf_rbf *rbf, const double *q, int64_t n, int32_t precision,

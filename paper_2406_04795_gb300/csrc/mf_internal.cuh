@@ -93,7 +93,8 @@ struct MfRbfDev {
   const double *sv64;  // [d][n]
   const double *alpha; // [n]
   const float *alpha32;// [n]
-  const float *strong32; // [n] ln(|alpha| / 1e-9): term needs the FP64 exp iff gamma r^2 below
+  const float *strong32; // [n] ln(|alpha| / tau): term needs the FP64 exp iff gamma r^2 below
+  const double *exp_tab; // [64] 2^(j/64), the table of mf_exp_neg
   double gamma, b;
   float screen_r2;     // keep a term in the FP64 sum iff r^2 (FP32) <= screen_r2
   double drop_bound;   // sum_i |alpha_i| exp(-gamma * screen cut): bound on dropped terms

@@ -34,7 +34,7 @@ struct MfRbfStats {
 };
 __global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alpha, float *sv32,
                               float *svlo32, double *sv64, float *alpha32, float *strong32,
-                              MfRbfStats *st);
+                              double *exp_tab, MfRbfStats *st);
 __global__ void k_seed_vertices(MfFrame F, MfTraceBufs B, const double *seeds, int64_t n);
 __global__ void k_seed_edges(MfFrame F, MfTraceBufs B, const double *seeds, int64_t n);
 __global__ void k_expand_vertices(MfFrame F, MfTraceBufs B, uint64_t e0, uint64_t n);
@@ -193,7 +193,7 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
     TV = pow2_at_least(MV + MV / 3 + 1);
     TC = pow2_at_least(MC + MC / 3 + 1);
     cell_edges = MC * (uint64_t)((d + 1) * d / 2);
-    need = 256 * 32 + nb * d * 16 + nb * 8 + TE * 12 + TV * 16 + TC * 8 + ME * (12 * d + 28) +
+    need = 256 * 33 + 64 * 8 + nb * d * 16 + nb * 8 + TE * 12 + TV * 16 + TC * 8 + ME * (12 * d + 28) +
            MV * (4 * d + 8) + MC * (5 * d + 8) + 8 + cell_edges * 8 + (MC / kScanTile + 2) * 8;
     if (need <= MF_NOALLOC_SCRATCH_BYTES || def < 1024) break;
   }
@@ -207,6 +207,7 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   float *svlo32 = (float *)cv.take(nb * d * 4);
   float *alpha32 = (float *)cv.take(nb * 4);
   float *strong32 = (float *)cv.take(nb * 4);
+  double *exp_tab = (double *)cv.take(64 * 8);
   MfTraceBufs B;
   memset(&B, 0, sizeof(B));
   B.etab_key = (unsigned long long *)cv.take(TE * 8);
@@ -239,7 +240,7 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   // Support vectors: the same preparation as mf_trace.
   cudaMemsetAsync(stats, 0, sizeof(MfRbfStats), st);
   k_prepare_rbf<<<(n + 255) / 256, 256, 0, st>>>(d, n, rbf->sv, rbf->alpha, sv32, svlo32, sv64,
-                                                  alpha32, strong32, stats);
+                                                  alpha32, strong32, exp_tab, stats);
   MfRbfStats hs;
   if (cudaMemcpyAsync(&hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
@@ -254,6 +255,7 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   R.alpha = rbf->alpha;
   R.alpha32 = alpha32;
   R.strong32 = strong32;
+  R.exp_tab = exp_tab;
   R.gamma = rbf->gamma;
   R.b = rbf->b;
   const double sa = hs.sum_abs_alpha > 0 ? hs.sum_abs_alpha : 1e-300;

@@ -230,14 +230,23 @@ def shell_trace(rng, d: int, n_sv: int, lam: float, n_seeds: int, n_free: int = 
     vector's shell 2 exp(-gamma r^2) = b has radius SHELL_LATTICE_RADIUS[d] *
     lambda; all seeds lie on the free vectors' shells."""
     sv = rng.uniform(-math.pi, math.pi, size=(n_sv, d))
-    alpha = 0.5 * np.abs(rng.normal(size=n_sv))
-    free = rng.choice(n_sv, size=n_free, replace=False)
-    alpha[free] = -2.0
+    alpha0 = 0.5 * np.abs(rng.normal(size=n_sv))
     r_shell = min(SHELL_LATTICE_RADIUS.get(d, 2.0) * lam, 0.8)
     gamma = math.log(2.0 / b) / (r_shell * r_shell)
     lo, hi = np.full(d, -math.pi), np.full(d, math.pi)
-    seeds = place_seeds(rng, sv, alpha, gamma, b, lo, hi, n_seeds, inner=sv[free],
-                        step=0.25 * r_shell, max_steps=16)
+    for attempt in range(32):
+        # a free vector crowded by obstacle vectors may have f >= 0 at its
+        # centre: draw other free vectors
+        alpha = alpha0.copy()
+        free = rng.choice(n_sv, size=n_free, replace=False)
+        alpha[free] = -2.0
+        try:
+            seeds = place_seeds(rng, sv, alpha, gamma, b, lo, hi, n_seeds, inner=sv[free],
+                                step=0.25 * r_shell, max_steps=16)
+            break
+        except ValueError:
+            if attempt == 31:
+                raise
     dh, radius = _dh_arm(rng, d, 0.04)
     reach = float(dh[:, 2].sum())
     centers = _ball(rng, 8, reach)
