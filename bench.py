@@ -8,7 +8,7 @@ for the device-timed value; the e2e figure copies the inputs from pinned host
 memory and reads the point verdicts back every step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--config d5|d3|d6] [--precision auto|fp64|mixed]
+                  [--config d5|d3|d6] [--precision auto|fp64|mixed|mixed_fp32]
 
 Under torchrun each rank traces its own independent workload (seed + rank):
 weak scaling, no collective on the data path.  `--impl reference` times the
@@ -32,8 +32,10 @@ sys.path.insert(0, ROOT)
 
 from paper_2406_04795_gb300 import workloads as W  # noqa: E402
 
-FP64_EXP_FLOPS = 26  # Cody-Waite reduction (2 FMA) + degree-11 Horner (11 FMA), 2 flops per FMA
-WEAK_EXP_FP64_FLOPS = 4  # reduced-cost exp: k = rint(a log2 e) (1 mul) + r = a - k ln2 (1 FMA)
+# FP64 flops of one table-driven exp: k (1 FMA), k - shift (1 add), r (2 FMA),
+# r^2 (1 mul), degree-5 polynomial (4 FMA), table product (1 FMA), 2^m (1 mul);
+# an FMA counts 2 flops
+FP64_EXP_FLOPS = 19
 
 
 def make_workload(cfg: str, rank: int, lam=None):
@@ -113,18 +115,31 @@ def roofline(stats, w, clocks, n_sms=152):
     d = w.d
     mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp64_peak = n_sms * 4.0 * mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
+    if dom == "eval" and w.precision not in ("fp64", "mixed_fp32"):
+        # tensor-core evaluation: the distance GEMM runs on tcgen05, every term
+        # then takes one MUFU ex2 (16 per SM per clock), which binds
+        ex2 = s["terms_weak"] / max(s["launches"], 1)
+        ach = ex2 / (ms_per_launch * 1e-3) / 1e12
+        mufu_peak = n_sms * 16.0 * mhz * 1e6 / 1e12
+        return {"kernel": "k_eval_tc", "bound": "alu", "achieved": ach, "peak": mufu_peak,
+                "unit": "TFLOP/s", "frac": ach / mufu_peak, "traffic": None,
+                "peak_source": "MUFU ex2: %d SMs x 16/clk x %.0f MHz (sampled); one ex2 per "
+                               "RBF term counted as one op" % (n_sms, mhz),
+                "work": "%d RBF terms (vertex x support vector)" % s["terms_weak"],
+                "phase_ms": {k: round(v["ms"], 3) for k, v in stats.items() if v["ms"] > 0}}
     if dom in ("roots", "eval"):
-        base = 5 * d + 5 if dom == "roots" else 3 * d + 3
-        per_strong = base + FP64_EXP_FLOPS
-        per_weak = base + WEAK_EXP_FP64_FLOPS
-        flops = (s["terms"] * per_strong + s["terms_weak"] * per_weak) / max(s["launches"], 1)
+        # a strong term: differences, squares (and, for roots, projections on
+        # the edge direction), -gamma r^2, exp, alpha e and the sums; weak terms
+        # run in FP32 and are not FP64 work
+        per_strong = (5 * d + 5 if dom == "roots" else 3 * d + 3) + FP64_EXP_FLOPS
+        flops = s["terms"] * per_strong / max(s["launches"], 1)
         ach = flops / (ms_per_launch * 1e-3) / 1e12
         return {"kernel": "k_roots_f64" if dom == "roots" else "k_eval_vertices_f64",
                 "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": ach / fp64_peak, "traffic": None,
                 "peak_source": "FP64 pipe: %d SMs x 2 DFMA/clk x %.0f MHz (sampled)" % (n_sms, mhz),
-                "work": "%d FP64-exp terms x %d flops + %d reduced-exp terms x %d FP64 flops" % (
-                    s["terms"], per_strong, s["terms_weak"], per_weak),
+                "work": "%d FP64 terms x %d flops (and %d FP32 weak terms, not counted)" % (
+                    s["terms"], per_strong, s["terms_weak"]),
                 "phase_ms": {k: round(v["ms"], 3) for k, v in stats.items() if v["ms"] > 0}}
     if dom == "certify_points":
         n_obs = int(w.obs_type.shape[0])
@@ -255,8 +270,8 @@ def run_gb300(args):
     w = make_workload(args.config, rank, args.lam)
     if args.precision == "fp64":
         w.precision = "fp64"
-    elif args.precision == "mixed":
-        w.precision = "mixed"
+    elif args.precision in ("mixed", "mixed_fp32"):
+        w.precision = args.precision
     ctx = Context(local, 0)
     proof = Proof(ctx, w)
     stream = torch.cuda.current_stream()
@@ -326,7 +341,7 @@ def run_gb300(args):
             "metric": "traced simplices/s", "value": value, "unit": "simplices/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if w.precision == "fp64" else "f32+f64",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "mixed_fp32": "f32+f64"}.get(w.precision, "bf16+f32+f64"),
             "data": "synthetic",
             "config": {"workload": w.name, "d": w.d, "lambda": w.lam,
                        "n_sv": int(w.sv.shape[0]), "gamma": w.gamma,
@@ -377,7 +392,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="d5", choices=["d3", "d5", "d6"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "mixed_fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lam", type=float, default=None,
                     help="override the lattice scale (small profiling cases)")

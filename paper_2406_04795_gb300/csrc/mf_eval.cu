@@ -134,6 +134,7 @@ int mf_prepare_rbf_at(mf_ctx *ctx, const mf_rbf *rbf, char *base, MfRbfDev *out,
   out->exp_tab = exp_tab;
   out->gamma = rbf->gamma;
   out->b = rbf->b;
+  out->sum_abs_alpha = h.sum_abs_alpha;
   // Screen: drop terms with gamma r^2 > T where sum|alpha| e^-T <= 1e-13.
   double sa = h.sum_abs_alpha > 0 ? h.sum_abs_alpha : 1e-300;
   double T = std::log(sa / 1e-13);
@@ -942,8 +943,10 @@ void mf_launch_eval_vertices_f64(const MfFrame &F, const MfRbfDev &R, const MfTr
 
 void mf_launch_eval_vertices_mixed(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
                                    int precision, double band, int sms, cudaStream_t st) {
-  (void)precision;
-  k_eval_mixed_f32<true><<<sms * 4, MIX_THREADS, 0, st>>>(F, R, B, nullptr, 0, nullptr, nullptr, band);
+  if (precision == MF_MIXED_BF16)
+    mf_launch_eval_vertices_tc(F, R, B, band, sms, st);
+  else
+    k_eval_mixed_f32<true><<<sms * 4, MIX_THREADS, 0, st>>>(F, R, B, nullptr, 0, nullptr, nullptr, band);
   switch (F.d) {
 #define MF_CASE(DD) \
   case DD: k_recheck_vertices_f64<DD><<<sms * 8, EVAL_WARPS * 32, 0, st>>>(F, R, B); break;

@@ -46,7 +46,7 @@ struct MfCounters {
   unsigned int err_table_full;     // a hash probe ran past the table
   unsigned int err_overflow;       // a list ran past its capacity
   unsigned int err_missing;        // a vertex expected in the table was absent
-  unsigned int pad;
+  unsigned int err_timeout;        // a bounded device-side wait gave up
 };
 
 // Pointers of one trace's resident device state (all owned by the context).
@@ -96,6 +96,7 @@ struct MfRbfDev {
   const float *strong32; // [n] ln(|alpha| / tau): term needs the FP64 exp iff gamma r^2 below
   const double *exp_tab; // [64] 2^(j/64), the table of mf_exp_neg
   double gamma, b;
+  double sum_abs_alpha;
   float screen_r2;     // keep a term in the FP64 sum iff r^2 (FP32) <= screen_r2
   double drop_bound;   // sum_i |alpha_i| exp(-gamma * screen cut): bound on dropped terms
   double weak_limit;   // allowed error of the FP32 weak terms (2.5e-13 - drop_bound)
@@ -360,6 +361,8 @@ void mf_launch_eval_vertices_mixed(const MfFrame &F, const MfRbfDev &R, const Mf
                                    int precision, double band, int sms, cudaStream_t st);
 void mf_launch_roots_f64(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
                          uint64_t n_edges, double tol, int sms, cudaStream_t st);
+void mf_launch_eval_vertices_tc(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
+                                double band, int sms, cudaStream_t st);
 
 // Context slots (each a separately grown device allocation).
 enum {

@@ -154,6 +154,7 @@ int sync_read(MfCounters *h, const MfCounters *d, cudaStream_t st) {
     return MF_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return MF_ERR_CUDA;
   if (h->err_table_full || h->err_missing) return MF_ERR_DEVICE;
+  if (h->err_timeout) return MF_ERR_TIMEOUT;
   if (h->err_overflow) return MF_ERR_MAXEDGES;
   return MF_OK;
 }
@@ -258,6 +259,7 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   R.exp_tab = exp_tab;
   R.gamma = rbf->gamma;
   R.b = rbf->b;
+  R.sum_abs_alpha = hs.sum_abs_alpha;
   const double sa = hs.sum_abs_alpha > 0 ? hs.sum_abs_alpha : 1e-300;
   double T = std::log(sa / 1e-13);
   T = T < 30.0 ? 30.0 : (T > 740.0 ? 740.0 : T);

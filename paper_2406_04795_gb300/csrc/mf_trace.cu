@@ -885,6 +885,8 @@ static int read_counters(mf_ctx *ctx, const MfTraceBufs &B, cudaStream_t st) {
     return mf_set_error(ctx, MF_ERR_DEVICE, "a resident hash table is full");
   if (h.err_missing)
     return mf_set_error(ctx, MF_ERR_DEVICE, "vertex missing from the vertex table");
+  if (h.err_timeout)
+    return mf_set_error(ctx, MF_ERR_TIMEOUT, "a tensor-core wait gave up");
   if (h.err_overflow || h.n_edges > B.max_edges || h.n_vertices > B.max_vertices ||
       h.n_cells > B.max_cells)
     return mf_set_error(ctx, MF_ERR_MAXEDGES,
@@ -1156,6 +1158,9 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
     ctx->prof.stats.terms[MF_PH_ROOTS] += (int64_t)h.root_terms;
     ctx->prof.stats.terms_weak[MF_PH_EVAL] += (int64_t)h.eval_terms_weak;
     ctx->prof.stats.terms_weak[MF_PH_ROOTS] += (int64_t)h.root_terms_weak;
+    // the tensor-core evaluation computes every term of every vertex
+    if (opts->precision == MF_MIXED_BF16)
+      ctx->prof.stats.terms_weak[MF_PH_EVAL] += (int64_t)h.n_vertices * rbf->n_sv;
   }
   {
     MfProfScope ps(ctx, MF_PH_COPY, st, 0);

@@ -36,7 +36,10 @@ def sizing_for(w) -> dict:
 
 
 def precision_of(w) -> int:
-    return mf.MF_FP64 if w.precision == "fp64" else mf.MF_MIXED_FP32
+    """fp64: FP64 throughout; mixed: distance GEMM on the tensor cores (BF16
+    split operands, FP32 accumulation) with FP64 recheck; mixed_fp32: FP32
+    SIMT distances with FP64 recheck."""
+    return {"fp64": mf.MF_FP64, "mixed_fp32": mf.MF_MIXED_FP32}.get(w.precision, mf.MF_MIXED_BF16)
 
 
 class Proof:

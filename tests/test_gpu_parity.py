@@ -57,7 +57,7 @@ def test_eval_fp64_and_mixed(ctx, d, n_sv, gamma):
         assert np.array_equal(fm[mask] >= 0, fo[mask] >= 0)
 
 
-@pytest.mark.parametrize("precision", [mf.MF_FP64, mf.MF_MIXED_FP32])
+@pytest.mark.parametrize("precision", [mf.MF_FP64, mf.MF_MIXED_FP32, mf.MF_MIXED_BF16])
 def test_d3_config_full_parity(ctx, precision):
     w = W.config_d3()
     g = P.gpu_trace(ctx, w, precision)
@@ -88,7 +88,7 @@ def test_result_independent_of_batch_cap(ctx, cap):
 
 @pytest.mark.parametrize("d,lam,n_sv,seed", [(2, 0.05, 12, 2), (3, 0.15, 20, 2), (4, 0.3, 16, 3),
                                              (5, 0.5, 16, 4), (6, 0.7, 12, 5)])
-@pytest.mark.parametrize("precision", [mf.MF_FP64, mf.MF_MIXED_FP32])
+@pytest.mark.parametrize("precision", [mf.MF_FP64, mf.MF_MIXED_FP32, mf.MF_MIXED_BF16])
 def test_random_problems_parity(ctx, d, lam, n_sv, seed, precision):
     w = W.random_small(d, n_sv, seed, lam, gamma=1.5, n_seeds=4, box=1.3)
     o = P.oracle_trace(w, roots=True, cells=d <= 5)
@@ -169,3 +169,23 @@ def test_two_call_capacity_pattern(ctx):
     assert out2.n_edges == E
     assert set(P.keys(big["edge_y"].cpu().numpy(), big["edge_mask"].cpu().numpy())) == \
         set(P.keys(r["edge_y"].cpu().numpy(), r["edge_mask"].cpu().numpy()))
+
+
+@pytest.mark.parametrize("d,lam", [(5, 0.3), (6, 0.5)])
+def test_tensor_core_eval_matches_fp64(ctx, d, lam):
+    """The tcgen05 vertex evaluation (many 128-vertex tiles, many 64-vector
+    chunks, ragged last tile) leaves every sign decision FP64-exact: the
+    traced set, cells and roots equal the FP64 path's, and the FP32 values it
+    keeps are within the band of the FP64 ones."""
+    w = W.config_d5(lam=lam) if d == 5 else W.config_d6(lam=lam, n_sv=4096)
+    a = P.gpu_trace(ctx, w, mf.MF_FP64)
+    b = P.gpu_trace(ctx, w, mf.MF_MIXED_BF16)
+    assert a["n_edges"] > 5000 and a["n_edges"] == b["n_edges"]
+    ka = {k: i for i, k in enumerate(P.keys(a["edge_y"], a["edge_mask"]))}
+    kb = P.keys(b["edge_y"], b["edge_mask"])
+    assert set(kb) == set(ka)
+    ia = np.array([ka[k] for k in kb])
+    assert np.max(np.abs(a["edge_t"][ia] - b["edge_t"])) <= 1e-9
+    assert np.max(np.abs(a["edge_f"][ia] - b["edge_f"])) <= 1e-3
+    assert set(P.cell_keys(a["cell_y"], a["cell_perm"])) == set(P.cell_keys(b["cell_y"], b["cell_perm"]))
+    assert 0 < b["n_recheck"] < b["n_vertices"]
