@@ -275,6 +275,15 @@ def run_gb300(args):
     ctx = Context(local, 0)
     proof = Proof(ctx, w)
     stream = torch.cuda.current_stream()
+    tune = None
+    if not args.no_autotune:
+        # untimed: launch variants and BFS chunk picked on this workload (one
+        # proof first, so that its capacities have grown to fit)
+        proof.step()
+        sz = proof.sizing
+        tune = ctx.autotune(w, precision=proof.precision, batch_cap=w.batch_cap,
+                            max_edges=sz["max_edges"], max_vertices=sz["max_vertices"],
+                            max_cells=sz["max_cells"], recheck_band=w.recheck_band)
 
     def barrier():
         if world > 1:
@@ -349,6 +358,7 @@ def run_gb300(args):
                        "precision": w.precision, "edges_per_proof": E,
                        "cells_per_proof": r["n_cells"], "vertices_per_proof": r["n_vertices"],
                        "bfs_levels": r["levels"], "ms_per_proof": ms_max,
+                       "autotune": tune,
                        "l2": "inputs larger than L2 (resident hash tables and lists are GBs)"},
             "e2e": {"value": e2e_edges_all / args.steps / (e2e_max / args.steps),
                     "unit": "simplices/s", "h2d_bytes_per_step": h2d,
@@ -394,6 +404,7 @@ def main():
     ap.add_argument("--config", default="d5", choices=["d3", "d5", "d6"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "mixed_fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--lam", type=float, default=None,
                     help="override the lattice scale (small profiling cases)")
     ap.add_argument("--no-extras", action="store_true",

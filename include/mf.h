@@ -44,7 +44,9 @@ extern "C" {
 #define MF_ERR_CUDA (-7)      /* a CUDA runtime call failed */
 #define MF_ERR_DEVICE (-8)    /* a device-side check failed (hash probe limit, index) */
 
-/* Arithmetic of the RBF evaluation (north-star "Precision"). */
+/* Arithmetic of the RBF evaluation.  The mixed paths re-evaluate in FP64 every
+ * vertex whose sign their error bound cannot decide, so all three trace the
+ * same set. */
 #define MF_FP64 0        /* FP64 differences and exp */
 #define MF_MIXED_BF16 1  /* distance GEMM on tcgen05 tensor cores (BF16 split, FP32
                             accumulate), FP32 exp, FP64 recheck of |f~| <= band */
@@ -296,6 +298,34 @@ typedef struct {
 int mf_ctx_set_profiling(mf_ctx *ctx, int enable);
 /* Copies the accumulated stats (zeros when profiling is off). */
 int mf_ctx_get_stats(mf_ctx *ctx, mf_stats *out);
+
+/* Autotuning (batched multi-trace and single traces; no counterpart in the
+ * paper, which runs fixed launch shapes).  mf_autotune traces the request
+ * once per BFS-chunk candidate (roots and cells off), then times on that
+ * trace the launch variants of the root solve (register cap x grid), of the
+ * FP64 vertex evaluation (grid) and, for MF_MIXED_BF16, of the tensor-core
+ * chunk width (64 or 128 support vectors per MMA).  The fastest of each is
+ * kept in the context and used by every later mf_trace on it; *out (host)
+ * receives the choices and their times.  Results of earlier traces are
+ * invalidated (mf_trace_fetch fails until the next mf_trace). */
+typedef struct {
+  int32_t roots_variant;       /* 0: up to 128 registers (2 blocks/SM), 1: 3 blocks/SM */
+  int32_t roots_blocks_per_sm; /* root-solve grid = this x SMs */
+  int32_t eval_blocks_per_sm;  /* FP64 vertex-evaluation grid = this x SMs */
+  int32_t tc_chunk;            /* support vectors per tensor-core MMA: 64 or 128 */
+  int64_t frontier_chunk;      /* edges per BFS expansion step; 0 = the batch cap */
+  double ms_bfs;               /* measured: breadth-first search with the chosen chunk */
+  double ms_roots;             /* measured: root solve of the sampled edges */
+  double ms_eval;              /* measured: evaluation of every traced vertex */
+  int32_t n_candidates;        /* launch variants timed */
+  int32_t pad;
+} mf_tune;
+int mf_autotune(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom, const mf_trace_opts *opts,
+                const double *seeds, int64_t n_seeds, mf_tune *out, void *stream);
+/* Applies launch choices (NULL restores the defaults) / reads the current ones
+ * (the ms_* and n_candidates fields are ignored / zero). */
+int mf_ctx_set_tune(mf_ctx *ctx, const mf_tune *t);
+int mf_ctx_get_tune(mf_ctx *ctx, mf_tune *out);
 
 #ifdef __cplusplus
 }

@@ -118,6 +118,19 @@ class Context:
             _buffers=res)
         return result
 
+    def autotune(self, w, precision=mf.MF_FP64, batch_cap=1 << 24, max_edges=1 << 22,
+                 max_vertices=0, max_cells=0, recheck_band=1e-3, root_tol=1e-12, stream=None):
+        """Times launch variants on a trace of workload w and keeps the
+        fastest for later traces on this context (mf_autotune)."""
+        r, keep = self.rbf(w.sv, w.alpha, w.gamma, w.b)
+        dom = self.domain(w.lo, w.hi, w.offset)
+        sd = _dev(w.seeds, torch.float64, self.device).reshape(-1, r.d)
+        opts = mf.mf_trace_opts(float(w.lam), int(batch_cap), int(precision), float(recheck_band),
+                                float(root_tol), int(max_edges), int(max_vertices), int(max_cells),
+                                0)
+        return mf.mf_autotune(self.h, r, dom, opts, sd.data_ptr(), sd.shape[0],
+                              _stream_handle(stream)).as_dict()
+
     def trace_batch(self, workloads, precisions=None, roots=True, cells=True, capacities=None,
                     batch_cap=1 << 24, recheck_band=1e-3, root_tol=1e-12, stream=None):
         """Traces many workloads in one batched call (mf_trace_batch).

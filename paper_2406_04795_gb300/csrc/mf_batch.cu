@@ -33,7 +33,7 @@ struct Bump {
 struct TraceLayout {
   size_t rbf, dom, cnt, etab_key, etab_val, vtab_key, vtab_f, ctab_key;
   size_t edge_y, edge_mask, edge_f, edge_t, edge_pt, vert_y, vert_slot, recheck;
-  size_t cell_y, cell_perm, cell_off, scan;
+  size_t cell_y, cell_perm, cell_sgn, cell_off, scan;
   uint64_t ME, MV, MC, TE, TV, TC;
   std::vector<int2> tab;
 };
@@ -130,6 +130,7 @@ int mf_layout_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom, const 
   const uint64_t mc = (o->flags & MF_WANT_CELLS) ? l->MC : 0;
   l->cell_y = bump->take(mc * d * 4 + 8);
   l->cell_perm = bump->take(mc * d + 8);
+  l->cell_sgn = bump->take(mc * 4 + 8);
   l->cell_off = bump->take((mc + 1) * 8);
   l->scan = bump->take((mc / 4096 + 2) * 8);
   return MF_OK;
@@ -170,6 +171,7 @@ int mf_setup_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_trace_opts *o, char 
   B.max_vertices = l->MV;
   B.cell_y = (int32_t *)(base + l->cell_y);
   B.cell_perm = (uint8_t *)(base + l->cell_perm);
+  B.cell_sgn = (uint32_t *)(base + l->cell_sgn);
   B.cell_off = (int64_t *)(base + l->cell_off);
   B.max_cells = (o->flags & MF_WANT_CELLS) ? l->MC : 0;
   S->precision = o->precision;

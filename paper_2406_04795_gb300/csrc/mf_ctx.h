@@ -11,6 +11,9 @@ struct MfTraceState {
   bool valid = false;
   MfFrame F;
   MfTraceBufs B;
+  MfRbfDev R;
+  int32_t precision = 0;
+  double band = 0.0, tol = 0.0;
   int64_t n_edges = 0, n_cells = 0, n_cell_edges = 0, n_vertices = 0, n_near_zero = 0,
           n_recheck = 0, n_boundary = 0, n_dead_seeds = 0, levels = 0, root_evals = 0;
   uint32_t flags = 0;
@@ -36,6 +39,7 @@ struct mf_ctx {
   MfCounters *h_counters = nullptr;  // pinned host mirror of the device counters
   MfTraceState last;
   MfProfiler prof;
+  MfTune tune;
 };
 
 void mf_frame_lattice(MfFrame *F, int d, double lam, const double *o);

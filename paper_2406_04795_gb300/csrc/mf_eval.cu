@@ -46,7 +46,7 @@ struct MfRbfStats {
 
 __global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alpha, float *sv32,
                               float *svlo32, double *sv64, float *alpha32, float *strong32,
-                              double *exp_tab, MfRbfStats *st) {
+                              double *exp_tab, double *sv64r, float *svhl, MfRbfStats *st) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < 64) exp_tab[j] = exp2((double)j / 64.0);
   double a = 0.0;
@@ -58,9 +58,18 @@ __global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alph
       if (!isfinite(s)) bad = 1;
       sv64[(int64_t)k * n + j] = s;
       const float hi = (float)s;
+      const float lo = (float)(s - (double)hi);
       sv32[(int64_t)k * n + j] = hi;
-      svlo32[(int64_t)k * n + j] = (float)(s - (double)hi);
+      svlo32[(int64_t)k * n + j] = lo;
+      sv64r[(int64_t)j * 8 + k] = s;
+      svhl[(int64_t)j * 16 + 2 * k] = hi;
+      svhl[(int64_t)j * 16 + 2 * k + 1] = lo;
       m = fmaxf(m, fabsf(hi));
+    }
+    for (int k = d; k < 8; k++) {
+      sv64r[(int64_t)j * 8 + k] = 0.0;
+      svhl[(int64_t)j * 16 + 2 * k] = 0.f;
+      svhl[(int64_t)j * 16 + 2 * k + 1] = 0.f;
     }
     double al = alpha[j];
     if (!isfinite(al)) bad = 1;
@@ -85,7 +94,7 @@ __global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alph
 size_t mf_rbf_prep_bytes(int d, int64_t n) {
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t nb = (size_t)n;
-  return 256 + al(nb * d * 8) + 2 * al(nb * d * 4) + 2 * al(nb * 4) + al(64 * 8);
+  return 256 + al(nb * d * 8) + 2 * al(nb * d * 4) + 2 * al(nb * 4) + al(64 * 8) + 2 * al(nb * 64);
 }
 
 int mf_prepare_rbf(mf_ctx *ctx, const mf_rbf *rbf, MfRbfDev *out, cudaStream_t st) {
@@ -112,10 +121,12 @@ int mf_prepare_rbf_at(mf_ctx *ctx, const mf_rbf *rbf, char *base, MfRbfDev *out,
   float *svlo32 = (float *)p; p += al(nb * d * 4);
   float *alpha32 = (float *)p; p += al(nb * 4);
   float *strong32 = (float *)p; p += al(nb * 4);
-  double *exp_tab = (double *)p;
+  double *exp_tab = (double *)p; p += al(64 * 8);
+  double *sv64r = (double *)p; p += al(nb * 64);
+  float *svhl = (float *)p;
   cudaMemsetAsync(dst, 0, sizeof(MfRbfStats), st);
   k_prepare_rbf<<<(n + 255) / 256, 256, 0, st>>>(d, n, rbf->sv, rbf->alpha, sv32, svlo32, sv64,
-                                                  alpha32, strong32, exp_tab, dst);
+                                                  alpha32, strong32, exp_tab, sv64r, svhl, dst);
   MfRbfStats h;
   int rc = mf_cuda_check(ctx, cudaMemcpyAsync(&h, dst, sizeof(h), cudaMemcpyDeviceToHost, st),
                          "prepare rbf");
@@ -132,6 +143,8 @@ int mf_prepare_rbf_at(mf_ctx *ctx, const mf_rbf *rbf, char *base, MfRbfDev *out,
   out->alpha32 = alpha32;
   out->strong32 = strong32;
   out->exp_tab = exp_tab;
+  out->sv64r = sv64r;
+  out->svhl = svhl;
   out->gamma = rbf->gamma;
   out->b = rbf->b;
   out->sum_abs_alpha = h.sum_abs_alpha;
@@ -221,12 +234,18 @@ __device__ __forceinline__ void f64_term(const MfRbfDev &R, const double *x, con
   if (j < 0) return;
   const int d = dim_of<D>(R.d);
   double r2 = 0.0, proj = 0.0;
+  const double2 *row = reinterpret_cast<const double2 *>(R.sv64r + (int64_t)j * 8);
 #pragma unroll
-  for (int k = 0; k < D; k++) {
-    if (k < d) {
-      double t = x[k] - R.sv64[(int64_t)k * R.n + j];
-      r2 = fma(t, t, r2);
-      if (GRAD) proj = fma(t, dir[k], proj);
+  for (int k2 = 0; k2 < (D + 1) / 2; k2++) {
+    const double2 s = __ldg(row + k2);
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int k = 2 * k2 + h;
+      if (k < D && k < d) {
+        const double t = x[k] - (h ? s.y : s.x);
+        r2 = fma(t, t, r2);
+        if (GRAD) proj = fma(t, dir[k], proj);
+      }
     }
   }
   const double e = R.alpha[j] * mf_exp_neg(-R.gamma * r2, R.exp_tab);
@@ -245,13 +264,18 @@ __device__ __forceinline__ void f32_weak_term(const MfRbfDev &R, const Split32<D
   const int d = dim_of<D>(R.d);
   const float g2 = (float)(R.gamma * 1.4426950408889634);
   float r2 = 0.f, proj = 0.f;
+  const float4 *row = reinterpret_cast<const float4 *>(R.svhl + (int64_t)j * 16);
 #pragma unroll
-  for (int k = 0; k < D; k++) {
-    if (k < d) {
-      const float t = (x.hi[k] - R.sv32[(int64_t)k * R.n + j]) +
-                      (x.lo[k] - R.svlo32[(int64_t)k * R.n + j]);
-      r2 = fmaf(t, t, r2);
-      if (GRAD) proj = fmaf(t, x.dir[k], proj);
+  for (int k2 = 0; k2 < (D + 1) / 2; k2++) {
+    const float4 s = __ldg(row + k2);
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int k = 2 * k2 + h;
+      if (k < D && k < d) {
+        const float t = (x.hi[k] - (h ? s.z : s.x)) + (x.lo[k] - (h ? s.w : s.y));
+        r2 = fmaf(t, t, r2);
+        if (GRAD) proj = fmaf(t, x.dir[k], proj);
+      }
     }
   }
   const float e = R.alpha32[j] * ex2_approx(-g2 * r2);
@@ -593,14 +617,20 @@ __device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const int *near
   for (int i = lane; i < total; i += 32) {
     const int j = i < ns ? near[i] : near[NEAR_CAP - 1 - (i - ns)];
     float r2 = 0.f, proj = 0.f;
+    const float4 *row = reinterpret_cast<const float4 *>(R.svhl + (int64_t)j * 16);
 #pragma unroll
-    for (int k = 0; k < D; k++) {
-      if (k < d) {
-        const float a = x1hi[k] - R.sv32[(int64_t)k * R.n + j];
-        const float b = fmaf(t, dir32[k], x1lo[k] - R.svlo32[(int64_t)k * R.n + j]);
-        const float df = a + b;
-        r2 = fmaf(df, df, r2);
-        proj = fmaf(df, dir32[k], proj);
+    for (int k2 = 0; k2 < (D + 1) / 2; k2++) {
+      const float4 s = __ldg(row + k2);
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int k = 2 * k2 + h;
+        if (k < D && k < d) {
+          const float a = x1hi[k] - (h ? s.z : s.x);
+          const float b = fmaf(t, dir32[k], x1lo[k] - (h ? s.w : s.y));
+          const float df = a + b;
+          r2 = fmaf(df, df, r2);
+          proj = fmaf(df, dir32[k], proj);
+        }
       }
     }
     const float e = R.alpha32[j] * ex2_approx(-g2 * r2);
@@ -784,8 +814,8 @@ __device__ __forceinline__ void root_flush(const MfTraceBufs &B, unsigned long l
   }
 }
 
-template <int D>
-__global__ void __launch_bounds__(ROOT_WARPS * 32) k_roots_f64(MfFrame F, MfRbfDev R, MfTraceBufs B,
+template <int D, int MINB>
+__global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(MfFrame F, MfRbfDev R, MfTraceBufs B,
                                                                uint64_t n_edges, double tol) {
   __shared__ int snear[ROOT_WARPS][NEAR_CAP];
   __shared__ int sq[ROOT_WARPS][2][64];
@@ -929,22 +959,24 @@ void mf_b_launch_roots(const MfSlot *slots, MfBatchPlan *P, int n, const int32_t
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-void mf_launch_eval_vertices_f64(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, int sms,
-                                 cudaStream_t st) {
+void mf_launch_eval_vertices_f64(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
+                                 const MfTune &T, int sms, cudaStream_t st) {
+  const int g = sms * T.eval_bps;
   switch (F.d) {
 #define MF_CASE(DD) \
-  case DD: k_eval_vertices_f64<DD><<<sms * 8, EVAL_WARPS * 32, 0, st>>>(F, R, B); break;
+  case DD: k_eval_vertices_f64<DD><<<g, EVAL_WARPS * 32, 0, st>>>(F, R, B); break;
     MF_CASE(2) MF_CASE(3) MF_CASE(4) MF_CASE(5) MF_CASE(6) MF_CASE(7)
 #undef MF_CASE
-    default: k_eval_vertices_f64<MF_MAXD><<<sms * 8, EVAL_WARPS * 32, 0, st>>>(F, R, B);
+    default: k_eval_vertices_f64<MF_MAXD><<<g, EVAL_WARPS * 32, 0, st>>>(F, R, B);
   }
   k_advance_eval<<<1, 1, 0, st>>>(B.cnt);
 }
 
 void mf_launch_eval_vertices_mixed(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
-                                   int precision, double band, int sms, cudaStream_t st) {
+                                   int precision, double band, const MfTune &T, int sms,
+                                   cudaStream_t st) {
   if (precision == MF_MIXED_BF16)
-    mf_launch_eval_vertices_tc(F, R, B, band, sms, st);
+    mf_launch_eval_vertices_tc(F, R, B, band, T.tc_chunk, sms, st);
   else
     k_eval_mixed_f32<true><<<sms * 4, MIX_THREADS, 0, st>>>(F, R, B, nullptr, 0, nullptr, nullptr, band);
   switch (F.d) {
@@ -957,16 +989,24 @@ void mf_launch_eval_vertices_mixed(const MfFrame &F, const MfRbfDev &R, const Mf
   k_advance_eval<<<1, 1, 0, st>>>(B.cnt);
 }
 
-void mf_launch_roots_f64(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, uint64_t n_edges,
-                         double tol, int sms, cudaStream_t st) {
-  if (n_edges == 0) return;
+template <int MINB>
+static void launch_roots(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, uint64_t n_edges,
+                         double tol, int grid, cudaStream_t st) {
   switch (F.d) {
 #define MF_CASE(DD) \
-  case DD: k_roots_f64<DD><<<sms * 4, ROOT_WARPS * 32, 0, st>>>(F, R, B, n_edges, tol); break;
+  case DD: k_roots_f64<DD, MINB><<<grid, ROOT_WARPS * 32, 0, st>>>(F, R, B, n_edges, tol); break;
     MF_CASE(2) MF_CASE(3) MF_CASE(4) MF_CASE(5) MF_CASE(6) MF_CASE(7)
 #undef MF_CASE
-    default: k_roots_f64<MF_MAXD><<<sms * 4, ROOT_WARPS * 32, 0, st>>>(F, R, B, n_edges, tol);
+    default: k_roots_f64<MF_MAXD, MINB><<<grid, ROOT_WARPS * 32, 0, st>>>(F, R, B, n_edges, tol);
   }
+}
+
+void mf_launch_roots_f64(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, uint64_t n_edges,
+                         double tol, const MfTune &T, int sms, cudaStream_t st) {
+  if (n_edges == 0) return;
+  const int grid = sms * T.roots_bps;
+  if (T.roots_variant == 1) launch_roots<3>(F, R, B, n_edges, tol, grid, st);
+  else launch_roots<2>(F, R, B, n_edges, tol, grid, st);
 }
 
 extern "C" int mf_eval(mf_ctx *ctx, const mf_rbf *rbf, const double *q, int64_t n, int32_t precision,

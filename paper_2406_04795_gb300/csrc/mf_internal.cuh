@@ -79,6 +79,7 @@ struct MfTraceBufs {
   int32_t *cell_y;     // [MC][d]
   uint8_t *cell_perm;  // [MC][d]
   int64_t *cell_off;   // [MC+1]
+  uint32_t *cell_sgn;  // [MC] per cell vertex i: bit i = in the vertex table, bit 16+i = f >= 0
   int64_t *cell_idx;   // [MC * (d+1)d/2]
   uint64_t max_cells;
   MfCounters *cnt;
@@ -95,6 +96,9 @@ struct MfRbfDev {
   const float *alpha32;// [n]
   const float *strong32; // [n] ln(|alpha| / tau): term needs the FP64 exp iff gamma r^2 below
   const double *exp_tab; // [64] 2^(j/64), the table of mf_exp_neg
+  // row-major copies for gathers (one support vector per 64-byte row):
+  const double *sv64r;   // [n][8] coordinates, zero-padded
+  const float *svhl;     // [n][16] (hi, lo) FP32 pairs of the coordinates
   double gamma, b;
   double sum_abs_alpha;
   float screen_r2;     // keep a term in the FP64 sum iff r^2 (FP32) <= screen_r2
@@ -353,16 +357,27 @@ void mf_exclusive_scan(const int64_t *in, int64_t *out, int64_t n, int64_t *scra
 uint64_t mf_next_pow2(uint64_t x);
 void mf_launch_seeds(const MfFrame &F, const MfTraceBufs &B, const double *seeds, int64_t n,
                      bool vertices, cudaStream_t s);
+// Launch choices picked by the autotuner (mf_autotune); the defaults serve
+// untuned contexts and the allocation-free entry point.
+struct MfTune {
+  int roots_variant = 0;         // 0: no register cap (2 blocks/SM), 1: 3 blocks/SM
+  int roots_bps = 4;             // root-solve blocks per SM in the grid
+  int eval_bps = 8;              // FP64 vertex-evaluation blocks per SM
+  int tc_chunk = 64;             // support vectors per tensor-core MMA: 64 or 128
+  uint64_t frontier_chunk = 0;   // BFS chunk in edges; 0 = the caller's batch cap
+};
+
 // Evaluate f at vertex-list entries [begin, end) read from the device counter
 // (FP64 path); writes vtab_f of each vertex's slot.
 void mf_launch_eval_vertices_f64(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
-                                 int sms, cudaStream_t st);
+                                 const MfTune &T, int sms, cudaStream_t st);
 void mf_launch_eval_vertices_mixed(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
-                                   int precision, double band, int sms, cudaStream_t st);
+                                   int precision, double band, const MfTune &T, int sms,
+                                   cudaStream_t st);
 void mf_launch_roots_f64(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
-                         uint64_t n_edges, double tol, int sms, cudaStream_t st);
+                         uint64_t n_edges, double tol, const MfTune &T, int sms, cudaStream_t st);
 void mf_launch_eval_vertices_tc(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
-                                double band, int sms, cudaStream_t st);
+                                double band, int n_chunk, int sms, cudaStream_t st);
 
 // Context slots (each a separately grown device allocation).
 enum {

@@ -34,7 +34,7 @@ struct MfRbfStats {
 };
 __global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alpha, float *sv32,
                               float *svlo32, double *sv64, float *alpha32, float *strong32,
-                              double *exp_tab, MfRbfStats *st);
+                              double *exp_tab, double *sv64r, float *svhl, MfRbfStats *st);
 __global__ void k_seed_vertices(MfFrame F, MfTraceBufs B, const double *seeds, int64_t n);
 __global__ void k_seed_edges(MfFrame F, MfTraceBufs B, const double *seeds, int64_t n);
 __global__ void k_expand_vertices(MfFrame F, MfTraceBufs B, uint64_t e0, uint64_t n);
@@ -194,7 +194,7 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
     TV = pow2_at_least(MV + MV / 3 + 1);
     TC = pow2_at_least(MC + MC / 3 + 1);
     cell_edges = MC * (uint64_t)((d + 1) * d / 2);
-    need = 256 * 33 + 64 * 8 + nb * d * 16 + nb * 8 + TE * 12 + TV * 16 + TC * 8 + ME * (12 * d + 28) +
+    need = 256 * 35 + 64 * 8 + nb * 128 + nb * d * 16 + nb * 8 + TE * 12 + TV * 16 + TC * 8 + ME * (12 * d + 28) +
            MV * (4 * d + 8) + MC * (5 * d + 8) + 8 + cell_edges * 8 + (MC / kScanTile + 2) * 8;
     if (need <= MF_NOALLOC_SCRATCH_BYTES || def < 1024) break;
   }
@@ -209,6 +209,8 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   float *alpha32 = (float *)cv.take(nb * 4);
   float *strong32 = (float *)cv.take(nb * 4);
   double *exp_tab = (double *)cv.take(64 * 8);
+  double *sv64r = (double *)cv.take(nb * 64);
+  float *svhl = (float *)cv.take(nb * 64);
   MfTraceBufs B;
   memset(&B, 0, sizeof(B));
   B.etab_key = (unsigned long long *)cv.take(TE * 8);
@@ -241,7 +243,7 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   // Support vectors: the same preparation as mf_trace.
   cudaMemsetAsync(stats, 0, sizeof(MfRbfStats), st);
   k_prepare_rbf<<<(n + 255) / 256, 256, 0, st>>>(d, n, rbf->sv, rbf->alpha, sv32, svlo32, sv64,
-                                                  alpha32, strong32, exp_tab, stats);
+                                                  alpha32, strong32, exp_tab, sv64r, svhl, stats);
   MfRbfStats hs;
   if (cudaMemcpyAsync(&hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
@@ -257,6 +259,8 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   R.alpha32 = alpha32;
   R.strong32 = strong32;
   R.exp_tab = exp_tab;
+  R.sv64r = sv64r;
+  R.svhl = svhl;
   R.gamma = rbf->gamma;
   R.b = rbf->b;
   R.sum_abs_alpha = hs.sum_abs_alpha;
@@ -280,8 +284,8 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
     return MF_ERR_CUDA;
   const double band = opts->recheck_band > 0 ? opts->recheck_band : 1e-3;
   auto eval = [&]() {
-    if (mixed) mf_launch_eval_vertices_mixed(F, R, B, opts->precision, band, sms, st);
-    else mf_launch_eval_vertices_f64(F, R, B, sms, st);
+    if (mixed) mf_launch_eval_vertices_mixed(F, R, B, opts->precision, band, MfTune(), sms, st);
+    else mf_launch_eval_vertices_f64(F, R, B, MfTune(), sms, st);
   };
   MfCounters h;
   if (n_seeds > 0) {
@@ -311,7 +315,8 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   }
   const uint64_t E = fe;
   if (opts->flags & MF_WANT_ROOTS)
-    mf_launch_roots_f64(F, R, B, E, opts->root_tol > 0 ? opts->root_tol : 1e-12, sms, st);
+    mf_launch_roots_f64(F, R, B, E, opts->root_tol > 0 ? opts->root_tol : 1e-12, MfTune(), sms,
+                        st);
   int64_t n_cells = 0, n_cell_edges = 0;
   if ((opts->flags & MF_WANT_CELLS) && E > 0) {
     k_cells_enum<<<(unsigned)((E * 32 + 255) / 256), 256, 0, st>>>(F, B, E);

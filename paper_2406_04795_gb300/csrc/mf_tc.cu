@@ -29,18 +29,24 @@
 #include "mf_tc_ptx.cuh"
 
 #define TC_M 128
-#define TC_N 64
 #define TC_K 32
-#define TC_COLS 128
 #define TC_DY_MAX 256
-#define TC_CTAS_PER_SM 4
-#define TC_SMEM_PER_CTA (52 * 1024)   // caps residency at TC_CTAS_PER_SM
-#define TC_WAIT_NS 2000000000ull      // bounded waits: 2 s
+#define TC_WAIT_NS 2000000000ull  // bounded waits: 2 s
 
+// Chunk width N (support vectors per MMA): 2 N TMEM columns per CTA, so
+// 512 / (2 N) CTAs share an SM; the shared-memory request caps residency there.
+template <int N>
+struct TcCfg {
+  static constexpr int kCols = 2 * N;
+  static constexpr int kCtasPerSm = 512 / (2 * N);
+  static constexpr int kSmemPerCta = (N == 64 ? 52 : 100) * 1024;
+};
+
+template <int N>
 struct TcShared {
   alignas(128) unsigned char a[TC_M * TC_K * 2];
-  alignas(128) unsigned char b[2][TC_N * TC_K * 2];
-  float alpha[2][TC_N];
+  alignas(128) unsigned char b[2][N * TC_K * 2];
+  float alpha[2][N];
   uint64_t bar[2];
   uint32_t tmem;
   int timeout;
@@ -80,10 +86,12 @@ __device__ __forceinline__ void tc_store_row(unsigned char *tile, int r, const f
   }
 }
 
-template <int D>
-__global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_eval_tc(MfFrame F, MfRbfDev R,
-                                                                  MfTraceBufs B, double band) {
-  __shared__ TcShared sh;
+template <int D, int N>
+__global__ void __launch_bounds__(TC_M, TcCfg<N>::kCtasPerSm) k_eval_tc(MfFrame F, MfRbfDev R,
+                                                                        MfTraceBufs B, double band) {
+  constexpr int TC_N = N;
+  constexpr uint32_t TC_COLS = TcCfg<N>::kCols;
+  __shared__ TcShared<N> sh;
   const int t = threadIdx.x, w = t >> 5;
   const uint64_t begin = B.cnt->v_evaluated;
   uint64_t end = B.cnt->n_vertices;
@@ -291,21 +299,29 @@ __global__ void __launch_bounds__(TC_M, TC_CTAS_PER_SM) k_eval_tc(MfFrame F, MfR
   }
 }
 
-// Vertex evaluation on the tensor cores; the caller launches the FP64
-// recheck of the queued vertices afterwards.
-void mf_launch_eval_vertices_tc(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
-                                double band, int sms, cudaStream_t st) {
-  const size_t dyn = TC_SMEM_PER_CTA - sizeof(TcShared);
-  const int grid = sms * TC_CTAS_PER_SM;
+// Vertex evaluation on the tensor cores with chunk width n_chunk (64 or
+// 128 support vectors per MMA); the caller launches the FP64 recheck of the
+// queued vertices afterwards.
+template <int N>
+static void launch_tc(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, double band,
+                      int sms, cudaStream_t st) {
+  const size_t dyn = TcCfg<N>::kSmemPerCta - sizeof(TcShared<N>);
+  const int grid = sms * TcCfg<N>::kCtasPerSm;
   switch (F.d) {
 #define MF_CASE(DD)                                                                       \
   case DD:                                                                                \
-    cudaFuncSetAttribute(k_eval_tc<DD>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+    cudaFuncSetAttribute(k_eval_tc<DD, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                          (int)dyn);                                                       \
-    k_eval_tc<DD><<<grid, TC_M, dyn, st>>>(F, R, B, band);                                \
+    k_eval_tc<DD, N><<<grid, TC_M, dyn, st>>>(F, R, B, band);                             \
     break;
     MF_CASE(2) MF_CASE(3) MF_CASE(4) MF_CASE(5) MF_CASE(6) MF_CASE(7) MF_CASE(8)
 #undef MF_CASE
     default: break;
   }
+}
+
+void mf_launch_eval_vertices_tc(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
+                                double band, int n_chunk, int sms, cudaStream_t st) {
+  if (n_chunk == 128) launch_tc<128>(F, R, B, band, sms, st);
+  else launch_tc<64>(F, R, B, band, sms, st);
 }

@@ -351,28 +351,54 @@ __global__ void k_cells_edges(MfFrame F, MfTraceBufs B, uint64_t n_cells, int64_
 template <bool FILL>
 __device__ __forceinline__ void cell_edges_item(const MfFrame &F, const MfTraceBufs &B, uint64_t c,
                                                 int64_t *cnt_or_off) {
+  // The cell's vertices v_0 = z, v_i = v_{i-1} + e(pi_{i-1}) (query type 5).
+  // Each of them lies in the domain iff it is in the vertex table: the BFS
+  // visits the third vertex of every 2-coface of a traced edge, and every
+  // vertex of this cell shares a 2-coface with the traced edge that made it.
+  // Inside one simplex all crossing edges between in-domain vertices are
+  // linked through 2-cofaces, so the traced edges of the cell are exactly its
+  // in-domain vertex pairs with different signs: the count pass needs only
+  // the d+1 vertex signs, and the fill pass looks up only those pairs.
   const int d = F.d;
   int32_t vi[MF_MAXD];
   int pi[MF_MAXD];
   load_y(B.cell_y + c * d, d, vi);
   for (int k = 0; k < d; k++) pi[k] = B.cell_perm[c * d + k];
-  int64_t pos = FILL ? cnt_or_off[c] : 0;
-  int64_t count = 0;
+  uint32_t sg;
+  if (!FILL) {
+    uint32_t in = 0, pos = 0;
+    int32_t w[MF_MAXD];
+    load_y(vi, d, w);
+    for (int i = 0; i <= d; i++) {
+      if (i > 0) w[pi[i - 1]] += 1;
+      const uint64_t slot = mf_table_find(B.vtab_key, B.vtab_mask, mf_vertex_key(F, w));
+      if (slot == ~0ull) continue;
+      in |= 1u << i;
+      if (B.vtab_f[slot] >= 0.0) pos |= 1u << i;
+    }
+    sg = in | (pos << 16);
+    B.cell_sgn[c] = sg;
+    cnt_or_off[c] = (int64_t)__popc(in & pos) * (int64_t)__popc(in & ~pos);
+    return;
+  }
+  sg = B.cell_sgn[c];
+  const uint32_t in = sg & 0xFFFFu, pos = sg >> 16;
+  int64_t at = cnt_or_off[c];
   for (int i = 0; i < d; i++) {
-    int32_t vj[MF_MAXD];
-    load_y(vi, d, vj);
     uint32_t mask = 0;
     for (int j = i + 1; j <= d; j++) {
       mask |= 1u << pi[j - 1];
-      vj[pi[j - 1]] += 1;
+      if (!((in >> i) & (in >> j) & 1u) || ((pos >> i) & 1u) == ((pos >> j) & 1u)) continue;
       const uint64_t slot = mf_table_find(B.etab_key, B.etab_mask, mf_edge_key(F, vi, mask));
-      if (slot == ~0ull) continue;
-      if (FILL) B.cell_idx[pos + count] = (int64_t)B.etab_val[slot];
-      count++;
+      if (slot == ~0ull) {
+        atomicOr(&B.cnt->err_missing, 2u);
+        B.cell_idx[at++] = -1;
+        continue;
+      }
+      B.cell_idx[at++] = (int64_t)B.etab_val[slot];
     }
     vi[pi[i]] += 1;
   }
-  if (!FILL) cnt_or_off[c] = count;
 }
 
 // ---------------------------------------------------------------------------
@@ -933,11 +959,12 @@ static int setup_buffers(mf_ctx *ctx, int d, uint64_t ME, uint64_t MV, uint64_t 
   B->vert_slot = (uint32_t *)v; v += al(MV * 4);
   B->recheck = mixed ? (uint32_t *)v : nullptr;
   B->max_vertices = MV;
-  size_t cb = al(MC * d * 4) + al(MC * d) + al((MC + 1) * 8);
+  size_t cb = al(MC * d * 4) + al(MC * d) + al(MC * 4) + al((MC + 1) * 8);
   char *c = (char *)mf_ctx_buffer(ctx, MF_SLOT_CELLS, cb);
   if (!c) return MF_ERR_OOM;
   B->cell_y = (int32_t *)c; c += al(MC * d * 4);
   B->cell_perm = (uint8_t *)c; c += al(MC * d);
+  B->cell_sgn = (uint32_t *)c; c += al(MC * 4);
   B->cell_off = (int64_t *)c;
   B->max_cells = MC;
   B->cnt = (MfCounters *)mf_ctx_buffer(ctx, MF_SLOT_COUNTERS, sizeof(MfCounters));
@@ -1033,7 +1060,8 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
   MfTraceBufs B;
   rc = setup_buffers(ctx, d, ME, MV, MC, mixed, &B);
   if (rc) return rc;
-  const uint64_t cap = opts->batch_cap_edges > 0 ? (uint64_t)opts->batch_cap_edges : (1ull << 24);
+  uint64_t cap = opts->batch_cap_edges > 0 ? (uint64_t)opts->batch_cap_edges : (1ull << 24);
+  if (ctx->tune.frontier_chunk > 0 && ctx->tune.frontier_chunk < cap) cap = ctx->tune.frontier_chunk;
   const double band = opts->recheck_band > 0 ? opts->recheck_band : 1e-3;
   const double tol = opts->root_tol > 0 ? opts->root_tol : 1e-12;
   const int sms = ctx->sms;
@@ -1044,8 +1072,8 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
   if (opts->flags & MF_WANT_CELLS) cudaMemsetAsync(B.ctab_key, 0xFF, (B.ctab_mask + 1) * 8, st);
 
   auto eval = [&]() {
-    if (mixed) mf_launch_eval_vertices_mixed(F, R, B, opts->precision, band, sms, st);
-    else mf_launch_eval_vertices_f64(F, R, B, sms, st);
+    if (mixed) mf_launch_eval_vertices_mixed(F, R, B, opts->precision, band, ctx->tune, sms, st);
+    else mf_launch_eval_vertices_f64(F, R, B, ctx->tune, sms, st);
   };
 
   // Locate edges (Fig. 3)
@@ -1095,7 +1123,7 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
   // Roots (the iterative intersection solve of Sec. VI), FP64 Newton.
   if (opts->flags & MF_WANT_ROOTS) {
     MfProfScope ps(ctx, MF_PH_ROOTS, st, E > 0 ? 1 : 0, (int64_t)E);
-    mf_launch_roots_f64(F, R, B, E, tol, sms, st);
+    mf_launch_roots_f64(F, R, B, E, tol, ctx->tune, sms, st);
   }
 
   // Cells (Sec. IV-C) and the cell -> edge CSR.
@@ -1140,6 +1168,10 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
   MfTraceState &L = ctx->last;
   L.F = F;
   L.B = B;
+  L.R = R;
+  L.precision = opts->precision;
+  L.band = band;
+  L.tol = tol;
   L.flags = opts->flags;
   const MfCounters &h = *ctx->h_counters;
   L.n_edges = (int64_t)E;

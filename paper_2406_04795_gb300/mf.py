@@ -35,7 +35,8 @@ EXPORTS = ("mf_ctx_create", "mf_ctx_destroy", "mf_last_error", "mf_ctx_bytes", "
            "mf_eval", "mf_trace", "mf_trace_fetch", "mf_certify", "mf_ctx_set_profiling",
            "mf_ctx_get_stats", "mf_trace_noalloc", "mf_trace_batch", "mf_domain_table",
            "mf_server_create", "mf_server_destroy", "mf_server_submit", "mf_server_step",
-           "mf_server_status", "mf_server_fetch")
+           "mf_server_status", "mf_server_fetch", "mf_autotune", "mf_ctx_set_tune",
+           "mf_ctx_get_tune")
 
 MF_PHASES = 12
 PHASE_NAMES = ("prepare", "seeds", "expand_vertices", "eval", "expand_edges", "roots", "cells",
@@ -86,6 +87,16 @@ class mf_stats(C.Structure):
                 ("terms_weak", C.c_int64 * MF_PHASES)]
 
 
+class mf_tune(C.Structure):
+    _fields_ = [("roots_variant", C.c_int32), ("roots_blocks_per_sm", C.c_int32),
+                ("eval_blocks_per_sm", C.c_int32), ("tc_chunk", C.c_int32),
+                ("frontier_chunk", C.c_int64), ("ms_bfs", C.c_double), ("ms_roots", C.c_double),
+                ("ms_eval", C.c_double), ("n_candidates", C.c_int32), ("pad", C.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad"}
+
+
 _lib = None
 
 
@@ -130,6 +141,13 @@ def load(build_if_missing: bool = True):
     L.mf_ctx_set_profiling.argtypes = [V, C.c_int]
     L.mf_ctx_get_stats.restype = C.c_int
     L.mf_ctx_get_stats.argtypes = [V, P(mf_stats)]
+    L.mf_autotune.restype = C.c_int
+    L.mf_autotune.argtypes = [V, P(mf_rbf), P(mf_domain), P(mf_trace_opts), V, C.c_int64,
+                              P(mf_tune), V]
+    L.mf_ctx_set_tune.restype = C.c_int
+    L.mf_ctx_set_tune.argtypes = [V, P(mf_tune)]
+    L.mf_ctx_get_tune.restype = C.c_int
+    L.mf_ctx_get_tune.argtypes = [V, P(mf_tune)]
     L.mf_server_create.restype = C.c_int
     L.mf_server_create.argtypes = [V, C.c_int32, C.c_size_t, P(V)]
     L.mf_server_destroy.restype = None
@@ -288,6 +306,24 @@ def mf_ctx_get_stats(ctx) -> dict:
     return {name: dict(ms=s.ms[i], launches=s.launches[i], units=s.units[i], terms=s.terms[i],
                        terms_weak=s.terms_weak[i])
             for i, name in enumerate(PHASE_NAMES)}
+
+
+def mf_autotune(ctx, rbf: mf_rbf, dom: mf_domain, opts: mf_trace_opts, seeds_ptr, n_seeds,
+                stream=0) -> mf_tune:
+    t = mf_tune()
+    _check(ctx, load().mf_autotune(ctx, C.byref(rbf), C.byref(dom), C.byref(opts), seeds_ptr,
+                                   n_seeds, C.byref(t), stream))
+    return t
+
+
+def mf_ctx_set_tune(ctx, t):
+    return _check(ctx, load().mf_ctx_set_tune(ctx, C.byref(t) if t is not None else None))
+
+
+def mf_ctx_get_tune(ctx) -> mf_tune:
+    t = mf_tune()
+    _check(ctx, load().mf_ctx_get_tune(ctx, C.byref(t)))
+    return t
 
 
 def mf_certify(ctx, robot: mf_robot, scene: mf_scene, points_ptr, n_points, d, off_ptr, idx_ptr,

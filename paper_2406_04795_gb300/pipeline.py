@@ -19,7 +19,9 @@ SIZING = {
     3: dict(max_edges=1 << 20, max_vertices=1 << 20, max_cells=1 << 22),
     4: dict(max_edges=1 << 22, max_vertices=1 << 22, max_cells=1 << 25),
     5: dict(max_edges=100_000_000, max_vertices=40_000_000, max_cells=1_000_000_000),
-    6: dict(max_edges=120_000_000, max_vertices=60_000_000, max_cells=1_600_000_000),
+    # d=6 at lambda=0.04 traces ~1.6e8 edges; its ~5e9 cells do not fit in HBM,
+    # so full-size d=6 proofs run at a coarser lambda
+    6: dict(max_edges=170_000_000, max_vertices=70_000_000, max_cells=5_000_000_000),
 }
 
 
@@ -31,6 +33,8 @@ def sizing_for(w) -> dict:
     (lambda_ref / lambda)^(d-1) (traced sets grow as lambda^-(d-1))."""
     base = SIZING.get(w.d, SIZING[6])
     f = (LAMBDA_REF.get(w.d, 0.04) / w.lam) ** (w.d - 1)
+    if abs(f - 1.0) > 1e-9:
+        f *= 1.6  # the power law is only approximate away from the reference lambda
     f = min(max(f, 1e-3), 4.0)
     return {k: int(max(v * f, 1 << 16)) for k, v in base.items()}
 
@@ -59,10 +63,20 @@ class Proof:
 
     def step(self, stream=None):
         w = self.w
-        r = self.ctx.trace(self.sv, self.alpha, w.gamma, w.b, w.lam, w.offset, w.lo, w.hi,
-                           self.seeds, precision=self.precision, roots=True, cells=True,
-                           batch_cap=w.batch_cap, recheck_band=w.recheck_band,
-                           outputs=self.outputs, stream=stream, **self.sizing)
+        for attempt in range(6):
+            try:
+                r = self.ctx.trace(self.sv, self.alpha, w.gamma, w.b, w.lam, w.offset, w.lo, w.hi,
+                                   self.seeds, precision=self.precision, roots=True, cells=True,
+                                   batch_cap=w.batch_cap, recheck_band=w.recheck_band,
+                                   outputs=self.outputs, stream=stream, **self.sizing)
+                break
+            except mf.MfError as e:
+                # capacities are estimates away from the reference lambda: grow
+                # them (on the first, untimed steps) and trace again
+                if e.code != mf.MF_ERR_MAXEDGES or attempt == 5:
+                    raise
+                self.sizing = {k: int(v * 2) for k, v in self.sizing.items()}
+                self.outputs = None
         self.outputs = r["_buffers"]
         v, m, cv = self.ctx.certify(self.dh, self.radius, self.otype, self.opose, self.odims,
                                     r["points"], r["cell_off"], r["cell_idx"], stream=stream)

@@ -189,3 +189,46 @@ def test_tensor_core_eval_matches_fp64(ctx, d, lam):
     assert np.max(np.abs(a["edge_f"][ia] - b["edge_f"])) <= 1e-3
     assert set(P.cell_keys(a["cell_y"], a["cell_perm"])) == set(P.cell_keys(b["cell_y"], b["cell_perm"]))
     assert 0 < b["n_recheck"] < b["n_vertices"]
+
+
+@pytest.mark.parametrize("precision", [mf.MF_FP64, mf.MF_MIXED_BF16])
+def test_autotune_choices_leave_results_unchanged(ctx, precision):
+    """mf_autotune picks launch variants from its candidate sets, and traces
+    under the tuned context equal those under the defaults element by
+    element (sets, roots and cells do not depend on launch shapes)."""
+    w = W.config_d5(lam=0.3)
+    try:
+        mf.mf_ctx_set_tune(ctx.h, None)
+        base = P.gpu_trace(ctx, w, precision)
+        t = ctx.autotune(w, precision=precision)
+        assert t["roots_variant"] in (0, 1) and t["roots_blocks_per_sm"] in (2, 4, 8)
+        assert t["eval_blocks_per_sm"] in (4, 8, 16) and t["tc_chunk"] in (64, 128)
+        assert t["frontier_chunk"] in (0, 1 << 20, 1 << 18) and t["n_candidates"] >= 8
+        assert t["ms_bfs"] > 0 and t["ms_roots"] > 0
+        got = mf.mf_ctx_get_tune(ctx.h).as_dict()
+        for k in ("roots_variant", "roots_blocks_per_sm", "eval_blocks_per_sm", "tc_chunk",
+                  "frontier_chunk"):
+            assert got[k] == t[k]
+        tuned = P.gpu_trace(ctx, w, precision)
+    finally:
+        mf.mf_ctx_set_tune(ctx.h, None)
+    ka = {k: i for i, k in enumerate(P.keys(base["edge_y"], base["edge_mask"]))}
+    kb = P.keys(tuned["edge_y"], tuned["edge_mask"])
+    assert set(kb) == set(ka)
+    ia = np.array([ka[k] for k in kb])
+    if precision == mf.MF_FP64:  # per-edge FP64 arithmetic: bit-identical
+        assert np.array_equal(base["edge_t"][ia], tuned["edge_t"])
+        assert np.array_equal(base["points"][ia], tuned["points"])
+    else:  # FP32 end values depend on the tile a vertex falls in
+        assert np.max(np.abs(base["edge_t"][ia] - tuned["edge_t"])) <= 1e-9
+    assert set(P.cell_keys(base["cell_y"], base["cell_perm"])) == \
+        set(P.cell_keys(tuned["cell_y"], tuned["cell_perm"]))
+
+
+def test_set_tune_rejects_out_of_range(ctx):
+    t = mf.mf_tune()
+    t.roots_variant, t.roots_blocks_per_sm, t.eval_blocks_per_sm = 0, 4, 8
+    t.tc_chunk = 96  # not a supported chunk width
+    with pytest.raises(mf.MfError):
+        mf.mf_ctx_set_tune(ctx.h, t)
+    mf.mf_ctx_set_tune(ctx.h, None)
