@@ -182,7 +182,7 @@ def cpu_baseline(w, budget_s=15.0):
     return {"value": rate, "unit": "simplices/s", "cores": 1, "kind": "oracle", "sample": sample}
 
 
-def run_served(ctx, n_requests, rate_hz, max_slots=48, hbm_bytes=120 << 30, seed=1005):
+def run_served(ctx, n_requests, rate_hz, max_slots=64, hbm_bytes=200 << 30, seed=1005):
     """Poisson stream of proof requests through the continuous-batching
     server: p50 / p99 latency (arrival -> results fetched) and simplices/s."""
     import torch
@@ -388,6 +388,12 @@ def run_gb300(args):
                                        "edges_per_proof": rm["n_edges"],
                                        "rechecked_vertices": rm["n_recheck"]}
             del pm
+            # the server gets a context of its own: the proofs' resident tables
+            # are released first, so that its arena can hold many requests
+            del proof
+            ctx.close()
+            torch.cuda.empty_cache()
+            ctx = Context(local, 0)
             line["served"] = run_served(ctx, args.served_requests, args.served_rate)
         print(json.dumps(line))
     ctx.close()

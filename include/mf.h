@@ -207,8 +207,9 @@ int mf_trace_batch(mf_ctx *ctx, int32_t n, const mf_rbf *rbfs, const mf_domain *
  * arena of hbm_bytes (one server per context).  Requests queue FIFO; each
  * mf_server_step admits queued requests while a slot is free and the
  * request's buffers (sized from its opts capacities, defaults 2^20 edges) fit
- * the arena, runs one breadth-first step of every running trace (a CUDA
- * graph captured at creation), and finishes traces whose search ended
+ * the arena, runs up to MF_SERVER_STEPS breadth-first steps of every running
+ * trace in one launch of a CUDA graph built at creation (a conditional loop
+ * whose body is one step of every slot), and finishes traces whose search ended
  * (roots, cells, CSR over just those slots).  A trace gives its slot back
  * when it finishes or fails; its results stay in the arena until fetched, so
  * a caller that never fetches eventually blocks admission by memory.  The
@@ -216,6 +217,7 @@ int mf_trace_batch(mf_ctx *ctx, int32_t n, const mf_rbf *rbfs, const mf_domain *
  * until the request is done, and passes the same stream to every step and
  * fetch of one server (memory handed back is reused in stream order). */
 typedef struct mf_server mf_server;
+#define MF_SERVER_STEPS 16 /* breadth-first steps per mf_server_step (fewer when all finish) */
 int mf_server_create(mf_ctx *ctx, int32_t max_slots, size_t hbm_bytes, mf_server **out);
 void mf_server_destroy(mf_server *s);
 /* Queues a request; *id receives its handle. */
@@ -302,7 +304,8 @@ int mf_ctx_get_stats(mf_ctx *ctx, mf_stats *out);
 /* Autotuning (batched multi-trace and single traces; no counterpart in the
  * paper, which runs fixed launch shapes).  mf_autotune traces the request
  * once per BFS-chunk candidate (roots and cells off), then times on that
- * trace the launch variants of the root solve (register cap x grid), of the
+ * trace the launch variants of the root solve (register cap x grid x group
+ * screen size), of the
  * FP64 vertex evaluation (grid) and, for MF_MIXED_BF16, of the tensor-core
  * chunk width (64 or 128 support vectors per MMA).  The fastest of each is
  * kept in the context and used by every later mf_trace on it; *out (host)
@@ -318,7 +321,7 @@ typedef struct {
   double ms_roots;             /* measured: root solve of the sampled edges */
   double ms_eval;              /* measured: evaluation of every traced vertex */
   int32_t n_candidates;        /* launch variants timed */
-  int32_t pad;
+  int32_t roots_group;         /* consecutive edges sharing one group screen (1: none) */
 } mf_tune;
 int mf_autotune(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom, const mf_trace_opts *opts,
                 const double *seeds, int64_t n_seeds, mf_tune *out, void *stream);

@@ -47,14 +47,14 @@ void launch_step(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, int n, bo
   mf_b_launch_update(slots, st, P, n, h, use_handle, s);
 }
 
-// Runs the BFS of all slots as one graph launch with a conditional WHILE
-// node.  Returns false if the graph could not be built (caller falls back).
-bool run_graph(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, int n, bool any_mixed,
-               int sms, cudaStream_t s) {
+// Builds the search loop: a graph whose conditional WHILE node has one step of
+// every slot as its body (k_b_update clears the condition when no slot is
+// active or the plan's step budget is used up).  nullptr if unavailable.
+cudaGraphExec_t build_loop(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, int n,
+                           bool any_mixed, int sms) {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cs = nullptr;
-  bool ok = false;
   do {
     if (cudaGraphCreate(&g, 0) != cudaSuccess) break;
     cudaGraphConditionalHandle h;
@@ -77,14 +77,23 @@ bool run_graph(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, int n, bool
     launch_step(slots, st, P, n, any_mixed, sms, h, 1, cs);
     cudaGraph_t captured = nullptr;
     if (cudaStreamEndCapture(cs, &captured) != cudaSuccess) break;
-    if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) break;
-    if (cudaGraphLaunch(exec, s) != cudaSuccess) break;
-    ok = cudaStreamSynchronize(s) == cudaSuccess;
+    if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
   } while (false);
-  if (!ok) cudaGetLastError();
-  if (exec) cudaGraphExecDestroy(exec);
+  if (!exec) cudaGetLastError();
   if (g) cudaGraphDestroy(g);
   if (cs) cudaStreamDestroy(cs);
+  return exec;
+}
+
+// Runs the BFS of all slots as one launch of the search loop.  Returns false
+// if the graph could not be built (the caller falls back to host steps).
+bool run_graph(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, int n, bool any_mixed,
+               int sms, cudaStream_t s) {
+  cudaGraphExec_t exec = build_loop(slots, st, P, n, any_mixed, sms);
+  if (!exec) return false;
+  bool ok = cudaGraphLaunch(exec, s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) cudaGetLastError();
+  cudaGraphExecDestroy(exec);
   return ok;
 }
 
@@ -510,16 +519,9 @@ extern "C" int mf_server_create(mf_ctx *ctx, int32_t max_slots, size_t hbm_bytes
   s->hstate.assign(max_slots, MfSlotState());
   cudaMemset(s->d_slots, 0, sizeof(MfSlot) * max_slots);
   cudaMemset(s->d_state, 0, sizeof(MfSlotState) * max_slots);
-  // capture one step of every slot as a graph (replayed by each mf_server_step)
-  cudaGraph_t g = nullptr;
-  if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
-      cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-    launch_step(s->d_slots, s->d_state, s->d_plan, max_slots, true, ctx->sms, 0, 0, s->cap_stream);
-    if (cudaStreamEndCapture(s->cap_stream, &g) == cudaSuccess && g) {
-      if (cudaGraphInstantiate(&s->step_exec, g, 0) != cudaSuccess) s->step_exec = nullptr;
-    }
-    if (g) cudaGraphDestroy(g);
-  }
+  // the search loop of every slot as one graph, replayed by each
+  // mf_server_step for up to MF_SERVER_STEPS breadth-first steps
+  s->step_exec = build_loop(s->d_slots, s->d_state, s->d_plan, max_slots, true, ctx->sms);
   cudaGetLastError();
   if (cudaDeviceSynchronize() != cudaSuccess) {
     mf_server_destroy(s);
@@ -650,8 +652,10 @@ extern "C" int mf_server_step(mf_server *s, void *stream, int32_t *n_running, in
   for (int t = 0; t < n; t++)
     if (s->slot_req[t] >= 0 && s->reqs[s->slot_req[t]].state == 1) running = true;
   if (running) {
-    // host-driven steps: the device step bound applies per batch, not per server
+    // the step count restarts per call; the loop pauses after the budget
+    static const int32_t budget = MF_SERVER_STEPS;
     cudaMemsetAsync(&s->d_plan->steps, 0, sizeof(unsigned long long), st);
+    cudaMemcpyAsync(&s->d_plan->budget, &budget, sizeof(budget), cudaMemcpyHostToDevice, st);
     if (s->step_exec) {
       if ((rc = mf_cuda_check(ctx, cudaGraphLaunch(s->step_exec, st), "server step"))) return rc;
     } else {

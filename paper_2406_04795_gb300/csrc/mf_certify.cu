@@ -37,33 +37,48 @@ __device__ __forceinline__ T box_F(const T *a, const T *dl, const T *h, T t) {
   return s;
 }
 
-// Squared distance from segment [a, a+dl] (box frame) to the box |p_i| <= h_i.
+template <typename T>
+__device__ __forceinline__ void cswap(T &x, T &y) {
+  const T lo = fmin(x, y), hi = fmax(x, y);
+  x = lo;
+  y = hi;
+}
+
+// Squared distance from segment [a, a+dl] (box frame) to the box |p_i| <= h_i:
+// the convex piecewise quadratic sum_i max(0, |a_i + t dl_i| - h_i)^2 over
+// t in [0, 1] (App. A), minimised on each piece between consecutive
+// breakpoints.  The breakpoints (0, 1 and the crossings of +-h_i, unused
+// slots = 2) are sorted by a fixed 19-comparator network, so every array
+// index is known at compile time.
 template <typename T>
 __device__ T seg_box_d2(const T *a, const T *dl, const T *h) {
   T bp[8];
-  int nb = 0;
-  bp[nb++] = 0;
-  bp[nb++] = 1;
+  bp[0] = 0;
+  bp[1] = 1;
 #pragma unroll
   for (int i = 0; i < 3; i++) {
+    T t1 = 2, t2 = 2;
     if (dl[i] != (T)0) {
-      const T t1 = (h[i] - a[i]) / dl[i], t2 = (-h[i] - a[i]) / dl[i];
-      if (t1 > (T)0 && t1 < (T)1) bp[nb++] = t1;
-      if (t2 > (T)0 && t2 < (T)1) bp[nb++] = t2;
+      t1 = (h[i] - a[i]) / dl[i];
+      t2 = (-h[i] - a[i]) / dl[i];
+      if (!(t1 > (T)0 && t1 < (T)1)) t1 = 2;
+      if (!(t2 > (T)0 && t2 < (T)1)) t2 = 2;
     }
+    bp[2 + 2 * i] = t1;
+    bp[3 + 2 * i] = t2;
   }
-  // insertion sort (<= 8 entries)
-  for (int i = 1; i < nb; i++) {
-    const T v = bp[i];
-    int j = i - 1;
-    while (j >= 0 && bp[j] > v) { bp[j + 1] = bp[j]; j--; }
-    bp[j + 1] = v;
-  }
+  cswap(bp[0], bp[2]); cswap(bp[1], bp[3]); cswap(bp[4], bp[6]); cswap(bp[5], bp[7]);
+  cswap(bp[0], bp[4]); cswap(bp[1], bp[5]); cswap(bp[2], bp[6]); cswap(bp[3], bp[7]);
+  cswap(bp[0], bp[1]); cswap(bp[2], bp[3]); cswap(bp[4], bp[5]); cswap(bp[6], bp[7]);
+  cswap(bp[2], bp[4]); cswap(bp[3], bp[5]);
+  cswap(bp[1], bp[4]); cswap(bp[3], bp[6]);
+  cswap(bp[1], bp[2]); cswap(bp[3], bp[4]); cswap(bp[5], bp[6]);
   T best = box_F<T>(a, dl, h, (T)0);
   best = fmin(best, box_F<T>(a, dl, h, (T)1));
-  for (int k = 0; k + 1 < nb; k++) {
+#pragma unroll
+  for (int k = 0; k < 7; k++) {
     const T ta = bp[k], tb = bp[k + 1];
-    if (!(tb > ta)) continue;
+    if (!(tb > ta) || tb > (T)1) continue;
     const T tm = (T)0.5 * (ta + tb);
     T A = 0, Bc = 0;
 #pragma unroll
@@ -110,11 +125,14 @@ __device__ T seg_obstacle_dist(const CertObsT<T> &o, const T *pa, const T *pb) {
   return dist > (T)0 ? dist : (T)0;
 }
 
-__global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int nl, const double *dh, const double *radius, int nobs,
-                                                    const int32_t *type, const double *pose,
-                                                    const double *dims, const double *pts,
-                                                    int64_t n, int d, uint8_t *verdict,
-                                                    double *margin) {
+// NL = number of links (compile time, so that the frame origins stay in
+// registers).
+template <int NL>
+__global__ void __launch_bounds__(CERT_THREADS) k_certify_points(const double *dh, const double *radius,
+                                                                 int nobs, const int32_t *type,
+                                                                 const double *pose, const double *dims,
+                                                                 const double *pts, int64_t n, int d,
+                                                                 uint8_t *verdict, double *margin) {
   __shared__ CertObs so[CERT_MAX_OBS];
   __shared__ CertObsT<float> sof[CERT_MAX_OBS];  // FP32 copy for the lower bounds
   __shared__ double sdh[MF_MAXD * 4], srad[MF_MAXD], ssa[MF_MAXD], sca[MF_MAXD];
@@ -129,8 +147,8 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int nl, const d
     so[i] = o;
     sof[i] = of;
   }
-  for (int i = threadIdx.x; i < nl * 4; i += blockDim.x) sdh[i] = dh[i];
-  for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+  for (int i = threadIdx.x; i < NL * 4; i += blockDim.x) sdh[i] = dh[i];
+  for (int i = threadIdx.x; i < NL; i += blockDim.x) {
     srad[i] = radius[i];
     sincos(dh[4 * i + 3], &ssa[i], &sca[i]);
   }
@@ -140,9 +158,10 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int nl, const d
   // forward kinematics: T = T * A_i with the standard DH link transform; keep
   // every frame origin (link i runs from origin i to origin i+1)
   double T[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};  // 3x4 row-major
-  double org[3 * (MF_MAXD + 1)];
+  double org[3 * (NL + 1)];
   org[0] = org[1] = org[2] = 0.0;
-  for (int i = 0; i < nl; i++) {
+#pragma unroll
+  for (int i = 0; i < NL; i++) {
     const double th = pts[p * d + i] + sdh[4 * i], dd = sdh[4 * i + 1], aa = sdh[4 * i + 2];
     double st, ct;
     sincos(th, &st, &ct);
@@ -168,36 +187,50 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int nl, const d
   // margin = max over (link, obstacle) of radius - distance.  Every pair first
   // gets the same distance computed in FP32; minus a slack of 1e-4 (1 + the
   // largest coordinate), far above the FP32 rounding of the computation
-  // (about 1e-6 of that scale), it is a lower bound lb on the true distance.
-  // A pair with radius - lb <= the best exact margin so far cannot change the
-  // maximum and is skipped; the pair with the largest radius - lb is
-  // evaluated first, so typically only it is evaluated in FP64.
-  float org32[3 * (MF_MAXD + 1)];
-  for (int k = 0; k < 3 * (nl + 1); k++) org32[k] = (float)org[k];
-  auto lower_bound = [&](int i, int k) -> float {
+  // (about 1e-6 of that scale), it is a lower bound lb on the true distance,
+  // and radius - lb an upper bound ub on the pair's margin.  The pair with the
+  // largest ub is evaluated in FP64; the others only if the second-largest ub
+  // exceeds that exact margin, and then only those whose ub does.
+  float org32[3 * (NL + 1)];
+#pragma unroll
+  for (int k = 0; k < 3 * (NL + 1); k++) org32[k] = (float)org[k];
+  auto upper = [&](int i, int k) -> float {
     const float *a = &org32[3 * i], *b = &org32[3 * i + 3];
     const float dist = seg_obstacle_dist<float>(sof[k], a, b);
     float scale = 1.f;
 #pragma unroll
     for (int c = 0; c < 3; c++)
       scale = fmaxf(scale, fmaxf(fmaxf(fabsf(a[c]), fabsf(b[c])), fabsf(sof[k].t[c]) + sof[k].h[c]));
-    return dist - 1e-4f * (1.f + scale);
+    return (float)srad[i] - (dist - 1e-4f * (1.f + scale));
   };
-  double best = -INFINITY;
+  float ub1 = -INFINITY, ub2 = -INFINITY;
   int bi = -1, bk = -1;
-  float bub = -INFINITY;
-  for (int i = 0; i < nl; i++)
+#pragma unroll
+  for (int i = 0; i < NL; i++)
     for (int k = 0; k < nobs; k++) {
-      const float ub = (float)srad[i] - lower_bound(i, k);
-      if (ub > bub) { bub = ub; bi = i; bk = k; }
+      const float ub = upper(i, k);
+      if (ub > ub1) {
+        ub2 = ub1;
+        ub1 = ub;
+        bi = i;
+        bk = k;
+      } else if (ub > ub2) {
+        ub2 = ub;
+      }
     }
-  if (bi >= 0) best = srad[bi] - seg_obstacle_dist(so[bk], &org[3 * bi], &org[3 * bi + 3]);
-  for (int i = 0; i < nl; i++)
-    for (int k = 0; k < nobs; k++) {
-      if (i == bi && k == bk) continue;
-      if ((double)((float)srad[i] - lower_bound(i, k)) <= best) continue;
-      best = fmax(best, srad[i] - seg_obstacle_dist(so[k], &org[3 * i], &org[3 * i + 3]));
-    }
+  double best = -INFINITY;
+#pragma unroll
+  for (int i = 0; i < NL; i++)
+    if (i == bi) best = srad[i] - seg_obstacle_dist(so[bk], &org[3 * i], &org[3 * i + 3]);
+  if ((double)ub2 > best) {
+#pragma unroll
+    for (int i = 0; i < NL; i++)
+      for (int k = 0; k < nobs; k++) {
+        if (i == bi && k == bk) continue;
+        if ((double)upper(i, k) <= best) continue;
+        best = fmax(best, srad[i] - seg_obstacle_dist(so[k], &org[3 * i], &org[3 * i + 3]));
+      }
+  }
   margin[p] = best;
   verdict[p] = best >= 0.0 ? 1 : 0;
 }
@@ -235,9 +268,18 @@ extern "C" int mf_certify(mf_ctx *ctx, const mf_robot *robot, const mf_scene *sc
   cudaMemsetAsync(bad, 0, sizeof(unsigned), st);
   if (n_points > 0) {
     MfProfScope ps(ctx, MF_PH_CERT_PTS, st, 1, n_points);
-    k_certify_points<<<(unsigned)((n_points + CERT_THREADS - 1) / CERT_THREADS), CERT_THREADS, 0,
-                       st>>>(robot->n_links, robot->dh, robot->radius, scene->n, scene->type,
-                             scene->pose, scene->dims, points, n_points, d, point_verdict, margin);
+    const unsigned g = (unsigned)((n_points + CERT_THREADS - 1) / CERT_THREADS);
+    switch (robot->n_links) {
+#define MF_CASE(NL)                                                                            \
+  case NL:                                                                                     \
+    k_certify_points<NL><<<g, CERT_THREADS, 0, st>>>(robot->dh, robot->radius, scene->n,       \
+                                                     scene->type, scene->pose, scene->dims,    \
+                                                     points, n_points, d, point_verdict, margin); \
+    break;
+      MF_CASE(1) MF_CASE(2) MF_CASE(3) MF_CASE(4) MF_CASE(5) MF_CASE(6) MF_CASE(7) MF_CASE(8)
+#undef MF_CASE
+      default: break;
+    }
   }
   if (n_cells > 0) {
     MfProfScope ps(ctx, MF_PH_CERT_CELLS, st, 1, n_cells);

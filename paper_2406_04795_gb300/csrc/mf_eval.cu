@@ -672,13 +672,15 @@ __device__ __forceinline__ F64Acc root_eval64(const MfRbfDev &R, const int *near
 }
 
 // Solves the root of edge e (all lanes of the warp); near: NEAR_CAP ints,
-// qs / qw: 64-entry queues, all in this warp's shared memory.  FP64 work that
-// is the same for every lane (coordinates, their splits) runs once per axis:
-// lane k < d computes axis k and shuffles broadcast it.
+// qs / qw: 64-entry queues, all in this warp's shared memory.  src (srcn
+// entries, ascending) lists the support vectors that can pass the segment
+// screen (a group screen's survivors); NULL screens all of them.  FP64 work
+// that is the same for every lane (coordinates, their splits) runs once per
+// axis: lane k < d computes axis k and shuffles broadcast it.
 template <int D>
 __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, uint64_t e,
-                          double tol, int *near, int *qs, int *qw, unsigned long long &evals,
-                          unsigned long long *terms) {
+                          double tol, const int *src, int srcn, int *near, int *qs, int *qw,
+                          unsigned long long &evals, unsigned long long *terms) {
   const int lane = threadIdx.x & 31;
   const int d = dim_of<D>(F.d);
   const unsigned lt = (1u << lane) - 1u;
@@ -716,16 +718,29 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
   }
   // 1. segment screen
   int ns = 0, nw = 0;
-  for (int base = 0; base < R.n; base += 32) {
-    const int j = base + lane;
+  const int total = src ? srcn : R.n;
+  for (int base = 0; base < total; base += 32) {
+    const int i = base + lane;
     bool keep = false, strong = false;
-    if (j < R.n) {
+    int j = 0;
+    if (i < total) {
       float p[D], pd = 0.f;
+      if (src) {
+        j = src[i];
+        const float4 *row = reinterpret_cast<const float4 *>(R.svhl + (int64_t)j * 16);
 #pragma unroll
-      for (int k = 0; k < D; k++) {
-        p[k] = k < d ? (R.sv32[(int64_t)k * R.n + j] - x1hi[k]) : 0.f;
-        pd = fmaf(p[k], dir32[k], pd);
+        for (int k2 = 0; k2 < (D + 1) / 2; k2++) {
+          const float4 v = __ldg(row + k2);
+          p[2 * k2] = 2 * k2 < d ? v.x - x1hi[2 * k2] : 0.f;
+          if (2 * k2 + 1 < D) p[2 * k2 + 1] = 2 * k2 + 1 < d ? v.z - x1hi[2 * k2 + 1] : 0.f;
+        }
+      } else {
+        j = i;
+#pragma unroll
+        for (int k = 0; k < D; k++) p[k] = k < d ? (R.sv32[(int64_t)k * R.n + j] - x1hi[k]) : 0.f;
       }
+#pragma unroll
+      for (int k = 0; k < D; k++) pd = fmaf(p[k], dir32[k], pd);
       const float tt = fminf(fmaxf(pd / dd32, 0.f), 1.f);
       float r2 = 0.f;
 #pragma unroll
@@ -814,16 +829,105 @@ __device__ __forceinline__ void root_flush(const MfTraceBufs &B, unsigned long l
   }
 }
 
+#define GROUP_CAP 1024
+
+// Group screen of edges [e0, e0 + ng) (consecutive edges of the BFS list lie
+// close together): c = mean of their 2 ng endpoints, Rg = largest endpoint
+// distance from c.  A support vector within r_s of a point of any of these
+// segments lies within r_s + Rg of c (the ball holds the segments), so the
+// list of those (ascending, margin 1e-4 relative + 1e-5 over the FP32
+// rounding) contains every vector the per-edge segment screen keeps, which
+// then sees the same candidates in the same order.  Returns the count, or -1
+// if more than GROUP_CAP pass (the edges then screen all vectors).
+template <int D>
+__device__ int group_screen(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, uint64_t e0,
+                            int ng, float rs, int *glist) {
+  const int lane = threadIdx.x & 31;
+  const int d = dim_of<D>(F.d);
+  const unsigned lt = (1u << lane) - 1u;
+  const bool have = lane < ng;
+  float a[D], b[D];
+  {
+    int32_t y[MF_MAXD];
+    double xa[MF_MAXD], xb[MF_MAXD];
+#pragma unroll
+    for (int k = 0; k < MF_MAXD; k++) y[k] = (have && k < d) ? B.edge_y[(e0 + lane) * d + k] : 0;
+    mf_vertex_x(F, y, xa);
+    mf_add_mask(d, y, have ? B.edge_mask[e0 + lane] : 0u, 1);
+    mf_vertex_x(F, y, xb);
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+      a[k] = (float)xa[k];
+      b[k] = (float)xb[k];
+    }
+  }
+  float c[D];
+#pragma unroll
+  for (int k = 0; k < D; k++) c[k] = mf_warp_sum_f(have ? a[k] + b[k] : 0.f) / (float)(2 * ng);
+  float r2 = 0.f;
+  if (have) {
+    float da = 0.f, db = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+      if (k < d) {
+        da = fmaf(a[k] - c[k], a[k] - c[k], da);
+        db = fmaf(b[k] - c[k], b[k] - c[k], db);
+      }
+    }
+    r2 = fmaxf(da, db);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(FULL, r2, o));
+  const float lim = (rs + sqrtf(r2)) * 1.0001f + 1e-5f, lim2 = lim * lim;
+  int gn = 0;
+  for (int base = 0; base < R.n; base += 32) {
+    const int j = base + lane;
+    bool keep = false;
+    if (j < R.n) {
+      float s2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; k++) {
+        if (k < d) {
+          const float t = R.sv32[(int64_t)k * R.n + j] - c[k];
+          s2 = fmaf(t, t, s2);
+        }
+      }
+      keep = s2 <= lim2;
+    }
+    const unsigned m = __ballot_sync(FULL, keep);
+    const int pos = gn + __popc(m & lt);
+    if (keep && pos < GROUP_CAP) glist[pos] = j;
+    gn += __popc(m);
+  }
+  __syncwarp();
+  return gn <= GROUP_CAP ? gn : -1;
+}
+
 template <int D, int MINB>
 __global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(MfFrame F, MfRbfDev R, MfTraceBufs B,
-                                                               uint64_t n_edges, double tol) {
+                                                               uint64_t n_edges, double tol,
+                                                               int group) {
   __shared__ int snear[ROOT_WARPS][NEAR_CAP];
   __shared__ int sq[ROOT_WARPS][2][64];
+  extern __shared__ int sgrp_all[];  // [ROOT_WARPS][GROUP_CAP] when group > 1
   const int w = threadIdx.x >> 5;
+  int *sgrp = sgrp_all + w * GROUP_CAP;
   const uint64_t nwarps = (uint64_t)gridDim.x * ROOT_WARPS;
+  const float rs = sqrtf(R.screen_r2);
   unsigned long long evals = 0, terms[2] = {0, 0};
-  for (uint64_t e = (uint64_t)blockIdx.x * ROOT_WARPS + w; e < n_edges; e += nwarps)
-    root_edge<D>(F, R, B, e, tol, snear[w], sq[w][0], sq[w][1], evals, terms);
+  if (group <= 1) {
+    for (uint64_t e = (uint64_t)blockIdx.x * ROOT_WARPS + w; e < n_edges; e += nwarps)
+      root_edge<D>(F, R, B, e, tol, nullptr, 0, snear[w], sq[w][0], sq[w][1], evals, terms);
+  } else {
+    const uint64_t G = (uint64_t)group;
+    for (uint64_t g0 = ((uint64_t)blockIdx.x * ROOT_WARPS + w) * G; g0 < n_edges; g0 += nwarps * G) {
+      const int ng = (int)(n_edges - g0 < G ? n_edges - g0 : G);
+      const int gn = group_screen<D>(F, R, B, g0, ng, rs, sgrp);
+      for (int q = 0; q < ng; q++)
+        root_edge<D>(F, R, B, g0 + q, tol, gn >= 0 ? sgrp : nullptr, gn, snear[w], sq[w][0],
+                     sq[w][1], evals, terms);
+    }
+  }
   root_flush(B, evals, terms);
 }
 
@@ -933,7 +1037,8 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32) k_b_roots(const MfSlot *slots
     const int t = mf_slot_of(P->pe, n, item);
     const MfSlot &S = slots[t];
     unsigned long long evals = 0, terms[2] = {0, 0};
-    root_edge<MF_MAXD>(S.F, S.R, S.B, item - P->pe[t], S.root_tol, snear[w], sq[w][0], sq[w][1], evals,
+    root_edge<MF_MAXD>(S.F, S.R, S.B, item - P->pe[t], S.root_tol, nullptr, 0, snear[w], sq[w][0],
+                       sq[w][1], evals,
               terms);
     root_flush(S.B, evals, terms);
   }
@@ -989,15 +1094,23 @@ void mf_launch_eval_vertices_mixed(const MfFrame &F, const MfRbfDev &R, const Mf
   k_advance_eval<<<1, 1, 0, st>>>(B.cnt);
 }
 
+template <int DD, int MINB>
+static void launch_roots_d(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
+                           uint64_t n_edges, double tol, int grid, int group, cudaStream_t st) {
+  const int dyn = group > 1 ? ROOT_WARPS * GROUP_CAP * (int)sizeof(int) : 0;
+  if (dyn) cudaFuncSetAttribute(k_roots_f64<DD, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  k_roots_f64<DD, MINB><<<grid, ROOT_WARPS * 32, dyn, st>>>(F, R, B, n_edges, tol, group);
+}
+
 template <int MINB>
 static void launch_roots(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, uint64_t n_edges,
-                         double tol, int grid, cudaStream_t st) {
+                         double tol, int grid, int group, cudaStream_t st) {
   switch (F.d) {
 #define MF_CASE(DD) \
-  case DD: k_roots_f64<DD, MINB><<<grid, ROOT_WARPS * 32, 0, st>>>(F, R, B, n_edges, tol); break;
+  case DD: launch_roots_d<DD, MINB>(F, R, B, n_edges, tol, grid, group, st); break;
     MF_CASE(2) MF_CASE(3) MF_CASE(4) MF_CASE(5) MF_CASE(6) MF_CASE(7)
 #undef MF_CASE
-    default: k_roots_f64<MF_MAXD, MINB><<<grid, ROOT_WARPS * 32, 0, st>>>(F, R, B, n_edges, tol);
+    default: launch_roots_d<MF_MAXD, MINB>(F, R, B, n_edges, tol, grid, group, st);
   }
 }
 
@@ -1005,8 +1118,8 @@ void mf_launch_roots_f64(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs 
                          double tol, const MfTune &T, int sms, cudaStream_t st) {
   if (n_edges == 0) return;
   const int grid = sms * T.roots_bps;
-  if (T.roots_variant == 1) launch_roots<3>(F, R, B, n_edges, tol, grid, st);
-  else launch_roots<2>(F, R, B, n_edges, tol, grid, st);
+  if (T.roots_variant == 1) launch_roots<3>(F, R, B, n_edges, tol, grid, T.roots_group, st);
+  else launch_roots<2>(F, R, B, n_edges, tol, grid, T.roots_group, st);
 }
 
 extern "C" int mf_eval(mf_ctx *ctx, const mf_rbf *rbf, const double *q, int64_t n, int32_t precision,

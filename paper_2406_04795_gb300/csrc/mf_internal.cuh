@@ -166,6 +166,7 @@ struct MfBatchPlan {  // per-step work prefixes over the slots
   unsigned long long v0[MF_MAX_SLOTS], r0[MF_MAX_SLOTS];
   unsigned long long steps;  // steps run since the plan was cleared
   int32_t overrun;           // the step limit stopped the search
+  int32_t budget;            // > 0: the graph loop pauses after this many steps
 };
 #define MF_MAX_STEPS (1ull << 22)  // bound on breadth-first steps of one batch
 
@@ -362,6 +363,7 @@ void mf_launch_seeds(const MfFrame &F, const MfTraceBufs &B, const double *seeds
 struct MfTune {
   int roots_variant = 0;         // 0: no register cap (2 blocks/SM), 1: 3 blocks/SM
   int roots_bps = 4;             // root-solve blocks per SM in the grid
+  int roots_group = 8;           // consecutive edges sharing one group screen (1 = none)
   int eval_bps = 8;              // FP64 vertex-evaluation blocks per SM
   int tc_chunk = 64;             // support vectors per tensor-core MMA: 64 or 128
   uint64_t frontier_chunk = 0;   // BFS chunk in edges; 0 = the caller's batch cap

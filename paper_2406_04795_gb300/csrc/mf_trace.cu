@@ -540,13 +540,16 @@ __global__ void k_b_advance(const MfSlot *slots, int n) {
 // keeps the enclosing graph loop running.
 __global__ void k_b_update(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, int n,
                            cudaGraphConditionalHandle handle, int use_handle) {
-  __shared__ int any, stop;
+  __shared__ int any, stop, pause;
   if (threadIdx.x == 0) {
     any = 0;
     // a hard bound on the number of steps: the loop ends even if a slot
     // never finished (reported as an overrun error)
-    stop = ++P->steps > MF_MAX_STEPS;
+    const unsigned long long s = ++P->steps;
+    stop = s > MF_MAX_STEPS;
     if (stop) P->overrun = 1;
+    // a step budget ends this launch of the loop; active slots stay active
+    pause = P->budget > 0 && s >= (unsigned long long)P->budget;
   }
   __syncthreads();
   const int t = threadIdx.x;
@@ -574,7 +577,7 @@ __global__ void k_b_update(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P,
     if (s.active) atomicOr(&any, 1);
   }
   __syncthreads();
-  if (threadIdx.x == 0 && use_handle) cudaGraphSetConditional(handle, any ? 1u : 0u);
+  if (threadIdx.x == 0 && use_handle) cudaGraphSetConditional(handle, (any && !pause) ? 1u : 0u);
 }
 
 // Traced-edge and cell prefixes.  mode 0: edges of slots that want roots;

@@ -4,7 +4,7 @@
 // Candidates:
 //   BFS chunk (edges per expansion step): the batch cap, 2^20, 2^18;
 //   root solve: register cap (2 or 3 blocks per SM) x grid (2, 4, 8 blocks
-//     per SM), on the first 2^20 traced edges;
+//     per SM) x group screen (1, 8, 16 edges), on the first 2^20 traced edges;
 //   FP64 vertex evaluation: grid (4, 8, 16 blocks per SM), all vertices;
 //   tensor-core evaluation (MF_MIXED_BF16): chunk width 64 or 128.
 // Each kernel candidate is timed three times with CUDA events on the
@@ -52,6 +52,7 @@ void to_public(const MfTune &t, mf_tune *o) {
   o->eval_blocks_per_sm = t.eval_bps;
   o->tc_chunk = t.tc_chunk;
   o->frontier_chunk = (int64_t)t.frontier_chunk;
+  o->roots_group = t.roots_group;
 }
 
 }  // namespace
@@ -66,13 +67,15 @@ extern "C" int mf_ctx_set_tune(mf_ctx *ctx, const mf_tune *t) {
   if (t) {
     if ((t->roots_variant != 0 && t->roots_variant != 1) || t->roots_blocks_per_sm < 1 ||
         t->roots_blocks_per_sm > 32 || t->eval_blocks_per_sm < 1 || t->eval_blocks_per_sm > 32 ||
-        (t->tc_chunk != 64 && t->tc_chunk != 128) || t->frontier_chunk < 0)
+        (t->tc_chunk != 64 && t->tc_chunk != 128) || t->frontier_chunk < 0 ||
+        t->roots_group < 1 || t->roots_group > 32)
       return mf_set_error(ctx, MF_ERR_INVALID, "mf_ctx_set_tune: value out of range");
     n.roots_variant = t->roots_variant;
     n.roots_bps = t->roots_blocks_per_sm;
     n.eval_bps = t->eval_blocks_per_sm;
     n.tc_chunk = t->tc_chunk;
     n.frontier_chunk = (uint64_t)t->frontier_chunk;
+    n.roots_group = t->roots_group;
   }
   ctx->tune = n;
   return MF_OK;
@@ -141,23 +144,25 @@ extern "C" int mf_autotune(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
   float best_roots = 1e30f;
   if (es > 0) {
     MfTune best = ctx->tune;
-    const int bps[3] = {2, 4, 8};
+    const int bps[3] = {2, 4, 8}, groups[3] = {1, 8, 16};
     for (int v = 0; v < 2; v++)
-      for (int g = 0; g < 3; g++) {
-        MfTune t = ctx->tune;
-        t.roots_variant = v;
-        t.roots_bps = bps[g];
-        const float ms = time_ms(
-            st, [&]() { mf_launch_roots_f64(L.F, L.R, L.B, es, L.tol, t, sms, st); }, 3);
-        n_cand++;
-        if (ms < best_roots) {
-          best_roots = ms;
-          best.roots_variant = v;
-          best.roots_bps = bps[g];
+      for (int g = 0; g < 3; g++)
+        for (int q = 0; q < 3; q++) {
+          MfTune t = ctx->tune;
+          t.roots_variant = v;
+          t.roots_bps = bps[g];
+          t.roots_group = groups[q];
+          const float ms = time_ms(
+              st, [&]() { mf_launch_roots_f64(L.F, L.R, L.B, es, L.tol, t, sms, st); }, 3);
+          n_cand++;
+          if (ms < best_roots) {
+            best_roots = ms;
+            best = t;
+          }
         }
-      }
     ctx->tune.roots_variant = best.roots_variant;
     ctx->tune.roots_bps = best.roots_bps;
+    ctx->tune.roots_group = best.roots_group;
   }
 
   // 3. vertex evaluation of every traced vertex, through scratch counters

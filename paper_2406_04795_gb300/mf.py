@@ -91,10 +91,10 @@ class mf_tune(C.Structure):
     _fields_ = [("roots_variant", C.c_int32), ("roots_blocks_per_sm", C.c_int32),
                 ("eval_blocks_per_sm", C.c_int32), ("tc_chunk", C.c_int32),
                 ("frontier_chunk", C.c_int64), ("ms_bfs", C.c_double), ("ms_roots", C.c_double),
-                ("ms_eval", C.c_double), ("n_candidates", C.c_int32), ("pad", C.c_int32)]
+                ("ms_eval", C.c_double), ("n_candidates", C.c_int32), ("roots_group", C.c_int32)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad"}
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 _lib = None

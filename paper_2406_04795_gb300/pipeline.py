@@ -19,13 +19,13 @@ SIZING = {
     3: dict(max_edges=1 << 20, max_vertices=1 << 20, max_cells=1 << 22),
     4: dict(max_edges=1 << 22, max_vertices=1 << 22, max_cells=1 << 25),
     5: dict(max_edges=100_000_000, max_vertices=40_000_000, max_cells=1_000_000_000),
-    # d=6 at lambda=0.04 traces ~1.6e8 edges; its ~5e9 cells do not fit in HBM,
-    # so full-size d=6 proofs run at a coarser lambda
-    6: dict(max_edges=170_000_000, max_vertices=70_000_000, max_cells=5_000_000_000),
+    # d=6 measured at lambda=0.2: 2.56e6 edges, 3.9e5 vertices, 7.1e7 cells; at
+    # lambda=0.04 the same power law gives ~8e9 edges, beyond one GPU's HBM
+    6: dict(max_edges=4_000_000, max_vertices=1_000_000, max_cells=120_000_000),
 }
 
 
-LAMBDA_REF = {3: 0.1, 4: 0.08, 5: 0.05, 6: 0.04}
+LAMBDA_REF = {3: 0.1, 4: 0.08, 5: 0.05, 6: 0.2}
 
 
 def sizing_for(w) -> dict:
@@ -35,7 +35,7 @@ def sizing_for(w) -> dict:
     f = (LAMBDA_REF.get(w.d, 0.04) / w.lam) ** (w.d - 1)
     if abs(f - 1.0) > 1e-9:
         f *= 1.6  # the power law is only approximate away from the reference lambda
-    f = min(max(f, 1e-3), 4.0)
+    f = min(max(f, 1e-3), 64.0)
     return {k: int(max(v * f, 1 << 16)) for k, v in base.items()}
 
 

@@ -203,11 +203,12 @@ def test_autotune_choices_leave_results_unchanged(ctx, precision):
         t = ctx.autotune(w, precision=precision)
         assert t["roots_variant"] in (0, 1) and t["roots_blocks_per_sm"] in (2, 4, 8)
         assert t["eval_blocks_per_sm"] in (4, 8, 16) and t["tc_chunk"] in (64, 128)
-        assert t["frontier_chunk"] in (0, 1 << 20, 1 << 18) and t["n_candidates"] >= 8
+        assert t["frontier_chunk"] in (0, 1 << 20, 1 << 18) and t["n_candidates"] >= 20
+        assert t["roots_group"] in (1, 8, 16)
         assert t["ms_bfs"] > 0 and t["ms_roots"] > 0
         got = mf.mf_ctx_get_tune(ctx.h).as_dict()
         for k in ("roots_variant", "roots_blocks_per_sm", "eval_blocks_per_sm", "tc_chunk",
-                  "frontier_chunk"):
+                  "frontier_chunk", "roots_group"):
             assert got[k] == t[k]
         tuned = P.gpu_trace(ctx, w, precision)
     finally:
@@ -227,8 +228,45 @@ def test_autotune_choices_leave_results_unchanged(ctx, precision):
 
 def test_set_tune_rejects_out_of_range(ctx):
     t = mf.mf_tune()
-    t.roots_variant, t.roots_blocks_per_sm, t.eval_blocks_per_sm = 0, 4, 8
+    t.roots_variant, t.roots_blocks_per_sm, t.eval_blocks_per_sm, t.roots_group = 0, 4, 8, 8
     t.tc_chunk = 96  # not a supported chunk width
     with pytest.raises(mf.MfError):
         mf.mf_ctx_set_tune(ctx.h, t)
     mf.mf_ctx_set_tune(ctx.h, None)
+
+
+def test_group_screen_roots_bit_identical(ctx):
+    """Edges sharing a group screen see the same candidates, in the same
+    order, as a full per-edge screen: roots and points are bit-identical."""
+    w = W.config_d5(lam=0.3)
+    out = {}
+    try:
+        for g in (1, 16):
+            t = mf.mf_ctx_get_tune(ctx.h)
+            t.roots_group = g
+            mf.mf_ctx_set_tune(ctx.h, t)
+            out[g] = P.gpu_trace(ctx, w, mf.MF_FP64, cells=False)
+    finally:
+        mf.mf_ctx_set_tune(ctx.h, None)
+    a, b = out[1], out[16]
+    ka = {k: i for i, k in enumerate(P.keys(a["edge_y"], a["edge_mask"]))}
+    ia = np.array([ka[k] for k in P.keys(b["edge_y"], b["edge_mask"])])
+    assert np.array_equal(a["edge_t"][ia], b["edge_t"])
+    assert np.array_equal(a["points"][ia], b["points"])
+
+
+@pytest.mark.parametrize("cfg", ["d5", "d6"])
+def test_certify_many_links_against_oracle(ctx, cfg):
+    """Certification of 5- and 6-link arms (boxes; boxes and spheres) on
+    random configurations: verdicts bit-exact away from |margin| < 1e-12,
+    margins within 1e-9 of the oracle's."""
+    w = W.config_d5() if cfg == "d5" else W.config_d6(n_sv=64)
+    rng = np.random.default_rng(11)
+    pts = rng.uniform(-np.pi, np.pi, size=(3000, w.d))
+    vg, mg, _ = ctx.certify(w.dh, w.radius, w.obs_type, w.obs_pose, w.obs_dims, pts, None, None)
+    vo, mo, _ = oracle.certify(w.dh, w.radius, w.obs_type, w.obs_pose, w.obs_dims, pts)
+    vg, mg = vg.cpu().numpy(), mg.cpu().numpy()
+    sure = np.abs(mo) > 1e-12
+    assert np.array_equal(vg[sure], vo[sure])
+    assert np.max(np.abs(mg - mo)) <= 1e-9
+    assert 0 < vg.sum() < len(vg)
