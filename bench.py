@@ -182,16 +182,17 @@ def cpu_baseline(w, budget_s=15.0):
     return {"value": rate, "unit": "simplices/s", "cores": 1, "kind": "oracle", "sample": sample}
 
 
-def run_served(ctx, n_requests, rate_hz, max_slots=64, hbm_bytes=200 << 30, seed=1005):
-    """Poisson stream of proof requests through the continuous-batching
-    server: p50 / p99 latency (arrival -> results fetched) and simplices/s."""
+def run_served(ctx, arrivals, reqs, precision, max_slots=64, hbm_bytes=200 << 30):
+    """Requests arriving at the given times (seconds) through the
+    continuous-batching server: p50 / p99 latency (arrival -> results
+    fetched), simplices/s over the wall time, failed requests."""
     import torch
     from paper_2406_04795_gb300 import mf
-    arrivals, reqs = W.served_requests(seed=seed, n_requests=n_requests, rate_hz=rate_hz)
+    n_requests = len(reqs)
     free, _ = torch.cuda.mem_get_info()
-    hbm_bytes = int(min(hbm_bytes, free - (8 << 30)))  # what the proofs before left free
+    hbm_bytes = int(min(hbm_bytes, 0.8 * free))  # inside the context's budget (0.9 x free)
     server = ctx.server(max_slots=max_slots, hbm_bytes=hbm_bytes)
-    lat, edges, nxt = [], 0, 0
+    lat, edges, nxt, failed = [], 0, 0, 0
     live = {}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -201,32 +202,49 @@ def run_served(ctx, n_requests, rate_hz, max_slots=64, hbm_bytes=200 << 30, seed
             raise RuntimeError("served run exceeded 600 s")
         while nxt < n_requests and arrivals[nxt] <= now:
             w = reqs[nxt]
-            rid = server.submit(w, precision=mf.MF_MIXED_FP32, **W.shell_capacity(w))
+            rid = server.submit(w, precision=precision, **W.shell_capacity(w))
             live[rid] = arrivals[nxt]
             nxt += 1
         if not live:
             time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
             continue
         server.step()
-        for rid in list(live):
-            state = server.status(rid)[0]
-            if state == 2 or state < 0:
-                if state == 2:
-                    edges += server.fetch(rid)["n_edges"]
-                else:
-                    try:
-                        server.fetch(rid)
-                    except mf.MfError:
-                        pass
-                lat.append(time.perf_counter() - t0 - live.pop(rid))
+        for rid in server.done():
+            if server.status(rid)[0] == 2:
+                edges += server.fetch(rid)["n_edges"]
+            else:
+                failed += 1
+                try:
+                    server.fetch(rid)
+                except mf.MfError:
+                    pass
+            lat.append(time.perf_counter() - t0 - live.pop(rid))
     wall = time.perf_counter() - t0
     server.close()
     lat_ms = np.array(lat) * 1e3
-    return {"requests": n_requests, "rate_hz": rate_hz, "slots": max_slots,
+    return {"requests": n_requests, "failed": failed, "slots": max_slots,
             "arena_gib": round(hbm_bytes / 2**30, 1),
             "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-            "simplices_per_s": edges / wall, "wall_s": wall, "precision": "mixed",
-            "workload": "d in {4,5,6}, 512-8192 SVs, lambda in [0.03,0.08], 1-16 seeds"}
+            "simplices_per_s": edges / wall, "simplices": edges, "wall_s": wall}
+
+
+def served_lines(ctx, n_requests, rate_hz, seed=1005):
+    """The served workload at its arrival rate (mixed precision), and the same
+    requests all at once on the mixed and on the FP64 path (capacity)."""
+    from paper_2406_04795_gb300 import mf
+    arrivals, reqs = W.served_requests(seed=seed, n_requests=n_requests, rate_hz=rate_hz)
+    out = run_served(ctx, arrivals, reqs, mf.MF_MIXED_FP32)
+    out.update({"rate_hz": rate_hz, "precision": "mixed",
+                "workload": "Poisson arrivals; d in {4,5,6}, 512-8192 SVs, lambda in [0.03,0.08], "
+                            "1-16 seeds"})
+    burst = np.zeros(len(reqs))
+    cap = {}
+    for name, prec in (("mixed", mf.MF_MIXED_FP32), ("fp64", mf.MF_FP64)):
+        r = run_served(ctx, burst, reqs, prec)
+        cap[name] = {"simplices_per_s": r["simplices_per_s"], "wall_s": r["wall_s"],
+                     "p50_ms": r["p50_ms"], "failed": r["failed"]}
+    out["saturated"] = cap
+    return out
 
 
 def run_reference(args):
@@ -260,6 +278,7 @@ def run_gb300(args):
     from paper_2406_04795_gb300 import mf
     from paper_2406_04795_gb300.api import Context
     from paper_2406_04795_gb300.pipeline import Proof, host_inputs
+    from paper_2406_04795_gb300.scaling import reduce_timing
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -334,16 +353,8 @@ def run_gb300(args):
     e2e_s = time.perf_counter() - t0
     barrier()
 
-    agg = torch.tensor([ms, float(edges), e2e_s, float(e2e_edges)], dtype=torch.float64,
-                       device="cuda")
-    if world > 1:
-        mx = agg.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = agg.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_max, edges_all, e2e_max, e2e_edges_all = mx[0].item(), sm[1].item(), mx[2].item(), sm[3].item()
-    else:
-        ms_max, edges_all, e2e_max, e2e_edges_all = ms, float(edges), e2e_s, float(e2e_edges)
+    ms_max, edges_all, e2e_max, e2e_edges_all = reduce_timing(ms, edges, e2e_s, e2e_edges, world,
+                                                              "cuda")
     if rank == 0:
         value = edges_all / args.steps / (ms_max * 1e-3)
         line = {
@@ -387,14 +398,15 @@ def run_gb300(args):
                                        "value": rm["n_edges"] / (msm * 1e-3),
                                        "edges_per_proof": rm["n_edges"],
                                        "rechecked_vertices": rm["n_recheck"]}
-            del pm
+            del pm, rm
             # the server gets a context of its own: the proofs' resident tables
-            # are released first, so that its arena can hold many requests
-            del proof
+            # and outputs are released first, so that its arena can hold many
+            # requests
+            del proof, r, v, m, cv
             ctx.close()
             torch.cuda.empty_cache()
             ctx = Context(local, 0)
-            line["served"] = run_served(ctx, args.served_requests, args.served_rate)
+            line["served"] = served_lines(ctx, args.served_requests, args.served_rate)
         print(json.dumps(line))
     ctx.close()
     if world > 1:

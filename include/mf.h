@@ -225,6 +225,9 @@ int mf_server_submit(mf_server *s, const mf_rbf *rbf, const mf_domain *dom,
                      const mf_trace_opts *opts, const double *seeds, int64_t n_seeds, int64_t *id);
 /* One scheduling round (see above); reports running and queued requests. */
 int mf_server_step(mf_server *s, void *stream, int32_t *n_running, int32_t *n_queued);
+/* Ids (host, up to cap) of requests that finished or failed since the last
+ * call, oldest first; *n receives how many were written. */
+int mf_server_done(mf_server *s, int64_t *ids, int32_t cap, int32_t *n);
 /* state: 0 queued, 1 running, 2 done, < 0 the request's error code; times are
  * host steady-clock seconds at submission, admission and completion. */
 int mf_server_status(mf_server *s, int64_t id, int32_t *state, double *t_submit, double *t_admit,

@@ -292,6 +292,10 @@ class Server:
     def status(self, rid):
         return mf.mf_server_status(self.ctx.h, self.h, rid)
 
+    def done(self):
+        """Ids of the requests that finished or failed since the last call."""
+        return mf.mf_server_done(self.ctx.h, self.h)
+
     def fetch(self, rid, stream=None):
         keep, sd, d, me, mc = self._keep[rid]
         # two-call pattern: the counts first (capacity error, request kept),

@@ -281,7 +281,9 @@ extern "C" int mf_trace_batch(mf_ctx *ctx, int32_t n, const mf_rbf *rbfs, const 
   // --- roots and cells of all traces
   {
     MfProfScope ps(ctx, MF_PH_ROOTS, st, 2);
-    mf_b_launch_roots(d_slots, d_plan, n, nullptr, sms, st);
+    uint32_t dims = 0;
+    for (int t = 0; t < n; t++) dims |= 1u << slots[t].F.d;
+    mf_b_launch_roots(d_slots, d_plan, n, nullptr, dims, ctx->tune.roots_group, sms, st);
   }
   bool any_cells = false;
   for (int t = 0; t < n; t++) any_cells = any_cells || (opts[t].flags & MF_WANT_CELLS);
@@ -461,6 +463,7 @@ struct Request {
   MfCounters cnt;
   int64_t n_cells = 0, n_ce = 0, levels = 0;
   MfSlot S;  // the descriptor of a finished trace: its results until fetched
+  int64_t id = 0;
 };
 
 }  // namespace
@@ -479,6 +482,7 @@ struct mf_server {
   std::vector<int64_t> slot_req;
   std::vector<MfSlotState> hstate;
   std::deque<int64_t> queue;
+  std::deque<int64_t> finished;  // done or failed, not yet reported by mf_server_done
   std::unordered_map<int64_t, Request> reqs;
   int64_t next_id = 1;
   cudaGraphExec_t step_exec = nullptr;
@@ -554,6 +558,7 @@ extern "C" int mf_server_submit(mf_server *s, const mf_rbf *rbf, const mf_domain
   r.t_submit = now_s();
   memset(&r.cnt, 0, sizeof(r.cnt));
   *id = s->next_id++;
+  r.id = *id;
   s->reqs[*id] = r;
   s->queue.push_back(*id);
   return MF_OK;
@@ -581,6 +586,7 @@ static void fail(mf_server *s, Request &r, int code, cudaStream_t st) {
   r.state = code;
   free_slot(s, r, st);
   free_memory(s, r);
+  s->finished.push_back(r.id);
 }
 
 extern "C" int mf_server_step(mf_server *s, void *stream, int32_t *n_running, int32_t *n_queued) {
@@ -605,6 +611,7 @@ extern "C" int mf_server_step(mf_server *s, void *stream, int32_t *n_running, in
     rc = mf_layout_trace(ctx, &r.rbf, &r.dom, &r.opts, &S, &l, &b);
     if (rc) {  // a malformed request fails alone
       r.state = rc;
+      s->finished.push_back(id);
       s->queue.pop_front();
       continue;
     }
@@ -612,6 +619,7 @@ extern "C" int mf_server_step(mf_server *s, void *stream, int32_t *n_running, in
     if (!s->alloc.take(b.off, &off)) {
       if (b.off > s->arena_bytes - s->data_off) {  // can never fit
         r.state = mf_set_error(ctx, MF_ERR_OOM, "request %lld exceeds the server budget", (long long)id);
+        s->finished.push_back(id);
         s->queue.pop_front();
         continue;
       }
@@ -621,6 +629,7 @@ extern "C" int mf_server_step(mf_server *s, void *stream, int32_t *n_running, in
     if (rc) {
       s->alloc.give(off, b.off);
       r.state = rc;
+      s->finished.push_back(id);
       s->queue.pop_front();
       continue;
     }
@@ -683,7 +692,9 @@ extern "C" int mf_server_step(mf_server *s, void *stream, int32_t *n_running, in
   }
   if (!fin.empty()) {
     cudaMemcpyAsync(s->d_only, only.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
-    mf_b_launch_roots(s->d_slots, s->d_plan, n, s->d_only, sms, st);
+    uint32_t dims = 0;
+    for (int t : fin) dims |= 1u << s->slots[t].F.d;
+    mf_b_launch_roots(s->d_slots, s->d_plan, n, s->d_only, dims, ctx->tune.roots_group, sms, st);
     bool cells = false;
     for (int t : fin) cells = cells || (s->slots[t].flags & MF_WANT_CELLS);
     if (cells) {
@@ -742,6 +753,7 @@ extern "C" int mf_server_step(mf_server *s, void *stream, int32_t *n_running, in
       r.levels = s->hstate[t].levels;
       r.state = 2;
       r.t_done = tnow;
+      s->finished.push_back(r.id);
       r.S = s->slots[t];
       free_slot(s, r, st);
     }
@@ -753,6 +765,17 @@ extern "C" int mf_server_step(mf_server *s, void *stream, int32_t *n_running, in
     *n_running = c;
   }
   if (n_queued) *n_queued = (int32_t)s->queue.size();
+  return MF_OK;
+}
+
+extern "C" int mf_server_done(mf_server *s, int64_t *ids, int32_t cap, int32_t *n) {
+  if (!s || !n || cap < 0 || (cap > 0 && !ids)) return MF_ERR_INVALID;
+  int32_t k = 0;
+  while (k < cap && !s->finished.empty()) {
+    ids[k++] = s->finished.front();
+    s->finished.pop_front();
+  }
+  *n = k;
   return MF_OK;
 }
 

@@ -125,11 +125,12 @@ __device__ T seg_obstacle_dist(const CertObsT<T> &o, const T *pa, const T *pb) {
   return dist > (T)0 ? dist : (T)0;
 }
 
-// NL = number of links (compile time, so that the frame origins stay in
-// registers).
-template <int NL>
-__global__ void __launch_bounds__(CERT_THREADS) k_certify_points(const double *dh, const double *radius,
-                                                                 int nobs, const int32_t *type,
+// The link loops stay rolled: unrolling them per link count inlines the
+// distance routines once per link and pass, which overflows the instruction
+// cache (measured: 45 no-instruction stall cycles per issue).
+__global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const double *dh,
+                                                                 const double *radius, int nobs,
+                                                                 const int32_t *type,
                                                                  const double *pose, const double *dims,
                                                                  const double *pts, int64_t n, int d,
                                                                  uint8_t *verdict, double *margin) {
@@ -158,9 +159,8 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(const double *d
   // forward kinematics: T = T * A_i with the standard DH link transform; keep
   // every frame origin (link i runs from origin i to origin i+1)
   double T[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};  // 3x4 row-major
-  double org[3 * (NL + 1)];
+  double org[3 * (MF_MAXD + 1)];
   org[0] = org[1] = org[2] = 0.0;
-#pragma unroll
   for (int i = 0; i < NL; i++) {
     const double th = pts[p * d + i] + sdh[4 * i], dd = sdh[4 * i + 1], aa = sdh[4 * i + 2];
     double st, ct;
@@ -191,8 +191,7 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(const double *d
   // and radius - lb an upper bound ub on the pair's margin.  The pair with the
   // largest ub is evaluated in FP64; the others only if the second-largest ub
   // exceeds that exact margin, and then only those whose ub does.
-  float org32[3 * (NL + 1)];
-#pragma unroll
+  float org32[3 * (MF_MAXD + 1)];
   for (int k = 0; k < 3 * (NL + 1); k++) org32[k] = (float)org[k];
   auto upper = [&](int i, int k) -> float {
     const float *a = &org32[3 * i], *b = &org32[3 * i + 3];
@@ -205,7 +204,6 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(const double *d
   };
   float ub1 = -INFINITY, ub2 = -INFINITY;
   int bi = -1, bk = -1;
-#pragma unroll
   for (int i = 0; i < NL; i++)
     for (int k = 0; k < nobs; k++) {
       const float ub = upper(i, k);
@@ -219,11 +217,8 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(const double *d
       }
     }
   double best = -INFINITY;
-#pragma unroll
-  for (int i = 0; i < NL; i++)
-    if (i == bi) best = srad[i] - seg_obstacle_dist(so[bk], &org[3 * i], &org[3 * i + 3]);
+  if (bi >= 0) best = srad[bi] - seg_obstacle_dist(so[bk], &org[3 * bi], &org[3 * bi + 3]);
   if ((double)ub2 > best) {
-#pragma unroll
     for (int i = 0; i < NL; i++)
       for (int k = 0; k < nobs; k++) {
         if (i == bi && k == bk) continue;
@@ -269,17 +264,9 @@ extern "C" int mf_certify(mf_ctx *ctx, const mf_robot *robot, const mf_scene *sc
   if (n_points > 0) {
     MfProfScope ps(ctx, MF_PH_CERT_PTS, st, 1, n_points);
     const unsigned g = (unsigned)((n_points + CERT_THREADS - 1) / CERT_THREADS);
-    switch (robot->n_links) {
-#define MF_CASE(NL)                                                                            \
-  case NL:                                                                                     \
-    k_certify_points<NL><<<g, CERT_THREADS, 0, st>>>(robot->dh, robot->radius, scene->n,       \
-                                                     scene->type, scene->pose, scene->dims,    \
-                                                     points, n_points, d, point_verdict, margin); \
-    break;
-      MF_CASE(1) MF_CASE(2) MF_CASE(3) MF_CASE(4) MF_CASE(5) MF_CASE(6) MF_CASE(7) MF_CASE(8)
-#undef MF_CASE
-      default: break;
-    }
+    k_certify_points<<<g, CERT_THREADS, 0, st>>>(robot->n_links, robot->dh, robot->radius,
+                                                 scene->n, scene->type, scene->pose, scene->dims,
+                                                 points, n_points, d, point_verdict, margin);
   }
   if (n_cells > 0) {
     MfProfScope ps(ctx, MF_PH_CERT_CELLS, st, 1, n_cells);

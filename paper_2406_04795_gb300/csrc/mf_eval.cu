@@ -588,9 +588,10 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_points_f64(MfRbfDev R,
 // 1. Segment screen (FP32): the support vectors within the FP64 screen
 //    distance of the whole segment are compacted into a per-warp list in
 //    shared memory, strong ones from the front, weak ones from the back.
-// 2. FP32 Newton from the linear interpolant of the end values, over that
-//    list, with hi/lo-split coordinates (x = x_hi + x_lo) so that differences
-//    keep FP32 relative accuracy; it also yields g''.
+// 2. FP32 Halley steps (t - 2 g g' / (2 g'^2 - g g''), Newton where the
+//    denominator is not positive) from the linear interpolant of the end
+//    values, over that list, with hi/lo-split coordinates (x = x_hi + x_lo)
+//    so that differences keep FP32 relative accuracy.
 // 3. FP64 Newton with a kept bracket [lo, hi] under the sign rule
 //    s = [f >= 0], over the same list (strong: FP64 exp; weak: FP32).  A
 //    step is final when |step| <= 1e-7, or on the first FP64 step when
@@ -677,10 +678,17 @@ __device__ __forceinline__ F64Acc root_eval64(const MfRbfDev &R, const int *near
 // screen (a group screen's survivors); NULL screens all of them.  FP64 work
 // that is the same for every lane (coordinates, their splits) runs once per
 // axis: lane k < d computes axis k and shuffles broadcast it.
+// Per-warp shared state of the FP64 stage (the point, the direction and the
+// FP32 split of the point): warp-uniform values kept out of registers.
+struct RootWarpState {
+  double x[MF_MAXD], dir[MF_MAXD];
+  float hl[3 * MF_MAXD];  // Split32<D> image: hi[D], lo[D], dir[D]
+};
+
 template <int D>
 __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, uint64_t e,
                           double tol, const int *src, int srcn, int *near, int *qs, int *qw,
-                          unsigned long long &evals, unsigned long long *terms) {
+                          RootWarpState *ws, unsigned long long &evals, unsigned long long *terms) {
   const int lane = threadIdx.x & 31;
   const int d = dim_of<D>(F.d);
   const unsigned lt = (1u << lane) - 1u;
@@ -705,12 +713,16 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
       __dadd_rn(__dmul_rn(F.lam, __dsub_rn((double)(yo + (int32_t)((mask >> ko) & 1u)), cs2)), F.o[ko]);
   const double diro = __dsub_rn(x2o, x1o);
   const float hio = (float)x1o, loo = (float)(x1o - (double)hio), d32o = (float)diro;
-  double dir[D], x[D];
+  double *dir = ws->dir, *x = ws->x;
+  Split32<D> &xs = *reinterpret_cast<Split32<D> *>(ws->hl);
   float x1hi[D], x1lo[D], dir32[D];
   float dd32 = 0.f;
+  if (lane < D) {
+    dir[lane] = lane < d ? diro : 0.0;
+    xs.dir[lane] = lane < d ? d32o : 0.f;
+  }
 #pragma unroll
   for (int k = 0; k < D; k++) {
-    dir[k] = k < d ? __shfl_sync(FULL, diro, k) : 0.0;
     x1hi[k] = k < d ? __shfl_sync(FULL, hio, k) : 0.f;
     x1lo[k] = k < d ? __shfl_sync(FULL, loo, k) : 0.f;
     dir32[k] = k < d ? __shfl_sync(FULL, d32o, k) : 0.f;
@@ -763,7 +775,8 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
   const bool overflow = ns + nw > NEAR_CAP;
   const double f0 = B.edge_f[2 * e], f1 = B.edge_f[2 * e + 1];
   const bool s1 = f0 >= 0.0;
-  // 2. FP32 Newton (bracketed) from the linear interpolant of the end values
+  // 2. FP32 Halley iteration (cubic: the evaluation yields g'' anyway),
+  //    bracketed, from the linear interpolant of the end values
   float t32 = (float)f0 / ((float)f0 - (float)f1);
   if (!(t32 > 0.f && t32 < 1.f)) t32 = 0.5f;
   float gpp = INFINITY;
@@ -774,7 +787,8 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
       const Root32 r = root_eval32<D>(R, near, ns, nw, x1hi, x1lo, dir32, dd32, b32, t32);
       gpp = r.gpp;
       if ((r.g >= 0.f) == s1) lo = t32; else hi = t32;
-      float tn = t32 - r.g / r.gp;
+      const float den = 2.f * r.gp * r.gp - r.g * r.gpp;
+      float tn = den > 0.f ? t32 - 2.f * r.g * r.gp / den : t32 - r.g / r.gp;
       if (!(tn > lo && tn < hi)) tn = 0.5f * (lo + hi);
       const float step = fabsf(tn - t32);
       t32 = tn;
@@ -788,14 +802,13 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
   for (int it = 0; it < 64; it++) {
     xo = __dadd_rn(x1o, __dmul_rn(t, diro));
     const float xho = (float)xo, xlo = (float)(xo - (double)xho);
-    Split32<D> xs;
-#pragma unroll
-    for (int k = 0; k < D; k++) {
-      x[k] = k < d ? __shfl_sync(FULL, xo, k) : 0.0;
-      xs.hi[k] = k < d ? __shfl_sync(FULL, xho, k) : 0.f;
-      xs.lo[k] = k < d ? __shfl_sync(FULL, xlo, k) : 0.f;
-      xs.dir[k] = dir32[k];
+    __syncwarp();  // the previous evaluation has read the state
+    if (lane < D) {
+      x[lane] = lane < d ? xo : 0.0;
+      xs.hi[lane] = lane < d ? xho : 0.f;
+      xs.lo[lane] = lane < d ? xlo : 0.f;
     }
+    __syncwarp();
     F64Acc a;
     if (overflow) {
       a = warp_f64<true, D>(R, x, dir, qs, qw, terms);
@@ -909,6 +922,7 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(MfFrame F, 
                                                                int group) {
   __shared__ int snear[ROOT_WARPS][NEAR_CAP];
   __shared__ int sq[ROOT_WARPS][2][64];
+  __shared__ RootWarpState sws[ROOT_WARPS];
   extern __shared__ int sgrp_all[];  // [ROOT_WARPS][GROUP_CAP] when group > 1
   const int w = threadIdx.x >> 5;
   int *sgrp = sgrp_all + w * GROUP_CAP;
@@ -917,7 +931,8 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(MfFrame F, 
   unsigned long long evals = 0, terms[2] = {0, 0};
   if (group <= 1) {
     for (uint64_t e = (uint64_t)blockIdx.x * ROOT_WARPS + w; e < n_edges; e += nwarps)
-      root_edge<D>(F, R, B, e, tol, nullptr, 0, snear[w], sq[w][0], sq[w][1], evals, terms);
+      root_edge<D>(F, R, B, e, tol, nullptr, 0, snear[w], sq[w][0], sq[w][1], &sws[w], evals,
+                   terms);
   } else {
     const uint64_t G = (uint64_t)group;
     for (uint64_t g0 = ((uint64_t)blockIdx.x * ROOT_WARPS + w) * G; g0 < n_edges; g0 += nwarps * G) {
@@ -925,7 +940,7 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(MfFrame F, 
       const int gn = group_screen<D>(F, R, B, g0, ng, rs, sgrp);
       for (int q = 0; q < ng; q++)
         root_edge<D>(F, R, B, g0 + q, tol, gn >= 0 ? sgrp : nullptr, gn, snear[w], sq[w][0],
-                     sq[w][1], evals, terms);
+                     sq[w][1], &sws[w], evals, terms);
     }
   }
   root_flush(B, evals, terms);
@@ -1025,22 +1040,39 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_b_eval(const MfSlot *slots,
   }
 }
 
-__global__ void __launch_bounds__(ROOT_WARPS * 32) k_b_roots(const MfSlot *slots, const MfBatchPlan *P,
-                                                            int n) {
+// Root solve of every slot of dimension D (the plan's pe prefix holds only
+// those): warps take runs of `group` consecutive items; a run that crosses a
+// slot boundary is split, each part sharing one group screen.
+template <int D>
+__global__ void __launch_bounds__(ROOT_WARPS * 32, 2) k_b_roots(const MfSlot *slots,
+                                                                const MfBatchPlan *P, int n,
+                                                                int group) {
   __shared__ int snear[ROOT_WARPS][NEAR_CAP];
   __shared__ int sq[ROOT_WARPS][2][64];
+  __shared__ RootWarpState sws[ROOT_WARPS];
+  extern __shared__ int sgrp_all[];  // [ROOT_WARPS][GROUP_CAP] when group > 1
   const int w = threadIdx.x >> 5;
+  int *sgrp = sgrp_all + w * GROUP_CAP;
   const unsigned long long total = P->pe[n];
+  const unsigned long long G = group > 1 ? (unsigned long long)group : 1ull;
   const unsigned long long nwarps = (unsigned long long)gridDim.x * ROOT_WARPS;
-  for (unsigned long long item = (unsigned long long)blockIdx.x * ROOT_WARPS + w; item < total;
-       item += nwarps) {
-    const int t = mf_slot_of(P->pe, n, item);
-    const MfSlot &S = slots[t];
-    unsigned long long evals = 0, terms[2] = {0, 0};
-    root_edge<MF_MAXD>(S.F, S.R, S.B, item - P->pe[t], S.root_tol, nullptr, 0, snear[w], sq[w][0],
-                       sq[w][1], evals,
-              terms);
-    root_flush(S.B, evals, terms);
+  for (unsigned long long g0 = ((unsigned long long)blockIdx.x * ROOT_WARPS + w) * G; g0 < total;
+       g0 += nwarps * G) {
+    const unsigned long long g1 = g0 + G < total ? g0 + G : total;
+    for (unsigned long long i = g0; i < g1;) {
+      const int t = mf_slot_of(P->pe, n, i);
+      const MfSlot &S = slots[t];
+      const unsigned long long end = P->pe[t + 1] < g1 ? P->pe[t + 1] : g1;
+      const uint64_t e0 = i - P->pe[t];
+      const int ng = (int)(end - i);
+      const int gn = G > 1 ? group_screen<D>(S.F, S.R, S.B, e0, ng, sqrtf(S.R.screen_r2), sgrp) : -1;
+      unsigned long long evals = 0, terms[2] = {0, 0};
+      for (int q = 0; q < ng; q++)
+        root_edge<D>(S.F, S.R, S.B, e0 + q, S.root_tol, gn >= 0 ? sgrp : nullptr, gn, snear[w],
+                     sq[w][0], sq[w][1], &sws[w], evals, terms);
+      root_flush(S.B, evals, terms);
+      i = end;
+    }
   }
 }
 
@@ -1055,10 +1087,23 @@ void mf_b_launch_eval(const MfSlot *slots, MfBatchPlan *P, int n, bool any_mixed
   mf_b_launch_advance(slots, n, s);
 }
 
-void mf_b_launch_roots(const MfSlot *slots, MfBatchPlan *P, int n, const int32_t *only, int sms,
-                       cudaStream_t s) {
-  mf_b_launch_plan_edges(slots, P, n, 0, only, s);
-  k_b_roots<<<sms * 4, ROOT_WARPS * 32, 0, s>>>(slots, P, n);
+void mf_b_launch_roots(const MfSlot *slots, MfBatchPlan *P, int n, const int32_t *only,
+                       uint32_t dims, int group, int sms, cudaStream_t s) {
+  const int dyn = group > 1 ? ROOT_WARPS * GROUP_CAP * (int)sizeof(int) : 0;
+  for (int dd = 2; dd <= MF_MAXD; dd++) {
+    if (!((dims >> dd) & 1u)) continue;
+    mf_b_launch_plan_edges(slots, P, n, 0, only, s, dd);
+    switch (dd) {
+#define MF_CASE(DD)                                                                            \
+  case DD:                                                                                     \
+    if (dyn) cudaFuncSetAttribute(k_b_roots<DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn); \
+    k_b_roots<DD><<<sms * 4, ROOT_WARPS * 32, dyn, s>>>(slots, P, n, group);                   \
+    break;
+      MF_CASE(2) MF_CASE(3) MF_CASE(4) MF_CASE(5) MF_CASE(6) MF_CASE(7) MF_CASE(8)
+#undef MF_CASE
+      default: break;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -139,16 +139,18 @@ void mf_b_launch_update(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, in
                         cudaGraphConditionalHandle h, int use_handle, cudaStream_t s);
 // `only` (device, n int32, may be NULL): restrict roots / cells / CSR to the
 // slots with a non-zero entry.
+// dim > 0 restricts mode 0 (roots) to the slots of that dimension.
 void mf_b_launch_plan_edges(const MfSlot *slots, MfBatchPlan *P, int n, int cells,
-                            const int32_t *only, cudaStream_t s);
+                            const int32_t *only, cudaStream_t s, int dim = 0);
 void mf_b_launch_cells(const MfSlot *slots, MfBatchPlan *P, int n, const int32_t *only, int sms,
                        cudaStream_t s);
 void mf_b_launch_cell_edges(const MfSlot *slots, MfBatchPlan *P, int n, bool fill,
                             const int32_t *only, int sms, cudaStream_t s);
 void mf_b_launch_eval(const MfSlot *slots, MfBatchPlan *P, int n, bool any_mixed, int sms,
                       cudaStream_t s);
-void mf_b_launch_roots(const MfSlot *slots, MfBatchPlan *P, int n, const int32_t *only, int sms,
-                       cudaStream_t s);
+// dims: bit d set when some slot has dimension d (one exact-d launch each).
+void mf_b_launch_roots(const MfSlot *slots, MfBatchPlan *P, int n, const int32_t *only,
+                       uint32_t dims, int group, int sms, cudaStream_t s);
 
 struct MfSlotState {  // breadth-first progress of one trace
   unsigned long long cursor;     // next frontier edge to expand

@@ -584,11 +584,11 @@ __global__ void k_b_update(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P,
 // mode 1: cells of slots that want cells (into pc); mode 2: edges of slots
 // that want cells.
 __global__ void k_b_plan_edges(const MfSlot *slots, MfBatchPlan *P, int n, int mode,
-                               const int32_t *only) {
+                               const int32_t *only, int dim) {
   __shared__ unsigned long long total;
   const int t = threadIdx.x;
   unsigned long long c = 0;
-  if (t < n && (!only || only[t]) && slots[t].B.cnt) {
+  if (t < n && (!only || only[t]) && slots[t].B.cnt && (dim <= 0 || slots[t].F.d == dim)) {
     const MfTraceBufs &B = slots[t].B;
     const uint32_t want = mode == 0 ? MF_WANT_ROOTS : MF_WANT_CELLS;
     if (slots[t].flags & want) {
@@ -649,18 +649,18 @@ void mf_b_launch_update(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, in
   k_b_update<<<1, MF_MAX_SLOTS, 0, s>>>(slots, st, P, n, h, use_handle);
 }
 void mf_b_launch_plan_edges(const MfSlot *slots, MfBatchPlan *P, int n, int cells,
-                            const int32_t *only, cudaStream_t s) {
-  k_b_plan_edges<<<1, MF_MAX_SLOTS, 0, s>>>(slots, P, n, cells, only);
+                            const int32_t *only, cudaStream_t s, int dim) {
+  k_b_plan_edges<<<1, MF_MAX_SLOTS, 0, s>>>(slots, P, n, cells, only, dim);
 }
 void mf_b_launch_cells(const MfSlot *slots, MfBatchPlan *P, int n, const int32_t *only, int sms,
                        cudaStream_t s) {
-  k_b_plan_edges<<<1, MF_MAX_SLOTS, 0, s>>>(slots, P, n, 2, only);
+  k_b_plan_edges<<<1, MF_MAX_SLOTS, 0, s>>>(slots, P, n, 2, only, 0);
   k_b_cells_enum<<<sms * 8, 256, 0, s>>>(slots, P, n);
 }
 void mf_b_launch_cell_edges(const MfSlot *slots, MfBatchPlan *P, int n, bool fill,
                             const int32_t *only, int sms, cudaStream_t s) {
   if (!fill) {
-    k_b_plan_edges<<<1, MF_MAX_SLOTS, 0, s>>>(slots, P, n, 1, only);
+    k_b_plan_edges<<<1, MF_MAX_SLOTS, 0, s>>>(slots, P, n, 1, only, 0);
     k_b_cell_edges<false><<<sms * 8, 256, 0, s>>>(slots, P, n);
   } else {
     k_b_cell_edges<true><<<sms * 8, 256, 0, s>>>(slots, P, n);

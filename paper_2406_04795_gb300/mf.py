@@ -35,7 +35,7 @@ EXPORTS = ("mf_ctx_create", "mf_ctx_destroy", "mf_last_error", "mf_ctx_bytes", "
            "mf_eval", "mf_trace", "mf_trace_fetch", "mf_certify", "mf_ctx_set_profiling",
            "mf_ctx_get_stats", "mf_trace_noalloc", "mf_trace_batch", "mf_domain_table",
            "mf_server_create", "mf_server_destroy", "mf_server_submit", "mf_server_step",
-           "mf_server_status", "mf_server_fetch", "mf_autotune", "mf_ctx_set_tune",
+           "mf_server_status", "mf_server_fetch", "mf_server_done", "mf_autotune", "mf_ctx_set_tune",
            "mf_ctx_get_tune")
 
 MF_PHASES = 12
@@ -160,6 +160,8 @@ def load(build_if_missing: bool = True):
     L.mf_server_status.restype = C.c_int
     L.mf_server_status.argtypes = [V, C.c_int64, P(C.c_int32), P(C.c_double), P(C.c_double),
                                    P(C.c_double)]
+    L.mf_server_done.restype = C.c_int
+    L.mf_server_done.argtypes = [V, P(C.c_int64), C.c_int32, P(C.c_int32)]
     L.mf_server_fetch.restype = C.c_int
     L.mf_server_fetch.argtypes = [V, C.c_int64, P(mf_trace_out), V]
     L.mf_domain_table.restype = C.c_int
@@ -259,6 +261,13 @@ def mf_server_status(ctx, server, rid):
     t = [C.c_double(), C.c_double(), C.c_double()]
     _check(ctx, load().mf_server_status(server, rid, C.byref(st), *[C.byref(x) for x in t]))
     return st.value, t[0].value, t[1].value, t[2].value
+
+
+def mf_server_done(ctx, server, cap=4096):
+    ids = (C.c_int64 * cap)()
+    n = C.c_int32()
+    _check(ctx, load().mf_server_done(server, ids, cap, C.byref(n)))
+    return [ids[i] for i in range(n.value)]
 
 
 def mf_server_fetch(ctx, server, rid, out: mf_trace_out, stream=0, check=True):

@@ -27,23 +27,22 @@ def test_server_results_equal_alone_under_queueing(ctx):
     ids, got, saw_queue, steps = [], {}, False, 0
     pending = list(range(len(ws)))
     while pending or len(got) < len(ids):
-        # two new requests arrive every other step while earlier ones run
+        # four requests at once (one more than the slots), then two every
+        # other step while earlier ones run
         if pending and steps % 2 == 0:
-            for _ in range(2):
+            for _ in range(4 if steps == 0 else 2):
                 if pending:
                     k = pending.pop(0)
                     ids.append(server.submit(ws[k], precision=precs[k], **W.shell_capacity(ws[k])))
         running, queued = server.step()
         assert running <= 3
         saw_queue = saw_queue or queued > 0
-        for k, rid in enumerate(ids):
-            if rid in got:
-                continue
+        for rid in server.done():  # each finished request is reported once
+            assert rid in ids and rid not in got
             state, t_sub, t_adm, t_done = server.status(rid)
-            assert state >= 0, "request %d failed: %d" % (k, state)
-            if state == 2:
-                assert t_sub <= t_adm <= t_done
-                got[rid] = server.fetch(rid)
+            assert state == 2, "request %d failed: %d" % (rid, state)
+            assert t_sub <= t_adm <= t_done
+            got[rid] = server.fetch(rid)
         steps += 1
         assert steps < 20000
     assert saw_queue, "the slot limit should have queued requests"

@@ -4,6 +4,7 @@ The exact lattice domain table (mf_domain_table) must reproduce, vertex by
 vertex, the oracle's decision "x(y) lies in the closed box", for vertices deep
 inside, outside and on the boundary of the box."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -52,3 +53,36 @@ def test_domain_table_matches_oracle_box_test(d, lam, box):
         n_in += bool(want)
     assert 0 < n_in < len(ys)
     del n_edge, cinv
+
+
+def _rank_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+    from paper_2406_04795_gb300.scaling import reduce_timing
+    import bench
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank,
+                            world_size=world)
+    try:
+        # each rank traces its own workload (seed + 10 rank) and reports its time
+        w = bench.make_workload("d3", rank)
+        res = reduce_timing(100.0 + rank, 1000 * (rank + 1), 2.0 * (rank + 1), 10 + rank, world,
+                            "cpu")
+        with open(os.path.join(out_dir, "r%d.txt" % rank), "w") as fh:
+            fh.write("%r %r %r %r %r\n" % (res + (float(w.sv[0, 0]),)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_weak_scaling_reduction_two_gloo_ranks(tmp_path):
+    """The multi-GPU bench path on CPU: two gloo ranks get distinct workloads
+    and agree on max time and summed units."""
+    import socket
+    import torch.multiprocessing as tmp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    tmp.spawn(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    rows = [open(tmp_path / ("r%d.txt" % r)).read().split() for r in range(2)]
+    for row in rows:
+        ms, units, e2e, e2e_units = (float(v) for v in row[:4])
+        assert (ms, units, e2e, e2e_units) == (101.0, 3000.0, 4.0, 21.0)
+    assert rows[0][4] != rows[1][4]  # different seeds per rank
