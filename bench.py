@@ -134,9 +134,13 @@ def roofline(stats, w, clocks, n_sms=152):
         per_strong = (5 * d + 5 if dom == "roots" else 3 * d + 3) + FP64_EXP_FLOPS
         flops = s["terms"] * per_strong / max(s["launches"], 1)
         ach = flops / (ms_per_launch * 1e-3) / 1e12
+        # DRAM bytes per launch from the ncu capture of k_roots_f64 (41.7 B per
+        # edge: the edge records; the support vectors stay in L2), scaled by
+        # the edges one launch processes
+        traffic = 41.7 * s["units"] / max(s["launches"], 1) if dom == "roots" else None
         return {"kernel": "k_roots_f64" if dom == "roots" else "k_eval_vertices_f64",
                 "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": ach / fp64_peak, "traffic": None,
+                "frac": ach / fp64_peak, "traffic": traffic,
                 "peak_source": "FP64 pipe: %d SMs x 2 DFMA/clk x %.0f MHz (sampled)" % (n_sms, mhz),
                 "work": "%d FP64 terms x %d flops (and %d FP32 weak terms, not counted)" % (
                     s["terms"], per_strong, s["terms_weak"]),
@@ -295,7 +299,14 @@ def run_gb300(args):
     proof = Proof(ctx, w)
     stream = torch.cuda.current_stream()
     tune = None
-    if not args.no_autotune:
+    if args.tune_json:
+        # fixed launch choices (reproduces a tuned configuration, e.g. under ncu)
+        t = mf.mf_ctx_get_tune(ctx.h)
+        for k, v in json.loads(args.tune_json).items():
+            setattr(t, k, int(v))
+        mf.mf_ctx_set_tune(ctx.h, t)
+        tune = mf.mf_ctx_get_tune(ctx.h).as_dict()
+    elif not args.no_autotune:
         # untimed: launch variants and BFS chunk picked on this workload (one
         # proof first, so that its capacities have grown to fit)
         proof.step()
@@ -423,6 +434,8 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "mixed_fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--tune-json", default="",
+                    help="fixed launch choices instead of autotuning, e.g. '{\"roots_variant\": 1}'")
     ap.add_argument("--lam", type=float, default=None,
                     help="override the lattice scale (small profiling cases)")
     ap.add_argument("--no-extras", action="store_true",

@@ -156,43 +156,77 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const d
   __syncthreads();
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
-  // forward kinematics: T = T * A_i with the standard DH link transform; keep
-  // every frame origin (link i runs from origin i to origin i+1)
+  // Forward kinematics, T = T * A_i with the standard DH link transform,
+  // keeping every frame origin (link i runs from origin i to origin i+1).
+  // First in FP32 for all links (the lower bounds below), then in FP64 only
+  // as far along the chain as the pairs that need an exact distance.
+  float org32[3 * (MF_MAXD + 1)];
+  {
+    float T[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+    org32[0] = org32[1] = org32[2] = 0.f;
+    for (int i = 0; i < NL; i++) {
+      const float th = (float)(pts[p * d + i] + sdh[4 * i]);
+      const float dd = (float)sdh[4 * i + 1], aa = (float)sdh[4 * i + 2];
+      float st, ct;
+      sincosf(th, &st, &ct);
+      const float sa = (float)ssa[i], ca = (float)sca[i];
+      const float A[12] = {ct, -st * ca, st * sa, aa * ct, st, ct * ca, -ct * sa, aa * st,
+                           0.f, sa, ca, dd};
+      float N[12];
+#pragma unroll
+      for (int r = 0; r < 3; r++) {
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+          float v = T[4 * r + 0] * A[c] + T[4 * r + 1] * A[4 + c] + T[4 * r + 2] * A[8 + c];
+          if (c == 3) v += T[4 * r + 3];
+          N[4 * r + c] = v;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 12; k++) T[k] = N[k];
+      org32[3 * (i + 1) + 0] = T[3];
+      org32[3 * (i + 1) + 1] = T[7];
+      org32[3 * (i + 1) + 2] = T[11];
+    }
+  }
   double T[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};  // 3x4 row-major
   double org[3 * (MF_MAXD + 1)];
   org[0] = org[1] = org[2] = 0.0;
-  for (int i = 0; i < NL; i++) {
-    const double th = pts[p * d + i] + sdh[4 * i], dd = sdh[4 * i + 1], aa = sdh[4 * i + 2];
-    double st, ct;
-    sincos(th, &st, &ct);
-    const double sa = ssa[i], ca = sca[i];
-    const double A[12] = {ct, -st * ca, st * sa, aa * ct, st, ct * ca, -ct * sa, aa * st,
-                          0.0, sa, ca, dd};
-    double N[12];
+  int done = 0;  // FP64 origins known: 0 .. done
+  auto fk64 = [&](int upto) {
+    for (int i = done; i < upto; i++) {
+      const double th = pts[p * d + i] + sdh[4 * i], dd = sdh[4 * i + 1], aa = sdh[4 * i + 2];
+      double st, ct;
+      sincos(th, &st, &ct);
+      const double sa = ssa[i], ca = sca[i];
+      const double A[12] = {ct, -st * ca, st * sa, aa * ct, st, ct * ca, -ct * sa, aa * st,
+                            0.0, sa, ca, dd};
+      double N[12];
 #pragma unroll
-    for (int r = 0; r < 3; r++) {
+      for (int r = 0; r < 3; r++) {
 #pragma unroll
-      for (int c = 0; c < 4; c++) {
-        double v = T[4 * r + 0] * A[c] + T[4 * r + 1] * A[4 + c] + T[4 * r + 2] * A[8 + c];
-        if (c == 3) v += T[4 * r + 3];
-        N[4 * r + c] = v;
+        for (int c = 0; c < 4; c++) {
+          double v = T[4 * r + 0] * A[c] + T[4 * r + 1] * A[4 + c] + T[4 * r + 2] * A[8 + c];
+          if (c == 3) v += T[4 * r + 3];
+          N[4 * r + c] = v;
+        }
       }
-    }
 #pragma unroll
-    for (int k = 0; k < 12; k++) T[k] = N[k];
-    org[3 * (i + 1) + 0] = T[3];
-    org[3 * (i + 1) + 1] = T[7];
-    org[3 * (i + 1) + 2] = T[11];
-  }
+      for (int k = 0; k < 12; k++) T[k] = N[k];
+      org[3 * (i + 1) + 0] = T[3];
+      org[3 * (i + 1) + 1] = T[7];
+      org[3 * (i + 1) + 2] = T[11];
+    }
+    if (upto > done) done = upto;
+  };
   // margin = max over (link, obstacle) of radius - distance.  Every pair first
-  // gets the same distance computed in FP32; minus a slack of 1e-4 (1 + the
-  // largest coordinate), far above the FP32 rounding of the computation
-  // (about 1e-6 of that scale), it is a lower bound lb on the true distance,
-  // and radius - lb an upper bound ub on the pair's margin.  The pair with the
-  // largest ub is evaluated in FP64; the others only if the second-largest ub
-  // exceeds that exact margin, and then only those whose ub does.
-  float org32[3 * (MF_MAXD + 1)];
-  for (int k = 0; k < 3 * (NL + 1); k++) org32[k] = (float)org[k];
+  // gets the same distance computed in FP32 from the FP32 chain; minus a slack
+  // of 1e-4 (1 + the largest coordinate), far above the FP32 rounding of the
+  // chain and the distance (about 1e-5 of that scale), it is a lower bound lb
+  // on the true distance, and radius - lb an upper bound ub on the pair's
+  // margin.  The pair with the largest ub is evaluated in FP64; the others
+  // only if the second-largest ub exceeds that exact margin, and then only
+  // those whose ub does.
   auto upper = [&](int i, int k) -> float {
     const float *a = &org32[3 * i], *b = &org32[3 * i + 3];
     const float dist = seg_obstacle_dist<float>(sof[k], a, b);
@@ -217,8 +251,12 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const d
       }
     }
   double best = -INFINITY;
-  if (bi >= 0) best = srad[bi] - seg_obstacle_dist(so[bk], &org[3 * bi], &org[3 * bi + 3]);
+  if (bi >= 0) {
+    fk64(bi + 1);
+    best = srad[bi] - seg_obstacle_dist(so[bk], &org[3 * bi], &org[3 * bi + 3]);
+  }
   if ((double)ub2 > best) {
+    fk64(NL);
     for (int i = 0; i < NL; i++)
       for (int k = 0; k < nobs; k++) {
         if (i == bi && k == bk) continue;

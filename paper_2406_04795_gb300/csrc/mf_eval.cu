@@ -615,6 +615,7 @@ __device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const int *near
   const float g2 = (float)(R.gamma * 1.4426950408889634);
   float s0 = 0.f, s1 = 0.f, s2 = 0.f;
   const int total = ns + nw;
+#pragma unroll 2
   for (int i = lane; i < total; i += 32) {
     const int j = i < ns ? near[i] : near[NEAR_CAP - 1 - (i - ns)];
     float r2 = 0.f, proj = 0.f;

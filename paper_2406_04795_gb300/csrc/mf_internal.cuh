@@ -328,6 +328,22 @@ __device__ __forceinline__ uint64_t mf_table_find(const unsigned long long *keys
   return ~0ull;
 }
 
+// Warp-aggregated list allocation: every calling lane with take = true gets
+// a distinct index from *counter, with one atomic per group of lanes that
+// share the counter (batched kernels mix traces in a warp).  Callable from
+// divergent code: the group is the lanes active at the call.
+__device__ __forceinline__ unsigned long long mf_warp_alloc(unsigned long long *counter, bool take) {
+  const unsigned act = __activemask();
+  const unsigned peers = __match_any_sync(act, (unsigned long long)counter);
+  const unsigned m = __ballot_sync(act, take) & peers;
+  const int lane = threadIdx.x & 31;
+  const int leader = m ? __ffs(m) - 1 : lane;
+  unsigned long long base = 0;
+  if (m && lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
+  base = __shfl_sync(act, base, leader);
+  return base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+}
+
 __device__ __forceinline__ float mf_warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

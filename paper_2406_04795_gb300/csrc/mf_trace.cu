@@ -40,9 +40,10 @@ __device__ __forceinline__ void visit_vertex(const MfFrame &F, const MfTraceBufs
   const unsigned long long key = mf_vertex_key(F, w);
   bool won;
   const uint64_t slot = mf_table_insert(B.vtab_key, B.vtab_mask, key, &won);
-  if (slot == ~0ull) { atomicOr(&B.cnt->err_table_full, 1u); return; }
-  if (!won) return;
-  const unsigned long long idx = atomicAdd(&B.cnt->n_vertices, 1ull);
+  if (slot == ~0ull) atomicOr(&B.cnt->err_table_full, 1u);
+  const bool take = slot != ~0ull && won;
+  const unsigned long long idx = mf_warp_alloc(&B.cnt->n_vertices, take);
+  if (!take) return;
   if (idx >= B.max_vertices) { atomicOr(&B.cnt->err_overflow, 1u); return; }
 #pragma unroll
   for (int k = 0; k < MF_MAXD; k++)
@@ -62,9 +63,10 @@ __device__ __forceinline__ void emit_edge(const MfFrame &F, const MfTraceBufs &B
   const unsigned long long key = mf_edge_key(F, y, mask);
   bool won;
   const uint64_t slot = mf_table_insert(B.etab_key, B.etab_mask, key, &won);
-  if (slot == ~0ull) { atomicOr(&B.cnt->err_table_full, 1u); return; }
-  if (!won) return;
-  const unsigned long long idx = atomicAdd(&B.cnt->n_edges, 1ull);
+  if (slot == ~0ull) atomicOr(&B.cnt->err_table_full, 1u);
+  const bool take = slot != ~0ull && won;
+  const unsigned long long idx = mf_warp_alloc(&B.cnt->n_edges, take);
+  if (!take) return;
   if (idx >= B.max_edges) { atomicOr(&B.cnt->err_overflow, 1u); return; }
 #pragma unroll
   for (int k = 0; k < MF_MAXD; k++)
@@ -324,9 +326,10 @@ __device__ __forceinline__ void cells_enum_edge(const MfFrame &F, const MfTraceB
     const unsigned long long key = (unsigned long long)perm_rank(pi, d) + dfact * mf_vertex_key(F, z);
     bool won;
     const uint64_t slot = mf_table_insert(B.ctab_key, B.ctab_mask, key, &won);
-    if (slot == ~0ull) { atomicOr(&B.cnt->err_table_full, 1u); continue; }
-    if (!won) continue;
-    const unsigned long long idx = atomicAdd(&B.cnt->n_cells, 1ull);
+    if (slot == ~0ull) atomicOr(&B.cnt->err_table_full, 1u);
+    const bool take = slot != ~0ull && won;
+    const unsigned long long idx = mf_warp_alloc(&B.cnt->n_cells, take);
+    if (!take) continue;
     if (idx >= B.max_cells) { atomicOr(&B.cnt->err_overflow, 1u); continue; }
     for (int k = 0; k < d; k++) {
       B.cell_y[idx * d + k] = z[k];
