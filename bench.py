@@ -196,7 +196,7 @@ def run_served(ctx, arrivals, reqs, precision, max_slots=64, hbm_bytes=200 << 30
     free, _ = torch.cuda.mem_get_info()
     hbm_bytes = int(min(hbm_bytes, 0.8 * free))  # inside the context's budget (0.9 x free)
     server = ctx.server(max_slots=max_slots, hbm_bytes=hbm_bytes)
-    lat, edges, nxt, failed = [], 0, 0, 0
+    lat, edges, nxt, failed, codes = [], 0, 0, 0, {}
     live = {}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -214,10 +214,12 @@ def run_served(ctx, arrivals, reqs, precision, max_slots=64, hbm_bytes=200 << 30
             continue
         server.step()
         for rid in server.done():
-            if server.status(rid)[0] == 2:
+            state = server.status(rid)[0]
+            if state == 2:
                 edges += server.fetch(rid)["n_edges"]
             else:
                 failed += 1
+                codes[str(state)] = codes.get(str(state), 0) + 1
                 try:
                     server.fetch(rid)
                 except mf.MfError:
@@ -226,7 +228,7 @@ def run_served(ctx, arrivals, reqs, precision, max_slots=64, hbm_bytes=200 << 30
     wall = time.perf_counter() - t0
     server.close()
     lat_ms = np.array(lat) * 1e3
-    return {"requests": n_requests, "failed": failed, "slots": max_slots,
+    return {"requests": n_requests, "failed": failed, "failed_codes": codes, "slots": max_slots,
             "arena_gib": round(hbm_bytes / 2**30, 1),
             "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
             "simplices_per_s": edges / wall, "simplices": edges, "wall_s": wall}

@@ -464,6 +464,7 @@ struct Request {
   int64_t n_cells = 0, n_ce = 0, levels = 0;
   MfSlot S;  // the descriptor of a finished trace: its results until fetched
   int64_t id = 0;
+  bool wait_idx = false;  // cells counted, waiting for arena room for the CSR index
 };
 
 }  // namespace
@@ -596,6 +597,44 @@ extern "C" int mf_server_step(mf_server *s, void *stream, int32_t *n_running, in
   cudaStream_t st = (cudaStream_t)stream;
   const int n = s->max_slots, sms = ctx->sms;
   int rc;
+  // --- finish traces that waited for room for their CSR index
+  {
+    std::vector<int32_t> only(n, 0);
+    std::vector<int> ready;
+    for (int t = 0; t < n; t++) {
+      if (s->slot_req[t] < 0) continue;
+      Request &r = s->reqs[s->slot_req[t]];
+      if (!r.wait_idx) continue;
+      size_t off;
+      if (!s->alloc.take((size_t)r.n_ce * 8, &off)) continue;
+      r.idx_off = off;
+      r.idx_bytes = (size_t)r.n_ce * 8;
+      s->slots[t].B.cell_idx = (int64_t *)(s->arena + s->data_off + off);
+      cudaMemcpyAsync(s->d_slots + t, &s->slots[t], sizeof(MfSlot), cudaMemcpyHostToDevice, st);
+      only[t] = 1;
+      ready.push_back(t);
+    }
+    if (!ready.empty()) {
+      cudaMemcpyAsync(s->d_only, only.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
+      mf_b_launch_plan_edges(s->d_slots, s->d_plan, n, 1, s->d_only, st);
+      mf_b_launch_cell_edges(s->d_slots, s->d_plan, n, true, s->d_only, sms, st);
+      for (int t : ready)
+        cudaMemcpyAsync(&s->reqs[s->slot_req[t]].cnt, s->slots[t].B.cnt, sizeof(MfCounters),
+                        cudaMemcpyDeviceToHost, st);
+      if ((rc = mf_cuda_check(ctx, cudaStreamSynchronize(st), "server CSR fill"))) return rc;
+      const double tnow = now_s();
+      for (int t : ready) {
+        Request &r = s->reqs[s->slot_req[t]];
+        r.wait_idx = false;
+        r.levels = s->hstate[t].levels;
+        r.state = 2;
+        r.t_done = tnow;
+        s->finished.push_back(r.id);
+        r.S = s->slots[t];
+        free_slot(s, r, st);
+      }
+    }
+  }
   // --- admission: FIFO, while a slot is free and the request's buffers fit
   std::vector<int> fresh;
   while (!s->queue.empty()) {
@@ -682,7 +721,7 @@ extern "C" int mf_server_step(mf_server *s, void *stream, int32_t *n_running, in
   for (int t = 0; t < n; t++) {
     if (s->slot_req[t] < 0) continue;
     Request &r = s->reqs[s->slot_req[t]];
-    if (r.state != 1 || s->hstate[t].active) continue;
+    if (r.state != 1 || s->hstate[t].active || r.wait_idx) continue;
     if (s->hstate[t].err) {
       fail(s, r, mf_set_error(ctx, MF_ERR_MAXEDGES, "request exceeded its capacities"), st);
       continue;
@@ -730,7 +769,12 @@ extern "C" int mf_server_step(mf_server *s, void *stream, int32_t *n_running, in
         if (r.state != 1 || r.n_ce <= 0) continue;
         size_t off;
         if (!s->alloc.take((size_t)r.n_ce * 8, &off)) {
-          fail(s, r, mf_set_error(ctx, MF_ERR_OOM, "server budget: no room for a cell index"), st);
+          if ((size_t)r.n_ce * 8 > s->arena_bytes - s->data_off) {
+            fail(s, r, mf_set_error(ctx, MF_ERR_OOM, "server budget: no room for a cell index"), st);
+          } else {  // room frees up as results are fetched: fill on a later step
+            r.wait_idx = true;
+            only[t] = 0;
+          }
           continue;
         }
         r.idx_off = off;
@@ -738,6 +782,9 @@ extern "C" int mf_server_step(mf_server *s, void *stream, int32_t *n_running, in
         s->slots[t].B.cell_idx = (int64_t *)(s->arena + s->data_off + off);
         cudaMemcpyAsync(s->d_slots + t, &s->slots[t], sizeof(MfSlot), cudaMemcpyHostToDevice, st);
       }
+      // the fill reuses the count pass's plan; slots now waiting are masked out
+      cudaMemcpyAsync(s->d_only, only.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
+      mf_b_launch_plan_edges(s->d_slots, s->d_plan, n, 1, s->d_only, st);
       mf_b_launch_cell_edges(s->d_slots, s->d_plan, n, true, s->d_only, sms, st);
     }
     for (int t : fin)
@@ -749,7 +796,7 @@ extern "C" int mf_server_step(mf_server *s, void *stream, int32_t *n_running, in
     for (int t : fin) {
       if (s->slot_req[t] < 0) continue;
       Request &r = s->reqs[s->slot_req[t]];
-      if (r.state != 1) continue;
+      if (r.state != 1 || r.wait_idx) continue;
       r.levels = s->hstate[t].levels;
       r.state = 2;
       r.t_done = tnow;

@@ -261,7 +261,7 @@ def shell_capacity(w) -> dict:
     lattice radii, so edges depend on d only (measured: d=4 ~1e5, d=5 ~5e5,
     d=6 ~1e6 per two shells); cells per edge grow with d."""
     me = {2: 1 << 16, 3: 1 << 17, 4: 1 << 19, 5: 1 << 21, 6: 1 << 22}.get(w.d, 1 << 22)
-    cells_per_edge = {2: 2, 3: 3, 4: 6, 5: 12, 6: 20}.get(w.d, 24)
+    cells_per_edge = {2: 2, 3: 3, 4: 8, 5: 12, 6: 32}.get(w.d, 40)
     return dict(max_edges=me, max_vertices=me, max_cells=me * cells_per_edge)
 
 
