@@ -605,7 +605,11 @@ struct Root32 {
   float g, gp, gpp;
 };
 
-// FP32 evaluation of g, g', g'' at t over the near list (all lanes).
+// FP32 evaluation of g, g', g'' at t over the strong entries of the near
+// list (all lanes).  The weak entries are below tau e^(1/2) = 5e-10 each, so
+// even a few hundred of them shift g by less than its FP32 rounding (~1e-7
+// of sum |terms|); the FP32 stage leaves them to the FP64 step, which sums
+// every kept term.
 template <int D>
 __device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const int *near, int ns, int nw,
                                               const float *x1hi, const float *x1lo,
@@ -614,7 +618,8 @@ __device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const int *near
   const int d = dim_of<D>(R.d);
   const float g2 = (float)(R.gamma * 1.4426950408889634);
   float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-  const int total = ns + nw;
+  (void)nw;
+  const int total = ns;
 #pragma unroll 2
   for (int i = lane; i < total; i += 32) {
     const int j = i < ns ? near[i] : near[NEAR_CAP - 1 - (i - ns)];
@@ -729,9 +734,14 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
     dir32[k] = k < d ? __shfl_sync(FULL, d32o, k) : 0.f;
     dd32 = fmaf(dir32[k], dir32[k], dd32);
   }
-  // 1. segment screen
+  // 1. segment screen.  Every segment point lies within |dir|/2 of the
+  //    midpoint, so a vector farther than r_s + |dir|/2 from it (with a
+  //    rounding margin) cannot pass; only the others get the exact
+  //    point-to-segment test.
   int ns = 0, nw = 0;
   const int total = src ? srcn : R.n;
+  const float inv_dd = 1.f / dd32;
+  const float pre = (sqrtf(R.screen_r2) + 0.5f * sqrtf(dd32)) * 1.0001f + 1e-5f, pre2 = pre * pre;
   for (int base = 0; base < total; base += 32) {
     const int i = base + lane;
     bool keep = false, strong = false;
@@ -752,17 +762,25 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
 #pragma unroll
         for (int k = 0; k < D; k++) p[k] = k < d ? (R.sv32[(int64_t)k * R.n + j] - x1hi[k]) : 0.f;
       }
-#pragma unroll
-      for (int k = 0; k < D; k++) pd = fmaf(p[k], dir32[k], pd);
-      const float tt = fminf(fmaxf(pd / dd32, 0.f), 1.f);
-      float r2 = 0.f;
+      float dm2 = 0.f;
 #pragma unroll
       for (int k = 0; k < D; k++) {
-        const float q = fmaf(-tt, dir32[k], p[k]);
-        r2 = fmaf(q, q, r2);
+        const float u = fmaf(-0.5f, dir32[k], p[k]);
+        dm2 = fmaf(u, u, dm2);
       }
-      keep = r2 <= R.screen_r2;
-      strong = g32 * r2 < R.strong32[j] + 0.5f;
+      if (dm2 <= pre2) {
+#pragma unroll
+        for (int k = 0; k < D; k++) pd = fmaf(p[k], dir32[k], pd);
+        const float tt = fminf(fmaxf(pd * inv_dd, 0.f), 1.f);
+        float r2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+          const float q = fmaf(-tt, dir32[k], p[k]);
+          r2 = fmaf(q, q, r2);
+        }
+        keep = r2 <= R.screen_r2;
+        strong = g32 * r2 < R.strong32[j] + 0.5f;
+      }
     }
     const unsigned ms = __ballot_sync(FULL, keep && strong);
     const unsigned mw = __ballot_sync(FULL, keep && !strong);
@@ -789,11 +807,15 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
       gpp = r.gpp;
       if ((r.g >= 0.f) == s1) lo = t32; else hi = t32;
       const float den = 2.f * r.gp * r.gp - r.g * r.gpp;
-      float tn = den > 0.f ? t32 - 2.f * r.g * r.gp / den : t32 - r.g / r.gp;
-      if (!(tn > lo && tn < hi)) tn = 0.5f * (lo + hi);
+      const bool halley = den > 0.f;
+      float tn = halley ? t32 - 2.f * r.g * r.gp / den : t32 - r.g / r.gp;
+      const bool inside = tn > lo && tn < hi;
+      if (!inside) tn = 0.5f * (lo + hi);
       const float step = fabsf(tn - t32);
       t32 = tn;
-      if (step <= 2e-6f) break;
+      // a Halley step of size s leaves an error of order s^3: below 1e-3
+      // the FP32 noise floor is reached and the FP64 step finishes
+      if (step <= 2e-6f || (halley && inside && step <= 1e-3f)) break;
     }
   }
   // 3. FP64 Newton with a kept bracket
