@@ -21,7 +21,10 @@
 // from shared memory, FP32 differences and ex2, and a per-point rigorous bound
 // B on |f~ - f|; points with |f~| <= max(B, band) are re-evaluated in FP64.
 #include <cmath>
+#include <algorithm>
 #include <cstdio>
+#include <utility>
+#include <vector>
 
 #include "mf_internal.cuh"
 #include "mf_ctx.h"
@@ -44,17 +47,21 @@ struct MfRbfStats {
   int bad;  // NaN / Inf in the inputs
 };
 
-__global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alpha, float *sv32,
-                              float *svlo32, double *sv64, float *alpha32, float *strong32,
-                              double *exp_tab, double *sv64r, float *svhl, MfRbfStats *st) {
+// Prepared vector j is the caller's vector perm[j] (identity when perm is
+// NULL); alpha64 receives the permuted alpha.
+__global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alpha, const int32_t *perm,
+                              float *sv32, float *svlo32, double *sv64, double *alpha64,
+                              float *alpha32, float *strong32, double *exp_tab, double *sv64r,
+                              float *svhl, MfRbfStats *st) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < 64) exp_tab[j] = exp2((double)j / 64.0);
   double a = 0.0;
   float m = 0.f;
   int bad = 0;
   if (j < n) {
+    const int64_t src = perm ? perm[j] : j;
     for (int k = 0; k < d; k++) {
-      double s = sv[(int64_t)j * d + k];
+      double s = sv[src * d + k];
       if (!isfinite(s)) bad = 1;
       sv64[(int64_t)k * n + j] = s;
       const float hi = (float)s;
@@ -71,8 +78,9 @@ __global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alph
       svhl[(int64_t)j * 16 + 2 * k] = 0.f;
       svhl[(int64_t)j * 16 + 2 * k + 1] = 0.f;
     }
-    double al = alpha[j];
+    double al = alpha[src];
     if (!isfinite(al)) bad = 1;
+    alpha64[j] = al;
     alpha32[j] = (float)al;
     a = fabs(al);
     // strong iff gamma r^2 < ln(|alpha| / tau)
@@ -91,10 +99,62 @@ __global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alph
   }
 }
 
+// Per block of 32 consecutive prepared vectors: FP32 bounding box (one warp
+// per block).
+__global__ void k_rbf_blocks(int d, int n, int nblk, const float *sv32, float *blo, float *bhi) {
+  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (b >= nblk) return;
+  const int j = b * 32 + lane;
+  for (int k = 0; k < d; k++) {
+    float lo = j < n ? sv32[(int64_t)k * n + j] : INFINITY, hi = j < n ? lo : -INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(FULL, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(FULL, hi, o));
+    }
+    if (lane == 0) {
+      blo[(int64_t)k * nblk + b] = lo;
+      bhi[(int64_t)k * nblk + b] = hi;
+    }
+  }
+}
+
 size_t mf_rbf_prep_bytes(int d, int64_t n) {
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  const size_t nb = (size_t)n;
-  return 256 + al(nb * d * 8) + 2 * al(nb * d * 4) + 2 * al(nb * 4) + al(64 * 8) + 2 * al(nb * 64);
+  const size_t nb = (size_t)n, nblk = (nb + 31) / 32;
+  return 256 + al(nb * d * 8) + 2 * al(nb * d * 4) + 2 * al(nb * 4) + al(64 * 8) + 2 * al(nb * 64) +
+         al(nb * 8) + al(nb * 4) + 2 * al(nblk * d * 4);
+}
+
+// Orders the vectors along a Morton (Z-order) curve of their coordinates:
+// bits of the quantised coordinates interleaved, 64 / d bits per axis.
+static void morton_order(int d, int n, const std::vector<double> &sv, std::vector<int32_t> &perm) {
+  double lo[MF_MAXD], hi[MF_MAXD];
+  for (int k = 0; k < d; k++) lo[k] = INFINITY, hi[k] = -INFINITY;
+  for (int j = 0; j < n; j++)
+    for (int k = 0; k < d; k++) {
+      const double v = sv[(size_t)j * d + k];
+      if (std::isfinite(v)) lo[k] = std::min(lo[k], v), hi[k] = std::max(hi[k], v);
+    }
+  const int bits = 64 / d;
+  const double top = (double)((1ull << bits) - 1);
+  std::vector<std::pair<uint64_t, int32_t>> code(n);
+  for (int j = 0; j < n; j++) {
+    uint64_t q[MF_MAXD];
+    for (int k = 0; k < d; k++) {
+      const double v = sv[(size_t)j * d + k], w = hi[k] - lo[k];
+      double u = (std::isfinite(v) && w > 0) ? (v - lo[k]) / w * top : 0.0;
+      u = u < 0 ? 0 : (u > top ? top : u);
+      q[k] = (uint64_t)u;
+    }
+    uint64_t c = 0;
+    for (int b = bits - 1; b >= 0; b--)
+      for (int k = 0; k < d; k++) c = (c << 1) | ((q[k] >> b) & 1u);
+    code[j] = {c, j};
+  }
+  std::sort(code.begin(), code.end());
+  perm.resize(n);
+  for (int j = 0; j < n; j++) perm[j] = code[j].second;
 }
 
 int mf_prepare_rbf(mf_ctx *ctx, const mf_rbf *rbf, MfRbfDev *out, cudaStream_t st) {
@@ -123,10 +183,31 @@ int mf_prepare_rbf_at(mf_ctx *ctx, const mf_rbf *rbf, char *base, MfRbfDev *out,
   float *strong32 = (float *)p; p += al(nb * 4);
   double *exp_tab = (double *)p; p += al(64 * 8);
   double *sv64r = (double *)p; p += al(nb * 64);
-  float *svhl = (float *)p;
+  float *svhl = (float *)p; p += al(nb * 64);
+  double *alpha64 = (double *)p; p += al(nb * 8);
+  int32_t *perm = (int32_t *)p; p += al(nb * 4);
+  const int nblk = (n + 31) / 32;
+  float *blo = (float *)p; p += al((size_t)nblk * d * 4);
+  float *bhi = (float *)p;
+  // Morton order of the vectors (host): spatially compact 32-vector blocks
+  {
+    std::vector<double> hsv((size_t)n * d);
+    int rc0 = mf_cuda_check(ctx, cudaMemcpyAsync(hsv.data(), rbf->sv, hsv.size() * 8,
+                                                 cudaMemcpyDeviceToHost, st), "prepare rbf");
+    if (rc0) return rc0;
+    if ((rc0 = mf_cuda_check(ctx, cudaStreamSynchronize(st), "prepare rbf"))) return rc0;
+    std::vector<int32_t> hperm;
+    morton_order(d, n, hsv, hperm);
+    rc0 = mf_cuda_check(ctx, cudaMemcpyAsync(perm, hperm.data(), (size_t)n * 4,
+                                             cudaMemcpyHostToDevice, st), "prepare rbf");
+    if (rc0) return rc0;
+    if ((rc0 = mf_cuda_check(ctx, cudaStreamSynchronize(st), "prepare rbf"))) return rc0;
+  }
   cudaMemsetAsync(dst, 0, sizeof(MfRbfStats), st);
-  k_prepare_rbf<<<(n + 255) / 256, 256, 0, st>>>(d, n, rbf->sv, rbf->alpha, sv32, svlo32, sv64,
-                                                  alpha32, strong32, exp_tab, sv64r, svhl, dst);
+  k_prepare_rbf<<<(n + 255) / 256, 256, 0, st>>>(d, n, rbf->sv, rbf->alpha, perm, sv32, svlo32, sv64,
+                                                  alpha64, alpha32, strong32, exp_tab, sv64r, svhl,
+                                                  dst);
+  k_rbf_blocks<<<(nblk + 7) / 8, 256, 0, st>>>(d, n, nblk, sv32, blo, bhi);
   MfRbfStats h;
   int rc = mf_cuda_check(ctx, cudaMemcpyAsync(&h, dst, sizeof(h), cudaMemcpyDeviceToHost, st),
                          "prepare rbf");
@@ -139,12 +220,15 @@ int mf_prepare_rbf_at(mf_ctx *ctx, const mf_rbf *rbf, char *base, MfRbfDev *out,
   out->sv32 = sv32;
   out->svlo32 = svlo32;
   out->sv64 = sv64;
-  out->alpha = rbf->alpha;
+  out->alpha = alpha64;
   out->alpha32 = alpha32;
   out->strong32 = strong32;
   out->exp_tab = exp_tab;
   out->sv64r = sv64r;
   out->svhl = svhl;
+  out->blk_lo = blo;
+  out->blk_hi = bhi;
+  out->nblk = nblk;
   out->gamma = rbf->gamma;
   out->b = rbf->b;
   out->sum_abs_alpha = h.sum_abs_alpha;
@@ -308,8 +392,27 @@ __device__ F64Acc warp_f64_pass(const MfRbfDev &R, const double *x, const double
   const Split32<D> xs = split32<D>(d, x, dir);
   int ns = 0, nw = 0;
   const unsigned lt = (1u << lane) - 1u;
-  for (int base = 0; base < R.n; base += 32) {
-    const int j = base + lane;
+  // blocks of 32 vectors whose box is farther than the screen distance (with
+  // a rounding margin) hold no vector that passes: they are skipped whole
+  const float box2 = R.screen_r2 * 1.001f + 1e-5f;
+  for (int bb0 = 0; bb0 < R.nblk; bb0 += 32) {
+    bool bkeep = false;
+    if (bb0 + lane < R.nblk) {
+      float q2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; k++)
+        if (k < d) {
+          const float lo = R.blk_lo[(int64_t)k * R.nblk + bb0 + lane];
+          const float hi = R.blk_hi[(int64_t)k * R.nblk + bb0 + lane];
+          const float t = fmaxf(fmaxf(lo - xs.hi[k], xs.hi[k] - hi), 0.f);
+          q2 = fmaf(t, t, q2);
+        }
+      bkeep = q2 <= box2;
+    }
+    unsigned bm = __ballot_sync(FULL, bkeep);
+  while (bm) {
+    const int j = (bb0 + __ffs(bm) - 1) * 32 + lane;
+    bm &= bm - 1;
     bool keep = false, strong = false;
     if (j < R.n) {
       float r2 = 0.f;
@@ -338,6 +441,7 @@ __device__ F64Acc warp_f64_pass(const MfRbfDev &R, const double *x, const double
       const int jj = pop32(qw, nw, lane);
       f32_weak_term<GRAD, D>(R, xs, jj, acc);
     }
+  }
   }
   __syncwarp();
   const int js = lane < ns ? qs[lane] : -1;
@@ -739,17 +843,15 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
   //    rounding margin) cannot pass; only the others get the exact
   //    point-to-segment test.
   int ns = 0, nw = 0;
-  const int total = src ? srcn : R.n;
   const float inv_dd = 1.f / dd32;
   const float pre = (sqrtf(R.screen_r2) + 0.5f * sqrtf(dd32)) * 1.0001f + 1e-5f, pre2 = pre * pre;
-  for (int base = 0; base < total; base += 32) {
-    const int i = base + lane;
+  // one round: lane tests vector j (gathered row for a group list, or the
+  // coalesced coordinate arrays) and the survivors are compacted
+  auto screen_round = [&](bool valid, int j, bool gathered) {
     bool keep = false, strong = false;
-    int j = 0;
-    if (i < total) {
+    if (valid) {
       float p[D], pd = 0.f;
-      if (src) {
-        j = src[i];
+      if (gathered) {
         const float4 *row = reinterpret_cast<const float4 *>(R.svhl + (int64_t)j * 16);
 #pragma unroll
         for (int k2 = 0; k2 < (D + 1) / 2; k2++) {
@@ -758,7 +860,6 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
           if (2 * k2 + 1 < D) p[2 * k2 + 1] = 2 * k2 + 1 < d ? v.z - x1hi[2 * k2 + 1] : 0.f;
         }
       } else {
-        j = i;
 #pragma unroll
         for (int k = 0; k < D; k++) p[k] = k < d ? (R.sv32[(int64_t)k * R.n + j] - x1hi[k]) : 0.f;
       }
@@ -789,6 +890,38 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
     if (keep && !strong && ns + cw < NEAR_CAP) near[NEAR_CAP - 1 - cw] = j;
     ns += __popc(ms);
     nw += __popc(mw);
+  };
+  if (src) {
+    for (int base = 0; base < srcn; base += 32) {
+      const int i = base + lane;
+      screen_round(i < srcn, i < srcn ? src[i] : 0, true);
+    }
+  } else {
+    // whole blocks of 32 vectors whose box lies beyond the prefilter ball
+    // (looser by 1e-3 for the rounding of the two paths) are skipped
+    const float box2 = pre2 * 1.001f + 1e-5f;
+    for (int bb0 = 0; bb0 < R.nblk; bb0 += 32) {
+      bool bkeep = false;
+      if (bb0 + lane < R.nblk) {
+        float q2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; k++)
+          if (k < d) {
+            const float m = fmaf(0.5f, dir32[k], x1hi[k]);
+            const float lo = R.blk_lo[(int64_t)k * R.nblk + bb0 + lane];
+            const float hi = R.blk_hi[(int64_t)k * R.nblk + bb0 + lane];
+            const float t = fmaxf(fmaxf(lo - m, m - hi), 0.f);
+            q2 = fmaf(t, t, q2);
+          }
+        bkeep = q2 <= box2;
+      }
+      unsigned bm = __ballot_sync(FULL, bkeep);
+      while (bm) {
+        const int jj = (bb0 + __ffs(bm) - 1) * 32 + lane;
+        bm &= bm - 1;
+        screen_round(jj < R.n, jj, false);
+      }
+    }
   }
   __syncwarp();
   const bool overflow = ns + nw > NEAR_CAP;

@@ -99,6 +99,10 @@ struct MfRbfDev {
   // row-major copies for gathers (one support vector per 64-byte row):
   const double *sv64r;   // [n][8] coordinates, zero-padded
   const float *svhl;     // [n][16] (hi, lo) FP32 pairs of the coordinates
+  // blocks of 32 consecutive vectors (the preparation orders the vectors
+  // along a Morton curve, so a block is spatially compact): FP32 box of sv32
+  const float *blk_lo, *blk_hi;  // [d][nblk]
+  int32_t nblk;
   double gamma, b;
   double sum_abs_alpha;
   float screen_r2;     // keep a term in the FP64 sum iff r^2 (FP32) <= screen_r2

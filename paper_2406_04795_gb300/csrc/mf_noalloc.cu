@@ -32,9 +32,11 @@ struct MfRbfStats {
   float max_abs_s;
   int bad;
 };
-__global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alpha, float *sv32,
-                              float *svlo32, double *sv64, float *alpha32, float *strong32,
-                              double *exp_tab, double *sv64r, float *svhl, MfRbfStats *st);
+__global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alpha, const int32_t *perm,
+                              float *sv32, float *svlo32, double *sv64, double *alpha64,
+                              float *alpha32, float *strong32, double *exp_tab, double *sv64r,
+                              float *svhl, MfRbfStats *st);
+__global__ void k_rbf_blocks(int d, int n, int nblk, const float *sv32, float *blo, float *bhi);
 __global__ void k_seed_vertices(MfFrame F, MfTraceBufs B, const double *seeds, int64_t n);
 __global__ void k_seed_edges(MfFrame F, MfTraceBufs B, const double *seeds, int64_t n);
 __global__ void k_expand_vertices(MfFrame F, MfTraceBufs B, uint64_t e0, uint64_t n);
@@ -194,7 +196,7 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
     TV = pow2_at_least(MV + MV / 3 + 1);
     TC = pow2_at_least(MC + MC / 3 + 1);
     cell_edges = MC * (uint64_t)((d + 1) * d / 2);
-    need = 256 * 35 + 64 * 8 + nb * 128 + nb * d * 16 + nb * 8 + TE * 12 + TV * 16 + TC * 8 + ME * (12 * d + 28) +
+    need = 256 * 38 + 64 * 8 + nb * 136 + ((nb + 31) / 32) * d * 8 + nb * d * 16 + nb * 8 + TE * 12 + TV * 16 + TC * 8 + ME * (12 * d + 28) +
            MV * (4 * d + 8) + MC * (5 * d + 8) + 8 + cell_edges * 8 + (MC / kScanTile + 2) * 8;
     if (need <= MF_NOALLOC_SCRATCH_BYTES || def < 1024) break;
   }
@@ -211,6 +213,10 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   double *exp_tab = (double *)cv.take(64 * 8);
   double *sv64r = (double *)cv.take(nb * 64);
   float *svhl = (float *)cv.take(nb * 64);
+  double *alpha64 = (double *)cv.take(nb * 8);
+  const int nblk = (n + 31) / 32;
+  float *blo = (float *)cv.take((size_t)nblk * d * 4);
+  float *bhi = (float *)cv.take((size_t)nblk * d * 4);
   MfTraceBufs B;
   memset(&B, 0, sizeof(B));
   B.etab_key = (unsigned long long *)cv.take(TE * 8);
@@ -242,8 +248,12 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
 
   // Support vectors: the same preparation as mf_trace.
   cudaMemsetAsync(stats, 0, sizeof(MfRbfStats), st);
-  k_prepare_rbf<<<(n + 255) / 256, 256, 0, st>>>(d, n, rbf->sv, rbf->alpha, sv32, svlo32, sv64,
-                                                  alpha32, strong32, exp_tab, sv64r, svhl, stats);
+  // vectors in the caller's order (no host pass): the block screen still
+  // holds, it just skips fewer blocks
+  k_prepare_rbf<<<(n + 255) / 256, 256, 0, st>>>(d, n, rbf->sv, rbf->alpha, nullptr, sv32, svlo32,
+                                                  sv64, alpha64, alpha32, strong32, exp_tab, sv64r,
+                                                  svhl, stats);
+  k_rbf_blocks<<<(nblk + 7) / 8, 256, 0, st>>>(d, n, nblk, sv32, blo, bhi);
   MfRbfStats hs;
   if (cudaMemcpyAsync(&hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
@@ -255,12 +265,15 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   R.sv32 = sv32;
   R.svlo32 = svlo32;
   R.sv64 = sv64;
-  R.alpha = rbf->alpha;
+  R.alpha = alpha64;
   R.alpha32 = alpha32;
   R.strong32 = strong32;
   R.exp_tab = exp_tab;
   R.sv64r = sv64r;
   R.svhl = svhl;
+  R.blk_lo = blo;
+  R.blk_hi = bhi;
+  R.nblk = nblk;
   R.gamma = rbf->gamma;
   R.b = rbf->b;
   R.sum_abs_alpha = hs.sum_abs_alpha;

@@ -277,53 +277,62 @@ __global__ void k_cells_enum(MfFrame F, MfTraceBufs B, uint64_t n_edges) {
   cells_enum_edge(F, B, e, lane);
 }
 
-// The n-cofaces j = lane, lane + 32, ... of edge e.
+// The n-cofaces j = lane, lane + 32, ... of edge e.  Orderings and
+// permutations are kept as 4-bit nibbles in 64-bit words, so the decode
+// needs no indexed arrays (they would live in local memory).
 __device__ __forceinline__ void cells_enum_edge(const MfFrame &F, const MfTraceBufs &B, uint64_t e,
                                                 int lane) {
   const int d = F.d;
   int32_t y[MF_MAXD];
   load_y(B.edge_y + e * d, d, y);
   const uint32_t S = B.edge_mask[e];
-  int ls[MF_MAXD + 1], lt[MF_MAXD + 1], n1 = 0, n2 = 0;
+  uint64_t ls = 0, lt = 0;  // the elements of p1 and of p2 (with d), ascending
+  int n1 = 0, n2 = 0;
   for (int i = 0; i <= d; i++) {
-    if (i < d && ((S >> i) & 1u)) ls[n1++] = i;
-    else lt[n2++] = i;
+    if (i < d && ((S >> i) & 1u)) ls |= (uint64_t)i << (4 * n1++);
+    else lt |= (uint64_t)i << (4 * n2++);
   }
   const uint32_t f1 = c_fact[n1], total = f1 * c_fact[n2];
   const unsigned long long dfact = c_fact[d];
   for (uint32_t j = lane; j < total; j += 32) {
-    int sigma[MF_MAXD + 1];
-    // Lehmer decode of each part
-    {
-      int pool[MF_MAXD + 1];
-      uint32_t r = j % f1;
-      for (int i = 0; i < n1; i++) pool[i] = ls[i];
-      for (int i = 0; i < n1; i++) {
-        const uint32_t f = c_fact[n1 - 1 - i], q = r / f;
+    // Lehmer decode of each part: sigma_i at nibble i
+    uint64_t sig = 0;
+    int at = 0;
+    uint32_t rr[2] = {j % f1, j / f1};
+#pragma unroll
+    for (int part = 0; part < 2; part++) {
+      uint64_t pool = part ? lt : ls;
+      const int np = part ? n2 : n1;
+      uint32_t r = rr[part];
+      for (int i = 0; i < np; i++) {
+        const uint32_t f = c_fact[np - 1 - i], q = r / f;
         r -= q * f;
-        sigma[i] = pool[q];
-        for (int k = q; k < n1 - 1 - i; k++) pool[k] = pool[k + 1];
-      }
-      r = j / f1;
-      for (int i = 0; i < n2; i++) pool[i] = lt[i];
-      for (int i = 0; i < n2; i++) {
-        const uint32_t f = c_fact[n2 - 1 - i], q = r / f;
-        r -= q * f;
-        sigma[n1 + i] = pool[q];
-        for (int k = q; k < n2 - 1 - i; k++) pool[k] = pool[k + 1];
+        sig |= ((pool >> (4 * q)) & 15ull) << (4 * at++);
+        const uint64_t low = q ? (pool & ((1ull << (4 * q)) - 1ull)) : 0ull;
+        pool = low | ((pool >> (4 * (q + 1))) << (4 * q));
       }
     }
+    // rotate so that d comes last: vertex z = y + e(sigma_0..sigma_{p-1}) - 1
     int p = 0;
-    while (sigma[p] != d) p++;
+    uint32_t inc = 0;
+    for (int i = 0; i <= d; i++) {
+      const int v = (int)((sig >> (4 * i)) & 15ull);
+      if (v == d) p = i;
+    }
+    for (int i = 0; i < p; i++) inc |= 1u << ((sig >> (4 * i)) & 15ull);
     int32_t z[MF_MAXD];
-    load_y(y, d, z);
-    for (int i = 0; i < p; i++) z[sigma[i]] += 1;
-    for (int k = 0; k < d; k++) z[k] -= 1;
-    int pi[MF_MAXD];
-    int m = 0;
-    for (int i = p + 1; i <= d; i++) pi[m++] = sigma[i];
-    for (int i = 0; i < p; i++) pi[m++] = sigma[i];
-    const unsigned long long key = (unsigned long long)perm_rank(pi, d) + dfact * mf_vertex_key(F, z);
+#pragma unroll
+    for (int k = 0; k < MF_MAXD; k++) z[k] = k < d ? y[k] + (int32_t)((inc >> k) & 1u) - 1 : 0;
+    // pi = sigma_{p+1..d}, sigma_{0..p-1}; its Lehmer rank
+    const uint64_t hi = sig >> (4 * (p + 1)), lo = p ? (sig & ((1ull << (4 * p)) - 1ull)) : 0ull;
+    const uint64_t pi = hi | (lo << (4 * (d - p)));
+    uint32_t used = 0, rank = 0;
+    for (int i = 0; i < d; i++) {
+      const uint32_t v = (uint32_t)((pi >> (4 * i)) & 15ull);
+      rank += (uint32_t)__popc(((1u << v) - 1u) & ~used) * c_fact[d - 1 - i];
+      used |= 1u << v;
+    }
+    const unsigned long long key = (unsigned long long)rank + dfact * mf_vertex_key(F, z);
     bool won;
     const uint64_t slot = mf_table_insert(B.ctab_key, B.ctab_mask, key, &won);
     if (slot == ~0ull) atomicOr(&B.cnt->err_table_full, 1u);
@@ -333,7 +342,7 @@ __device__ __forceinline__ void cells_enum_edge(const MfFrame &F, const MfTraceB
     if (idx >= B.max_cells) { atomicOr(&B.cnt->err_overflow, 1u); continue; }
     for (int k = 0; k < d; k++) {
       B.cell_y[idx * d + k] = z[k];
-      B.cell_perm[idx * d + k] = (uint8_t)pi[k];
+      B.cell_perm[idx * d + k] = (uint8_t)((pi >> (4 * k)) & 15ull);
     }
   }
 }
