@@ -101,7 +101,7 @@ __device__ T seg_box_d2(const T *a, const T *dl, const T *h) {
 }
 
 template <typename T>
-__device__ T seg_obstacle_dist(const CertObsT<T> &o, const T *pa, const T *pb) {
+__device__ __noinline__ T seg_obstacle_dist(const CertObsT<T> &o, const T *pa, const T *pb) {
   T a[3], b[3], dl[3];
   // local = R^T (p - t)
   const T wa[3] = {pa[0] - o.t[0], pa[1] - o.t[1], pa[2] - o.t[2]};

@@ -699,14 +699,17 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_points_f64(MfRbfDev R,
 // 3. FP64 Newton with a kept bracket [lo, hi] under the sign rule
 //    s = [f >= 0], over the same list (strong: FP64 exp; weak: FP32).  A
 //    step is final when |step| <= 1e-7, or on the first FP64 step when
-//    |g''| step^2 <= 5e-11 |g'| (the remaining Newton error is then below
-//    ~3e-11 in t).  Lists that overflow fall back to full per-point screening.
+//    |step| <= 1e-5 and |g''| step^2 <= 5e-11 |g'| (the remaining Newton
+//    error is then below ~1e-9 in t).  That first step takes g' from the
+//    last FP32 evaluation, carried to t by its g'', where the FP32 sum of
+//    g' terms had little cancellation; it then needs only the FP64 g.
+//    Lists that overflow fall back to full per-point screening.
 // ---------------------------------------------------------------------------
 #define ROOT_WARPS 8
 #define NEAR_CAP 1024
 
 struct Root32 {
-  float g, gp, gpp;
+  float g, gp, gpp, gpa;  // gpa: the sum of |g'| terms (cancellation measure)
 };
 
 // FP32 evaluation of g, g', g'' at t over the strong entries of the near
@@ -721,7 +724,7 @@ __device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const int *near
   const int lane = threadIdx.x & 31;
   const int d = dim_of<D>(R.d);
   const float g2 = (float)(R.gamma * 1.4426950408889634);
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s1a = 0.f;
   (void)nw;
   const int total = ns;
 #pragma unroll 2
@@ -747,38 +750,41 @@ __device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const int *near
     const float e = R.alpha32[j] * ex2_approx(-g2 * r2);
     s0 += e;
     s1 = fmaf(e, proj, s1);
+    s1a = fmaf(fabsf(e), fabsf(proj), s1a);
     s2 = fmaf(e * proj, proj, s2);
   }
   s0 = mf_warp_sum_f(s0);
   s1 = mf_warp_sum_f(s1);
+  s1a = mf_warp_sum_f(s1a);
   s2 = mf_warp_sum_f(s2);
   const float gm = (float)R.gamma;
   Root32 r;
   r.g = s0 + b32;
   r.gp = -2.f * gm * s1;
+  r.gpa = 2.f * gm * s1a;
   r.gpp = 4.f * gm * gm * s2 - 2.f * gm * dd32 * s0;
   return r;
 }
 
 // FP64 evaluation of g and g' at x over the near list (all lanes); xs is x
 // split into FP32 hi/lo parts for the weak terms.
-template <bool ALL_STRONG, int D>
+template <bool ALL_STRONG, bool GRAD, int D>
 __device__ __forceinline__ F64Acc root_eval64(const MfRbfDev &R, const int *near, int ns, int nw,
                                               const double *x, const double *dir, const Split32<D> &xs,
                                               unsigned long long *terms) {
   const int lane = threadIdx.x & 31;
   F64Acc acc = {0.0, 0.0, 0.f, 0.f, 0.f};
-  for (int i = lane; i < ns; i += 32) f64_term<true, D>(R, x, dir, near[i], acc);
+  for (int i = lane; i < ns; i += 32) f64_term<GRAD, D>(R, x, dir, near[i], acc);
   if (ALL_STRONG) {
-    for (int i = lane; i < nw; i += 32) f64_term<true, D>(R, x, dir, near[NEAR_CAP - 1 - i], acc);
+    for (int i = lane; i < nw; i += 32) f64_term<GRAD, D>(R, x, dir, near[NEAR_CAP - 1 - i], acc);
   } else {
-    for (int i = lane; i < nw; i += 32) f32_weak_term<true, D>(R, xs, near[NEAR_CAP - 1 - i], acc);
+    for (int i = lane; i < nw; i += 32) f32_weak_term<GRAD, D>(R, xs, near[NEAR_CAP - 1 - i], acc);
   }
   terms[0] += ns + (ALL_STRONG ? nw : 0);
   terms[1] += ALL_STRONG ? 0 : nw;
   acc.f = mf_warp_sum_d(acc.f) + (double)mf_warp_sum_f(acc.wf) + R.b;
   acc.weak = mf_warp_sum_f(acc.weak);
-  acc.g = -2.0 * R.gamma * (mf_warp_sum_d(acc.g) + (double)mf_warp_sum_f(acc.wg));
+  acc.g = GRAD ? -2.0 * R.gamma * (mf_warp_sum_d(acc.g) + (double)mf_warp_sum_f(acc.wg)) : 0.0;
   return acc;
 }
 
@@ -931,13 +937,20 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
   //    bracketed, from the linear interpolant of the end values
   float t32 = (float)f0 / ((float)f0 - (float)f1);
   if (!(t32 > 0.f && t32 < 1.f)) t32 = 0.5f;
-  float gpp = INFINITY;
+  // the last FP32 evaluation: g'', g', t, and whether its g' is trusted
+  float gpp = INFINITY, gp32 = 0.f, t_eval = 0.f;
+  bool gp_ok = false;
   if (!overflow) {
     const float b32 = (float)R.b;
     float lo = 0.f, hi = 1.f;
     for (int it = 0; it < 12; it++) {
       const Root32 r = root_eval32<D>(R, near, ns, nw, x1hi, x1lo, dir32, dd32, b32, t32);
       gpp = r.gpp;
+      gp32 = r.gp;
+      t_eval = t32;
+      // per-term FP32 errors stay below ~1e-5 relative, so with at most 4x
+      // cancellation g' is good to ~5e-5
+      gp_ok = r.gpa <= 4.f * fabsf(r.gp);
       if ((r.g >= 0.f) == s1) lo = t32; else hi = t32;
       const float den = 2.f * r.gp * r.gp - r.g * r.gpp;
       const bool halley = den > 0.f;
@@ -966,12 +979,24 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
     }
     __syncwarp();
     F64Acc a;
+    // The first step reuses the FP32 stage's g', carried to t by its g''
+    // (relative error below ~5e-5 when the FP32 sum had little
+    // cancellation: a final step of at most 1e-5 then errs by < 1e-9);
+    // later steps take the FP64 g'.
+    const double gp_est = (double)gp32 + (double)gpp * (t - (double)t_eval);
+    const bool reuse = it == 0 && !overflow && gp_ok && gp32 != 0.f && isfinite(gp_est) &&
+                       fabs(gp_est) > 0.5 * fabs((double)gp32);
     if (overflow) {
       a = warp_f64<true, D>(R, x, dir, qs, qw, terms);
-    } else {
-      a = root_eval64<false, D>(R, near, ns, nw, x, dir, xs, terms);
+    } else if (reuse) {
+      a = root_eval64<false, false, D>(R, near, ns, nw, x, dir, xs, terms);
       if ((double)a.weak * 1.01 * R.weak_rel > R.weak_limit)
-        a = root_eval64<true, D>(R, near, ns, nw, x, dir, xs, terms);
+        a = root_eval64<true, false, D>(R, near, ns, nw, x, dir, xs, terms);
+      a.g = gp_est;
+    } else {
+      a = root_eval64<false, true, D>(R, near, ns, nw, x, dir, xs, terms);
+      if ((double)a.weak * 1.01 * R.weak_rel > R.weak_limit)
+        a = root_eval64<true, true, D>(R, near, ns, nw, x, dir, xs, terms);
     }
     evals++;
     if (a.f == 0.0) break;
@@ -982,7 +1007,7 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
     const double step = fabs(tn - t);
     t = tn;
     if (step <= tol || step <= 1e-7 || hi - lo <= 9.094947017729282e-13 ||
-        (it == 0 && gpp64 * step * step <= 5e-11 * fabs(a.g)))
+        (it == 0 && step <= 1e-5 && gpp64 * step * step <= 5e-11 * fabs(a.g)))
       break;
   }
   if (lane == 0) B.edge_t[e] = t;
