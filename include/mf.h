@@ -169,6 +169,16 @@ int mf_locate(mf_ctx *ctx, int32_t d, double lambda, const double *offset_host,
 int mf_domain_table(int32_t d, double lambda, const mf_domain *dom, int32_t *smin, int32_t *span,
                     int32_t *tab, int64_t cap);
 
+/* The 64-bit vertex keys of the tracing hash tables (host only, no GPU
+ * needed).  y: host [n][d] lattice vertices; keys: host [n]; in_range: host
+ * [n] or NULL, 1 where y lies inside the key packing (keys of such vertices
+ * are distinct), else 0 (the key aliases another vertex).  The packing covers
+ * every vertex within three lattice steps of the box; edge keys are
+ * key * 2^d + mask and cell keys key * d! + rank.  MF_ERR_DOMAIN when edge or
+ * cell keys of this domain and lambda would not fit 64 bits. */
+int mf_vertex_keys(int32_t d, double lambda, const mf_domain *dom, const int32_t *y, int64_t n,
+                   uint64_t *keys, uint8_t *in_range);
+
 /* f at n arbitrary points (the RBF kernel evaluation of the traced path).
  * q: device [n][d]; f_out: device [n].  precision as in mf_trace_opts; the
  * mixed paths apply the same FP64 recheck band (band <= 0 means 1e-3). */

@@ -125,6 +125,52 @@ __device__ __noinline__ T seg_obstacle_dist(const CertObsT<T> &o, const T *pa, c
   return dist > (T)0 ? dist : (T)0;
 }
 
+// Lower bound on the distance from segment [pa, pb] to an obstacle, in FP32
+// (eta: a bound on this routine's own rounding of the squared distance).
+// Box: in the box frame F(t) = sum_i max(0, |a_i + t dl_i| - h_i)^2 is convex
+// and C^1 in t; three clamped Newton steps on F' from the projection of the
+// box centre reach, or come near, its minimiser t*, and convexity gives
+// F(t*) >= F(t) - |F'(t)| (t or 1 - t), whatever t is.  Every lane does the
+// same work (no breakpoint sort, no divergence).  Sphere: the exact distance.
+__device__ __forceinline__ float seg_obstacle_lb32(const CertObsT<float> &o, const float *pa,
+                                                   const float *pb, float eta) {
+  const float wa[3] = {pa[0] - o.t[0], pa[1] - o.t[1], pa[2] - o.t[2]};
+  const float wb[3] = {pb[0] - o.t[0], pb[1] - o.t[1], pb[2] - o.t[2]};
+  float a[3], dl[3];
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    a[i] = o.R[i] * wa[0] + o.R[3 + i] * wa[1] + o.R[6 + i] * wa[2];
+    dl[i] = (o.R[i] * wb[0] + o.R[3 + i] * wb[1] + o.R[6 + i] * wb[2]) - a[i];
+  }
+  const float dd = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
+  float t = 0.f;
+  if (dd > 0.f) t = fminf(fmaxf(-(a[0] * dl[0] + a[1] * dl[1] + a[2] * dl[2]) / dd, 0.f), 1.f);
+  if (o.type != MF_BOX) {
+    const float c0 = fmaf(t, dl[0], a[0]), c1 = fmaf(t, dl[1], a[1]), c2 = fmaf(t, dl[2], a[2]);
+    return fmaxf(sqrtf(c0 * c0 + c1 * c1 + c2 * c2) - o.h[0], 0.f);
+  }
+  float F = 0.f, G = 0.f;  // F(t) and F'(t) / 2
+#pragma unroll
+  for (int it = 0; it <= 3; it++) {
+    float H = 0.f;  // F''(t) / 2
+    F = 0.f;
+    G = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      const float p = fmaf(t, dl[i], a[i]);
+      const float q = fabsf(p) - o.h[i];
+      if (q > 0.f) {
+        F = fmaf(q, q, F);
+        G = fmaf(copysignf(q, p), dl[i], G);
+        H = fmaf(dl[i], dl[i], H);
+      }
+    }
+    if (it < 3 && H > 0.f) t = fminf(fmaxf(t - G / H, 0.f), 1.f);
+  }
+  const float lbF = F - 2.f * fabsf(G) * (G > 0.f ? t : 1.f - t) - eta;
+  return lbF > 0.f ? sqrtf(lbF) : 0.f;
+}
+
 // The link loops stay rolled: unrolling them per link count inlines the
 // distance routines once per link and pass, which overflows the instruction
 // cache (measured: 45 no-instruction stall cycles per issue).
@@ -220,21 +266,24 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const d
     if (upto > done) done = upto;
   };
   // margin = max over (link, obstacle) of radius - distance.  Every pair first
-  // gets the same distance computed in FP32 from the FP32 chain; minus a slack
-  // of 1e-4 (1 + the largest coordinate), far above the FP32 rounding of the
-  // chain and the distance (about 1e-5 of that scale), it is a lower bound lb
-  // on the true distance, and radius - lb an upper bound ub on the pair's
-  // margin.  The pair with the largest ub is evaluated in FP64; the others
-  // only if the second-largest ub exceeds that exact margin, and then only
-  // those whose ub does.
+  // gets a lower bound on its distance in FP32 from the FP32 chain
+  // (seg_obstacle_lb32); minus a slack of 1e-4 (1 + the largest coordinate),
+  // far above the FP32 rounding of the chain (about 1e-5 of that scale), it
+  // bounds the true distance from below, and radius - bound is an upper
+  // bound ub on the pair's margin.  The pair with the largest ub is evaluated
+  // exactly (FP64 chain to its link, FP64 distance); the others only if the
+  // second-largest ub exceeds that exact margin, and then only those whose
+  // ub does.  The result is the exact maximum.
   auto upper = [&](int i, int k) -> float {
     const float *a = &org32[3 * i], *b = &org32[3 * i + 3];
-    const float dist = seg_obstacle_dist<float>(sof[k], a, b);
     float scale = 1.f;
 #pragma unroll
     for (int c = 0; c < 3; c++)
       scale = fmaxf(scale, fmaxf(fmaxf(fabsf(a[c]), fabsf(b[c])), fabsf(sof[k].t[c]) + sof[k].h[c]));
-    return (float)srad[i] - (dist - 1e-4f * (1.f + scale));
+    // local coordinates are below 2 scale: the bound's own rounding of the
+    // squared distance stays far below 4e-5 (1 + scale)^2
+    const float eta = 4e-5f * (1.f + scale) * (1.f + scale);
+    return (float)srad[i] - (seg_obstacle_lb32(sof[k], a, b, eta) - 1e-4f * (1.f + scale));
   };
   float ub1 = -INFINITY, ub2 = -INFINITY;
   int bi = -1, bk = -1;

@@ -2,6 +2,7 @@
 // translation units: the lattice frame of one trace, integer simplex keys,
 // open-addressing hash tables, and the trace's device counters.
 #pragma once
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -11,14 +12,23 @@
 
 // Lattice frame of one trace: the Ã_d realisation x = lam * (y - c * sum(y)) + o
 // (Sec. II-B; L = I - c 1 1^T, c = (1 - 1/sqrt(d+1))/d), the closed C-space box,
-// and the mixed-radix packing of lattice vertices into 64-bit keys.
+// and the packing of lattice vertices into 64-bit keys.
 struct MfFrame {
   int32_t d;
   double lam, c, cinv;  // cinv = c * sqrt(d+1): L^-1 = I + cinv 1 1^T
   double o[MF_MAXD], lo[MF_MAXD], hi[MF_MAXD];
-  int32_t ymin[MF_MAXD];    // lowest encodable lattice coordinate per axis
-  int32_t range[MF_MAXD];   // encodable values per axis
-  uint64_t stride[MF_MAXD]; // mixed-radix place value per axis
+  int32_t ymin[MF_MAXD];    // bounding box of the box's lattice coordinates,
+  int32_t range[MF_MAXD];   // with a margin of 3 (domain-table search range)
+  // Vertex keys, a sheared mixed radix: with s = sum(y) and
+  // q(s) = floor(s * qc / 2^32) ~ c s, the digits are s - kmin_s and
+  // y_i - q(s) - zmin[i] for i < d-1 (y_{d-1} follows from s).  y_i - q(s)
+  // tracks (x_i - o_i) / lam, so the key space spans the box itself, not the
+  // bounding box of its lattice coordinates (smaller by ~(1 + d cinv)^d / sqrt(d+1)).
+  uint32_t qc;
+  int32_t kmin_s, kspan_s;
+  int32_t zmin[MF_MAXD];
+  uint64_t kstride[MF_MAXD];  // place value of digit i < d-1
+  uint64_t sstride;           // place value of the s digit
   // Optional exact domain table: for s = sum(y) in [smin, smin + sspan) and
   // each axis i, the interval of y_i whose x_i (computed as mf_vertex_x does)
   // lies in [lo_i, hi_i].  NULL: the domain test evaluates x in FP64.
@@ -164,7 +174,7 @@ struct MfSlotState {  // breadth-first progress of one trace
 };
 
 struct MfBatchPlan {  // per-step work prefixes over the slots
-  unsigned long long px[MF_MAX_SLOTS + 1];  // expansion items (edges << d)
+  unsigned long long px[MF_MAX_SLOTS + 1];  // edges of this expansion chunk
   unsigned long long pv[MF_MAX_SLOTS + 1];  // vertices to evaluate
   unsigned long long pr[MF_MAX_SLOTS + 1];  // vertices to re-check in FP64
   unsigned long long pe[MF_MAX_SLOTS + 1];  // traced edges (roots, cells)
@@ -235,20 +245,81 @@ __device__ __forceinline__ bool mf_vertex_in(const MfFrame &F, const int32_t *y)
   return mf_in_box(F, x);
 }
 
-__device__ __forceinline__ unsigned long long mf_vertex_key(const MfFrame &F, const int32_t *y) {
-  unsigned long long k = 0;
+// Vertex key (the packing described at MfFrame).  Unique over the vertices
+// the kernels key: those within one lattice step of a point of the box.
+__host__ __device__ __forceinline__ unsigned long long mf_vertex_key(const MfFrame &F,
+                                                                     const int32_t *y) {
+  // |s| < 2^30 on encodable vertices, so s, q and every digit fit 32 bits
+  int s = 0;
+#ifdef __CUDA_ARCH__
 #pragma unroll
+#endif
   for (int i = 0; i < MF_MAXD; i++)
-    if (i < F.d) k += (unsigned long long)(uint32_t)(y[i] - F.ymin[i]) * F.stride[i];
+    if (i < F.d) s += y[i];
+  const int q = (int)(((long long)s * (long long)F.qc) >> 32);  // floor: arithmetic shift
+  unsigned long long k = (unsigned long long)(uint32_t)(s - F.kmin_s) * F.sstride;
+#ifdef __CUDA_ARCH__
+#pragma unroll
+#endif
+  for (int i = 0; i < MF_MAXD - 1; i++)
+    if (i < F.d - 1) k += (unsigned long long)(uint32_t)(y[i] - q - F.zmin[i]) * F.kstride[i];
   return k;
 }
 
-__device__ __forceinline__ bool mf_vertex_encodable(const MfFrame &F, const int32_t *y) {
-  bool ok = true;
-#pragma unroll
-  for (int i = 0; i < MF_MAXD; i++)
-    if (i < F.d) ok = ok && (y[i] >= F.ymin[i]) && (y[i] - F.ymin[i] < F.range[i]);
-  return ok;
+// Host: is y inside the packing's digit ranges (its key then unique)?
+static inline bool mf_vertex_in_packing(const MfFrame &F, const int32_t *y) {
+  long long s = 0;
+  for (int i = 0; i < F.d; i++) s += y[i];
+  if (s < F.kmin_s || s - F.kmin_s >= F.kspan_s) return false;
+  const long long q = (s * (long long)F.qc) >> 32;
+  for (int i = 0; i < F.d - 1; i++) {
+    const long long z = (long long)y[i] - q - F.zmin[i];
+    const long long next = i + 1 < F.d - 1 ? (long long)F.kstride[i + 1] : (long long)F.sstride;
+    if (z < 0 || z >= next / (long long)F.kstride[i]) return false;
+  }
+  return true;
+}
+
+// Host: sets the key packing of a frame whose lattice and box are set; false
+// when vertex, edge (vkey 2^d + mask) or cell (d! vkey + rank) keys would not
+// fit 64 bits.  Every vertex the kernels key lies within one lattice step
+// (|dy_i| <= 1) of a point p of the box; the packing covers three.  With
+// u = (p - o) / lam in [A, B] and s' = sqrt(d+1) sum(u), such a vertex has
+// y_i - c s within 2k of u_i (k steps, d c < 1), y_i - q(s) within [-e, 1 + e]
+// of that, and s within d k of s': margins 8 and 9 on the digits, 3d + 2 on s.
+static inline bool mf_frame_pack_keys(MfFrame *F) {
+  const int d = F->d;
+  F->qc = (uint32_t)std::llround(F->c * 4294967296.0);  // c < 1
+  double sa = 0.0, sb = 0.0;
+  long long zmin[MF_MAXD], zr[MF_MAXD];
+  for (int i = 0; i < d; i++) {
+    const double A = (F->lo[i] - F->o[i]) / F->lam, B = (F->hi[i] - F->o[i]) / F->lam;
+    if (!(std::fabs(A) < 1e9 && std::fabs(B) < 1e9)) return false;
+    zmin[i] = (long long)std::floor(A) - 8;
+    zr[i] = (long long)std::ceil(B) + 9 - zmin[i] + 1;
+    sa += A;
+    sb += B;
+  }
+  const double r = std::sqrt((double)(d + 1));
+  const long long s0 = (long long)std::floor(r * sa) - 3 * d - 2;
+  const long long s1 = (long long)std::ceil(r * sb) + 3 * d + 2;
+  if (s0 < -(1ll << 29) || s1 > (1ll << 29)) return false;  // s, q and digits fit int32
+  F->kmin_s = (int32_t)s0;
+  F->kspan_s = (int32_t)(s1 - s0 + 1);
+  unsigned __int128 prod = 1;
+  for (int i = 0; i < d - 1; i++) {
+    F->zmin[i] = (int32_t)zmin[i];
+    F->kstride[i] = (uint64_t)prod;
+    prod *= (unsigned __int128)zr[i];
+    if (prod > ((unsigned __int128)1 << 62)) return false;
+  }
+  F->sstride = (uint64_t)prod;
+  prod *= (unsigned __int128)(s1 - s0 + 1);
+  if (prod > ((unsigned __int128)1 << 62)) return false;
+  unsigned __int128 fact = 1;
+  for (int i = 2; i <= d; i++) fact *= i;
+  const unsigned __int128 lim = ((unsigned __int128)1 << 64) - 2;
+  return !((prod << d) > lim || prod * fact > lim);
 }
 
 // Edge (y, p1) with p1 a non-empty mask over {0..d-1}: key = vidx * 2^d + p1.

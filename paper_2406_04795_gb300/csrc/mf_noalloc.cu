@@ -132,7 +132,6 @@ int frame_for(int d, double lam, const mf_domain *dom, MfFrame *F) {
     slo += dom->lo[j] - dom->offset[j];
     shi += dom->hi[j] - dom->offset[j];
   }
-  unsigned __int128 prod = 1;
   for (int i = 0; i < d; i++) {
     const double a = ((dom->lo[i] - dom->offset[i]) + F->cinv * slo) / lam;
     const double b = ((dom->hi[i] - dom->offset[i]) + F->cinv * shi) / lam;
@@ -140,15 +139,8 @@ int frame_for(int d, double lam, const mf_domain *dom, MfFrame *F) {
     const long long ymin = (long long)std::floor(a) - 3, ymax = (long long)std::ceil(b) + 3;
     F->ymin[i] = (int32_t)ymin;
     F->range[i] = (int32_t)(ymax - ymin + 1);
-    F->stride[i] = (uint64_t)prod;
-    prod *= (unsigned __int128)F->range[i];
-    if (prod > ((unsigned __int128)1 << 62)) return MF_ERR_DOMAIN;
   }
-  unsigned __int128 fact = 1;
-  for (int i = 2; i <= d; i++) fact *= i;
-  const unsigned __int128 lim = ((unsigned __int128)1 << 64) - 2;
-  if ((prod << d) > lim || prod * fact > lim) return MF_ERR_DOMAIN;
-  return MF_OK;
+  return mf_frame_pack_keys(F) ? MF_OK : MF_ERR_DOMAIN;
 }
 
 int sync_read(MfCounters *h, const MfCounters *d, cudaStream_t st) {
@@ -315,7 +307,7 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   while (fe > fs) {
     for (uint64_t a = fs; a < fe; a += cap) {
       const uint64_t m = fe - a < cap ? fe - a : cap;
-      const unsigned g = (unsigned)(((m << d) + 255) / 256);
+      const unsigned g = (unsigned)((m + 255) / 256);  // a warp per 32 edges, 8 per block
       k_expand_vertices<<<g, 256, 0, st>>>(F, B, a, m);
       eval();
       k_expand_edges<<<g, 256, 0, st>>>(F, B, a, m);

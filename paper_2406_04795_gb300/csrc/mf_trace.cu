@@ -10,12 +10,12 @@
 //                while level L-1 was expanded, so the list is also the queue.
 //
 // One BFS level, per frontier chunk of <= batch_cap edges:
-//   k_expand_vertices  thread per (edge, M), M a non-empty mask over {0..d-1}:
-//                      the new vertex w of every 2-simplex coface (query type 3)
-//                      is inserted into the vertex table; first inserters append
+//   k_expand_vertices  warp per 32 edges, lane per coface item (the new
+//                      vertex w of one 2-simplex coface, query type 3): w is
+//                      inserted into the vertex table; first inserters append
 //                      it to the vertex list.
 //   eval               f at the newly appended vertices (FP64 or mixed).
-//   k_expand_edges     same threads: sign of f(w) decides which of the coface's
+//   k_expand_edges     same items: sign of f(w) decides which of the coface's
 //                      two edges through w crosses (query type 4); insert it into
 //                      the edge table; first inserters append it to the edge list.
 #include <algorithm>
@@ -157,94 +157,154 @@ __global__ void k_seed_edges(MfFrame F, MfTraceBufs B, const double *seeds, int6
 //   M a proper subset of S : triangle (y, (M, S\M, p2)),          new vertex y + e(M)
 //   M a subset of T        : triangle (y, (S, M, rest)),          new vertex y + e(S) + e(M)
 //                            triangle (y - e(M), (M, S, rest)),    new vertex y - e(M)
+// Each new vertex is one work item: 2^|S| - 2 + 2 (2^|T| - 1) per edge.
 // ---------------------------------------------------------------------------
-// Visits the new vertices of the cofaces of edge e selected by mask M;
-// returns how many of them lie outside the box.
-__device__ __forceinline__ unsigned expand_vertices_item(const MfFrame &F, const MfTraceBufs &B,
-                                                         uint64_t e, uint32_t M) {
-  const int d = F.d;
-  int32_t y[MF_MAXD], w[MF_MAXD];
-  load_y(B.edge_y + e * d, d, y);
-  const uint32_t S = B.edge_mask[e];
-  unsigned nb = 0;
-  if ((M & ~S) == 0 && M != S) {
-    load_y(y, d, w);
-    mf_add_mask(d, w, M, 1);
-    if (vertex_in(F, w)) visit_vertex(F, B, w); else nb++;
-  }
-  if ((M & S) == 0) {
-    load_y(y, d, w);
-    mf_add_mask(d, w, S | M, 1);
-    if (vertex_in(F, w)) visit_vertex(F, B, w); else nb++;
-    load_y(y, d, w);
-    mf_add_mask(d, w, M, -1);
-    if (vertex_in(F, w)) visit_vertex(F, B, w); else nb++;
-  }
-  return nb;
+__device__ __forceinline__ uint32_t expand_item_count(uint32_t S, int d) {
+  const int k = __popc(S);
+  return (1u << k) - 2u + 2u * ((1u << (d - k)) - 1u);
 }
 
-__global__ void k_expand_vertices(MfFrame F, MfTraceBufs B, uint64_t e0, uint64_t n) {
+// The v-th subset of `mask` in binary counting order: bit j of v selects the
+// j-th lowest set bit of mask.
+__device__ __forceinline__ uint32_t deposit_bits(uint32_t v, uint32_t mask) {
+  uint32_t r = 0;
+  for (uint32_t m = mask; m && v; m &= m - 1u, v >>= 1)
+    if (v & 1u) r |= m & (0u - m);
+  return r;
+}
+
+// Item r of edge (y, S): kind 0 -> vertex y + e(M), M the (r+1)-th subset of
+// S (r < 2^|S| - 2, so M is proper and non-empty); otherwise with
+// r' = r - (2^|S| - 2), M is the (r'/2 + 1)-th subset of T and kind 1 ->
+// y + e(S) + e(M) (r' even), kind 2 -> y - e(M) (r' odd).
+__device__ __forceinline__ uint32_t expand_item_decode(uint32_t S, int d, uint32_t r, int *kind) {
+  const uint32_t nsub = (1u << __popc(S)) - 2u;
+  if (r < nsub) {
+    *kind = 0;
+    return deposit_bits(r + 1u, S);
+  }
+  r -= nsub;
+  *kind = 1 + (int)(r & 1u);
+  return deposit_bits((r >> 1) + 1u, ~S & ((1u << d) - 1u));
+}
+
+// Visits the new vertex of one item; returns 1 if it lies outside the box.
+__device__ __forceinline__ unsigned expand_vertices_item(const MfFrame &F, const MfTraceBufs &B,
+                                                         uint64_t e, uint32_t S, int kind,
+                                                         uint32_t M) {
   const int d = F.d;
-  const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  const uint64_t ei = tid >> d;
-  const uint32_t M = (uint32_t)(tid & ((1u << d) - 1u));
-  if (ei >= n || M == 0) return;
-  const unsigned nb = expand_vertices_item(F, B, e0 + ei, M);
-  if (nb) atomicAdd(&B.cnt->n_boundary, (unsigned long long)nb);
+  int32_t w[MF_MAXD];
+  load_y(B.edge_y + e * d, d, w);
+  if (kind == 0) mf_add_mask(d, w, M, 1);
+  else if (kind == 1) mf_add_mask(d, w, S | M, 1);
+  else mf_add_mask(d, w, M, -1);
+  if (vertex_in(F, w)) {
+    visit_vertex(F, B, w);
+    return 0;
+  }
+  return 1;
 }
 
 // Under the sign rule s = [f >= 0] a crossing triangle has exactly two
 // crossing edges (Sec. IV-A): the parent and the one joining the new vertex w
 // to the parent end whose sign differs from s(w).
 __device__ __forceinline__ void expand_edges_item(const MfFrame &F, const MfTraceBufs &B,
-                                                  uint64_t e, uint32_t M);
-
-__global__ void k_expand_edges(MfFrame F, MfTraceBufs B, uint64_t e0, uint64_t n) {
+                                                  uint64_t e, uint32_t S, int kind, uint32_t M) {
   const int d = F.d;
-  const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  const uint64_t ei = tid >> d;
-  const uint32_t M = (uint32_t)(tid & ((1u << d) - 1u));
-  if (ei >= n || M == 0) return;
-  expand_edges_item(F, B, e0 + ei, M);
+  int32_t y[MF_MAXD], w[MF_MAXD];
+  load_y(B.edge_y + e * d, d, y);
+  load_y(y, d, w);
+  if (kind == 0) mf_add_mask(d, w, M, 1);
+  else if (kind == 1) mf_add_mask(d, w, S | M, 1);
+  else mf_add_mask(d, w, M, -1);
+  if (!vertex_in(F, w)) return;
+  const double f0 = B.edge_f[2 * e], f1 = B.edge_f[2 * e + 1];
+  const double fw = lookup_f(F, B, w);
+  const bool cross0 = (fw >= 0.0) != (f0 >= 0.0);
+  if (kind == 0) {
+    if (cross0) emit_edge(F, B, y, M, f0, fw);
+    else emit_edge(F, B, w, S & ~M, fw, f1);
+  } else if (kind == 1) {
+    if (cross0) {
+      emit_edge(F, B, y, S | M, f0, fw);
+    } else {
+      mf_add_mask(d, y, S, 1);
+      emit_edge(F, B, y, M, f1, fw);
+    }
+  } else {
+    if (cross0) emit_edge(F, B, w, M, fw, f0);
+    else emit_edge(F, B, w, M | S, fw, f1);
+  }
 }
 
-__device__ __forceinline__ void expand_edges_item(const MfFrame &F, const MfTraceBufs &B,
-                                                  uint64_t e, uint32_t M) {
+// Inclusive warp scan of the per-lane item counts into s_end[0..31]; returns
+// the warp's total.  Item j then belongs to the first lane o with
+// s_end[o] > j, as local item j - s_end[o - 1].
+__device__ __forceinline__ uint32_t expand_warp_scan(uint32_t c, uint32_t *s_end) {
+  const int lane = threadIdx.x & 31;
+  uint32_t inc = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  s_end[lane] = inc;
+  __syncwarp();
+  return __shfl_sync(0xffffffffu, inc, 31);
+}
+
+__device__ __forceinline__ int expand_owner(const uint32_t *s_end, uint32_t j, uint32_t *local) {
+  int o = 0;
+#pragma unroll
+  for (int step = 16; step; step >>= 1)
+    if (s_end[o + step - 1] <= j) o += step;
+  *local = j - (o ? s_end[o - 1] : 0u);
+  return o;
+}
+
+#define EXPAND_WARPS 8
+
+// Warp per 32 consecutive edges of [e0, e0 + n), lane per coface item, so
+// that no lane idles on masks that select no coface.
+template <bool EDGES>
+__device__ __forceinline__ void expand_warp(const MfFrame &F, const MfTraceBufs &B, uint64_t e0,
+                                            uint64_t n) {
+  __shared__ uint32_t s_end[EXPAND_WARPS][32], s_S[EXPAND_WARPS][32];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const uint64_t first = (blockIdx.x * (uint64_t)EXPAND_WARPS + wi) * 32;
+  if (first >= n) return;  // whole warp
   const int d = F.d;
-  int32_t y[MF_MAXD], w[MF_MAXD], u[MF_MAXD];
-  load_y(B.edge_y + e * d, d, y);
-  const uint32_t S = B.edge_mask[e];
-  const double f0 = B.edge_f[2 * e], f1 = B.edge_f[2 * e + 1];
-  const bool s0 = f0 >= 0.0;
-  if ((M & ~S) == 0 && M != S) {
-    load_y(y, d, w);
-    mf_add_mask(d, w, M, 1);
-    if (vertex_in(F, w)) {
-      const double fw = lookup_f(F, B, w);
-      if ((fw >= 0.0) != s0) emit_edge(F, B, y, M, f0, fw);
-      else emit_edge(F, B, w, S & ~M, fw, f1);
-    }
+  uint32_t S = 0, c = 0;
+  if (first + lane < n) {
+    S = B.edge_mask[e0 + first + lane];
+    c = S ? expand_item_count(S, d) : 0u;
   }
-  if ((M & S) == 0) {
-    load_y(y, d, w);
-    mf_add_mask(d, w, S | M, 1);
-    if (vertex_in(F, w)) {
-      const double fw = lookup_f(F, B, w);
-      if ((fw >= 0.0) != s0) emit_edge(F, B, y, S | M, f0, fw);
-      else {
-        load_y(y, d, u);
-        mf_add_mask(d, u, S, 1);
-        emit_edge(F, B, u, M, f1, fw);
-      }
-    }
-    load_y(y, d, w);
-    mf_add_mask(d, w, M, -1);
-    if (vertex_in(F, w)) {
-      const double fw = lookup_f(F, B, w);
-      if ((fw >= 0.0) != s0) emit_edge(F, B, w, M, fw, f0);
-      else emit_edge(F, B, w, M | S, fw, f1);
-    }
+  s_S[wi][lane] = S;
+  const uint32_t total = expand_warp_scan(c, s_end[wi]);
+  unsigned nb = 0;
+  for (uint32_t j = lane; j < total; j += 32) {
+    uint32_t r;
+    const int o = expand_owner(s_end[wi], j, &r);
+    const uint32_t So = s_S[wi][o];
+    int kind;
+    const uint32_t M = expand_item_decode(So, d, r, &kind);
+    if (EDGES) expand_edges_item(F, B, e0 + first + o, So, kind, M);
+    else nb += expand_vertices_item(F, B, e0 + first + o, So, kind, M);
   }
+  if (!EDGES) {
+    nb = __reduce_add_sync(0xffffffffu, nb);
+    if (lane == 0 && nb) atomicAdd(&B.cnt->n_boundary, (unsigned long long)nb);
+  }
+}
+
+__global__ void __launch_bounds__(EXPAND_WARPS * 32) k_expand_vertices(MfFrame F, MfTraceBufs B,
+                                                                       uint64_t e0, uint64_t n) {
+  expand_warp<false>(F, B, e0, n);
+}
+
+__global__ void __launch_bounds__(EXPAND_WARPS * 32) k_expand_edges(MfFrame F, MfTraceBufs B,
+                                                                    uint64_t e0, uint64_t n) {
+  expand_warp<true>(F, B, e0, n);
 }
 
 // ---------------------------------------------------------------------------
@@ -475,7 +535,7 @@ __global__ void k_b_plan_expand(const MfSlot *slots, MfSlotState *st, MfBatchPla
       chunk = left < slots[t].cap ? left : slots[t].cap;
     }
     st[t].chunk_n = chunk;
-    cnt = chunk << slots[t].F.d;
+    cnt = chunk;
   }
   const unsigned long long ex = block_scan_u64(cnt, &total);
   if (t < n) P->px[t] = ex;
@@ -483,24 +543,45 @@ __global__ void k_b_plan_expand(const MfSlot *slots, MfSlotState *st, MfBatchPla
 }
 
 template <bool EDGES>
-__global__ void k_b_expand(const MfSlot *slots, const MfSlotState *st, const MfBatchPlan *P, int n) {
+__global__ void __launch_bounds__(EXPAND_WARPS * 32) k_b_expand(const MfSlot *slots,
+                                                                const MfSlotState *st,
+                                                                const MfBatchPlan *P, int n) {
+  __shared__ uint32_t s_end[EXPAND_WARPS][32], s_S[EXPAND_WARPS][32];
+  __shared__ int s_t[EXPAND_WARPS][32];
+  __shared__ unsigned long long s_e[EXPAND_WARPS][32];
   const unsigned long long total = P->px[n];
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long item = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-       item < total; item += stride) {
-    const int t = mf_slot_of(P->px, n, item);
-    const MfSlot &S = slots[t];
-    const int d = S.F.d;
-    const unsigned long long local = item - P->px[t];
-    const uint32_t M = (uint32_t)(local & ((1u << d) - 1u));
-    if (M == 0) continue;
-    const uint64_t e = st[t].cursor + (local >> d);
-    if (EDGES) {
-      expand_edges_item(S.F, S.B, e, M);
-    } else {
-      const unsigned nb = expand_vertices_item(S.F, S.B, e, M);
-      if (nb) atomicAdd(&S.B.cnt->n_boundary, (unsigned long long)nb);
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * EXPAND_WARPS;
+  for (unsigned long long g = blockIdx.x * (unsigned long long)EXPAND_WARPS + wi; g * 32 < total;
+       g += nwarps) {
+    const unsigned long long item = g * 32 + lane;
+    uint32_t S = 0, c = 0;
+    int t = 0;
+    unsigned long long e = 0;
+    if (item < total) {
+      t = mf_slot_of(P->px, n, item);
+      e = st[t].cursor + (item - P->px[t]);
+      S = slots[t].B.edge_mask[e];
+      c = S ? expand_item_count(S, slots[t].F.d) : 0u;
     }
+    s_S[wi][lane] = S;
+    s_t[wi][lane] = t;
+    s_e[wi][lane] = e;
+    const uint32_t nit = expand_warp_scan(c, s_end[wi]);
+    for (uint32_t j = lane; j < nit; j += 32) {
+      uint32_t r;
+      const int o = expand_owner(s_end[wi], j, &r);
+      const MfSlot &SL = slots[s_t[wi][o]];
+      const uint32_t So = s_S[wi][o];
+      int kind;
+      const uint32_t M = expand_item_decode(So, SL.F.d, r, &kind);
+      if (EDGES) {
+        expand_edges_item(SL.F, SL.B, s_e[wi][o], So, kind, M);
+      } else if (expand_vertices_item(SL.F, SL.B, s_e[wi][o], So, kind, M)) {
+        atomicAdd(&SL.B.cnt->n_boundary, 1ull);
+      }
+    }
+    __syncwarp();  // the next group overwrites this warp's shared entries
   }
 }
 
@@ -644,9 +725,9 @@ void mf_b_launch_expand(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, in
                         int sms, cudaStream_t s) {
   if (!edges) {
     k_b_plan_expand<<<1, MF_MAX_SLOTS, 0, s>>>(slots, st, P, n);
-    k_b_expand<false><<<sms * 8, 256, 0, s>>>(slots, st, P, n);
+    k_b_expand<false><<<sms * 8, EXPAND_WARPS * 32, 0, s>>>(slots, st, P, n);
   } else {
-    k_b_expand<true><<<sms * 8, 256, 0, s>>>(slots, st, P, n);
+    k_b_expand<true><<<sms * 8, EXPAND_WARPS * 32, 0, s>>>(slots, st, P, n);
   }
 }
 void mf_b_launch_plan_eval(const MfSlot *slots, MfBatchPlan *P, int n, bool recheck, cudaStream_t s) {
@@ -774,9 +855,9 @@ static uint64_t next_pow2(uint64_t x) {
   return p;
 }
 
-// Builds the frame: lattice constants, the box, and the key packing.  The box
-// maps under L^-1 to per-axis lattice ranges; a margin of 3 covers the
-// vertices of n-cofaces and rounding.  Fails if keys do not fit 64 bits.
+// Builds the frame: lattice constants, the box, the bounding box of its
+// lattice coordinates (the box under L^-1, margin 3; the domain table searches
+// it) and the key packing.  Fails if keys do not fit 64 bits.
 static int build_frame(mf_ctx *ctx, int d, double lam, const mf_domain *dom, MfFrame *F) {
   mf_frame_lattice(F, d, lam, dom->offset);
   double slo = 0.0, shi = 0.0;
@@ -789,7 +870,6 @@ static int build_frame(mf_ctx *ctx, int d, double lam, const mf_domain *dom, MfF
     slo += dom->lo[j] - dom->offset[j];
     shi += dom->hi[j] - dom->offset[j];
   }
-  unsigned __int128 prod = 1;
   for (int i = 0; i < d; i++) {
     const double a = ((dom->lo[i] - dom->offset[i]) + F->cinv * slo) / lam;
     const double b = ((dom->hi[i] - dom->offset[i]) + F->cinv * shi) / lam;
@@ -798,15 +878,8 @@ static int build_frame(mf_ctx *ctx, int d, double lam, const mf_domain *dom, MfF
     const long long ymin = (long long)std::floor(a) - 3, ymax = (long long)std::ceil(b) + 3;
     F->ymin[i] = (int32_t)ymin;
     F->range[i] = (int32_t)(ymax - ymin + 1);
-    F->stride[i] = (uint64_t)prod;
-    prod *= (unsigned __int128)F->range[i];
-    if (prod > ((unsigned __int128)1 << 62))
-      return mf_set_error(ctx, MF_ERR_DOMAIN, "lattice keys need more than 64 bits");
   }
-  unsigned __int128 fact = 1;
-  for (int i = 2; i <= d; i++) fact *= i;
-  const unsigned __int128 lim = ((unsigned __int128)1 << 64) - 2;
-  if ((prod << d) > lim || prod * fact > lim)
+  if (!mf_frame_pack_keys(F))
     return mf_set_error(ctx, MF_ERR_DOMAIN,
                         "edge/cell keys need more than 64 bits (domain too large for lambda)");
   return MF_OK;
@@ -1110,11 +1183,10 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
   while (fe > fs) {
     for (uint64_t a = fs; a < fe; a += cap) {
       const uint64_t n = std::min(cap, fe - a);
-      const uint64_t threads = n << d;
-      const unsigned g = (unsigned)((threads + 255) / 256);
+      const unsigned g = (unsigned)((n + EXPAND_WARPS * 32 - 1) / (EXPAND_WARPS * 32));
       {
         MfProfScope ps(ctx, MF_PH_EXPAND_V, st, 1, (int64_t)n);
-        k_expand_vertices<<<g, 256, 0, st>>>(F, B, a, n);
+        k_expand_vertices<<<g, EXPAND_WARPS * 32, 0, st>>>(F, B, a, n);
       }
       {
         MfProfScope ps(ctx, MF_PH_EVAL, st, mixed ? 3 : 2);
@@ -1122,7 +1194,7 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
       }
       {
         MfProfScope ps(ctx, MF_PH_EXPAND_E, st, 1, (int64_t)n);
-        k_expand_edges<<<g, 256, 0, st>>>(F, B, a, n);
+        k_expand_edges<<<g, EXPAND_WARPS * 32, 0, st>>>(F, B, a, n);
       }
     }
     rc = mf_cuda_check(ctx, cudaGetLastError(), "BFS kernels");
@@ -1222,4 +1294,18 @@ extern "C" int mf_trace_fetch(mf_ctx *ctx, mf_trace_out *out, void *stream) {
   if (!ctx->last.valid) return mf_set_error(ctx, MF_ERR_INVALID, "no trace result to fetch");
   cudaSetDevice(ctx->device);
   return copy_out(ctx, ctx->last, out, (cudaStream_t)stream);
+}
+
+extern "C" int mf_vertex_keys(int32_t d, double lambda, const mf_domain *dom, const int32_t *y,
+                              int64_t n, uint64_t *keys, uint8_t *in_range) {
+  if (d < 2 || d > MF_MAXD || !(lambda > 0.0) || !dom || n < 0 || (n > 0 && (!y || !keys)))
+    return MF_ERR_INVALID;
+  MfFrame F;
+  const int rc = build_frame(nullptr, d, lambda, dom, &F);
+  if (rc) return rc;
+  for (int64_t i = 0; i < n; i++) {
+    keys[i] = mf_vertex_key(F, y + i * d);
+    if (in_range) in_range[i] = mf_vertex_in_packing(F, y + i * d) ? 1 : 0;
+  }
+  return MF_OK;
 }

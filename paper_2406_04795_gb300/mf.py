@@ -36,7 +36,7 @@ EXPORTS = ("mf_ctx_create", "mf_ctx_destroy", "mf_last_error", "mf_ctx_bytes", "
            "mf_ctx_get_stats", "mf_trace_noalloc", "mf_trace_batch", "mf_domain_table",
            "mf_server_create", "mf_server_destroy", "mf_server_submit", "mf_server_step",
            "mf_server_status", "mf_server_fetch", "mf_server_done", "mf_autotune", "mf_ctx_set_tune",
-           "mf_ctx_get_tune")
+           "mf_ctx_get_tune", "mf_vertex_keys")
 
 MF_PHASES = 12
 PHASE_NAMES = ("prepare", "seeds", "expand_vertices", "eval", "expand_edges", "roots", "cells",
@@ -167,6 +167,8 @@ def load(build_if_missing: bool = True):
     L.mf_domain_table.restype = C.c_int
     L.mf_domain_table.argtypes = [C.c_int32, C.c_double, P(mf_domain), P(C.c_int32), P(C.c_int32),
                                   V, C.c_int64]
+    L.mf_vertex_keys.restype = C.c_int
+    L.mf_vertex_keys.argtypes = [C.c_int32, C.c_double, P(mf_domain), V, C.c_int64, V, V]
     L.mf_trace_batch.restype = C.c_int
     L.mf_trace_batch.argtypes = [V, C.c_int32, P(mf_rbf), P(mf_domain), P(mf_trace_opts),
                                  P(C.c_void_p), P(C.c_int64), P(mf_trace_out), V]
@@ -288,6 +290,20 @@ def mf_domain_table(d, lam, dom: mf_domain):
     if rc != MF_OK:
         raise MfError(rc, "mf_domain_table")
     return smin.value, tab
+
+
+def mf_vertex_keys(d, lam, dom: mf_domain, y):
+    """(keys uint64[n], in_range bool[n]) of lattice vertices y [n][d] under
+    the tracing tables' key packing (host only)."""
+    import numpy as np
+    y = np.ascontiguousarray(y, dtype=np.int32).reshape(-1, d)
+    keys = np.zeros(y.shape[0], dtype=np.uint64)
+    ok = np.zeros(y.shape[0], dtype=np.uint8)
+    rc = load().mf_vertex_keys(d, lam, C.byref(dom), y.ctypes.data_as(C.c_void_p), y.shape[0],
+                               keys.ctypes.data_as(C.c_void_p), ok.ctypes.data_as(C.c_void_p))
+    if rc != MF_OK:
+        raise MfError(rc, "mf_vertex_keys")
+    return keys, ok.astype(bool)
 
 
 def mf_trace_batch(ctx, rbfs, doms, opts, seed_ptrs, n_seeds, outs, stream=0, check=True):

@@ -55,6 +55,45 @@ def test_domain_table_matches_oracle_box_test(d, lam, box):
     del n_edge, cinv
 
 
+@pytest.mark.parametrize("d,lam,box", [(2, 0.1, 1.0), (3, 0.02, math.pi), (5, 0.05, math.pi),
+                                       (6, 0.03, math.pi), (6, 0.02, math.pi), (8, 0.3, 2.0)])
+def test_vertex_keys_unique_near_the_box(d, lam, box):
+    """Every vertex within three lattice steps of a point of the box lies in
+    the key packing, and distinct vertices get distinct keys."""
+    rng = np.random.default_rng(100 + d)
+    lo, hi = -box * np.ones(d), box * np.ones(d)
+    off = W.lattice_offset(d, lam)
+    dom = _dom(lo, hi, off)
+    # box points: uniform, on faces and at corners
+    pts = rng.uniform(lo, hi, size=(300, d))
+    k = rng.integers(0, d, size=300)
+    pts[np.arange(300), k] = np.where(rng.integers(0, 2, size=300), hi[k], lo[k])
+    corners = np.where(rng.integers(0, 2, size=(100, d)), hi, lo)
+    ys = []
+    for p in np.concatenate([pts, corners]):
+        y, _ = oracle.locate(d, lam, off, p)
+        y = np.array(y, dtype=np.int64)
+        for _ in range(40):
+            ys.append(y + rng.integers(-3, 4, size=d))
+        ys.append(y)
+    ys = np.unique(np.array(ys), axis=0)
+    keys, ok = mf.mf_vertex_keys(d, lam, dom, ys)
+    assert ok.all()
+    assert np.unique(keys).size == ys.shape[0]
+    # far outside: reported as outside the packing
+    _, ok_far = mf.mf_vertex_keys(d, lam, dom, ys[:5] + 10_000)
+    assert not ok_far.any()
+
+
+def test_vertex_keys_reject_too_fine_lattice():
+    d = 6
+    off = W.lattice_offset(d, 0.005)
+    dom = _dom(-math.pi * np.ones(d), math.pi * np.ones(d), off)
+    with pytest.raises(mf.MfError) as e:
+        mf.mf_vertex_keys(d, 0.005, dom, np.zeros((1, d), np.int32))
+    assert e.value.code == mf.MF_ERR_DOMAIN
+
+
 def _rank_main(rank, world, port, out_dir):
     import torch.distributed as dist
     from paper_2406_04795_gb300.scaling import reduce_timing
