@@ -10,6 +10,7 @@
 // piece (at most 7).  This extends App. A's sphere/box test (a sphere is the
 // zero-length capsule) to capsules.
 #include <cmath>
+#include <vector>
 
 #include "mf_internal.cuh"
 #include "mf_ctx.h"
@@ -100,8 +101,39 @@ __device__ T seg_box_d2(const T *a, const T *dl, const T *h) {
   return best;
 }
 
+// Exact distance from segment [a, a+dl] (box frame) to the box in FP64, from
+// a start t near the minimiser (the FP32 bound's): Newton steps on F' land on
+// the minimiser of the piece they are in, and convexity certifies the result,
+// min F >= F(t) - |F'(t)| (t or 1 - t).  When that leaves more than 2e-12 of
+// room in the distance, the breakpoint method decides.
+__device__ double seg_box_dist64(const double *a, const double *dl, const double *h, double t) {
+  double F = 0.0, G = 0.0;  // F(t) and F'(t) / 2
+  for (int it = 0;; it++) {
+    double H = 0.0;  // F''(t) / 2
+    F = 0.0;
+    G = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      const double p = fma(t, dl[i], a[i]);
+      const double q = fabs(p) - h[i];
+      if (q > 0.0) {
+        F = fma(q, q, F);
+        G = fma(copysign(q, p), dl[i], G);
+        H = fma(dl[i], dl[i], H);
+      }
+    }
+    if (it == 2 || !(H > 0.0)) break;
+    const double tn = fmin(fmax(t - G / H, 0.0), 1.0);
+    if (tn == t) break;
+    t = tn;
+  }
+  const double D = sqrt(F);
+  if (2.0 * fabs(G) * (G > 0.0 ? t : 1.0 - t) <= 2e-12 * D) return D;
+  return sqrt(seg_box_d2<double>(a, dl, h));
+}
+
 template <typename T>
-__device__ __noinline__ T seg_obstacle_dist(const CertObsT<T> &o, const T *pa, const T *pb) {
+__device__ __noinline__ T seg_obstacle_dist(const CertObsT<T> &o, const T *pa, const T *pb, T t0) {
   T a[3], b[3], dl[3];
   // local = R^T (p - t)
   const T wa[3] = {pa[0] - o.t[0], pa[1] - o.t[1], pa[2] - o.t[2]};
@@ -112,7 +144,7 @@ __device__ __noinline__ T seg_obstacle_dist(const CertObsT<T> &o, const T *pa, c
     b[i] = o.R[i] * wb[0] + o.R[3 + i] * wb[1] + o.R[6 + i] * wb[2];
     dl[i] = b[i] - a[i];
   }
-  if (o.type == MF_BOX) return sqrt(seg_box_d2<T>(a, dl, o.h));
+  if (o.type == MF_BOX) return seg_box_dist64(a, dl, o.h, t0);
   // sphere at the local origin: clamped projection of the centre
   const T dd = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
   T t = 0;
@@ -133,7 +165,7 @@ __device__ __noinline__ T seg_obstacle_dist(const CertObsT<T> &o, const T *pa, c
 // F(t*) >= F(t) - |F'(t)| (t or 1 - t), whatever t is.  Every lane does the
 // same work (no breakpoint sort, no divergence).  Sphere: the exact distance.
 __device__ __forceinline__ float seg_obstacle_lb32(const CertObsT<float> &o, const float *pa,
-                                                   const float *pb, float eta) {
+                                                   const float *pb, float eta, float *tmin) {
   const float wa[3] = {pa[0] - o.t[0], pa[1] - o.t[1], pa[2] - o.t[2]};
   const float wb[3] = {pb[0] - o.t[0], pb[1] - o.t[1], pb[2] - o.t[2]};
   float a[3], dl[3];
@@ -146,6 +178,7 @@ __device__ __forceinline__ float seg_obstacle_lb32(const CertObsT<float> &o, con
   float t = 0.f;
   if (dd > 0.f) t = fminf(fmaxf(-(a[0] * dl[0] + a[1] * dl[1] + a[2] * dl[2]) / dd, 0.f), 1.f);
   if (o.type != MF_BOX) {
+    *tmin = t;
     const float c0 = fmaf(t, dl[0], a[0]), c1 = fmaf(t, dl[1], a[1]), c2 = fmaf(t, dl[2], a[2]);
     return fmaxf(sqrtf(c0 * c0 + c1 * c1 + c2 * c2) - o.h[0], 0.f);
   }
@@ -167,8 +200,32 @@ __device__ __forceinline__ float seg_obstacle_lb32(const CertObsT<float> &o, con
     }
     if (it < 3 && H > 0.f) t = fminf(fmaxf(t - G / H, 0.f), 1.f);
   }
+  *tmin = t;
   const float lbF = F - 2.f * fabsf(G) * (G > 0.f ? t : 1.f - t) - eta;
   return lbF > 0.f ? sqrtf(lbF) : 0.f;
+}
+
+// FP64 sine and cosine by table lookup (P. T. P. Tang, "Table-lookup
+// algorithms for elementary functions and their error analysis", 1991):
+// x = k pi/64 + r with |r| <= pi/128, pi/64 in two parts (the first has 25
+// significant bits, so k P1 is exact for |k| < 2^28), sin and cos of
+// j pi/64 (j = k mod 128) from the table, and sin r, cos r - 1 from their
+// Taylor polynomials (truncation below 1e-20 relative for |r| <= pi/128).
+#define CERT_PI64_HI 0x1.921fb5p-5
+#define CERT_PI64_LO 4.966642116727561e-10
+__device__ __forceinline__ void cert_sincos(double x, const double2 *tab, double *s, double *c) {
+  const double kd = rint(x * 20.371832715762604);  // x 64 / pi
+  if (!(fabs(kd) < 268435456.0)) {
+    sincos(x, s, c);
+    return;
+  }
+  const double r = fma(-kd, CERT_PI64_LO, fma(-kd, CERT_PI64_HI, x));
+  const double2 e = tab[(int)kd & 127];  // (sin, cos)(j pi / 64)
+  const double r2 = r * r;
+  const double sr = fma(r * r2, fma(r2, fma(r2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), r);
+  const double cm = r2 * fma(r2, fma(r2, fma(r2, 1.0 / 40320.0, -1.0 / 720.0), 1.0 / 24.0), -0.5);
+  *s = fma(e.x, cm, fma(e.y, sr, e.x));
+  *c = fma(e.y, cm, fma(-e.x, sr, e.y));
 }
 
 // The link loops stay rolled: unrolling them per link count inlines the
@@ -179,10 +236,15 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const d
                                                                  const int32_t *type,
                                                                  const double *pose, const double *dims,
                                                                  const double *pts, int64_t n, int d,
+                                                                 const double2 *sctab,
                                                                  uint8_t *verdict, double *margin) {
   __shared__ CertObs so[CERT_MAX_OBS];
   __shared__ CertObsT<float> sof[CERT_MAX_OBS];  // FP32 copy for the lower bounds
   __shared__ double sdh[MF_MAXD * 4], srad[MF_MAXD], ssa[MF_MAXD], sca[MF_MAXD];
+  // FP32 copies, so that the FP32 passes convert nothing on the FP64 pipe
+  __shared__ float sdh32[MF_MAXD * 4], srad32[MF_MAXD], ssa32[MF_MAXD], sca32[MF_MAXD];
+  __shared__ double2 ssc[128];
+  for (int i = threadIdx.x; i < 128; i += blockDim.x) ssc[i] = sctab[i];
   for (int i = threadIdx.x; i < nobs; i += blockDim.x) {
     CertObs o;
     CertObsT<float> of;
@@ -194,10 +256,16 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const d
     so[i] = o;
     sof[i] = of;
   }
-  for (int i = threadIdx.x; i < NL * 4; i += blockDim.x) sdh[i] = dh[i];
+  for (int i = threadIdx.x; i < NL * 4; i += blockDim.x) {
+    sdh[i] = dh[i];
+    sdh32[i] = (float)dh[i];
+  }
   for (int i = threadIdx.x; i < NL; i += blockDim.x) {
     srad[i] = radius[i];
+    srad32[i] = (float)radius[i];
     sincos(dh[4 * i + 3], &ssa[i], &sca[i]);
+    ssa32[i] = (float)ssa[i];
+    sca32[i] = (float)sca[i];
   }
   __syncthreads();
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -211,11 +279,11 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const d
     float T[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
     org32[0] = org32[1] = org32[2] = 0.f;
     for (int i = 0; i < NL; i++) {
-      const float th = (float)(pts[p * d + i] + sdh[4 * i]);
-      const float dd = (float)sdh[4 * i + 1], aa = (float)sdh[4 * i + 2];
+      const float th = (float)pts[p * d + i] + sdh32[4 * i];
+      const float dd = sdh32[4 * i + 1], aa = sdh32[4 * i + 2];
       float st, ct;
       sincosf(th, &st, &ct);
-      const float sa = (float)ssa[i], ca = (float)sca[i];
+      const float sa = ssa32[i], ca = sca32[i];
       const float A[12] = {ct, -st * ca, st * sa, aa * ct, st, ct * ca, -ct * sa, aa * st,
                            0.f, sa, ca, dd};
       float N[12];
@@ -243,7 +311,7 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const d
     for (int i = done; i < upto; i++) {
       const double th = pts[p * d + i] + sdh[4 * i], dd = sdh[4 * i + 1], aa = sdh[4 * i + 2];
       double st, ct;
-      sincos(th, &st, &ct);
+      cert_sincos(th, ssc, &st, &ct);
       const double sa = ssa[i], ca = sca[i];
       const double A[12] = {ct, -st * ca, st * sa, aa * ct, st, ct * ca, -ct * sa, aa * st,
                             0.0, sa, ca, dd};
@@ -274,7 +342,7 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const d
   // exactly (FP64 chain to its link, FP64 distance); the others only if the
   // second-largest ub exceeds that exact margin, and then only those whose
   // ub does.  The result is the exact maximum.
-  auto upper = [&](int i, int k) -> float {
+  auto upper = [&](int i, int k, float *tmin) -> float {
     const float *a = &org32[3 * i], *b = &org32[3 * i + 3];
     float scale = 1.f;
 #pragma unroll
@@ -283,18 +351,20 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const d
     // local coordinates are below 2 scale: the bound's own rounding of the
     // squared distance stays far below 4e-5 (1 + scale)^2
     const float eta = 4e-5f * (1.f + scale) * (1.f + scale);
-    return (float)srad[i] - (seg_obstacle_lb32(sof[k], a, b, eta) - 1e-4f * (1.f + scale));
+    return srad32[i] - (seg_obstacle_lb32(sof[k], a, b, eta, tmin) - 1e-4f * (1.f + scale));
   };
-  float ub1 = -INFINITY, ub2 = -INFINITY;
+  float ub1 = -INFINITY, ub2 = -INFINITY, tb = 0.f;
   int bi = -1, bk = -1;
   for (int i = 0; i < NL; i++)
     for (int k = 0; k < nobs; k++) {
-      const float ub = upper(i, k);
+      float tk;
+      const float ub = upper(i, k, &tk);
       if (ub > ub1) {
         ub2 = ub1;
         ub1 = ub;
         bi = i;
         bk = k;
+        tb = tk;
       } else if (ub > ub2) {
         ub2 = ub;
       }
@@ -302,15 +372,17 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const d
   double best = -INFINITY;
   if (bi >= 0) {
     fk64(bi + 1);
-    best = srad[bi] - seg_obstacle_dist(so[bk], &org[3 * bi], &org[3 * bi + 3]);
+    best = srad[bi] - seg_obstacle_dist(so[bk], &org[3 * bi], &org[3 * bi + 3], (double)tb);
   }
   if ((double)ub2 > best) {
     fk64(NL);
     for (int i = 0; i < NL; i++)
       for (int k = 0; k < nobs; k++) {
         if (i == bi && k == bk) continue;
-        if ((double)upper(i, k) <= best) continue;
-        best = fmax(best, srad[i] - seg_obstacle_dist(so[k], &org[3 * i], &org[3 * i + 3]));
+        float tk;
+        if ((double)upper(i, k, &tk) <= best) continue;
+        best = fmax(best, srad[i] - seg_obstacle_dist(so[k], &org[3 * i], &org[3 * i + 3],
+                                                      (double)tk));
       }
   }
   margin[p] = best;
@@ -345,15 +417,33 @@ extern "C" int mf_certify(mf_ctx *ctx, const mf_robot *robot, const mf_scene *sc
     return mf_set_error(ctx, MF_ERR_INVALID, "mf_certify: bad arguments");
   cudaSetDevice(ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
-  unsigned *bad = (unsigned *)mf_ctx_buffer(ctx, MF_SLOT_CERT, 256);
+  unsigned *bad = (unsigned *)mf_ctx_buffer(ctx, MF_SLOT_CERT, 256 + 128 * sizeof(double2));
   if (!bad) return MF_ERR_OOM;
+  const double2 *sctab = (const double2 *)((char *)bad + 256);
   cudaMemsetAsync(bad, 0, sizeof(unsigned), st);
+  {
+    // (sin, cos)(j pi / 64), rounded from extended precision
+    static const std::vector<double> tab = [] {
+      std::vector<double> v(256);
+      const long double pi = 3.141592653589793238462643383279502884L;
+      for (int j = 0; j < 128; j++) {
+        v[2 * j] = (double)std::sin((long double)j * pi / 64.0L);
+        v[2 * j + 1] = (double)std::cos((long double)j * pi / 64.0L);
+      }
+      return v;
+    }();
+    int rc = mf_cuda_check(ctx, cudaMemcpyAsync((void *)sctab, tab.data(), 256 * sizeof(double),
+                                                cudaMemcpyHostToDevice, st),
+                           "mf_certify table");
+    if (rc) return rc;
+  }
   if (n_points > 0) {
     MfProfScope ps(ctx, MF_PH_CERT_PTS, st, 1, n_points);
     const unsigned g = (unsigned)((n_points + CERT_THREADS - 1) / CERT_THREADS);
     k_certify_points<<<g, CERT_THREADS, 0, st>>>(robot->n_links, robot->dh, robot->radius,
                                                  scene->n, scene->type, scene->pose, scene->dims,
-                                                 points, n_points, d, point_verdict, margin);
+                                                 points, n_points, d, sctab, point_verdict,
+                                                 margin);
   }
   if (n_cells > 0) {
     MfProfScope ps(ctx, MF_PH_CERT_CELLS, st, 1, n_cells);
