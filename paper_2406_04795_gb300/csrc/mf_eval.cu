@@ -243,6 +243,9 @@ int mf_prepare_rbf_at(mf_ctx *ctx, const mf_rbf *rbf, char *base, MfRbfDev *out,
   // relative error of a weak FP32 term on the kept range gamma r^2 <= T + 1/2
   out->weak_rel = 1.1 * ((d + 2) * 5.9604644775390625e-08 * (T + 0.5)) + 9.5367431640625e-07 +
                   2.0 * 5.9604644775390625e-08;
+  out->weak_limit32 = (float)out->weak_limit;
+  out->drop_bound32 = (float)out->drop_bound;
+  out->weak_rel32 = (float)out->weak_rel;
   out->smax = h.max_abs_s;
   return MF_OK;
 }
@@ -460,7 +463,7 @@ template <bool GRAD, int D>
 __device__ __forceinline__ F64Acc warp_f64(const MfRbfDev &R, const double *x, const double *dir,
                                            int *qs, int *qw, unsigned long long *terms) {
   F64Acc a = warp_f64_pass<GRAD, false, D>(R, x, dir, qs, qw, terms);
-  if ((double)a.weak * 1.01 * R.weak_rel > R.weak_limit)
+  if (a.weak * (1.01f * R.weak_rel32) > R.weak_limit32)
     a = warp_f64_pass<GRAD, true, D>(R, x, dir, qs, qw, terms);
   return a;
 }
@@ -697,7 +700,9 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_points_f64(MfRbfDev R,
 //    values, over that list, with hi/lo-split coordinates (x = x_hi + x_lo)
 //    so that differences keep FP32 relative accuracy.
 // 3. FP64 Newton with a kept bracket [lo, hi] under the sign rule
-//    s = [f >= 0], over the same list (strong: FP64 exp; weak: FP32).  A
+//    s = [f >= 0], over the same list: terms that can exceed ROOT_TAU = 1e-8
+//    with the FP64 exp, the rest in FP32 under a bound that keeps their
+//    error from moving t by more than 1e-10 (else every term in FP64).  A
 //    step is final when |step| <= 1e-7, or on the first FP64 step when
 //    |step| <= 1e-5 and |g''| step^2 <= 5e-11 |g'| (the remaining Newton
 //    error is then below ~1e-9 in t).  That first step takes g' from the
@@ -707,6 +712,12 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_points_f64(MfRbfDev R,
 // ---------------------------------------------------------------------------
 #define ROOT_WARPS 8
 #define NEAR_CAP 1024
+#define MID_CAP 256
+// The root's FP64 step evaluates in FP64 only the terms that can exceed
+// ROOT_TAU = 1e-8 (strong32 shifted by ln(ROOT_TAU / STRONG_TAU)); the band
+// between STRONG_TAU and ROOT_TAU ("mid") joins the FP32 stage's list and is
+// summed in FP32 with the weak terms in the FP64 step.
+#define ROOT_TAU_SHIFT 3.5065579f
 
 struct Root32 {
   float g, gp, gpp, gpa;  // gpa: the sum of |g'| terms (cancellation measure)
@@ -718,18 +729,18 @@ struct Root32 {
 // of sum |terms|); the FP32 stage leaves them to the FP64 step, which sums
 // every kept term.
 template <int D>
-__device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const int *near, int ns, int nw,
-                                              const float *x1hi, const float *x1lo,
-                                              const float *dir32, float dd32, float b32, float t) {
+__device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const int *near, int ns,
+                                              const int *midl, int nm, const float *x1hi,
+                                              const float *x1lo, const float *dir32, float dd32,
+                                              float b32, float t) {
   const int lane = threadIdx.x & 31;
   const int d = dim_of<D>(R.d);
   const float g2 = (float)(R.gamma * 1.4426950408889634);
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s1a = 0.f;
-  (void)nw;
-  const int total = ns;
+  const int total = ns + nm;
 #pragma unroll 2
   for (int i = lane; i < total; i += 32) {
-    const int j = i < ns ? near[i] : near[NEAR_CAP - 1 - (i - ns)];
+    const int j = i < ns ? near[i] : midl[i - ns];
     float r2 = 0.f, proj = 0.f;
     const float4 *row = reinterpret_cast<const float4 *>(R.svhl + (int64_t)j * 16);
 #pragma unroll
@@ -770,18 +781,21 @@ __device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const int *near
 // split into FP32 hi/lo parts for the weak terms.
 template <bool ALL_STRONG, bool GRAD, int D>
 __device__ __forceinline__ F64Acc root_eval64(const MfRbfDev &R, const int *near, int ns, int nw,
-                                              const double *x, const double *dir, const Split32<D> &xs,
+                                              const int *midl, int nm, const double *x,
+                                              const double *dir, const Split32<D> &xs,
                                               unsigned long long *terms) {
   const int lane = threadIdx.x & 31;
   F64Acc acc = {0.0, 0.0, 0.f, 0.f, 0.f};
   for (int i = lane; i < ns; i += 32) f64_term<GRAD, D>(R, x, dir, near[i], acc);
-  if (ALL_STRONG) {
-    for (int i = lane; i < nw; i += 32) f64_term<GRAD, D>(R, x, dir, near[NEAR_CAP - 1 - i], acc);
-  } else {
-    for (int i = lane; i < nw; i += 32) f32_weak_term<GRAD, D>(R, xs, near[NEAR_CAP - 1 - i], acc);
+  // mid entries, then weak ones, as one list
+  const int nr = nm + nw;
+  for (int i = lane; i < nr; i += 32) {
+    const int j = i < nm ? midl[i] : near[NEAR_CAP - 1 - (i - nm)];
+    if (ALL_STRONG) f64_term<GRAD, D>(R, x, dir, j, acc);
+    else f32_weak_term<GRAD, D>(R, xs, j, acc);
   }
-  terms[0] += ns + (ALL_STRONG ? nw : 0);
-  terms[1] += ALL_STRONG ? 0 : nw;
+  terms[0] += ns + (ALL_STRONG ? nr : 0);
+  terms[1] += ALL_STRONG ? 0 : nr;
   acc.f = mf_warp_sum_d(acc.f) + (double)mf_warp_sum_f(acc.wf) + R.b;
   acc.weak = mf_warp_sum_f(acc.weak);
   acc.g = GRAD ? -2.0 * R.gamma * (mf_warp_sum_d(acc.g) + (double)mf_warp_sum_f(acc.wg)) : 0.0;
@@ -794,6 +808,17 @@ __device__ __forceinline__ F64Acc root_eval64(const MfRbfDev &R, const int *near
 // screen (a group screen's survivors); NULL screens all of them.  FP64 work
 // that is the same for every lane (coordinates, their splits) runs once per
 // axis: lane k < d computes axis k and shuffles broadcast it.
+// The FP32 part of a root evaluation (mid and weak terms) errs by at most
+// weak_rel * sum|terms|; with the dropped terms (drop_bound) that must stay
+// below 1e-10 |g'| (t then moves by at most 1e-10), or below the vertex
+// evaluation's own limit, whichever is larger.  Otherwise the point is
+// evaluated again with every kept term in FP64.
+// (The check runs in FP32: the 1.01 factor covers its roundings.)
+__device__ __forceinline__ bool root_fp32_part_too_coarse(const MfRbfDev &R, float weak, float gp) {
+  const float lim = fmaxf(R.weak_limit32, 0.99e-10f * fabsf(gp) - R.drop_bound32);
+  return weak * (1.01f * R.weak_rel32) > lim;
+}
+
 // Per-warp shared state of the FP64 stage (the point, the direction and the
 // FP32 split of the point): warp-uniform values kept out of registers.
 struct RootWarpState {
@@ -803,7 +828,8 @@ struct RootWarpState {
 
 template <int D>
 __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, uint64_t e,
-                          double tol, const int *src, int srcn, int *near, int *qs, int *qw,
+                          double tol, const int *src, int srcn, int *near, int *midl, int *qs,
+                          int *qw,
                           RootWarpState *ws, unsigned long long &evals, unsigned long long *terms) {
   const int lane = threadIdx.x & 31;
   const int d = dim_of<D>(F.d);
@@ -848,13 +874,13 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
   //    midpoint, so a vector farther than r_s + |dir|/2 from it (with a
   //    rounding margin) cannot pass; only the others get the exact
   //    point-to-segment test.
-  int ns = 0, nw = 0;
+  int ns = 0, nm = 0, nw = 0;
   const float inv_dd = 1.f / dd32;
   const float pre = (sqrtf(R.screen_r2) + 0.5f * sqrtf(dd32)) * 1.0001f + 1e-5f, pre2 = pre * pre;
   // one round: lane tests vector j (gathered row for a group list, or the
   // coalesced coordinate arrays) and the survivors are compacted
   auto screen_round = [&](bool valid, int j, bool gathered) {
-    bool keep = false, strong = false;
+    bool keep = false, strong = false, strong64 = false;
     if (valid) {
       float p[D], pd = 0.f;
       if (gathered) {
@@ -886,15 +912,22 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
           r2 = fmaf(q, q, r2);
         }
         keep = r2 <= R.screen_r2;
-        strong = g32 * r2 < R.strong32[j] + 0.5f;
+        const float s32 = R.strong32[j];
+        strong = g32 * r2 < s32 + 0.5f;
+        strong64 = g32 * r2 < s32 + (0.5f - ROOT_TAU_SHIFT);
       }
     }
-    const unsigned ms = __ballot_sync(FULL, keep && strong);
+    // strong64 entries fill near from the front, weak ones from the back,
+    // mid ones (strong, not strong64) fill midl
+    const unsigned ms = __ballot_sync(FULL, keep && strong64);
+    const unsigned mm = __ballot_sync(FULL, keep && strong && !strong64);
     const unsigned mw = __ballot_sync(FULL, keep && !strong);
-    const int cs = ns + __popc(ms & lt), cw = nw + __popc(mw & lt);
-    if (keep && strong && cs + nw < NEAR_CAP) near[cs] = j;
+    const int cs = ns + __popc(ms & lt), cm = nm + __popc(mm & lt), cw = nw + __popc(mw & lt);
+    if (keep && strong64 && cs + nw < NEAR_CAP) near[cs] = j;
+    if (keep && strong && !strong64 && cm < MID_CAP) midl[cm] = j;
     if (keep && !strong && ns + cw < NEAR_CAP) near[NEAR_CAP - 1 - cw] = j;
     ns += __popc(ms);
+    nm += __popc(mm);
     nw += __popc(mw);
   };
   if (src) {
@@ -930,7 +963,7 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
     }
   }
   __syncwarp();
-  const bool overflow = ns + nw > NEAR_CAP;
+  const bool overflow = ns + nw > NEAR_CAP || nm > MID_CAP;
   const double f0 = B.edge_f[2 * e], f1 = B.edge_f[2 * e + 1];
   const bool s1 = f0 >= 0.0;
   // 2. FP32 Halley iteration (cubic: the evaluation yields g'' anyway),
@@ -944,7 +977,7 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
     const float b32 = (float)R.b;
     float lo = 0.f, hi = 1.f;
     for (int it = 0; it < 12; it++) {
-      const Root32 r = root_eval32<D>(R, near, ns, nw, x1hi, x1lo, dir32, dd32, b32, t32);
+      const Root32 r = root_eval32<D>(R, near, ns, midl, nm, x1hi, x1lo, dir32, dd32, b32, t32);
       gpp = r.gpp;
       gp32 = r.gp;
       t_eval = t32;
@@ -964,9 +997,11 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
       if (step <= 2e-6f || (halley && inside && step <= 1e-3f)) break;
     }
   }
-  // 3. FP64 Newton with a kept bracket
+  // 3. FP64 Newton with a kept bracket.  Values that only steer the
+  //    iteration (g', step sizes, the acceptance tests) stay in FP32: each
+  //    FP64 instruction occupies the FP64 pipe for the whole warp.
   double t = (double)t32, xo = 0.0;
-  const double gpp64 = fabs((double)gpp);
+  const float gppf = fabsf(gpp), tolf = (float)tol;
   double lo = 0.0, hi = 1.0;
   for (int it = 0; it < 64; it++) {
     xo = __dadd_rn(x1o, __dmul_rn(t, diro));
@@ -983,31 +1018,39 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
     // (relative error below ~5e-5 when the FP32 sum had little
     // cancellation: a final step of at most 1e-5 then errs by < 1e-9);
     // later steps take the FP64 g'.
-    const double gp_est = (double)gp32 + (double)gpp * (t - (double)t_eval);
-    const bool reuse = it == 0 && !overflow && gp_ok && gp32 != 0.f && isfinite(gp_est) &&
-                       fabs(gp_est) > 0.5 * fabs((double)gp32);
+    float gpf = 0.f;
+    bool reuse = false;
+    if (it == 0 && !overflow && gp_ok) {
+      gpf = fmaf(gpp, (float)t - t_eval, gp32);
+      reuse = gp32 != 0.f && isfinite(gpf) && fabsf(gpf) > 0.5f * fabsf(gp32);
+    }
     if (overflow) {
       a = warp_f64<true, D>(R, x, dir, qs, qw, terms);
+      gpf = (float)a.g;
     } else if (reuse) {
-      a = root_eval64<false, false, D>(R, near, ns, nw, x, dir, xs, terms);
-      if ((double)a.weak * 1.01 * R.weak_rel > R.weak_limit)
-        a = root_eval64<true, false, D>(R, near, ns, nw, x, dir, xs, terms);
-      a.g = gp_est;
+      a = root_eval64<false, false, D>(R, near, ns, nw, midl, nm, x, dir, xs, terms);
+      if (root_fp32_part_too_coarse(R, a.weak, gpf))
+        a = root_eval64<true, false, D>(R, near, ns, nw, midl, nm, x, dir, xs, terms);
     } else {
-      a = root_eval64<false, true, D>(R, near, ns, nw, x, dir, xs, terms);
-      if ((double)a.weak * 1.01 * R.weak_rel > R.weak_limit)
-        a = root_eval64<true, true, D>(R, near, ns, nw, x, dir, xs, terms);
+      a = root_eval64<false, true, D>(R, near, ns, nw, midl, nm, x, dir, xs, terms);
+      gpf = (float)a.g;
+      if (root_fp32_part_too_coarse(R, a.weak, gpf)) {
+        a = root_eval64<true, true, D>(R, near, ns, nw, midl, nm, x, dir, xs, terms);
+        gpf = (float)a.g;
+      }
     }
     evals++;
-    if (a.f == 0.0) break;
-    if ((a.f >= 0.0) == s1) lo = t; else hi = t;
+    // sign of f from its bits (f = +-0 ends the iteration)
+    const long long fb = __double_as_longlong(a.f);
+    if ((fb << 1) == 0) break;
+    if ((fb >= 0) == s1) lo = t; else hi = t;
     // the derivative only steers the step: its reciprocal in FP32 suffices
-    double tn = t - a.f * (double)(1.0f / (float)a.g);
+    double tn = fma(-a.f, (double)(1.0f / gpf), t);
     if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
-    const double step = fabs(tn - t);
+    const float step = fabsf((float)(tn - t));
     t = tn;
-    if (step <= tol || step <= 1e-7 || hi - lo <= 9.094947017729282e-13 ||
-        (it == 0 && step <= 1e-5 && gpp64 * step * step <= 5e-11 * fabs(a.g)))
+    if (step <= tolf || step <= 1e-7f || hi - lo <= 9.094947017729282e-13 ||
+        (it == 0 && step <= 1e-5f && gppf * step * step <= 5e-11f * fabsf(gpf)))
       break;
   }
   if (lane == 0) B.edge_t[e] = t;
@@ -1102,6 +1145,7 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(MfFrame F, 
                                                                uint64_t n_edges, double tol,
                                                                int group) {
   __shared__ int snear[ROOT_WARPS][NEAR_CAP];
+  __shared__ int smid[ROOT_WARPS][MID_CAP];
   __shared__ int sq[ROOT_WARPS][2][64];
   __shared__ RootWarpState sws[ROOT_WARPS];
   extern __shared__ int sgrp_all[];  // [ROOT_WARPS][GROUP_CAP] when group > 1
@@ -1112,16 +1156,16 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(MfFrame F, 
   unsigned long long evals = 0, terms[2] = {0, 0};
   if (group <= 1) {
     for (uint64_t e = (uint64_t)blockIdx.x * ROOT_WARPS + w; e < n_edges; e += nwarps)
-      root_edge<D>(F, R, B, e, tol, nullptr, 0, snear[w], sq[w][0], sq[w][1], &sws[w], evals,
-                   terms);
+      root_edge<D>(F, R, B, e, tol, nullptr, 0, snear[w], smid[w], sq[w][0], sq[w][1], &sws[w],
+                   evals, terms);
   } else {
     const uint64_t G = (uint64_t)group;
     for (uint64_t g0 = ((uint64_t)blockIdx.x * ROOT_WARPS + w) * G; g0 < n_edges; g0 += nwarps * G) {
       const int ng = (int)(n_edges - g0 < G ? n_edges - g0 : G);
       const int gn = group_screen<D>(F, R, B, g0, ng, rs, sgrp);
       for (int q = 0; q < ng; q++)
-        root_edge<D>(F, R, B, g0 + q, tol, gn >= 0 ? sgrp : nullptr, gn, snear[w], sq[w][0],
-                     sq[w][1], &sws[w], evals, terms);
+        root_edge<D>(F, R, B, g0 + q, tol, gn >= 0 ? sgrp : nullptr, gn, snear[w], smid[w],
+                     sq[w][0], sq[w][1], &sws[w], evals, terms);
     }
   }
   root_flush(B, evals, terms);
@@ -1229,6 +1273,7 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, 2) k_b_roots(const MfSlot *sl
                                                                 const MfBatchPlan *P, int n,
                                                                 int group) {
   __shared__ int snear[ROOT_WARPS][NEAR_CAP];
+  __shared__ int smid[ROOT_WARPS][MID_CAP];
   __shared__ int sq[ROOT_WARPS][2][64];
   __shared__ RootWarpState sws[ROOT_WARPS];
   extern __shared__ int sgrp_all[];  // [ROOT_WARPS][GROUP_CAP] when group > 1
@@ -1250,7 +1295,7 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, 2) k_b_roots(const MfSlot *sl
       unsigned long long evals = 0, terms[2] = {0, 0};
       for (int q = 0; q < ng; q++)
         root_edge<D>(S.F, S.R, S.B, e0 + q, S.root_tol, gn >= 0 ? sgrp : nullptr, gn, snear[w],
-                     sq[w][0], sq[w][1], &sws[w], evals, terms);
+                     smid[w], sq[w][0], sq[w][1], &sws[w], evals, terms);
       root_flush(S.B, evals, terms);
       i = end;
     }

@@ -119,6 +119,7 @@ struct MfRbfDev {
   double drop_bound;   // sum_i |alpha_i| exp(-gamma * screen cut): bound on dropped terms
   double weak_limit;   // allowed error of the FP32 weak terms (2.5e-13 - drop_bound)
   double weak_rel;     // relative error bound of one FP32 weak term
+  float weak_limit32, drop_bound32, weak_rel32;  // FP32 copies for the FP32 checks
   float smax;          // max |s_ik| over all support-vector coordinates
 };
 

@@ -277,6 +277,9 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   R.weak_limit = 2.5e-13 - R.drop_bound;
   R.weak_rel = 1.1 * ((d + 2) * 5.9604644775390625e-08 * (T + 0.5)) + 9.5367431640625e-07 +
                2.0 * 5.9604644775390625e-08;
+  R.weak_limit32 = (float)R.weak_limit;
+  R.drop_bound32 = (float)R.drop_bound;
+  R.weak_rel32 = (float)R.weak_rel;
   R.smax = hs.max_abs_s;
 
   // Everything that must start empty.
