@@ -273,17 +273,50 @@ __device__ __forceinline__ int dim_of(int rt) {
   return D < MF_MAXD ? D : rt;
 }
 
+// (All lanes, converged.)  Lane k < d converts axis k and shuffles
+// broadcast the parts: each FP64 instruction holds the FP64 pipe for the
+// whole warp, so one conversion per lane serves every axis at once.
 template <int D>
 __device__ __forceinline__ Split32<D> split32(int d, const double *x, const double *dir) {
-  Split32<D> s;
+  const int lane = threadIdx.x & 31;
   d = dim_of<D>(d);
+  double xk = 0.0, dk = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; k++)
+    if (k == lane) {
+      xk = x[k];
+      dk = dir ? dir[k] : 0.0;
+    }
+  const float h = (float)xk, l = (float)(xk - (double)h), dd = (float)dk;
+  Split32<D> s;
 #pragma unroll
   for (int k = 0; k < D; k++) {
-    s.hi[k] = k < d ? (float)x[k] : 0.f;
-    s.lo[k] = k < d ? (float)(x[k] - (double)s.hi[k]) : 0.f;
-    s.dir[k] = (k < d && dir) ? (float)dir[k] : 0.f;
+    s.hi[k] = k < d ? __shfl_sync(FULL, h, k) : 0.f;
+    s.lo[k] = k < d ? __shfl_sync(FULL, l, k) : 0.f;
+    s.dir[k] = k < d ? __shfl_sync(FULL, dd, k) : 0.f;
   }
   return s;
+}
+
+// mf_vertex_x in every lane (all lanes, converged): lane k < d computes
+// axis k with the same operations and the values are broadcast.
+template <int D>
+__device__ __forceinline__ void vertex_x_lanes(const MfFrame &F, const int32_t *y, double *x) {
+  const int lane = threadIdx.x & 31;
+  const int d = dim_of<D>(F.d);
+  const int ko = lane < d ? lane : 0;
+  long long sy = 0;
+  int32_t yo = 0;
+#pragma unroll
+  for (int k = 0; k < D; k++)
+    if (k < d) {
+      sy += y[k];
+      if (k == ko) yo = y[k];
+    }
+  const double cs = __dmul_rn(F.c, (double)sy);
+  const double xo = __dadd_rn(__dmul_rn(F.lam, __dsub_rn((double)yo, cs)), F.o[ko]);
+#pragma unroll
+  for (int k = 0; k < D; k++) x[k] = k < d ? __shfl_sync(FULL, xo, k) : 0.0;
 }
 
 // e^x for x <= 0 in FP64 by the table-driven method of P. T. P. Tang
@@ -482,12 +515,10 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_vertices_f64(MfFrame F
   unsigned long long terms[2] = {0, 0};
   for (uint64_t i = begin + (uint64_t)blockIdx.x * EVAL_WARPS + w; i < end; i += nwarps) {
     int32_t y[MF_MAXD];
-    double xm[MF_MAXD], x[D];
+    double x[D];
 #pragma unroll
     for (int k = 0; k < MF_MAXD; k++) y[k] = k < F.d ? B.vert_y[i * F.d + k] : 0;
-    mf_vertex_x(F, y, xm);
-#pragma unroll
-    for (int k = 0; k < D; k++) x[k] = xm[k];
+    vertex_x_lanes<D>(F, y, x);
     F64Acc a = warp_f64<false, D>(R, x, nullptr, sq[w][0], sq[w][1], terms);
     if (lane == 0) {
       B.vtab_f[B.vert_slot[i]] = a.f;
@@ -513,12 +544,10 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_recheck_vertices_f64(MfFram
   for (uint64_t q = begin + (uint64_t)blockIdx.x * EVAL_WARPS + w; q < end; q += nwarps) {
     const uint32_t i = B.recheck[q];
     int32_t y[MF_MAXD];
-    double xm[MF_MAXD], x[D];
+    double x[D];
 #pragma unroll
     for (int k = 0; k < MF_MAXD; k++) y[k] = k < F.d ? B.vert_y[(uint64_t)i * F.d + k] : 0;
-    mf_vertex_x(F, y, xm);
-#pragma unroll
-    for (int k = 0; k < D; k++) x[k] = xm[k];
+    vertex_x_lanes<D>(F, y, x);
     F64Acc a = warp_f64<false, D>(R, x, nullptr, sq[w][0], sq[w][1], terms);
     if (lane == 0) {
       B.vtab_f[B.vert_slot[i]] = a.f;
@@ -1239,7 +1268,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_b_eval(const MfSlot *slots,
     double x[MF_MAXD];
 #pragma unroll
     for (int k = 0; k < MF_MAXD; k++) y[k] = k < d ? S.B.vert_y[i * d + k] : 0;
-    mf_vertex_x(S.F, y, x);
+    vertex_x_lanes<MF_MAXD>(S.F, y, x);
     const uint32_t slot = S.B.vert_slot[i];
     if (recheck || S.precision == MF_FP64) {
       unsigned long long terms[2] = {0, 0};
