@@ -183,6 +183,12 @@ int mf_setup_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_trace_opts *o, char 
   B.cell_sgn = (uint32_t *)(base + l->cell_sgn);
   B.cell_off = (int64_t *)(base + l->cell_off);
   B.max_cells = (o->flags & MF_WANT_CELLS) ? l->MC : 0;
+  B.vtab_idx = nullptr;  // no per-vertex lists: the root screen scans the blocks
+  B.vlist = nullptr;
+  B.vlist_off = nullptr;
+  B.vlist_n = nullptr;
+  B.vlist_cap = 0;
+  B.list_r2 = 0.f;
   S->precision = o->precision;
   S->band = o->recheck_band > 0 ? o->recheck_band : 1e-3;
   S->root_tol = o->root_tol > 0 ? o->root_tol : 1e-12;

@@ -418,9 +418,13 @@ __device__ __forceinline__ int pop32(int *q, int &n, int lane) {
 // All lanes pass the same x (FP64) and get f (and, with GRAD, g = grad f . dir).
 // qs, qw: two 64-entry per-warp queues.  ALL_STRONG puts every kept term in
 // the strong queue.  terms[0/1] count strong / weak terms.
+// lbuf (LIST_CAP entries, NULL for none) receives the vectors within
+// sqrt(list_r2) of x (all of them when *nl <= LIST_CAP), *nl their count.
+#define LIST_CAP 512
 template <bool GRAD, bool ALL_STRONG, int D>
 __device__ F64Acc warp_f64_pass(const MfRbfDev &R, const double *x, const double *dir, int *qs,
-                                int *qw, unsigned long long *terms) {
+                                int *qw, unsigned long long *terms, int *lbuf = nullptr,
+                                float list_r2 = 0.f, int *nl = nullptr) {
   const int lane = threadIdx.x & 31;
   const int d = dim_of<D>(R.d);
   const float g32 = (float)R.gamma;
@@ -430,7 +434,8 @@ __device__ F64Acc warp_f64_pass(const MfRbfDev &R, const double *x, const double
   const unsigned lt = (1u << lane) - 1u;
   // blocks of 32 vectors whose box is farther than the screen distance (with
   // a rounding margin) hold no vector that passes: they are skipped whole
-  const float box2 = R.screen_r2 * 1.001f + 1e-5f;
+  const float box2 = fmaxf(R.screen_r2, lbuf ? list_r2 : 0.f) * 1.001f + 1e-5f;
+  int nlist = 0;
   for (int bb0 = 0; bb0 < R.nblk; bb0 += 32) {
     bool bkeep = false;
     if (bb0 + lane < R.nblk) {
@@ -449,7 +454,7 @@ __device__ F64Acc warp_f64_pass(const MfRbfDev &R, const double *x, const double
   while (bm) {
     const int j = (bb0 + __ffs(bm) - 1) * 32 + lane;
     bm &= bm - 1;
-    bool keep = false, strong = false;
+    bool keep = false, strong = false, listed = false;
     if (j < R.n) {
       float r2 = 0.f;
 #pragma unroll
@@ -460,6 +465,13 @@ __device__ F64Acc warp_f64_pass(const MfRbfDev &R, const double *x, const double
         }
       keep = r2 <= R.screen_r2;
       strong = ALL_STRONG || (g32 * r2 < R.strong32[j] + 0.5f);
+      listed = r2 <= list_r2;
+    }
+    if (lbuf) {
+      const unsigned ml = __ballot_sync(FULL, listed);
+      const int pos = nlist + __popc(ml & lt);
+      if (listed && pos < LIST_CAP) lbuf[pos] = j;
+      nlist += __popc(ml);
     }
     const unsigned ms = __ballot_sync(FULL, keep && strong);
     const unsigned mw = __ballot_sync(FULL, keep && !strong);
@@ -488,14 +500,17 @@ __device__ F64Acc warp_f64_pass(const MfRbfDev &R, const double *x, const double
   acc.f = mf_warp_sum_d(acc.f) + (double)mf_warp_sum_f(acc.wf) + R.b;
   acc.weak = mf_warp_sum_f(acc.weak);
   if (GRAD) acc.g = -2.0 * R.gamma * (mf_warp_sum_d(acc.g) + (double)mf_warp_sum_f(acc.wg));
+  if (nl) *nl = nlist;
   return acc;
 }
 
 // f with total error <= 2.5e-13 (dropped + weak terms), all lanes.
 template <bool GRAD, int D>
 __device__ __forceinline__ F64Acc warp_f64(const MfRbfDev &R, const double *x, const double *dir,
-                                           int *qs, int *qw, unsigned long long *terms) {
-  F64Acc a = warp_f64_pass<GRAD, false, D>(R, x, dir, qs, qw, terms);
+                                           int *qs, int *qw, unsigned long long *terms,
+                                           int *lbuf = nullptr, float list_r2 = 0.f,
+                                           int *nl = nullptr) {
+  F64Acc a = warp_f64_pass<GRAD, false, D>(R, x, dir, qs, qw, terms, lbuf, list_r2, nl);
   if (a.weak * (1.01f * R.weak_rel32) > R.weak_limit32)
     a = warp_f64_pass<GRAD, true, D>(R, x, dir, qs, qw, terms);
   return a;
@@ -507,6 +522,7 @@ __device__ __forceinline__ F64Acc warp_f64(const MfRbfDev &R, const double *x, c
 template <int D>
 __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_vertices_f64(MfFrame F, MfRbfDev R, MfTraceBufs B) {
   __shared__ int sq[EVAL_WARPS][2][64];
+  __shared__ int slist[EVAL_WARPS][LIST_CAP];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint64_t begin = B.cnt->v_evaluated;
   uint64_t end = B.cnt->n_vertices;
@@ -519,10 +535,27 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_vertices_f64(MfFrame F
 #pragma unroll
     for (int k = 0; k < MF_MAXD; k++) y[k] = k < F.d ? B.vert_y[i * F.d + k] : 0;
     vertex_x_lanes<D>(F, y, x);
-    F64Acc a = warp_f64<false, D>(R, x, nullptr, sq[w][0], sq[w][1], terms);
+    int nl = 0;
+    F64Acc a = warp_f64<false, D>(R, x, nullptr, sq[w][0], sq[w][1], terms,
+                                  B.vlist ? slist[w] : nullptr, B.list_r2, &nl);
     if (lane == 0) {
       B.vtab_f[B.vert_slot[i]] = a.f;
       if (fabs(a.f) < 1e-12) atomicAdd(&B.cnt->n_near_zero, 1ull);
+    }
+    if (B.vlist) {
+      // the vertex's list for the root screen, if it fits the pool
+      unsigned long long off = 0;
+      if (lane == 0 && nl <= LIST_CAP) off = atomicAdd(&B.cnt->n_vlist, (unsigned long long)nl);
+      off = __shfl_sync(FULL, off, 0);
+      const bool ok = nl <= LIST_CAP && off + nl <= B.vlist_cap;
+      __syncwarp();
+      if (ok)
+        for (int q = lane; q < nl; q += 32) B.vlist[off + q] = slist[w][q];
+      if (lane == 0) {
+        B.vlist_off[i] = off;
+        B.vlist_n[i] = ok ? (uint32_t)nl : MF_NO_LIST;
+      }
+      __syncwarp();
     }
   }
   if (lane == 0 && (terms[0] | terms[1])) {
@@ -959,6 +992,30 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
     nm += __popc(mm);
     nw += __popc(mw);
   };
+  if (!src && B.vlist) {
+    // the base vertex's list from its FP64 evaluation: a superset of the
+    // vectors this screen can keep (its radius covers the screen radius
+    // around every point of the edge)
+    uint32_t nl = MF_NO_LIST;
+    unsigned long long off = 0;
+    if (lane == 0) {
+      int32_t yv[MF_MAXD];
+#pragma unroll
+      for (int k = 0; k < MF_MAXD; k++) yv[k] = k < d ? B.edge_y[e * d + k] : 0;
+      const uint64_t slot = mf_table_find(B.vtab_key, B.vtab_mask, mf_vertex_key(F, yv));
+      if (slot != ~0ull) {
+        const uint32_t vi = B.vtab_idx[slot];
+        nl = B.vlist_n[vi];
+        off = B.vlist_off[vi];
+      }
+    }
+    nl = __shfl_sync(FULL, nl, 0);
+    off = __shfl_sync(FULL, off, 0);
+    if (nl != MF_NO_LIST) {
+      src = B.vlist + off;
+      srcn = (int)nl;
+    }
+  }
   if (src) {
     for (int base = 0; base < srcn; base += 32) {
       const int i = base + lane;

@@ -53,6 +53,7 @@ struct MfCounters {
   unsigned long long root_terms;   // RBF terms with FP64 exp, root solve
   unsigned long long eval_terms_weak;  // RBF terms with the reduced-cost exp, vertex evaluation
   unsigned long long root_terms_weak;  // RBF terms with the reduced-cost exp, root solve
+  unsigned long long n_vlist;      // entries taken from the per-vertex list pool
   unsigned int err_table_full;     // a hash probe ran past the table
   unsigned int err_overflow;       // a list ran past its capacity
   unsigned int err_missing;        // a vertex expected in the table was absent
@@ -93,7 +94,18 @@ struct MfTraceBufs {
   int64_t *cell_idx;   // [MC * (d+1)d/2]
   uint64_t max_cells;
   MfCounters *cnt;
+  // Per-vertex support-vector lists for the root screen (FP64 path; NULL:
+  // none).  Vertex i's list holds every vector within sqrt(list_r2) of it,
+  // a radius that covers the screen radius around any point of an edge
+  // leaving the vertex.
+  uint32_t *vtab_idx;   // [vertex table size] vertex-list index of each slot
+  int32_t *vlist;       // pool of vector indices
+  uint64_t *vlist_off;  // [MV] offset of vertex i's list in the pool
+  uint32_t *vlist_n;    // [MV] its length, MF_NO_LIST when it has none
+  uint64_t vlist_cap;   // pool capacity (entries)
+  float list_r2;
 };
+#define MF_NO_LIST 0xFFFFFFFFu
 
 // Prepared RBF: structure-of-arrays copies for coalesced streaming.
 struct MfRbfDev {
@@ -490,5 +502,6 @@ enum {
   MF_SLOT_DOMTAB = 10,
   MF_SLOT_BATCH = 11,
   MF_SLOT_SERVER = 12,
-  MF_NUM_SLOTS = 13
+  MF_SLOT_VLIST = 13,
+  MF_NUM_SLOTS = 14
 };

@@ -49,6 +49,7 @@ __device__ __forceinline__ void visit_vertex(const MfFrame &F, const MfTraceBufs
   for (int k = 0; k < MF_MAXD; k++)
     if (k < F.d) B.vert_y[idx * F.d + k] = w[k];
   B.vert_slot[idx] = (uint32_t)slot;
+  if (B.vtab_idx) B.vtab_idx[slot] = (uint32_t)idx;
 }
 
 __device__ __forceinline__ double lookup_f(const MfFrame &F, const MfTraceBufs &B, const int32_t *w) {
@@ -1014,7 +1015,7 @@ static int read_counters(mf_ctx *ctx, const MfTraceBufs &B, cudaStream_t st) {
 
 // Carves the trace's buffers from the context slots.
 static int setup_buffers(mf_ctx *ctx, int d, uint64_t ME, uint64_t MV, uint64_t MC, bool mixed,
-                         MfTraceBufs *B) {
+                         int n_sv, MfTraceBufs *B) {
   memset(B, 0, sizeof(*B));
   // load factor <= 3/4 at capacity
   const uint64_t TE = next_pow2(ME + ME / 3 + 1), TV = next_pow2(MV + MV / 3 + 1),
@@ -1057,6 +1058,24 @@ static int setup_buffers(mf_ctx *ctx, int d, uint64_t ME, uint64_t MV, uint64_t 
   B->max_cells = MC;
   B->cnt = (MfCounters *)mf_ctx_buffer(ctx, MF_SLOT_COUNTERS, sizeof(MfCounters));
   if (!B->cnt) return MF_ERR_OOM;
+  // FP64 path: per-vertex lists for the root screen, when they fit the
+  // budget (else the root screen scans the vector blocks)
+  if (!mixed && n_sv > 0) {
+    const uint64_t per = (uint64_t)std::min(n_sv, 192);
+    const uint64_t cap = MV * per;
+    const size_t lb = al(TV * 4) + al(MV * 8) + al(MV * 4) + al(cap * 4);
+    std::string keep = ctx->err;
+    char *l = (char *)mf_ctx_buffer(ctx, MF_SLOT_VLIST, lb);
+    if (l) {
+      B->vtab_idx = (uint32_t *)l; l += al(TV * 4);
+      B->vlist_off = (uint64_t *)l; l += al(MV * 8);
+      B->vlist_n = (uint32_t *)l; l += al(MV * 4);
+      B->vlist = (int32_t *)l;
+      B->vlist_cap = cap;
+    } else {
+      ctx->err = keep;
+    }
+  }
   return MF_OK;
 }
 
@@ -1146,8 +1165,17 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
     return mf_set_error(ctx, MF_ERR_INVALID, "max_edges / max_vertices must be < 2^32");
   const bool mixed = opts->precision != MF_FP64;
   MfTraceBufs B;
-  rc = setup_buffers(ctx, d, ME, MV, MC, mixed, &B);
+  rc = setup_buffers(ctx, d, ME, MV, MC, mixed, (int)rbf->n_sv, &B);
   if (rc) return rc;
+  if (B.vlist) {
+    // list radius: the screen radius around any point of an edge from the
+    // vertex; the longest edge is lam |L e(M)|, |L e(M)|^2 = k (1 - 2ck + c^2 k d)
+    // for |M| = k; margins cover the FP32 distances of both screens
+    double m2 = 0.0;
+    for (int k = 1; k <= d; k++) m2 = std::max(m2, k * (1.0 - 2.0 * F.c * k + F.c * F.c * k * d));
+    const double rl = std::sqrt((double)R.screen_r2) * 1.0001 + opts->lambda * std::sqrt(m2) + 1e-4;
+    B.list_r2 = (float)(rl * rl);
+  }
   uint64_t cap = opts->batch_cap_edges > 0 ? (uint64_t)opts->batch_cap_edges : (1ull << 24);
   if (ctx->tune.frontier_chunk > 0 && ctx->tune.frontier_chunk < cap) cap = ctx->tune.frontier_chunk;
   const double band = opts->recheck_band > 0 ? opts->recheck_band : 1e-3;
