@@ -31,7 +31,7 @@ struct Bump {
 };
 
 struct TraceLayout {
-  size_t rbf, dom, cnt, etab_key, etab_val, vtab_key, vtab_f, ctab_key;
+  size_t rbf, dom, cnt, etab_key, vtab_key, ctab_key;
   size_t edge_y, edge_mask, edge_f, edge_t, edge_pt, vert_y, vert_slot, recheck;
   size_t cell_y, cell_perm, cell_sgn, cell_off, scan;
   uint64_t ME, MV, MC, TE, TV, TC;
@@ -123,10 +123,8 @@ int mf_layout_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom, const 
   l->rbf = bump->take(mf_rbf_prep_bytes(d, r.n_sv));
   l->dom = bump->take(l->tab.size() * sizeof(int2) + 8);
   l->cnt = bump->take(sizeof(MfCounters));
-  l->etab_key = bump->take(l->TE * 8);
-  l->etab_val = bump->take(l->TE * 4);
-  l->vtab_key = bump->take(l->TV * 8);
-  l->vtab_f = bump->take(l->TV * 8);
+  l->etab_key = bump->take(l->TE * 16);
+  l->vtab_key = bump->take(l->TV * 16);
   l->ctab_key = bump->take((o->flags & MF_WANT_CELLS) ? l->TC * 8 : 8);
   l->edge_y = bump->take(l->ME * d * 4);
   l->edge_mask = bump->take(l->ME * 4);
@@ -161,10 +159,8 @@ int mf_setup_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_trace_opts *o, char 
   MfTraceBufs &B = S->B;
   B.cnt = (MfCounters *)(base + l->cnt);
   B.etab_key = (unsigned long long *)(base + l->etab_key);
-  B.etab_val = (uint32_t *)(base + l->etab_val);
   B.etab_mask = l->TE - 1;
   B.vtab_key = (unsigned long long *)(base + l->vtab_key);
-  B.vtab_f = (double *)(base + l->vtab_f);
   B.vtab_mask = l->TV - 1;
   B.ctab_key = (unsigned long long *)(base + l->ctab_key);
   B.ctab_mask = (o->flags & MF_WANT_CELLS) ? l->TC - 1 : 0;
@@ -195,8 +191,8 @@ int mf_setup_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_trace_opts *o, char 
   S->cap = o->batch_cap_edges > 0 ? (uint64_t)o->batch_cap_edges : (1ull << 24);
   S->flags = o->flags;
   cudaMemsetAsync(B.cnt, 0, sizeof(MfCounters), st);
-  cudaMemsetAsync(B.etab_key, 0xFF, l->TE * 8, st);
-  cudaMemsetAsync(B.vtab_key, 0xFF, l->TV * 8, st);
+  cudaMemsetAsync(B.etab_key, 0xFF, l->TE * 16, st);
+  cudaMemsetAsync(B.vtab_key, 0xFF, l->TV * 16, st);
   if (o->flags & MF_WANT_CELLS) cudaMemsetAsync(B.ctab_key, 0xFF, l->TC * 8, st);
   return MF_OK;
 }

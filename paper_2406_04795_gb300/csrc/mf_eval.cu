@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_vertices_f64(MfFrame F
     F64Acc a = warp_f64<false, D>(R, x, nullptr, sq[w][0], sq[w][1], terms,
                                   B.vlist ? slist[w] : nullptr, B.list_r2, &nl);
     if (lane == 0) {
-      B.vtab_f[B.vert_slot[i]] = a.f;
+      mf_vtab_f(B, B.vert_slot[i]) = a.f;
       if (fabs(a.f) < 1e-12) atomicAdd(&B.cnt->n_near_zero, 1ull);
     }
     if (B.vlist) {
@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_recheck_vertices_f64(MfFram
     vertex_x_lanes<D>(F, y, x);
     F64Acc a = warp_f64<false, D>(R, x, nullptr, sq[w][0], sq[w][1], terms);
     if (lane == 0) {
-      B.vtab_f[B.vert_slot[i]] = a.f;
+      mf_vtab_f(B, B.vert_slot[i]) = a.f;
       if (fabs(a.f) < 1e-12) atomicAdd(&B.cnt->n_near_zero, 1ull);
     }
   }
@@ -718,7 +718,7 @@ __global__ void __launch_bounds__(MIX_THREADS) k_eval_mixed_f32(MfFrame F, MfRbf
       const bool recheck = fabs(fx) <= fmax(bound, band);
       if (VERTS) {
         const uint32_t slot = B.vert_slot[idx[v]];
-        B.vtab_f[slot] = fx;
+        mf_vtab_f(B, slot) = fx;
         if (recheck) {
           unsigned long long q = atomicAdd(&B.cnt->n_recheck, 1ull);
           if (q < B.max_vertices) B.recheck[q] = (uint32_t)idx[v];
@@ -781,6 +781,28 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_points_f64(MfRbfDev R,
 // summed in FP32 with the weak terms in the FP64 step.
 #define ROOT_TAU_SHIFT 3.5065579f
 
+// Warp sums of four values, every lane receiving all four: a transposed
+// butterfly (lanes split the values between halves, then quarters, before
+// the plain butterfly), 10 shuffles and 6 adds instead of 20 and 20.
+__device__ __forceinline__ void warp_sum4(float &a, float &b, float &c, float &e) {
+  const int lane = threadIdx.x & 31;
+  const bool up = lane & 16, odd = lane & 8;
+  // lower half keeps (a, b), upper half keeps (c, e)
+  const float r0 = __shfl_xor_sync(FULL, up ? a : c, 16);
+  const float r1 = __shfl_xor_sync(FULL, up ? b : e, 16);
+  const float x = (up ? c : a) + r0, y = (up ? e : b) + r1;
+  // then lanes with bit 3 clear keep x, the others y
+  float z = (odd ? y : x) + __shfl_xor_sync(FULL, odd ? x : y, 8);
+  z += __shfl_xor_sync(FULL, z, 4);
+  z += __shfl_xor_sync(FULL, z, 2);
+  z += __shfl_xor_sync(FULL, z, 1);
+  // lanes 0, 8, 16, 24 hold the totals of a, b, c, e
+  a = __shfl_sync(FULL, z, 0);
+  b = __shfl_sync(FULL, z, 8);
+  c = __shfl_sync(FULL, z, 16);
+  e = __shfl_sync(FULL, z, 24);
+}
+
 struct Root32 {
   float g, gp, gpp, gpa;  // gpa: the sum of |g'| terms (cancellation measure)
 };
@@ -826,10 +848,7 @@ __device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const int *near
     s1a = fmaf(fabsf(e), fabsf(proj), s1a);
     s2 = fmaf(e * proj, proj, s2);
   }
-  s0 = mf_warp_sum_f(s0);
-  s1 = mf_warp_sum_f(s1);
-  s1a = mf_warp_sum_f(s1a);
-  s2 = mf_warp_sum_f(s2);
+  warp_sum4(s0, s1, s1a, s2);
   const float gm = (float)R.gamma;
   Root32 r;
   r.g = s0 + b32;
@@ -1002,7 +1021,7 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
       int32_t yv[MF_MAXD];
 #pragma unroll
       for (int k = 0; k < MF_MAXD; k++) yv[k] = k < d ? B.edge_y[e * d + k] : 0;
-      const uint64_t slot = mf_table_find(B.vtab_key, B.vtab_mask, mf_vertex_key(F, yv));
+      const uint64_t slot = mf_table_find<2>(B.vtab_key, B.vtab_mask, mf_vertex_key(F, yv));
       if (slot != ~0ull) {
         const uint32_t vi = B.vtab_idx[slot];
         nl = B.vlist_n[vi];
@@ -1331,7 +1350,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_b_eval(const MfSlot *slots,
       unsigned long long terms[2] = {0, 0};
       const F64Acc a = warp_f64<false, MF_MAXD>(S.R, x, nullptr, sq[w][0], sq[w][1], terms);
       if (lane == 0) {
-        S.B.vtab_f[slot] = a.f;
+        mf_vtab_f(S.B, slot) = a.f;
         if (fabs(a.f) < 1e-12) atomicAdd(&S.B.cnt->n_near_zero, 1ull);
         atomicAdd(&S.B.cnt->eval_terms, terms[0]);
         atomicAdd(&S.B.cnt->eval_terms_weak, terms[1]);
@@ -1340,7 +1359,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_b_eval(const MfSlot *slots,
       double f, bound;
       warp_f32_bound(S.R, x, f, bound);
       if (lane == 0) {
-        S.B.vtab_f[slot] = f;
+        mf_vtab_f(S.B, slot) = f;
         if (fabs(f) <= fmax(bound, S.band)) {
           const unsigned long long q = atomicAdd(&S.B.cnt->n_recheck, 1ull);
           if (q < S.B.max_vertices) S.B.recheck[q] = (uint32_t)i;

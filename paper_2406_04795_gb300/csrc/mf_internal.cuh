@@ -63,12 +63,12 @@ struct MfCounters {
 // Pointers of one trace's resident device state (all owned by the context).
 struct MfTraceBufs {
   // edge hash table: key -> index into the edge list
-  unsigned long long *etab_key;
-  uint32_t *etab_val;
+  // 16-byte slots (key word, then the value word), so that a probe that
+  // finds its key has the value in the same memory sector
+  unsigned long long *etab_key;  // [TE][2]: key, edge-list index (u32)
   uint64_t etab_mask;
   // vertex hash table: key -> f
-  unsigned long long *vtab_key;
-  double *vtab_f;
+  unsigned long long *vtab_key;  // [TV][2]: key, f (f64)
   uint64_t vtab_mask;
   // cell hash table (keys only; winners append to the cell list)
   unsigned long long *ctab_key;
@@ -386,14 +386,15 @@ __device__ __forceinline__ uint64_t mf_hash64(unsigned long long k) {
 
 // Insert-if-absent.  Returns the slot; *won = true iff this call inserted.
 // Returns ~0ull if the table is full (probe count exceeded its size).
+template <int STRIDE = 1>
 __device__ __forceinline__ uint64_t mf_table_insert(unsigned long long *keys, uint64_t mask,
                                                     unsigned long long key, bool *won) {
   uint64_t h = mf_hash64(key) & mask;
   for (uint64_t probe = 0; probe <= mask; probe++) {
-    unsigned long long cur = keys[h];
+    unsigned long long cur = keys[h * STRIDE];
     if (cur == key) { *won = false; return h; }
     if (cur == MF_EMPTY_KEY) {
-      unsigned long long prev = atomicCAS(&keys[h], MF_EMPTY_KEY, key);
+      unsigned long long prev = atomicCAS(&keys[h * STRIDE], MF_EMPTY_KEY, key);
       if (prev == MF_EMPTY_KEY) { *won = true; return h; }
       if (prev == key) { *won = false; return h; }
     }
@@ -404,16 +405,25 @@ __device__ __forceinline__ uint64_t mf_table_insert(unsigned long long *keys, ui
 }
 
 // Lookup; returns the slot or ~0ull if absent.
+template <int STRIDE = 1>
 __device__ __forceinline__ uint64_t mf_table_find(const unsigned long long *keys, uint64_t mask,
                                                   unsigned long long key) {
   uint64_t h = mf_hash64(key) & mask;
   for (uint64_t probe = 0; probe <= mask; probe++) {
-    unsigned long long cur = keys[h];
+    unsigned long long cur = keys[h * STRIDE];
     if (cur == key) return h;
     if (cur == MF_EMPTY_KEY) return ~0ull;
     h = (h + 1) & mask;
   }
   return ~0ull;
+}
+
+// Value words of the interleaved vertex and edge tables.
+__device__ __forceinline__ double &mf_vtab_f(const MfTraceBufs &B, uint64_t slot) {
+  return reinterpret_cast<double *>(B.vtab_key)[2 * slot + 1];
+}
+__device__ __forceinline__ uint32_t &mf_etab_val(const MfTraceBufs &B, uint64_t slot) {
+  return *reinterpret_cast<uint32_t *>(B.etab_key + 2 * slot + 1);
 }
 
 // Warp-aggregated list allocation: every calling lane with take = true gets
@@ -476,7 +486,7 @@ struct MfTune {
 };
 
 // Evaluate f at vertex-list entries [begin, end) read from the device counter
-// (FP64 path); writes vtab_f of each vertex's slot.
+// (FP64 path); writes f into each vertex's table slot.
 void mf_launch_eval_vertices_f64(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
                                  const MfTune &T, int sms, cudaStream_t st);
 void mf_launch_eval_vertices_mixed(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,

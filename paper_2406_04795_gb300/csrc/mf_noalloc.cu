@@ -68,9 +68,9 @@ __global__ void k_noalloc_cell_edges(MfFrame F, MfTraceBufs B, uint64_t n_cells,
     for (int j = i + 1; j <= d; j++) {
       mask |= 1u << pi[j - 1];
       vj[pi[j - 1]] += 1;
-      const uint64_t slot = mf_table_find(B.etab_key, B.etab_mask, mf_edge_key(F, vi, mask));
+      const uint64_t slot = mf_table_find<2>(B.etab_key, B.etab_mask, mf_edge_key(F, vi, mask));
       if (slot == ~0ull) continue;
-      if (FILL) B.cell_idx[pos + count] = (int64_t)B.etab_val[slot];
+      if (FILL) B.cell_idx[pos + count] = (int64_t)mf_etab_val(B, slot);
       count++;
     }
     vi[pi[i]] += 1;
@@ -188,7 +188,7 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
     TV = pow2_at_least(MV + MV / 3 + 1);
     TC = pow2_at_least(MC + MC / 3 + 1);
     cell_edges = MC * (uint64_t)((d + 1) * d / 2);
-    need = 256 * 38 + 64 * 8 + nb * 136 + ((nb + 31) / 32) * d * 8 + nb * d * 16 + nb * 8 + TE * 12 + TV * 16 + TC * 8 + ME * (12 * d + 28) +
+    need = 256 * 38 + 64 * 8 + nb * 136 + ((nb + 31) / 32) * d * 8 + nb * d * 16 + nb * 8 + TE * 16 + TV * 16 + TC * 8 + ME * (12 * d + 28) +
            MV * (4 * d + 8) + MC * (5 * d + 8) + 8 + cell_edges * 8 + (MC / kScanTile + 2) * 8;
     if (need <= MF_NOALLOC_SCRATCH_BYTES || def < 1024) break;
   }
@@ -211,10 +211,8 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   float *bhi = (float *)cv.take((size_t)nblk * d * 4);
   MfTraceBufs B;
   memset(&B, 0, sizeof(B));
-  B.etab_key = (unsigned long long *)cv.take(TE * 8);
-  B.etab_val = (uint32_t *)cv.take(TE * 4);
-  B.vtab_key = (unsigned long long *)cv.take(TV * 8);
-  B.vtab_f = (double *)cv.take(TV * 8);
+  B.etab_key = (unsigned long long *)cv.take(TE * 16);
+  B.vtab_key = (unsigned long long *)cv.take(TV * 16);
   B.ctab_key = (unsigned long long *)cv.take(TC * 8);
   B.etab_mask = TE - 1;
   B.vtab_mask = TV - 1;
@@ -284,8 +282,8 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
 
   // Everything that must start empty.
   cudaMemsetAsync(cnt, 0, sizeof(MfCounters), st);
-  cudaMemsetAsync(B.etab_key, 0xFF, TE * 8, st);
-  cudaMemsetAsync(B.vtab_key, 0xFF, TV * 8, st);
+  cudaMemsetAsync(B.etab_key, 0xFF, TE * 16, st);
+  cudaMemsetAsync(B.vtab_key, 0xFF, TV * 16, st);
   cudaMemsetAsync(B.ctab_key, 0xFF, TC * 8, st);
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

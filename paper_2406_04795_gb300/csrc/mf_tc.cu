@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(TC_M, TcCfg<N>::kCtasPerSm) k_eval_tc(MfFrame 
       const double bound = 1.05 * (coord + expo + other) + 1e-30 + R.sum_abs_alpha * 1.2e-38;
       const double fx = (double)acc + R.b;
       const uint32_t slot = B.vert_slot[v];
-      B.vtab_f[slot] = fx;
+      mf_vtab_f(B, slot) = fx;
       if (far || fabs(fx) <= fmax(bound, band)) {
         const unsigned long long q = atomicAdd(&B.cnt->n_recheck, 1ull);
         if (q < B.max_vertices) B.recheck[q] = (uint32_t)v;

@@ -39,7 +39,7 @@ __device__ __forceinline__ void load_y(const int32_t *src, int d, int32_t *y) {
 __device__ __forceinline__ void visit_vertex(const MfFrame &F, const MfTraceBufs &B, const int32_t *w) {
   const unsigned long long key = mf_vertex_key(F, w);
   bool won;
-  const uint64_t slot = mf_table_insert(B.vtab_key, B.vtab_mask, key, &won);
+  const uint64_t slot = mf_table_insert<2>(B.vtab_key, B.vtab_mask, key, &won);
   if (slot == ~0ull) atomicOr(&B.cnt->err_table_full, 1u);
   const bool take = slot != ~0ull && won;
   const unsigned long long idx = mf_warp_alloc(&B.cnt->n_vertices, take);
@@ -53,9 +53,9 @@ __device__ __forceinline__ void visit_vertex(const MfFrame &F, const MfTraceBufs
 }
 
 __device__ __forceinline__ double lookup_f(const MfFrame &F, const MfTraceBufs &B, const int32_t *w) {
-  const uint64_t slot = mf_table_find(B.vtab_key, B.vtab_mask, mf_vertex_key(F, w));
+  const uint64_t slot = mf_table_find<2>(B.vtab_key, B.vtab_mask, mf_vertex_key(F, w));
   if (slot == ~0ull) { atomicOr(&B.cnt->err_missing, 1u); return 0.0; }
-  return B.vtab_f[slot];
+  return mf_vtab_f(B, slot);
 }
 
 // Appends edge (y, mask) with end values (fa at y, fb at y + e(mask)) if new.
@@ -63,7 +63,7 @@ __device__ __forceinline__ void emit_edge(const MfFrame &F, const MfTraceBufs &B
                                           uint32_t mask, double fa, double fb) {
   const unsigned long long key = mf_edge_key(F, y, mask);
   bool won;
-  const uint64_t slot = mf_table_insert(B.etab_key, B.etab_mask, key, &won);
+  const uint64_t slot = mf_table_insert<2>(B.etab_key, B.etab_mask, key, &won);
   if (slot == ~0ull) atomicOr(&B.cnt->err_table_full, 1u);
   const bool take = slot != ~0ull && won;
   const unsigned long long idx = mf_warp_alloc(&B.cnt->n_edges, take);
@@ -75,7 +75,7 @@ __device__ __forceinline__ void emit_edge(const MfFrame &F, const MfTraceBufs &B
   B.edge_mask[idx] = mask;
   B.edge_f[2 * idx] = fa;
   B.edge_f[2 * idx + 1] = fb;
-  B.etab_val[slot] = (uint32_t)idx;
+  mf_etab_val(B, slot) = (uint32_t)idx;
 }
 
 __device__ __forceinline__ bool vertex_in(const MfFrame &F, const int32_t *v) {
@@ -444,10 +444,10 @@ __device__ __forceinline__ void cell_edges_item(const MfFrame &F, const MfTraceB
     load_y(vi, d, w);
     for (int i = 0; i <= d; i++) {
       if (i > 0) w[pi[i - 1]] += 1;
-      const uint64_t slot = mf_table_find(B.vtab_key, B.vtab_mask, mf_vertex_key(F, w));
+      const uint64_t slot = mf_table_find<2>(B.vtab_key, B.vtab_mask, mf_vertex_key(F, w));
       if (slot == ~0ull) continue;
       in |= 1u << i;
-      if (B.vtab_f[slot] >= 0.0) pos |= 1u << i;
+      if (mf_vtab_f(B, slot) >= 0.0) pos |= 1u << i;
     }
     sg = in | (pos << 16);
     B.cell_sgn[c] = sg;
@@ -462,13 +462,13 @@ __device__ __forceinline__ void cell_edges_item(const MfFrame &F, const MfTraceB
     for (int j = i + 1; j <= d; j++) {
       mask |= 1u << pi[j - 1];
       if (!((in >> i) & (in >> j) & 1u) || ((pos >> i) & 1u) == ((pos >> j) & 1u)) continue;
-      const uint64_t slot = mf_table_find(B.etab_key, B.etab_mask, mf_edge_key(F, vi, mask));
+      const uint64_t slot = mf_table_find<2>(B.etab_key, B.etab_mask, mf_edge_key(F, vi, mask));
       if (slot == ~0ull) {
         atomicOr(&B.cnt->err_missing, 2u);
         B.cell_idx[at++] = -1;
         continue;
       }
-      B.cell_idx[at++] = (int64_t)B.etab_val[slot];
+      B.cell_idx[at++] = (int64_t)mf_etab_val(B, slot);
     }
     vi[pi[i]] += 1;
   }
@@ -1021,13 +1021,11 @@ static int setup_buffers(mf_ctx *ctx, int d, uint64_t ME, uint64_t MV, uint64_t 
   const uint64_t TE = next_pow2(ME + ME / 3 + 1), TV = next_pow2(MV + MV / 3 + 1),
                  TC = next_pow2(MC + MC / 3 + 1);
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  size_t tb = al(TE * 8) + al(TE * 4) + al(TV * 8) + al(TV * 8) + al(TC * 8);
+  size_t tb = al(TE * 16) + al(TV * 16) + al(TC * 8);
   char *t = (char *)mf_ctx_buffer(ctx, MF_SLOT_TABLES, tb);
   if (!t) return MF_ERR_OOM;
-  B->etab_key = (unsigned long long *)t; t += al(TE * 8);
-  B->etab_val = (uint32_t *)t; t += al(TE * 4);
-  B->vtab_key = (unsigned long long *)t; t += al(TV * 8);
-  B->vtab_f = (double *)t; t += al(TV * 8);
+  B->etab_key = (unsigned long long *)t; t += al(TE * 16);
+  B->vtab_key = (unsigned long long *)t; t += al(TV * 16);
   B->ctab_key = (unsigned long long *)t;
   B->etab_mask = TE - 1;
   B->vtab_mask = TV - 1;
@@ -1183,8 +1181,8 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
   const int sms = ctx->sms;
 
   cudaMemsetAsync(B.cnt, 0, sizeof(MfCounters), st);
-  cudaMemsetAsync(B.etab_key, 0xFF, (B.etab_mask + 1) * 8, st);
-  cudaMemsetAsync(B.vtab_key, 0xFF, (B.vtab_mask + 1) * 8, st);
+  cudaMemsetAsync(B.etab_key, 0xFF, (B.etab_mask + 1) * 16, st);
+  cudaMemsetAsync(B.vtab_key, 0xFF, (B.vtab_mask + 1) * 16, st);
   if (opts->flags & MF_WANT_CELLS) cudaMemsetAsync(B.ctab_key, 0xFF, (B.ctab_mask + 1) * 8, st);
 
   auto eval = [&]() {
