@@ -309,52 +309,90 @@ __global__ void __launch_bounds__(EXPAND_WARPS * 32) k_expand_edges(MfFrame F, M
 }
 
 // ---------------------------------------------------------------------------
-// Cells (Sec. IV-C): the |p1|!|p2|! n-simplex cofaces of every traced edge,
-// de-duplicated through the cell table.  Coface j orders p1's elements by the
-// Lehmer code j mod |p1|! and p2's by j / |p1|!; the walk is then rotated so
-// that d comes last: vertex z = y + sum_{i<pos(d)} e_sigma_i - 1.
-// Key = rank(pi) + d! * key(z).
+// Cells (Sec. IV-C): the |p1|!|p2|! n-simplex cofaces of every traced edge.
+// Coface j orders p1's elements by the Lehmer code j mod |p1|! and p2's by
+// j / |p1|!; the walk is then rotated so that d comes last: vertex
+// z = y + sum_{i<pos(d)} e_sigma_i - 1, permutation pi.
+//
+// A cell has several traced edges (every pair of in-domain vertices of
+// opposite sign: they are connected through crossing triangles whose
+// vertices are in the domain, which the search follows).  It is emitted once,
+// by its canonical pair: the first such pair (i, j), i < j, in the order of
+// its vertices z, z + e(pi_0), ...  The vertex signs come from the edge's
+// link table, so the cell needs no hash table, and its sign mask and CSR
+// row length are known when it is written.
 // ---------------------------------------------------------------------------
 __constant__ uint32_t c_fact[13] = {1u, 1u, 2u, 6u, 24u, 120u, 720u, 5040u, 40320u, 362880u,
                                     3628800u, 39916800u, 479001600u};
 
-__device__ __forceinline__ uint32_t perm_rank(const int *pi, int d) {
-  uint32_t r = 0;
-  for (int i = 0; i < d; i++) {
-    int less = 0;
-    for (int k = i + 1; k < d; k++) less += pi[k] < pi[i];
-    r += (uint32_t)less * c_fact[d - 1 - i];
-  }
-  return r;
-}
+// Link table of edge (y, S): every vertex of an n-coface of the edge is
+// y + e(M) for M within S (a), y + e(S) + e(M) (b) or y - e(M) (c) for M
+// within T = {0..d-1} \ S, indexed by M's bits compressed to S or T.
+// Entry bit 0: in the vertex table (in the domain); bit 1: f >= 0.
+#define LINK_MAX (1 << MF_MAXD)
+struct CellLink {
+  uint8_t a[LINK_MAX], b[LINK_MAX], c[LINK_MAX];
+};
+#define CELL_WARPS 8
 
 __device__ __forceinline__ void cells_enum_edge(const MfFrame &F, const MfTraceBufs &B, uint64_t e,
-                                                int lane);
+                                                int lane, CellLink &L);
 
-__global__ void k_cells_enum(MfFrame F, MfTraceBufs B, uint64_t n_edges) {
+__global__ void __launch_bounds__(CELL_WARPS * 32) k_cells_enum(MfFrame F, MfTraceBufs B,
+                                                                uint64_t n_edges) {
+  __shared__ CellLink sl[CELL_WARPS];
   const int lane = threadIdx.x & 31;
   const uint64_t e = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   if (e >= n_edges) return;
-  cells_enum_edge(F, B, e, lane);
+  cells_enum_edge(F, B, e, lane, sl[threadIdx.x >> 5]);
 }
 
-// The n-cofaces j = lane, lane + 32, ... of edge e.  Orderings and
-// permutations are kept as 4-bit nibbles in 64-bit words, so the decode
-// needs no indexed arrays (they would live in local memory).
+// The n-cofaces j = lane, lane + 32, ... of edge e (all lanes of the warp).
+// Orderings and permutations are kept as 4-bit nibbles in 64-bit words, so
+// the decode needs no indexed arrays (they would live in local memory).
 __device__ __forceinline__ void cells_enum_edge(const MfFrame &F, const MfTraceBufs &B, uint64_t e,
-                                                int lane) {
+                                                int lane, CellLink &L) {
   const int d = F.d;
   int32_t y[MF_MAXD];
   load_y(B.edge_y + e * d, d, y);
-  const uint32_t S = B.edge_mask[e];
+  const uint32_t S = B.edge_mask[e], T = ~S & ((1u << d) - 1u);
+  const int n1 = __popc(S), n2 = d + 1 - n1;
+  // the link table, one vertex lookup per entry
+  const int na = 1 << n1, nb = 1 << (n2 - 1);
+  __syncwarp();  // the previous edge's cofaces have read the table
+  for (int q = lane; q < na + 2 * nb; q += 32) {
+    int32_t w[MF_MAXD];
+    load_y(y, d, w);
+    uint8_t *dst;
+    if (q < na) {
+      mf_add_mask(d, w, deposit_bits((uint32_t)q, S), 1);
+      dst = &L.a[q];
+    } else if (q < na + nb) {
+      const uint32_t r = (uint32_t)(q - na);
+      mf_add_mask(d, w, S | deposit_bits(r, T), 1);
+      dst = &L.b[r];
+    } else {
+      const uint32_t r = (uint32_t)(q - na - nb);
+      mf_add_mask(d, w, deposit_bits(r, T), -1);
+      dst = &L.c[r];
+    }
+    uint8_t code = 0;
+    if (vertex_in(F, w)) {
+      const uint64_t slot = mf_table_find<2>(B.vtab_key, B.vtab_mask, mf_vertex_key(F, w));
+      if (slot != ~0ull) code = mf_vtab_f(B, slot) >= 0.0 ? 3 : 1;
+    }
+    *dst = code;
+  }
+  __syncwarp();
   uint64_t ls = 0, lt = 0;  // the elements of p1 and of p2 (with d), ascending
-  int n1 = 0, n2 = 0;
-  for (int i = 0; i <= d; i++) {
-    if (i < d && ((S >> i) & 1u)) ls |= (uint64_t)i << (4 * n1++);
-    else lt |= (uint64_t)i << (4 * n2++);
+  {
+    int c1 = 0, c2 = 0;
+    for (int i = 0; i <= d; i++) {
+      if (i < d && ((S >> i) & 1u)) ls |= (uint64_t)i << (4 * c1++);
+      else lt |= (uint64_t)i << (4 * c2++);
+    }
   }
   const uint32_t f1 = c_fact[n1], total = f1 * c_fact[n2];
-  const unsigned long long dfact = c_fact[d];
   for (uint32_t j = lane; j < total; j += 32) {
     // Lehmer decode of each part: sigma_i at nibble i
     uint64_t sig = 0;
@@ -373,38 +411,59 @@ __device__ __forceinline__ void cells_enum_edge(const MfFrame &F, const MfTraceB
         pool = low | ((pool >> (4 * (q + 1))) << (4 * q));
       }
     }
-    // rotate so that d comes last: vertex z = y + e(sigma_0..sigma_{p-1}) - 1
-    int p = 0;
-    uint32_t inc = 0;
-    for (int i = 0; i <= d; i++) {
-      const int v = (int)((sig >> (4 * i)) & 15ull);
-      if (v == d) p = i;
+    int p = 0;  // position of d in sigma
+    for (int i = 0; i <= d; i++)
+      if ((int)((sig >> (4 * i)) & 15ull) == d) p = i;
+    // vertex signs in the cell's order: y sits at position a = d - p and
+    // y + e(S) at a + n1; positions a + m (m <= p) are y + e(sigma_0..m-1),
+    // positions i < a are y - e(sigma_{p+i+1..d})
+    const int a = d - p;
+    uint32_t inm = 0, posm = 0, ia = 0, ib = 0, ic = 0;
+    for (int m = 0; m <= p; m++) {
+      if (m > 0) {
+        const uint32_t v = (uint32_t)((sig >> (4 * (m - 1))) & 15ull);
+        if (m - 1 < n1) ia |= 1u << __popc(S & ((1u << v) - 1u));
+        else ib |= 1u << __popc(T & ((1u << v) - 1u));
+      }
+      const uint32_t code = m <= n1 ? L.a[ia] : L.b[ib];
+      inm |= (code & 1u) << (a + m);
+      posm |= ((code >> 1) & 1u) << (a + m);
     }
-    for (int i = 0; i < p; i++) inc |= 1u << ((sig >> (4 * i)) & 15ull);
-    int32_t z[MF_MAXD];
-#pragma unroll
-    for (int k = 0; k < MF_MAXD; k++) z[k] = k < d ? y[k] + (int32_t)((inc >> k) & 1u) - 1 : 0;
-    // pi = sigma_{p+1..d}, sigma_{0..p-1}; its Lehmer rank
-    const uint64_t hi = sig >> (4 * (p + 1)), lo = p ? (sig & ((1ull << (4 * p)) - 1ull)) : 0ull;
-    const uint64_t pi = hi | (lo << (4 * (d - p)));
-    uint32_t used = 0, rank = 0;
-    for (int i = 0; i < d; i++) {
-      const uint32_t v = (uint32_t)((pi >> (4 * i)) & 15ull);
-      rank += (uint32_t)__popc(((1u << v) - 1u) & ~used) * c_fact[d - 1 - i];
-      used |= 1u << v;
+    for (int i = a - 1; i >= 0; i--) {
+      const uint32_t v = (uint32_t)((sig >> (4 * (p + i + 1))) & 15ull);
+      ic |= 1u << __popc(T & ((1u << v) - 1u));
+      const uint32_t code = L.c[ic];
+      inm |= (code & 1u) << i;
+      posm |= ((code >> 1) & 1u) << i;
     }
-    const unsigned long long key = (unsigned long long)rank + dfact * mf_vertex_key(F, z);
-    bool won;
-    const uint64_t slot = mf_table_insert(B.ctab_key, B.ctab_mask, key, &won);
-    if (slot == ~0ull) atomicOr(&B.cnt->err_table_full, 1u);
-    const bool take = slot != ~0ull && won;
+    // canonical pair: the first position with an in-domain vertex of the
+    // other sign after it, and the first such vertex
+    const uint32_t P = inm & posm, N = inm & ~posm;
+    int ci = -1, cj = -1;
+    for (int i = 0; i < d && ci < 0; i++) {
+      if (!((inm >> i) & 1u)) continue;
+      const uint32_t other = (((P >> i) & 1u) ? N : P) >> (i + 1);
+      if (other) {
+        ci = i;
+        cj = i + 1 + __ffs(other) - 1;
+      }
+    }
+    const bool take = ci == a && cj == a + n1;
     const unsigned long long idx = mf_warp_alloc(&B.cnt->n_cells, take);
     if (!take) continue;
     if (idx >= B.max_cells) { atomicOr(&B.cnt->err_overflow, 1u); continue; }
+    // z = y + e(sigma_0..sigma_{p-1}) - 1; pi = sigma_{p+1..d}, sigma_{0..p-1}
+    uint32_t inc = 0;
+    for (int i = 0; i < p; i++) inc |= 1u << ((sig >> (4 * i)) & 15ull);
+    const uint64_t hi = sig >> (4 * (p + 1)), lo = p ? (sig & ((1ull << (4 * p)) - 1ull)) : 0ull;
+    const uint64_t pi = hi | (lo << (4 * (d - p)));
     for (int k = 0; k < d; k++) {
-      B.cell_y[idx * d + k] = z[k];
+      B.cell_y[idx * d + k] = y[k] + (int32_t)((inc >> k) & 1u) - 1;
       B.cell_perm[idx * d + k] = (uint8_t)((pi >> (4 * k)) & 15ull);
     }
+    // sign mask and CSR row length (paths without these arrays count later)
+    if (B.cell_sgn) B.cell_sgn[idx] = inm | (posm << 16);
+    if (B.cell_off) B.cell_off[idx] = (int64_t)__popc(P) * (int64_t)__popc(N);
   }
 }
 
@@ -696,14 +755,16 @@ __global__ void k_b_plan_edges(const MfSlot *slots, MfBatchPlan *P, int n, int m
   if (t == 0) p[n] = total;
 }
 
-__global__ void k_b_cells_enum(const MfSlot *slots, const MfBatchPlan *P, int n) {
+__global__ void __launch_bounds__(CELL_WARPS * 32) k_b_cells_enum(const MfSlot *slots,
+                                                                  const MfBatchPlan *P, int n) {
+  __shared__ CellLink sl[CELL_WARPS];
   const unsigned long long total = P->pe[n];
   const int lane = threadIdx.x & 31;
   const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
   for (unsigned long long item = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
        item < total; item += nwarps) {
     const int t = mf_slot_of(P->pe, n, item);
-    cells_enum_edge(slots[t].F, slots[t].B, item - P->pe[t], lane);
+    cells_enum_edge(slots[t].F, slots[t].B, item - P->pe[t], lane, sl[threadIdx.x >> 5]);
   }
 }
 
@@ -1018,18 +1079,15 @@ static int setup_buffers(mf_ctx *ctx, int d, uint64_t ME, uint64_t MV, uint64_t 
                          int n_sv, MfTraceBufs *B) {
   memset(B, 0, sizeof(*B));
   // load factor <= 3/4 at capacity
-  const uint64_t TE = next_pow2(ME + ME / 3 + 1), TV = next_pow2(MV + MV / 3 + 1),
-                 TC = next_pow2(MC + MC / 3 + 1);
+  const uint64_t TE = next_pow2(ME + ME / 3 + 1), TV = next_pow2(MV + MV / 3 + 1);
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  size_t tb = al(TE * 16) + al(TV * 16) + al(TC * 8);
+  size_t tb = al(TE * 16) + al(TV * 16);
   char *t = (char *)mf_ctx_buffer(ctx, MF_SLOT_TABLES, tb);
   if (!t) return MF_ERR_OOM;
   B->etab_key = (unsigned long long *)t; t += al(TE * 16);
   B->vtab_key = (unsigned long long *)t; t += al(TV * 16);
-  B->ctab_key = (unsigned long long *)t;
   B->etab_mask = TE - 1;
   B->vtab_mask = TV - 1;
-  B->ctab_mask = TC - 1;
   size_t eb = al(ME * d * 4) + al(ME * 4) + al(ME * 16) + al(ME * 8) + al(ME * d * 8);
   char *e = (char *)mf_ctx_buffer(ctx, MF_SLOT_EDGES, eb);
   if (!e) return MF_ERR_OOM;
@@ -1183,7 +1241,6 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
   cudaMemsetAsync(B.cnt, 0, sizeof(MfCounters), st);
   cudaMemsetAsync(B.etab_key, 0xFF, (B.etab_mask + 1) * 16, st);
   cudaMemsetAsync(B.vtab_key, 0xFF, (B.vtab_mask + 1) * 16, st);
-  if (opts->flags & MF_WANT_CELLS) cudaMemsetAsync(B.ctab_key, 0xFF, (B.ctab_mask + 1) * 8, st);
 
   auto eval = [&]() {
     if (mixed) mf_launch_eval_vertices_mixed(F, R, B, opts->precision, band, ctx->tune, sms, st);
@@ -1256,8 +1313,8 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
                                                 ((size_t)n_cells / SCAN_TILE + 2) * 8);
     if (!scratch) return MF_ERR_OOM;
     {
-      MfProfScope ps(ctx, MF_PH_CSR, st, 4, n_cells);
-      k_cells_edges<false><<<g, 256, 0, st>>>(F, B, (uint64_t)n_cells, B.cell_off);
+      // the enumeration wrote each cell's sign mask and CSR row length
+      MfProfScope ps(ctx, MF_PH_CSR, st, 3, n_cells);
       exclusive_scan(B.cell_off, B.cell_off, n_cells, scratch, st);
     }
     rc = mf_cuda_check(ctx, cudaMemcpyAsync(&n_cell_edges, B.cell_off + n_cells, 8,
