@@ -134,10 +134,11 @@ def roofline(stats, w, clocks, n_sms=152):
         per_strong = (5 * d + 5 if dom == "roots" else 3 * d + 3) + FP64_EXP_FLOPS
         flops = s["terms"] * per_strong / max(s["launches"], 1)
         ach = flops / (ms_per_launch * 1e-3) / 1e12
-        # DRAM bytes per launch from the ncu capture of k_roots_f64 (41.7 B per
-        # edge: the edge records; the support vectors stay in L2), scaled by
-        # the edges one launch processes
-        traffic = 41.7 * s["units"] / max(s["launches"], 1) if dom == "roots" else None
+        # DRAM bytes per launch from the ncu capture of k_roots_f64 on the
+        # lambda = 0.15 case (340 B per edge: the edge records and the base
+        # vertices' support-vector lists), scaled by the edges one launch
+        # processes
+        traffic = 339.7 * s["units"] / max(s["launches"], 1) if dom == "roots" else None
         return {"kernel": "k_roots_f64" if dom == "roots" else "k_eval_vertices_f64",
                 "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": ach / fp64_peak, "traffic": traffic,
