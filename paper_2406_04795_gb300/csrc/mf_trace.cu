@@ -394,9 +394,9 @@ __device__ __forceinline__ void cells_enum_edge(const MfFrame &F, const MfTraceB
   }
   const uint32_t f1 = c_fact[n1], total = f1 * c_fact[n2];
   for (uint32_t j = lane; j < total; j += 32) {
-    // Lehmer decode of each part: sigma_i at nibble i
+    // Lehmer decode of each part: sigma_i at nibble i; p = position of d
     uint64_t sig = 0;
-    int at = 0;
+    int at = 0, p = 0;
     uint32_t rr[2] = {j % f1, j / f1};
 #pragma unroll
     for (int part = 0; part < 2; part++) {
@@ -406,14 +406,13 @@ __device__ __forceinline__ void cells_enum_edge(const MfFrame &F, const MfTraceB
       for (int i = 0; i < np; i++) {
         const uint32_t f = c_fact[np - 1 - i], q = r / f;
         r -= q * f;
-        sig |= ((pool >> (4 * q)) & 15ull) << (4 * at++);
+        const uint64_t v = (pool >> (4 * q)) & 15ull;
+        if (v == (uint64_t)d) p = at;
+        sig |= v << (4 * at++);
         const uint64_t low = q ? (pool & ((1ull << (4 * q)) - 1ull)) : 0ull;
         pool = low | ((pool >> (4 * (q + 1))) << (4 * q));
       }
     }
-    int p = 0;  // position of d in sigma
-    for (int i = 0; i <= d; i++)
-      if ((int)((sig >> (4 * i)) & 15ull) == d) p = i;
     // vertex signs in the cell's order: y sits at position a = d - p and
     // y + e(S) at a + n1; positions a + m (m <= p) are y + e(sigma_0..m-1),
     // positions i < a are y - e(sigma_{p+i+1..d})
@@ -436,20 +435,26 @@ __device__ __forceinline__ void cells_enum_edge(const MfFrame &F, const MfTraceB
       inm |= (code & 1u) << i;
       posm |= ((code >> 1) & 1u) << i;
     }
-    // canonical pair: the first position with an in-domain vertex of the
-    // other sign after it, and the first such vertex
+    // canonical pair: the first position i with an in-domain vertex of the
+    // other sign after it (a positive vertex below the highest negative one,
+    // or the reverse), and the first such vertex j after it
     const uint32_t P = inm & posm, N = inm & ~posm;
-    int ci = -1, cj = -1;
-    for (int i = 0; i < d && ci < 0; i++) {
-      if (!((inm >> i) & 1u)) continue;
-      const uint32_t other = (((P >> i) & 1u) ? N : P) >> (i + 1);
-      if (other) {
-        ci = i;
-        cj = i + 1 + __ffs(other) - 1;
-      }
+    const uint32_t belowN = N ? (1u << (31 - __clz(N))) - 1u : 0u;  // positions below N's top
+    const uint32_t belowP = P ? (1u << (31 - __clz(P))) - 1u : 0u;
+    const uint32_t cand = (P & belowN) | (N & belowP);
+    const int ci = cand ? __ffs(cand) - 1 : -1;
+    bool take = false;
+    if (ci == a) {
+      const uint32_t other = (((P >> ci) & 1u) ? N : P) >> (ci + 1);
+      take = ci + __ffs(other) == a + n1;
     }
-    const bool take = ci == a && cj == a + n1;
-    const unsigned long long idx = mf_warp_alloc(&B.cnt->n_cells, take);
+    // one trace per warp here: a ballot-based allocation suffices
+    const unsigned act = __activemask(), m = __ballot_sync(act, take);
+    unsigned long long base = 0;
+    const int leader = m ? __ffs(m) - 1 : lane;
+    if (m && lane == leader) base = atomicAdd(&B.cnt->n_cells, (unsigned long long)__popc(m));
+    base = __shfl_sync(act, base, leader);
+    const unsigned long long idx = base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
     if (!take) continue;
     if (idx >= B.max_cells) { atomicOr(&B.cnt->err_overflow, 1u); continue; }
     // z = y + e(sigma_0..sigma_{p-1}) - 1; pi = sigma_{p+1..d}, sigma_{0..p-1}
