@@ -15,7 +15,12 @@
 // idle on skipped terms and each batch of 32 runs one code path.  The weak
 // terms' error is bounded on the fly (their summed magnitude times a relative
 // bound computed on the host); if the bound would push the total error above
-// 2.5e-13 the point is evaluated again with every kept term strong.
+// 2.5e-13 the point is evaluated again with every kept term strong.  Every
+// FP64 instruction holds the FP64 pipe for the whole warp, so values that
+// are the same for all lanes (coordinates, splits) are computed one axis per
+// lane and broadcast.  The vertex evaluation also records, per vertex, the
+// support vectors within the root screen's reach (the per-vertex lists the
+// root solve screens instead of all vectors).
 //
 // Mixed FP32 SIMT path: one thread per two points, support vectors broadcast
 // from shared memory, FP32 differences and ex2, and a per-point rigorous bound
@@ -755,8 +760,11 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_points_f64(MfRbfDev R,
 // g(0) and g(1) of opposite sign (Sec. VI's "iterative algorithm").
 //
 // 1. Segment screen (FP32): the support vectors within the FP64 screen
-//    distance of the whole segment are compacted into a per-warp list in
-//    shared memory, strong ones from the front, weak ones from the back.
+//    distance of the whole segment are compacted into per-warp lists in
+//    shared memory: terms above ROOT_TAU from the front of one list, weak
+//    ones from its back, the band between (mid) in a second list.  The
+//    candidates are the base vertex's list when the FP64 vertex evaluation
+//    recorded one, else all vectors by 32-vector block.
 // 2. FP32 Halley steps (t - 2 g g' / (2 g'^2 - g g''), Newton where the
 //    denominator is not positive) from the linear interpolant of the end
 //    values, over that list, with hi/lo-split coordinates (x = x_hi + x_lo)
