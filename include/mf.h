@@ -18,7 +18,7 @@
  *    stream).  Calls enqueue their kernels on it and return after the counts
  *    they report are known (they synchronise that stream).
  *  - The context owns its resident device memory (hash tables, frontier and
- *    vertex lists, cell tables) inside the HBM budget given at creation.
+ *    vertex lists, cell lists) inside the HBM budget given at creation.
  *  - Multi-dimensional arrays are row-major.  d is the configuration-space
  *    dimension, 2 <= d <= MF_MAXD.
  */
@@ -87,7 +87,7 @@ typedef struct {
   double root_tol;         /* root solve stops when |Newton step| <= root_tol; 0 = 1e-12 */
   int64_t max_edges;       /* capacity of the resident edge table; 0 = 2^24 */
   int64_t max_vertices;    /* capacity of the vertex table; 0 = max_edges */
-  int64_t max_cells;       /* capacity of the cell table; 0 = 2 * max_edges */
+  int64_t max_cells;       /* capacity of the cell list; 0 = 2 * max_edges */
   uint32_t flags;          /* MF_WANT_ROOTS | MF_WANT_CELLS */
 } mf_trace_opts;
 
@@ -174,8 +174,8 @@ int mf_domain_table(int32_t d, double lambda, const mf_domain *dom, int32_t *smi
  * [n] or NULL, 1 where y lies inside the key packing (keys of such vertices
  * are distinct), else 0 (the key aliases another vertex).  The packing covers
  * every vertex within three lattice steps of the box; edge keys are
- * key * 2^d + mask and cell keys key * d! + rank.  MF_ERR_DOMAIN when edge or
- * cell keys of this domain and lambda would not fit 64 bits. */
+ * key * 2^d + mask.  MF_ERR_DOMAIN when edge keys of this domain and lambda
+ * would not fit 64 bits. */
 int mf_vertex_keys(int32_t d, double lambda, const mf_domain *dom, const int32_t *y, int64_t n,
                    uint64_t *keys, uint8_t *in_range);
 

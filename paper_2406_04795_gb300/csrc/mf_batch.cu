@@ -31,10 +31,10 @@ struct Bump {
 };
 
 struct TraceLayout {
-  size_t rbf, dom, cnt, etab_key, vtab_key, ctab_key;
+  size_t rbf, dom, cnt, etab_key, vtab_key;
   size_t edge_y, edge_mask, edge_f, edge_t, edge_pt, vert_y, vert_slot, recheck;
   size_t cell_y, cell_perm, cell_sgn, cell_off, scan;
-  uint64_t ME, MV, MC, TE, TV, TC;
+  uint64_t ME, MV, MC, TE, TV;
   std::vector<int2> tab;
 };
 
@@ -119,13 +119,11 @@ int mf_layout_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom, const 
     return mf_set_error(ctx, MF_ERR_INVALID, "max_edges / max_vertices must be < 2^32");
   l->TE = mf_next_pow2(l->ME + l->ME / 3 + 1);
   l->TV = mf_next_pow2(l->MV + l->MV / 3 + 1);
-  l->TC = mf_next_pow2(l->MC + l->MC / 3 + 1);
   l->rbf = bump->take(mf_rbf_prep_bytes(d, r.n_sv));
   l->dom = bump->take(l->tab.size() * sizeof(int2) + 8);
   l->cnt = bump->take(sizeof(MfCounters));
   l->etab_key = bump->take(l->TE * 16);
   l->vtab_key = bump->take(l->TV * 16);
-  l->ctab_key = bump->take((o->flags & MF_WANT_CELLS) ? l->TC * 8 : 8);
   l->edge_y = bump->take(l->ME * d * 4);
   l->edge_mask = bump->take(l->ME * 4);
   l->edge_f = bump->take(l->ME * 16);
@@ -162,8 +160,6 @@ int mf_setup_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_trace_opts *o, char 
   B.etab_mask = l->TE - 1;
   B.vtab_key = (unsigned long long *)(base + l->vtab_key);
   B.vtab_mask = l->TV - 1;
-  B.ctab_key = (unsigned long long *)(base + l->ctab_key);
-  B.ctab_mask = (o->flags & MF_WANT_CELLS) ? l->TC - 1 : 0;
   B.edge_y = (int32_t *)(base + l->edge_y);
   B.edge_mask = (uint32_t *)(base + l->edge_mask);
   B.edge_f = (double *)(base + l->edge_f);
@@ -193,7 +189,6 @@ int mf_setup_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_trace_opts *o, char 
   cudaMemsetAsync(B.cnt, 0, sizeof(MfCounters), st);
   cudaMemsetAsync(B.etab_key, 0xFF, l->TE * 16, st);
   cudaMemsetAsync(B.vtab_key, 0xFF, l->TV * 16, st);
-  if (o->flags & MF_WANT_CELLS) cudaMemsetAsync(B.ctab_key, 0xFF, l->TC * 8, st);
   return MF_OK;
 }
 

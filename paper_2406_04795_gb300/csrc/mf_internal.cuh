@@ -71,8 +71,6 @@ struct MfTraceBufs {
   unsigned long long *vtab_key;  // [TV][2]: key, f (f64)
   uint64_t vtab_mask;
   // cell hash table (keys only; winners append to the cell list)
-  unsigned long long *ctab_key;
-  uint64_t ctab_mask;
   // edge list (insertion order; each BFS level is a contiguous range)
   int32_t *edge_y;     // [ME][d]
   uint32_t *edge_mask; // [ME]
@@ -294,8 +292,8 @@ static inline bool mf_vertex_in_packing(const MfFrame &F, const int32_t *y) {
 }
 
 // Host: sets the key packing of a frame whose lattice and box are set; false
-// when vertex, edge (vkey 2^d + mask) or cell (d! vkey + rank) keys would not
-// fit 64 bits.  Every vertex the kernels key lies within one lattice step
+// when vertex or edge (vkey 2^d + mask) keys would not fit 64 bits (cells
+// are written once each and need no key).  Every vertex the kernels key lies within one lattice step
 // (|dy_i| <= 1) of a point p of the box; the packing covers three.  With
 // u = (p - o) / lam in [A, B] and s' = sqrt(d+1) sum(u), such a vertex has
 // y_i - c s within 2k of u_i (k steps, d c < 1), y_i - q(s) within [-e, 1 + e]
@@ -329,10 +327,8 @@ static inline bool mf_frame_pack_keys(MfFrame *F) {
   F->sstride = (uint64_t)prod;
   prod *= (unsigned __int128)(s1 - s0 + 1);
   if (prod > ((unsigned __int128)1 << 62)) return false;
-  unsigned __int128 fact = 1;
-  for (int i = 2; i <= d; i++) fact *= i;
   const unsigned __int128 lim = ((unsigned __int128)1 << 64) - 2;
-  return !((prod << d) > lim || prod * fact > lim);
+  return !((prod << d) > lim);
 }
 
 // Edge (y, p1) with p1 a non-empty mask over {0..d-1}: key = vidx * 2^d + p1.

@@ -178,7 +178,7 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
 
   // Capacities: the caller's; a zero leaves the largest default that fits.
   const size_t nb = (size_t)n;
-  uint64_t ME = 0, MV = 0, MC = 0, TE = 0, TV = 0, TC = 0, cell_edges = 0;
+  uint64_t ME = 0, MV = 0, MC = 0, TE = 0, TV = 0, cell_edges = 0;
   size_t need = 0;
   for (uint64_t def = 1ull << 17;; def >>= 1) {
     ME = opts->max_edges > 0 ? (uint64_t)opts->max_edges : def;
@@ -186,9 +186,8 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
     MC = opts->max_cells > 0 ? (uint64_t)opts->max_cells : 2 * ME;
     TE = pow2_at_least(ME + ME / 3 + 1);
     TV = pow2_at_least(MV + MV / 3 + 1);
-    TC = pow2_at_least(MC + MC / 3 + 1);
     cell_edges = MC * (uint64_t)((d + 1) * d / 2);
-    need = 256 * 38 + 64 * 8 + nb * 136 + ((nb + 31) / 32) * d * 8 + nb * d * 16 + nb * 8 + TE * 16 + TV * 16 + TC * 8 + ME * (12 * d + 28) +
+    need = 256 * 38 + 64 * 8 + nb * 136 + ((nb + 31) / 32) * d * 8 + nb * d * 16 + nb * 8 + TE * 16 + TV * 16 + ME * (12 * d + 28) +
            MV * (4 * d + 8) + MC * (5 * d + 8) + 8 + cell_edges * 8 + (MC / kScanTile + 2) * 8;
     if (need <= MF_NOALLOC_SCRATCH_BYTES || def < 1024) break;
   }
@@ -213,10 +212,8 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   memset(&B, 0, sizeof(B));
   B.etab_key = (unsigned long long *)cv.take(TE * 16);
   B.vtab_key = (unsigned long long *)cv.take(TV * 16);
-  B.ctab_key = (unsigned long long *)cv.take(TC * 8);
   B.etab_mask = TE - 1;
   B.vtab_mask = TV - 1;
-  B.ctab_mask = TC - 1;
   B.edge_y = (int32_t *)cv.take(ME * d * 4);
   B.edge_mask = (uint32_t *)cv.take(ME * 4);
   B.edge_f = (double *)cv.take(ME * 16);
@@ -284,7 +281,6 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   cudaMemsetAsync(cnt, 0, sizeof(MfCounters), st);
   cudaMemsetAsync(B.etab_key, 0xFF, TE * 16, st);
   cudaMemsetAsync(B.vtab_key, 0xFF, TV * 16, st);
-  cudaMemsetAsync(B.ctab_key, 0xFF, TC * 8, st);
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return MF_ERR_CUDA;

@@ -5,7 +5,7 @@
 // Device state of one trace (all resident in the context):
 //   edge table   key(y, p1) -> index in the edge list     (dedup, Sec. IV-A)
 //   vertex table key(y)     -> f(y)                        (each vertex evaluated once)
-//   cell table   key(z, pi)                               (dedup of n-cofaces, Sec. IV-C)
+//   cell list    (z, pi), each n-coface written once by its canonical pair (Sec. IV-C)
 //   edge list    insertion order; BFS level L is the contiguous range appended
 //                while level L-1 was expanded, so the list is also the queue.
 //
@@ -948,7 +948,7 @@ static int build_frame(mf_ctx *ctx, int d, double lam, const mf_domain *dom, MfF
   }
   if (!mf_frame_pack_keys(F))
     return mf_set_error(ctx, MF_ERR_DOMAIN,
-                        "edge/cell keys need more than 64 bits (domain too large for lambda)");
+                        "edge keys need more than 64 bits (domain too large for lambda)");
   return MF_OK;
 }
 
