@@ -125,3 +125,25 @@ def test_weak_scaling_reduction_two_gloo_ranks(tmp_path):
         ms, units, e2e, e2e_units = (float(v) for v in row[:4])
         assert (ms, units, e2e, e2e_units) == (101.0, 3000.0, 4.0, 21.0)
     assert rows[0][4] != rows[1][4]  # different seeds per rank
+
+
+@pytest.mark.parametrize("d,lam", [(2, 0.3), (3, 0.1), (5, 0.05), (6, 0.04), (8, 0.2)])
+def test_longest_edge_bound_for_vertex_lists(d, lam):
+    """The per-vertex lists of the root screen assume every edge (y, y + e(M))
+    is at most lam * max_k sqrt(k (1 - 2ck + c^2 k d)) long (|M| = k): check
+    it against the oracle's lattice map for every mask, and that it is
+    attained."""
+    rng = np.random.default_rng(d)
+    c = oracle.lattice_c(d)
+    bound = lam * max(math.sqrt(k * (1 - 2 * c * k + c * c * k * d)) for k in range(1, d + 1))
+    off = W.lattice_offset(d, lam)
+    longest = 0.0
+    for _ in range(20):
+        y = rng.integers(-50, 50, size=d)
+        x0 = oracle.vertex_x(d, lam, off, y[None, :])[0]
+        for m in range(1, 1 << d):
+            e = np.array([(m >> k) & 1 for k in range(d)])
+            x1 = oracle.vertex_x(d, lam, off, (y + e)[None, :])[0]
+            longest = max(longest, float(np.linalg.norm(x1 - x0)))
+    assert longest <= bound * (1 + 1e-12)
+    assert longest >= bound * (1 - 1e-9)
