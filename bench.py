@@ -155,9 +155,13 @@ def roofline(stats, w, clocks, n_sms=152):
                 "peak_source": "FP64 pipe at the sampled clock",
                 "phase_ms": {k: round(v["ms"], 3) for k, v in stats.items() if v["ms"] > 0}}
     # table phases: algorithmic bytes = one 32-byte sector per hash probe / record touched
+    # (cells: one sector per link-vertex lookup, 2^k + 2^(d-k+1) with k ~ d/2;
+    # csr fill: one sector per traced pair, ~(d+1) per cell, and its index)
+    k = d // 2
     per_unit = {"expand_vertices": (4 * d + 4) + 32 * (2 ** d),
                 "expand_edges": (4 * d + 20) + 64 * (2 ** d),
-                "cells": (4 * d + 4) + 64 * 60, "csr": (5 * d) + 32 * (d + 1) * d + 16}.get(dom, 64)
+                "cells": (4 * d + 4) + 32 * (2 ** k + 2 ** (d - k + 1)),
+                "csr": (5 * d) + (32 + 8) * (d + 1)}.get(dom, 64)
     by = s["units"] * per_unit / max(s["launches"], 1)
     ach = by / (ms_per_launch * 1e-3) / 1e9
     return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
