@@ -87,7 +87,8 @@ def test_result_independent_of_batch_cap(ctx, cap):
 
 
 @pytest.mark.parametrize("d,lam,n_sv,seed", [(2, 0.05, 12, 2), (3, 0.15, 20, 2), (4, 0.3, 16, 3),
-                                             (5, 0.5, 16, 4), (6, 0.7, 12, 5)])
+                                             (5, 0.5, 16, 4), (6, 0.7, 12, 5), (7, 0.9, 10, 6),
+                                             (8, 1.1, 8, 7)])
 @pytest.mark.parametrize("precision", [mf.MF_FP64, mf.MF_MIXED_FP32, mf.MF_MIXED_BF16])
 def test_random_problems_parity(ctx, d, lam, n_sv, seed, precision):
     w = W.random_small(d, n_sv, seed, lam, gamma=1.5, n_seeds=4, box=1.3)
