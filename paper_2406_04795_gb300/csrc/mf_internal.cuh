@@ -475,7 +475,7 @@ void mf_launch_seeds(const MfFrame &F, const MfTraceBufs &B, const double *seeds
 struct MfTune {
   int roots_variant = 0;         // 0: no register cap (2 blocks/SM), 1: 3 blocks/SM
   int roots_bps = 4;             // root-solve blocks per SM in the grid
-  int roots_group = 8;           // consecutive edges sharing one group screen (1 = none)
+  int roots_group = 1;           // consecutive edges sharing one group screen (1 = none)
   int eval_bps = 8;              // FP64 vertex-evaluation blocks per SM
   int tc_chunk = 64;             // support vectors per tensor-core MMA: 64 or 128
   uint64_t frontier_chunk = 0;   // BFS chunk in edges; 0 = the caller's batch cap
