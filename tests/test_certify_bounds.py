@@ -87,3 +87,28 @@ def test_fp64_certificate_accepts_only_exact_minima():
             accepted += 1
             assert abs(D - exact) <= 2e-12 + 1e-14 * (1 + exact)
     assert accepted > 2500  # the breakpoint fallback is rare
+
+
+def test_table_driven_sincos_method():
+    """The FP64 chain's sin/cos: x = k pi/64 + r with a two-part pi/64 (the
+    first part has 25 significant bits), a 128-entry table of sin/cos(j pi/64)
+    and Taylor polynomials on |r| <= pi/128 (Tang, 1991).  Restated here in
+    float64; within a few ulps of libm for |x| <= 20."""
+    p1 = float.fromhex("0x1.921fb5p-5")
+    p2 = 4.966642116727561e-10
+    assert abs((p1 + p2) - math.pi / 64) < 1e-17
+    assert (p1 * 2 ** 29).is_integer()  # k * p1 exact for |k| < 2^28
+    tab = [(math.sin(j * math.pi / 64), math.cos(j * math.pi / 64)) for j in range(128)]
+    rng = np.random.default_rng(13)
+    worst = 0.0
+    for x in rng.uniform(-20, 20, 50000):
+        kd = float(np.rint(x * 20.371832715762604))
+        r = (x - kd * p1) - kd * p2
+        s0, c0 = tab[int(kd) & 127]
+        r2 = r * r
+        sr = r * r2 * (r2 * (r2 * (-1 / 5040) + 1 / 120) - 1 / 6) + r
+        cm = r2 * (r2 * (r2 * (r2 * (1 / 40320) - 1 / 720) + 1 / 24) - 0.5)
+        s = s0 * cm + (c0 * sr + s0)
+        c = c0 * cm + (-s0 * sr + c0)
+        worst = max(worst, abs(s - math.sin(x)), abs(c - math.cos(x)))
+    assert worst < 1e-15
