@@ -74,9 +74,8 @@ def barycentric(P, x):
 def brute_trace(d, lam, c, o, lo, hi, fvals_fn, seeds):
     """Traced set by exhaustive enumeration of a box of the lattice.
 
-    Returns (edges: set of (y, mask)), levels: dict edge -> BFS distance from
-    the seed edges, n_vertices (vertices touched by traced edges and their
-    in-box cofaces)."""
+    Returns (edges: set of (y, mask), levels: dict edge -> BFS distance from
+    the seed edges).  brute_counts derives the evaluation counters from it."""
     cinv = c * math.sqrt(d + 1)
     s_lo = float(np.sum(np.asarray(lo) - o))
     s_hi = float(np.sum(np.asarray(hi) - o))
@@ -178,3 +177,58 @@ def brute_trace(d, lam, c, o, lo, hi, fvals_fn, seeds):
                 level[n] = level[k] + 1
                 q.append(n)
     return traced, level
+
+
+def brute_counts(d, lam, c, o, lo, hi, fvals_fn, seeds, traced):
+    """The tracing counters derived from the traced set by Kuhn-simplex
+    enumeration, independently of the oracle's permutahedral queries.
+
+    f is evaluated at (i) the in-box vertices of each seed's n-simplex that
+    belong to an in-box edge of it (at least two in-box vertices), and (ii)
+    the vertices of every 2-simplex containing a traced edge whose three
+    vertices are all in the box.  A (traced edge, 2-simplex) pair whose third
+    vertex leaves the box is a boundary pair.  Returns (n_vertices,
+    n_boundary, n_near_zero)."""
+    cinv = c * math.sqrt(d + 1)
+    lo, hi, o = np.asarray(lo), np.asarray(hi), np.asarray(o)
+
+    def inbox(v):
+        x = lattice_x(d, lam, c, o, np.asarray([v]))[0]
+        return bool(np.all(x >= lo) and np.all(x <= hi))
+
+    evaluated = set()
+    for x in np.atleast_2d(seeds):
+        yp = (np.asarray(x) - o + cinv * np.sum(np.asarray(x) - o)) / lam
+        base = np.floor(yp).astype(np.int64)
+        found = None
+        for off in itertools.product((-1, 0, 1), repeat=d):
+            z = base + np.asarray(off)
+            for pi in itertools.permutations(range(d)):
+                vs = np.array(kuhn_vertices(z, pi))
+                bc = barycentric(lattice_x(d, lam, c, o, vs), np.asarray(x))
+                if np.all(bc >= -1e-12):
+                    found = vs
+                    break
+            if found is not None:
+                break
+        assert found is not None
+        ins = [tuple(int(t) for t in v) for v in found if inbox(v)]
+        if len(ins) >= 2:
+            evaluated.update(ins)
+    boundary = 0
+    for (y, mask) in traced:
+        a = tuple(y)
+        b = tuple(y[i] + ((mask >> i) & 1) for i in range(d))
+        for tri in triangles_containing_edge(a, b):
+            (w,) = tuple(tri - {a, b})
+            if inbox(w):
+                evaluated.update((a, b, w))
+            else:
+                boundary += 1
+    if evaluated:
+        V = np.array(sorted(evaluated), dtype=np.int64)
+        fv = fvals_fn(lattice_x(d, lam, c, o, V))
+        near = int(np.sum(np.abs(fv) < 1e-12))
+    else:
+        near = 0
+    return len(evaluated), boundary, near

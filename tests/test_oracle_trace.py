@@ -37,6 +37,11 @@ def test_traced_set_equals_brute_force_components(d, lam, n_sv, seed):
            for y, m, L in zip(r["edge_y"], r["edge_mask"], r["edge_level"])}
     assert lev == level
     assert r["levels"] == (max(level.values()) + 1 if level else 0)
+    # the counters the GPU is compared with bit-exactly, from the same
+    # enumeration: vertices evaluated, boundary pairs, near-zero vertices
+    nv, nb, nz = B.brute_counts(d, w.lam, c, w.offset, w.lo, w.hi, fv, w.seeds, traced)
+    assert (r["n_vertices"], r["n_boundary"], r["n_near_zero"]) == (nv, nb, nz)
+    assert nb > 0 or d == 2
 
 
 def test_lattice_x_matches_numpy_operation_order():
