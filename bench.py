@@ -36,6 +36,10 @@ from paper_2406_04795_gb300 import workloads as W  # noqa: E402
 # r^2 (1 mul), degree-5 polynomial (4 FMA), table product (1 FMA), 2^m (1 mul);
 # an FMA counts 2 flops
 FP64_EXP_FLOPS = 19
+# DRAM bytes per traced edge of k_roots_f64 from its ncu capture (per-edge
+# dram__bytes_read.sum + dram__bytes_write.sum on the lambda = 0.15 case of
+# the d=5 workload); None once the kernel has changed since the capture
+ROOTS_DRAM_BYTES_PER_EDGE = None
 
 
 def make_workload(cfg: str, rank: int, lam=None):
@@ -105,77 +109,93 @@ def measured_peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
-def roofline(stats, w, clocks, n_sms=152):
-    """Roofline of the dominant phase: FP64 pipe for the RBF phases
-    (2 FP64 FMA per SM per clock on GB300), HBM for the table phases."""
+def roofline(stats, w, rates, E, ms_proof, n_proofs):
+    """Roofline of the dominant phase against the measured peaks: the FP64
+    pipe (mf_probe_rates FP64 FMA probe) for the RBF phases, the MUFU ex2
+    probe for the tensor-core evaluation, the STREAM copy for the table
+    phases.  Work is counted in kept terms: the screened sum evaluates in FP64
+    only the terms that can exceed 3e-10 (1e-8 in the root step), so the dense
+    N x (vertices + root evaluations) count of an unscreened sum does not
+    apply.  Also the whole proof's per-edge time against its bound
+    max(FP64 flops / FP64 peak, ex2 / ex2 rate, bytes / HBM)."""
     peaks, src = measured_peaks()
     dom = max(stats, key=lambda k: stats[k]["ms"])
     s = stats[dom]
     ms_per_launch = s["ms"] / max(s["launches"], 1)
     d = w.d
-    mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp64_peak = n_sms * 4.0 * mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
+    fp64_peak = 2.0 * rates["fp64_fma_per_s"] / 1e12  # TFLOP/s, measured
+    ex2_peak = rates["ex2_per_s"] / 1e12             # T ex2/s, measured
+    phase_ms = {k: round(v["ms"], 3) for k, v in stats.items() if v["ms"] > 0}
+    per_root = 5 * d + 5 + FP64_EXP_FLOPS
+    per_eval = 3 * d + 3 + FP64_EXP_FLOPS
+    # proof level (per traced edge): FP64 flops of all kept FP64 terms,
+    # ex2 of all FP32 terms (weak terms; every term of a tensor-core tile),
+    # and the algorithmic bytes of the table phases
+    f64 = stats["roots"]["terms"] * per_root + stats["eval"]["terms"] * per_eval
+    ex2 = stats["roots"]["terms_weak"] + stats["eval"]["terms_weak"]
+    k = d // 2
+    by = (stats["expand_vertices"]["units"] * ((4 * d + 4) + 32 * 2 ** d) +
+          stats["expand_edges"]["units"] * ((4 * d + 20) + 64 * 2 ** d) +
+          stats["roots"]["units"] * (40 + 8 * d + 8 + 8 * d) +
+          stats["cells"]["units"] * ((4 * d + 4) + 32 * (2 ** k + 2 ** (d - k + 1))) +
+          stats["csr"]["units"] * ((5 * d) + (32 + 8) * (d + 1)))
+    steps = max(n_proofs, 1)
+    t_f64 = f64 / steps / (fp64_peak * 1e12)
+    t_ex2 = ex2 / steps / (ex2_peak * 1e12)
+    t_hbm = by / steps / (peaks["hbm_gbs"] * 1e9)
+    t_bound = max(t_f64, t_ex2, t_hbm)
+    proof = {"ns_per_edge": ms_proof * 1e6 / max(E, 1), "bound_ns_per_edge": t_bound * 1e9 / max(E, 1),
+             "frac": t_bound / (ms_proof * 1e-3), "bound_by": ["fp64", "ex2", "hbm"][
+                 [t_f64, t_ex2, t_hbm].index(t_bound)],
+             "fp64_ms": t_f64 * 1e3, "ex2_ms": t_ex2 * 1e3, "hbm_ms": t_hbm * 1e3}
+    base = {"phase_ms": phase_ms, "proof": proof,
+            "measured_rates": {k: v for k, v in rates.items()}}
     if dom == "eval" and w.precision not in ("fp64", "mixed_fp32"):
         # tensor-core evaluation: the distance GEMM runs on tcgen05, every term
-        # then takes one MUFU ex2 (16 per SM per clock), which binds
-        ex2 = s["terms_weak"] / max(s["launches"], 1)
-        ach = ex2 / (ms_per_launch * 1e-3) / 1e12
-        mufu_peak = n_sms * 16.0 * mhz * 1e6 / 1e12
-        return {"kernel": "k_eval_tc", "bound": "alu", "achieved": ach, "peak": mufu_peak,
-                "unit": "TFLOP/s", "frac": ach / mufu_peak, "traffic": None,
-                "peak_source": "MUFU ex2: %d SMs x 16/clk x %.0f MHz (sampled); one ex2 per "
-                               "RBF term counted as one op" % (n_sms, mhz),
-                "work": "%d RBF terms (vertex x support vector)" % s["terms_weak"],
-                "phase_ms": {k: round(v["ms"], 3) for k, v in stats.items() if v["ms"] > 0}}
+        # then takes one MUFU ex2, which binds
+        ex = s["terms_weak"] / max(s["launches"], 1)
+        ach = ex / (ms_per_launch * 1e-3) / 1e12
+        return dict(base, kernel="k_eval_tc", bound="alu", achieved=ach, peak=ex2_peak,
+                    unit="T ex2/s", frac=ach / ex2_peak, traffic=None,
+                    peak_source="measured: mf_probe_rates ex2.approx probe",
+                    work="%d RBF terms (vertex x support vector), one ex2 each" % s["terms_weak"])
     if dom in ("roots", "eval"):
-        # a strong term: differences, squares (and, for roots, projections on
-        # the edge direction), -gamma r^2, exp, alpha e and the sums; weak terms
-        # run in FP32 and are not FP64 work
-        per_strong = (5 * d + 5 if dom == "roots" else 3 * d + 3) + FP64_EXP_FLOPS
-        flops = s["terms"] * per_strong / max(s["launches"], 1)
+        per = per_root if dom == "roots" else per_eval
+        flops = s["terms"] * per / max(s["launches"], 1)
         ach = flops / (ms_per_launch * 1e-3) / 1e12
-        # DRAM bytes per launch from the ncu capture of k_roots_f64 on the
-        # lambda = 0.15 case (340 B per edge: the edge records and the base
-        # vertices' support-vector lists), scaled by the edges one launch
-        # processes
-        traffic = 339.7 * s["units"] / max(s["launches"], 1) if dom == "roots" else None
-        return {"kernel": "k_roots_f64" if dom == "roots" else "k_eval_vertices_f64",
-                "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": ach / fp64_peak, "traffic": traffic,
-                "peak_source": "FP64 pipe: %d SMs x 2 DFMA/clk x %.0f MHz (sampled)" % (n_sms, mhz),
-                "work": "%d FP64 terms x %d flops (and %d FP32 weak terms, not counted)" % (
-                    s["terms"], per_strong, s["terms_weak"]),
-                "phase_ms": {k: round(v["ms"], 3) for k, v in stats.items() if v["ms"] > 0}}
+        # DRAM bytes per edge from the ncu capture of k_roots_f64 (profiles/),
+        # scaled by the edges one launch processes
+        traffic = ROOTS_DRAM_BYTES_PER_EDGE * s["units"] / max(s["launches"], 1) \
+            if dom == "roots" and ROOTS_DRAM_BYTES_PER_EDGE else None
+        return dict(base, kernel="k_roots_f64" if dom == "roots" else "k_eval_vertices_f64",
+                    bound="alu", achieved=ach, peak=fp64_peak, unit="TFLOP/s", frac=ach / fp64_peak,
+                    traffic=traffic,
+                    peak_source="measured: mf_probe_rates FP64 FMA probe (2 flops per FMA)",
+                    work="%d kept FP64 terms x %d flops (and %d FP32 weak terms, not counted)" % (
+                        s["terms"], per, s["terms_weak"]))
     if dom == "certify_points":
         n_obs = int(w.obs_type.shape[0])
         flops = s["units"] * d * (60 + n_obs * 150) / max(s["launches"], 1)
         ach = flops / (ms_per_launch * 1e-3) / 1e12
-        return {"kernel": "k_certify_points", "bound": "alu", "achieved": ach, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
-                "peak_source": "FP64 pipe at the sampled clock",
-                "phase_ms": {k: round(v["ms"], 3) for k, v in stats.items() if v["ms"] > 0}}
+        return dict(base, kernel="k_certify_points", bound="alu", achieved=ach, peak=fp64_peak,
+                    unit="TFLOP/s", frac=ach / fp64_peak, traffic=None,
+                    peak_source="measured: mf_probe_rates FP64 FMA probe")
     # table phases: algorithmic bytes = one 32-byte sector per hash probe / record touched
-    # (cells: one sector per link-vertex lookup, 2^k + 2^(d-k+1) with k ~ d/2;
-    # csr fill: one sector per traced pair, ~(d+1) per cell, and its index)
-    k = d // 2
     per_unit = {"expand_vertices": (4 * d + 4) + 32 * (2 ** d),
                 "expand_edges": (4 * d + 20) + 64 * (2 ** d),
                 "cells": (4 * d + 4) + 32 * (2 ** k + 2 ** (d - k + 1)),
                 "csr": (5 * d) + (32 + 8) * (d + 1)}.get(dom, 64)
-    by = s["units"] * per_unit / max(s["launches"], 1)
-    ach = by / (ms_per_launch * 1e-3) / 1e9
-    return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
-            "phase_ms": {k: round(v["ms"], 3) for k, v in stats.items() if v["ms"] > 0}}
+    byl = s["units"] * per_unit / max(s["launches"], 1)
+    ach = byl / (ms_per_launch * 1e-3) / 1e9
+    return dict(base, kernel=dom, bound="hbm", achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",
+                frac=ach / peaks["hbm_gbs"], traffic=None, peak_source=src)
 
 
-def cpu_baseline(w, budget_s=15.0):
-    """The FP64 oracle on a bounded sample of the same workload: trace (with
-    roots and cells) until max_edges edges exist, then certify those points."""
+def _oracle_rate(w, threads, budget_s):
     import oracle
     oracle.build()
+    used = oracle.set_threads(threads)
     n = 200
-    rate, sample = None, None
     while True:
         t0 = time.perf_counter()
         r = oracle.trace(w.sv, w.alpha, w.gamma, w.b, w.lam, w.offset, w.lo, w.hi, w.seeds,
@@ -184,11 +204,30 @@ def cpu_baseline(w, budget_s=15.0):
                        r["cell_off"], r["cell_idx"])
         dt = time.perf_counter() - t0
         E = len(r["edge_t"])
-        rate, sample = E / dt, "first %d edges of the BFS (+ roots, cells, certify) in %.1f s" % (E, dt)
         if dt > budget_s / 4 or E < n:
-            break
+            return E / dt, E, dt, used
         n *= 4
-    return {"value": rate, "unit": "simplices/s", "cores": 1, "kind": "oracle", "sample": sample}
+
+
+def cpu_baseline(w, E_proof=None, budget_s=15.0):
+    """The FP64 oracle on a bounded sample of the same workload: trace (with
+    roots and cells) until max_edges edges exist, then certify those points;
+    on all host cores (its per-edge root and certification loops are OpenMP)
+    and on one.  The per-edge cost is dominated by the bisection roots
+    (50 + 17 f evaluations per edge), which cost the same on every edge, so
+    the BFS prefix is a fair sample of the proof's per-edge cost."""
+    import oracle
+    rate, E, dt, cores = _oracle_rate(w, 0, budget_s)
+    rate1, E1, dt1, _ = _oracle_rate(w, 1, budget_s / 2)
+    oracle.set_threads(0)
+    out = {"value": rate, "unit": "simplices/s", "cores": cores, "kind": "oracle",
+           "sample": "first %d edges of the BFS (+ roots, cells, certify) in %.1f s on %d threads;"
+                     " %d edges in %.1f s on 1 thread" % (E, dt, cores, E1, dt1),
+           "value_1core": rate1, "host_cores": os.cpu_count()}
+    if E_proof:
+        out["ms_per_proof_est"] = 1e3 * E_proof / rate
+        out["ms_per_proof_est_1core"] = 1e3 * E_proof / rate1
+    return out
 
 
 def run_served(ctx, arrivals, reqs, precision, max_slots=64, hbm_bytes=200 << 30):
@@ -240,21 +279,120 @@ def run_served(ctx, arrivals, reqs, precision, max_slots=64, hbm_bytes=200 << 30
 
 
 def served_lines(ctx, n_requests, rate_hz, seed=1005):
-    """The served workload at its arrival rate (mixed precision), and the same
-    requests all at once on the mixed and on the FP64 path (capacity)."""
+    """The served workload at its arrival rate on the mixed path (distance
+    GEMM on the tensor cores, FP64 recheck), and the same requests all at once
+    on the mixed and on the FP64 path (capacity)."""
     from paper_2406_04795_gb300 import mf
     arrivals, reqs = W.served_requests(seed=seed, n_requests=n_requests, rate_hz=rate_hz)
-    out = run_served(ctx, arrivals, reqs, mf.MF_MIXED_FP32)
-    out.update({"rate_hz": rate_hz, "precision": "mixed",
+    out = run_served(ctx, arrivals, reqs, mf.MF_MIXED_BF16)
+    out.update({"rate_hz": rate_hz, "precision": "mixed_bf16",
                 "workload": "Poisson arrivals; d in {4,5,6}, 512-8192 SVs, lambda in [0.03,0.08], "
                             "1-16 seeds"})
     burst = np.zeros(len(reqs))
     cap = {}
-    for name, prec in (("mixed", mf.MF_MIXED_FP32), ("fp64", mf.MF_FP64)):
+    for name, prec in (("mixed_bf16", mf.MF_MIXED_BF16), ("fp64", mf.MF_FP64)):
         r = run_served(ctx, burst, reqs, prec)
         cap[name] = {"simplices_per_s": r["simplices_per_s"], "wall_s": r["wall_s"],
                      "p50_ms": r["p50_ms"], "failed": r["failed"]}
     out["saturated"] = cap
+    return out
+
+
+def _proof_ms(ctx, w, reps=2):
+    """Device-timed ms per proof of workload w (after one untimed proof)."""
+    import torch
+    from paper_2406_04795_gb300.pipeline import Proof
+    p = Proof(ctx, w)
+    p.step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        r, v, m, cv = p.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, p, r
+
+
+def config_lines(ctx, d6_lam=0.15):
+    """The other BASELINE configurations, each one line (untimed by the main
+    metric): d=3 FP64; d=6 mixed BF16 at the finest lambda traced here, with
+    sampled root and point errors against the FP64 oracle."""
+    import oracle
+    out = {}
+    w3 = W.config_d3()
+    ms, p, r = _proof_ms(ctx, w3, reps=5)
+    out["d3_fp64"] = {"workload": w3.name, "lambda": w3.lam, "n_sv": int(w3.sv.shape[0]),
+                      "ms_per_proof": ms, "simplices_per_s": r["n_edges"] / (ms * 1e-3),
+                      "edges_per_proof": r["n_edges"], "cells_per_proof": r["n_cells"]}
+    del p, r
+    w6 = W.config_d6(lam=d6_lam)
+    ms, p, r = _proof_ms(ctx, w6)
+    E = r["n_edges"]
+    rng = np.random.default_rng(6)
+    idx = np.sort(rng.choice(E, min(E, 400), replace=False))
+    y = r["edge_y"][idx].cpu().numpy()
+    m = r["edge_mask"][idx].cpu().numpy().astype(np.uint32)
+    oracle.set_threads(0)
+    f2, t, pt, multi = oracle.edge_roots(w6.sv, w6.alpha, w6.gamma, w6.b, w6.lam, w6.offset, y, m)
+    ok = (multi == 0) & np.all(np.abs(f2) >= 1e-12, axis=1)
+    dt = np.abs(r["edge_t"][idx].cpu().numpy() - t)[ok]
+    df = np.abs(r["edge_f"][idx].cpu().numpy() - f2)
+    dp = np.abs(r["points"][idx].cpu().numpy() - pt)[ok]
+    out["d6_mixed_bf16"] = {
+        "workload": w6.name, "lambda": w6.lam, "lambda_config": 0.04, "n_sv": int(w6.sv.shape[0]),
+        "ms_per_proof": ms, "simplices_per_s": E / (ms * 1e-3), "edges_per_proof": E,
+        "cells_per_proof": r["n_cells"], "vertices_per_proof": r["n_vertices"],
+        "rechecked_vertices": r["n_recheck"],
+        "error_vs_oracle": {"sampled_edges": int(ok.sum()), "max_dt": float(dt.max()),
+                            "max_dpoint": float(dp.max()), "max_df_edge_ends": float(df.max()),
+                            "sign_mismatches": int(np.sum((f2 >= 0) != (r["edge_f"][idx].cpu().numpy() >= 0)))},
+        "note": "lambda 0.04 gives ~8e9 edges (lambda^-5 law), beyond one GPU's memory"}
+    del p, r
+    return out
+
+
+def batched_line(ctx, n_traces=64, seed=1003):
+    """64 independent traces (d in {4,5,6}, 256-8192 SVs, lambda in
+    [0.03, 0.1]) in one mf_trace_batch call, on the mixed (tensor-core) and
+    FP64 paths, against the same traces one mf_trace call at a time.
+    Capacities come from one untimed mf_trace of each trace (x1.25)."""
+    import torch
+    from paper_2406_04795_gb300 import mf
+    ws = W.config_batched(seed=seed, n_traces=n_traces)
+    caps, E_tot = [], 0
+    for w in ws:
+        r = ctx.trace(w.sv, w.alpha, w.gamma, w.b, w.lam, w.offset, w.lo, w.hi, w.seeds,
+                      precision=mf.MF_FP64, **W.shell_capacity(w))
+        caps.append(dict(max_edges=int(r["n_edges"] * 1.25) + 4096,
+                         max_vertices=int(r["n_vertices"] * 1.25) + 4096,
+                         max_cells=int(r["n_cells"] * 1.25) + 4096))
+        E_tot += r["n_edges"]
+        del r
+    torch.cuda.empty_cache()
+    out = {"traces": n_traces, "edges": E_tot,
+           "workload": "d in {4,5,6}, 256-8192 SVs log-uniform, lambda in [0.03, 0.1], 1-64 seeds"}
+    for name, prec in (("mixed_bf16", mf.MF_MIXED_BF16), ("fp64", mf.MF_FP64)):
+        ctx.trace_batch(ws, precisions=[prec] * n_traces, capacities=caps)  # untimed
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        got = ctx.trace_batch(ws, precisions=[prec] * n_traces, capacities=caps)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        E = sum(g["n_edges"] for g in got)
+        del got
+        t0 = time.perf_counter()
+        for w, c in zip(ws, caps):
+            r = ctx.trace(w.sv, w.alpha, w.gamma, w.b, w.lam, w.offset, w.lo, w.hi, w.seeds,
+                          precision=prec, **c)
+            del r
+        torch.cuda.synchronize()
+        dt1 = time.perf_counter() - t0
+        out[name] = {"simplices_per_s": E / dt, "ms": dt * 1e3,
+                     "one_at_a_time_simplices_per_s": E / dt1, "one_at_a_time_ms": dt1 * 1e3}
+    out["tune"] = mf.mf_ctx_get_tune(ctx.h).as_dict()
+    torch.cuda.empty_cache()
     return out
 
 
@@ -326,6 +464,9 @@ def run_gb300(args):
         if world > 1:
             dist.barrier()
 
+    # measured roofline denominators (FP64 FMA, FP32 FMA, ex2, table exp)
+    rates = mf.mf_probe_rates(ctx.h).as_dict()
+
     for _ in range(max(args.warmup, 0)):
         proof.step()
     torch.cuda.synchronize()
@@ -391,27 +532,22 @@ def run_gb300(args):
                        "l2": "inputs larger than L2 (resident hash tables and lists are GBs)"},
             "e2e": {"value": e2e_edges_all / args.steps / (e2e_max / args.steps),
                     "unit": "simplices/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": E},
+                    "d2h_bytes_per_step": E,
+                    "note": "inputs (support vectors, seeds, robot, scene) copied in and the "
+                            "per-point verdicts read back every step; the traced set stays "
+                            "resident on the device, as the paper returns only C_free points"},
             "gpu_launches": launches,
             "clocks": clocks,
-            "roofline": roofline(stats, w, clocks),
+            "roofline": roofline(stats, w, rates, E, ms_max, args.steps),
         }
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(w)
+            line["cpu_baseline"] = cpu_baseline(w, E_proof=E)
         if world == 1 and not args.no_extras:
-            # the same proof on the mixed-precision path
+            # the same proof on the other precision (mixed: distance GEMM on
+            # the tensor cores, FP64 recheck, roots to 1e-6)
             wm = make_workload(args.config, rank, args.lam)
             wm.precision = "mixed" if w.precision == "fp64" else "fp64"
-            pm = Proof(ctx, wm)
-            pm.step()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(2):
-                rm, _, _, _ = pm.step()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            msm = e0.elapsed_time(e1) / 2
+            msm, pm, rm = _proof_ms(ctx, wm)
             line["other_precision"] = {"precision": wm.precision, "ms_per_proof": msm,
                                        "value": rm["n_edges"] / (msm * 1e-3),
                                        "edges_per_proof": rm["n_edges"],
@@ -421,6 +557,14 @@ def run_gb300(args):
             # and outputs are released first, so that its arena can hold many
             # requests
             del proof, r, v, m, cv
+            ctx.close()
+            torch.cuda.empty_cache()
+            ctx = Context(local, 0)
+            line["configs"] = config_lines(ctx)
+            ctx.close()
+            torch.cuda.empty_cache()
+            ctx = Context(local, 0)
+            line["batched"] = batched_line(ctx)
             ctx.close()
             torch.cuda.empty_cache()
             ctx = Context(local, 0)

@@ -55,6 +55,12 @@ extern "C" {
 /* mf_trace_opts.flags */
 #define MF_WANT_ROOTS 1u /* solve t and the intersection point of every traced edge */
 #define MF_WANT_CELLS 2u /* crossing n-simplices and the cell -> edge CSR */
+/* Root accuracy.  The FP64 path solves every root to |t - t*| <= 1e-9.  The
+ * mixed paths solve to |t - t*| <= 1e-6 (their stated tolerance): FP32
+ * iterations, then one FP64 Newton step that takes in FP64 the terms that can
+ * exceed 1e-5 and sums the rest in FP32 under a bound that moves t by at most
+ * 1e-7.  This flag gives a mixed path the FP64 path's 1e-9 root solve. */
+#define MF_ROOTS_FP64_EXACT 4u
 
 typedef struct mf_ctx mf_ctx;
 
@@ -272,7 +278,12 @@ int mf_certify(mf_ctx *ctx, const mf_robot *robot, const mf_scene *scene, const 
  * exit.  It calls no cudaMalloc/cudaFree and no allocating library routine.
  *  - Runs on the current device.  Its first call on a device looks up the
  *    array's address (cudaGetSymbolAddress); make that call before any stream
- *    capture.
+ *    capture.  Under CUDA's lazy module loading the array is reserved on a
+ *    device when the library's device code is loaded there: by that first
+ *    call, or earlier by any launch of the library's kernels on the device.
+ *    Make the first call at start-up, before device memory is reserved
+ *    elsewhere; if the module cannot be loaded then, the call returns
+ *    MF_ERR_CUDA (not MF_ERR_OOM).
  *  - Capacities: opts->max_edges / max_vertices / max_cells, or (when 0) the
  *    largest default that fits.  Requests whose tables and lists exceed the
  *    array return MF_ERR_OOM; output buffers that are too small return
@@ -342,6 +353,28 @@ int mf_autotune(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom, const mf_t
  * (the ms_* and n_candidates fields are ignored / zero). */
 int mf_ctx_set_tune(mf_ctx *ctx, const mf_tune *t);
 int mf_ctx_get_tune(mf_ctx *ctx, mf_tune *out);
+
+/* Measured throughput of the pipes that bound the traced path on this GPU
+ * (no counterpart in the paper; the denominators of the roofline the
+ * benchmark reports).  Each probe kernel runs independent chains on every SM
+ * (8 blocks of 256 threads per SM) and the best of three timed launches is
+ * kept.  Rates are thread-level operations per second. */
+typedef struct {
+  double fp64_fma_per_s;  /* FP64 fused multiply-adds */
+  double fp32_fma_per_s;  /* FP32 fused multiply-adds */
+  double ex2_per_s;       /* FP32 ex2.approx (MUFU) */
+  double exp_neg_per_s;   /* the FP64 table-driven exp of the RBF terms */
+  int32_t sm_count;
+  double sm_clock_mhz;    /* the device's nominal SM clock */
+} mf_rates;
+int mf_probe_rates(mf_ctx *ctx, mf_rates *out, void *stream);
+
+/* Accuracy diagnostic of the FP64 exp the RBF kernels use (Tang's
+ * table-driven method, ACM TOMS 15(2), 1989): y_table[i] = that exp of x[i],
+ * y_lib[i] = CUDA's exp(x[i]), for comparison on the host.  x, y_*: device
+ * [n]; meant for x in [-708, 0] (the kernels' arguments are -gamma r^2). */
+int mf_diag_exp(mf_ctx *ctx, const double *x, int64_t n, double *y_table, double *y_lib,
+                void *stream);
 
 #ifdef __cplusplus
 }

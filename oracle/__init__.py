@@ -27,9 +27,15 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+                               "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's per-edge and per-point loops (n <= 0:
+    all cores); returns the count in use.  Results do not depend on it."""
+    return int(lib().or_set_threads(int(n)))
 
 
 class Simplex(C.Structure):
@@ -104,6 +110,8 @@ def lib():
         L.or_certify.argtypes = [P(Robot), P(Scene), P(C.c_double), C.c_int64, C.c_int32,
                                  P(C.c_int64), P(C.c_int64), C.c_int64,
                                  P(C.c_uint8), P(C.c_double), P(C.c_uint8)]
+        L.or_set_threads.restype = C.c_int
+        L.or_set_threads.argtypes = [C.c_int]
         _lib = L
     return _lib
 

@@ -333,6 +333,7 @@ double or_f(const or_rbf *r, const double *q) {
 }
 
 void or_f_batch(const or_rbf *r, const double *q, int64_t n, double *out) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; i++) out[i] = or_f(r, q + i * r->d);
 }
 
@@ -449,6 +450,7 @@ void or_edge_roots(const or_rbf *rbf, double lam, const double *o, const int32_t
                    const uint32_t *emask, int64_t n, double *f2, double *t, double *pt,
                    uint8_t *mr) {
   int d = rbf->d;
+#pragma omp parallel for schedule(dynamic, 16)
   for (int64_t i = 0; i < n; i++) {
     or_simplex e;
     or_simplex_zero(&e);
@@ -583,7 +585,13 @@ int or_trace(const or_rbf *rbf, double lam, const double *o, const double *lo, c
     res->edge_f[2 * i + 1] = ef[2 * i + 1];
     res->edge_t[i] = 0.0;
     res->edge_multiroot[i] = 0;
-    if (want_roots) {
+  }
+  /* The roots are independent per edge: the loop runs on all host threads
+   * (OpenMP), each edge with the same arithmetic as a serial loop. */
+  if (want_roots) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < E; i++) {
+      const or_simplex *e = &((or_simplex *)eset.recs)[i];
       int32_t v[2 * OR_MAXD];
       double x1[OR_MAXD], x2[OR_MAXD];
       or_simplex_vertices(d, e, v);
@@ -825,8 +833,9 @@ double or_segment_obstacle_dist(const double *a, const double *b, int32_t type, 
 void or_certify(const or_robot *r, const or_scene *sc, const double *points, int64_t P, int32_t d,
                 const int64_t *cell_off, const int64_t *cell_idx, int64_t n_cells,
                 uint8_t *verdict, double *margin, uint8_t *cell_verdict) {
-  double org[3 * (OR_MAXD + 1)];
+#pragma omp parallel for schedule(dynamic, 64)
   for (int64_t p = 0; p < P; p++) {
+    double org[3 * (OR_MAXD + 1)];
     or_fk(r, points + p * d, org);
     double best = -INFINITY;
     for (int i = 0; i < r->n_links; i++)
@@ -844,4 +853,20 @@ void or_certify(const or_robot *r, const or_scene *sc, const double *points, int
     for (int64_t j = cell_off[c]; j < cell_off[c + 1]; j++) v = (uint8_t)(v & verdict[cell_idx[j]]);
     cell_verdict[c] = v;
   }
+}
+
+/* Host threads of the parallel loops (roots, f batches, certification);
+ * n <= 0 restores all cores.  Returns the count now in use. */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n <= 0) n = omp_get_num_procs();
+  omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }

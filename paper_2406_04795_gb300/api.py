@@ -83,18 +83,22 @@ class Context:
 
     def trace(self, sv, alpha, gamma, b, lam, offset, lo, hi, seeds, precision=mf.MF_FP64,
               roots=True, cells=True, batch_cap=1 << 24, max_edges=1 << 22, max_vertices=0,
-              max_cells=0, recheck_band=1e-3, root_tol=1e-12, stream=None, outputs=None):
+              max_cells=0, recheck_band=1e-3, root_tol=1e-12, stream=None, outputs=None,
+              exact_roots=False):
         """Traces the zero set; returns a dict of device tensors and counters.
 
         ``outputs`` may hold preallocated output tensors (as returned by an
-        earlier call) to avoid allocations in timed loops."""
+        earlier call) to avoid allocations in timed loops.  ``exact_roots``
+        gives a mixed precision the FP64 path's root accuracy
+        (MF_ROOTS_FP64_EXACT)."""
         r, keep = self.rbf(sv, alpha, gamma, b)
         d = r.d
         dom = self.domain(lo, hi, offset)
         seeds_t = _dev(seeds, torch.float64, self.device).reshape(-1, d)
         opts = mf.mf_trace_opts(float(lam), int(batch_cap), int(precision), float(recheck_band),
                                 float(root_tol), int(max_edges), int(max_vertices), int(max_cells),
-                                (mf.MF_WANT_ROOTS if roots else 0) | (mf.MF_WANT_CELLS if cells else 0))
+                                (mf.MF_WANT_ROOTS if roots else 0) | (mf.MF_WANT_CELLS if cells else 0)
+                                | (mf.MF_ROOTS_FP64_EXACT if exact_roots else 0))
         st = _stream_handle(stream)
         res = outputs if outputs is not None else {}
         out = self._out_struct(res, d)
@@ -132,7 +136,8 @@ class Context:
                               _stream_handle(stream)).as_dict()
 
     def trace_batch(self, workloads, precisions=None, roots=True, cells=True, capacities=None,
-                    batch_cap=1 << 24, recheck_band=1e-3, root_tol=1e-12, stream=None):
+                    batch_cap=1 << 24, recheck_band=1e-3, root_tol=1e-12, stream=None,
+                    exact_roots=False):
         """Traces many workloads in one batched call (mf_trace_batch).
 
         workloads: objects with sv, alpha, gamma, b, lam, offset, lo, hi, seeds.
@@ -148,7 +153,8 @@ class Context:
         seeds = (C.c_void_p * n)()
         nseeds = (C.c_int64 * n)()
         keep, bufs = [], []
-        flags = (mf.MF_WANT_ROOTS if roots else 0) | (mf.MF_WANT_CELLS if cells else 0)
+        flags = (mf.MF_WANT_ROOTS if roots else 0) | (mf.MF_WANT_CELLS if cells else 0) | \
+            (mf.MF_ROOTS_FP64_EXACT if exact_roots else 0)
         for t, w in enumerate(workloads):
             r, k = self.rbf(w.sv, w.alpha, w.gamma, w.b)
             keep.append(k)
@@ -275,13 +281,15 @@ class Server:
             pass
 
     def submit(self, w, precision=mf.MF_MIXED_FP32, roots=True, cells=True, max_edges=1 << 20,
-               max_vertices=0, max_cells=0, batch_cap=1 << 24, recheck_band=1e-3, root_tol=1e-12):
+               max_vertices=0, max_cells=0, batch_cap=1 << 24, recheck_band=1e-3, root_tol=1e-12,
+               exact_roots=False):
         r, keep = self.ctx.rbf(w.sv, w.alpha, w.gamma, w.b)
         dom = self.ctx.domain(w.lo, w.hi, w.offset)
         sd = _dev(w.seeds, torch.float64, self.ctx.device).reshape(-1, r.d)
         opts = mf.mf_trace_opts(float(w.lam), int(batch_cap), int(precision), float(recheck_band),
                                 float(root_tol), int(max_edges), int(max_vertices), int(max_cells),
-                                (mf.MF_WANT_ROOTS if roots else 0) | (mf.MF_WANT_CELLS if cells else 0))
+                                (mf.MF_WANT_ROOTS if roots else 0) | (mf.MF_WANT_CELLS if cells else 0)
+                                | (mf.MF_ROOTS_FP64_EXACT if exact_roots else 0))
         rid = mf.mf_server_submit(self.ctx.h, self.h, r, dom, opts, sd.data_ptr(), sd.shape[0])
         self._keep[rid] = (keep, sd, r.d, max_edges, max_cells or 2 * max_edges)
         return rid

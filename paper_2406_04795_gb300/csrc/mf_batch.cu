@@ -34,15 +34,17 @@ struct TraceLayout {
   size_t rbf, dom, cnt, etab_key, vtab_key;
   size_t edge_y, edge_mask, edge_f, edge_t, edge_pt, vert_y, vert_slot, recheck;
   size_t cell_y, cell_perm, cell_sgn, cell_off, scan;
-  uint64_t ME, MV, MC, TE, TV;
+  size_t vtab_idx, vlist_off, vlist_n, vlist;  // root-screen lists (0 bytes: none)
+  uint64_t ME, MV, MC, TE, TV, VL;
   std::vector<int2> tab;
 };
 
 // One step of every active trace (captured into the graph's loop body).
 void launch_step(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, int n, bool any_mixed,
-                 int sms, cudaGraphConditionalHandle h, int use_handle, cudaStream_t s) {
+                 int tc_chunk, int sms, cudaGraphConditionalHandle h, int use_handle,
+                 cudaStream_t s) {
   mf_b_launch_expand(slots, st, P, n, false, sms, s);
-  mf_b_launch_eval(slots, P, n, any_mixed, sms, s);
+  mf_b_launch_eval(slots, P, n, any_mixed, tc_chunk, sms, s);
   mf_b_launch_expand(slots, st, P, n, true, sms, s);
   mf_b_launch_update(slots, st, P, n, h, use_handle, s);
 }
@@ -51,7 +53,7 @@ void launch_step(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, int n, bo
 // every slot as its body (k_b_update clears the condition when no slot is
 // active or the plan's step budget is used up).  nullptr if unavailable.
 cudaGraphExec_t build_loop(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, int n,
-                           bool any_mixed, int sms) {
+                           bool any_mixed, int tc_chunk, int sms) {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cs = nullptr;
@@ -74,7 +76,7 @@ cudaGraphExec_t build_loop(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P,
     if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       break;
-    launch_step(slots, st, P, n, any_mixed, sms, h, 1, cs);
+    launch_step(slots, st, P, n, any_mixed, tc_chunk, sms, h, 1, cs);
     cudaGraph_t captured = nullptr;
     if (cudaStreamEndCapture(cs, &captured) != cudaSuccess) break;
     if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
@@ -88,8 +90,8 @@ cudaGraphExec_t build_loop(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P,
 // Runs the BFS of all slots as one launch of the search loop.  Returns false
 // if the graph could not be built (the caller falls back to host steps).
 bool run_graph(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P, int n, bool any_mixed,
-               int sms, cudaStream_t s) {
-  cudaGraphExec_t exec = build_loop(slots, st, P, n, any_mixed, sms);
+               int tc_chunk, int sms, cudaStream_t s) {
+  cudaGraphExec_t exec = build_loop(slots, st, P, n, any_mixed, tc_chunk, sms);
   if (!exec) return false;
   bool ok = cudaGraphLaunch(exec, s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
   if (!ok) cudaGetLastError();
@@ -138,6 +140,13 @@ int mf_layout_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom, const 
   l->cell_sgn = bump->take(mc * 4 + 8);
   l->cell_off = bump->take((mc + 1) * 8);
   l->scan = bump->take((mc / 4096 + 2) * 8);
+  // root-screen lists: up to min(n_sv, 128) vectors per vertex on average;
+  // vertices past the pool screen the vector blocks instead
+  l->VL = (o->flags & MF_WANT_ROOTS) ? l->MV * (uint64_t)(r.n_sv < 128 ? r.n_sv : 128) : 0;
+  l->vtab_idx = bump->take(l->VL ? l->TV * 4 : 8);
+  l->vlist_off = bump->take(l->VL ? l->MV * 8 : 8);
+  l->vlist_n = bump->take(l->VL ? l->MV * 4 : 8);
+  l->vlist = bump->take(l->VL * 4 + 8);
   return MF_OK;
 }
 
@@ -175,12 +184,21 @@ int mf_setup_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_trace_opts *o, char 
   B.cell_sgn = (uint32_t *)(base + l->cell_sgn);
   B.cell_off = (int64_t *)(base + l->cell_off);
   B.max_cells = (o->flags & MF_WANT_CELLS) ? l->MC : 0;
-  B.vtab_idx = nullptr;  // no per-vertex lists: the root screen scans the blocks
-  B.vlist = nullptr;
-  B.vlist_off = nullptr;
-  B.vlist_n = nullptr;
-  B.vlist_cap = 0;
-  B.list_r2 = 0.f;
+  if (l->VL) {
+    B.vtab_idx = (uint32_t *)(base + l->vtab_idx);
+    B.vlist_off = (uint64_t *)(base + l->vlist_off);
+    B.vlist_n = (uint32_t *)(base + l->vlist_n);
+    B.vlist = (int32_t *)(base + l->vlist);
+    B.vlist_cap = l->VL;
+    B.list_r2 = mf_list_r2(S->F, S->R);
+  } else {  // no per-vertex lists: the root screen scans the blocks
+    B.vtab_idx = nullptr;
+    B.vlist = nullptr;
+    B.vlist_off = nullptr;
+    B.vlist_n = nullptr;
+    B.vlist_cap = 0;
+    B.list_r2 = 0.f;
+  }
   S->precision = o->precision;
   S->band = o->recheck_band > 0 ? o->recheck_band : 1e-3;
   S->root_tol = o->root_tol > 0 ? o->root_tol : 1e-12;
@@ -237,7 +255,7 @@ extern "C" int mf_trace_batch(mf_ctx *ctx, int32_t n, const mf_rbf *rbfs, const 
     MfProfScope ps(ctx, MF_PH_SEEDS, st, 2 * n + 5);
     for (int t = 0; t < n; t++)
       if (n_seeds[t] > 0) mf_launch_seeds(slots[t].F, slots[t].B, seeds[t], n_seeds[t], true, st);
-    mf_b_launch_eval(d_slots, d_plan, n, any_mixed, sms, st);
+    mf_b_launch_eval(d_slots, d_plan, n, any_mixed, ctx->tune.tc_chunk, sms, st);
     for (int t = 0; t < n; t++)
       if (n_seeds[t] > 0) mf_launch_seeds(slots[t].F, slots[t].B, seeds[t], n_seeds[t], false, st);
     mf_b_launch_init(d_slots, d_state, n, st);
@@ -247,12 +265,12 @@ extern "C" int mf_trace_batch(mf_ctx *ctx, int32_t n, const mf_rbf *rbfs, const 
   // --- search edges (Fig. 4) of all traces: one graph launch
   {
     MfProfScope ps(ctx, MF_PH_EXPAND_V, st, 1, n);
-    if (!run_graph(d_slots, d_state, d_plan, n, any_mixed, sms, st)) {
+    if (!run_graph(d_slots, d_state, d_plan, n, any_mixed, ctx->tune.tc_chunk, sms, st)) {
       // host-driven steps (same kernels) when conditional graphs are unavailable
       std::vector<MfSlotState> hs(n);
       for (long it = 0; it < (1l << 24); it++) {
         cudaGraphConditionalHandle none = 0;
-        launch_step(d_slots, d_state, d_plan, n, any_mixed, sms, none, 0, st);
+        launch_step(d_slots, d_state, d_plan, n, any_mixed, ctx->tune.tc_chunk, sms, none, 0, st);
         rc = mf_cuda_check(ctx, cudaMemcpyAsync(hs.data(), d_state, sizeof(MfSlotState) * n,
                                                 cudaMemcpyDeviceToHost, st),
                            "batch state");
@@ -485,6 +503,7 @@ struct mf_server {
   int64_t next_id = 1;
   cudaGraphExec_t step_exec = nullptr;
   cudaStream_t cap_stream = nullptr;
+  int tc_chunk = 64;  // tensor-core chunk width the step graph was built with
 };
 
 extern "C" int mf_server_create(mf_ctx *ctx, int32_t max_slots, size_t hbm_bytes, mf_server **out) {
@@ -523,7 +542,9 @@ extern "C" int mf_server_create(mf_ctx *ctx, int32_t max_slots, size_t hbm_bytes
   cudaMemset(s->d_state, 0, sizeof(MfSlotState) * max_slots);
   // the search loop of every slot as one graph, replayed by each
   // mf_server_step for up to MF_SERVER_STEPS breadth-first steps
-  s->step_exec = build_loop(s->d_slots, s->d_state, s->d_plan, max_slots, true, ctx->sms);
+  s->step_exec = build_loop(s->d_slots, s->d_state, s->d_plan, max_slots, true,
+                            ctx->tune.tc_chunk, ctx->sms);
+  s->tc_chunk = ctx->tune.tc_chunk;
   cudaGetLastError();
   if (cudaDeviceSynchronize() != cudaSuccess) {
     mf_server_destroy(s);
@@ -685,7 +706,7 @@ extern "C" int mf_server_step(mf_server *s, void *stream, int32_t *n_running, in
       const Request &r = s->reqs[s->slot_req[t]];
       if (r.n_seeds > 0) mf_launch_seeds(s->slots[t].F, s->slots[t].B, r.seeds, r.n_seeds, true, st);
     }
-    mf_b_launch_eval(s->d_slots, s->d_plan, n, true, sms, st);
+    mf_b_launch_eval(s->d_slots, s->d_plan, n, true, s->tc_chunk, sms, st);
     for (int t : fresh) {
       const Request &r = s->reqs[s->slot_req[t]];
       if (r.n_seeds > 0) mf_launch_seeds(s->slots[t].F, s->slots[t].B, r.seeds, r.n_seeds, false, st);
@@ -704,7 +725,7 @@ extern "C" int mf_server_step(mf_server *s, void *stream, int32_t *n_running, in
     if (s->step_exec) {
       if ((rc = mf_cuda_check(ctx, cudaGraphLaunch(s->step_exec, st), "server step"))) return rc;
     } else {
-      launch_step(s->d_slots, s->d_state, s->d_plan, n, true, sms, 0, 0, st);
+      launch_step(s->d_slots, s->d_state, s->d_plan, n, true, s->tc_chunk, sms, 0, 0, st);
     }
   }
   rc = mf_cuda_check(ctx, cudaMemcpyAsync(s->hstate.data(), s->d_state, sizeof(MfSlotState) * n,

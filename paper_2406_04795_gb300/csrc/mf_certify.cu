@@ -210,7 +210,8 @@ __device__ __forceinline__ float seg_obstacle_lb32(const CertObsT<float> &o, con
 // x = k pi/64 + r with |r| <= pi/128, pi/64 in two parts (the first has 25
 // significant bits, so k P1 is exact for |k| < 2^28), sin and cos of
 // j pi/64 (j = k mod 128) from the table, and sin r, cos r - 1 from their
-// Taylor polynomials (truncation below 1e-20 relative for |r| <= pi/128).
+// Taylor polynomials (the first dropped terms at |r| = pi/128: r^9/9! about
+// 9e-21, i.e. 4e-19 relative, for sin r; r^10/10! about 2e-23 for cos r - 1).
 #define CERT_PI64_HI 0x1.921fb5p-5
 #define CERT_PI64_LO 4.966642116727561e-10
 __device__ __forceinline__ void cert_sincos(double x, const double2 *tab, double *s, double *c) {

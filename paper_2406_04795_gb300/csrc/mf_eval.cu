@@ -523,6 +523,98 @@ __device__ __forceinline__ F64Acc warp_f64(const MfRbfDev &R, const double *x, c
 
 #define EVAL_WARPS 8
 
+// Stores the root-screen list of vertex i (nl entries in lbuf, all lanes
+// call): a pool range when it fits, else the vertex is marked as having none
+// (its edges then screen the vector blocks).
+__device__ __forceinline__ void store_vertex_list(const MfTraceBufs &B, uint64_t i, int nl,
+                                                  const int *lbuf) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long off = 0;
+  if (lane == 0 && nl <= LIST_CAP) off = atomicAdd(&B.cnt->n_vlist, (unsigned long long)nl);
+  off = __shfl_sync(FULL, off, 0);
+  const bool ok = nl <= LIST_CAP && off + nl <= B.vlist_cap;
+  __syncwarp();
+  if (ok)
+    for (int q = lane; q < nl; q += 32) B.vlist[off + q] = lbuf[q];
+  if (lane == 0) {
+    B.vlist_off[i] = off;
+    B.vlist_n[i] = ok ? (uint32_t)nl : MF_NO_LIST;
+  }
+  __syncwarp();
+}
+
+// The root-screen list of the point with FP32 coordinates xh (all lanes):
+// the vectors with FP32 r^2 <= list_r2, computed and ordered exactly as
+// warp_f64_pass lists them, so both evaluators give a vertex the same list.
+// Returns the count (entries beyond LIST_CAP are counted, not stored).
+template <int D>
+__device__ int warp_vertex_list(const MfRbfDev &R, const float *xh, float list_r2, int *lbuf) {
+  const int lane = threadIdx.x & 31;
+  const int d = dim_of<D>(R.d);
+  const unsigned lt = (1u << lane) - 1u;
+  const float box2 = list_r2 * 1.001f + 1e-5f;
+  int nlist = 0;
+  for (int bb0 = 0; bb0 < R.nblk; bb0 += 32) {
+    bool bkeep = false;
+    if (bb0 + lane < R.nblk) {
+      float q2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; k++)
+        if (k < d) {
+          const float lo = R.blk_lo[(int64_t)k * R.nblk + bb0 + lane];
+          const float hi = R.blk_hi[(int64_t)k * R.nblk + bb0 + lane];
+          const float t = fmaxf(fmaxf(lo - xh[k], xh[k] - hi), 0.f);
+          q2 = fmaf(t, t, q2);
+        }
+      bkeep = q2 <= box2;
+    }
+    unsigned bm = __ballot_sync(FULL, bkeep);
+    while (bm) {
+      const int j = (bb0 + __ffs(bm) - 1) * 32 + lane;
+      bm &= bm - 1;
+      bool listed = false;
+      if (j < R.n) {
+        float r2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; k++)
+          if (k < d) {
+            const float t = xh[k] - R.sv32[(int64_t)k * R.n + j];
+            r2 = fmaf(t, t, r2);
+          }
+        listed = r2 <= list_r2;
+      }
+      const unsigned ml = __ballot_sync(FULL, listed);
+      const int pos = nlist + __popc(ml & lt);
+      if (listed && pos < LIST_CAP) lbuf[pos] = j;
+      nlist += __popc(ml);
+    }
+  }
+  __syncwarp();
+  return nlist;
+}
+
+// Root-screen lists of vertex-list entries [v_evaluated, n_vertices) on the
+// mixed paths, whose evaluators do not screen (warp per vertex).
+template <int D>
+__global__ void __launch_bounds__(EVAL_WARPS * 32) k_vertex_lists(MfFrame F, MfRbfDev R, MfTraceBufs B) {
+  __shared__ int slist[EVAL_WARPS][LIST_CAP];
+  const int w = threadIdx.x >> 5;
+  const uint64_t begin = B.cnt->v_evaluated;
+  uint64_t end = B.cnt->n_vertices;
+  if (end > B.max_vertices) end = B.max_vertices;
+  const uint64_t nwarps = (uint64_t)gridDim.x * EVAL_WARPS;
+  for (uint64_t i = begin + (uint64_t)blockIdx.x * EVAL_WARPS + w; i < end; i += nwarps) {
+    int32_t y[MF_MAXD];
+    double x[D];
+#pragma unroll
+    for (int k = 0; k < MF_MAXD; k++) y[k] = k < F.d ? B.vert_y[i * F.d + k] : 0;
+    vertex_x_lanes<D>(F, y, x);
+    const Split32<D> xs = split32<D>(F.d, x, nullptr);
+    const int nl = warp_vertex_list<D>(R, xs.hi, B.list_r2, slist[w]);
+    store_vertex_list(B, i, nl, slist[w]);
+  }
+}
+
 // f at vertex-list entries [v_evaluated, n_vertices) (FP64).
 template <int D>
 __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_vertices_f64(MfFrame F, MfRbfDev R, MfTraceBufs B) {
@@ -547,21 +639,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_vertices_f64(MfFrame F
       mf_vtab_f(B, B.vert_slot[i]) = a.f;
       if (fabs(a.f) < 1e-12) atomicAdd(&B.cnt->n_near_zero, 1ull);
     }
-    if (B.vlist) {
-      // the vertex's list for the root screen, if it fits the pool
-      unsigned long long off = 0;
-      if (lane == 0 && nl <= LIST_CAP) off = atomicAdd(&B.cnt->n_vlist, (unsigned long long)nl);
-      off = __shfl_sync(FULL, off, 0);
-      const bool ok = nl <= LIST_CAP && off + nl <= B.vlist_cap;
-      __syncwarp();
-      if (ok)
-        for (int q = lane; q < nl; q += 32) B.vlist[off + q] = slist[w][q];
-      if (lane == 0) {
-        B.vlist_off[i] = off;
-        B.vlist_n[i] = ok ? (uint32_t)nl : MF_NO_LIST;
-      }
-      __syncwarp();
-    }
+    if (B.vlist) store_vertex_list(B, i, nl, slist[w]);  // the root screen's list
   }
   if (lane == 0 && (terms[0] | terms[1])) {
     atomicAdd(&B.cnt->eval_terms, terms[0]);
@@ -788,6 +866,10 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_eval_points_f64(MfRbfDev R,
 // between STRONG_TAU and ROOT_TAU ("mid") joins the FP32 stage's list and is
 // summed in FP32 with the weak terms in the FP64 step.
 #define ROOT_TAU_SHIFT 3.5065579f
+// The mixed paths need |dt| <= 1e-6 only: their FP64 step takes the terms
+// that can exceed 1e-5 (shift ln(1e-5 / STRONG_TAU)); the FP32 part may then
+// move t by up to 1e-7 and the accepted Newton step leaves < 1e-7.
+#define ROOT_TAU_SHIFT_FAST 10.414313f
 
 // Warp sums of four values, every lane receiving all four: a transposed
 // butterfly (lanes split the values between halves, then quarters, before
@@ -903,8 +985,9 @@ __device__ __forceinline__ F64Acc root_eval64(const MfRbfDev &R, const int *near
 // evaluation's own limit, whichever is larger.  Otherwise the point is
 // evaluated again with every kept term in FP64.
 // (The check runs in FP32: the 1.01 factor covers its roundings.)
-__device__ __forceinline__ bool root_fp32_part_too_coarse(const MfRbfDev &R, float weak, float gp) {
-  const float lim = fmaxf(R.weak_limit32, 0.99e-10f * fabsf(gp) - R.drop_bound32);
+__device__ __forceinline__ bool root_fp32_part_too_coarse(const MfRbfDev &R, float weak, float gp,
+                                                          bool fast) {
+  const float lim = fmaxf(R.weak_limit32, (fast ? 0.99e-7f : 0.99e-10f) * fabsf(gp) - R.drop_bound32);
   return weak * (1.01f * R.weak_rel32) > lim;
 }
 
@@ -919,7 +1002,8 @@ template <int D>
 __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, uint64_t e,
                           double tol, const int *src, int srcn, int *near, int *midl, int *qs,
                           int *qw,
-                          RootWarpState *ws, unsigned long long &evals, unsigned long long *terms) {
+                          RootWarpState *ws, unsigned long long &evals, unsigned long long *terms,
+                          bool fast) {
   const int lane = threadIdx.x & 31;
   const int d = dim_of<D>(F.d);
   const unsigned lt = (1u << lane) - 1u;
@@ -966,6 +1050,7 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
   int ns = 0, nm = 0, nw = 0;
   const float inv_dd = 1.f / dd32;
   const float pre = (sqrtf(R.screen_r2) + 0.5f * sqrtf(dd32)) * 1.0001f + 1e-5f, pre2 = pre * pre;
+  const float shift64 = 0.5f - (fast ? ROOT_TAU_SHIFT_FAST : ROOT_TAU_SHIFT);
   // one round: lane tests vector j (gathered row for a group list, or the
   // coalesced coordinate arrays) and the survivors are compacted
   auto screen_round = [&](bool valid, int j, bool gathered) {
@@ -1003,7 +1088,7 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
         keep = r2 <= R.screen_r2;
         const float s32 = R.strong32[j];
         strong = g32 * r2 < s32 + 0.5f;
-        strong64 = g32 * r2 < s32 + (0.5f - ROOT_TAU_SHIFT);
+        strong64 = g32 * r2 < s32 + shift64;
       }
     }
     // strong64 entries fill near from the front, weak ones from the back,
@@ -1077,6 +1162,7 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
   }
   __syncwarp();
   const bool overflow = ns + nw > NEAR_CAP || nm > MID_CAP;
+  if (overflow && lane == 0) atomicAdd(&B.cnt->root_overflow, 1ull);
   const double f0 = B.edge_f[2 * e], f1 = B.edge_f[2 * e + 1];
   const bool s1 = f0 >= 0.0;
   // 2. FP32 Halley iteration (cubic: the evaluation yields g'' anyway),
@@ -1142,12 +1228,12 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
       gpf = (float)a.g;
     } else if (reuse) {
       a = root_eval64<false, false, D>(R, near, ns, nw, midl, nm, x, dir, xs, terms);
-      if (root_fp32_part_too_coarse(R, a.weak, gpf))
+      if (root_fp32_part_too_coarse(R, a.weak, gpf, fast))
         a = root_eval64<true, false, D>(R, near, ns, nw, midl, nm, x, dir, xs, terms);
     } else {
       a = root_eval64<false, true, D>(R, near, ns, nw, midl, nm, x, dir, xs, terms);
       gpf = (float)a.g;
-      if (root_fp32_part_too_coarse(R, a.weak, gpf)) {
+      if (root_fp32_part_too_coarse(R, a.weak, gpf, fast)) {
         a = root_eval64<true, true, D>(R, near, ns, nw, midl, nm, x, dir, xs, terms);
         gpf = (float)a.g;
       }
@@ -1162,8 +1248,12 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
     if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
     const float step = fabsf((float)(tn - t));
     t = tn;
+    // a first step of s after the FP32 stage errs by ~|g''| s^2 / (2 |g'|)
+    // (Newton remainder) plus 5e-5 s (the reused g'): below 1e-9 for
+    // s <= 1e-5 and the remainder test, below 2e-7 in the fast mode
     if (step <= tolf || step <= 1e-7f || hi - lo <= 9.094947017729282e-13 ||
-        (it == 0 && step <= 1e-5f && gppf * step * step <= 5e-11f * fabsf(gpf)))
+        (it == 0 && step <= (fast ? 1e-3f : 1e-5f) &&
+         gppf * step * step <= (fast ? 1e-7f : 5e-11f) * fabsf(gpf)))
       break;
   }
   if (lane == 0) B.edge_t[e] = t;
@@ -1256,7 +1346,7 @@ __device__ int group_screen(const MfFrame &F, const MfRbfDev &R, const MfTraceBu
 template <int D, int MINB>
 __global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(MfFrame F, MfRbfDev R, MfTraceBufs B,
                                                                uint64_t n_edges, double tol,
-                                                               int group) {
+                                                               int group, int fast) {
   __shared__ int snear[ROOT_WARPS][NEAR_CAP];
   __shared__ int smid[ROOT_WARPS][MID_CAP];
   __shared__ int sq[ROOT_WARPS][2][64];
@@ -1270,7 +1360,7 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(MfFrame F, 
   if (group <= 1) {
     for (uint64_t e = (uint64_t)blockIdx.x * ROOT_WARPS + w; e < n_edges; e += nwarps)
       root_edge<D>(F, R, B, e, tol, nullptr, 0, snear[w], smid[w], sq[w][0], sq[w][1], &sws[w],
-                   evals, terms);
+                   evals, terms, fast != 0);
   } else {
     const uint64_t G = (uint64_t)group;
     for (uint64_t g0 = ((uint64_t)blockIdx.x * ROOT_WARPS + w) * G; g0 < n_edges; g0 += nwarps * G) {
@@ -1278,7 +1368,7 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(MfFrame F, 
       const int gn = group_screen<D>(F, R, B, g0, ng, rs, sgrp);
       for (int q = 0; q < ng; q++)
         root_edge<D>(F, R, B, g0 + q, tol, gn >= 0 ? sgrp : nullptr, gn, snear[w], smid[w],
-                     sq[w][0], sq[w][1], &sws[w], evals, terms);
+                     sq[w][0], sq[w][1], &sws[w], evals, terms, fast != 0);
     }
   }
   root_flush(B, evals, terms);
@@ -1337,6 +1427,7 @@ __device__ void warp_f32_bound(const MfRbfDev &R, const double *x, double &f, do
 __global__ void __launch_bounds__(EVAL_WARPS * 32) k_b_eval(const MfSlot *slots, const MfBatchPlan *P,
                                                            int n, int recheck) {
   __shared__ int sq[EVAL_WARPS][2][64];
+  __shared__ int slist[EVAL_WARPS][LIST_CAP];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned long long *pfx = recheck ? P->pr : P->pv;
   const unsigned long long total = pfx[n];
@@ -1345,6 +1436,8 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_b_eval(const MfSlot *slots,
        item += nwarps) {
     const int t = mf_slot_of(pfx, n, item);
     const MfSlot &S = slots[t];
+    // MF_MIXED_BF16 slots are evaluated by the tensor-core tiles
+    if (!recheck && S.precision == MF_MIXED_BF16) continue;
     const int d = S.F.d;
     const unsigned long long local = item - pfx[t];
     const uint64_t i = recheck ? (uint64_t)S.B.recheck[P->r0[t] + local] : P->v0[t] + local;
@@ -1356,13 +1449,18 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_b_eval(const MfSlot *slots,
     const uint32_t slot = S.B.vert_slot[i];
     if (recheck || S.precision == MF_FP64) {
       unsigned long long terms[2] = {0, 0};
-      const F64Acc a = warp_f64<false, MF_MAXD>(S.R, x, nullptr, sq[w][0], sq[w][1], terms);
+      // FP64 slots record the root-screen list in the same pass
+      const bool lists = !recheck && S.B.vlist;
+      int nl = 0;
+      const F64Acc a = warp_f64<false, MF_MAXD>(S.R, x, nullptr, sq[w][0], sq[w][1], terms,
+                                                lists ? slist[w] : nullptr, S.B.list_r2, &nl);
       if (lane == 0) {
         mf_vtab_f(S.B, slot) = a.f;
         if (fabs(a.f) < 1e-12) atomicAdd(&S.B.cnt->n_near_zero, 1ull);
         atomicAdd(&S.B.cnt->eval_terms, terms[0]);
         atomicAdd(&S.B.cnt->eval_terms_weak, terms[1]);
       }
+      if (lists) store_vertex_list(S.B, i, nl, slist[w]);
     } else {
       double f, bound;
       warp_f32_bound(S.R, x, f, bound);
@@ -1375,6 +1473,31 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) k_b_eval(const MfSlot *slots,
         }
       }
     }
+  }
+}
+
+// Root-screen lists of the new vertices of the mixed slots (their
+// evaluators do not screen); FP64 slots list in k_b_eval.
+__global__ void __launch_bounds__(EVAL_WARPS * 32) k_b_lists(const MfSlot *slots, const MfBatchPlan *P,
+                                                            int n) {
+  __shared__ int slist[EVAL_WARPS][LIST_CAP];
+  const int w = threadIdx.x >> 5;
+  const unsigned long long total = P->pv[n];
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * EVAL_WARPS;
+  for (unsigned long long item = (unsigned long long)blockIdx.x * EVAL_WARPS + w; item < total;
+       item += nwarps) {
+    const int t = mf_slot_of(P->pv, n, item);
+    const MfSlot &S = slots[t];
+    if (S.precision == MF_FP64 || !S.B.vlist) continue;
+    const uint64_t i = P->v0[t] + (item - P->pv[t]);
+    int32_t y[MF_MAXD];
+    double x[MF_MAXD];
+#pragma unroll
+    for (int k = 0; k < MF_MAXD; k++) y[k] = k < S.F.d ? S.B.vert_y[i * S.F.d + k] : 0;
+    vertex_x_lanes<MF_MAXD>(S.F, y, x);
+    const Split32<MF_MAXD> xs = split32<MF_MAXD>(S.F.d, x, nullptr);
+    const int nl = warp_vertex_list<MF_MAXD>(S.R, xs.hi, S.B.list_r2, slist[w]);
+    store_vertex_list(S.B, i, nl, slist[w]);
   }
 }
 
@@ -1408,18 +1531,21 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, 2) k_b_roots(const MfSlot *sl
       unsigned long long evals = 0, terms[2] = {0, 0};
       for (int q = 0; q < ng; q++)
         root_edge<D>(S.F, S.R, S.B, e0 + q, S.root_tol, gn >= 0 ? sgrp : nullptr, gn, snear[w],
-                     smid[w], sq[w][0], sq[w][1], &sws[w], evals, terms);
+                     smid[w], sq[w][0], sq[w][1], &sws[w], evals, terms,
+                     S.precision != MF_FP64 && !(S.flags & MF_ROOTS_FP64_EXACT));
       root_flush(S.B, evals, terms);
       i = end;
     }
   }
 }
 
-void mf_b_launch_eval(const MfSlot *slots, MfBatchPlan *P, int n, bool any_mixed, int sms,
-                      cudaStream_t s) {
+void mf_b_launch_eval(const MfSlot *slots, MfBatchPlan *P, int n, bool any_mixed, int tc_chunk,
+                      int sms, cudaStream_t s) {
   mf_b_launch_plan_eval(slots, P, n, false, s);
   k_b_eval<<<sms * 8, EVAL_WARPS * 32, 0, s>>>(slots, P, n, 0);
   if (any_mixed) {
+    mf_b_launch_eval_tc(slots, P, n, tc_chunk, sms, s);
+    k_b_lists<<<sms * 8, EVAL_WARPS * 32, 0, s>>>(slots, P, n);
     mf_b_launch_plan_eval(slots, P, n, true, s);
     k_b_eval<<<sms * 8, EVAL_WARPS * 32, 0, s>>>(slots, P, n, 1);
   }
@@ -1468,6 +1594,15 @@ void mf_launch_eval_vertices_mixed(const MfFrame &F, const MfRbfDev &R, const Mf
     mf_launch_eval_vertices_tc(F, R, B, band, T.tc_chunk, sms, st);
   else
     k_eval_mixed_f32<true><<<sms * 4, MIX_THREADS, 0, st>>>(F, R, B, nullptr, 0, nullptr, nullptr, band);
+  if (B.vlist) {  // the root screen's per-vertex lists
+    switch (F.d) {
+#define MF_CASE(DD) \
+  case DD: k_vertex_lists<DD><<<sms * 8, EVAL_WARPS * 32, 0, st>>>(F, R, B); break;
+      MF_CASE(2) MF_CASE(3) MF_CASE(4) MF_CASE(5) MF_CASE(6) MF_CASE(7)
+#undef MF_CASE
+      default: k_vertex_lists<MF_MAXD><<<sms * 8, EVAL_WARPS * 32, 0, st>>>(F, R, B);
+    }
+  }
   switch (F.d) {
 #define MF_CASE(DD) \
   case DD: k_recheck_vertices_f64<DD><<<sms * 8, EVAL_WARPS * 32, 0, st>>>(F, R, B); break;
@@ -1480,30 +1615,178 @@ void mf_launch_eval_vertices_mixed(const MfFrame &F, const MfRbfDev &R, const Mf
 
 template <int DD, int MINB>
 static void launch_roots_d(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
-                           uint64_t n_edges, double tol, int grid, int group, cudaStream_t st) {
+                           uint64_t n_edges, double tol, int grid, int group, int fast,
+                           cudaStream_t st) {
   const int dyn = group > 1 ? ROOT_WARPS * GROUP_CAP * (int)sizeof(int) : 0;
   if (dyn) cudaFuncSetAttribute(k_roots_f64<DD, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-  k_roots_f64<DD, MINB><<<grid, ROOT_WARPS * 32, dyn, st>>>(F, R, B, n_edges, tol, group);
+  k_roots_f64<DD, MINB><<<grid, ROOT_WARPS * 32, dyn, st>>>(F, R, B, n_edges, tol, group, fast);
 }
 
 template <int MINB>
 static void launch_roots(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, uint64_t n_edges,
-                         double tol, int grid, int group, cudaStream_t st) {
+                         double tol, int grid, int group, int fast, cudaStream_t st) {
   switch (F.d) {
 #define MF_CASE(DD) \
-  case DD: launch_roots_d<DD, MINB>(F, R, B, n_edges, tol, grid, group, st); break;
+  case DD: launch_roots_d<DD, MINB>(F, R, B, n_edges, tol, grid, group, fast, st); break;
     MF_CASE(2) MF_CASE(3) MF_CASE(4) MF_CASE(5) MF_CASE(6) MF_CASE(7)
 #undef MF_CASE
-    default: launch_roots_d<MF_MAXD, MINB>(F, R, B, n_edges, tol, grid, group, st);
+    default: launch_roots_d<MF_MAXD, MINB>(F, R, B, n_edges, tol, grid, group, fast, st);
   }
 }
 
 void mf_launch_roots_f64(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, uint64_t n_edges,
-                         double tol, const MfTune &T, int sms, cudaStream_t st) {
+                         double tol, const MfTune &T, int sms, cudaStream_t st, bool fast) {
   if (n_edges == 0) return;
   const int grid = sms * T.roots_bps;
-  if (T.roots_variant == 1) launch_roots<3>(F, R, B, n_edges, tol, grid, T.roots_group, st);
-  else launch_roots<2>(F, R, B, n_edges, tol, grid, T.roots_group, st);
+  if (T.roots_variant == 1) launch_roots<3>(F, R, B, n_edges, tol, grid, T.roots_group, fast, st);
+  else launch_roots<2>(F, R, B, n_edges, tol, grid, T.roots_group, fast, st);
+}
+
+// ---------------------------------------------------------------------------
+// Throughput probes (the denominators of the FP64 and MUFU rooflines) and the
+// accuracy diagnostic of the table-driven exp.  Each probe thread runs
+// independent chains, so the measured rate is the pipe's throughput.
+// ---------------------------------------------------------------------------
+#define PROBE_CHAINS 8
+__global__ void k_probe_dfma(int iters, double seed, double *sink) {
+  double a[PROBE_CHAINS];
+#pragma unroll
+  for (int i = 0; i < PROBE_CHAINS; i++) a[i] = seed + 1e-9 * threadIdx.x + i;
+  const double m = 0.9999999, c = 1e-7;
+  for (int it = 0; it < iters; it++) {
+#pragma unroll
+    for (int i = 0; i < PROBE_CHAINS; i++) a[i] = fma(a[i], m, c);
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int i = 0; i < PROBE_CHAINS; i++) t += a[i];
+  if (t == 1234.5) sink[0] = t;  // keeps the chains alive
+}
+
+__global__ void k_probe_ffma(int iters, float seed, float *sink) {
+  float a[PROBE_CHAINS];
+#pragma unroll
+  for (int i = 0; i < PROBE_CHAINS; i++) a[i] = seed + 1e-6f * threadIdx.x + i;
+  const float m = 0.9999f, c = 1e-4f;
+  for (int it = 0; it < iters; it++) {
+#pragma unroll
+    for (int i = 0; i < PROBE_CHAINS; i++) a[i] = fmaf(a[i], m, c);
+  }
+  float t = 0.f;
+#pragma unroll
+  for (int i = 0; i < PROBE_CHAINS; i++) t += a[i];
+  if (t == 1234.5f) sink[0] = t;
+}
+
+__global__ void k_probe_ex2(int iters, float *sink) {
+  float a[PROBE_CHAINS];
+#pragma unroll
+  for (int i = 0; i < PROBE_CHAINS; i++) a[i] = -0.5f - 1e-6f * threadIdx.x - 0.01f * i;
+  for (int it = 0; it < iters; it++) {
+#pragma unroll
+    for (int i = 0; i < PROBE_CHAINS; i++) a[i] = -ex2_approx(a[i]);
+  }
+  float t = 0.f;
+#pragma unroll
+  for (int i = 0; i < PROBE_CHAINS; i++) t += a[i];
+  if (t == 1234.5f) sink[0] = t;
+}
+
+__global__ void k_probe_expneg(int iters, const double *tab, double *sink) {
+  constexpr int C = 4;
+  double x[C], acc[C];
+#pragma unroll
+  for (int i = 0; i < C; i++) {
+    x[i] = -0.5 - 1e-7 * threadIdx.x - 3.1 * i;
+    acc[i] = 0.0;
+  }
+  for (int it = 0; it < iters; it++) {
+#pragma unroll
+    for (int i = 0; i < C; i++) {
+      acc[i] += mf_exp_neg(x[i], tab);
+      x[i] -= 1e-3;
+    }
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int i = 0; i < C; i++) t += acc[i];
+  if (t == 1234.5) sink[0] = t;
+}
+
+__global__ void k_exp_table(double *tab) {
+  const int j = threadIdx.x;
+  if (j < 64) tab[j] = exp2((double)j / 64.0);  // as the RBF preparation builds it
+}
+
+__global__ void k_diag_exp(const double *tab, const double *x, int64_t n, double *y_tab,
+                           double *y_lib) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  y_tab[i] = mf_exp_neg(x[i], tab);
+  y_lib[i] = exp(x[i]);
+}
+
+extern "C" int mf_probe_rates(mf_ctx *ctx, mf_rates *out, void *stream) {
+  if (!ctx || !out) return MF_ERR_INVALID;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  double *buf = (double *)mf_ctx_buffer(ctx, MF_SLOT_SCAN, 64 * 8 + 256);
+  if (!buf) return MF_ERR_OOM;
+  double *tab = buf, *sink = buf + 64;
+  k_exp_table<<<1, 64, 0, st>>>(tab);
+  const int blocks = ctx->sms * 8, threads = 256;
+  const double nthreads = (double)blocks * threads;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  // best of three timed launches after one warm-up
+  auto timed = [&](auto launch) {
+    launch();
+    float best = 1e30f;
+    for (int r = 0; r < 3; r++) {
+      cudaEventRecord(e0, st);
+      launch();
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) best = ms;
+    }
+    return (double)best * 1e-3;
+  };
+  const int it_d = 4096, it_f = 65536, it_x = 16384, it_e = 1024;
+  const double t_d = timed([&]() { k_probe_dfma<<<blocks, threads, 0, st>>>(it_d, 1.0, sink); });
+  const double t_f =
+      timed([&]() { k_probe_ffma<<<blocks, threads, 0, st>>>(it_f, 1.f, (float *)sink); });
+  const double t_x = timed([&]() { k_probe_ex2<<<blocks, threads, 0, st>>>(it_x, (float *)sink); });
+  const double t_e = timed([&]() { k_probe_expneg<<<blocks, threads, 0, st>>>(it_e, tab, sink); });
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const int rc = mf_cuda_check(ctx, cudaGetLastError(), "probe kernels");
+  if (rc) return rc;
+  out->fp64_fma_per_s = nthreads * PROBE_CHAINS * it_d / t_d;
+  out->fp32_fma_per_s = nthreads * PROBE_CHAINS * it_f / t_f;
+  out->ex2_per_s = nthreads * PROBE_CHAINS * it_x / t_x;
+  out->exp_neg_per_s = nthreads * 4.0 * it_e / t_e;
+  int mhz = 0;
+  cudaDeviceGetAttribute(&mhz, cudaDevAttrClockRate, ctx->device);
+  out->sm_count = ctx->sms;
+  out->sm_clock_mhz = mhz / 1000.0;
+  return MF_OK;
+}
+
+extern "C" int mf_diag_exp(mf_ctx *ctx, const double *x, int64_t n, double *y_table, double *y_lib,
+                           void *stream) {
+  if (!ctx || n < 0 || (n > 0 && (!x || !y_table || !y_lib))) return MF_ERR_INVALID;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  double *tab = (double *)mf_ctx_buffer(ctx, MF_SLOT_SCAN, 64 * 8 + 256);
+  if (!tab) return MF_ERR_OOM;
+  k_exp_table<<<1, 64, 0, st>>>(tab);
+  if (n > 0) k_diag_exp<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tab, x, n, y_table, y_lib);
+  const int rc = mf_cuda_check(ctx, cudaGetLastError(), "mf_diag_exp");
+  if (rc) return rc;
+  return mf_cuda_check(ctx, cudaStreamSynchronize(st), "mf_diag_exp");
 }
 
 extern "C" int mf_eval(mf_ctx *ctx, const mf_rbf *rbf, const double *q, int64_t n, int32_t precision,
@@ -1512,6 +1795,12 @@ extern "C" int mf_eval(mf_ctx *ctx, const mf_rbf *rbf, const double *q, int64_t 
   if (n < 0 || (n > 0 && (!q || !f_out)) ||
       (precision != MF_FP64 && precision != MF_MIXED_FP32 && precision != MF_MIXED_BF16))
     return mf_set_error(ctx, MF_ERR_INVALID, "mf_eval: bad arguments");
+  // the tensor-core GEMM is exact only for small integer offsets between
+  // lattice vertices of a tile; arbitrary points have no such structure
+  if (precision == MF_MIXED_BF16)
+    return mf_set_error(ctx, MF_ERR_INVALID,
+                        "mf_eval: MF_MIXED_BF16 evaluates lattice vertices only (mf_trace); use "
+                        "MF_MIXED_FP32 or MF_FP64 for arbitrary points");
   cudaSetDevice(ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
   MfRbfDev R;

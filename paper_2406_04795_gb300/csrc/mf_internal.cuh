@@ -54,6 +54,7 @@ struct MfCounters {
   unsigned long long eval_terms_weak;  // RBF terms with the reduced-cost exp, vertex evaluation
   unsigned long long root_terms_weak;  // RBF terms with the reduced-cost exp, root solve
   unsigned long long n_vlist;      // entries taken from the per-vertex list pool
+  unsigned long long root_overflow;  // edges whose screen lists overflowed (full re-evaluation)
   unsigned int err_table_full;     // a hash probe ran past the table
   unsigned int err_overflow;       // a list ran past its capacity
   unsigned int err_missing;        // a vertex expected in the table was absent
@@ -139,6 +140,7 @@ struct MfRbfDev {
 // trace through a prefix array over the slots.
 // ------------------------------------------------------------------------
 #define MF_MAX_SLOTS 1024
+#define MF_TC_TILE 128  // vertices per tensor-core tile (the MMA's M)
 
 struct MfSlot {  // one trace of a batch (device-resident descriptor)
   MfFrame F;
@@ -171,8 +173,13 @@ void mf_b_launch_cells(const MfSlot *slots, MfBatchPlan *P, int n, const int32_t
                        cudaStream_t s);
 void mf_b_launch_cell_edges(const MfSlot *slots, MfBatchPlan *P, int n, bool fill,
                             const int32_t *only, int sms, cudaStream_t s);
-void mf_b_launch_eval(const MfSlot *slots, MfBatchPlan *P, int n, bool any_mixed, int sms,
-                      cudaStream_t s);
+// Vertex evaluation of every slot: FP64 or FP32 SIMT warps, the tensor-core
+// tiles of MF_MIXED_BF16 slots (tc_chunk support vectors per MMA), the FP64
+// recheck of the mixed slots, and the per-vertex root-screen lists.
+void mf_b_launch_eval(const MfSlot *slots, MfBatchPlan *P, int n, bool any_mixed, int tc_chunk,
+                      int sms, cudaStream_t s);
+void mf_b_launch_eval_tc(const MfSlot *slots, const MfBatchPlan *P, int n, int n_chunk, int sms,
+                         cudaStream_t st);
 // dims: bit d set when some slot has dimension d (one exact-d launch each).
 void mf_b_launch_roots(const MfSlot *slots, MfBatchPlan *P, int n, const int32_t *only,
                        uint32_t dims, int group, int sms, cudaStream_t s);
@@ -190,6 +197,7 @@ struct MfBatchPlan {  // per-step work prefixes over the slots
   unsigned long long pr[MF_MAX_SLOTS + 1];  // vertices to re-check in FP64
   unsigned long long pe[MF_MAX_SLOTS + 1];  // traced edges (roots, cells)
   unsigned long long pc[MF_MAX_SLOTS + 1];  // cells (CSR)
+  unsigned long long pt[MF_MAX_SLOTS + 1];  // tensor-core tiles (MF_MIXED_BF16 slots)
   unsigned long long v0[MF_MAX_SLOTS], r0[MF_MAX_SLOTS];
   unsigned long long steps;  // steps run since the plan was cleared
   int32_t overrun;           // the step limit stopped the search
@@ -464,12 +472,30 @@ int mf_ctx_sm_count(mf_ctx *ctx);
 int mf_prepare_rbf(mf_ctx *ctx, const mf_rbf *rbf, MfRbfDev *out, cudaStream_t st);
 size_t mf_rbf_prep_bytes(int d, int64_t n);
 int mf_prepare_rbf_at(mf_ctx *ctx, const mf_rbf *rbf, char *base, MfRbfDev *out, cudaStream_t st);
+// Squared radius of a vertex's root-screen list: the screen radius around
+// any point of an edge leaving the vertex.  The longest edge is lam |L e(M)|
+// with |L e(M)|^2 = k (1 - 2ck + c^2 k d) for |M| = k; the margins cover the
+// FP32 distances of both screens.
+static inline float mf_list_r2(const MfFrame &F, const MfRbfDev &R) {
+  double m2 = 0.0;
+  for (int k = 1; k <= F.d; k++) {
+    const double v = k * (1.0 - 2.0 * F.c * k + F.c * F.c * k * F.d);
+    if (v > m2) m2 = v;
+  }
+  const double rl = std::sqrt((double)R.screen_r2) * 1.0001 + F.lam * std::sqrt(m2) + 1e-4;
+  return (float)(rl * rl);
+}
 // Trace host helpers (mf_trace.cu).
 int mf_build_frame(mf_ctx *ctx, int d, double lam, const mf_domain *dom, MfFrame *F);
 void mf_exclusive_scan(const int64_t *in, int64_t *out, int64_t n, int64_t *scratch, cudaStream_t st);
 uint64_t mf_next_pow2(uint64_t x);
 void mf_launch_seeds(const MfFrame &F, const MfTraceBufs &B, const double *seeds, int64_t n,
                      bool vertices, cudaStream_t s);
+// The crossing n-simplices of edges [0, n_edges) with their sign masks and
+// CSR row lengths (in B.cell_off), and, once cell_off is scanned, the CSR
+// fill of B.cell_idx (a missing edge sets err_missing).
+void mf_launch_cells_enum(const MfFrame &F, const MfTraceBufs &B, uint64_t n_edges, cudaStream_t st);
+void mf_launch_cells_fill(const MfFrame &F, const MfTraceBufs &B, uint64_t n_cells, cudaStream_t st);
 // Launch choices picked by the autotuner (mf_autotune); the defaults serve
 // untuned contexts and the allocation-free entry point.
 struct MfTune {
@@ -488,8 +514,11 @@ void mf_launch_eval_vertices_f64(const MfFrame &F, const MfRbfDev &R, const MfTr
 void mf_launch_eval_vertices_mixed(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
                                    int precision, double band, const MfTune &T, int sms,
                                    cudaStream_t st);
+// fast: the mixed paths' root accuracy (|dt| <= 1e-6 instead of 1e-9), with
+// fewer terms in the FP64 step.
 void mf_launch_roots_f64(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
-                         uint64_t n_edges, double tol, const MfTune &T, int sms, cudaStream_t st);
+                         uint64_t n_edges, double tol, const MfTune &T, int sms, cudaStream_t st,
+                         bool fast = false);
 void mf_launch_eval_vertices_tc(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
                                 double band, int n_chunk, int sms, cudaStream_t st);
 

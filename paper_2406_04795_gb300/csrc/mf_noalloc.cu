@@ -14,9 +14,14 @@
 //
 // Set-up: the first call on a device (with that device current) looks up the
 // array's device address with cudaGetSymbolAddress; make that first call
-// before any stream capture.  Every call on a device shares the one array and
-// clears what must start empty (counters, hash tables); two calls that overlap
-// on the GPU (different streams, threads) race on it and must not be issued.
+// before any stream capture.  Under CUDA's lazy module loading the library's
+// device code, and with it the array, is loaded on a device by the first call
+// or the first launch of any of the library's kernels there: that is the
+// moment the array's memory is taken, so make that first call at start-up,
+// before the device memory is reserved elsewhere.  Every call on a device
+// shares the one array and clears what must start empty (counters, hash
+// tables); two calls that overlap on the GPU (different streams, threads)
+// race on it and must not be issued.
 #include <cmath>
 #include <cstring>
 
@@ -41,43 +46,6 @@ __global__ void k_seed_vertices(MfFrame F, MfTraceBufs B, const double *seeds, i
 __global__ void k_seed_edges(MfFrame F, MfTraceBufs B, const double *seeds, int64_t n);
 __global__ void k_expand_vertices(MfFrame F, MfTraceBufs B, uint64_t e0, uint64_t n);
 __global__ void k_expand_edges(MfFrame F, MfTraceBufs B, uint64_t e0, uint64_t n);
-__global__ void k_cells_enum(MfFrame F, MfTraceBufs B, uint64_t n_edges);
-__global__ void k_scan_tiles(const int64_t *in, int64_t *out, int64_t n, int64_t *tile_tot);
-__global__ void k_scan_totals(int64_t *tile_tot, int64_t ntiles, int64_t *grand);
-__global__ void k_scan_add(int64_t *out, int64_t n, const int64_t *tile_tot);
-
-// Cell -> traced edges for this entry point: the (d+1)d/2 edges of each cell
-// looked up in the edge table (count pass, then fill pass at the scanned
-// offsets).  Same rule as mf_trace's CSR.
-template <bool FILL>
-__global__ void k_noalloc_cell_edges(MfFrame F, MfTraceBufs B, uint64_t n_cells,
-                                     int64_t *cnt_or_off) {
-  const int d = F.d;
-  const uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (c >= n_cells) return;
-  int32_t vi[MF_MAXD];
-  int pi[MF_MAXD];
-  for (int k = 0; k < MF_MAXD; k++) vi[k] = k < d ? B.cell_y[c * d + k] : 0;
-  for (int k = 0; k < d; k++) pi[k] = B.cell_perm[c * d + k];
-  const int64_t pos = FILL ? cnt_or_off[c] : 0;
-  int64_t count = 0;
-  for (int i = 0; i < d; i++) {
-    int32_t vj[MF_MAXD];
-    for (int k = 0; k < MF_MAXD; k++) vj[k] = vi[k];
-    uint32_t mask = 0;
-    for (int j = i + 1; j <= d; j++) {
-      mask |= 1u << pi[j - 1];
-      vj[pi[j - 1]] += 1;
-      const uint64_t slot = mf_table_find<2>(B.etab_key, B.etab_mask, mf_edge_key(F, vi, mask));
-      if (slot == ~0ull) continue;
-      if (FILL) B.cell_idx[pos + count] = (int64_t)mf_etab_val(B, slot);
-      count++;
-    }
-    vi[pi[i]] += 1;
-  }
-  if (!FILL) cnt_or_off[c] = count;
-}
-
 namespace {
 
 const int64_t kScanTile = 512 * 8;
@@ -98,16 +66,67 @@ unsigned char *scratch_base(int dev) {
   return g_scratch_ptr[dev];
 }
 
+// Sequential 256-byte aligned carving of the array.  A take that does not
+// fit marks the carver failed (sticky); the same carve sequence run over a
+// null base with no capacity measures the bytes a request needs, so the size
+// check and the layout cannot diverge.
 struct Carver {
   unsigned char *base;
-  size_t used = 0, cap;
+  size_t used, cap;
+  bool failed;
   void *take(size_t bytes) {
-    size_t a = (used + 255) & ~(size_t)255;
-    if (a + bytes > cap) return nullptr;
+    const size_t a = (used + 255) & ~(size_t)255;
     used = a + bytes;
-    return base + a;
+    if (used > cap) {
+      failed = true;
+      return nullptr;
+    }
+    return base ? base + a : nullptr;
   }
 };
+
+struct NoallocLayout {
+  MfCounters *cnt;
+  MfRbfStats *stats;
+  double *sv64, *exp_tab, *sv64r, *alpha64;
+  float *sv32, *svlo32, *alpha32, *strong32, *svhl, *blo, *bhi;
+  int64_t *scan_tmp;
+};
+
+// Every region of one call, in order; B receives the trace buffers.
+void carve(Carver &cv, int d, size_t nb, uint64_t ME, uint64_t MV, uint64_t MC, uint64_t TE,
+           uint64_t TV, uint64_t cell_edges, NoallocLayout &L, MfTraceBufs &B) {
+  L.cnt = (MfCounters *)cv.take(sizeof(MfCounters));
+  L.stats = (MfRbfStats *)cv.take(sizeof(MfRbfStats));
+  L.sv64 = (double *)cv.take(nb * d * 8);
+  L.sv32 = (float *)cv.take(nb * d * 4);
+  L.svlo32 = (float *)cv.take(nb * d * 4);
+  L.alpha32 = (float *)cv.take(nb * 4);
+  L.strong32 = (float *)cv.take(nb * 4);
+  L.exp_tab = (double *)cv.take(64 * 8);
+  L.sv64r = (double *)cv.take(nb * 64);
+  L.svhl = (float *)cv.take(nb * 64);
+  L.alpha64 = (double *)cv.take(nb * 8);
+  const size_t nblk = (nb + 31) / 32;
+  L.blo = (float *)cv.take(nblk * d * 4);
+  L.bhi = (float *)cv.take(nblk * d * 4);
+  B.etab_key = (unsigned long long *)cv.take(TE * 16);
+  B.vtab_key = (unsigned long long *)cv.take(TV * 16);
+  B.edge_y = (int32_t *)cv.take(ME * d * 4);
+  B.edge_mask = (uint32_t *)cv.take(ME * 4);
+  B.edge_f = (double *)cv.take(ME * 16);
+  B.edge_t = (double *)cv.take(ME * 8);
+  B.edge_pt = (double *)cv.take(ME * d * 8);
+  B.vert_y = (int32_t *)cv.take(MV * d * 4);
+  B.vert_slot = (uint32_t *)cv.take(MV * 4);
+  B.recheck = (uint32_t *)cv.take(MV * 4);
+  B.cell_y = (int32_t *)cv.take(MC * d * 4);
+  B.cell_perm = (uint8_t *)cv.take(MC * d);
+  B.cell_sgn = (uint32_t *)cv.take(MC * 4);
+  B.cell_off = (int64_t *)cv.take((MC + 1) * 8);
+  B.cell_idx = (int64_t *)cv.take(cell_edges * 8);
+  L.scan_tmp = (int64_t *)cv.take((MC / kScanTile + 2) * 8);
+}
 
 uint64_t pow2_at_least(uint64_t x) {
   uint64_t p = 1;
@@ -179,6 +198,9 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   // Capacities: the caller's; a zero leaves the largest default that fits.
   const size_t nb = (size_t)n;
   uint64_t ME = 0, MV = 0, MC = 0, TE = 0, TV = 0, cell_edges = 0;
+  NoallocLayout L;
+  MfTraceBufs B;
+  memset(&B, 0, sizeof(B));
   size_t need = 0;
   for (uint64_t def = 1ull << 17;; def >>= 1) {
     ME = opts->max_edges > 0 ? (uint64_t)opts->max_edges : def;
@@ -187,51 +209,29 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
     TE = pow2_at_least(ME + ME / 3 + 1);
     TV = pow2_at_least(MV + MV / 3 + 1);
     cell_edges = MC * (uint64_t)((d + 1) * d / 2);
-    need = 256 * 38 + 64 * 8 + nb * 136 + ((nb + 31) / 32) * d * 8 + nb * d * 16 + nb * 8 + TE * 16 + TV * 16 + ME * (12 * d + 28) +
-           MV * (4 * d + 8) + MC * (5 * d + 8) + 8 + cell_edges * 8 + (MC / kScanTile + 2) * 8;
+    Carver dry{nullptr, 0, ~(size_t)0, false};
+    carve(dry, d, nb, ME, MV, MC, TE, TV, cell_edges, L, B);
+    need = dry.used;
     if (need <= MF_NOALLOC_SCRATCH_BYTES || def < 1024) break;
   }
   if (ME >= (1ull << 32) || MV >= (1ull << 32) || need > MF_NOALLOC_SCRATCH_BYTES)
     return MF_ERR_OOM;  // the request does not fit the fixed scratch array
-  Carver cv{base, 0, MF_NOALLOC_SCRATCH_BYTES};
-  MfCounters *cnt = (MfCounters *)cv.take(sizeof(MfCounters));
-  MfRbfStats *stats = (MfRbfStats *)cv.take(sizeof(MfRbfStats));
-  double *sv64 = (double *)cv.take(nb * d * 8);
-  float *sv32 = (float *)cv.take(nb * d * 4);
-  float *svlo32 = (float *)cv.take(nb * d * 4);
-  float *alpha32 = (float *)cv.take(nb * 4);
-  float *strong32 = (float *)cv.take(nb * 4);
-  double *exp_tab = (double *)cv.take(64 * 8);
-  double *sv64r = (double *)cv.take(nb * 64);
-  float *svhl = (float *)cv.take(nb * 64);
-  double *alpha64 = (double *)cv.take(nb * 8);
+  Carver cv{base, 0, MF_NOALLOC_SCRATCH_BYTES, false};
+  carve(cv, d, nb, ME, MV, MC, TE, TV, cell_edges, L, B);
+  if (cv.failed) return MF_ERR_OOM;
+  MfCounters *cnt = L.cnt;
+  MfRbfStats *stats = L.stats;
+  double *sv64 = L.sv64, *exp_tab = L.exp_tab, *sv64r = L.sv64r, *alpha64 = L.alpha64;
+  float *sv32 = L.sv32, *svlo32 = L.svlo32, *alpha32 = L.alpha32, *strong32 = L.strong32;
+  float *svhl = L.svhl, *blo = L.blo, *bhi = L.bhi;
+  int64_t *scan_tmp = L.scan_tmp;
   const int nblk = (n + 31) / 32;
-  float *blo = (float *)cv.take((size_t)nblk * d * 4);
-  float *bhi = (float *)cv.take((size_t)nblk * d * 4);
-  MfTraceBufs B;
-  memset(&B, 0, sizeof(B));
-  B.etab_key = (unsigned long long *)cv.take(TE * 16);
-  B.vtab_key = (unsigned long long *)cv.take(TV * 16);
   B.etab_mask = TE - 1;
   B.vtab_mask = TV - 1;
-  B.edge_y = (int32_t *)cv.take(ME * d * 4);
-  B.edge_mask = (uint32_t *)cv.take(ME * 4);
-  B.edge_f = (double *)cv.take(ME * 16);
-  B.edge_t = (double *)cv.take(ME * 8);
-  B.edge_pt = (double *)cv.take(ME * d * 8);
   B.max_edges = ME;
-  B.vert_y = (int32_t *)cv.take(MV * d * 4);
-  B.vert_slot = (uint32_t *)cv.take(MV * 4);
-  B.recheck = (uint32_t *)cv.take(MV * 4);
   B.max_vertices = MV;
-  B.cell_y = (int32_t *)cv.take(MC * d * 4);
-  B.cell_perm = (uint8_t *)cv.take(MC * d);
-  B.cell_off = (int64_t *)cv.take((MC + 1) * 8);
-  B.cell_idx = (int64_t *)cv.take(cell_edges * 8);
   B.max_cells = MC;
   B.cnt = cnt;
-  int64_t *scan_tmp = (int64_t *)cv.take((MC / kScanTile + 2) * 8);
-  if (!scan_tmp) return MF_ERR_OOM;
 
   // Support vectors: the same preparation as mf_trace.
   cudaMemsetAsync(stats, 0, sizeof(MfRbfStats), st);
@@ -318,24 +318,22 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   const uint64_t E = fe;
   if (opts->flags & MF_WANT_ROOTS)
     mf_launch_roots_f64(F, R, B, E, opts->root_tol > 0 ? opts->root_tol : 1e-12, MfTune(), sms,
-                        st);
+                        st, mixed && !(opts->flags & MF_ROOTS_FP64_EXACT));
   int64_t n_cells = 0, n_cell_edges = 0;
   if ((opts->flags & MF_WANT_CELLS) && E > 0) {
-    k_cells_enum<<<(unsigned)((E * 32 + 255) / 256), 256, 0, st>>>(F, B, E);
+    // mf_trace's cell rule: the enumeration writes each cell's sign mask and
+    // CSR row length, the scan turns the lengths into offsets, the fill
+    // looks up the cell's traced edges (a missing one is an error)
+    mf_launch_cells_enum(F, B, E, st);
     if ((rc = sync_read(&h, cnt, st))) return rc;
     n_cells = (int64_t)h.n_cells;
-    const unsigned g = (unsigned)((n_cells + 255) / 256);
-    k_noalloc_cell_edges<false><<<g, 256, 0, st>>>(F, B, (uint64_t)n_cells, B.cell_off);
-    const int64_t ntiles = (n_cells + kScanTile - 1) / kScanTile;
-    k_scan_tiles<<<(unsigned)ntiles, 512, 0, st>>>(B.cell_off, B.cell_off, n_cells, scan_tmp);
-    k_scan_totals<<<1, 512, 0, st>>>(scan_tmp, ntiles, B.cell_off + n_cells);
-    k_scan_add<<<(unsigned)((n_cells + 255) / 256), 256, 0, st>>>(B.cell_off, n_cells, scan_tmp);
+    mf_exclusive_scan(B.cell_off, B.cell_off, n_cells, scan_tmp, st);
     if (cudaMemcpyAsync(&n_cell_edges, B.cell_off + n_cells, 8, cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return MF_ERR_CUDA;
     if ((uint64_t)n_cell_edges > cell_edges) return MF_ERR_MAXEDGES;
-    k_noalloc_cell_edges<true><<<g, 256, 0, st>>>(F, B, (uint64_t)n_cells, B.cell_off);
+    mf_launch_cells_fill(F, B, (uint64_t)n_cells, st);
   }
   if (cudaGetLastError() != cudaSuccess) return MF_ERR_CUDA;
   if ((rc = sync_read(&h, cnt, st))) return rc;

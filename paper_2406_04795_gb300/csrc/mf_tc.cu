@@ -28,7 +28,7 @@
 #include "mf_ctx.h"
 #include "mf_tc_ptx.cuh"
 
-#define TC_M 128
+#define TC_M MF_TC_TILE
 #define TC_K 32
 #define TC_DY_MAX 256
 #define TC_WAIT_NS 2000000000ull  // bounded waits: 2 s
@@ -86,21 +86,198 @@ __device__ __forceinline__ void tc_store_row(unsigned char *tile, int r, const f
   }
 }
 
-template <int D, int N>
-__global__ void __launch_bounds__(TC_M, TcCfg<N>::kCtasPerSm) k_eval_tc(MfFrame F, MfRbfDev R,
-                                                                        MfTraceBufs B, double band) {
-  constexpr int TC_N = N;
-  constexpr uint32_t TC_COLS = TcCfg<N>::kCols;
-  __shared__ TcShared<N> sh;
-  const int t = threadIdx.x, w = t >> 5;
-  const uint64_t begin = B.cnt->v_evaluated;
-  uint64_t end = B.cnt->n_vertices;
-  if (end > B.max_vertices) end = B.max_vertices;
-  if (begin >= end) return;
-  const uint64_t ntiles = (end - begin + TC_M - 1) / TC_M;
-  if (blockIdx.x >= ntiles) return;  // uniform per CTA, before any allocation
+// mbarrier phases and outstanding commits of a CTA's two chunk accumulators;
+// kept across tiles (the barriers live as long as the CTA).
+struct TcPipe {
+  uint32_t phase0 = 0, phase1 = 0;
+  int pending0 = 0, pending1 = 0;  // commits issued and not yet waited for
+};
 
-  if (w == 0) mf_tmem_alloc(&sh.tmem, TC_COLS);
+// One tile: f at the vertices [v_first, v_end) (at most TC_M) of one trace's
+// vertex list, every chunk of support vectors through the MMA; vertices the
+// bound cannot decide go to the trace's FP64 recheck queue.  All threads of
+// the CTA call it; returns false when a bounded wait gave up.
+template <int D, int N>
+__device__ __forceinline__ bool tc_tile(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
+                                        double band, uint64_t v_first, uint64_t v_end,
+                                        TcShared<N> &sh, uint32_t tmem, TcPipe &pp) {
+  constexpr int TC_N = N;
+  const int t = threadIdx.x, w = t >> 5;
+  const uint32_t lane_base = (uint32_t)(32 * w) << 16;
+  const uint32_t idesc = mf_tc_idesc_bf16(TC_M, TC_N);
+  const float g2 = (float)(R.gamma * 1.4426950408889634);
+  const float lam2 = (float)(2.0 * F.lam);
+  const float c32 = (float)F.c;
+  const int nchunks = (R.n + TC_N - 1) / TC_N;
+  const uint64_t v = v_first + t;
+  const bool valid = v < v_end;
+  int32_t y[D];
+#pragma unroll
+  for (int k = 0; k < D; k++) y[k] = valid ? B.vert_y[v * D + k] : 0;
+  if (t == 0) {
+    int32_t ym[MF_MAXD];
+    double q0[MF_MAXD];
+#pragma unroll
+    for (int k = 0; k < MF_MAXD; k++) ym[k] = k < D ? y[k] : 0;
+    mf_vertex_x(F, ym, q0);
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+      sh.y0[k] = y[k];
+      sh.q0hi[k] = (float)q0[k];
+      sh.q0lo[k] = (float)(q0[k] - (double)sh.q0hi[k]);
+    }
+  }
+  __syncthreads();
+  // this vertex relative to the tile base
+  int32_t dy[D];
+  bool far = false;
+  long long sdy = 0;
+  double dyn2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; k++) {
+    dy[k] = valid ? y[k] - sh.y0[k] : 0;
+    far = far || dy[k] > TC_DY_MAX || dy[k] < -TC_DY_MAX;
+    sdy += dy[k];
+    dyn2 += (double)dy[k] * (double)dy[k];
+  }
+  double qq = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; k++) {
+    const double l = (double)dy[k] - F.c * (double)sdy;
+    qq = fma(l, l, qq);
+  }
+  qq *= F.lam * F.lam;
+  {
+    float row[TC_K];
+#pragma unroll
+    for (int c = 0; c < TC_K; c++) {
+      float val = 0.f;
+      if (c < 3 * D) val = far ? 0.f : (float)dy[c % D];
+      else if (c < 3 * D + 3) val = 1.f;
+      row[c] = val;
+    }
+    tc_store_row(sh.a, t, row);
+  }
+  const float kq = -g2 * (float)qq;
+  float acc = 0.f, aab = 0.f, qa = 0.f;
+  bool ok = true;
+
+  for (int c = 0; c <= nchunks; c++) {
+    const int buf = c & 1;
+    if (c < nchunks) {
+      if (t < TC_N) {
+        // row t of chunk c: support vector j
+        const int j = c * TC_N + t;
+        float row[TC_K];
+#pragma unroll
+        for (int k = 0; k < TC_K; k++) row[k] = 0.f;
+        float al = 0.f;
+        if (j < R.n) {
+          float u[D], su = 0.f, cc = 0.f;
+#pragma unroll
+          for (int k = 0; k < D; k++) {
+            u[k] = (sh.q0hi[k] - R.sv32[(int64_t)k * R.n + j]) +
+                   (sh.q0lo[k] - R.svlo32[(int64_t)k * R.n + j]);
+            su += u[k];
+            cc = fmaf(u[k], u[k], cc);
+          }
+          const float cs = c32 * su;
+#pragma unroll
+          for (int k = 0; k < D; k++) {
+            float h, m, l;
+            tc_split3(lam2 * (u[k] - cs), h, m, l);
+            row[k] = h;
+            row[D + k] = m;
+            row[2 * D + k] = l;
+          }
+          float h, m, l;
+          tc_split3(cc, h, m, l);
+          row[3 * D] = h;
+          row[3 * D + 1] = m;
+          row[3 * D + 2] = l;
+          al = R.alpha32[j];
+        }
+        tc_store_row(sh.b[buf], t, row);
+        sh.alpha[buf][t] = al;
+      }
+      mf_fence_proxy_async_smem();
+      mf_tc_fence_before();
+      __syncthreads();
+      if (t == 0) {
+        mf_tc_fence_after();
+        const uint32_t a0 = mf_smem_u32(sh.a), b0 = mf_smem_u32(sh.b[buf]);
+        const uint32_t dcol = tmem + (uint32_t)(buf * TC_N);
+        mf_tc_mma_bf16(dcol, mf_tc_desc(a0, 128, 512), mf_tc_desc(b0, 128, 512), idesc, 0u);
+        mf_tc_mma_bf16(dcol, mf_tc_desc(a0 + 256, 128, 512), mf_tc_desc(b0 + 256, 128, 512), idesc,
+                       1u);
+        mf_tc_commit(&sh.bar[buf]);
+      }
+      if (buf) pp.pending1 = 1; else pp.pending0 = 1;
+    }
+    if (c > 0) {
+      const int pb = buf ^ 1;  // chunk c - 1
+      const bool got = mf_mbar_wait(&sh.bar[pb], pb ? pp.phase1 : pp.phase0, TC_WAIT_NS);
+      if (pb) { pp.phase1 ^= 1u; pp.pending1 = 0; } else { pp.phase0 ^= 1u; pp.pending0 = 0; }
+      if (!got) sh.timeout = 1;
+      mf_tc_fence_after();
+#pragma unroll
+      for (int h = 0; h < TC_N / 32; h++) {
+        float dv[32];
+        mf_tmem_ld32(tmem + lane_base + (uint32_t)(pb * TC_N + 32 * h), dv);
+        float part = 0.f;
+#pragma unroll
+        for (int i = 0; i < 32; i++) {
+          const float arg = fmaf(dv[i], -g2, kq);
+          const float term = sh.alpha[pb][32 * h + i] * tc_ex2(arg);
+          part += term;
+          aab += fabsf(term);
+          qa = fmaf(fabsf(term), fabsf(arg), qa);
+        }
+        acc += part;
+      }
+      mf_tc_fence_before();
+    }
+    __syncthreads();
+    if (sh.timeout) {
+      ok = false;
+      break;
+    }
+  }
+  if (!ok) return false;
+
+  if (valid) {
+    // |f~ - f| bound (u = 2^-24): MMA accumulation and operand rounding
+    // scale with |dy| |w| and |u|^2, which are bounded through r and qq
+    // (|u| <= r + sqrt(qq)); exponent rounding through sum |t| |arg|; ex2,
+    // products and the blocked FP32 sums through sum |t|.
+    const double u = 5.9604644775390625e-08;
+    const double A = (double)aab, Qa = (double)qa;
+    const double Q = 1.01 * Qa / (double)g2 + 1e-300;  // sum |t| r^2
+    const double a1 = 80.0 * 2.0 * F.lam * sqrt(dyn2);
+    const double a2 = 72.0 + D;
+    const double coord = R.gamma * u *
+                         (a1 * sqrt(A * Q) + (a1 * sqrt(qq) + (2.0 * a2 + 1.0) * qq) * A + 2.0 * a2 * Q);
+    const double expo = 3.0 * 0.6931471805599453 * u * Qa;
+    const double other = (9.5367431640625e-07 + (34.0 + 2.0 * nchunks) * u) * A;
+    const double bound = 1.05 * (coord + expo + other) + 1e-30 + R.sum_abs_alpha * 1.2e-38;
+    const double fx = (double)acc + R.b;
+    const uint32_t slot = B.vert_slot[v];
+    mf_vtab_f(B, slot) = fx;
+    if (far || fabs(fx) <= fmax(bound, band)) {
+      const unsigned long long q = atomicAdd(&B.cnt->n_recheck, 1ull);
+      if (q < B.max_vertices) B.recheck[q] = (uint32_t)v;
+      else atomicOr(&B.cnt->err_overflow, 1u);
+    }
+  }
+  __syncthreads();  // the next tile rewrites A and the tile base
+  return true;
+}
+
+// TMEM columns and barriers of a CTA: allocated once, used by every tile.
+template <int N>
+__device__ __forceinline__ void tc_begin(TcShared<N> &sh) {
+  const int t = threadIdx.x, w = t >> 5;
+  if (w == 0) mf_tmem_alloc(&sh.tmem, TcCfg<N>::kCols);
   if (t == 0) {
     mf_mbar_init(&sh.bar[0], 1);
     mf_mbar_init(&sh.bar[1], 1);
@@ -110,193 +287,76 @@ __global__ void __launch_bounds__(TC_M, TcCfg<N>::kCtasPerSm) k_eval_tc(MfFrame 
   mf_tc_fence_before();
   __syncthreads();
   mf_tc_fence_after();
-  const uint32_t tmem = sh.tmem;
-  const uint32_t lane_base = (uint32_t)(32 * w) << 16;
-  const uint32_t idesc = mf_tc_idesc_bf16(TC_M, TC_N);
-  const float g2 = (float)(R.gamma * 1.4426950408889634);
-  const float lam2 = (float)(2.0 * F.lam);
-  const float c32 = (float)F.c;
-  const int nchunks = (R.n + TC_N - 1) / TC_N;
-  uint32_t phase0 = 0, phase1 = 0;
-  int pending0 = 0, pending1 = 0;  // commits issued and not yet waited for
-  bool ok = true;
+}
 
-  for (uint64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    const uint64_t v = begin + tile * TC_M + t;
-    const bool valid = v < end;
-    int32_t y[D];
-#pragma unroll
-    for (int k = 0; k < D; k++) y[k] = valid ? B.vert_y[v * D + k] : 0;
-    if (t == 0) {
-      int32_t ym[MF_MAXD];
-      double q0[MF_MAXD];
-#pragma unroll
-      for (int k = 0; k < MF_MAXD; k++) ym[k] = k < D ? y[k] : 0;
-      mf_vertex_x(F, ym, q0);
-#pragma unroll
-      for (int k = 0; k < D; k++) {
-        sh.y0[k] = y[k];
-        sh.q0hi[k] = (float)q0[k];
-        sh.q0lo[k] = (float)(q0[k] - (double)sh.q0hi[k]);
-      }
-    }
-    __syncthreads();
-    // this vertex relative to the tile base
-    int32_t dy[D];
-    bool far = false;
-    long long sdy = 0;
-    double dyn2 = 0.0;
-#pragma unroll
-    for (int k = 0; k < D; k++) {
-      dy[k] = valid ? y[k] - sh.y0[k] : 0;
-      far = far || dy[k] > TC_DY_MAX || dy[k] < -TC_DY_MAX;
-      sdy += dy[k];
-      dyn2 += (double)dy[k] * (double)dy[k];
-    }
-    double qq = 0.0;
-#pragma unroll
-    for (int k = 0; k < D; k++) {
-      const double l = (double)dy[k] - F.c * (double)sdy;
-      qq = fma(l, l, qq);
-    }
-    qq *= F.lam * F.lam;
-    {
-      float row[TC_K];
-#pragma unroll
-      for (int c = 0; c < TC_K; c++) {
-        float val = 0.f;
-        if (c < 3 * D) val = far ? 0.f : (float)dy[c % D];
-        else if (c < 3 * D + 3) val = 1.f;
-        row[c] = val;
-      }
-      tc_store_row(sh.a, t, row);
-    }
-    const float kq = -g2 * (float)qq;
-    float acc = 0.f, aab = 0.f, qa = 0.f;
-
-    for (int c = 0; c <= nchunks; c++) {
-      const int buf = c & 1;
-      if (c < nchunks) {
-        if (t < TC_N) {
-          // row t of chunk c: support vector j
-          const int j = c * TC_N + t;
-          float row[TC_K];
-#pragma unroll
-          for (int k = 0; k < TC_K; k++) row[k] = 0.f;
-          float al = 0.f;
-          if (j < R.n) {
-            float u[D], su = 0.f, cc = 0.f;
-#pragma unroll
-            for (int k = 0; k < D; k++) {
-              u[k] = (sh.q0hi[k] - R.sv32[(int64_t)k * R.n + j]) +
-                     (sh.q0lo[k] - R.svlo32[(int64_t)k * R.n + j]);
-              su += u[k];
-              cc = fmaf(u[k], u[k], cc);
-            }
-            const float cs = c32 * su;
-#pragma unroll
-            for (int k = 0; k < D; k++) {
-              float h, m, l;
-              tc_split3(lam2 * (u[k] - cs), h, m, l);
-              row[k] = h;
-              row[D + k] = m;
-              row[2 * D + k] = l;
-            }
-            float h, m, l;
-            tc_split3(cc, h, m, l);
-            row[3 * D] = h;
-            row[3 * D + 1] = m;
-            row[3 * D + 2] = l;
-            al = R.alpha32[j];
-          }
-          tc_store_row(sh.b[buf], t, row);
-          sh.alpha[buf][t] = al;
-        }
-        mf_fence_proxy_async_smem();
-        mf_tc_fence_before();
-        __syncthreads();
-        if (t == 0) {
-          mf_tc_fence_after();
-          const uint32_t a0 = mf_smem_u32(sh.a), b0 = mf_smem_u32(sh.b[buf]);
-          const uint32_t dcol = tmem + (uint32_t)(buf * TC_N);
-          mf_tc_mma_bf16(dcol, mf_tc_desc(a0, 128, 512), mf_tc_desc(b0, 128, 512), idesc, 0u);
-          mf_tc_mma_bf16(dcol, mf_tc_desc(a0 + 256, 128, 512), mf_tc_desc(b0 + 256, 128, 512), idesc,
-                         1u);
-          mf_tc_commit(&sh.bar[buf]);
-        }
-        if (buf) pending1 = 1; else pending0 = 1;
-      }
-      if (c > 0) {
-        const int pb = buf ^ 1;  // chunk c - 1
-        const bool got = mf_mbar_wait(&sh.bar[pb], pb ? phase1 : phase0, TC_WAIT_NS);
-        if (pb) { phase1 ^= 1u; pending1 = 0; } else { phase0 ^= 1u; pending0 = 0; }
-        if (!got) sh.timeout = 1;
-        mf_tc_fence_after();
-#pragma unroll
-        for (int h = 0; h < TC_N / 32; h++) {
-          float dv[32];
-          mf_tmem_ld32(tmem + lane_base + (uint32_t)(pb * TC_N + 32 * h), dv);
-          float part = 0.f;
-#pragma unroll
-          for (int i = 0; i < 32; i++) {
-            const float arg = fmaf(dv[i], -g2, kq);
-            const float term = sh.alpha[pb][32 * h + i] * tc_ex2(arg);
-            part += term;
-            aab += fabsf(term);
-            qa = fmaf(fabsf(term), fabsf(arg), qa);
-          }
-          acc += part;
-        }
-        mf_tc_fence_before();
-      }
-      __syncthreads();
-      if (sh.timeout) {
-        ok = false;
-        break;
-      }
-    }
-    if (!ok) break;
-
-    if (valid) {
-      // |f~ - f| bound (u = 2^-24): MMA accumulation and operand rounding
-      // scale with |dy| |w| and |u|^2, which are bounded through r and qq
-      // (|u| <= r + sqrt(qq)); exponent rounding through sum |t| |arg|; ex2,
-      // products and the blocked FP32 sums through sum |t|.
-      const double u = 5.9604644775390625e-08;
-      const double A = (double)aab, Qa = (double)qa;
-      const double Q = 1.01 * Qa / (double)g2 + 1e-300;  // sum |t| r^2
-      const double a1 = 80.0 * 2.0 * F.lam * sqrt(dyn2);
-      const double a2 = 72.0 + D;
-      const double coord = R.gamma * u *
-                           (a1 * sqrt(A * Q) + (a1 * sqrt(qq) + (2.0 * a2 + 1.0) * qq) * A + 2.0 * a2 * Q);
-      const double expo = 3.0 * 0.6931471805599453 * u * Qa;
-      const double other = (9.5367431640625e-07 + (34.0 + 2.0 * nchunks) * u) * A;
-      const double bound = 1.05 * (coord + expo + other) + 1e-30 + R.sum_abs_alpha * 1.2e-38;
-      const double fx = (double)acc + R.b;
-      const uint32_t slot = B.vert_slot[v];
-      mf_vtab_f(B, slot) = fx;
-      if (far || fabs(fx) <= fmax(bound, band)) {
-        const unsigned long long q = atomicAdd(&B.cnt->n_recheck, 1ull);
-        if (q < B.max_vertices) B.recheck[q] = (uint32_t)v;
-        else atomicOr(&B.cnt->err_overflow, 1u);
-      }
-    }
-    __syncthreads();  // the next tile rewrites A and the tile base
-  }
-
+// After a wait gave up (ok false): flags it, gives in-flight MMAs a bounded
+// chance to finish, then frees the columns.
+template <int N>
+__device__ __forceinline__ void tc_end(TcShared<N> &sh, TcPipe &pp, bool ok, MfCounters *cnt) {
+  const int t = threadIdx.x, w = t >> 5;
   if (!ok) {
-    // a wait gave up: flag it, then give in-flight MMAs a bounded chance to
-    // finish before the columns are freed
-    if (t == 0) atomicOr(&B.cnt->err_timeout, 1u);
-    if (pending0) mf_mbar_wait(&sh.bar[0], phase0, TC_WAIT_NS);
-    if (pending1) mf_mbar_wait(&sh.bar[1], phase1, TC_WAIT_NS);
+    if (t == 0) atomicOr(&cnt->err_timeout, 1u);
+    if (pp.pending0) mf_mbar_wait(&sh.bar[0], pp.phase0, TC_WAIT_NS);
+    if (pp.pending1) mf_mbar_wait(&sh.bar[1], pp.phase1, TC_WAIT_NS);
   }
   mf_tc_fence_before();
   __syncthreads();
   if (w == 0) {
     mf_tc_fence_after();
-    mf_tmem_dealloc(tmem, TC_COLS);
+    mf_tmem_dealloc(sh.tmem, TcCfg<N>::kCols);
   }
+}
+
+template <int D, int N>
+__global__ void __launch_bounds__(TC_M, TcCfg<N>::kCtasPerSm) k_eval_tc(MfFrame F, MfRbfDev R,
+                                                                        MfTraceBufs B, double band) {
+  __shared__ TcShared<N> sh;
+  const uint64_t begin = B.cnt->v_evaluated;
+  uint64_t end = B.cnt->n_vertices;
+  if (end > B.max_vertices) end = B.max_vertices;
+  if (begin >= end) return;
+  const uint64_t ntiles = (end - begin + TC_M - 1) / TC_M;
+  if (blockIdx.x >= ntiles) return;  // uniform per CTA, before any allocation
+  tc_begin<N>(sh);
+  TcPipe pp;
+  bool ok = true;
+  for (uint64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const uint64_t v0 = begin + tile * TC_M;
+    ok = tc_tile<D, N>(F, R, B, band, v0, v0 + TC_M < end ? v0 + TC_M : end, sh, sh.tmem, pp);
+  }
+  tc_end<N>(sh, pp, ok, B.cnt);
+}
+
+// Batched form: the tiles of every MF_MIXED_BF16 slot of a batch (the plan's
+// pt prefix; a tile never spans two traces), each with its trace's frame,
+// support vectors and tables.
+template <int N>
+__global__ void __launch_bounds__(TC_M, TcCfg<N>::kCtasPerSm) k_b_eval_tc(const MfSlot *slots,
+                                                                          const MfBatchPlan *P,
+                                                                          int n) {
+  __shared__ TcShared<N> sh;
+  const unsigned long long ntiles = P->pt[n];
+  if (blockIdx.x >= ntiles) return;  // uniform per CTA, before any allocation
+  tc_begin<N>(sh);
+  TcPipe pp;
+  bool ok = true;
+  MfCounters *last = nullptr;
+  for (unsigned long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int s = mf_slot_of(P->pt, n, tile);
+    const MfSlot &S = slots[s];
+    last = S.B.cnt;
+    const uint64_t end = P->v0[s] + (P->pv[s + 1] - P->pv[s]);
+    const uint64_t v0 = P->v0[s] + (tile - P->pt[s]) * TC_M;
+    const uint64_t v1 = v0 + TC_M < end ? v0 + TC_M : end;
+    switch (S.F.d) {
+#define MF_CASE(DD) \
+  case DD: ok = tc_tile<DD, N>(S.F, S.R, S.B, S.band, v0, v1, sh, sh.tmem, pp); break;
+      MF_CASE(2) MF_CASE(3) MF_CASE(4) MF_CASE(5) MF_CASE(6) MF_CASE(7) MF_CASE(8)
+#undef MF_CASE
+      default: break;
+    }
+  }
+  tc_end<N>(sh, pp, ok, last);
 }
 
 // Vertex evaluation on the tensor cores with chunk width n_chunk (64 or
@@ -324,4 +384,17 @@ void mf_launch_eval_vertices_tc(const MfFrame &F, const MfRbfDev &R, const MfTra
                                 double band, int n_chunk, int sms, cudaStream_t st) {
   if (n_chunk == 128) launch_tc<128>(F, R, B, band, sms, st);
   else launch_tc<64>(F, R, B, band, sms, st);
+}
+
+void mf_b_launch_eval_tc(const MfSlot *slots, const MfBatchPlan *P, int n, int n_chunk, int sms,
+                         cudaStream_t st) {
+  if (n_chunk == 128) {
+    const size_t dyn = TcCfg<128>::kSmemPerCta - sizeof(TcShared<128>);
+    cudaFuncSetAttribute(k_b_eval_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    k_b_eval_tc<128><<<sms * TcCfg<128>::kCtasPerSm, TC_M, dyn, st>>>(slots, P, n);
+  } else {
+    const size_t dyn = TcCfg<64>::kSmemPerCta - sizeof(TcShared<64>);
+    cudaFuncSetAttribute(k_b_eval_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    k_b_eval_tc<64><<<sms * TcCfg<64>::kCtasPerSm, TC_M, dyn, st>>>(slots, P, n);
+  }
 }

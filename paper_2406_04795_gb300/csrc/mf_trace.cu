@@ -103,6 +103,18 @@ __global__ void k_seed_vertices(MfFrame F, MfTraceBufs B, const double *seeds, i
   int32_t v[MF_MAXD];
   int perm[MF_MAXD];
   mf_locate_point(F, x, v, perm);
+  // f is needed at the vertices of the simplex's in-box edges: none when
+  // fewer than two of its vertices lie in the box
+  int n_in = 0;
+  {
+    int32_t u[MF_MAXD];
+    for (int k = 0; k < MF_MAXD; k++) u[k] = v[k];
+    for (int j = 0; j <= d; j++) {
+      n_in += vertex_in(F, u) ? 1 : 0;
+      if (j < d) u[perm[j]] += 1;
+    }
+  }
+  if (n_in < 2) return;
   for (int j = 0; j <= d; j++) {
     if (vertex_in(F, v)) visit_vertex(F, B, v);
     if (j < d) v[perm[j]] += 1;
@@ -582,7 +594,7 @@ __global__ void k_b_init(const MfSlot *slots, MfSlotState *st, int n) {
   s.cursor = 0;
   s.level_end = c->n_edges < slots[t].B.max_edges ? c->n_edges : slots[t].B.max_edges;
   s.chunk_n = 0;
-  s.err = (c->err_table_full || c->err_missing || c->err_overflow) ? 1 : 0;
+  s.err = (c->err_table_full || c->err_missing || c->err_overflow || c->err_timeout) ? 1 : 0;
   s.active = (s.level_end > 0 && !s.err) ? 1 : 0;
   s.levels = s.level_end > 0 ? 1 : 0;
   s.pad = 0;
@@ -650,22 +662,31 @@ __global__ void __launch_bounds__(EXPAND_WARPS * 32) k_b_expand(const MfSlot *sl
   }
 }
 
-// Vertex-evaluation and FP64-recheck ranges of every slot.
+// Vertex-evaluation and FP64-recheck ranges of every slot, and the
+// tensor-core tiles of the MF_MIXED_BF16 slots.
 __global__ void k_b_plan_eval(const MfSlot *slots, MfBatchPlan *P, int n) {
-  __shared__ unsigned long long total;
+  __shared__ unsigned long long total, ttotal;
   const int t = threadIdx.x;
-  unsigned long long cv = 0;
+  unsigned long long cv = 0, ct = 0;
   if (t < n && slots[t].B.cnt) {  // empty (zeroed) descriptors hold no trace
     const MfTraceBufs &B = slots[t].B;
     const unsigned long long v0 = B.cnt->v_evaluated;
     unsigned long long v1 = B.cnt->n_vertices;
     if (v1 > B.max_vertices) v1 = B.max_vertices;
     cv = v1 > v0 ? v1 - v0 : 0;
+    if (slots[t].precision == MF_MIXED_BF16) ct = (cv + MF_TC_TILE - 1) / MF_TC_TILE;
     P->v0[t] = v0;
   }
-  unsigned long long ex = block_scan_u64(cv, &total);
-  if (t < n) P->pv[t] = ex;
-  if (t == 0) P->pv[n] = total;
+  const unsigned long long ex = block_scan_u64(cv, &total);
+  const unsigned long long et = block_scan_u64(ct, &ttotal);
+  if (t < n) {
+    P->pv[t] = ex;
+    P->pt[t] = et;
+  }
+  if (t == 0) {
+    P->pv[n] = total;
+    P->pt[n] = ttotal;
+  }
 }
 
 __global__ void k_b_plan_recheck(const MfSlot *slots, MfBatchPlan *P, int n) {
@@ -721,7 +742,8 @@ __global__ void k_b_update(const MfSlot *slots, MfSlotState *st, MfBatchPlan *P,
     if (s.cursor >= s.level_end) {
       const MfCounters *c = slots[t].B.cnt;
       const unsigned long long ne = c->n_edges;
-      if (c->err_table_full || c->err_missing || c->err_overflow || ne > slots[t].B.max_edges) {
+      if (c->err_table_full || c->err_missing || c->err_overflow || c->err_timeout ||
+          ne > slots[t].B.max_edges) {
         s.err = 1;
         s.active = 0;
       } else if (ne > s.level_end) {
@@ -1047,6 +1069,14 @@ void mf_exclusive_scan(const int64_t *in, int64_t *out, int64_t n, int64_t *scra
   exclusive_scan(in, out, n, scratch, st);
 }
 uint64_t mf_next_pow2(uint64_t x) { return next_pow2(x); }
+void mf_launch_cells_fill(const MfFrame &F, const MfTraceBufs &B, uint64_t n_cells, cudaStream_t st) {
+  if (n_cells == 0) return;
+  k_cells_edges<true><<<(unsigned)((n_cells + 255) / 256), 256, 0, st>>>(F, B, n_cells, B.cell_off);
+}
+void mf_launch_cells_enum(const MfFrame &F, const MfTraceBufs &B, uint64_t n_edges, cudaStream_t st) {
+  if (n_edges == 0) return;
+  k_cells_enum<<<(unsigned)((n_edges * 32 + 255) / 256), 256, 0, st>>>(F, B, n_edges);
+}
 void mf_launch_seeds(const MfFrame &F, const MfTraceBufs &B, const double *seeds, int64_t n,
                      bool vertices, cudaStream_t s) {
   const unsigned g = (unsigned)((n + 127) / 128);
@@ -1119,9 +1149,9 @@ static int setup_buffers(mf_ctx *ctx, int d, uint64_t ME, uint64_t MV, uint64_t 
   B->max_cells = MC;
   B->cnt = (MfCounters *)mf_ctx_buffer(ctx, MF_SLOT_COUNTERS, sizeof(MfCounters));
   if (!B->cnt) return MF_ERR_OOM;
-  // FP64 path: per-vertex lists for the root screen, when they fit the
-  // budget (else the root screen scans the vector blocks)
-  if (!mixed && n_sv > 0) {
+  // per-vertex lists for the root screen, when they fit the budget (else
+  // the root screen scans the vector blocks)
+  if (n_sv > 0) {
     const uint64_t per = (uint64_t)std::min(n_sv, 192);
     const uint64_t cap = MV * per;
     const size_t lb = al(TV * 4) + al(MV * 8) + al(MV * 4) + al(cap * 4);
@@ -1228,15 +1258,7 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
   MfTraceBufs B;
   rc = setup_buffers(ctx, d, ME, MV, MC, mixed, (int)rbf->n_sv, &B);
   if (rc) return rc;
-  if (B.vlist) {
-    // list radius: the screen radius around any point of an edge from the
-    // vertex; the longest edge is lam |L e(M)|, |L e(M)|^2 = k (1 - 2ck + c^2 k d)
-    // for |M| = k; margins cover the FP32 distances of both screens
-    double m2 = 0.0;
-    for (int k = 1; k <= d; k++) m2 = std::max(m2, k * (1.0 - 2.0 * F.c * k + F.c * F.c * k * d));
-    const double rl = std::sqrt((double)R.screen_r2) * 1.0001 + opts->lambda * std::sqrt(m2) + 1e-4;
-    B.list_r2 = (float)(rl * rl);
-  }
+  if (B.vlist) B.list_r2 = mf_list_r2(F, R);
   uint64_t cap = opts->batch_cap_edges > 0 ? (uint64_t)opts->batch_cap_edges : (1ull << 24);
   if (ctx->tune.frontier_chunk > 0 && ctx->tune.frontier_chunk < cap) cap = ctx->tune.frontier_chunk;
   const double band = opts->recheck_band > 0 ? opts->recheck_band : 1e-3;
@@ -1255,7 +1277,7 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
   // Locate edges (Fig. 3)
   if (n_seeds > 0) {
     const unsigned g = (unsigned)((n_seeds + 127) / 128);
-    MfProfScope ps(ctx, MF_PH_SEEDS, st, mixed ? 5 : 4, n_seeds);
+    MfProfScope ps(ctx, MF_PH_SEEDS, st, mixed ? (B.vlist ? 6 : 5) : 4, n_seeds);
     k_seed_vertices<<<g, 128, 0, st>>>(F, B, seeds, n_seeds);
     eval();
     k_seed_edges<<<g, 128, 0, st>>>(F, B, seeds, n_seeds);
@@ -1277,7 +1299,7 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
         k_expand_vertices<<<g, EXPAND_WARPS * 32, 0, st>>>(F, B, a, n);
       }
       {
-        MfProfScope ps(ctx, MF_PH_EVAL, st, mixed ? 3 : 2);
+        MfProfScope ps(ctx, MF_PH_EVAL, st, mixed ? (B.vlist ? 4 : 3) : 2);
         eval();
       }
       {
@@ -1298,7 +1320,8 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
   // Roots (the iterative intersection solve of Sec. VI), FP64 Newton.
   if (opts->flags & MF_WANT_ROOTS) {
     MfProfScope ps(ctx, MF_PH_ROOTS, st, E > 0 ? 1 : 0, (int64_t)E);
-    mf_launch_roots_f64(F, R, B, E, tol, ctx->tune, sms, st);
+    mf_launch_roots_f64(F, R, B, E, tol, ctx->tune, sms, st,
+                        mixed && !(opts->flags & MF_ROOTS_FP64_EXACT));
   }
 
   // Cells (Sec. IV-C) and the cell -> edge CSR.

@@ -153,7 +153,10 @@ extern "C" int mf_autotune(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
           t.roots_bps = bps[g];
           t.roots_group = groups[q];
           const float ms = time_ms(
-              st, [&]() { mf_launch_roots_f64(L.F, L.R, L.B, es, L.tol, t, sms, st); }, 3);
+              st, [&]() {
+                mf_launch_roots_f64(L.F, L.R, L.B, es, L.tol, t, sms, st,
+                                    L.precision != MF_FP64 && !(L.flags & MF_ROOTS_FP64_EXACT));
+              }, 3);
           n_cand++;
           if (ms < best_roots) {
             best_roots = ms;

@@ -27,6 +27,7 @@ MF_MIXED_FP32 = 2
 
 MF_WANT_ROOTS = 1
 MF_WANT_CELLS = 2
+MF_ROOTS_FP64_EXACT = 4
 
 MF_BOX = 0
 MF_SPHERE = 1
@@ -36,7 +37,7 @@ EXPORTS = ("mf_ctx_create", "mf_ctx_destroy", "mf_last_error", "mf_ctx_bytes", "
            "mf_ctx_get_stats", "mf_trace_noalloc", "mf_trace_batch", "mf_domain_table",
            "mf_server_create", "mf_server_destroy", "mf_server_submit", "mf_server_step",
            "mf_server_status", "mf_server_fetch", "mf_server_done", "mf_autotune", "mf_ctx_set_tune",
-           "mf_ctx_get_tune", "mf_vertex_keys")
+           "mf_ctx_get_tune", "mf_vertex_keys", "mf_probe_rates", "mf_diag_exp")
 
 MF_PHASES = 12
 PHASE_NAMES = ("prepare", "seeds", "expand_vertices", "eval", "expand_edges", "roots", "cells",
@@ -85,6 +86,15 @@ class mf_stats(C.Structure):
     _fields_ = [("ms", C.c_double * MF_PHASES), ("launches", C.c_int64 * MF_PHASES),
                 ("units", C.c_int64 * MF_PHASES), ("terms", C.c_int64 * MF_PHASES),
                 ("terms_weak", C.c_int64 * MF_PHASES)]
+
+
+class mf_rates(C.Structure):
+    _fields_ = [("fp64_fma_per_s", C.c_double), ("fp32_fma_per_s", C.c_double),
+                ("ex2_per_s", C.c_double), ("exp_neg_per_s", C.c_double),
+                ("sm_count", C.c_int32), ("sm_clock_mhz", C.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class mf_tune(C.Structure):
@@ -175,6 +185,10 @@ def load(build_if_missing: bool = True):
     L.mf_trace_noalloc.restype = C.c_int
     L.mf_trace_noalloc.argtypes = [P(mf_rbf), P(mf_domain), P(mf_trace_opts), V, C.c_int64,
                                    P(mf_trace_out), V]
+    L.mf_probe_rates.restype = C.c_int
+    L.mf_probe_rates.argtypes = [V, P(mf_rates), V]
+    L.mf_diag_exp.restype = C.c_int
+    L.mf_diag_exp.argtypes = [V, V, C.c_int64, V, V, V]
     _lib = L
     return L
 
@@ -339,6 +353,16 @@ def mf_autotune(ctx, rbf: mf_rbf, dom: mf_domain, opts: mf_trace_opts, seeds_ptr
     _check(ctx, load().mf_autotune(ctx, C.byref(rbf), C.byref(dom), C.byref(opts), seeds_ptr,
                                    n_seeds, C.byref(t), stream))
     return t
+
+
+def mf_probe_rates(ctx, stream=0) -> mf_rates:
+    r = mf_rates()
+    _check(ctx, load().mf_probe_rates(ctx, C.byref(r), stream))
+    return r
+
+
+def mf_diag_exp(ctx, x_ptr, n, y_table_ptr, y_lib_ptr, stream=0):
+    return _check(ctx, load().mf_diag_exp(ctx, x_ptr, n, y_table_ptr, y_lib_ptr, stream))
 
 
 def mf_ctx_set_tune(ctx, t):

@@ -178,3 +178,31 @@ def test_fullsize_certify_sampled(full):
     sure = np.abs(mo) > 1e-12
     assert np.array_equal(vg[sure], vo[sure])
     assert np.max(np.abs(mg - mo)) <= 1e-9
+
+
+def test_fullsize_cell_verdicts_sampled(full):
+    """Sampled cells: the cell verdict is the AND of its points' verdicts,
+    each point's verdict recomputed by the oracle (cells with a point whose
+    |margin| <= 1e-12 are skipped: its verdict is not pinned)."""
+    w, r = full["w"], full["r"]
+    nc = r["n_cells"]
+    idx = np.sort(full["rng"].choice(nc, 400, replace=False))
+    off = r["cell_off"]
+    lo_hi = torch.stack([off[idx], off[idx + 1]], 1).cpu().numpy()
+    rows = [r["cell_idx"][int(a):int(b)].cpu().numpy() for a, b in lo_hi]
+    allp = np.unique(np.concatenate([x for x in rows if x.size] or [np.zeros(0, np.int64)]))
+    pts = r["points"][torch.as_tensor(allp, device=r["points"].device)].cpu().numpy()
+    vo, mo, _ = oracle.certify(w.dh, w.radius, w.obs_type, w.obs_pose, w.obs_dims, pts)
+    pos = {int(p): i for i, p in enumerate(allp)}
+    cv = full["cv"][torch.as_tensor(idx, device=full["cv"].device)].cpu().numpy()
+    checked = both = 0
+    for c, row in enumerate(rows):
+        if row.size == 0:
+            continue
+        k = np.array([pos[int(e)] for e in row])
+        if np.any(np.abs(mo[k]) <= 1e-12):
+            continue
+        assert int(cv[c]) == int(np.all(vo[k] == 1)), c
+        checked += 1
+        both += int(cv[c])
+    assert checked > 300 and 0 < both < checked

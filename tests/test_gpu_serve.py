@@ -22,7 +22,7 @@ def ctx():
 def test_server_results_equal_alone_under_queueing(ctx):
     ws = W.config_batched(n_traces=5, lam_scale=3.0) + [W.config_d3()]
     ws += W.config_batched(seed=77, n_traces=3, lam_scale=3.5)
-    precs = [mf.MF_MIXED_FP32 if i % 2 == 0 else mf.MF_FP64 for i in range(len(ws))]
+    precs = [(mf.MF_MIXED_FP32, mf.MF_FP64, mf.MF_MIXED_BF16)[i % 3] for i in range(len(ws))]
     server = ctx.server(max_slots=3, hbm_bytes=24 << 30)
     ids, got, saw_queue, steps = [], {}, False, 0
     pending = list(range(len(ws)))
@@ -51,7 +51,9 @@ def test_server_results_equal_alone_under_queueing(ctx):
         alone = ctx.trace(w.sv, w.alpha, w.gamma, w.b, w.lam, w.offset, w.lo, w.hi, w.seeds,
                           precision=precs[k], **W.shell_capacity(w))
         assert got[rid]["n_edges"] > 10
-        _same(_np(got[rid]), _np(alone), f_tol=1e-12 if precs[k] == mf.MF_FP64 else 1e-3)
+        fp64 = precs[k] == mf.MF_FP64
+        _same(_np(got[rid]), _np(alone), f_tol=1e-12 if fp64 else 1e-3,
+              t_tol=1e-9 if fp64 else 2e-6)
     server.close()
 
 
