@@ -63,7 +63,9 @@ class TraceResult(C.Structure):
 
 class Robot(C.Structure):
     _fields_ = [("n_links", C.c_int32), ("dh", C.POINTER(C.c_double)),
-                ("radius", C.POINTER(C.c_double))]
+                ("radius", C.POINTER(C.c_double)), ("n_spheres", C.c_int32),
+                ("sphere_link", C.POINTER(C.c_int32)), ("sphere_center", C.POINTER(C.c_double)),
+                ("sphere_radius", C.POINTER(C.c_double))]
 
 
 class Scene(C.Structure):
@@ -110,6 +112,12 @@ def lib():
         L.or_certify.argtypes = [P(Robot), P(Scene), P(C.c_double), C.c_int64, C.c_int32,
                                  P(C.c_int64), P(C.c_int64), C.c_int64,
                                  P(C.c_uint8), P(C.c_double), P(C.c_uint8)]
+        L.or_fk_frames.argtypes = [P(Robot), P(C.c_double), P(C.c_double)]
+        L.or_lipschitz.argtypes = [P(Robot), P(C.c_double)]
+        L.or_certify_ex.argtypes = [P(Robot), P(Scene), P(C.c_double), C.c_int64, C.c_int32,
+                                    P(C.c_int64), P(C.c_int64), C.c_int64, P(C.c_uint8),
+                                    P(C.c_double), P(C.c_int32), P(C.c_uint8), P(C.c_uint8),
+                                    P(C.c_double)]
         L.or_set_threads.restype = C.c_int
         L.or_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -289,10 +297,25 @@ def edge_roots(sv, alpha, gamma, b, lam, o, edge_y, edge_mask):
 # Certification
 # --------------------------------------------------------------------------
 class _RobotHold:
-    def __init__(self, dh, radius):
+    """radius None: no link capsules; spheres = (link [n], centre [n][3] in
+    frame T_{link+1}, radius [n]) or None."""
+
+    def __init__(self, dh, radius, spheres=None):
         self.dh = _f64(dh).reshape(-1, 4)
-        self.radius = _f64(radius)
-        self.s = Robot(self.dh.shape[0], _p(self.dh, C.c_double), _p(self.radius, C.c_double))
+        self.radius = None if radius is None else _f64(radius)
+        rad = _p(self.radius, C.c_double) if self.radius is not None else None
+        if spheres is None:
+            self.sl = np.zeros(1, np.int32)
+            self.sc = np.zeros(3)
+            self.sr = np.zeros(1)
+            ns = 0
+        else:
+            self.sl = np.ascontiguousarray(spheres[0], dtype=np.int32)
+            self.sc = _f64(spheres[1]).reshape(-1, 3)
+            self.sr = _f64(spheres[2])
+            ns = self.sl.shape[0]
+        self.s = Robot(self.dh.shape[0], _p(self.dh, C.c_double), rad, ns,
+                       _p(self.sl, C.c_int32), _p(self.sc, C.c_double), _p(self.sr, C.c_double))
 
 
 class _SceneHold:
@@ -321,6 +344,54 @@ def segment_obstacle_dist(a, b, typ, pose, dims):
 def segseg_dist(p1, q1, p2, q2):
     args = [_f64(v) for v in (p1, q1, p2, q2)]
     return lib().or_segseg_dist(*[_p(v, C.c_double) for v in args])
+
+
+def fk_frames(dh, q):
+    """Frames T_0 .. T_n of the chain, each 3x4 [R | t]."""
+    r = _RobotHold(dh, np.zeros(len(np.atleast_1d(q))))
+    q = _f64(q)
+    out = np.zeros((r.dh.shape[0] + 1, 12))
+    lib().or_fk_frames(C.byref(r.s), _p(q, C.c_double), _p(out, C.c_double))
+    return out.reshape(-1, 3, 4)
+
+
+def lipschitz(dh, radius, spheres=None):
+    """Per robot element (capsules, then spheres) and joint: the bound on how
+    far a point of the element moves per radian of that joint."""
+    r = _RobotHold(dh, radius, spheres)
+    ne = (r.dh.shape[0] if radius is not None else 0) + int(r.s.n_spheres)
+    L = np.zeros((max(ne, 1), r.dh.shape[0]))
+    lib().or_lipschitz(C.byref(r.s), _p(L, C.c_double))
+    return L[:ne]
+
+
+def certify_ex(dh, radius, types, pose, dims, points, cell_off=None, cell_idx=None,
+               spheres=None):
+    """Per point: verdict, margin, deciding element; per cell: the AND of its
+    points' verdicts, the whole-cell (Lipschitz) verdict and its slack."""
+    r = _RobotHold(dh, radius, spheres)
+    s = _SceneHold(types, pose, dims)
+    d = r.dh.shape[0]
+    pts = _f64(points).reshape(-1, d)
+    P = pts.shape[0]
+    if cell_off is None:
+        cell_off = np.zeros(1, dtype=np.int64)
+        cell_idx = np.zeros(1, dtype=np.int64)
+    cell_off = np.ascontiguousarray(cell_off, dtype=np.int64)
+    cell_idx = np.ascontiguousarray(cell_idx if len(cell_idx) else np.zeros(1), dtype=np.int64)
+    nc = cell_off.shape[0] - 1
+    verdict = np.zeros(max(P, 1), dtype=np.uint8)
+    margin = np.zeros(max(P, 1))
+    elem = np.zeros(max(P, 1), dtype=np.int32)
+    cv = np.zeros(max(nc, 1), dtype=np.uint8)
+    whole = np.zeros(max(nc, 1), dtype=np.uint8)
+    slack = np.zeros(max(nc, 1))
+    lib().or_certify_ex(C.byref(r.s), C.byref(s.s), _p(pts, C.c_double), P, d,
+                        _p(cell_off, C.c_int64), _p(cell_idx, C.c_int64), nc,
+                        _p(verdict, C.c_uint8), _p(margin, C.c_double), _p(elem, C.c_int32),
+                        _p(cv, C.c_uint8), _p(whole, C.c_uint8), _p(slack, C.c_double))
+    return dict(verdict=verdict[:P], margin=margin[:P], element=elem[:P], cell_verdict=cv[:nc],
+                cell_whole=whole[:nc], cell_slack=slack[:nc])
 
 
 def certify(dh, radius, types, pose, dims, points, cell_off=None, cell_idx=None):

@@ -687,14 +687,22 @@ out:
 typedef struct {
   int32_t n_links;
   const double *dh;     /* [n][4]: theta0, d, a, alpha */
-  const double *radius; /* [n] capsule radius of link i */
+  const double *radius; /* [n] capsule radius of link i; NULL: no capsules */
+  /* Spheres fixed to the links (the paper's robot model, Sec. VI): sphere s
+   * rides on link sphere_link[s], its centre sphere_center[s] given in the
+   * frame T_{link+1} of the body that joint `link` turns. */
+  int32_t n_spheres;
+  const int32_t *sphere_link;
+  const double *sphere_center; /* [n_spheres][3] */
+  const double *sphere_radius; /* [n_spheres] */
 } or_robot;
 
 typedef struct {
   int32_t n;
-  const int32_t *type;  /* 0 = box, 1 = sphere */
-  const double *pose;   /* [n][12]: R (row-major, box frame -> world), then t */
-  const double *dims;   /* [n][3]: box side lengths l_x,l_y,l_z; sphere radius in [0] */
+  const int32_t *type;  /* 0 = box, 1 = sphere, 2 = cylinder */
+  const double *pose;   /* [n][12]: R (row-major, obstacle frame -> world), then t */
+  const double *dims;   /* [n][3]: box side lengths l_x,l_y,l_z; sphere radius in [0];
+                           cylinder radius r_c in [0] and height h in [1] (axis = local z) */
 } or_scene;
 
 static void mat4_mul(const double *A, const double *B, double *C) {
@@ -726,6 +734,26 @@ void or_fk(const or_robot *r, const double *q, double *origins) {
     origins[3 * (i + 1) + 0] = T[3];
     origins[3 * (i + 1) + 1] = T[7];
     origins[3 * (i + 1) + 2] = T[11];
+  }
+}
+
+/* All frames T_0 .. T_n of the chain as 3x4 row-major [R | t]. */
+void or_fk_frames(const or_robot *r, const double *q, double *frames) {
+  double T[16] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1};
+  for (int k = 0; k < 12; k++) frames[k] = T[k];
+  for (int i = 0; i < r->n_links; i++) {
+    double th = q[i] + r->dh[4 * i + 0], dd = r->dh[4 * i + 1], aa = r->dh[4 * i + 2], al = r->dh[4 * i + 3];
+    double ct = cos(th), st = sin(th), ca = cos(al), sa = sin(al);
+    double Rz[16] = {ct, -st, 0, 0, st, ct, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1};
+    double Tz[16] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, dd, 0, 0, 0, 1};
+    double Tx[16] = {1, 0, 0, aa, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1};
+    double Rx[16] = {1, 0, 0, 0, 0, ca, -sa, 0, 0, sa, ca, 0, 0, 0, 0, 1};
+    double A[16], B[16], C[16];
+    mat4_mul(T, Rz, A);
+    mat4_mul(A, Tz, B);
+    mat4_mul(B, Tx, C);
+    mat4_mul(C, Rx, T);
+    for (int k = 0; k < 12; k++) frames[12 * (i + 1) + k] = T[k];
   }
 }
 
@@ -808,6 +836,49 @@ static void to_local(const double *pose, const double *p, double *out) {
   for (int i = 0; i < 3; i++) out[i] = pose[0 + i] * w[0] + pose[3 + i] * w[1] + pose[6 + i] * w[2];
 }
 
+/* Distance from a point to the origin-centred solid cylinder of radius rc
+ * and height h with axis z (App. A, sphere vs cylinder): the radial excess
+ * sqrt(x^2 + y^2) - rc and the axial excess |z| - h/2, each counted when
+ * positive; inside both it is 0. */
+static double point_cylinder(const double *p, double rc, double h) {
+  double rho = sqrt(p[0] * p[0] + p[1] * p[1]);
+  double u = rho - rc, v = fabs(p[2]) - 0.5 * h;
+  if (u < 0.0) u = 0.0;
+  if (v < 0.0) v = 0.0;
+  return sqrt(u * u + v * v);
+}
+
+/* Distance from segment [a,b] (cylinder frame) to the cylinder: the distance
+ * to a convex set is convex along the segment, so golden-section search on
+ * [0,1] finds its minimum (100 steps shrink the bracket below 1e-20; the end
+ * points are checked too). */
+static double segment_cylinder_local(const double *a, const double *b, double rc, double h) {
+  const double g = 0.6180339887498949;
+  double p[3];
+#define OR_CYL_AT(t) (p[0] = a[0] + (t) * (b[0] - a[0]), p[1] = a[1] + (t) * (b[1] - a[1]), \
+                      p[2] = a[2] + (t) * (b[2] - a[2]), point_cylinder(p, rc, h))
+  double lo = 0.0, hi = 1.0;
+  double x1 = hi - g * (hi - lo), x2 = lo + g * (hi - lo);
+  double f1 = OR_CYL_AT(x1), f2 = OR_CYL_AT(x2);
+  for (int it = 0; it < 100; it++) {
+    if (f1 <= f2) {
+      hi = x2; x2 = x1; f2 = f1;
+      x1 = hi - g * (hi - lo); f1 = OR_CYL_AT(x1);
+    } else {
+      lo = x1; x1 = x2; f1 = f2;
+      x2 = lo + g * (hi - lo); f2 = OR_CYL_AT(x2);
+    }
+  }
+  double best = f1 < f2 ? f1 : f2;
+  double e0 = OR_CYL_AT(0.0), e1 = OR_CYL_AT(1.0);
+  double em = OR_CYL_AT(0.5 * (lo + hi));
+#undef OR_CYL_AT
+  if (e0 < best) best = e0;
+  if (e1 < best) best = e1;
+  if (em < best) best = em;
+  return best;
+}
+
 double or_segment_obstacle_dist(const double *a, const double *b, int32_t type, const double *pose,
                                 const double *dims) {
   double la[3], lb[3];
@@ -817,6 +888,7 @@ double or_segment_obstacle_dist(const double *a, const double *b, int32_t type, 
     double h[3] = {0.5 * dims[0], 0.5 * dims[1], 0.5 * dims[2]};
     return segment_box_local(la, lb, h);
   }
+  if (type == 2) return segment_cylinder_local(la, lb, dims[0], dims[1]);
   /* sphere at the frame origin: distance from the centre to the segment */
   double d[3] = {lb[0] - la[0], lb[1] - la[1], lb[2] - la[2]};
   double m[3] = {-la[0], -la[1], -la[2]};
@@ -827,32 +899,130 @@ double or_segment_obstacle_dist(const double *a, const double *b, int32_t type, 
   return cd > 0.0 ? cd : 0.0;
 }
 
-/* Per point: margin = max over links and obstacles of (radius - distance);
- * verdict = 1 (in collision, i.e. in C_obs) iff margin >= 0.  Per cell: the
- * AND of its points' verdicts (cell_off/cell_idx index the points). */
-void or_certify(const or_robot *r, const or_scene *sc, const double *points, int64_t P, int32_t d,
-                const int64_t *cell_off, const int64_t *cell_idx, int64_t n_cells,
-                uint8_t *verdict, double *margin, uint8_t *cell_verdict) {
+/* Robot elements: the link capsules (when radius is given), then the spheres.
+ * Element e's end points at a configuration, from the frames of or_fk_frames. */
+static int n_elements(const or_robot *r) { return (r->radius ? r->n_links : 0) + r->n_spheres; }
+
+static void element_at(const or_robot *r, const double *frames, int e, double *pa, double *pb,
+                       double *rad, int *link) {
+  int nc = r->radius ? r->n_links : 0;
+  if (e < nc) {
+    for (int k = 0; k < 3; k++) {
+      pa[k] = frames[12 * e + 4 * k + 3];
+      pb[k] = frames[12 * (e + 1) + 4 * k + 3];
+    }
+    *rad = r->radius[e];
+    *link = e;
+    return;
+  }
+  int s = e - nc, l = r->sphere_link[s];
+  const double *F = frames + 12 * (l + 1), *c = r->sphere_center + 3 * s;
+  for (int k = 0; k < 3; k++) pa[k] = pb[k] = F[4 * k] * c[0] + F[4 * k + 1] * c[1] + F[4 * k + 2] * c[2] + F[4 * k + 3];
+  *rad = r->sphere_radius[s];
+  *link = l;
+}
+
+/* Lipschitz constants of the robot elements (the whole-cell certificate):
+ * turning joint k by dq moves a point x of the body by at most |dq| times
+ * its distance to the joint axis, which is at most |x - o_k|.  For a point of
+ * element e on link l >= k that is at most sum_{m=k..l} |o_{m+1} - o_m| (+ |c|
+ * for a sphere centre c in frame T_{l+1}), with |o_{m+1} - o_m| =
+ * sqrt(d_m^2 + a_m^2) whatever the configuration; joints after l do not move
+ * it.  L[e * n_links + k]. */
+void or_lipschitz(const or_robot *r, double *L) {
+  int ne = n_elements(r), nc = r->radius ? r->n_links : 0;
+  for (int e = 0; e < ne; e++) {
+    int l = e < nc ? e : r->sphere_link[e - nc];
+    double extra = 0.0;
+    if (e >= nc) {
+      const double *c = r->sphere_center + 3 * (e - nc);
+      extra = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    }
+    for (int k = 0; k < r->n_links; k++) {
+      double s = 0.0;
+      if (k <= l) {
+        for (int m = k; m <= l; m++)
+          s += sqrt(r->dh[4 * m + 1] * r->dh[4 * m + 1] + r->dh[4 * m + 2] * r->dh[4 * m + 2]);
+        s += extra;
+      }
+      L[e * r->n_links + k] = s;
+    }
+  }
+}
+
+/* Per point: margin = max over robot elements and obstacles of
+ * (radius - distance); verdict = 1 (in collision, i.e. in C_obs) iff
+ * margin >= 0; element = the first element reaching the maximum.  Per cell
+ * (cell_off/cell_idx index the points): the AND of its points' verdicts, and
+ * the whole-cell certificate: the cell's piece of the traced manifold is the
+ * convex hull of its points, every q in it has |q_k - p_jk| <= span_jk =
+ * max_l |p_lk - p_jk|, and element e's margin is at least margin_j -
+ * sum_k L[e][k] |q_k - p_jk| (distances are 1-Lipschitz in the element's
+ * points); so slack = max_j (margin_j - sum_k L[e_j][k] span_jk) >= 0
+ * certifies every point of the piece (whole = 1). */
+void or_certify_ex(const or_robot *r, const or_scene *sc, const double *points, int64_t P,
+                   int32_t d, const int64_t *cell_off, const int64_t *cell_idx, int64_t n_cells,
+                   uint8_t *verdict, double *margin, int32_t *element, uint8_t *cell_verdict,
+                   uint8_t *cell_whole, double *cell_slack) {
+  int ne = n_elements(r);
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t p = 0; p < P; p++) {
-    double org[3 * (OR_MAXD + 1)];
-    or_fk(r, points + p * d, org);
+    double frames[12 * (OR_MAXD + 1)];
+    or_fk_frames(r, points + p * d, frames);
     double best = -INFINITY;
-    for (int i = 0; i < r->n_links; i++)
+    int be = -1;
+    for (int e = 0; e < ne; e++) {
+      double pa[3], pb[3], rad;
+      int link;
+      element_at(r, frames, e, pa, pb, &rad, &link);
       for (int k = 0; k < sc->n; k++) {
-        double dist = or_segment_obstacle_dist(org + 3 * i, org + 3 * (i + 1), sc->type[k],
-                                               sc->pose + 12 * k, sc->dims + 3 * k);
-        double m = r->radius[i] - dist;
-        if (m > best) best = m;
+        double dist = or_segment_obstacle_dist(pa, pb, sc->type[k], sc->pose + 12 * k, sc->dims + 3 * k);
+        double m = rad - dist;
+        if (m > best) { best = m; be = e; }
       }
+    }
     margin[p] = best;
     verdict[p] = best >= 0.0 ? 1 : 0;
+    if (element) element[p] = be;
+  }
+  double *L = NULL;
+  if (cell_whole || cell_slack) {
+    L = (double *)malloc(sizeof(double) * (size_t)(ne > 0 ? ne : 1) * (size_t)r->n_links);
+    if (L) or_lipschitz(r, L);
   }
   for (int64_t c = 0; c < n_cells; c++) {
     uint8_t v = 1;
     for (int64_t j = cell_off[c]; j < cell_off[c + 1]; j++) v = (uint8_t)(v & verdict[cell_idx[j]]);
-    cell_verdict[c] = v;
+    if (cell_verdict) cell_verdict[c] = v;
+    if (!L) continue;
+    double slack = -INFINITY;
+    for (int64_t j = cell_off[c]; j < cell_off[c + 1]; j++) {
+      int64_t pj = cell_idx[j];
+      int e = element ? element[pj] : -1;
+      if (e < 0) continue;
+      double drop = 0.0;
+      for (int k = 0; k < d; k++) {
+        double span = 0.0;
+        for (int64_t l = cell_off[c]; l < cell_off[c + 1]; l++) {
+          double u = fabs(points[cell_idx[l] * d + k] - points[pj * d + k]);
+          if (u > span) span = u;
+        }
+        drop += L[e * r->n_links + k] * span;
+      }
+      double s = margin[pj] - drop;
+      if (s > slack) slack = s;
+    }
+    if (cell_slack) cell_slack[c] = slack;
+    if (cell_whole) cell_whole[c] = slack >= 0.0 ? 1 : 0;
   }
+  free(L);
+}
+
+void or_certify(const or_robot *r, const or_scene *sc, const double *points, int64_t P, int32_t d,
+                const int64_t *cell_off, const int64_t *cell_idx, int64_t n_cells,
+                uint8_t *verdict, double *margin, uint8_t *cell_verdict) {
+  or_certify_ex(r, sc, points, P, d, cell_off, cell_idx, n_cells, verdict, margin, NULL,
+                cell_verdict, NULL, NULL);
 }
 
 /* Host threads of the parallel loops (roots, f batches, certification);
