@@ -528,6 +528,9 @@ def run_gb300(args):
                        "precision": w.precision, "edges_per_proof": E,
                        "cells_per_proof": r["n_cells"], "vertices_per_proof": r["n_vertices"],
                        "bfs_levels": r["levels"], "ms_per_proof": ms_max,
+                       "cells_points_in_collision": int(cv.sum().item()) if r["n_cells"] else 0,
+                       "cells_whole_certified": int(proof.whole.sum().item())
+                       if r["n_cells"] and proof.whole is not None else 0,
                        "autotune": tune,
                        "l2": "inputs larger than L2 (resident hash tables and lists are GBs)"},
             "e2e": {"value": e2e_edges_all / args.steps / (e2e_max / args.steps),

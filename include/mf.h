@@ -131,21 +131,36 @@ typedef struct {
 
 /* Serial arm for certification: frame T_{i+1} = T_i Rz(q_i + theta_i) Tz(d_i)
  * Tx(a_i) Rx(alpha_i), T_0 = identity; link i is the capsule between the
- * origins of T_i and T_{i+1} with radius radius[i]. */
+ * origins of T_i and T_{i+1} with radius radius[i].  The robot's elements are
+ * its link capsules (elements 0 .. n_links-1, when radius is given) followed
+ * by its spheres.  Spheres are the paper's robot model (Sec. VI: each link
+ * as a set of spheres): sphere s rides on link sphere_link[s] (the body that
+ * joint sphere_link[s] turns) with its centre given in that link's frame
+ * T_{link+1}.  A zero-initialised tail (n_spheres = 0) means capsules only;
+ * radius = NULL means spheres only. */
 typedef struct {
   int32_t n_links;        /* == d of the points */
   const double *dh;       /* device [n_links][4]: theta_i, d_i, a_i, alpha_i */
-  const double *radius;   /* device [n_links] */
+  const double *radius;   /* device [n_links] capsule radii, or NULL: no capsules */
+  int32_t n_spheres;      /* 0 .. MF_MAX_SPHERES */
+  const int32_t *sphere_link;   /* device [n_spheres], in [0, n_links) */
+  const double *sphere_center;  /* device [n_spheres][3], in frame T_{link+1} */
+  const double *sphere_radius;  /* device [n_spheres] */
 } mf_robot;
+#define MF_MAX_SPHERES 64
 
 #define MF_BOX 0
 #define MF_SPHERE 1
+#define MF_CYLINDER 2
 typedef struct {
   int32_t n;
-  const int32_t *type;    /* device [n]: MF_BOX / MF_SPHERE */
+  const int32_t *type;    /* device [n]: MF_BOX / MF_SPHERE / MF_CYLINDER */
   const double *pose;     /* device [n][12]: rotation R (row-major, obstacle frame
                              -> world) followed by the translation t */
-  const double *dims;     /* device [n][3]: box side lengths; sphere radius in [0] */
+  const double *dims;     /* device [n][3]: box side lengths; sphere radius in [0];
+                             cylinder radius in [0] and height in [1], centred on
+                             the frame origin with the local z axis as its axis
+                             (App. A, sphere vs cylinder) */
 } mf_scene;
 
 /* Creates a context on `device` whose resident allocations never exceed
@@ -263,6 +278,34 @@ int mf_certify(mf_ctx *ctx, const mf_robot *robot, const mf_scene *scene, const 
                int64_t n_points, int32_t d, const int64_t *cell_edge_off,
                const int64_t *cell_edge_idx, int64_t n_cells, uint8_t *point_verdict,
                double *margin, uint8_t *cell_verdict, void *stream);
+
+/* Outputs of mf_certify_ex (caller-owned device buffers; NULL = not wanted,
+ * except point_verdict and margin). */
+typedef struct {
+  uint8_t *point_verdict; /* [n_points] 1 iff the point is in collision (C_obs) */
+  double *margin;         /* [n_points] max over elements and obstacles of radius - distance */
+  int16_t *element;       /* [n_points] the element of that maximum (capsules, then spheres) */
+  uint8_t *cell_verdict;  /* [n_cells] AND of the verdicts of the cell's points */
+  uint8_t *cell_whole;    /* [n_cells] 1 iff the whole-cell certificate holds (below) */
+  double *cell_slack;     /* [n_cells] the certificate's slack (>= 0: certified) */
+} mf_certify_out;
+
+/* Certification as mf_certify, with the robot's spheres, cylinder obstacles,
+ * the deciding element of every point, and the whole-cell certificate (the
+ * rigorous form of the cell check that the paper's prior work uses, Sec.
+ * IV-A; the paper itself checks points, Sec. V-C).  A cell's piece of the
+ * traced manifold is the convex hull of its points.  Turning joint k by dq
+ * moves a point of element e by at most L[e][k] |dq|, with L[e][k] the sum of
+ * the link lengths sqrt(d_m^2 + a_m^2), m = k .. link(e) (plus |centre| for a
+ * sphere; 0 for joints after the element's link).  So with span_jk the
+ * largest |p_lk - p_jk| over the cell's points, every configuration of the
+ * piece keeps element e_j's margin at least margin_j - sum_k L[e_j][k]
+ * span_jk; slack = the maximum of that over the cell's points, and
+ * cell_whole = (slack >= 0) certifies the whole piece in collision. */
+int mf_certify_ex(mf_ctx *ctx, const mf_robot *robot, const mf_scene *scene, const double *points,
+                  int64_t n_points, int32_t d, const int64_t *cell_edge_off,
+                  const int64_t *cell_edge_idx, int64_t n_cells, const mf_certify_out *out,
+                  void *stream);
 
 /* Size of the fixed device array used by mf_trace_noalloc (64 MiB). */
 #define MF_NOALLOC_SCRATCH_BYTES (64ull << 20)

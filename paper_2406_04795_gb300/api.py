@@ -233,30 +233,62 @@ class Context:
 
     def certify(self, dh, radius, types, pose, dims, points, cell_off=None, cell_idx=None,
                 stream=None):
-        dh_t = _dev(dh, torch.float64, self.device).reshape(-1, 4)
-        rad_t = _dev(radius, torch.float64, self.device)
-        ty_t = _dev(types, torch.int32, self.device)
-        po_t = _dev(pose, torch.float64, self.device).reshape(-1, 12)
-        di_t = _dev(dims, torch.float64, self.device).reshape(-1, 3)
+        """Point verdicts, margins and per-cell AND of the point verdicts
+        (mf_certify)."""
+        r = self.certify_ex(dh, radius, types, pose, dims, points, cell_off, cell_idx,
+                            whole=False, stream=stream)
+        return r["verdict"], r["margin"], r["cell_verdict"]
+
+    def certify_ex(self, dh, radius, types, pose, dims, points, cell_off=None, cell_idx=None,
+                   spheres=None, whole=True, stream=None):
+        """mf_certify_ex: radius None = no link capsules; spheres = (link [n],
+        centre [n][3] in frame T_{link+1}, radius [n]) or None.  Returns device
+        tensors verdict, margin, element and, with cells, cell_verdict and
+        (whole=True) cell_whole / cell_slack."""
+        dev = self.device
+        dh_t = _dev(dh, torch.float64, dev).reshape(-1, 4)
+        rad_t = None if radius is None else _dev(radius, torch.float64, dev)
+        ty_t = _dev(types, torch.int32, dev)
+        po_t = _dev(pose, torch.float64, dev).reshape(-1, 12)
+        di_t = _dev(dims, torch.float64, dev).reshape(-1, 3)
         d = dh_t.shape[0]
-        pts = _dev(points, torch.float64, self.device).reshape(-1, d)
+        pts = _dev(points, torch.float64, dev).reshape(-1, d)
         P = pts.shape[0]
-        verdict = torch.empty(max(P, 1), dtype=torch.uint8, device=self.device)
-        margin = torch.empty(max(P, 1), dtype=torch.float64, device=self.device)
-        robot = mf.mf_robot(d, dh_t.data_ptr(), rad_t.data_ptr())
-        scene = mf.mf_scene(ty_t.shape[0], ty_t.data_ptr(), po_t.data_ptr(), di_t.data_ptr())
-        if cell_off is not None and cell_off.shape[0] > 1:
-            off_t = _dev(cell_off, torch.int64, self.device)
-            idx_t = _dev(cell_idx, torch.int64, self.device)
-            nc = off_t.shape[0] - 1
-            cv = torch.empty(nc, dtype=torch.uint8, device=self.device)
-            offp, idxp, cvp = off_t.data_ptr(), idx_t.data_ptr() if idx_t.numel() else None, cv.data_ptr()
+        res = dict(verdict=torch.empty(max(P, 1), dtype=torch.uint8, device=dev),
+                   margin=torch.empty(max(P, 1), dtype=torch.float64, device=dev),
+                   element=torch.empty(max(P, 1), dtype=torch.int16, device=dev))
+        if spheres is not None:
+            sl = _dev(spheres[0], torch.int32, dev)
+            sc = _dev(spheres[1], torch.float64, dev).reshape(-1, 3)
+            sr = _dev(spheres[2], torch.float64, dev)
+            sph = (int(sl.shape[0]), sl.data_ptr(), sc.data_ptr(), sr.data_ptr())
         else:
-            nc, offp, idxp, cvp, cv = 0, None, None, None, torch.empty(0, dtype=torch.uint8,
-                                                                        device=self.device)
-        mf.mf_certify(self.h, robot, scene, pts.data_ptr(), P, d, offp, idxp, nc, verdict.data_ptr(),
-                      margin.data_ptr(), cvp, _stream_handle(stream))
-        return verdict[:P], margin[:P], cv
+            sph = (0, None, None, None)
+        robot = mf.mf_robot(d, dh_t.data_ptr(), rad_t.data_ptr() if rad_t is not None else None,
+                            *sph)
+        scene = mf.mf_scene(ty_t.shape[0], ty_t.data_ptr(), po_t.data_ptr(), di_t.data_ptr())
+        out = mf.mf_certify_out(res["verdict"].data_ptr(), res["margin"].data_ptr(),
+                                res["element"].data_ptr(), None, None, None)
+        nc, offp, idxp = 0, None, None
+        if cell_off is not None and cell_off.shape[0] > 1:
+            off_t = _dev(cell_off, torch.int64, dev)
+            idx_t = _dev(cell_idx, torch.int64, dev)
+            nc = off_t.shape[0] - 1
+            offp, idxp = off_t.data_ptr(), idx_t.data_ptr() if idx_t.numel() else None
+            res["cell_verdict"] = torch.empty(nc, dtype=torch.uint8, device=dev)
+            out.cell_verdict = res["cell_verdict"].data_ptr()
+            if whole:
+                res["cell_whole"] = torch.empty(nc, dtype=torch.uint8, device=dev)
+                res["cell_slack"] = torch.empty(nc, dtype=torch.float64, device=dev)
+                out.cell_whole = res["cell_whole"].data_ptr()
+                out.cell_slack = res["cell_slack"].data_ptr()
+        else:
+            res["cell_verdict"] = torch.empty(0, dtype=torch.uint8, device=dev)
+        mf.mf_certify_ex(self.h, robot, scene, pts.data_ptr(), P, d, offp, idxp, nc, out,
+                         _stream_handle(stream))
+        for k in ("verdict", "margin", "element"):
+            res[k] = res[k][:P]
+        return res
 
 
 class Server:

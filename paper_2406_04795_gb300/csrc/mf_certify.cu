@@ -1,6 +1,8 @@
 // mf_certify.cu -- certification of traced points (Sec. V-C, App. A):
 // forward kinematics of a serial DH arm and the exact distance between each
-// link capsule and each box / sphere obstacle, in FP64.
+// robot element (link capsules; spheres fixed to the links, the paper's robot
+// model) and each box / sphere / cylinder obstacle, in FP64; and the
+// whole-cell certificate of each crossing n-simplex's manifold piece.
 //
 // Capsule/box distance: in the box frame the squared distance from the
 // segment point p(t) = a + t (b - a) to the box is
@@ -9,6 +11,13 @@
 // minimum over [0,1] is found exactly by minimising the quadratic of every
 // piece (at most 7).  This extends App. A's sphere/box test (a sphere is the
 // zero-length capsule) to capsules.
+//
+// Capsule/cylinder distance: in the cylinder frame
+//   F(t) = max(0, rho(t) - r_c)^2 + max(0, |z(t)| - h/2)^2,
+// rho the distance to the axis, is the squared distance to the solid
+// cylinder (App. A's ring-region test is its zero-length case); it is convex
+// and C^1, so bracketed Newton steps on F' find its minimum and the same
+// convexity certificate as for boxes proves it.
 #include <cmath>
 #include <vector>
 
@@ -22,7 +31,7 @@ template <typename T>
 struct CertObsT {
   T R[9];
   T t[3];
-  T h[3];  // box half extents; sphere radius in h[0]
+  T h[3];  // box half extents; sphere radius in h[0]; cylinder radius, half height
   int type;
 };
 typedef CertObsT<double> CertObs;
@@ -132,6 +141,52 @@ __device__ double seg_box_dist64(const double *a, const double *dl, const double
   return sqrt(seg_box_d2<double>(a, dl, h));
 }
 
+// F(t), F'(t) / 2 and F''(t) / 2 of the squared segment/cylinder distance
+// (cylinder frame, radius rc, half height hh).  F is convex and C^1: the
+// axis term vanishes near rho = 0 and the cap term near z = 0.
+template <typename T>
+__device__ __forceinline__ void cyl_fgh(const T *a, const T *dl, T rc, T hh, T t, T &F, T &G, T &H) {
+  const T x = fma(t, dl[0], a[0]), y = fma(t, dl[1], a[1]), z = fma(t, dl[2], a[2]);
+  F = G = H = 0;
+  const T rho = sqrt(fma(x, x, y * y));
+  const T qr = rho - rc;
+  if (qr > (T)0) {
+    const T rp = fma(x, dl[0], y * dl[1]) / rho;                       // rho'
+    const T rpp = (fma(dl[0], dl[0], dl[1] * dl[1]) - rp * rp) / rho;  // rho''
+    F = qr * qr;
+    G = qr * rp;
+    H = fma(qr, rpp, rp * rp);
+  }
+  const T qz = fabs(z) - hh;
+  if (qz > (T)0) {
+    F = fma(qz, qz, F);
+    G = fma(copysign(qz, z), dl[2], G);
+    H = fma(dl[2], dl[2], H);
+  }
+}
+
+// Exact distance from segment [a, a+dl] (cylinder frame) to the cylinder in
+// FP64 from a start t: Newton steps on F' kept inside a bracket of the
+// minimiser (F' is non-decreasing), until the convexity certificate
+// min F >= F(t) - |F'(t)| (t or 1 - t) leaves at most 2e-12 of room in the
+// distance.
+__device__ double seg_cyl_dist64(const double *a, const double *dl, double rc, double hh, double t) {
+  double lo = 0.0, hi = 1.0, best = INFINITY;
+  for (int it = 0; it < 80; it++) {
+    double F, G, H;
+    cyl_fgh<double>(a, dl, rc, hh, t, F, G, H);
+    best = fmin(best, F);
+    const double D = sqrt(F);
+    if (F == 0.0 || G == 0.0 || 2.0 * fabs(G) * (G > 0.0 ? t : 1.0 - t) <= 2e-12 * D) return D;
+    if (G > 0.0) hi = t; else lo = t;
+    double tn = H > 0.0 ? t - G / H : 0.5 * (lo + hi);
+    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    if (hi - lo <= 1e-17) break;
+    t = tn;
+  }
+  return sqrt(best);
+}
+
 template <typename T>
 __device__ __noinline__ T seg_obstacle_dist(const CertObsT<T> &o, const T *pa, const T *pb, T t0) {
   T a[3], b[3], dl[3];
@@ -145,6 +200,7 @@ __device__ __noinline__ T seg_obstacle_dist(const CertObsT<T> &o, const T *pa, c
     dl[i] = b[i] - a[i];
   }
   if (o.type == MF_BOX) return seg_box_dist64(a, dl, o.h, t0);
+  if (o.type == MF_CYLINDER) return seg_cyl_dist64(a, dl, o.h[0], o.h[1], t0);
   // sphere at the local origin: clamped projection of the centre
   const T dd = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
   T t = 0;
@@ -177,6 +233,19 @@ __device__ __forceinline__ float seg_obstacle_lb32(const CertObsT<float> &o, con
   const float dd = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
   float t = 0.f;
   if (dd > 0.f) t = fminf(fmaxf(-(a[0] * dl[0] + a[1] * dl[1] + a[2] * dl[2]) / dd, 0.f), 1.f);
+  if (o.type == MF_CYLINDER) {
+    // convex and C^1 as for boxes: three clamped Newton steps, then the
+    // convexity bound
+    float F = 0.f, G = 0.f, H = 0.f;
+#pragma unroll
+    for (int it = 0; it <= 3; it++) {
+      cyl_fgh<float>(a, dl, o.h[0], o.h[1], t, F, G, H);
+      if (it < 3 && H > 0.f) t = fminf(fmaxf(t - G / H, 0.f), 1.f);
+    }
+    *tmin = t;
+    const float lbF = F - 2.f * fabsf(G) * (G > 0.f ? t : 1.f - t) - eta;
+    return lbF > 0.f ? sqrtf(lbF) : 0.f;
+  }
   if (o.type != MF_BOX) {
     *tmin = t;
     const float c0 = fmaf(t, dl[0], a[0]), c1 = fmaf(t, dl[1], a[1]), c2 = fmaf(t, dl[2], a[2]);
@@ -232,19 +301,22 @@ __device__ __forceinline__ void cert_sincos(double x, const double2 *tab, double
 // The link loops stay rolled: unrolling them per link count inlines the
 // distance routines once per link and pass, which overflows the instruction
 // cache (measured: 45 no-instruction stall cycles per issue).
-__global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const double *dh,
-                                                                 const double *radius, int nobs,
-                                                                 const int32_t *type,
-                                                                 const double *pose, const double *dims,
-                                                                 const double *pts, int64_t n, int d,
-                                                                 const double2 *sctab,
-                                                                 uint8_t *verdict, double *margin) {
+// Elements: link capsules e < NC (NC = NL with capsules, 0 without), then
+// spheres e - NC on their links.
+__global__ void __launch_bounds__(CERT_THREADS, 5) k_certify_points(
+    int NL, const double *dh, const double *radius, int NS, const int32_t *sph_link,
+    const double *sph_c, const double *sph_r, int nobs, const int32_t *type, const double *pose,
+    const double *dims, const double *pts, int64_t n, int d, const double2 *sctab, uint8_t *verdict,
+    double *margin, int16_t *element) {
   __shared__ CertObs so[CERT_MAX_OBS];
   __shared__ CertObsT<float> sof[CERT_MAX_OBS];  // FP32 copy for the lower bounds
   __shared__ double sdh[MF_MAXD * 4], srad[MF_MAXD], ssa[MF_MAXD], sca[MF_MAXD];
   // FP32 copies, so that the FP32 passes convert nothing on the FP64 pipe
   __shared__ float sdh32[MF_MAXD * 4], srad32[MF_MAXD], ssa32[MF_MAXD], sca32[MF_MAXD];
   __shared__ double2 ssc[128];
+  __shared__ int ssl[MF_MAX_SPHERES];
+  __shared__ double ssc64[MF_MAX_SPHERES * 3], ssr64[MF_MAX_SPHERES];
+  __shared__ float ssc32[MF_MAX_SPHERES * 3], ssr32[MF_MAX_SPHERES];
   for (int i = threadIdx.x; i < 128; i += blockDim.x) ssc[i] = sctab[i];
   for (int i = threadIdx.x; i < nobs; i += blockDim.x) {
     CertObs o;
@@ -252,8 +324,11 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const d
     for (int k = 0; k < 9; k++) of.R[k] = (float)(o.R[k] = pose[12 * i + k]);
     for (int k = 0; k < 3; k++) of.t[k] = (float)(o.t[k] = pose[12 * i + 9 + k]);
     of.type = o.type = type[i];
-    for (int k = 0; k < 3; k++)
-      of.h[k] = (float)(o.h[k] = o.type == MF_BOX ? 0.5 * dims[3 * i + k] : dims[3 * i + k]);
+    for (int k = 0; k < 3; k++) {
+      double h = dims[3 * i + k];
+      if (o.type == MF_BOX || (o.type == MF_CYLINDER && k == 1)) h *= 0.5;
+      of.h[k] = (float)(o.h[k] = h);
+    }
     so[i] = o;
     sof[i] = of;
   }
@@ -262,20 +337,29 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const d
     sdh32[i] = (float)dh[i];
   }
   for (int i = threadIdx.x; i < NL; i += blockDim.x) {
-    srad[i] = radius[i];
-    srad32[i] = (float)radius[i];
+    srad[i] = radius ? radius[i] : 0.0;
+    srad32[i] = (float)srad[i];
     sincos(dh[4 * i + 3], &ssa[i], &sca[i]);
     ssa32[i] = (float)ssa[i];
     sca32[i] = (float)sca[i];
   }
+  for (int i = threadIdx.x; i < NS; i += blockDim.x) {
+    ssl[i] = sph_link[i];
+    ssr64[i] = sph_r[i];
+    ssr32[i] = (float)sph_r[i];
+    for (int k = 0; k < 3; k++) ssc32[3 * i + k] = (float)(ssc64[3 * i + k] = sph_c[3 * i + k]);
+  }
   __syncthreads();
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
+  const int NC = radius ? NL : 0, NE = NC + NS;
   // Forward kinematics, T = T * A_i with the standard DH link transform,
-  // keeping every frame origin (link i runs from origin i to origin i+1).
-  // First in FP32 for all links (the lower bounds below), then in FP64 only
-  // as far along the chain as the pairs that need an exact distance.
+  // keeping every frame origin (link i runs from origin i to origin i+1) and,
+  // when the robot has spheres, every rotation.  First in FP32 for all links
+  // (the lower bounds below), then in FP64 only as far along the chain as the
+  // pairs that need an exact distance.
   float org32[3 * (MF_MAXD + 1)];
+  float rot32[9 * (MF_MAXD + 1)];
   {
     float T[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
     org32[0] = org32[1] = org32[2] = 0.f;
@@ -302,10 +386,17 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const d
       org32[3 * (i + 1) + 0] = T[3];
       org32[3 * (i + 1) + 1] = T[7];
       org32[3 * (i + 1) + 2] = T[11];
+      if (NS) {
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+          for (int c = 0; c < 3; c++) rot32[9 * (i + 1) + 3 * r + c] = T[4 * r + c];
+      }
     }
   }
   double T[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};  // 3x4 row-major
   double org[3 * (MF_MAXD + 1)];
+  double rot[9 * (MF_MAXD + 1)];
   org[0] = org[1] = org[2] = 0.0;
   int done = 0;  // FP64 origins known: 0 .. done
   auto fk64 = [&](int upto) {
@@ -331,11 +422,51 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const d
       org[3 * (i + 1) + 0] = T[3];
       org[3 * (i + 1) + 1] = T[7];
       org[3 * (i + 1) + 2] = T[11];
+      if (NS) {
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+          for (int c = 0; c < 3; c++) rot[9 * (i + 1) + 3 * r + c] = T[4 * r + c];
+      }
     }
     if (upto > done) done = upto;
   };
-  // margin = max over (link, obstacle) of radius - distance.  Every pair first
-  // gets a lower bound on its distance in FP32 from the FP32 chain
+  // element e: its link, and its segment (a sphere is a zero-length one) in
+  // FP32 from the FP32 chain
+  auto elem32 = [&](int e, float *a, float *b) -> float {
+    if (e < NC) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        a[c] = org32[3 * e + c];
+        b[c] = org32[3 * e + 3 + c];
+      }
+      return srad32[e];
+    }
+    const int s = e - NC, f = ssl[s] + 1;
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+      a[r] = b[r] = fmaf(rot32[9 * f + 3 * r], ssc32[3 * s],
+                         fmaf(rot32[9 * f + 3 * r + 1], ssc32[3 * s + 1],
+                              fmaf(rot32[9 * f + 3 * r + 2], ssc32[3 * s + 2], org32[3 * f + r])));
+    return ssr32[s];
+  };
+  // the same in FP64 (after fk64 past the element's link)
+  auto exact = [&](int e, int k, double t0) -> double {
+    if (e < NC) {
+      fk64(e + 1);
+      return srad[e] - seg_obstacle_dist(so[k], &org[3 * e], &org[3 * e + 3], t0);
+    }
+    const int s = e - NC, f = ssl[s] + 1;
+    fk64(f);
+    double c[3];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+      c[r] = rot[9 * f + 3 * r] * ssc64[3 * s] + rot[9 * f + 3 * r + 1] * ssc64[3 * s + 1] +
+             rot[9 * f + 3 * r + 2] * ssc64[3 * s + 2] + org[3 * f + r];
+    return ssr64[s] - seg_obstacle_dist(so[k], c, c, t0);
+  };
+  // margin = max over (element, obstacle) of radius - distance.  Every pair
+  // first gets a lower bound on its distance in FP32 from the FP32 chain
   // (seg_obstacle_lb32); minus a slack of 1e-4 (1 + the largest coordinate),
   // far above the FP32 rounding of the chain (about 1e-5 of that scale), it
   // bounds the true distance from below, and radius - bound is an upper
@@ -343,8 +474,9 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const d
   // exactly (FP64 chain to its link, FP64 distance); the others only if the
   // second-largest ub exceeds that exact margin, and then only those whose
   // ub does.  The result is the exact maximum.
-  auto upper = [&](int i, int k, float *tmin) -> float {
-    const float *a = &org32[3 * i], *b = &org32[3 * i + 3];
+  auto upper = [&](int e, int k, float *tmin) -> float {
+    float a[3], b[3];
+    const float rad = elem32(e, a, b);
     float scale = 1.f;
 #pragma unroll
     for (int c = 0; c < 3; c++)
@@ -352,18 +484,18 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const d
     // local coordinates are below 2 scale: the bound's own rounding of the
     // squared distance stays far below 4e-5 (1 + scale)^2
     const float eta = 4e-5f * (1.f + scale) * (1.f + scale);
-    return srad32[i] - (seg_obstacle_lb32(sof[k], a, b, eta, tmin) - 1e-4f * (1.f + scale));
+    return rad - (seg_obstacle_lb32(sof[k], a, b, eta, tmin) - 1e-4f * (1.f + scale));
   };
   float ub1 = -INFINITY, ub2 = -INFINITY, tb = 0.f;
   int bi = -1, bk = -1;
-  for (int i = 0; i < NL; i++)
+  for (int e = 0; e < NE; e++)
     for (int k = 0; k < nobs; k++) {
       float tk;
-      const float ub = upper(i, k, &tk);
+      const float ub = upper(e, k, &tk);
       if (ub > ub1) {
         ub2 = ub1;
         ub1 = ub;
-        bi = i;
+        bi = e;
         bk = k;
         tb = tk;
       } else if (ub > ub2) {
@@ -371,23 +503,75 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(int NL, const d
       }
     }
   double best = -INFINITY;
+  int be = -1;
   if (bi >= 0) {
-    fk64(bi + 1);
-    best = srad[bi] - seg_obstacle_dist(so[bk], &org[3 * bi], &org[3 * bi + 3], (double)tb);
+    best = exact(bi, bk, (double)tb);
+    be = bi;
   }
   if ((double)ub2 > best) {
-    fk64(NL);
-    for (int i = 0; i < NL; i++)
+    for (int e = 0; e < NE; e++)
       for (int k = 0; k < nobs; k++) {
-        if (i == bi && k == bk) continue;
+        if (e == bi && k == bk) continue;
         float tk;
-        if ((double)upper(i, k, &tk) <= best) continue;
-        best = fmax(best, srad[i] - seg_obstacle_dist(so[k], &org[3 * i], &org[3 * i + 3],
-                                                      (double)tk));
+        if ((double)upper(e, k, &tk) <= best) continue;
+        const double m = exact(e, k, (double)tk);
+        if (m > best) {
+          best = m;
+          be = e;
+        }
       }
   }
   margin[p] = best;
   verdict[p] = best >= 0.0 ? 1 : 0;
+  if (element) element[p] = (int16_t)be;
+}
+
+// Whole-cell certificate (one thread per cell): with lo_k / hi_k the range of
+// coordinate k over the cell's points, span_jk = max(hi_k - p_jk, p_jk - lo_k)
+// and slack = max_j (margin_j - sum_k L[e_j][k] span_jk); the piece of the
+// manifold in the cell (the hull of its points) is in collision when
+// slack >= 0.
+__global__ void k_certify_cells_whole(const int64_t *off, const int64_t *idx, int64_t n_cells,
+                                      const double *pts, int d, const double *margin,
+                                      const int16_t *element, const double *L, int NE,
+                                      int64_t n_points, uint8_t *whole, double *slack_out,
+                                      unsigned *bad) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  const int64_t j0 = off[c], j1 = off[c + 1];
+  double lo[MF_MAXD], hi[MF_MAXD];
+#pragma unroll
+  for (int k = 0; k < MF_MAXD; k++) {
+    lo[k] = INFINITY;
+    hi[k] = -INFINITY;
+  }
+  for (int64_t j = j0; j < j1; j++) {
+    const int64_t i = idx[j];
+    if (i < 0 || i >= n_points) {
+      atomicOr(bad, 1u);
+      continue;
+    }
+    for (int k = 0; k < d; k++) {
+      const double v = pts[i * d + k];
+      lo[k] = fmin(lo[k], v);
+      hi[k] = fmax(hi[k], v);
+    }
+  }
+  double slack = -INFINITY;
+  for (int64_t j = j0; j < j1; j++) {
+    const int64_t i = idx[j];
+    if (i < 0 || i >= n_points) continue;
+    const int e = element[i];
+    if (e < 0 || e >= NE) continue;
+    double drop = 0.0;
+    for (int k = 0; k < d; k++) {
+      const double v = pts[i * d + k];
+      drop = fma(L[e * d + k], fmax(hi[k] - v, v - lo[k]), drop);
+    }
+    slack = fmax(slack, margin[i] - drop);
+  }
+  if (whole) whole[c] = slack >= 0.0 ? 1 : 0;
+  if (slack_out) slack_out[c] = slack;
 }
 
 __global__ void k_certify_cells(const int64_t *off, const int64_t *idx, int64_t n_cells,
@@ -404,23 +588,63 @@ __global__ void k_certify_cells(const int64_t *off, const int64_t *idx, int64_t 
   cell_verdict[c] = v;
 }
 
-extern "C" int mf_certify(mf_ctx *ctx, const mf_robot *robot, const mf_scene *scene,
-                          const double *points, int64_t n_points, int32_t d,
-                          const int64_t *cell_off, const int64_t *cell_idx, int64_t n_cells,
-                          uint8_t *point_verdict, double *margin, uint8_t *cell_verdict,
-                          void *stream) {
+// Lipschitz table L[e][k] of the robot's elements (host, FP64, from the DH
+// parameters and sphere centres): the sum of the link lengths
+// sqrt(d_m^2 + a_m^2) from joint k to the element's link, plus |centre| for a
+// sphere; 0 for joints after the element's link.  Rounded up by 1e-12
+// relative so that the device sum stays a bound.
+static void lipschitz_table(int NL, const std::vector<double> &dh, bool caps, int NS,
+                            const std::vector<int32_t> &sl, const std::vector<double> &sc,
+                            std::vector<double> &L) {
+  const int NC = caps ? NL : 0, NE = NC + NS;
+  L.assign((size_t)NE * NL, 0.0);
+  for (int e = 0; e < NE; e++) {
+    const int link = e < NC ? e : sl[e - NC];
+    double extra = 0.0;
+    if (e >= NC) {
+      const double *c = &sc[3 * (e - NC)];
+      extra = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    }
+    for (int k = 0; k <= link && k < NL; k++) {
+      double s = extra;
+      for (int m = k; m <= link; m++) s += std::hypot(dh[4 * m + 1], dh[4 * m + 2]);
+      L[(size_t)e * NL + k] = s * (1.0 + 1e-12);
+    }
+  }
+}
+
+extern "C" int mf_certify_ex(mf_ctx *ctx, const mf_robot *robot, const mf_scene *scene,
+                             const double *points, int64_t n_points, int32_t d,
+                             const int64_t *cell_off, const int64_t *cell_idx, int64_t n_cells,
+                             const mf_certify_out *out, void *stream) {
   if (!ctx) return MF_ERR_INVALID;
-  if (!robot || !scene || d < 1 || d > MF_MAXD || robot->n_links != d || n_points < 0 ||
-      n_cells < 0 || scene->n < 0 || scene->n > CERT_MAX_OBS || !robot->dh || !robot->radius ||
+  const bool want_cells = out && (out->cell_verdict || out->cell_whole || out->cell_slack);
+  if (!robot || !scene || !out || d < 1 || d > MF_MAXD || robot->n_links != d || n_points < 0 ||
+      n_cells < 0 || scene->n < 0 || scene->n > CERT_MAX_OBS || !robot->dh ||
+      robot->n_spheres < 0 || robot->n_spheres > MF_MAX_SPHERES ||
+      (robot->n_spheres > 0 &&
+       (!robot->sphere_link || !robot->sphere_center || !robot->sphere_radius)) ||
+      (!robot->radius && robot->n_spheres == 0) ||
       (scene->n > 0 && (!scene->type || !scene->pose || !scene->dims)) ||
-      (n_points > 0 && (!points || !point_verdict || !margin)) ||
-      (n_cells > 0 && (!cell_off || !cell_idx || !cell_verdict)))
+      (n_points > 0 && (!points || !out->point_verdict || !out->margin)) ||
+      (n_cells > 0 && want_cells && (!cell_off || !cell_idx)))
     return mf_set_error(ctx, MF_ERR_INVALID, "mf_certify: bad arguments");
   cudaSetDevice(ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
-  unsigned *bad = (unsigned *)mf_ctx_buffer(ctx, MF_SLOT_CERT, 256 + 128 * sizeof(double2));
-  if (!bad) return MF_ERR_OOM;
-  const double2 *sctab = (const double2 *)((char *)bad + 256);
+  const int NL = robot->n_links, NS = robot->n_spheres;
+  const int NE = (robot->radius ? NL : 0) + NS;
+  const bool whole = n_cells > 0 && (out->cell_whole || out->cell_slack);
+  // scratch: error word, the sin/cos table, the Lipschitz table, and the
+  // per-point elements when the caller wants a whole-cell verdict only
+  const size_t o_tab = 256, o_L = o_tab + 128 * sizeof(double2);
+  const size_t o_el = o_L + (((size_t)NE * NL * 8 + 255) & ~(size_t)255);
+  const size_t need_el = whole && !out->element ? (size_t)n_points * 2 : 0;
+  char *scr = (char *)mf_ctx_buffer(ctx, MF_SLOT_CERT, o_el + need_el + 256);
+  if (!scr) return MF_ERR_OOM;
+  unsigned *bad = (unsigned *)scr;
+  const double2 *sctab = (const double2 *)(scr + o_tab);
+  double *dL = (double *)(scr + o_L);
+  int16_t *elem = out->element ? out->element : (need_el ? (int16_t *)(scr + o_el) : nullptr);
   cudaMemsetAsync(bad, 0, sizeof(unsigned), st);
   {
     // (sin, cos)(j pi / 64), rounded from extended precision
@@ -438,18 +662,49 @@ extern "C" int mf_certify(mf_ctx *ctx, const mf_robot *robot, const mf_scene *sc
                            "mf_certify table");
     if (rc) return rc;
   }
+  std::vector<double> hL;
+  if (whole) {
+    // the table needs the DH parameters and sphere centres on the host
+    std::vector<double> hdh((size_t)NL * 4), hsc((size_t)NS * 3);
+    std::vector<int32_t> hsl(NS);
+    int rc = mf_cuda_check(ctx, cudaMemcpyAsync(hdh.data(), robot->dh, hdh.size() * 8,
+                                                cudaMemcpyDeviceToHost, st), "mf_certify dh");
+    if (!rc && NS)
+      rc = mf_cuda_check(ctx, cudaMemcpyAsync(hsc.data(), robot->sphere_center, hsc.size() * 8,
+                                              cudaMemcpyDeviceToHost, st), "mf_certify spheres");
+    if (!rc && NS)
+      rc = mf_cuda_check(ctx, cudaMemcpyAsync(hsl.data(), robot->sphere_link, hsl.size() * 4,
+                                              cudaMemcpyDeviceToHost, st), "mf_certify spheres");
+    if (!rc) rc = mf_cuda_check(ctx, cudaStreamSynchronize(st), "mf_certify robot");
+    if (rc) return rc;
+    for (int s = 0; s < NS; s++)
+      if (hsl[s] < 0 || hsl[s] >= NL)
+        return mf_set_error(ctx, MF_ERR_INVALID, "mf_certify: sphere %d on link %d", s, hsl[s]);
+    lipschitz_table(NL, hdh, robot->radius != nullptr, NS, hsl, hsc, hL);
+    if (!hL.empty()) {
+      rc = mf_cuda_check(ctx, cudaMemcpyAsync(dL, hL.data(), hL.size() * 8, cudaMemcpyHostToDevice, st),
+                         "mf_certify lipschitz");
+      if (rc) return rc;
+    }
+  }
   if (n_points > 0) {
     MfProfScope ps(ctx, MF_PH_CERT_PTS, st, 1, n_points);
     const unsigned g = (unsigned)((n_points + CERT_THREADS - 1) / CERT_THREADS);
-    k_certify_points<<<g, CERT_THREADS, 0, st>>>(robot->n_links, robot->dh, robot->radius,
-                                                 scene->n, scene->type, scene->pose, scene->dims,
-                                                 points, n_points, d, sctab, point_verdict,
-                                                 margin);
+    k_certify_points<<<g, CERT_THREADS, 0, st>>>(
+        NL, robot->dh, robot->radius, NS, robot->sphere_link, robot->sphere_center,
+        robot->sphere_radius, scene->n, scene->type, scene->pose, scene->dims, points, n_points,
+        d, sctab, out->point_verdict, out->margin, elem);
   }
-  if (n_cells > 0) {
+  if (n_cells > 0 && out->cell_verdict) {
     MfProfScope ps(ctx, MF_PH_CERT_CELLS, st, 1, n_cells);
     k_certify_cells<<<(unsigned)((n_cells + 255) / 256), 256, 0, st>>>(
-        cell_off, cell_idx, n_cells, point_verdict, n_points, cell_verdict, bad);
+        cell_off, cell_idx, n_cells, out->point_verdict, n_points, out->cell_verdict, bad);
+  }
+  if (whole) {
+    MfProfScope ps(ctx, MF_PH_CERT_CELLS, st, 1, n_cells);
+    k_certify_cells_whole<<<(unsigned)((n_cells + 255) / 256), 256, 0, st>>>(
+        cell_off, cell_idx, n_cells, points, d, out->margin, elem, dL, NE, n_points,
+        out->cell_whole, out->cell_slack, bad);
   }
   int rc = mf_cuda_check(ctx, cudaGetLastError(), "mf_certify launch");
   if (rc) return rc;
@@ -462,4 +717,20 @@ extern "C" int mf_certify(mf_ctx *ctx, const mf_robot *robot, const mf_scene *sc
   mf_prof_collect(ctx);
   if (hb) return mf_set_error(ctx, MF_ERR_INVALID, "cell_edge_idx holds an index outside [0, n_points)");
   return MF_OK;
+}
+
+extern "C" int mf_certify(mf_ctx *ctx, const mf_robot *robot, const mf_scene *scene,
+                          const double *points, int64_t n_points, int32_t d,
+                          const int64_t *cell_off, const int64_t *cell_idx, int64_t n_cells,
+                          uint8_t *point_verdict, double *margin, uint8_t *cell_verdict,
+                          void *stream) {
+  if (!ctx) return MF_ERR_INVALID;
+  if (n_cells > 0 && !cell_verdict)
+    return mf_set_error(ctx, MF_ERR_INVALID, "mf_certify: bad arguments");
+  mf_certify_out o = {};
+  o.point_verdict = point_verdict;
+  o.margin = margin;
+  o.cell_verdict = cell_verdict;
+  return mf_certify_ex(ctx, robot, scene, points, n_points, d, cell_off, cell_idx, n_cells, &o,
+                       stream);
 }

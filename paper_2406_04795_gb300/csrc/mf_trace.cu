@@ -145,7 +145,10 @@ __global__ void k_seed_edges(MfFrame F, MfTraceBufs B, const double *seeds, int6
   load_y(y, d, vi);
   for (int i = 0; i < d; i++) {
     const bool in_i = vertex_in(F, vi);
-    const double fi = in_i ? lookup_f(F, B, vi) : 0.0;
+    // f is known at a vertex only if it belongs to an in-box edge: looked up
+    // when the first such edge appears
+    double fi = 0.0;
+    bool have_fi = false;
     uint32_t mask = 0;
     int32_t vj[MF_MAXD];
     load_y(vi, d, vj);
@@ -153,6 +156,10 @@ __global__ void k_seed_edges(MfFrame F, MfTraceBufs B, const double *seeds, int6
       mask |= 1u << perm[j - 1];
       vj[perm[j - 1]] += 1;
       if (!in_i || !vertex_in(F, vj)) continue;
+      if (!have_fi) {
+        fi = lookup_f(F, B, vi);
+        have_fi = true;
+      }
       const double fj = lookup_f(F, B, vj);
       if ((fi >= 0.0) == (fj >= 0.0)) continue;
       any = true;

@@ -31,13 +31,16 @@ MF_ROOTS_FP64_EXACT = 4
 
 MF_BOX = 0
 MF_SPHERE = 1
+MF_CYLINDER = 2
+MF_MAX_SPHERES = 64
 
 EXPORTS = ("mf_ctx_create", "mf_ctx_destroy", "mf_last_error", "mf_ctx_bytes", "mf_locate",
            "mf_eval", "mf_trace", "mf_trace_fetch", "mf_certify", "mf_ctx_set_profiling",
            "mf_ctx_get_stats", "mf_trace_noalloc", "mf_trace_batch", "mf_domain_table",
            "mf_server_create", "mf_server_destroy", "mf_server_submit", "mf_server_step",
            "mf_server_status", "mf_server_fetch", "mf_server_done", "mf_autotune", "mf_ctx_set_tune",
-           "mf_ctx_get_tune", "mf_vertex_keys", "mf_probe_rates", "mf_diag_exp")
+           "mf_ctx_get_tune", "mf_vertex_keys", "mf_probe_rates", "mf_diag_exp",
+           "mf_certify_ex")
 
 MF_PHASES = 12
 PHASE_NAMES = ("prepare", "seeds", "expand_vertices", "eval", "expand_edges", "roots", "cells",
@@ -75,7 +78,15 @@ class mf_trace_out(C.Structure):
 
 
 class mf_robot(C.Structure):
-    _fields_ = [("n_links", C.c_int32), ("dh", C.c_void_p), ("radius", C.c_void_p)]
+    _fields_ = [("n_links", C.c_int32), ("dh", C.c_void_p), ("radius", C.c_void_p),
+                ("n_spheres", C.c_int32), ("sphere_link", C.c_void_p),
+                ("sphere_center", C.c_void_p), ("sphere_radius", C.c_void_p)]
+
+
+class mf_certify_out(C.Structure):
+    _fields_ = [("point_verdict", C.c_void_p), ("margin", C.c_void_p), ("element", C.c_void_p),
+                ("cell_verdict", C.c_void_p), ("cell_whole", C.c_void_p),
+                ("cell_slack", C.c_void_p)]
 
 
 class mf_scene(C.Structure):
@@ -185,6 +196,9 @@ def load(build_if_missing: bool = True):
     L.mf_trace_noalloc.restype = C.c_int
     L.mf_trace_noalloc.argtypes = [P(mf_rbf), P(mf_domain), P(mf_trace_opts), V, C.c_int64,
                                    P(mf_trace_out), V]
+    L.mf_certify_ex.restype = C.c_int
+    L.mf_certify_ex.argtypes = [V, P(mf_robot), P(mf_scene), V, C.c_int64, C.c_int32, V, V,
+                                C.c_int64, P(mf_certify_out), V]
     L.mf_probe_rates.restype = C.c_int
     L.mf_probe_rates.argtypes = [V, P(mf_rates), V]
     L.mf_diag_exp.restype = C.c_int
@@ -353,6 +367,13 @@ def mf_autotune(ctx, rbf: mf_rbf, dom: mf_domain, opts: mf_trace_opts, seeds_ptr
     _check(ctx, load().mf_autotune(ctx, C.byref(rbf), C.byref(dom), C.byref(opts), seeds_ptr,
                                    n_seeds, C.byref(t), stream))
     return t
+
+
+def mf_certify_ex(ctx, robot: mf_robot, scene: mf_scene, points_ptr, n_points, d, off_ptr,
+                  idx_ptr, n_cells, out: mf_certify_out, stream=0):
+    return _check(ctx, load().mf_certify_ex(ctx, C.byref(robot), C.byref(scene), points_ptr,
+                                            n_points, d, off_ptr, idx_ptr, n_cells, C.byref(out),
+                                            stream))
 
 
 def mf_probe_rates(ctx, stream=0) -> mf_rates:

@@ -1,7 +1,8 @@
 """One proof = one pass of the traced path on one workload: ``mf_trace`` (locate
 seeds, breadth-first tracing, roots, cells and their CSR) followed by
-``mf_certify`` (forward kinematics and capsule/obstacle checks of every
-intersection point, AND over each cell).  Inputs stay resident on the device;
+``mf_certify_ex`` (forward kinematics and capsule/obstacle checks of every
+intersection point, AND over each cell, and the whole-cell certificate of each
+cell's manifold piece).  Inputs stay resident on the device;
 outputs are preallocated after the first call so that repeated steps allocate
 nothing."""
 from __future__ import annotations
@@ -60,6 +61,7 @@ class Proof:
         self.otype, self.opose, self.odims = t(w.obs_type, torch.int32), t(w.obs_pose), t(w.obs_dims)
         self.outputs = None
         self.last = None
+        self.whole = None
 
     def step(self, stream=None):
         w = self.w
@@ -78,8 +80,13 @@ class Proof:
                 self.sizing = {k: int(v * 2) for k, v in self.sizing.items()}
                 self.outputs = None
         self.outputs = r["_buffers"]
-        v, m, cv = self.ctx.certify(self.dh, self.radius, self.otype, self.opose, self.odims,
-                                    r["points"], r["cell_off"], r["cell_idx"], stream=stream)
+        # points (verdicts, margins), the AND over each cell's points, and the
+        # whole-cell (Lipschitz) certificate of each cell's manifold piece
+        c = self.ctx.certify_ex(self.dh, self.radius, self.otype, self.opose, self.odims,
+                                r["points"], r["cell_off"], r["cell_idx"], whole=True,
+                                stream=stream)
+        v, m, cv = c["verdict"], c["margin"], c["cell_verdict"]
+        self.whole = c.get("cell_whole")
         self.last = (r, v, m, cv)
         return r, v, m, cv
 

@@ -44,7 +44,7 @@ def test_binding_structs_match_header_layout(tmp_path):
     """Every ctypes struct has the C compiler's size and field offsets."""
     from paper_2406_04795_gb300 import mf
     structs = [mf.mf_rbf, mf.mf_domain, mf.mf_trace_opts, mf.mf_trace_out, mf.mf_robot,
-               mf.mf_scene, mf.mf_stats, mf.mf_tune, mf.mf_rates]
+               mf.mf_scene, mf.mf_stats, mf.mf_tune, mf.mf_rates, mf.mf_certify_out]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mf.h"', "int main(void){"]
     expect = []
     for s in structs:
