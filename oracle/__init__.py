@@ -112,6 +112,13 @@ def lib():
         L.or_certify.argtypes = [P(Robot), P(Scene), P(C.c_double), C.c_int64, C.c_int32,
                                  P(C.c_int64), P(C.c_int64), C.c_int64,
                                  P(C.c_uint8), P(C.c_double), P(C.c_uint8)]
+        L.or_subdiv_template.restype = C.c_int
+        L.or_subdiv_template.argtypes = [C.c_int, C.c_int, P(C.c_int32), P(C.c_int64),
+                                         P(C.c_int32), P(C.c_int64)]
+        L.or_subdiv.restype = C.c_int
+        L.or_subdiv.argtypes = [P(Rbf), C.c_double, C.c_int, P(C.c_double), P(C.c_double),
+                                P(C.c_double), P(C.c_double), C.c_int64, C.c_int,
+                                P(TraceResult), P(C.c_int64)]
         L.or_fk_frames.argtypes = [P(Robot), P(C.c_double), P(C.c_double)]
         L.or_lipschitz.argtypes = [P(Robot), P(C.c_double)]
         L.or_certify_ex.argtypes = [P(Robot), P(Scene), P(C.c_double), C.c_int64, C.c_int32,
@@ -271,6 +278,48 @@ def trace(sv, alpha, gamma, b, lam, o, lo, hi, seeds, roots=True, cells=True, ma
                    cell_perm=_arr(r.cell_perm, Cn * d, np.uint8).reshape(Cn, d),
                    cell_off=off, cell_idx=_arr(r.cell_idx, int(off[-1]) if Cn else 0, np.int64))
     lib().or_trace_free(C.byref(r))
+    return out
+
+
+def subdiv_template(d, k):
+    """The local triangulation of the subdivided reference n-simplex
+    (Sec. V-B): vertices [nv][d] (local coordinates v') and edges [ne] as
+    (vertex index, local mask M')."""
+    nv, ne = C.c_int64(), C.c_int64()
+    lib().or_subdiv_template(d, k, None, C.byref(nv), None, C.byref(ne))
+    v = np.zeros((max(nv.value, 1), d), np.int32)
+    e = np.zeros((max(ne.value, 1), 2), np.int32)
+    lib().or_subdiv_template(d, k, _p(v, C.c_int32), C.byref(nv), _p(e, C.c_int32), C.byref(ne))
+    return v[:nv.value], e[:ne.value]
+
+
+def subdiv(sv, alpha, gamma, b, lam, k, o, lo, hi, seeds, roots=True):
+    """Batch triangulation (Sec. V-B): the crossing edges of the scale-lam
+    local triangulations of the crossing n-simplices of the coarse trace at
+    scale k * lam.  Returns the trace dict (no cells) and 'n_coarse_cells'."""
+    h = _RbfHold(sv, alpha, gamma, b)
+    d = h.sv.shape[1]
+    o, lo, hi = _f64(o), _f64(lo), _f64(hi)
+    seeds = _f64(np.atleast_2d(seeds)).reshape(-1, d)
+    res = TraceResult()
+    nco = C.c_int64()
+    rc = lib().or_subdiv(C.byref(h.s), float(lam), int(k), _p(o, C.c_double), _p(lo, C.c_double),
+                         _p(hi, C.c_double), _p(seeds, C.c_double), seeds.shape[0], int(roots),
+                         C.byref(res), C.byref(nco))
+    if rc:
+        raise RuntimeError("or_subdiv failed")
+    E = res.n_edges
+    out = dict(
+        d=d,
+        edge_y=_arr(res.edge_y, E * d, np.int32).reshape(E, d),
+        edge_mask=_arr(res.edge_mask, E, np.uint32),
+        edge_f=_arr(res.edge_f, 2 * E, np.float64).reshape(E, 2),
+        edge_t=_arr(res.edge_t, E, np.float64),
+        edge_pt=_arr(res.edge_pt, E * d, np.float64).reshape(E, d),
+        edge_multiroot=_arr(res.edge_multiroot, E, np.uint8),
+        n_vertices=res.n_vertices, n_near_zero=res.n_near_zero, n_dead_seeds=res.n_dead_seeds,
+        levels=res.levels, n_coarse_cells=int(nco.value))
+    lib().or_trace_free(C.byref(res))
     return out
 
 

@@ -681,6 +681,171 @@ out:
 }
 
 /* ------------------------------------------------------------------------ */
+/* Batch triangulation (Sec. V-B, Figs. 5-6, Eqs. bc and local).             */
+/* ------------------------------------------------------------------------ */
+/* Inside test of a local vertex v' of the subdivided n-simplex (Eq. local,
+ * read with "no less than 0": the closed simplex, so that the local edges on
+ * its faces, such as the first edge of Fig. 5, are kept):
+ *   k - v'_0 >= 0,  v'_{i-1} - v'_i >= 0,  v'_{n-1} >= 0. */
+static int local_inside(int d, int k, const int32_t *m) {
+  if (k - m[0] < 0) return 0;
+  for (int i = 1; i < d; i++)
+    if (m[i - 1] - m[i] < 0) return 0;
+  return m[d - 1] >= 0;
+}
+
+/* The local triangulation of the subdivided reference n-simplex (computed
+ * once and shared by all n-simplices, Sec. V-B): its vertices (all v' that
+ * pass the inside test) and its edges (v', v' + e(M') for a non-empty local
+ * mask M', both inside).  verts [nv][d], edges [ne][2] = (vertex index, M');
+ * NULL arrays only count.  Returns 0. */
+int or_subdiv_template(int d, int k, int32_t *verts, int64_t *nv, int32_t *edges, int64_t *ne) {
+  int64_t cv = 0, ce = 0;
+  int32_t m[OR_MAXD], m2[OR_MAXD];
+  /* every v' in [0, k]^d in lexicographic order, kept if inside */
+  int64_t total = 1;
+  for (int i = 0; i < d; i++) total *= (k + 1);
+  for (int64_t code = 0; code < total; code++) {
+    int64_t c = code;
+    for (int i = d - 1; i >= 0; i--) { m[i] = (int32_t)(c % (k + 1)); c /= (k + 1); }
+    if (!local_inside(d, k, m)) continue;
+    for (uint32_t M = 1; M < (1u << d); M++) {
+      for (int i = 0; i < d; i++) m2[i] = m[i] + (int32_t)((M >> i) & 1u);
+      if (!local_inside(d, k, m2)) continue;
+      if (edges) { edges[2 * ce] = (int32_t)cv; edges[2 * ce + 1] = (int32_t)M; }
+      ce++;
+    }
+    if (verts) for (int i = 0; i < d; i++) verts[cv * d + i] = m[i];
+    cv++;
+  }
+  *nv = cv;
+  *ne = ce;
+  return 0;
+}
+
+/* Batch triangulation: trace at the coarse scale k * lam (same offset o),
+ * take its crossing n-simplices, and in each the local triangulation of
+ * scale lam: local vertex v' maps to the lattice vertex
+ *   y = k z + sum_j v'_j e(pi_j)                    (Eq. bc, lattice units)
+ * of the n-simplex (z, pi), local edge (v', M') to the edge (y, pi(M')).
+ * The result is every such edge with both vertices in the box and a sign
+ * change, de-duplicated (edges on shared faces come from several
+ * n-simplices), with roots as in or_trace.  res->levels = the coarse trace's
+ * BFS levels; *n_coarse receives its crossing n-simplices. */
+int or_subdiv(const or_rbf *rbf, double lam, int k, const double *o, const double *lo,
+              const double *hi, const double *seeds, int64_t n_seeds, int want_roots,
+              or_trace_result *res, int64_t *n_coarse) {
+  int d = rbf->d;
+  memset(res, 0, sizeof(*res));
+  if (d < 2 || d > OR_MAXD || !(lam > 0.0) || k < 1 || k > 64) return -1;
+  or_trace_result coarse;
+  if (or_trace(rbf, k * lam, o, lo, hi, seeds, n_seeds, 0, 1, 0, &coarse)) return -1;
+  *n_coarse = coarse.n_cells;
+  int64_t nv, ne;
+  or_subdiv_template(d, k, NULL, &nv, NULL, &ne);
+  int32_t *tv = (int32_t *)malloc((size_t)(nv ? nv : 1) * d * sizeof(int32_t));
+  int32_t *te = (int32_t *)malloc((size_t)(ne ? ne : 1) * 2 * sizeof(int32_t));
+  tctx c;
+  c.d = d; c.lam = lam; c.o = o; c.lo = lo; c.hi = hi; c.rbf = rbf; c.n_near_zero = 0;
+  or_set eset;
+  int rc = -1, have_v = 0, have_e = 0;
+  size_t cap = 1024;
+  double *ef = (double *)malloc(cap * 2 * sizeof(double));
+  if (!tv || !te || !ef) goto out0;
+  or_subdiv_template(d, k, tv, &nv, te, &ne);
+  if (set_init(&c.vmap, sizeof(vrec), sizeof(int32_t) * OR_MAXD)) goto out0;
+  have_v = 1;
+  if (set_init(&eset, sizeof(or_simplex), sizeof(or_simplex))) goto out0;
+  have_e = 1;
+  for (int64_t ci = 0; ci < coarse.n_cells; ci++) {
+    const int32_t *z = coarse.cell_y + ci * d;
+    const uint8_t *pi = coarse.cell_perm + ci * d;
+    for (int64_t ei = 0; ei < ne; ei++) {
+      const int32_t *m = tv + (int64_t)te[2 * ei] * d;
+      uint32_t Ml = (uint32_t)te[2 * ei + 1];
+      or_simplex e;
+      or_simplex_zero(&e);
+      for (int i = 0; i < d; i++) e.y[i] = k * z[i];
+      uint32_t M = 0;
+      for (int j = 0; j < d; j++) {
+        e.y[pi[j]] += m[j];
+        if ((Ml >> j) & 1u) M |= 1u << pi[j];
+      }
+      e.k = 1;
+      e.part[0] = M;
+      e.part[1] = ((2u << d) - 1u) & ~M;
+      double f0, f1;
+      int x = edge_crosses(&c, &e, &f0, &f1);
+      if (x < 0) goto out0;
+      if (!x) continue;
+      int ins;
+      long idx = set_insert(&eset, &e, &ins);
+      if (idx < 0) goto out0;
+      if (ins) {
+        if ((size_t)idx >= cap) {
+          cap *= 2;
+          ef = (double *)realloc(ef, cap * 2 * sizeof(double));
+          if (!ef) goto out0;
+        }
+        ef[2 * idx] = f0;
+        ef[2 * idx + 1] = f1;
+      }
+    }
+  }
+  {
+    int64_t E = (int64_t)eset.n;
+    res->d = d;
+    res->n_edges = E;
+    res->edge_y = (int32_t *)malloc((size_t)(E ? E : 1) * d * sizeof(int32_t));
+    res->edge_mask = (uint32_t *)malloc((size_t)(E ? E : 1) * sizeof(uint32_t));
+    res->edge_level = (int32_t *)calloc((size_t)(E ? E : 1), sizeof(int32_t));
+    res->edge_f = (double *)malloc((size_t)(E ? E : 1) * 2 * sizeof(double));
+    res->edge_t = (double *)calloc((size_t)(E ? E : 1), sizeof(double));
+    res->edge_pt = (double *)calloc((size_t)(E ? E : 1) * d, sizeof(double));
+    res->edge_multiroot = (uint8_t *)calloc((size_t)(E ? E : 1), 1);
+    if (!res->edge_y || !res->edge_mask || !res->edge_level || !res->edge_f || !res->edge_t ||
+        !res->edge_pt || !res->edge_multiroot)
+      goto out0;
+    for (int64_t i = 0; i < E; i++) {
+      const or_simplex *e = &((or_simplex *)eset.recs)[i];
+      for (int q = 0; q < d; q++) res->edge_y[i * d + q] = e->y[q];
+      res->edge_mask[i] = e->part[0];
+      res->edge_f[2 * i] = ef[2 * i];
+      res->edge_f[2 * i + 1] = ef[2 * i + 1];
+    }
+    if (want_roots) {
+#pragma omp parallel for schedule(dynamic, 16)
+      for (int64_t i = 0; i < E; i++) {
+        const or_simplex *e = &((or_simplex *)eset.recs)[i];
+        int32_t v[2 * OR_MAXD];
+        double x1[OR_MAXD], x2[OR_MAXD];
+        or_simplex_vertices(d, e, v);
+        or_vertex_x(d, lam, o, v, x1);
+        or_vertex_x(d, lam, o, v + d, x2);
+        double t = root_bisect(rbf, d, x1, x2, ef[2 * i]);
+        res->edge_t[i] = t;
+        for (int q = 0; q < d; q++) res->edge_pt[i * d + q] = seg_point(x1[q], x2[q], t);
+        res->edge_multiroot[i] = (uint8_t)multiroot(rbf, d, x1, x2);
+      }
+    }
+    res->levels = coarse.levels;
+    res->n_vertices = (int64_t)c.vmap.n;
+    res->n_near_zero = c.n_near_zero;
+    res->n_dead_seeds = coarse.n_dead_seeds;
+  }
+  rc = 0;
+out0:
+  free(tv);
+  free(te);
+  free(ef);
+  if (have_e) set_free(&eset);
+  if (have_v) set_free(&c.vmap);
+  or_trace_free(&coarse);
+  if (rc) or_trace_free(res);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Certification (Sec. V-C, App. A): forward kinematics of a serial DH arm   */
 /* and the exact capsule/obstacle distance.                                   */
 /* ------------------------------------------------------------------------ */

@@ -232,3 +232,28 @@ def brute_counts(d, lam, c, o, lo, hi, fvals_fn, seeds, traced):
     else:
         near = 0
     return len(evaluated), boundary, near
+
+
+def brute_crossing_edges(d, lam, c, o, lo, hi, fvals_fn):
+    """Every lattice edge (y, mask) with both vertices in the box and a sign
+    change of f (binary signs), by enumerating a box of the lattice."""
+    cinv = c * math.sqrt(d + 1)
+    s_lo = float(np.sum(np.asarray(lo) - o))
+    s_hi = float(np.sum(np.asarray(hi) - o))
+    ymin = [int(math.floor(((lo[i] - o[i]) + cinv * s_lo) / lam)) - 2 for i in range(d)]
+    ymax = [int(math.ceil(((hi[i] - o[i]) + cinv * s_hi) / lam)) + 2 for i in range(d)]
+    axes = [np.arange(ymin[i], ymax[i] + 1) for i in range(d)]
+    grid = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, d)
+    X = lattice_x(d, lam, c, o, grid)
+    inb = np.all((X >= np.asarray(lo)[None]) & (X <= np.asarray(hi)[None]), axis=1)
+    Yin = grid[inb]
+    sign = fvals_fn(X[inb]) >= 0.0
+    index = {tuple(y): i for i, y in enumerate(Yin.tolist())}
+    out = set()
+    for mask in range(1, 1 << d):
+        em = np.array([(mask >> i) & 1 for i in range(d)], dtype=np.int64)
+        for i, y in enumerate(Yin.tolist()):
+            j = index.get(tuple(np.asarray(y) + em))
+            if j is not None and sign[i] != sign[j]:
+                out.add((tuple(y), mask))
+    return out
