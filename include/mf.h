@@ -232,6 +232,35 @@ int mf_trace_batch(mf_ctx *ctx, int32_t n, const mf_rbf *rbfs, const mf_domain *
                    const mf_trace_opts *opts, const double *const *seeds, const int64_t *n_seeds,
                    mf_trace_out *outs, void *stream);
 
+/* Batch triangulation (Sec. V-B, Figs. 5-6, Eqs. bc and local).  The
+ * manifold is traced at the coarse scale k * opts->lambda (same offset); each
+ * crossing n-simplex (z, pi) of that trace is then subdivided into the
+ * triangulation of scale opts->lambda inside it: the local vertices v' with
+ * k >= v'_0 >= ... >= v'_{d-1} >= 0 (Eq. local, read as the closed simplex),
+ * mapped to the lattice vertices y = k z + sum_j v'_j e(pi_j) (Eq. bc), and
+ * the local edges between them, the same template for every n-simplex.  The
+ * result is every such edge with both vertices in the box and a sign change,
+ * with its root as mf_trace solves it.  It is the direct trace at
+ * opts->lambda wherever the coarse trace's n-simplices cover the manifold;
+ * it misses fine crossings inside coarse n-simplices whose vertices all
+ * share one sign.
+ *
+ * mf_subdiv_begin runs the coarse trace (capacities from opts, cells wanted)
+ * and keeps its n-simplices in the context; *n_coarse_cells receives their
+ * number.  Each mf_subdiv_next then processes the next cells_per_batch of
+ * them (0 = all at once) into `out` as mf_trace does (edges, end values,
+ * roots and points when opts asks for roots; no cells), with fine tables of
+ * opts->max_edges / max_vertices that start empty every batch: the memory
+ * is bounded by the batch, and an edge on a face shared by n-simplices of
+ * two batches is reported by both.  *cells_left receives the n-simplices
+ * still to do (0: finished; further calls return empty batches).  Any other
+ * tracing, evaluation or tuning call on the context ends the subdivision.
+ * k: 1 .. 16. */
+int mf_subdiv_begin(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom, const mf_trace_opts *opts,
+                    int32_t k, const double *seeds, int64_t n_seeds, int64_t cells_per_batch,
+                    int64_t *n_coarse_cells, void *stream);
+int mf_subdiv_next(mf_ctx *ctx, mf_trace_out *out, int64_t *cells_left, void *stream);
+
 /* Proof server (continuous batching of tracing requests; the paper's
  * planner-side loop is out of scope, this is the serving runtime around the
  * traced path).  The server holds up to max_slots concurrent traces in an HBM

@@ -122,6 +122,47 @@ class Context:
             _buffers=res)
         return result
 
+    def subdiv(self, w, k, precision=mf.MF_FP64, cells_per_batch=0, max_edges=1 << 22,
+               max_vertices=0, max_cells=0, roots=True, exact_roots=False, recheck_band=1e-3,
+               root_tol=1e-12, stream=None, each_batch=None):
+        """Batch triangulation (mf_subdiv_begin / next) of workload w at its
+        lambda with coarse factor k.  max_* size the coarse trace and each
+        batch's fine tables.  Returns the batches' edges concatenated (an
+        edge on a face shared by two batches appears in both) and counters;
+        each_batch(batch_dict) is called per batch when given."""
+        r, keep = self.rbf(w.sv, w.alpha, w.gamma, w.b)
+        d = r.d
+        dom = self.domain(w.lo, w.hi, w.offset)
+        sd = _dev(w.seeds, torch.float64, self.device).reshape(-1, d)
+        flags = (mf.MF_WANT_ROOTS if roots else 0) | (mf.MF_ROOTS_FP64_EXACT if exact_roots else 0)
+        opts = mf.mf_trace_opts(float(w.lam), 1 << 24, int(precision), float(recheck_band),
+                                float(root_tol), int(max_edges), int(max_vertices), int(max_cells),
+                                flags)
+        st = _stream_handle(stream)
+        n_coarse = mf.mf_subdiv_begin(self.h, r, dom, opts, int(k), sd.data_ptr(), sd.shape[0],
+                                      int(cells_per_batch), st)
+        res = self._alloc_outputs(d, int(max_edges), 1, 1)
+        out = self._out_struct(res, d)
+        parts, counts = [], dict(n_vertices=0, n_recheck=0, n_near_zero=0, root_evals=0, batches=0)
+        left = n_coarse
+        while left > 0:
+            left = mf.mf_subdiv_next(self.h, out, st)
+            E = out.n_edges
+            b = {k2: res[k2][:E].clone() for k2 in ("edge_y", "edge_mask", "edge_f", "edge_t",
+                                                    "points")}
+            b["n_edges"] = E
+            if each_batch is not None:
+                each_batch(b)
+            parts.append(b)
+            for k2 in ("n_vertices", "n_recheck", "n_near_zero", "root_evals"):
+                counts[k2] += getattr(out, k2)
+            counts["batches"] += 1
+        cat = {k2: (torch.cat([p[k2] for p in parts]) if parts else res[k2][:0])
+               for k2 in ("edge_y", "edge_mask", "edge_f", "edge_t", "points")}
+        cat.update(counts, n_edges=int(sum(p["n_edges"] for p in parts)), n_coarse_cells=n_coarse,
+                   levels=out.levels, n_dead_seeds=out.n_dead_seeds)
+        return cat
+
     def autotune(self, w, precision=mf.MF_FP64, batch_cap=1 << 24, max_edges=1 << 22,
                  max_vertices=0, max_cells=0, recheck_band=1e-3, root_tol=1e-12, stream=None):
         """Times launch variants on a trace of workload w and keeps the

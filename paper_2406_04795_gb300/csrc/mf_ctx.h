@@ -19,6 +19,25 @@ struct MfTraceState {
   uint32_t flags = 0;
 };
 
+// Batch triangulation in progress (mf_subdiv_begin / mf_subdiv_next): the
+// coarse trace's crossing n-simplices and the shared local template live in
+// MF_SLOT_SUBDIV; each batch reuses the trace slots for its fine tables.
+struct MfSubdivState {
+  bool valid = false;
+  MfFrame F;  // the fine frame (scale lambda) with its domain table
+  MfRbfDev R;
+  int32_t k = 0, precision = 0;
+  uint32_t flags = 0;
+  double band = 0.0, tol = 0.0;
+  uint64_t ME = 0, MV = 0;
+  int64_t n_cells = 0, next = 0, per_batch = 0, coarse_levels = 0, dead_seeds = 0;
+  const int32_t *cell_y = nullptr;   // [n_cells][d] coarse cells (z)
+  const uint8_t *cell_perm = nullptr;  // [n_cells][d] (pi)
+  const uint8_t *tv = nullptr;       // [nv][d] local template vertices v'
+  const uint32_t *te = nullptr;      // [ne] local edges: (vertex index << 8) | local mask
+  int32_t nv = 0, ne = 0;
+};
+
 // Event pairs recorded around library launches while profiling is on.
 struct MfProfiler {
   bool on = false;
@@ -38,6 +57,7 @@ struct mf_ctx {
   size_t slot_bytes[MF_NUM_SLOTS] = {};
   MfCounters *h_counters = nullptr;  // pinned host mirror of the device counters
   MfTraceState last;
+  MfSubdivState sub;
   MfProfiler prof;
   MfTune tune;
 };

@@ -1792,6 +1792,7 @@ extern "C" int mf_diag_exp(mf_ctx *ctx, const double *x, int64_t n, double *y_ta
 extern "C" int mf_eval(mf_ctx *ctx, const mf_rbf *rbf, const double *q, int64_t n, int32_t precision,
                        double band, double *f_out, void *stream) {
   if (!ctx) return MF_ERR_INVALID;
+  ctx->sub.valid = false;  // its slots are reused here
   if (n < 0 || (n > 0 && (!q || !f_out)) ||
       (precision != MF_FP64 && precision != MF_MIXED_FP32 && precision != MF_MIXED_BF16))
     return mf_set_error(ctx, MF_ERR_INVALID, "mf_eval: bad arguments");

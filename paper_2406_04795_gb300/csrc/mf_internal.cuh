@@ -446,6 +446,53 @@ __device__ __forceinline__ unsigned long long mf_warp_alloc(unsigned long long *
   return base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
 }
 
+// ------------------------------------------------------------------------
+// Vertex and edge tables of a trace (the tracing and batch-triangulation
+// kernels share them).
+// ------------------------------------------------------------------------
+// Inserts an in-domain vertex into the vertex table; first inserter appends it.
+__device__ __forceinline__ void mf_visit_vertex(const MfFrame &F, const MfTraceBufs &B, const int32_t *w) {
+  const unsigned long long key = mf_vertex_key(F, w);
+  bool won;
+  const uint64_t slot = mf_table_insert<2>(B.vtab_key, B.vtab_mask, key, &won);
+  if (slot == ~0ull) atomicOr(&B.cnt->err_table_full, 1u);
+  const bool take = slot != ~0ull && won;
+  const unsigned long long idx = mf_warp_alloc(&B.cnt->n_vertices, take);
+  if (!take) return;
+  if (idx >= B.max_vertices) { atomicOr(&B.cnt->err_overflow, 1u); return; }
+#pragma unroll
+  for (int k = 0; k < MF_MAXD; k++)
+    if (k < F.d) B.vert_y[idx * F.d + k] = w[k];
+  B.vert_slot[idx] = (uint32_t)slot;
+  if (B.vtab_idx) B.vtab_idx[slot] = (uint32_t)idx;
+}
+
+__device__ __forceinline__ double mf_lookup_f(const MfFrame &F, const MfTraceBufs &B, const int32_t *w) {
+  const uint64_t slot = mf_table_find<2>(B.vtab_key, B.vtab_mask, mf_vertex_key(F, w));
+  if (slot == ~0ull) { atomicOr(&B.cnt->err_missing, 1u); return 0.0; }
+  return mf_vtab_f(B, slot);
+}
+
+// Appends edge (y, mask) with end values (fa at y, fb at y + e(mask)) if new.
+__device__ __forceinline__ void mf_emit_edge(const MfFrame &F, const MfTraceBufs &B, const int32_t *y,
+                                          uint32_t mask, double fa, double fb) {
+  const unsigned long long key = mf_edge_key(F, y, mask);
+  bool won;
+  const uint64_t slot = mf_table_insert<2>(B.etab_key, B.etab_mask, key, &won);
+  if (slot == ~0ull) atomicOr(&B.cnt->err_table_full, 1u);
+  const bool take = slot != ~0ull && won;
+  const unsigned long long idx = mf_warp_alloc(&B.cnt->n_edges, take);
+  if (!take) return;
+  if (idx >= B.max_edges) { atomicOr(&B.cnt->err_overflow, 1u); return; }
+#pragma unroll
+  for (int k = 0; k < MF_MAXD; k++)
+    if (k < F.d) B.edge_y[idx * F.d + k] = y[k];
+  B.edge_mask[idx] = mask;
+  B.edge_f[2 * idx] = fa;
+  B.edge_f[2 * idx + 1] = fb;
+  mf_etab_val(B, slot) = (uint32_t)idx;
+}
+
 __device__ __forceinline__ float mf_warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -538,5 +585,6 @@ enum {
   MF_SLOT_BATCH = 11,
   MF_SLOT_SERVER = 12,
   MF_SLOT_VLIST = 13,
-  MF_NUM_SLOTS = 14
+  MF_SLOT_SUBDIV = 14,
+  MF_NUM_SLOTS = 15
 };

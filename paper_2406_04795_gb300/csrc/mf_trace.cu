@@ -35,49 +35,6 @@ __device__ __forceinline__ void load_y(const int32_t *src, int d, int32_t *y) {
   for (int k = 0; k < MF_MAXD; k++) y[k] = k < d ? src[k] : 0;
 }
 
-// Inserts an in-domain vertex into the vertex table; first inserter appends it.
-__device__ __forceinline__ void visit_vertex(const MfFrame &F, const MfTraceBufs &B, const int32_t *w) {
-  const unsigned long long key = mf_vertex_key(F, w);
-  bool won;
-  const uint64_t slot = mf_table_insert<2>(B.vtab_key, B.vtab_mask, key, &won);
-  if (slot == ~0ull) atomicOr(&B.cnt->err_table_full, 1u);
-  const bool take = slot != ~0ull && won;
-  const unsigned long long idx = mf_warp_alloc(&B.cnt->n_vertices, take);
-  if (!take) return;
-  if (idx >= B.max_vertices) { atomicOr(&B.cnt->err_overflow, 1u); return; }
-#pragma unroll
-  for (int k = 0; k < MF_MAXD; k++)
-    if (k < F.d) B.vert_y[idx * F.d + k] = w[k];
-  B.vert_slot[idx] = (uint32_t)slot;
-  if (B.vtab_idx) B.vtab_idx[slot] = (uint32_t)idx;
-}
-
-__device__ __forceinline__ double lookup_f(const MfFrame &F, const MfTraceBufs &B, const int32_t *w) {
-  const uint64_t slot = mf_table_find<2>(B.vtab_key, B.vtab_mask, mf_vertex_key(F, w));
-  if (slot == ~0ull) { atomicOr(&B.cnt->err_missing, 1u); return 0.0; }
-  return mf_vtab_f(B, slot);
-}
-
-// Appends edge (y, mask) with end values (fa at y, fb at y + e(mask)) if new.
-__device__ __forceinline__ void emit_edge(const MfFrame &F, const MfTraceBufs &B, const int32_t *y,
-                                          uint32_t mask, double fa, double fb) {
-  const unsigned long long key = mf_edge_key(F, y, mask);
-  bool won;
-  const uint64_t slot = mf_table_insert<2>(B.etab_key, B.etab_mask, key, &won);
-  if (slot == ~0ull) atomicOr(&B.cnt->err_table_full, 1u);
-  const bool take = slot != ~0ull && won;
-  const unsigned long long idx = mf_warp_alloc(&B.cnt->n_edges, take);
-  if (!take) return;
-  if (idx >= B.max_edges) { atomicOr(&B.cnt->err_overflow, 1u); return; }
-#pragma unroll
-  for (int k = 0; k < MF_MAXD; k++)
-    if (k < F.d) B.edge_y[idx * F.d + k] = y[k];
-  B.edge_mask[idx] = mask;
-  B.edge_f[2 * idx] = fa;
-  B.edge_f[2 * idx + 1] = fb;
-  mf_etab_val(B, slot) = (uint32_t)idx;
-}
-
 __device__ __forceinline__ bool vertex_in(const MfFrame &F, const int32_t *v) {
   return mf_vertex_in(F, v);
 }
@@ -116,7 +73,7 @@ __global__ void k_seed_vertices(MfFrame F, MfTraceBufs B, const double *seeds, i
   }
   if (n_in < 2) return;
   for (int j = 0; j <= d; j++) {
-    if (vertex_in(F, v)) visit_vertex(F, B, v);
+    if (vertex_in(F, v)) mf_visit_vertex(F, B, v);
     if (j < d) v[perm[j]] += 1;
   }
 }
@@ -157,13 +114,13 @@ __global__ void k_seed_edges(MfFrame F, MfTraceBufs B, const double *seeds, int6
       vj[perm[j - 1]] += 1;
       if (!in_i || !vertex_in(F, vj)) continue;
       if (!have_fi) {
-        fi = lookup_f(F, B, vi);
+        fi = mf_lookup_f(F, B, vi);
         have_fi = true;
       }
-      const double fj = lookup_f(F, B, vj);
+      const double fj = mf_lookup_f(F, B, vj);
       if ((fi >= 0.0) == (fj >= 0.0)) continue;
       any = true;
-      emit_edge(F, B, vi, mask, fi, fj);
+      mf_emit_edge(F, B, vi, mask, fi, fj);
     }
     vi[perm[i]] += 1;
   }
@@ -219,7 +176,7 @@ __device__ __forceinline__ unsigned expand_vertices_item(const MfFrame &F, const
   else if (kind == 1) mf_add_mask(d, w, S | M, 1);
   else mf_add_mask(d, w, M, -1);
   if (vertex_in(F, w)) {
-    visit_vertex(F, B, w);
+    mf_visit_vertex(F, B, w);
     return 0;
   }
   return 1;
@@ -239,21 +196,21 @@ __device__ __forceinline__ void expand_edges_item(const MfFrame &F, const MfTrac
   else mf_add_mask(d, w, M, -1);
   if (!vertex_in(F, w)) return;
   const double f0 = B.edge_f[2 * e], f1 = B.edge_f[2 * e + 1];
-  const double fw = lookup_f(F, B, w);
+  const double fw = mf_lookup_f(F, B, w);
   const bool cross0 = (fw >= 0.0) != (f0 >= 0.0);
   if (kind == 0) {
-    if (cross0) emit_edge(F, B, y, M, f0, fw);
-    else emit_edge(F, B, w, S & ~M, fw, f1);
+    if (cross0) mf_emit_edge(F, B, y, M, f0, fw);
+    else mf_emit_edge(F, B, w, S & ~M, fw, f1);
   } else if (kind == 1) {
     if (cross0) {
-      emit_edge(F, B, y, S | M, f0, fw);
+      mf_emit_edge(F, B, y, S | M, f0, fw);
     } else {
       mf_add_mask(d, y, S, 1);
-      emit_edge(F, B, y, M, f1, fw);
+      mf_emit_edge(F, B, y, M, f1, fw);
     }
   } else {
-    if (cross0) emit_edge(F, B, w, M, fw, f0);
-    else emit_edge(F, B, w, M | S, fw, f1);
+    if (cross0) mf_emit_edge(F, B, w, M, fw, f0);
+    else mf_emit_edge(F, B, w, M | S, fw, f1);
   }
 }
 
@@ -1076,6 +1033,10 @@ void mf_exclusive_scan(const int64_t *in, int64_t *out, int64_t n, int64_t *scra
   exclusive_scan(in, out, n, scratch, st);
 }
 uint64_t mf_next_pow2(uint64_t x) { return next_pow2(x); }
+int mf_setup_buffers(mf_ctx *ctx, int d, uint64_t ME, uint64_t MV, uint64_t MC, bool mixed, int n_sv,
+                     MfTraceBufs *B);
+int mf_build_domain_table(mf_ctx *ctx, MfFrame *F, cudaStream_t st);
+int mf_read_counters(mf_ctx *ctx, const MfTraceBufs &B, cudaStream_t st);
 void mf_launch_cells_fill(const MfFrame &F, const MfTraceBufs &B, uint64_t n_cells, cudaStream_t st) {
   if (n_cells == 0) return;
   k_cells_edges<true><<<(unsigned)((n_cells + 255) / 256), 256, 0, st>>>(F, B, n_cells, B.cell_off);
@@ -1234,6 +1195,7 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
                         mf_trace_out *out, void *stream) {
   if (!ctx) return MF_ERR_INVALID;
   ctx->last.valid = false;
+  ctx->sub.valid = false;  // its slots are reused here
   if (!rbf || !dom || !opts || !out || n_seeds < 0 || (n_seeds > 0 && !seeds))
     return mf_set_error(ctx, MF_ERR_INVALID, "mf_trace: NULL argument");
   if (!(opts->lambda > 0.0) || !std::isfinite(opts->lambda))
@@ -1426,4 +1388,16 @@ extern "C" int mf_vertex_keys(int32_t d, double lambda, const mf_domain *dom, co
     if (in_range) in_range[i] = mf_vertex_in_packing(F, y + i * d) ? 1 : 0;
   }
   return MF_OK;
+}
+
+// Host helpers shared with the batch triangulation (mf_subdiv.cu).
+int mf_setup_buffers(mf_ctx *ctx, int d, uint64_t ME, uint64_t MV, uint64_t MC, bool mixed, int n_sv,
+                     MfTraceBufs *B) {
+  return setup_buffers(ctx, d, ME, MV, MC, mixed, n_sv, B);
+}
+int mf_build_domain_table(mf_ctx *ctx, MfFrame *F, cudaStream_t st) {
+  return build_domain_table(ctx, F, st);
+}
+int mf_read_counters(mf_ctx *ctx, const MfTraceBufs &B, cudaStream_t st) {
+  return read_counters(ctx, B, st);
 }

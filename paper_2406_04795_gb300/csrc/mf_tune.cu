@@ -92,6 +92,7 @@ extern "C" int mf_autotune(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
                            const mf_trace_opts *opts, const double *seeds, int64_t n_seeds,
                            mf_tune *out, void *stream) {
   if (!ctx) return MF_ERR_INVALID;
+  ctx->sub.valid = false;  // its slots are reused here
   if (!rbf || !dom || !opts || !out)
     return mf_set_error(ctx, MF_ERR_INVALID, "mf_autotune: bad arguments");
   cudaSetDevice(ctx->device);

@@ -40,7 +40,7 @@ EXPORTS = ("mf_ctx_create", "mf_ctx_destroy", "mf_last_error", "mf_ctx_bytes", "
            "mf_server_create", "mf_server_destroy", "mf_server_submit", "mf_server_step",
            "mf_server_status", "mf_server_fetch", "mf_server_done", "mf_autotune", "mf_ctx_set_tune",
            "mf_ctx_get_tune", "mf_vertex_keys", "mf_probe_rates", "mf_diag_exp",
-           "mf_certify_ex")
+           "mf_certify_ex", "mf_subdiv_begin", "mf_subdiv_next")
 
 MF_PHASES = 12
 PHASE_NAMES = ("prepare", "seeds", "expand_vertices", "eval", "expand_edges", "roots", "cells",
@@ -196,6 +196,11 @@ def load(build_if_missing: bool = True):
     L.mf_trace_noalloc.restype = C.c_int
     L.mf_trace_noalloc.argtypes = [P(mf_rbf), P(mf_domain), P(mf_trace_opts), V, C.c_int64,
                                    P(mf_trace_out), V]
+    L.mf_subdiv_begin.restype = C.c_int
+    L.mf_subdiv_begin.argtypes = [V, P(mf_rbf), P(mf_domain), P(mf_trace_opts), C.c_int32, V,
+                                  C.c_int64, C.c_int64, P(C.c_int64), V]
+    L.mf_subdiv_next.restype = C.c_int
+    L.mf_subdiv_next.argtypes = [V, P(mf_trace_out), P(C.c_int64), V]
     L.mf_certify_ex.restype = C.c_int
     L.mf_certify_ex.argtypes = [V, P(mf_robot), P(mf_scene), V, C.c_int64, C.c_int32, V, V,
                                 C.c_int64, P(mf_certify_out), V]
@@ -367,6 +372,20 @@ def mf_autotune(ctx, rbf: mf_rbf, dom: mf_domain, opts: mf_trace_opts, seeds_ptr
     _check(ctx, load().mf_autotune(ctx, C.byref(rbf), C.byref(dom), C.byref(opts), seeds_ptr,
                                    n_seeds, C.byref(t), stream))
     return t
+
+
+def mf_subdiv_begin(ctx, rbf: mf_rbf, dom: mf_domain, opts: mf_trace_opts, k, seeds_ptr, n_seeds,
+                    cells_per_batch, stream=0) -> int:
+    n = C.c_int64()
+    _check(ctx, load().mf_subdiv_begin(ctx, C.byref(rbf), C.byref(dom), C.byref(opts), k,
+                                       seeds_ptr, n_seeds, cells_per_batch, C.byref(n), stream))
+    return n.value
+
+
+def mf_subdiv_next(ctx, out: mf_trace_out, stream=0) -> int:
+    left = C.c_int64()
+    _check(ctx, load().mf_subdiv_next(ctx, C.byref(out), C.byref(left), stream))
+    return left.value
 
 
 def mf_certify_ex(ctx, robot: mf_robot, scene: mf_scene, points_ptr, n_points, d, off_ptr,
