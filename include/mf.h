@@ -61,6 +61,14 @@ extern "C" {
  * exceed 1e-5 and sums the rest in FP32 under a bound that moves t by at most
  * 1e-7.  This flag gives a mixed path the FP64 path's 1e-9 root solve. */
 #define MF_ROOTS_FP64_EXACT 4u
+/* Sorted output (mf_trace and mf_trace_fetch; the batched, served and
+ * allocation-free entry points reject it): edges in increasing order of their
+ * 64-bit edge key (mf_vertex_keys(y) * 2^d + mask), cells in increasing order
+ * of (vertex key of z, pi read as base-8 digits with pi_0 most significant),
+ * and the cell -> edge CSR in the new orders (each row keeps its pairs in
+ * vertex order).  Without it the order is the search's insertion order,
+ * which depends on the scheduling of atomics. */
+#define MF_SORT_OUTPUT 8u
 
 typedef struct mf_ctx mf_ctx;
 
@@ -295,6 +303,12 @@ int mf_server_status(mf_server *s, int64_t id, int32_t *state, double *t_submit,
 /* Copies a done request's results (as mf_trace does) and releases its
  * memory; a failed request returns its error code and is forgotten. */
 int mf_server_fetch(mf_server *s, int64_t id, mf_trace_out *out, void *stream);
+/* Runs mf_server_step until request id is done or has failed, or until
+ * timeout_ms of host wall time have passed (MF_ERR_TIMEOUT; the request keeps
+ * running and can be waited for again).  *state receives its state as
+ * mf_server_status reports it.  Requests finished meanwhile are reported by
+ * mf_server_done as usual. */
+int mf_server_wait(mf_server *s, int64_t id, double timeout_ms, void *stream, int32_t *state);
 
 /* Certification (Sec. V-C, App. A): forward kinematics of every point, exact
  * capsule/box and capsule/sphere distances, per-point margin

@@ -84,7 +84,7 @@ class Context:
     def trace(self, sv, alpha, gamma, b, lam, offset, lo, hi, seeds, precision=mf.MF_FP64,
               roots=True, cells=True, batch_cap=1 << 24, max_edges=1 << 22, max_vertices=0,
               max_cells=0, recheck_band=1e-3, root_tol=1e-12, stream=None, outputs=None,
-              exact_roots=False):
+              exact_roots=False, sort=False):
         """Traces the zero set; returns a dict of device tensors and counters.
 
         ``outputs`` may hold preallocated output tensors (as returned by an
@@ -98,7 +98,8 @@ class Context:
         opts = mf.mf_trace_opts(float(lam), int(batch_cap), int(precision), float(recheck_band),
                                 float(root_tol), int(max_edges), int(max_vertices), int(max_cells),
                                 (mf.MF_WANT_ROOTS if roots else 0) | (mf.MF_WANT_CELLS if cells else 0)
-                                | (mf.MF_ROOTS_FP64_EXACT if exact_roots else 0))
+                                | (mf.MF_ROOTS_FP64_EXACT if exact_roots else 0)
+                                | (mf.MF_SORT_OUTPUT if sort else 0))
         st = _stream_handle(stream)
         res = outputs if outputs is not None else {}
         out = self._out_struct(res, d)
@@ -281,11 +282,12 @@ class Context:
         return r["verdict"], r["margin"], r["cell_verdict"]
 
     def certify_ex(self, dh, radius, types, pose, dims, points, cell_off=None, cell_idx=None,
-                   spheres=None, whole=True, stream=None):
+                   spheres=None, whole=True, slack=True, stream=None):
         """mf_certify_ex: radius None = no link capsules; spheres = (link [n],
         centre [n][3] in frame T_{link+1}, radius [n]) or None.  Returns device
         tensors verdict, margin, element and, with cells, cell_verdict and
-        (whole=True) cell_whole / cell_slack."""
+        (whole=True) cell_whole and (slack=True) cell_slack; without the
+        slack the library decides most cells in FP32 under an error bound."""
         dev = self.device
         dh_t = _dev(dh, torch.float64, dev).reshape(-1, 4)
         rad_t = None if radius is None else _dev(radius, torch.float64, dev)
@@ -320,9 +322,10 @@ class Context:
             out.cell_verdict = res["cell_verdict"].data_ptr()
             if whole:
                 res["cell_whole"] = torch.empty(nc, dtype=torch.uint8, device=dev)
-                res["cell_slack"] = torch.empty(nc, dtype=torch.float64, device=dev)
                 out.cell_whole = res["cell_whole"].data_ptr()
-                out.cell_slack = res["cell_slack"].data_ptr()
+                if slack:
+                    res["cell_slack"] = torch.empty(nc, dtype=torch.float64, device=dev)
+                    out.cell_slack = res["cell_slack"].data_ptr()
         else:
             res["cell_verdict"] = torch.empty(0, dtype=torch.uint8, device=dev)
         mf.mf_certify_ex(self.h, robot, scene, pts.data_ptr(), P, d, offp, idxp, nc, out,
@@ -372,6 +375,12 @@ class Server:
 
     def status(self, rid):
         return mf.mf_server_status(self.ctx.h, self.h, rid)
+
+    def wait(self, rid, timeout_ms, stream=None):
+        """Steps the server until request rid is done or failed (returns its
+        state), or until timeout_ms passes (returns None)."""
+        rc, state = mf.mf_server_wait(self.ctx.h, self.h, rid, timeout_ms, _stream_handle(stream))
+        return None if rc == mf.MF_ERR_TIMEOUT else state
 
     def done(self):
         """Ids of the requests that finished or failed since the last call."""

@@ -109,6 +109,8 @@ int mf_layout_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom, const 
   if (r.d < 2 || r.d > MF_MAXD || r.n_sv < 1 || !(o->lambda > 0.0) || !std::isfinite(o->lambda) ||
       (o->precision != MF_FP64 && o->precision != MF_MIXED_FP32 && o->precision != MF_MIXED_BF16))
     return mf_set_error(ctx, MF_ERR_INVALID, "bad trace arguments");
+  if (o->flags & MF_SORT_OUTPUT)
+    return mf_set_error(ctx, MF_ERR_INVALID, "MF_SORT_OUTPUT is for mf_trace only");
   memset(S, 0, sizeof(*S));
   int rc = mf_build_frame(ctx, r.d, o->lambda, dom, &S->F);
   if (rc) return rc;
@@ -916,4 +918,22 @@ extern "C" int mf_server_fetch(mf_server *s, int64_t id, mf_trace_out *o, void *
   if (rc) return rc;
   release(s, it, st);
   return MF_OK;
+}
+
+extern "C" int mf_server_wait(mf_server *s, int64_t id, double timeout_ms, void *stream,
+                              int32_t *state) {
+  if (!s || !state || !(timeout_ms >= 0.0)) return MF_ERR_INVALID;
+  const double t_end = now_s() + timeout_ms * 1e-3;
+  for (;;) {
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return mf_set_error(s->ctx, MF_ERR_INVALID, "unknown request");
+    *state = it->second.state;
+    if (*state == 2 || *state < 0) return MF_OK;
+    if (now_s() >= t_end)
+      return mf_set_error(s->ctx, MF_ERR_TIMEOUT, "request %lld not done after %.1f ms",
+                          (long long)id, timeout_ms);
+    int32_t running = 0, queued = 0;
+    const int rc = mf_server_step(s, stream, &running, &queued);
+    if (rc) return rc;
+  }
 }

@@ -303,11 +303,11 @@ __device__ __forceinline__ void cert_sincos(double x, const double2 *tab, double
 // cache (measured: 45 no-instruction stall cycles per issue).
 // Elements: link capsules e < NC (NC = NL with capsules, 0 without), then
 // spheres e - NC on their links.
-__global__ void __launch_bounds__(CERT_THREADS, 5) k_certify_points(
+__global__ void __launch_bounds__(CERT_THREADS) k_certify_points(
     int NL, const double *dh, const double *radius, int NS, const int32_t *sph_link,
     const double *sph_c, const double *sph_r, int nobs, const int32_t *type, const double *pose,
     const double *dims, const double *pts, int64_t n, int d, const double2 *sctab, uint8_t *verdict,
-    double *margin, int16_t *element) {
+    double *margin, int16_t *element, float *rec32) {
   __shared__ CertObs so[CERT_MAX_OBS];
   __shared__ CertObsT<float> sof[CERT_MAX_OBS];  // FP32 copy for the lower bounds
   __shared__ double sdh[MF_MAXD * 4], srad[MF_MAXD], ssa[MF_MAXD], sca[MF_MAXD];
@@ -450,20 +450,28 @@ __global__ void __launch_bounds__(CERT_THREADS, 5) k_certify_points(
                               fmaf(rot32[9 * f + 3 * r + 2], ssc32[3 * s + 2], org32[3 * f + r])));
     return ssr32[s];
   };
-  // the same in FP64 (after fk64 past the element's link)
+  // the same in FP64 (after fk64 past the element's link); one call site
+  // for the chain and the distance keeps the kernel's code small
   auto exact = [&](int e, int k, double t0) -> double {
-    if (e < NC) {
-      fk64(e + 1);
-      return srad[e] - seg_obstacle_dist(so[k], &org[3 * e], &org[3 * e + 3], t0);
-    }
-    const int s = e - NC, f = ssl[s] + 1;
+    const bool cap = e < NC;
+    const int s = e - NC, f = cap ? e + 1 : ssl[s] + 1;
     fk64(f);
-    double c[3];
+    double a[3], b[3], rad;
+    if (cap) {
 #pragma unroll
-    for (int r = 0; r < 3; r++)
-      c[r] = rot[9 * f + 3 * r] * ssc64[3 * s] + rot[9 * f + 3 * r + 1] * ssc64[3 * s + 1] +
-             rot[9 * f + 3 * r + 2] * ssc64[3 * s + 2] + org[3 * f + r];
-    return ssr64[s] - seg_obstacle_dist(so[k], c, c, t0);
+      for (int r = 0; r < 3; r++) {
+        a[r] = org[3 * e + r];
+        b[r] = org[3 * e + 3 + r];
+      }
+      rad = srad[e];
+    } else {
+#pragma unroll
+      for (int r = 0; r < 3; r++)
+        a[r] = b[r] = rot[9 * f + 3 * r] * ssc64[3 * s] + rot[9 * f + 3 * r + 1] * ssc64[3 * s + 1] +
+                      rot[9 * f + 3 * r + 2] * ssc64[3 * s + 2] + org[3 * f + r];
+      rad = ssr64[s];
+    }
+    return rad - seg_obstacle_dist(so[k], a, b, t0);
   };
   // margin = max over (element, obstacle) of radius - distance.  Every pair
   // first gets a lower bound on its distance in FP32 from the FP32 chain
@@ -502,28 +510,45 @@ __global__ void __launch_bounds__(CERT_THREADS, 5) k_certify_points(
         ub2 = ub;
       }
     }
+  // exact margins: first the pair with the largest bound, then (if the
+  // second-largest bound reaches that margin) every pair whose bound does;
+  // ties (e.g. several elements inside obstacles, margin = radius) go to the
+  // lowest element index, as in the oracle
   double best = -INFINITY;
   int be = -1;
-  if (bi >= 0) {
-    best = exact(bi, bk, (double)tb);
-    be = bi;
-  }
-  if ((double)ub2 > best) {
-    for (int e = 0; e < NE; e++)
-      for (int k = 0; k < nobs; k++) {
-        if (e == bi && k == bk) continue;
-        float tk;
-        if ((double)upper(e, k, &tk) <= best) continue;
-        const double m = exact(e, k, (double)tk);
-        if (m > best) {
-          best = m;
-          be = e;
-        }
-      }
+  for (int q = -1; q < NE * nobs;) {
+    int e, k;
+    float t0;
+    if (q < 0) {
+      if (bi < 0) break;
+      e = bi;
+      k = bk;
+      t0 = tb;
+    } else {
+      e = q / nobs;
+      k = q - e * nobs;
+      q++;
+      if (e == bi && k == bk) continue;
+      const double ub = (double)upper(e, k, &t0);
+      if (ub < best || (ub == best && e > be)) continue;
+    }
+    const double m = exact(e, k, (double)t0);
+    if (m > best || (m == best && e < be)) {
+      best = m;
+      be = e;
+    }
+    if (q < 0) {
+      if (!((double)ub2 >= best)) break;
+      q = 0;
+    }
   }
   margin[p] = best;
   verdict[p] = best >= 0.0 ? 1 : 0;
   if (element) element[p] = (int16_t)be;
+  if (rec32) {  // FP32 coordinates and margin for the whole-cell certificate
+    for (int k = 0; k < d; k++) rec32[p * (d + 1) + k] = (float)pts[p * d + k];
+    rec32[p * (d + 1) + d] = (float)best;
+  }
 }
 
 // Whole-cell certificate (one thread per cell): with lo_k / hi_k the range of
@@ -613,6 +638,103 @@ static void lipschitz_table(int NL, const std::vector<double> &dh, bool caps, in
   }
 }
 
+// The same certificate in FP32 from the points' FP32 records (coordinates
+// and margin), one thread per cell.  With u = 2^-24, P the largest |p| of
+// the cell and s_k the spans, the FP32 slack of point j differs from the
+// exact one by at most
+//   eps_j = 2 u (2 |m_j| + sum_k L_k (2 P + (d + 4) s_k))
+// (rounding of the coordinates, margin and constants to FP32, of the spans,
+// the products, the d-term sum and the final difference, with a factor 2 to
+// spare).  The cell is decided when some point has slack_j - eps_j >= 0
+// (certified) or every point has slack_j + eps_j < 0 (not certified);
+// otherwise it is recomputed in FP64 from the points and margins as
+// k_certify_cells_whole does.
+__global__ void k_certify_cells_whole32(const int64_t *off, const int64_t *idx, int64_t n_cells,
+                                        const float *rec32, const double *pts, int d,
+                                        const double *margin, const int16_t *element,
+                                        const float *L32, const double *L, int NE,
+                                        int64_t n_points, uint8_t *whole, unsigned *bad) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  const int64_t j0 = off[c], j1 = off[c + 1];
+  float lo[MF_MAXD], hi[MF_MAXD];
+#pragma unroll
+  for (int k = 0; k < MF_MAXD; k++) {
+    lo[k] = INFINITY;
+    hi[k] = -INFINITY;
+  }
+  float P = 0.f;
+  for (int64_t j = j0; j < j1; j++) {
+    const int64_t i = idx[j];
+    if (i < 0 || i >= n_points) {
+      atomicOr(bad, 1u);
+      continue;
+    }
+    const float *r = rec32 + i * (d + 1);
+    for (int k = 0; k < d; k++) {
+      const float v = r[k];
+      lo[k] = fminf(lo[k], v);
+      hi[k] = fmaxf(hi[k], v);
+      P = fmaxf(P, fabsf(v));
+    }
+  }
+  const float u = 5.9604644775390625e-08f;
+  bool yes = false, undecided = false;
+  for (int64_t j = j0; j < j1 && !yes; j++) {
+    const int64_t i = idx[j];
+    if (i < 0 || i >= n_points) continue;
+    const int e = element[i];
+    if (e < 0 || e >= NE) continue;
+    const float *r = rec32 + i * (d + 1);
+    float drop = 0.f, lsum = 0.f;
+    for (int k = 0; k < d; k++) {
+      const float v = r[k];
+      const float sp = fmaxf(hi[k] - v, v - lo[k]);
+      const float Lk = L32[e * d + k];
+      drop = fmaf(Lk, sp, drop);
+      lsum = fmaf(Lk, fmaf((float)(d + 4), sp, 2.f * P), lsum);
+    }
+    const float m = r[d];
+    const float sl = m - drop;
+    const float eps = 2.f * u * (2.f * fabsf(m) + lsum) + 1e-30f;
+    if (sl - eps >= 0.f) yes = true;
+    else if (sl + eps >= 0.f) undecided = true;
+  }
+  if (!yes && undecided) {
+    // close to the decision: the exact FP64 certificate
+    double dlo[MF_MAXD], dhi[MF_MAXD];
+#pragma unroll
+    for (int k = 0; k < MF_MAXD; k++) {
+      dlo[k] = INFINITY;
+      dhi[k] = -INFINITY;
+    }
+    for (int64_t j = j0; j < j1; j++) {
+      const int64_t i = idx[j];
+      if (i < 0 || i >= n_points) continue;
+      for (int k = 0; k < d; k++) {
+        const double v = pts[i * d + k];
+        dlo[k] = fmin(dlo[k], v);
+        dhi[k] = fmax(dhi[k], v);
+      }
+    }
+    double slack = -INFINITY;
+    for (int64_t j = j0; j < j1; j++) {
+      const int64_t i = idx[j];
+      if (i < 0 || i >= n_points) continue;
+      const int e = element[i];
+      if (e < 0 || e >= NE) continue;
+      double drop = 0.0;
+      for (int k = 0; k < d; k++) {
+        const double v = pts[i * d + k];
+        drop = fma(L[e * d + k], fmax(dhi[k] - v, v - dlo[k]), drop);
+      }
+      slack = fmax(slack, margin[i] - drop);
+    }
+    yes = slack >= 0.0;
+  }
+  whole[c] = yes ? 1 : 0;
+}
+
 extern "C" int mf_certify_ex(mf_ctx *ctx, const mf_robot *robot, const mf_scene *scene,
                              const double *points, int64_t n_points, int32_t d,
                              const int64_t *cell_off, const int64_t *cell_idx, int64_t n_cells,
@@ -636,14 +758,23 @@ extern "C" int mf_certify_ex(mf_ctx *ctx, const mf_robot *robot, const mf_scene 
   const bool whole = n_cells > 0 && (out->cell_whole || out->cell_slack);
   // scratch: error word, the sin/cos table, the Lipschitz table, and the
   // per-point elements when the caller wants a whole-cell verdict only
+  // (the FP32 whole-cell pass, used when the slack itself is not wanted,
+  // also needs the points' FP32 records)
+  const bool fast = whole && !out->cell_slack;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t o_tab = 256, o_L = o_tab + 128 * sizeof(double2);
-  const size_t o_el = o_L + (((size_t)NE * NL * 8 + 255) & ~(size_t)255);
-  const size_t need_el = whole && !out->element ? (size_t)n_points * 2 : 0;
-  char *scr = (char *)mf_ctx_buffer(ctx, MF_SLOT_CERT, o_el + need_el + 256);
+  const size_t o_L32 = o_L + al((size_t)NE * NL * 8 + 8);
+  const size_t o_el = o_L32 + al((size_t)NE * NL * 4 + 8);
+  const size_t need_el = whole && !out->element ? al((size_t)n_points * 2 + 8) : 0;
+  const size_t o_rec = o_el + need_el;
+  const size_t need_rec = fast ? (size_t)n_points * (d + 1) * 4 : 0;
+  char *scr = (char *)mf_ctx_buffer(ctx, MF_SLOT_CERT, o_rec + need_rec + 256);
   if (!scr) return MF_ERR_OOM;
   unsigned *bad = (unsigned *)scr;
   const double2 *sctab = (const double2 *)(scr + o_tab);
   double *dL = (double *)(scr + o_L);
+  float *dL32 = (float *)(scr + o_L32);
+  float *rec32 = fast ? (float *)(scr + o_rec) : nullptr;
   int16_t *elem = out->element ? out->element : (need_el ? (int16_t *)(scr + o_el) : nullptr);
   cudaMemsetAsync(bad, 0, sizeof(unsigned), st);
   {
@@ -663,6 +794,7 @@ extern "C" int mf_certify_ex(mf_ctx *ctx, const mf_robot *robot, const mf_scene 
     if (rc) return rc;
   }
   std::vector<double> hL;
+  std::vector<float> hL32;  // kept alive until the stream synchronises
   if (whole) {
     // the table needs the DH parameters and sphere centres on the host
     std::vector<double> hdh((size_t)NL * 4), hsc((size_t)NS * 3);
@@ -681,9 +813,15 @@ extern "C" int mf_certify_ex(mf_ctx *ctx, const mf_robot *robot, const mf_scene 
       if (hsl[s] < 0 || hsl[s] >= NL)
         return mf_set_error(ctx, MF_ERR_INVALID, "mf_certify: sphere %d on link %d", s, hsl[s]);
     lipschitz_table(NL, hdh, robot->radius != nullptr, NS, hsl, hsc, hL);
+    hL32.resize(hL.size());
+    for (size_t i = 0; i < hL.size(); i++) hL32[i] = (float)hL[i];
     if (!hL.empty()) {
       rc = mf_cuda_check(ctx, cudaMemcpyAsync(dL, hL.data(), hL.size() * 8, cudaMemcpyHostToDevice, st),
                          "mf_certify lipschitz");
+      if (!rc)
+        rc = mf_cuda_check(ctx, cudaMemcpyAsync(dL32, hL32.data(), hL32.size() * 4,
+                                                cudaMemcpyHostToDevice, st),
+                           "mf_certify lipschitz");
       if (rc) return rc;
     }
   }
@@ -693,7 +831,7 @@ extern "C" int mf_certify_ex(mf_ctx *ctx, const mf_robot *robot, const mf_scene 
     k_certify_points<<<g, CERT_THREADS, 0, st>>>(
         NL, robot->dh, robot->radius, NS, robot->sphere_link, robot->sphere_center,
         robot->sphere_radius, scene->n, scene->type, scene->pose, scene->dims, points, n_points,
-        d, sctab, out->point_verdict, out->margin, elem);
+        d, sctab, out->point_verdict, out->margin, elem, rec32);
   }
   if (n_cells > 0 && out->cell_verdict) {
     MfProfScope ps(ctx, MF_PH_CERT_CELLS, st, 1, n_cells);
@@ -702,9 +840,14 @@ extern "C" int mf_certify_ex(mf_ctx *ctx, const mf_robot *robot, const mf_scene 
   }
   if (whole) {
     MfProfScope ps(ctx, MF_PH_CERT_CELLS, st, 1, n_cells);
-    k_certify_cells_whole<<<(unsigned)((n_cells + 255) / 256), 256, 0, st>>>(
-        cell_off, cell_idx, n_cells, points, d, out->margin, elem, dL, NE, n_points,
-        out->cell_whole, out->cell_slack, bad);
+    if (fast)
+      k_certify_cells_whole32<<<(unsigned)((n_cells + 255) / 256), 256, 0, st>>>(
+          cell_off, cell_idx, n_cells, rec32, points, d, out->margin, elem, dL32, dL, NE,
+          n_points, out->cell_whole, bad);
+    else
+      k_certify_cells_whole<<<(unsigned)((n_cells + 255) / 256), 256, 0, st>>>(
+          cell_off, cell_idx, n_cells, points, d, out->margin, elem, dL, NE, n_points,
+          out->cell_whole, out->cell_slack, bad);
   }
   int rc = mf_cuda_check(ctx, cudaGetLastError(), "mf_certify launch");
   if (rc) return rc;

@@ -17,7 +17,15 @@ struct MfTraceState {
   int64_t n_edges = 0, n_cells = 0, n_cell_edges = 0, n_vertices = 0, n_near_zero = 0,
           n_recheck = 0, n_boundary = 0, n_dead_seeds = 0, levels = 0, root_evals = 0;
   uint32_t flags = 0;
+  // MF_SORT_OUTPUT: the sorted orders (new -> old) and the edges' inverse,
+  // in MF_SLOT_SORT, with a scan scratch for the CSR copy
+  bool sorted = false;
+  const uint32_t *perm_e = nullptr, *inv_e = nullptr, *perm_c = nullptr;
+  int64_t *sort_scan = nullptr;
 };
+
+int mf_sort_trace(mf_ctx *ctx, MfTraceState &L, cudaStream_t st);
+int mf_copy_out_sorted(mf_ctx *ctx, const MfTraceState &L, mf_trace_out *out, cudaStream_t st);
 
 // Batch triangulation in progress (mf_subdiv_begin / mf_subdiv_next): the
 // coarse trace's crossing n-simplices and the shared local template live in

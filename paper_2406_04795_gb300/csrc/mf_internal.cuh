@@ -586,5 +586,6 @@ enum {
   MF_SLOT_SERVER = 12,
   MF_SLOT_VLIST = 13,
   MF_SLOT_SUBDIV = 14,
-  MF_NUM_SLOTS = 15
+  MF_SLOT_SORT = 15,
+  MF_NUM_SLOTS = 16
 };

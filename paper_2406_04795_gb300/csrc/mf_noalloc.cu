@@ -182,7 +182,8 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
       !(rbf->gamma > 0.0) || !std::isfinite(rbf->gamma) || !std::isfinite(rbf->b) ||
       !(opts->lambda > 0.0) || !std::isfinite(opts->lambda) ||
       (opts->precision != MF_FP64 && opts->precision != MF_MIXED_FP32 &&
-       opts->precision != MF_MIXED_BF16))
+       opts->precision != MF_MIXED_BF16) ||
+      (opts->flags & MF_SORT_OUTPUT))
     return MF_ERR_INVALID;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MF_ERR_CUDA;

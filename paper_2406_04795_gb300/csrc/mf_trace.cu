@@ -1153,6 +1153,21 @@ static int copy_out(mf_ctx *ctx, const MfTraceState &L, mf_trace_out *out, cudaS
   const MfTraceBufs &B = L.B;
   bool small = false;
   const size_t E = (size_t)L.n_edges;
+  if (L.sorted) {
+    // the sorted order: gathers instead of copies
+    small = ((out->edge_y || out->edge_mask || out->edge_f || out->edge_t || out->points) &&
+             out->cap_edges < L.n_edges) ||
+            ((L.flags & MF_WANT_CELLS) && (out->cell_y || out->cell_perm || out->cell_edge_off) &&
+             out->cap_cells < L.n_cells) ||
+            ((L.flags & MF_WANT_CELLS) && out->cell_edge_idx && out->cap_cell_edges < L.n_cell_edges);
+    if (small)
+      return mf_set_error(ctx, MF_ERR_CAPACITY,
+                          "output buffers too small: need %lld edges, %lld cells, %lld cell edges",
+                          (long long)L.n_edges, (long long)L.n_cells, (long long)L.n_cell_edges);
+    int rc = mf_copy_out_sorted(ctx, L, out, st);
+    if (rc) return rc;
+    return mf_cuda_check(ctx, cudaStreamSynchronize(st), "copy out");
+  }
   auto cp = [&](void *dst, const void *src, size_t bytes) {
     if (dst && bytes) cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st);
   };
@@ -1351,6 +1366,13 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
   L.n_dead_seeds = (int64_t)h.n_dead_seeds;
   L.levels = levels;
   L.root_evals = (int64_t)h.root_evals;
+  L.sorted = false;
+  if (opts->flags & MF_SORT_OUTPUT) {
+    MfProfScope ps(ctx, MF_PH_COPY, st, 0);
+    rc = mf_sort_trace(ctx, L, st);
+    if (rc) return rc;
+    L.sorted = true;
+  }
   L.valid = true;
   if (ctx->prof.on) {
     ctx->prof.stats.terms[MF_PH_EVAL] += (int64_t)h.eval_terms;

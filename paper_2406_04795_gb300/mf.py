@@ -28,6 +28,7 @@ MF_MIXED_FP32 = 2
 MF_WANT_ROOTS = 1
 MF_WANT_CELLS = 2
 MF_ROOTS_FP64_EXACT = 4
+MF_SORT_OUTPUT = 8
 
 MF_BOX = 0
 MF_SPHERE = 1
@@ -40,7 +41,8 @@ EXPORTS = ("mf_ctx_create", "mf_ctx_destroy", "mf_last_error", "mf_ctx_bytes", "
            "mf_server_create", "mf_server_destroy", "mf_server_submit", "mf_server_step",
            "mf_server_status", "mf_server_fetch", "mf_server_done", "mf_autotune", "mf_ctx_set_tune",
            "mf_ctx_get_tune", "mf_vertex_keys", "mf_probe_rates", "mf_diag_exp",
-           "mf_certify_ex", "mf_subdiv_begin", "mf_subdiv_next")
+           "mf_certify_ex", "mf_subdiv_begin", "mf_subdiv_next",
+           "mf_server_wait")
 
 MF_PHASES = 12
 PHASE_NAMES = ("prepare", "seeds", "expand_vertices", "eval", "expand_edges", "roots", "cells",
@@ -196,6 +198,8 @@ def load(build_if_missing: bool = True):
     L.mf_trace_noalloc.restype = C.c_int
     L.mf_trace_noalloc.argtypes = [P(mf_rbf), P(mf_domain), P(mf_trace_opts), V, C.c_int64,
                                    P(mf_trace_out), V]
+    L.mf_server_wait.restype = C.c_int
+    L.mf_server_wait.argtypes = [V, C.c_int64, C.c_double, V, P(C.c_int32)]
     L.mf_subdiv_begin.restype = C.c_int
     L.mf_subdiv_begin.argtypes = [V, P(mf_rbf), P(mf_domain), P(mf_trace_opts), C.c_int32, V,
                                   C.c_int64, C.c_int64, P(C.c_int64), V]
@@ -372,6 +376,15 @@ def mf_autotune(ctx, rbf: mf_rbf, dom: mf_domain, opts: mf_trace_opts, seeds_ptr
     _check(ctx, load().mf_autotune(ctx, C.byref(rbf), C.byref(dom), C.byref(opts), seeds_ptr,
                                    n_seeds, C.byref(t), stream))
     return t
+
+
+def mf_server_wait(ctx, server, rid, timeout_ms, stream=0, check=True):
+    """Returns (rc, state); raises on errors other than MF_ERR_TIMEOUT unless check=False."""
+    st = C.c_int32()
+    rc = load().mf_server_wait(server, rid, float(timeout_ms), stream, C.byref(st))
+    if check and rc not in (MF_OK, MF_ERR_TIMEOUT):
+        _check(ctx, rc)
+    return rc, st.value
 
 
 def mf_subdiv_begin(ctx, rbf: mf_rbf, dom: mf_domain, opts: mf_trace_opts, k, seeds_ptr, n_seeds,

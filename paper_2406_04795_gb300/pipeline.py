@@ -84,7 +84,7 @@ class Proof:
         # whole-cell (Lipschitz) certificate of each cell's manifold piece
         c = self.ctx.certify_ex(self.dh, self.radius, self.otype, self.opose, self.odims,
                                 r["points"], r["cell_off"], r["cell_idx"], whole=True,
-                                stream=stream)
+                                slack=False, stream=stream)
         v, m, cv = c["verdict"], c["margin"], c["cell_verdict"]
         self.whole = c.get("cell_whole")
         self.last = (r, v, m, cv)

@@ -119,6 +119,13 @@ def test_whole_cell_certificate_against_oracle(ctx):
     gw = _compare(g, o, cells=True)
     assert 50 < gw.sum() < gw.shape[0]
     assert np.all(gw <= g["cell_verdict"].cpu().numpy())
+    # without the slack output the library decides cells in FP32 under its
+    # error bound and recomputes the close ones in FP64: the same verdicts
+    f = ctx.certify_ex(dh, radius, types, pose, dims, pts, off, idx, spheres=spheres, slack=False)
+    fw = f["cell_whole"].cpu().numpy()
+    clear = np.abs(o["cell_slack"]) > 1e-9
+    assert np.array_equal(fw[clear], o["cell_whole"][clear])
+    assert np.array_equal(fw, gw)
 
 
 def test_traced_cells_whole_certificate(ctx):
@@ -133,4 +140,7 @@ def test_traced_cells_whole_certificate(ctx):
                         g["cell_idx"])
     oc = oracle.certify_ex(w.dh, w.radius, types, pose, dims, g["points"], g["cell_off"],
                            g["cell_idx"])
-    _compare(gc, oc, cells=True)
+    gw = _compare(gc, oc, cells=True)
+    fc = ctx.certify_ex(w.dh, w.radius, types, pose, dims, g["points"], g["cell_off"],
+                        g["cell_idx"], slack=False)
+    assert np.array_equal(fc["cell_whole"].cpu().numpy(), gw)

@@ -73,3 +73,18 @@ def test_server_fetch_before_done_and_oversized(ctx):
         server.fetch(big)
     assert server.fetch(rid)["n_edges"] > 1000
     server.close()
+
+
+def test_server_wait_is_bounded(ctx):
+    """mf_server_wait returns MF_ERR_TIMEOUT (the request still running) when
+    the limit is too short, and the request's final state once it is done."""
+    server = ctx.server(max_slots=2, hbm_bytes=4 << 30)
+    w = W.config_d3()
+    rid = server.submit(w, precision=mf.MF_FP64, max_edges=1 << 18)
+    assert server.wait(rid, 0.0) is None  # no time at all: not done yet
+    assert server.status(rid)[0] in (0, 1)
+    state = server.wait(rid, 60_000.0)
+    assert state == 2
+    assert list(server.done()) == [rid]
+    assert server.fetch(rid)["n_edges"] > 1000
+    server.close()
