@@ -179,7 +179,7 @@ class Context:
 
     def trace_batch(self, workloads, precisions=None, roots=True, cells=True, capacities=None,
                     batch_cap=1 << 24, recheck_band=1e-3, root_tol=1e-12, stream=None,
-                    exact_roots=False):
+                    exact_roots=False, sort=False):
         """Traces many workloads in one batched call (mf_trace_batch).
 
         workloads: objects with sv, alpha, gamma, b, lam, offset, lo, hi, seeds.
@@ -196,7 +196,7 @@ class Context:
         nseeds = (C.c_int64 * n)()
         keep, bufs = [], []
         flags = (mf.MF_WANT_ROOTS if roots else 0) | (mf.MF_WANT_CELLS if cells else 0) | \
-            (mf.MF_ROOTS_FP64_EXACT if exact_roots else 0)
+            (mf.MF_ROOTS_FP64_EXACT if exact_roots else 0) | (mf.MF_SORT_OUTPUT if sort else 0)
         for t, w in enumerate(workloads):
             r, k = self.rbf(w.sv, w.alpha, w.gamma, w.b)
             keep.append(k)

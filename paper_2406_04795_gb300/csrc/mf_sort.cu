@@ -13,7 +13,9 @@
 //                   tile in order, ranks the keys of one digit among
 //                   themselves with __match_any_sync and writes them after
 //                   the keys of earlier warps and tiles: stable.
+#include <algorithm>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "mf_internal.cuh"
