@@ -317,39 +317,80 @@ def _proof_ms(ctx, w, reps=2):
 
 def config_lines(ctx, d6_lam=0.15):
     """The other BASELINE configurations, each one line (untimed by the main
-    metric): d=3 FP64; d=6 mixed BF16 at the finest lambda traced here, with
-    sampled root and point errors against the FP64 oracle."""
-    import oracle
-    out = {}
+    metric): d=3 FP64; d=6 mixed BF16 at the finest lambda traced here.  The
+    proofs' sampled edges are kept for the oracle comparison of the CPU
+    baseline leg."""
+    out, keep = {}, {}
     w3 = W.config_d3()
     ms, p, r = _proof_ms(ctx, w3, reps=5)
     out["d3_fp64"] = {"workload": w3.name, "lambda": w3.lam, "n_sv": int(w3.sv.shape[0]),
                       "ms_per_proof": ms, "simplices_per_s": r["n_edges"] / (ms * 1e-3),
-                      "edges_per_proof": r["n_edges"], "cells_per_proof": r["n_cells"]}
+                      "edges_per_proof": r["n_edges"], "cells_per_proof": r["n_cells"],
+                      "cells_points_in_collision": int(p.last[3].sum().item()),
+                      "cells_whole_certified": int(p.whole.sum().item())}
+    keep["d3"] = dict(w=w3, points=r["points"].cpu().numpy(), off=r["cell_off"].cpu().numpy(),
+                      idx=r["cell_idx"].cpu().numpy(), cv=p.last[3].cpu().numpy(),
+                      whole=p.whole.cpu().numpy())
     del p, r
     w6 = W.config_d6(lam=d6_lam)
     ms, p, r = _proof_ms(ctx, w6)
     E = r["n_edges"]
     rng = np.random.default_rng(6)
     idx = np.sort(rng.choice(E, min(E, 400), replace=False))
-    y = r["edge_y"][idx].cpu().numpy()
-    m = r["edge_mask"][idx].cpu().numpy().astype(np.uint32)
-    oracle.set_threads(0)
-    f2, t, pt, multi = oracle.edge_roots(w6.sv, w6.alpha, w6.gamma, w6.b, w6.lam, w6.offset, y, m)
-    ok = (multi == 0) & np.all(np.abs(f2) >= 1e-12, axis=1)
-    dt = np.abs(r["edge_t"][idx].cpu().numpy() - t)[ok]
-    df = np.abs(r["edge_f"][idx].cpu().numpy() - f2)
-    dp = np.abs(r["points"][idx].cpu().numpy() - pt)[ok]
+    keep["d6"] = dict(w=w6, y=r["edge_y"][idx].cpu().numpy(),
+                      m=r["edge_mask"][idx].cpu().numpy().astype(np.uint32),
+                      t=r["edge_t"][idx].cpu().numpy(), f=r["edge_f"][idx].cpu().numpy(),
+                      pt=r["points"][idx].cpu().numpy())
     out["d6_mixed_bf16"] = {
         "workload": w6.name, "lambda": w6.lam, "lambda_config": 0.04, "n_sv": int(w6.sv.shape[0]),
         "ms_per_proof": ms, "simplices_per_s": E / (ms * 1e-3), "edges_per_proof": E,
         "cells_per_proof": r["n_cells"], "vertices_per_proof": r["n_vertices"],
         "rechecked_vertices": r["n_recheck"],
-        "error_vs_oracle": {"sampled_edges": int(ok.sum()), "max_dt": float(dt.max()),
-                            "max_dpoint": float(dp.max()), "max_df_edge_ends": float(df.max()),
-                            "sign_mismatches": int(np.sum((f2 >= 0) != (r["edge_f"][idx].cpu().numpy() >= 0)))},
-        "note": "lambda 0.04 gives ~8e9 edges (lambda^-5 law), beyond one GPU's memory"}
+        "note": "lambda 0.04 gives ~8e9 edges (lambda^-5 law), beyond one GPU's memory; its "
+                "sampled error against the FP64 oracle is in cpu_baseline.d6_error_vs_oracle"}
     del p, r
+    return out, keep
+
+
+def oracle_checks(keep):
+    """CPU-baseline leg: the FP64 oracle on the samples the GPU lines kept:
+    the d=6 mixed proof's sampled roots and end values (error vs the oracle),
+    and the d=3 proof's cells: the point-only verdict's false-certify rate
+    against dense sampling of each cell's piece (convex combinations of its
+    points), and that no whole-cell certified cell has a free sample."""
+    import oracle
+    oracle.set_threads(0)
+    out = {}
+    if "d6" in keep:
+        k = keep["d6"]
+        w6 = k["w"]
+        f2, t, pt, multi = oracle.edge_roots(w6.sv, w6.alpha, w6.gamma, w6.b, w6.lam, w6.offset,
+                                             k["y"], k["m"])
+        ok = (multi == 0) & np.all(np.abs(f2) >= 1e-12, axis=1)
+        out["d6_error_vs_oracle"] = {
+            "sampled_edges": int(ok.sum()), "max_dt": float(np.abs(k["t"] - t)[ok].max()),
+            "max_dpoint": float(np.abs(k["pt"] - pt)[ok].max()),
+            "max_df_edge_ends": float(np.abs(k["f"] - f2).max()),
+            "sign_mismatches": int(np.sum((f2 >= 0) != (k["f"] >= 0)))}
+    if "d3" in keep:
+        k = keep["d3"]
+        w = k["w"]
+        rng = np.random.default_rng(7)
+        cells = np.flatnonzero(k["cv"])
+        pick = rng.choice(cells, min(len(cells), 300), replace=False)
+        false_pt = false_whole = 0
+        for c in pick:
+            P = k["points"][k["idx"][k["off"][c]:k["off"][c + 1]]]
+            S = rng.dirichlet(np.ones(P.shape[0]), size=200) @ P
+            v, _, _ = oracle.certify(w.dh, w.radius, w.obs_type, w.obs_pose, w.obs_dims, S)
+            free = not v.all()
+            false_pt += free
+            false_whole += free and bool(k["whole"][c])
+        out["d3_cells_dense_sampling"] = {
+            "cells_sampled": int(len(pick)), "samples_per_cell": 200,
+            "point_only_false_certify": int(false_pt),
+            "point_only_false_certify_rate": float(false_pt) / max(len(pick), 1),
+            "whole_certified_with_free_sample": int(false_whole)}
     return out
 
 
@@ -563,7 +604,9 @@ def run_gb300(args):
             ctx.close()
             torch.cuda.empty_cache()
             ctx = Context(local, 0)
-            line["configs"] = config_lines(ctx)
+            line["configs"], keep = config_lines(ctx)
+            if "cpu_baseline" in line:
+                line["cpu_baseline"].update(oracle_checks(keep))
             ctx.close()
             torch.cuda.empty_cache()
             ctx = Context(local, 0)

@@ -327,7 +327,8 @@ int mf_certify(mf_ctx *ctx, const mf_robot *robot, const mf_scene *scene, const 
 typedef struct {
   uint8_t *point_verdict; /* [n_points] 1 iff the point is in collision (C_obs) */
   double *margin;         /* [n_points] max over elements and obstacles of radius - distance */
-  int16_t *element;       /* [n_points] the element of that maximum (capsules, then spheres) */
+  int16_t *element;       /* [n_points] the deciding element (capsules, then spheres): the
+                             lowest index whose margin is within 1e-9 of the maximum */
   uint8_t *cell_verdict;  /* [n_cells] AND of the verdicts of the cell's points */
   uint8_t *cell_whole;    /* [n_cells] 1 iff the whole-cell certificate holds (below) */
   double *cell_slack;     /* [n_cells] the certificate's slack (>= 0: certified) */
@@ -343,8 +344,11 @@ typedef struct {
  * sphere; 0 for joints after the element's link).  So with span_jk the
  * largest |p_lk - p_jk| over the cell's points, every configuration of the
  * piece keeps element e_j's margin at least margin_j - sum_k L[e_j][k]
- * span_jk; slack = the maximum of that over the cell's points, and
- * cell_whole = (slack >= 0) certifies the whole piece in collision. */
+ * span_jk; slack = the maximum over the cell's points of margin_j - 1e-9 -
+ * sum_k L[e_j][k] span_jk (the 1e-9 covers the deciding element's own margin,
+ * within 1e-9 of margin_j), and cell_whole = (slack >= 0) certifies the whole
+ * piece in collision.  The margin stops at the element's radius inside an
+ * obstacle (distances are 0 there), which bounds what a cell can certify. */
 int mf_certify_ex(mf_ctx *ctx, const mf_robot *robot, const mf_scene *scene, const double *points,
                   int64_t n_points, int32_t d, const int64_t *cell_edge_off,
                   const int64_t *cell_edge_idx, int64_t n_cells, const mf_certify_out *out,

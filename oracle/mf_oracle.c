@@ -1064,6 +1064,8 @@ double or_segment_obstacle_dist(const double *a, const double *b, int32_t type, 
   return cd > 0.0 ? cd : 0.0;
 }
 
+#define OR_ELEM_TIE 1e-9
+
 /* Robot elements: the link capsules (when radius is given), then the spheres.
  * Element e's end points at a configuration, from the frames of or_fk_frames. */
 static int n_elements(const or_robot *r) { return (r->radius ? r->n_links : 0) + r->n_spheres; }
@@ -1117,14 +1119,15 @@ void or_lipschitz(const or_robot *r, double *L) {
 
 /* Per point: margin = max over robot elements and obstacles of
  * (radius - distance); verdict = 1 (in collision, i.e. in C_obs) iff
- * margin >= 0; element = the first element reaching the maximum.  Per cell
+ * margin >= 0; element = the lowest-index element whose own margin is within
+ * 1e-9 of that maximum.  Per cell
  * (cell_off/cell_idx index the points): the AND of its points' verdicts, and
  * the whole-cell certificate: the cell's piece of the traced manifold is the
  * convex hull of its points, every q in it has |q_k - p_jk| <= span_jk =
- * max_l |p_lk - p_jk|, and element e's margin is at least margin_j -
- * sum_k L[e][k] |q_k - p_jk| (distances are 1-Lipschitz in the element's
- * points); so slack = max_j (margin_j - sum_k L[e_j][k] span_jk) >= 0
- * certifies every point of the piece (whole = 1). */
+ * max_l |p_lk - p_jk|, and element e's margin is at least its margin at p_j
+ * minus sum_k L[e][k] |q_k - p_jk| (distances are 1-Lipschitz in the
+ * element's points); so slack = max_j (margin_j - 1e-9 - sum_k L[e_j][k]
+ * span_jk) >= 0 certifies every point of the piece (whole = 1). */
 void or_certify_ex(const or_robot *r, const or_scene *sc, const double *points, int64_t P,
                    int32_t d, const int64_t *cell_off, const int64_t *cell_idx, int64_t n_cells,
                    uint8_t *verdict, double *margin, int32_t *element, uint8_t *cell_verdict,
@@ -1134,18 +1137,25 @@ void or_certify_ex(const or_robot *r, const or_scene *sc, const double *points, 
   for (int64_t p = 0; p < P; p++) {
     double frames[12 * (OR_MAXD + 1)];
     or_fk_frames(r, points + p * d, frames);
-    double best = -INFINITY;
-    int be = -1;
+    double best = -INFINITY, em[OR_MAXD + 256]; /* up to 256 spheres */
     for (int e = 0; e < ne; e++) {
       double pa[3], pb[3], rad;
       int link;
       element_at(r, frames, e, pa, pb, &rad, &link);
+      em[e] = -INFINITY;
       for (int k = 0; k < sc->n; k++) {
         double dist = or_segment_obstacle_dist(pa, pb, sc->type[k], sc->pose + 12 * k, sc->dims + 3 * k);
         double m = rad - dist;
-        if (m > best) { best = m; be = e; }
+        if (m > em[e]) em[e] = m;
       }
+      if (em[e] > best) best = em[e];
     }
+    /* the deciding element: the lowest index whose margin is within
+     * OR_ELEM_TIE of the maximum (elements inside obstacles all reach their
+     * radius; the certificate below subtracts the same OR_ELEM_TIE) */
+    int be = -1;
+    for (int e = 0; e < ne && be < 0; e++)
+      if (em[e] >= best - OR_ELEM_TIE) be = e;
     margin[p] = best;
     verdict[p] = best >= 0.0 ? 1 : 0;
     if (element) element[p] = be;
@@ -1174,7 +1184,7 @@ void or_certify_ex(const or_robot *r, const or_scene *sc, const double *points, 
         }
         drop += L[e * r->n_links + k] * span;
       }
-      double s = margin[pj] - drop;
+      double s = (margin[pj] - OR_ELEM_TIE) - drop;
       if (s > slack) slack = s;
     }
     if (cell_slack) cell_slack[c] = slack;

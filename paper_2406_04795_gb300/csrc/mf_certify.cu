@@ -26,6 +26,7 @@
 
 #define CERT_MAX_OBS 128
 #define CERT_THREADS 128
+#define CERT_ELEM_TIE 1e-9  // margins this close to the maximum tie
 
 template <typename T>
 struct CertObsT {
@@ -511,9 +512,7 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(
       }
     }
   // exact margins: first the pair with the largest bound, then (if the
-  // second-largest bound reaches that margin) every pair whose bound does;
-  // ties (e.g. several elements inside obstacles, margin = radius) go to the
-  // lowest element index, as in the oracle
+  // second-largest bound exceeds that margin) every pair whose bound does
   double best = -INFINITY;
   int be = -1;
   for (int q = -1; q < NE * nobs;) {
@@ -529,17 +528,31 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(
       k = q - e * nobs;
       q++;
       if (e == bi && k == bk) continue;
-      const double ub = (double)upper(e, k, &t0);
-      if (ub < best || (ub == best && e > be)) continue;
+      if ((double)upper(e, k, &t0) <= best) continue;
     }
     const double m = exact(e, k, (double)t0);
-    if (m > best || (m == best && e < be)) {
+    if (m > best) {
       best = m;
       be = e;
     }
     if (q < 0) {
-      if (!((double)ub2 >= best)) break;
+      if (!((double)ub2 > best)) break;
       q = 0;
+    }
+  }
+  // the deciding element: the lowest index whose margin is within
+  // CERT_ELEM_TIE of the maximum (elements inside obstacles all reach their
+  // radius; the whole-cell certificate subtracts the same tolerance)
+  for (int e = 0; e < be; e++) {
+    bool found = false;
+    for (int k = 0; k < nobs && !found; k++) {
+      float t0;
+      if ((double)upper(e, k, &t0) < best - CERT_ELEM_TIE) continue;
+      found = exact(e, k, (double)t0) >= best - CERT_ELEM_TIE;
+    }
+    if (found) {
+      be = e;
+      break;
     }
   }
   margin[p] = best;
@@ -593,7 +606,7 @@ __global__ void k_certify_cells_whole(const int64_t *off, const int64_t *idx, in
       const double v = pts[i * d + k];
       drop = fma(L[e * d + k], fmax(hi[k] - v, v - lo[k]), drop);
     }
-    slack = fmax(slack, margin[i] - drop);
+    slack = fmax(slack, (margin[i] - CERT_ELEM_TIE) - drop);
   }
   if (whole) whole[c] = slack >= 0.0 ? 1 : 0;
   if (slack_out) slack_out[c] = slack;
@@ -697,8 +710,9 @@ __global__ void k_certify_cells_whole32(const int64_t *off, const int64_t *idx, 
     const float m = r[d];
     const float sl = m - drop;
     const float eps = 2.f * u * (2.f * fabsf(m) + lsum) + 1e-30f;
-    if (sl - eps >= 0.f) yes = true;
-    else if (sl + eps >= 0.f) undecided = true;
+    // certified iff the exact slack margin - tie - drop is >= 0
+    if (sl - eps >= (float)CERT_ELEM_TIE) yes = true;
+    else if (sl + eps >= (float)CERT_ELEM_TIE) undecided = true;
   }
   if (!yes && undecided) {
     // close to the decision: the exact FP64 certificate
@@ -728,7 +742,7 @@ __global__ void k_certify_cells_whole32(const int64_t *off, const int64_t *idx, 
         const double v = pts[i * d + k];
         drop = fma(L[e * d + k], fmax(dhi[k] - v, v - dlo[k]), drop);
       }
-      slack = fmax(slack, margin[i] - drop);
+      slack = fmax(slack, (margin[i] - CERT_ELEM_TIE) - drop);
     }
     yes = slack >= 0.0;
   }

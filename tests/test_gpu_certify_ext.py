@@ -48,7 +48,7 @@ def _scene(rng, reach, n_box=6, n_sph=4, n_cyl=6):
     return np.array(types, np.int32), np.array(poses), np.array(dims)
 
 
-def _robot(rng, n, spheres_per_link=3):
+def _robot(rng, n, spheres_per_link=3, radius=0.04):
     dh = np.zeros((n, 4))
     dh[:, 0] = rng.uniform(-1, 1, n)
     dh[:, 1] = rng.uniform(0, 0.2, n)
@@ -59,7 +59,7 @@ def _robot(rng, n, spheres_per_link=3):
                        rng.uniform(-0.03, 0.03, link.shape[0]),
                        rng.uniform(-0.03, 0.03, link.shape[0])], 1)
     rad = rng.uniform(0.03, 0.08, link.shape[0])
-    return dh, np.full(n, 0.04), (link, centre, rad)
+    return dh, np.full(n, radius), (link, centre, rad)
 
 
 def _compare(g, o, cells=False):
@@ -99,21 +99,26 @@ def test_elements_and_cylinders_against_oracle(ctx, d, mode):
 
 
 def test_whole_cell_certificate_against_oracle(ctx):
-    """Point clouds as cells (3-8 points, spreads 0.002-0.05 rad) around random
-    configurations of a 5-link arm with spheres, boxes, spheres and cylinders."""
+    """Point clouds as cells (3-8 points, spreads 0.0005-0.01 rad) around
+    random configurations of a 5-link arm (capsules of radius 0.06, spheres)
+    among boxes, spheres and cylinders: about a quarter of the cells have
+    every point in collision, and most of those are certified whole."""
     rng = np.random.default_rng(47)
     d = 5
-    dh, radius, spheres = _robot(rng, d)
-    types, pose, dims = _scene(rng, float(dh[:, 2].sum()) * 0.5, 8, 4, 8)
+    dh, radius, spheres = _robot(rng, d, radius=0.06)
+    types, pose, dims = _scene(rng, float(dh[:, 2].sum()) * 0.9, 4, 2, 4)
     pts, off = [], [0]
     for _ in range(3000):
         m = int(rng.integers(3, 9))
         pts.append(rng.uniform(-math.pi, math.pi, d) +
-                   rng.normal(scale=rng.choice([0.002, 0.01, 0.05]), size=(m, d)))
+                   rng.normal(scale=rng.choice([0.0005, 0.002, 0.01]), size=(m, d)))
         off.append(off[-1] + m)
     pts = np.concatenate(pts)
     off = np.array(off, np.int64)
-    idx = rng.permutation(pts.shape[0]).astype(np.int64)  # rows in any order
+    # the points stored in a shuffled order: the rows index them where they are
+    perm = rng.permutation(pts.shape[0])
+    pts = pts[perm]
+    idx = np.argsort(perm).astype(np.int64)
     g = ctx.certify_ex(dh, radius, types, pose, dims, pts, off, idx, spheres=spheres)
     o = oracle.certify_ex(dh, radius, types, pose, dims, pts, off, idx, spheres=spheres)
     gw = _compare(g, o, cells=True)
