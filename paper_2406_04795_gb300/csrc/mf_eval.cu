@@ -948,6 +948,20 @@ __device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const int *near
   return r;
 }
 
+// The FP32 part of a root evaluation at xs: the mid entries, then the weak
+// ones, as one lane-strided list (accumulated into acc.wf / wg / weak).
+template <bool GRAD, int D>
+__device__ __forceinline__ void root_fp32_part(const MfRbfDev &R, const int *near, int nw,
+                                               const int *midl, int nm, const Split32<D> &xs,
+                                               F64Acc &acc) {
+  const int lane = threadIdx.x & 31;
+  const int nr = nm + nw;
+  for (int i = lane; i < nr; i += 32) {
+    const int j = i < nm ? midl[i] : near[NEAR_CAP - 1 - (i - nm)];
+    f32_weak_term<GRAD, D>(R, xs, j, acc);
+  }
+}
+
 // FP64 evaluation of g and g' at x over the near list (all lanes); xs is x
 // split into FP32 hi/lo parts for the weak terms.
 template <bool ALL_STRONG, bool GRAD, int D>
@@ -960,10 +974,13 @@ __device__ __forceinline__ F64Acc root_eval64(const MfRbfDev &R, const int *near
   for (int i = lane; i < ns; i += 32) f64_term<GRAD, D>(R, x, dir, near[i], acc);
   // mid entries, then weak ones, as one list
   const int nr = nm + nw;
-  for (int i = lane; i < nr; i += 32) {
-    const int j = i < nm ? midl[i] : near[NEAR_CAP - 1 - (i - nm)];
-    if (ALL_STRONG) f64_term<GRAD, D>(R, x, dir, j, acc);
-    else f32_weak_term<GRAD, D>(R, xs, j, acc);
+  if (ALL_STRONG) {
+    for (int i = lane; i < nr; i += 32) {
+      const int j = i < nm ? midl[i] : near[NEAR_CAP - 1 - (i - nm)];
+      f64_term<GRAD, D>(R, x, dir, j, acc);
+    }
+  } else {
+    root_fp32_part<GRAD, D>(R, near, nw, midl, nm, xs, acc);
   }
   terms[0] += ns + (ALL_STRONG ? nr : 0);
   terms[1] += ALL_STRONG ? 0 : nr;
@@ -991,6 +1008,16 @@ __device__ __forceinline__ bool root_fp32_part_too_coarse(const MfRbfDev &R, flo
   return weak * (1.01f * R.weak_rel32) > lim;
 }
 
+// A root step handed to the lane-per-edge FP64 kernel (k_roots_defer): the
+// edge, the FP32 stage's t (where the FP64 evaluation happens), the reused
+// g' there and |g''|, the FP32 part of g at t (mid and weak terms, already
+// checked against its error bound), and its strong entries in the list pool.
+struct __align__(16) RootRec {
+  unsigned long long e;
+  float t, gp, gpp, wf;
+  uint32_t off, ns;
+};
+
 // Per-warp shared state of the FP64 stage (the point, the direction and the
 // FP32 split of the point): warp-uniform values kept out of registers.
 struct RootWarpState {
@@ -1003,7 +1030,7 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
                           double tol, const int *src, int srcn, int *near, int *midl, int *qs,
                           int *qw,
                           RootWarpState *ws, unsigned long long &evals, unsigned long long *terms,
-                          bool fast) {
+                          bool fast, bool defer) {
   const int lane = threadIdx.x & 31;
   const int d = dim_of<D>(F.d);
   const unsigned lt = (1u << lane) - 1u;
@@ -1223,6 +1250,40 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
       gpf = fmaf(gpp, (float)t - t_eval, gp32);
       reuse = gp32 != 0.f && isfinite(gpf) && fabsf(gpf) > 0.5f * fabsf(gp32);
     }
+    if (defer && reuse) {
+      // the common case -- one FP64 step with the reused g' -- runs lane per
+      // edge in k_roots_defer: this warp computes the step's FP32 part and
+      // hands over the strong entries (unless the part's error bound is too
+      // coarse or the pools are full; the step then runs here)
+      F64Acc part = {0.0, 0.0, 0.f, 0.f, 0.f};
+      root_fp32_part<false, D>(R, near, nw, midl, nm, xs, part);
+      const float wf = mf_warp_sum_f(part.wf), weak = mf_warp_sum_f(part.weak);
+      if (!root_fp32_part_too_coarse(R, weak, gpf, fast)) {
+        unsigned long long at = 0, lat = 0;
+        if (lane == 0) {
+          at = atomicAdd(&B.cnt->n_defer, 1ull);
+          lat = atomicAdd(&B.cnt->n_defer_list, (unsigned long long)ns);
+        }
+        at = __shfl_sync(FULL, at, 0);
+        lat = __shfl_sync(FULL, lat, 0);
+        if (at < B.defer_cap && lat + ns <= B.defer_list_cap) {
+          for (int i = lane; i < ns; i += 32) B.defer_list[lat + i] = near[i];
+          if (lane == 0) {
+            RootRec r;
+            r.e = e;
+            r.t = t32;
+            r.gp = gpf;
+            r.gpp = gppf;
+            r.wf = wf;
+            r.off = (uint32_t)lat;
+            r.ns = (uint32_t)ns;
+            reinterpret_cast<RootRec *>(B.defer_rec)[at] = r;
+          }
+          terms[1] += nm + nw;
+          return;
+        }
+      }
+    }
     if (overflow) {
       a = warp_f64<true, D>(R, x, dir, qs, qw, terms);
       gpf = (float)a.g;
@@ -1343,10 +1404,13 @@ __device__ int group_screen(const MfFrame &F, const MfRbfDev &R, const MfTraceBu
   return gn <= GROUP_CAP ? gn : -1;
 }
 
+// Root solve of edges [e0, e0 + n) (list == NULL), or of the edges listed
+// in list[0 .. min(*n_list, n)) (the redo queue).  defer: hand the common
+// single-step case to k_roots_defer.
 template <int D, int MINB>
-__global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(MfFrame F, MfRbfDev R, MfTraceBufs B,
-                                                               uint64_t n_edges, double tol,
-                                                               int group, int fast) {
+__global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(
+    MfFrame F, MfRbfDev R, MfTraceBufs B, uint64_t e0, uint64_t n_edges, double tol, int group,
+    int fast, int defer, const uint64_t *list, const unsigned long long *n_list) {
   __shared__ int snear[ROOT_WARPS][NEAR_CAP];
   __shared__ int smid[ROOT_WARPS][MID_CAP];
   __shared__ int sq[ROOT_WARPS][2][64];
@@ -1357,21 +1421,122 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(MfFrame F, 
   const uint64_t nwarps = (uint64_t)gridDim.x * ROOT_WARPS;
   const float rs = sqrtf(R.screen_r2);
   unsigned long long evals = 0, terms[2] = {0, 0};
-  if (group <= 1) {
-    for (uint64_t e = (uint64_t)blockIdx.x * ROOT_WARPS + w; e < n_edges; e += nwarps)
-      root_edge<D>(F, R, B, e, tol, nullptr, 0, snear[w], smid[w], sq[w][0], sq[w][1], &sws[w],
-                   evals, terms, fast != 0);
+  if (list) {
+    const uint64_t nl = *n_list < n_edges ? *n_list : n_edges;
+    for (uint64_t i = (uint64_t)blockIdx.x * ROOT_WARPS + w; i < nl; i += nwarps)
+      root_edge<D>(F, R, B, list[i], tol, nullptr, 0, snear[w], smid[w], sq[w][0], sq[w][1],
+                   &sws[w], evals, terms, fast != 0, false);
+  } else if (group <= 1) {
+    for (uint64_t i = (uint64_t)blockIdx.x * ROOT_WARPS + w; i < n_edges; i += nwarps)
+      root_edge<D>(F, R, B, e0 + i, tol, nullptr, 0, snear[w], smid[w], sq[w][0], sq[w][1],
+                   &sws[w], evals, terms, fast != 0, defer != 0);
   } else {
     const uint64_t G = (uint64_t)group;
     for (uint64_t g0 = ((uint64_t)blockIdx.x * ROOT_WARPS + w) * G; g0 < n_edges; g0 += nwarps * G) {
       const int ng = (int)(n_edges - g0 < G ? n_edges - g0 : G);
-      const int gn = group_screen<D>(F, R, B, g0, ng, rs, sgrp);
+      const int gn = group_screen<D>(F, R, B, e0 + g0, ng, rs, sgrp);
       for (int q = 0; q < ng; q++)
-        root_edge<D>(F, R, B, g0 + q, tol, gn >= 0 ? sgrp : nullptr, gn, snear[w], smid[w],
-                     sq[w][0], sq[w][1], &sws[w], evals, terms, fast != 0);
+        root_edge<D>(F, R, B, e0 + g0 + q, tol, gn >= 0 ? sgrp : nullptr, gn, snear[w], smid[w],
+                     sq[w][0], sq[w][1], &sws[w], evals, terms, fast != 0, defer != 0);
     }
   }
   root_flush(B, evals, terms);
+}
+
+// The deferred FP64 root steps, one thread per record: the edge's end points
+// and the evaluation point x = x1 + t (x2 - x1) in the operation order of
+// root_edge, g = (FP64 strong terms, summed in list order) + (FP32 part) + b,
+// one Newton step with the reused g' under root_edge's acceptance tests.
+// Accepted steps write t and the point; the others go to the redo queue.
+template <int D>
+__global__ void __launch_bounds__(256) k_roots_defer(MfFrame F, MfRbfDev R, MfTraceBufs B,
+                                                     uint64_t cap, double tol, int fast) {
+  const unsigned long long nrec = B.cnt->n_defer < cap ? B.cnt->n_defer : cap;
+  const int d = dim_of<D>(F.d);
+  const float tolf = (float)tol;
+  unsigned long long terms = 0, evals = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nrec;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const RootRec rec = reinterpret_cast<const RootRec *>(B.defer_rec)[i];
+    const uint64_t e = rec.e;
+    long long sy = 0;
+    int32_t y[D];
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+      y[k] = k < d ? B.edge_y[e * d + k] : 0;
+      sy += y[k];
+    }
+    const uint32_t mask = B.edge_mask[e] & ((1u << d) - 1u);
+    const double cs1 = __dmul_rn(F.c, (double)sy);
+    const double cs2 = __dmul_rn(F.c, (double)(sy + __popc(mask)));
+    const double t = (double)rec.t;
+    double x1[D], dir[D], x[D];
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+      if (k < d) {
+        x1[k] = __dadd_rn(__dmul_rn(F.lam, __dsub_rn((double)y[k], cs1)), F.o[k]);
+        const double x2 = __dadd_rn(
+            __dmul_rn(F.lam, __dsub_rn((double)(y[k] + (int32_t)((mask >> k) & 1u)), cs2)), F.o[k]);
+        dir[k] = __dsub_rn(x2, x1[k]);
+        x[k] = __dadd_rn(x1[k], __dmul_rn(t, dir[k]));
+      } else {
+        x1[k] = dir[k] = x[k] = 0.0;
+      }
+    }
+    double fs = 0.0;
+    for (uint32_t q = 0; q < rec.ns; q++) {
+      const int j = B.defer_list[rec.off + q];
+      double r2 = 0.0;
+      const double2 *row = reinterpret_cast<const double2 *>(R.sv64r + (int64_t)j * 8);
+#pragma unroll
+      for (int k2 = 0; k2 < (D + 1) / 2; k2++) {
+        const double2 sv = __ldg(row + k2);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const int k = 2 * k2 + h;
+          if (k < D && k < d) {
+            const double u = x[k] - (h ? sv.y : sv.x);
+            r2 = fma(u, u, r2);
+          }
+        }
+      }
+      fs += R.alpha[j] * mf_exp_neg(-R.gamma * r2, R.exp_tab);
+    }
+    terms += rec.ns;
+    evals++;
+    const double f = fs + (double)rec.wf + R.b;
+    double tn = t;
+    bool ok = true;
+    const long long fb = __double_as_longlong(f);
+    if ((fb << 1) != 0) {  // f = +-0 keeps t
+      const bool s1 = B.edge_f[2 * e] >= 0.0;
+      double lo = 0.0, hi = 1.0;
+      if ((fb >= 0) == s1) lo = t; else hi = t;
+      tn = fma(-f, (double)(1.0f / rec.gp), t);
+      ok = tn > lo && tn < hi;
+      if (ok) {
+        const float step = fabsf((float)(tn - t));
+        ok = step <= tolf || step <= 1e-7f || hi - lo <= 9.094947017729282e-13 ||
+             (step <= (fast ? 1e-3f : 1e-5f) &&
+              rec.gpp * step * step <= (fast ? 1e-7f : 5e-11f) * fabsf(rec.gp));
+      }
+    }
+    if (ok) {
+      B.edge_t[e] = tn;
+#pragma unroll
+      for (int k = 0; k < D; k++)
+        if (k < d) B.edge_pt[e * d + k] = __dadd_rn(x1[k], __dmul_rn(tn, dir[k]));
+    } else {
+      const unsigned long long q = atomicAdd(&B.cnt->n_redo, 1ull);
+      if (q < cap) B.redo[q] = e;
+    }
+  }
+  // warp totals of the counters
+  unsigned long long te = mf_warp_sum_ull(evals), tt = mf_warp_sum_ull(terms);
+  if ((threadIdx.x & 31) == 0 && te) {
+    atomicAdd(&B.cnt->root_evals, te);
+    atomicAdd(&B.cnt->root_terms, tt);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1532,7 +1697,7 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, 2) k_b_roots(const MfSlot *sl
       for (int q = 0; q < ng; q++)
         root_edge<D>(S.F, S.R, S.B, e0 + q, S.root_tol, gn >= 0 ? sgrp : nullptr, gn, snear[w],
                      smid[w], sq[w][0], sq[w][1], &sws[w], evals, terms,
-                     S.precision != MF_FP64 && !(S.flags & MF_ROOTS_FP64_EXACT));
+                     S.precision != MF_FP64 && !(S.flags & MF_ROOTS_FP64_EXACT), false);
       root_flush(S.B, evals, terms);
       i = end;
     }
@@ -1615,22 +1780,39 @@ void mf_launch_eval_vertices_mixed(const MfFrame &F, const MfRbfDev &R, const Mf
 
 template <int DD, int MINB>
 static void launch_roots_d(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B,
-                           uint64_t n_edges, double tol, int grid, int group, int fast,
+                           uint64_t n_edges, double tol, int grid, int group, int fast, int sms,
                            cudaStream_t st) {
   const int dyn = group > 1 ? ROOT_WARPS * GROUP_CAP * (int)sizeof(int) : 0;
   if (dyn) cudaFuncSetAttribute(k_roots_f64<DD, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-  k_roots_f64<DD, MINB><<<grid, ROOT_WARPS * 32, dyn, st>>>(F, R, B, n_edges, tol, group, fast);
+  if (!B.defer_rec || B.defer_cap == 0) {
+    k_roots_f64<DD, MINB><<<grid, ROOT_WARPS * 32, dyn, st>>>(F, R, B, 0, n_edges, tol, group, fast,
+                                                             0, nullptr, nullptr);
+    return;
+  }
+  // chunks of defer_cap edges: the warp kernel (deferring the common
+  // single-step case), the lane-per-edge FP64 steps, then the redo queue
+  const size_t off_defer = offsetof(MfCounters, n_defer);
+  const size_t span = offsetof(MfCounters, n_redo) + sizeof(unsigned long long) - off_defer;
+  for (uint64_t e0 = 0; e0 < n_edges; e0 += B.defer_cap) {
+    const uint64_t n = n_edges - e0 < B.defer_cap ? n_edges - e0 : B.defer_cap;
+    cudaMemsetAsync((char *)B.cnt + off_defer, 0, span, st);
+    k_roots_f64<DD, MINB><<<grid, ROOT_WARPS * 32, dyn, st>>>(F, R, B, e0, n, tol, group, fast, 1,
+                                                             nullptr, nullptr);
+    k_roots_defer<DD><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(F, R, B, B.defer_cap, tol, fast);
+    k_roots_f64<DD, MINB><<<sms * 4, ROOT_WARPS * 32, 0, st>>>(F, R, B, 0, B.defer_cap, tol, 1,
+                                                              fast, 0, B.redo, &B.cnt->n_redo);
+  }
 }
 
 template <int MINB>
 static void launch_roots(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, uint64_t n_edges,
-                         double tol, int grid, int group, int fast, cudaStream_t st) {
+                         double tol, int grid, int group, int fast, int sms, cudaStream_t st) {
   switch (F.d) {
 #define MF_CASE(DD) \
-  case DD: launch_roots_d<DD, MINB>(F, R, B, n_edges, tol, grid, group, fast, st); break;
+  case DD: launch_roots_d<DD, MINB>(F, R, B, n_edges, tol, grid, group, fast, sms, st); break;
     MF_CASE(2) MF_CASE(3) MF_CASE(4) MF_CASE(5) MF_CASE(6) MF_CASE(7)
 #undef MF_CASE
-    default: launch_roots_d<MF_MAXD, MINB>(F, R, B, n_edges, tol, grid, group, fast, st);
+    default: launch_roots_d<MF_MAXD, MINB>(F, R, B, n_edges, tol, grid, group, fast, sms, st);
   }
 }
 
@@ -1638,8 +1820,8 @@ void mf_launch_roots_f64(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs 
                          double tol, const MfTune &T, int sms, cudaStream_t st, bool fast) {
   if (n_edges == 0) return;
   const int grid = sms * T.roots_bps;
-  if (T.roots_variant == 1) launch_roots<3>(F, R, B, n_edges, tol, grid, T.roots_group, fast, st);
-  else launch_roots<2>(F, R, B, n_edges, tol, grid, T.roots_group, fast, st);
+  if (T.roots_variant == 1) launch_roots<3>(F, R, B, n_edges, tol, grid, T.roots_group, fast, sms, st);
+  else launch_roots<2>(F, R, B, n_edges, tol, grid, T.roots_group, fast, sms, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -3,6 +3,7 @@
 // open-addressing hash tables, and the trace's device counters.
 #pragma once
 #include <cmath>
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -55,6 +56,9 @@ struct MfCounters {
   unsigned long long root_terms_weak;  // RBF terms with the reduced-cost exp, root solve
   unsigned long long n_vlist;      // entries taken from the per-vertex list pool
   unsigned long long root_overflow;  // edges whose screen lists overflowed (full re-evaluation)
+  unsigned long long n_defer;      // root steps handed to the lane-per-edge FP64 kernel
+  unsigned long long n_defer_list; // their strong-term list entries
+  unsigned long long n_redo;       // deferred steps not accepted (solved again in full)
   unsigned int err_table_full;     // a hash probe ran past the table
   unsigned int err_overflow;       // a list ran past its capacity
   unsigned int err_missing;        // a vertex expected in the table was absent
@@ -103,6 +107,13 @@ struct MfTraceBufs {
   uint32_t *vlist_n;    // [MV] its length, MF_NO_LIST when it has none
   uint64_t vlist_cap;   // pool capacity (entries)
   float list_r2;
+  // Deferred FP64 root steps of one chunk of edges (NULL: none): records of
+  // the edges whose single FP64 Newton step runs lane per edge, their
+  // strong-term lists, and the queue of edges to solve again in full.
+  void *defer_rec;          // [defer_cap] records (32 bytes each)
+  int32_t *defer_list;      // [defer_list_cap] support-vector indices
+  uint64_t *redo;           // [defer_cap] edge indices
+  uint64_t defer_cap, defer_list_cap;
 };
 #define MF_NO_LIST 0xFFFFFFFFu
 
@@ -493,6 +504,11 @@ __device__ __forceinline__ void mf_emit_edge(const MfFrame &F, const MfTraceBufs
   mf_etab_val(B, slot) = (uint32_t)idx;
 }
 
+__device__ __forceinline__ unsigned long long mf_warp_sum_ull(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 __device__ __forceinline__ float mf_warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -587,5 +603,6 @@ enum {
   MF_SLOT_VLIST = 13,
   MF_SLOT_SUBDIV = 14,
   MF_SLOT_SORT = 15,
-  MF_NUM_SLOTS = 16
+  MF_SLOT_DEFER = 16,
+  MF_NUM_SLOTS = 17
 };

@@ -1117,6 +1117,24 @@ static int setup_buffers(mf_ctx *ctx, int d, uint64_t ME, uint64_t MV, uint64_t 
   B->max_cells = MC;
   B->cnt = (MfCounters *)mf_ctx_buffer(ctx, MF_SLOT_COUNTERS, sizeof(MfCounters));
   if (!B->cnt) return MF_ERR_OOM;
+  // deferred FP64 root steps: chunks of up to 4M edges, ~48 strong entries
+  // each on average (when the budget allows; else every step runs in the
+  // warp-per-edge kernel)
+  {
+    const uint64_t dc = std::min<uint64_t>(ME, 1ull << 22), dl = dc * 48;
+    const size_t db = al(dc * 32) + al(dc * 8) + al(dl * 4);
+    std::string keep = ctx->err;
+    char *q = (char *)mf_ctx_buffer(ctx, MF_SLOT_DEFER, db);
+    if (q) {
+      B->defer_rec = q; q += al(dc * 32);
+      B->redo = (uint64_t *)q; q += al(dc * 8);
+      B->defer_list = (int32_t *)q;
+      B->defer_cap = dc;
+      B->defer_list_cap = dl;
+    } else {
+      ctx->err = keep;
+    }
+  }
   // per-vertex lists for the root screen, when they fit the budget (else
   // the root screen scans the vector blocks)
   if (n_sv > 0) {
