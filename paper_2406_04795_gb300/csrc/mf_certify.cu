@@ -27,6 +27,7 @@
 #define CERT_MAX_OBS 128
 #define CERT_THREADS 128
 #define CERT_ELEM_TIE 1e-9  // margins this close to the maximum tie
+#define CERT_MAX_ELEM (MF_MAXD + MF_MAX_SPHERES)
 
 template <typename T>
 struct CertObsT {
@@ -214,6 +215,22 @@ __device__ __noinline__ T seg_obstacle_dist(const CertObsT<T> &o, const T *pa, c
   return dist > (T)0 ? dist : (T)0;
 }
 
+// Whether the local point a + t dl lies inside the obstacle shrunk by dlt
+// (FP32; the point is evaluated directly, so the answer only depends on dlt
+// covering the coordinates' error).
+__device__ __forceinline__ bool point_deep_inside32(const CertObsT<float> &o, const float *a,
+                                                    const float *dl, float t, float dlt) {
+  const float x = fmaf(t, dl[0], a[0]), y = fmaf(t, dl[1], a[1]), z = fmaf(t, dl[2], a[2]);
+  if (o.type == MF_BOX)
+    return fabsf(x) <= o.h[0] - dlt && fabsf(y) <= o.h[1] - dlt && fabsf(z) <= o.h[2] - dlt;
+  if (o.type == MF_CYLINDER) {
+    const float rr = o.h[0] - dlt;
+    return rr > 0.f && fmaf(x, x, y * y) <= rr * rr && fabsf(z) <= o.h[1] - dlt;
+  }
+  const float rr = o.h[0] - dlt;
+  return rr > 0.f && fmaf(x, x, fmaf(y, y, z * z)) <= rr * rr;
+}
+
 // Lower bound on the distance from segment [pa, pb] to an obstacle, in FP32
 // (eta: a bound on this routine's own rounding of the squared distance).
 // Box: in the box frame F(t) = sum_i max(0, |a_i + t dl_i| - h_i)^2 is convex
@@ -221,8 +238,16 @@ __device__ __noinline__ T seg_obstacle_dist(const CertObsT<T> &o, const T *pa, c
 // box centre reach, or come near, its minimiser t*, and convexity gives
 // F(t*) >= F(t) - |F'(t)| (t or 1 - t), whatever t is.  Every lane does the
 // same work (no breakpoint sort, no divergence).  Sphere: the exact distance.
-__device__ __forceinline__ float seg_obstacle_lb32(const CertObsT<float> &o, const float *pa,
-                                                   const float *pb, float eta, float *tmin) {
+// *deep: a point of the segment lies inside the obstacle shrunk by dlt (the
+// distance is then exactly 0); tested only when the bound is 0.  Its
+// candidates: the middle of the segment's slab-clipped interval in the
+// shrunk box (boxes), the final t and the projection of the centre
+// (cylinders), the closest point (spheres).  Not inlined: the kernel calls
+// it from three places, and one copy keeps the code in the instruction
+// cache.
+__device__ __noinline__ float seg_obstacle_lb32(const CertObsT<float> &o, const float *pa,
+                                                const float *pb, float eta, float dlt, float *tmin,
+                                                bool *deep) {
   const float wa[3] = {pa[0] - o.t[0], pa[1] - o.t[1], pa[2] - o.t[2]};
   const float wb[3] = {pb[0] - o.t[0], pb[1] - o.t[1], pb[2] - o.t[2]};
   float a[3], dl[3];
@@ -237,6 +262,7 @@ __device__ __forceinline__ float seg_obstacle_lb32(const CertObsT<float> &o, con
   if (o.type == MF_CYLINDER) {
     // convex and C^1 as for boxes: three clamped Newton steps, then the
     // convexity bound
+    const float tc = t;
     float F = 0.f, G = 0.f, H = 0.f;
 #pragma unroll
     for (int it = 0; it <= 3; it++) {
@@ -245,12 +271,16 @@ __device__ __forceinline__ float seg_obstacle_lb32(const CertObsT<float> &o, con
     }
     *tmin = t;
     const float lbF = F - 2.f * fabsf(G) * (G > 0.f ? t : 1.f - t) - eta;
+    *deep = !(lbF > 0.f) &&
+            (point_deep_inside32(o, a, dl, tc, dlt) || point_deep_inside32(o, a, dl, t, dlt));
     return lbF > 0.f ? sqrtf(lbF) : 0.f;
   }
   if (o.type != MF_BOX) {
     *tmin = t;
     const float c0 = fmaf(t, dl[0], a[0]), c1 = fmaf(t, dl[1], a[1]), c2 = fmaf(t, dl[2], a[2]);
-    return fmaxf(sqrtf(c0 * c0 + c1 * c1 + c2 * c2) - o.h[0], 0.f);
+    const float lb = fmaxf(sqrtf(c0 * c0 + c1 * c1 + c2 * c2) - o.h[0], 0.f);
+    *deep = !(lb > 0.f) && point_deep_inside32(o, a, dl, t, dlt);
+    return lb;
   }
   float F = 0.f, G = 0.f;  // F(t) and F'(t) / 2
 #pragma unroll
@@ -272,6 +302,22 @@ __device__ __forceinline__ float seg_obstacle_lb32(const CertObsT<float> &o, con
   }
   *tmin = t;
   const float lbF = F - 2.f * fabsf(G) * (G > 0.f ? t : 1.f - t) - eta;
+  *deep = false;
+  if (!(lbF > 0.f)) {
+    // slab clipping against the shrunk box
+    float t0 = 0.f, t1 = 1.f;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      const float hs = o.h[i] - dlt;
+      if (dl[i] != 0.f) {
+        const float inv = 1.f / dl[i];
+        const float ta = (-hs - a[i]) * inv, tb = (hs - a[i]) * inv;
+        t0 = fmaxf(t0, fminf(ta, tb));
+        t1 = fminf(t1, fmaxf(ta, tb));
+      }
+    }
+    *deep = t0 <= t1 && point_deep_inside32(o, a, dl, 0.5f * (t0 + t1), dlt);
+  }
   return lbF > 0.f ? sqrtf(lbF) : 0.f;
 }
 
@@ -298,6 +344,10 @@ __device__ __forceinline__ void cert_sincos(double x, const double2 *tab, double
   *s = fma(e.x, cm, fma(e.y, sr, e.x));
   *c = fma(e.y, cm, fma(-e.x, sr, e.y));
 }
+
+// FP32 record of a point for the whole-cell certificate: coordinates,
+// margin, deciding element (int bits), padded to whole 16-byte units.
+__host__ __device__ __forceinline__ int cert_rec_stride(int d) { return (d + 2 + 3) & ~3; }
 
 // The link loops stay rolled: unrolling them per link count inlines the
 // distance routines once per link and pass, which overflows the instruction
@@ -483,7 +533,11 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(
   // exactly (FP64 chain to its link, FP64 distance); the others only if the
   // second-largest ub exceeds that exact margin, and then only those whose
   // ub does.  The result is the exact maximum.
-  auto upper = [&](int e, int k, float *tmin) -> float {
+  // A pair whose segment provably has a point inside the obstacle (a point
+  // inside it shrunk by the same 1e-4 (1 + scale), which covers the FP32
+  // chain's error in every coordinate) is at distance exactly 0: its margin
+  // is the element's radius, with no FP64 work (*deep).
+  auto upper = [&](int e, int k, float *tmin, bool *deep) -> float {
     float a[3], b[3];
     const float rad = elem32(e, a, b);
     float scale = 1.f;
@@ -493,14 +547,38 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(
     // local coordinates are below 2 scale: the bound's own rounding of the
     // squared distance stays far below 4e-5 (1 + scale)^2
     const float eta = 4e-5f * (1.f + scale) * (1.f + scale);
-    return rad - (seg_obstacle_lb32(sof[k], a, b, eta, tmin) - 1e-4f * (1.f + scale));
+    const float sl = 1e-4f * (1.f + scale);
+    return rad - (seg_obstacle_lb32(sof[k], a, b, eta, sl, tmin, deep) - sl);
   };
+  auto rad64 = [&](int e) -> double { return e < NC ? srad[e] : ssr64[e - NC]; };
+  // first pass: the deep pairs fix a margin without FP64 (best_in, reached
+  // first by element ein); the other pairs give bounds ub (largest ub1 at
+  // (bi, bk), second ub2; per element the largest, ube, and whether it has
+  // a deep pair)
   float ub1 = -INFINITY, ub2 = -INFINITY, tb = 0.f;
-  int bi = -1, bk = -1;
-  for (int e = 0; e < NE; e++)
+  int bi = -1, bk = -1, ein = -1;
+  double best_in = -INFINITY;
+  float ube[CERT_MAX_ELEM];
+  uint64_t deep_lo = 0, deep_hi = 0;  // elements 0..63, 64..
+  auto is_deep = [&](int e) -> bool {
+    return e < 64 ? ((deep_lo >> e) & 1ull) != 0 : ((deep_hi >> (e - 64)) & 1ull) != 0;
+  };
+  for (int e = 0; e < NE; e++) {
+    float um = -INFINITY;
     for (int k = 0; k < nobs; k++) {
       float tk;
-      const float ub = upper(e, k, &tk);
+      bool deep;
+      const float ub = upper(e, k, &tk, &deep);
+      if (deep) {
+        if (e < 64) deep_lo |= 1ull << e;
+        else deep_hi |= 1ull << (e - 64);
+        if (rad64(e) > best_in) {
+          best_in = rad64(e);
+          ein = e;
+        }
+        continue;
+      }
+      um = fmaxf(um, ub);
       if (ub > ub1) {
         ub2 = ub1;
         ub1 = ub;
@@ -511,10 +589,13 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(
         ub2 = ub;
       }
     }
-  // exact margins: first the pair with the largest bound, then (if the
-  // second-largest bound exceeds that margin) every pair whose bound does
-  double best = -INFINITY;
-  int be = -1;
+    ube[e] = um;
+  }
+  // exact margins of the other pairs: first the one with the largest bound
+  // (if it can exceed best_in), then (if the second-largest bound exceeds
+  // the maximum so far) every pair whose bound does
+  double best = best_in;
+  int be = ein;
   for (int q = -1; q < NE * nobs;) {
     int e, k;
     float t0;
@@ -523,12 +604,18 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(
       e = bi;
       k = bk;
       t0 = tb;
+      if (!((double)ub1 > best)) break;
     } else {
       e = q / nobs;
       k = q - e * nobs;
+      if (k == 0 && !((double)ube[e] > best)) {  // no pair of e can exceed best
+        q += nobs;
+        continue;
+      }
       q++;
       if (e == bi && k == bk) continue;
-      if ((double)upper(e, k, &t0) <= best) continue;
+      bool deep;
+      if ((double)upper(e, k, &t0, &deep) <= best || deep) continue;
     }
     const double m = exact(e, k, (double)t0);
     if (m > best) {
@@ -544,11 +631,15 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(
   // CERT_ELEM_TIE of the maximum (elements inside obstacles all reach their
   // radius; the whole-cell certificate subtracts the same tolerance)
   for (int e = 0; e < be; e++) {
-    bool found = false;
-    for (int k = 0; k < nobs && !found; k++) {
-      float t0;
-      if ((double)upper(e, k, &t0) < best - CERT_ELEM_TIE) continue;
-      found = exact(e, k, (double)t0) >= best - CERT_ELEM_TIE;
+    // an element with a deep pair has margin exactly its radius
+    bool found = is_deep(e) && rad64(e) >= best - CERT_ELEM_TIE;
+    if (!is_deep(e) && (double)ube[e] >= best - CERT_ELEM_TIE) {
+      for (int k = 0; k < nobs && !found; k++) {
+        float t0;
+        bool deep;
+        if ((double)upper(e, k, &t0, &deep) >= best - CERT_ELEM_TIE)
+          found = exact(e, k, (double)t0) >= best - CERT_ELEM_TIE;
+      }
     }
     if (found) {
       be = e;
@@ -558,9 +649,11 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(
   margin[p] = best;
   verdict[p] = best >= 0.0 ? 1 : 0;
   if (element) element[p] = (int16_t)be;
-  if (rec32) {  // FP32 coordinates and margin for the whole-cell certificate
-    for (int k = 0; k < d; k++) rec32[p * (d + 1) + k] = (float)pts[p * d + k];
-    rec32[p * (d + 1) + d] = (float)best;
+  if (rec32) {  // FP32 record for the whole-cell certificate
+    const int rs = cert_rec_stride(d);
+    for (int k = 0; k < d; k++) rec32[p * rs + k] = (float)pts[p * d + k];
+    rec32[p * rs + d] = (float)best;
+    rec32[p * rs + d + 1] = __int_as_float(be);
   }
 }
 
@@ -662,14 +755,81 @@ static void lipschitz_table(int NL, const std::vector<double> &dh, bool caps, in
 // (certified) or every point has slack_j + eps_j < 0 (not certified);
 // otherwise it is recomputed in FP64 from the points and margins as
 // k_certify_cells_whole does.
-__global__ void k_certify_cells_whole32(const int64_t *off, const int64_t *idx, int64_t n_cells,
-                                        const float *rec32, const double *pts, int d,
-                                        const double *margin, const int16_t *element,
-                                        const float *L32, const double *L, int NE,
-                                        int64_t n_points, uint8_t *whole, unsigned *bad) {
+// Rows of up to CERT_ROW_CACHE points are read once (the records stay in
+// registers for the second pass); longer rows read the rest twice.
+#define CERT_ROW_CACHE 9
+
+// Range of the cell's points (lo, hi per coordinate, P = largest |p|) from
+// one FP32 record (NV4 float4 units).
+template <int NV4>
+__device__ __forceinline__ void cert_rec_extend(const float4 (&v)[NV4], int d, float (&lo)[MF_MAXD],
+                                                float (&hi)[MF_MAXD], float &P) {
+#pragma unroll
+  for (int q = 0; q < NV4; q++) {
+    const float vv[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+    for (int h = 0; h < 4; h++) {
+      const int k = 4 * q + h;
+      if (k < MF_MAXD && k < d) {
+        lo[k] = fminf(lo[k], vv[h]);
+        hi[k] = fmaxf(hi[k], vv[h]);
+        P = fmaxf(P, fabsf(vv[h]));
+      }
+    }
+  }
+}
+
+// One point's FP32 slack test (see above): sets yes when it certifies the
+// cell, undecided when its error bound straddles the decision.
+template <int NV4>
+__device__ __forceinline__ void cert_rec_test(const float4 (&v)[NV4], int d, int NE,
+                                              const float (&lo)[MF_MAXD], const float (&hi)[MF_MAXD],
+                                              float P, const float *L32, bool &yes, bool &undecided) {
+  float m = 0.f;
+  int e = -1;
+#pragma unroll
+  for (int q = 0; q < NV4; q++) {
+    const float vv[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+    for (int h = 0; h < 4; h++) {
+      if (4 * q + h == d) m = vv[h];
+      if (4 * q + h == d + 1) e = __float_as_int(vv[h]);
+    }
+  }
+  if (e < 0 || e >= NE) return;
+  const float u = 5.9604644775390625e-08f;
+  float drop = 0.f, lsum = 0.f;
+#pragma unroll
+  for (int q = 0; q < NV4; q++) {
+    const float vv[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+    for (int h = 0; h < 4; h++) {
+      const int k = 4 * q + h;
+      if (k < MF_MAXD && k < d) {
+        const float sp = fmaxf(hi[k] - vv[h], vv[h] - lo[k]);
+        const float Lk = __ldg(L32 + e * d + k);
+        drop = fmaf(Lk, sp, drop);
+        lsum = fmaf(Lk, fmaf((float)(d + 4), sp, 2.f * P), lsum);
+      }
+    }
+  }
+  const float sl = m - drop;
+  const float eps = 2.f * u * (2.f * fabsf(m) + lsum) + 1e-30f;
+  // certified iff the exact slack margin - tie - drop is >= 0
+  if (sl - eps >= (float)CERT_ELEM_TIE) yes = true;
+  else if (sl + eps >= (float)CERT_ELEM_TIE) undecided = true;
+}
+
+template <int NV4>
+__global__ void __launch_bounds__(256) k_certify_cells_whole32(
+    const int64_t *off, const int64_t *idx, int64_t n_cells, const float *rec32, const double *pts,
+    int d, const double *margin, const int16_t *element, const float *L32, const double *L, int NE,
+    int64_t n_points, uint8_t *whole, unsigned *bad) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= n_cells) return;
   const int64_t j0 = off[c], j1 = off[c + 1];
+  const int64_t nr = j1 - j0;
+  const float4 *R4 = reinterpret_cast<const float4 *>(rec32);
   float lo[MF_MAXD], hi[MF_MAXD];
 #pragma unroll
   for (int k = 0; k < MF_MAXD; k++) {
@@ -677,42 +837,43 @@ __global__ void k_certify_cells_whole32(const int64_t *off, const int64_t *idx, 
     hi[k] = -INFINITY;
   }
   float P = 0.f;
-  for (int64_t j = j0; j < j1; j++) {
+  float4 cache[CERT_ROW_CACHE][NV4];
+  uint32_t valid = 0;
+#pragma unroll
+  for (int r = 0; r < CERT_ROW_CACHE; r++) {
+    const int64_t i = r < nr ? idx[j0 + r] : -1;
+    const bool in = i >= 0 && i < n_points;
+    if (r < nr && !in) atomicOr(bad, 1u);
+#pragma unroll
+    for (int q = 0; q < NV4; q++)
+      cache[r][q] = in ? __ldg(R4 + i * NV4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (in) {
+      cert_rec_extend<NV4>(cache[r], d, lo, hi, P);
+      valid |= 1u << r;
+    }
+  }
+  for (int64_t j = j0 + CERT_ROW_CACHE; j < j1; j++) {
     const int64_t i = idx[j];
     if (i < 0 || i >= n_points) {
       atomicOr(bad, 1u);
       continue;
     }
-    const float *r = rec32 + i * (d + 1);
-    for (int k = 0; k < d; k++) {
-      const float v = r[k];
-      lo[k] = fminf(lo[k], v);
-      hi[k] = fmaxf(hi[k], v);
-      P = fmaxf(P, fabsf(v));
-    }
+    float4 v[NV4];
+#pragma unroll
+    for (int q = 0; q < NV4; q++) v[q] = __ldg(R4 + i * NV4 + q);
+    cert_rec_extend<NV4>(v, d, lo, hi, P);
   }
-  const float u = 5.9604644775390625e-08f;
   bool yes = false, undecided = false;
-  for (int64_t j = j0; j < j1 && !yes; j++) {
+#pragma unroll
+  for (int r = 0; r < CERT_ROW_CACHE; r++)
+    if ((valid >> r) & 1u) cert_rec_test<NV4>(cache[r], d, NE, lo, hi, P, L32, yes, undecided);
+  for (int64_t j = j0 + CERT_ROW_CACHE; j < j1 && !yes; j++) {
     const int64_t i = idx[j];
     if (i < 0 || i >= n_points) continue;
-    const int e = element[i];
-    if (e < 0 || e >= NE) continue;
-    const float *r = rec32 + i * (d + 1);
-    float drop = 0.f, lsum = 0.f;
-    for (int k = 0; k < d; k++) {
-      const float v = r[k];
-      const float sp = fmaxf(hi[k] - v, v - lo[k]);
-      const float Lk = L32[e * d + k];
-      drop = fmaf(Lk, sp, drop);
-      lsum = fmaf(Lk, fmaf((float)(d + 4), sp, 2.f * P), lsum);
-    }
-    const float m = r[d];
-    const float sl = m - drop;
-    const float eps = 2.f * u * (2.f * fabsf(m) + lsum) + 1e-30f;
-    // certified iff the exact slack margin - tie - drop is >= 0
-    if (sl - eps >= (float)CERT_ELEM_TIE) yes = true;
-    else if (sl + eps >= (float)CERT_ELEM_TIE) undecided = true;
+    float4 v[NV4];
+#pragma unroll
+    for (int q = 0; q < NV4; q++) v[q] = __ldg(R4 + i * NV4 + q);
+    cert_rec_test<NV4>(v, d, NE, lo, hi, P, L32, yes, undecided);
   }
   if (!yes && undecided) {
     // close to the decision: the exact FP64 certificate
@@ -725,10 +886,13 @@ __global__ void k_certify_cells_whole32(const int64_t *off, const int64_t *idx, 
     for (int64_t j = j0; j < j1; j++) {
       const int64_t i = idx[j];
       if (i < 0 || i >= n_points) continue;
-      for (int k = 0; k < d; k++) {
-        const double v = pts[i * d + k];
-        dlo[k] = fmin(dlo[k], v);
-        dhi[k] = fmax(dhi[k], v);
+#pragma unroll
+      for (int k = 0; k < MF_MAXD; k++) {
+        if (k < d) {
+          const double v = pts[i * d + k];
+          dlo[k] = fmin(dlo[k], v);
+          dhi[k] = fmax(dhi[k], v);
+        }
       }
     }
     double slack = -INFINITY;
@@ -738,9 +902,12 @@ __global__ void k_certify_cells_whole32(const int64_t *off, const int64_t *idx, 
       const int e = element[i];
       if (e < 0 || e >= NE) continue;
       double drop = 0.0;
-      for (int k = 0; k < d; k++) {
-        const double v = pts[i * d + k];
-        drop = fma(L[e * d + k], fmax(dhi[k] - v, v - dlo[k]), drop);
+#pragma unroll
+      for (int k = 0; k < MF_MAXD; k++) {
+        if (k < d) {
+          const double v = pts[i * d + k];
+          drop = fma(L[e * d + k], fmax(dhi[k] - v, v - dlo[k]), drop);
+        }
       }
       slack = fmax(slack, (margin[i] - CERT_ELEM_TIE) - drop);
     }
@@ -781,7 +948,7 @@ extern "C" int mf_certify_ex(mf_ctx *ctx, const mf_robot *robot, const mf_scene 
   const size_t o_el = o_L32 + al((size_t)NE * NL * 4 + 8);
   const size_t need_el = whole && !out->element ? al((size_t)n_points * 2 + 8) : 0;
   const size_t o_rec = o_el + need_el;
-  const size_t need_rec = fast ? (size_t)n_points * (d + 1) * 4 : 0;
+  const size_t need_rec = fast ? (size_t)n_points * cert_rec_stride(d) * 4 : 0;
   char *scr = (char *)mf_ctx_buffer(ctx, MF_SLOT_CERT, o_rec + need_rec + 256);
   if (!scr) return MF_ERR_OOM;
   unsigned *bad = (unsigned *)scr;
@@ -854,10 +1021,20 @@ extern "C" int mf_certify_ex(mf_ctx *ctx, const mf_robot *robot, const mf_scene 
   }
   if (whole) {
     MfProfScope ps(ctx, MF_PH_CERT_CELLS, st, 1, n_cells);
-    if (fast)
-      k_certify_cells_whole32<<<(unsigned)((n_cells + 255) / 256), 256, 0, st>>>(
-          cell_off, cell_idx, n_cells, rec32, points, d, out->margin, elem, dL32, dL, NE,
-          n_points, out->cell_whole, bad);
+    const unsigned gc = (unsigned)((n_cells + 255) / 256);
+    const int nv4 = cert_rec_stride(d) / 4;
+    if (fast && nv4 == 1)
+      k_certify_cells_whole32<1><<<gc, 256, 0, st>>>(cell_off, cell_idx, n_cells, rec32, points, d,
+                                                      out->margin, elem, dL32, dL, NE, n_points,
+                                                      out->cell_whole, bad);
+    else if (fast && nv4 == 2)
+      k_certify_cells_whole32<2><<<gc, 256, 0, st>>>(cell_off, cell_idx, n_cells, rec32, points, d,
+                                                      out->margin, elem, dL32, dL, NE, n_points,
+                                                      out->cell_whole, bad);
+    else if (fast)
+      k_certify_cells_whole32<3><<<gc, 256, 0, st>>>(cell_off, cell_idx, n_cells, rec32, points, d,
+                                                      out->margin, elem, dL32, dL, NE, n_points,
+                                                      out->cell_whole, bad);
     else
       k_certify_cells_whole<<<(unsigned)((n_cells + 255) / 256), 256, 0, st>>>(
           cell_off, cell_idx, n_cells, points, d, out->margin, elem, dL, NE, n_points,

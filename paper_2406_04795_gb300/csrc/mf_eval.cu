@@ -1008,15 +1008,26 @@ __device__ __forceinline__ bool root_fp32_part_too_coarse(const MfRbfDev &R, flo
   return weak * (1.01f * R.weak_rel32) > lim;
 }
 
-// A root step handed to the lane-per-edge FP64 kernel (k_roots_defer): the
-// edge, the FP32 stage's t (where the FP64 evaluation happens), the reused
-// g' there and |g''|, the FP32 part of g at t (mid and weak terms, already
-// checked against its error bound), and its strong entries in the list pool.
+// A root step handed to the lane-per-edge FP64 kernels (k_roots_terms,
+// k_roots_finish): the edge (~0: none), the FP32 stage's t (where the FP64
+// evaluation happens), the reused g' there and |g''|, the FP32 part of g at
+// t (mid and weak terms, already checked against its error bound), and its
+// strong entries: ns of them, in the 8-entry chunks from chunk ch on.
 struct __align__(16) RootRec {
   unsigned long long e;
   float t, gp, gpp, wf;
-  uint32_t off, ns;
+  uint32_t ch, ns;
 };
+#define DEFER_CHUNK 8
+
+// The FP64 end points of edge e on axis k, in mf_vertex_x's operation order:
+// x1 = x(y), x2 = x(y + e(mask)), dir = x2 - x1.
+__device__ __forceinline__ void root_ends64(const MfFrame &F, double cs1, double cs2, int32_t yk,
+                                            uint32_t bit, int k, double &x1, double &dir) {
+  x1 = __dadd_rn(__dmul_rn(F.lam, __dsub_rn((double)yk, cs1)), F.o[k]);
+  const double x2 = __dadd_rn(__dmul_rn(F.lam, __dsub_rn((double)(yk + (int32_t)bit), cs2)), F.o[k]);
+  dir = __dsub_rn(x2, x1);
+}
 
 // Per-warp shared state of the FP64 stage (the point, the direction and the
 // FP32 split of the point): warp-uniform values kept out of registers.
@@ -1025,38 +1036,60 @@ struct RootWarpState {
   float hl[3 * MF_MAXD];  // Split32<D> image: hi[D], lo[D], dir[D]
 };
 
+// ep32 / ep64: the chunk's end points from k_roots_prep (edge e at row
+// e - ep0), or NULL (every lane k < d then computes axis k here in FP64).
 template <int D>
 __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, uint64_t e,
                           double tol, const int *src, int srcn, int *near, int *midl, int *qs,
                           int *qw,
                           RootWarpState *ws, unsigned long long &evals, unsigned long long *terms,
-                          bool fast, bool defer) {
+                          bool fast, bool defer, const float *ep32, const double *ep64,
+                          uint64_t ep0) {
   const int lane = threadIdx.x & 31;
   const int d = dim_of<D>(F.d);
   const unsigned lt = (1u << lane) - 1u;
   const float g32 = (float)R.gamma;
   const int ko = lane < d ? lane : 0;  // this lane's axis
-  // endpoints: x1 = x(y), x2 = x(y + e(mask)) in mf_vertex_x's operation order
-  long long sy = 0;
-  int32_t yo = 0;
-#pragma unroll
-  for (int k = 0; k < D; k++) {
-    if (k < d) {
-      const int32_t v = B.edge_y[e * d + k];
-      sy += v;
-      if (k == ko) yo = v;
-    }
-  }
-  const uint32_t mask = B.edge_mask[e] & ((1u << d) - 1u);
-  const double cs1 = __dmul_rn(F.c, (double)sy);
-  const double cs2 = __dmul_rn(F.c, (double)(sy + __popc(mask)));
-  const double x1o = __dadd_rn(__dmul_rn(F.lam, __dsub_rn((double)yo, cs1)), F.o[ko]);
-  const double x2o =
-      __dadd_rn(__dmul_rn(F.lam, __dsub_rn((double)(yo + (int32_t)((mask >> ko) & 1u)), cs2)), F.o[ko]);
-  const double diro = __dsub_rn(x2o, x1o);
-  const float hio = (float)x1o, loo = (float)(x1o - (double)hio), d32o = (float)diro;
   double *dir = ws->dir, *x = ws->x;
   Split32<D> &xs = *reinterpret_cast<Split32<D> *>(ws->hl);
+  // FP64 end points on this lane's axis
+  double x1o = 0.0, diro = 0.0;
+  float hio, loo, d32o, f0f, f1f;
+  bool s1;
+  if (ep32) {
+    const uint64_t r = e - ep0;
+    const float *row = ep32 + r * (uint64_t)MF_EP_ROW(d);
+    hio = lane < d ? row[lane] : 0.f;
+    loo = lane < d ? row[d + lane] : 0.f;
+    d32o = lane < d ? row[2 * d + lane] : 0.f;
+    f0f = row[3 * d];
+    f1f = row[3 * d + 1];
+    s1 = row[3 * d + 2] != 0.f;
+    x1o = ep64[r * 2 * d + ko];
+    diro = ep64[r * 2 * d + d + ko];
+  } else {
+    long long sy = 0;
+    int32_t yo = 0;
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+      if (k < d) {
+        const int32_t v = B.edge_y[e * d + k];
+        sy += v;
+        if (k == ko) yo = v;
+      }
+    }
+    const uint32_t mask = B.edge_mask[e] & ((1u << d) - 1u);
+    const double cs1 = __dmul_rn(F.c, (double)sy);
+    const double cs2 = __dmul_rn(F.c, (double)(sy + __popc(mask)));
+    root_ends64(F, cs1, cs2, yo, (mask >> ko) & 1u, ko, x1o, diro);
+    hio = (float)x1o;
+    loo = (float)(x1o - (double)hio);
+    d32o = (float)diro;
+    const double f0 = B.edge_f[2 * e], f1 = B.edge_f[2 * e + 1];
+    s1 = f0 >= 0.0;
+    f0f = (float)f0;
+    f1f = (float)f1;
+  }
   float x1hi[D], x1lo[D], dir32[D];
   float dd32 = 0.f;
   if (lane < D) {
@@ -1134,10 +1167,15 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
   if (!src && B.vlist) {
     // the base vertex's list from its FP64 evaluation: a superset of the
     // vectors this screen can keep (its radius covers the screen radius
-    // around every point of the edge)
+    // around every point of the edge); k_roots_prep has looked it up
     uint32_t nl = MF_NO_LIST;
     unsigned long long off = 0;
-    if (lane == 0) {
+    if (ep32) {
+      const float *row = ep32 + (e - ep0) * (uint64_t)MF_EP_ROW(d) + 3 * d + 3;
+      nl = __float_as_uint(row[0]);
+      off = (unsigned long long)__float_as_uint(row[1]) |
+            ((unsigned long long)__float_as_uint(row[2]) << 32);
+    } else if (lane == 0) {
       int32_t yv[MF_MAXD];
 #pragma unroll
       for (int k = 0; k < MF_MAXD; k++) yv[k] = k < d ? B.edge_y[e * d + k] : 0;
@@ -1190,11 +1228,9 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
   __syncwarp();
   const bool overflow = ns + nw > NEAR_CAP || nm > MID_CAP;
   if (overflow && lane == 0) atomicAdd(&B.cnt->root_overflow, 1ull);
-  const double f0 = B.edge_f[2 * e], f1 = B.edge_f[2 * e + 1];
-  const bool s1 = f0 >= 0.0;
   // 2. FP32 Halley iteration (cubic: the evaluation yields g'' anyway),
   //    bracketed, from the linear interpolant of the end values
-  float t32 = (float)f0 / ((float)f0 - (float)f1);
+  float t32 = f0f / (f0f - f1f);
   if (!(t32 > 0.f && t32 < 1.f)) t32 = 0.5f;
   // the last FP32 evaluation: g'', g', t, and whether its g' is trusted
   float gpp = INFINITY, gp32 = 0.f, t_eval = 0.f;
@@ -1252,33 +1288,44 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
     }
     if (defer && reuse) {
       // the common case -- one FP64 step with the reused g' -- runs lane per
-      // edge in k_roots_defer: this warp computes the step's FP32 part and
-      // hands over the strong entries (unless the part's error bound is too
-      // coarse or the pools are full; the step then runs here)
+      // edge in k_roots_terms / k_roots_finish: this warp computes the
+      // step's FP32 part and hands over the strong entries (unless the
+      // part's error bound is too coarse or the pools are full; the step
+      // then runs here)
       F64Acc part = {0.0, 0.0, 0.f, 0.f, 0.f};
       root_fp32_part<false, D>(R, near, nw, midl, nm, xs, part);
       const float wf = mf_warp_sum_f(part.wf), weak = mf_warp_sum_f(part.weak);
       if (!root_fp32_part_too_coarse(R, weak, gpf, fast)) {
+        const int nch = (ns + DEFER_CHUNK - 1) / DEFER_CHUNK;
         unsigned long long at = 0, lat = 0;
         if (lane == 0) {
           at = atomicAdd(&B.cnt->n_defer, 1ull);
-          lat = atomicAdd(&B.cnt->n_defer_list, (unsigned long long)ns);
+          lat = atomicAdd(&B.cnt->n_defer_list, (unsigned long long)nch * DEFER_CHUNK);
         }
         at = __shfl_sync(FULL, at, 0);
         lat = __shfl_sync(FULL, lat, 0);
-        if (at < B.defer_cap && lat + ns <= B.defer_list_cap) {
-          for (int i = lane; i < ns; i += 32) B.defer_list[lat + i] = near[i];
-          if (lane == 0) {
-            RootRec r;
-            r.e = e;
-            r.t = t32;
-            r.gp = gpf;
-            r.gpp = gppf;
-            r.wf = wf;
-            r.off = (uint32_t)lat;
-            r.ns = (uint32_t)ns;
-            reinterpret_cast<RootRec *>(B.defer_rec)[at] = r;
-          }
+        const bool rec_ok = at < B.defer_cap;
+        const bool ok = rec_ok && lat + (unsigned long long)nch * DEFER_CHUNK <= B.defer_list_cap;
+        const uint64_t c0 = lat / DEFER_CHUNK, ncap = B.defer_list_cap / DEFER_CHUNK;
+        if (ok) {
+          for (int i = lane; i < nch * DEFER_CHUNK; i += 32) B.defer_list[lat + i] = i < ns ? near[i] : -1;
+          for (int c = lane; c < nch; c += 32) B.defer_chunk[c0 + c] = (uint32_t)at;
+        } else {
+          // chunks granted within the pool stay unused
+          for (uint64_t c = c0 + lane; c < c0 + nch && c < ncap; c += 32) B.defer_chunk[c] = ~0u;
+        }
+        if (lane == 0 && rec_ok) {
+          RootRec r;
+          r.e = ok ? e : ~0ull;
+          r.t = t32;
+          r.gp = gpf;
+          r.gpp = gppf;
+          r.wf = wf;
+          r.ch = (uint32_t)c0;
+          r.ns = (uint32_t)ns;
+          reinterpret_cast<RootRec *>(B.defer_rec)[at] = r;
+        }
+        if (ok) {
           terms[1] += nm + nw;
           return;
         }
@@ -1406,11 +1453,14 @@ __device__ int group_screen(const MfFrame &F, const MfRbfDev &R, const MfTraceBu
 
 // Root solve of edges [e0, e0 + n) (list == NULL), or of the edges listed
 // in list[0 .. min(*n_list, n)) (the redo queue).  defer: hand the common
-// single-step case to k_roots_defer.
+// single-step case to k_roots_terms / k_roots_finish, with the end points
+// from k_roots_prep (B.ep32, rows from e0).
 template <int D, int MINB>
 __global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(
     MfFrame F, MfRbfDev R, MfTraceBufs B, uint64_t e0, uint64_t n_edges, double tol, int group,
     int fast, int defer, const uint64_t *list, const unsigned long long *n_list) {
+  const float *ep32 = defer ? B.ep32 : nullptr;
+  const double *ep64 = defer ? B.defer_x : nullptr;
   __shared__ int snear[ROOT_WARPS][NEAR_CAP];
   __shared__ int smid[ROOT_WARPS][MID_CAP];
   __shared__ int sq[ROOT_WARPS][2][64];
@@ -1425,11 +1475,11 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(
     const uint64_t nl = *n_list < n_edges ? *n_list : n_edges;
     for (uint64_t i = (uint64_t)blockIdx.x * ROOT_WARPS + w; i < nl; i += nwarps)
       root_edge<D>(F, R, B, list[i], tol, nullptr, 0, snear[w], smid[w], sq[w][0], sq[w][1],
-                   &sws[w], evals, terms, fast != 0, false);
+                   &sws[w], evals, terms, fast != 0, false, nullptr, nullptr, 0);
   } else if (group <= 1) {
     for (uint64_t i = (uint64_t)blockIdx.x * ROOT_WARPS + w; i < n_edges; i += nwarps)
       root_edge<D>(F, R, B, e0 + i, tol, nullptr, 0, snear[w], smid[w], sq[w][0], sq[w][1],
-                   &sws[w], evals, terms, fast != 0, defer != 0);
+                   &sws[w], evals, terms, fast != 0, defer != 0, ep32, ep64, e0);
   } else {
     const uint64_t G = (uint64_t)group;
     for (uint64_t g0 = ((uint64_t)blockIdx.x * ROOT_WARPS + w) * G; g0 < n_edges; g0 += nwarps * G) {
@@ -1437,55 +1487,129 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(
       const int gn = group_screen<D>(F, R, B, e0 + g0, ng, rs, sgrp);
       for (int q = 0; q < ng; q++)
         root_edge<D>(F, R, B, e0 + g0 + q, tol, gn >= 0 ? sgrp : nullptr, gn, snear[w], smid[w],
-                     sq[w][0], sq[w][1], &sws[w], evals, terms, fast != 0, defer != 0);
+                     sq[w][0], sq[w][1], &sws[w], evals, terms, fast != 0, defer != 0, ep32, ep64,
+                     e0);
     }
   }
   root_flush(B, evals, terms);
 }
 
-// The deferred FP64 root steps, one thread per record: the edge's end points
-// and the evaluation point x = x1 + t (x2 - x1) in the operation order of
-// root_edge, g = (FP64 strong terms, summed in list order) + (FP32 part) + b,
-// one Newton step with the reused g' under root_edge's acceptance tests.
-// Accepted steps write t and the point; the others go to the redo queue.
+// The end points of edges [e0, e0 + n), one thread per edge, for the warp
+// kernel of the deferred path: FP32 rows (x1 hi, x1 lo, dir, f(x1), f(x2),
+// [f(x1) >= 0]) in B.ep32 and the FP64 x1, dir in the first 2d cap doubles
+// of B.defer_x.
 template <int D>
-__global__ void __launch_bounds__(256) k_roots_defer(MfFrame F, MfRbfDev R, MfTraceBufs B,
-                                                     uint64_t cap, double tol, int fast) {
-  const unsigned long long nrec = B.cnt->n_defer < cap ? B.cnt->n_defer : cap;
+__global__ void __launch_bounds__(256) k_roots_prep(MfFrame F, MfTraceBufs B, uint64_t e0, uint64_t n) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
   const int d = dim_of<D>(F.d);
-  const float tolf = (float)tol;
-  unsigned long long terms = 0, evals = 0;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nrec;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    const RootRec rec = reinterpret_cast<const RootRec *>(B.defer_rec)[i];
-    const uint64_t e = rec.e;
-    long long sy = 0;
-    int32_t y[D];
+  const uint64_t e = e0 + i;
+  long long sy = 0;
+  int32_t y[D];
 #pragma unroll
-    for (int k = 0; k < D; k++) {
-      y[k] = k < d ? B.edge_y[e * d + k] : 0;
-      sy += y[k];
-    }
-    const uint32_t mask = B.edge_mask[e] & ((1u << d) - 1u);
-    const double cs1 = __dmul_rn(F.c, (double)sy);
-    const double cs2 = __dmul_rn(F.c, (double)(sy + __popc(mask)));
-    const double t = (double)rec.t;
-    double x1[D], dir[D], x[D];
+  for (int k = 0; k < D; k++) {
+    y[k] = k < d ? B.edge_y[e * d + k] : 0;
+    sy += y[k];
+  }
+  const uint32_t mask = B.edge_mask[e] & ((1u << d) - 1u);
+  const double cs1 = __dmul_rn(F.c, (double)sy);
+  const double cs2 = __dmul_rn(F.c, (double)(sy + __popc(mask)));
+  float *row = B.ep32 + i * (uint64_t)MF_EP_ROW(d);
+  double *row64 = B.defer_x + i * 2 * (uint64_t)d;
 #pragma unroll
-    for (int k = 0; k < D; k++) {
-      if (k < d) {
-        x1[k] = __dadd_rn(__dmul_rn(F.lam, __dsub_rn((double)y[k], cs1)), F.o[k]);
-        const double x2 = __dadd_rn(
-            __dmul_rn(F.lam, __dsub_rn((double)(y[k] + (int32_t)((mask >> k) & 1u)), cs2)), F.o[k]);
-        dir[k] = __dsub_rn(x2, x1[k]);
-        x[k] = __dadd_rn(x1[k], __dmul_rn(t, dir[k]));
-      } else {
-        x1[k] = dir[k] = x[k] = 0.0;
-      }
+  for (int k = 0; k < D; k++) {
+    if (k < d) {
+      double x1, dir;
+      root_ends64(F, cs1, cs2, y[k], (mask >> k) & 1u, k, x1, dir);
+      const float hi = (float)x1;
+      row[k] = hi;
+      row[d + k] = (float)(x1 - (double)hi);
+      row[2 * d + k] = (float)dir;
+      row64[k] = x1;
+      row64[d + k] = dir;
     }
+  }
+  const double f0 = B.edge_f[2 * e], f1 = B.edge_f[2 * e + 1];
+  row[3 * d] = (float)f0;
+  row[3 * d + 1] = (float)f1;
+  row[3 * d + 2] = f0 >= 0.0 ? 1.f : 0.f;
+  // the base vertex's root-screen list (MF_NO_LIST: none)
+  uint32_t nl = MF_NO_LIST;
+  unsigned long long off = 0;
+  if (B.vlist) {
+    int32_t yv[MF_MAXD];
+#pragma unroll
+    for (int k = 0; k < MF_MAXD; k++) yv[k] = k < d ? y[k < D ? k : 0] : 0;
+    const uint64_t slot = mf_table_find<2>(B.vtab_key, B.vtab_mask, mf_vertex_key(F, yv));
+    if (slot != ~0ull) {
+      const uint32_t vi = B.vtab_idx[slot];
+      nl = B.vlist_n[vi];
+      off = B.vlist_off[vi];
+    }
+  }
+  row[3 * d + 3] = __uint_as_float(nl);
+  row[3 * d + 4] = __uint_as_float((uint32_t)off);
+  row[3 * d + 5] = __uint_as_float((uint32_t)(off >> 32));
+}
+
+// The evaluation point x = x1 + t (x2 - x1) of each deferred step (thread
+// per record), in root_edge's operation order, into B.defer_x after the end
+// points' rows: record i at [2 d cap + i d].
+template <int D>
+__global__ void __launch_bounds__(256) k_roots_x(MfFrame F, MfTraceBufs B, uint64_t cap) {
+  const unsigned long long nrec = B.cnt->n_defer < cap ? B.cnt->n_defer : cap;
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= nrec) return;
+  const int d = dim_of<D>(F.d);
+  const RootRec rec = reinterpret_cast<const RootRec *>(B.defer_rec)[i];
+  if (rec.e == ~0ull) return;
+  long long sy = 0;
+  int32_t y[D];
+#pragma unroll
+  for (int k = 0; k < D; k++) {
+    y[k] = k < d ? B.edge_y[rec.e * d + k] : 0;
+    sy += y[k];
+  }
+  const uint32_t mask = B.edge_mask[rec.e] & ((1u << d) - 1u);
+  const double cs1 = __dmul_rn(F.c, (double)sy);
+  const double cs2 = __dmul_rn(F.c, (double)(sy + __popc(mask)));
+  const double t = (double)rec.t;
+  double *xp = B.defer_x + (cap * 2 * (uint64_t)d) + i * (uint64_t)d;
+#pragma unroll
+  for (int k = 0; k < D; k++) {
+    if (k < d) {
+      double x1, dir;
+      root_ends64(F, cs1, cs2, y[k], (mask >> k) & 1u, k, x1, dir);
+      xp[k] = __dadd_rn(x1, __dmul_rn(t, dir));
+    }
+  }
+}
+
+// FP64 sum of the strong terms of each 8-entry chunk (thread per chunk, so
+// lanes differ by at most the padding of a list's last chunk): alpha_j
+// exp(-gamma |x - s_j|^2) in list order, at the chunk's record's point.
+template <int D>
+__global__ void __launch_bounds__(256) k_roots_terms(MfRbfDev R, MfTraceBufs B, uint64_t cap) {
+  const unsigned long long nrec = B.cnt->n_defer < cap ? B.cnt->n_defer : cap;
+  const unsigned long long nl = B.cnt->n_defer_list;
+  const uint64_t nch = (nl < B.defer_list_cap ? nl : B.defer_list_cap) / DEFER_CHUNK;
+  const int d = dim_of<D>(R.d);
+  for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < nch;
+       c += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t r = B.defer_chunk[c];
+    if (r >= nrec) continue;
+    const double *xp = B.defer_x + (cap * 2 * (uint64_t)d) + r * (uint64_t)d;
+    double x[D];
+#pragma unroll
+    for (int k = 0; k < D; k++) x[k] = k < d ? xp[k] : 0.0;
+    const int4 *pl = reinterpret_cast<const int4 *>(B.defer_list + c * DEFER_CHUNK);
+    const int4 q0 = pl[0], q1 = pl[1];
+    const int js[DEFER_CHUNK] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
     double fs = 0.0;
-    for (uint32_t q = 0; q < rec.ns; q++) {
-      const int j = B.defer_list[rec.off + q];
+#pragma unroll
+    for (int q = 0; q < DEFER_CHUNK; q++) {
+      const int j = js[q];
+      if (j < 0 || j >= R.n) continue;
       double r2 = 0.0;
       const double2 *row = reinterpret_cast<const double2 *>(R.sv64r + (int64_t)j * 8);
 #pragma unroll
@@ -1500,35 +1624,75 @@ __global__ void __launch_bounds__(256) k_roots_defer(MfFrame F, MfRbfDev R, MfTr
           }
         }
       }
-      fs += R.alpha[j] * mf_exp_neg(-R.gamma * r2, R.exp_tab);
+      fs += __ldg(R.alpha + j) * mf_exp_neg(-R.gamma * r2, R.exp_tab);
     }
-    terms += rec.ns;
-    evals++;
-    const double f = fs + (double)rec.wf + R.b;
-    double tn = t;
-    bool ok = true;
-    const long long fb = __double_as_longlong(f);
-    if ((fb << 1) != 0) {  // f = +-0 keeps t
-      const bool s1 = B.edge_f[2 * e] >= 0.0;
-      double lo = 0.0, hi = 1.0;
-      if ((fb >= 0) == s1) lo = t; else hi = t;
-      tn = fma(-f, (double)(1.0f / rec.gp), t);
-      ok = tn > lo && tn < hi;
-      if (ok) {
-        const float step = fabsf((float)(tn - t));
-        ok = step <= tolf || step <= 1e-7f || hi - lo <= 9.094947017729282e-13 ||
-             (step <= (fast ? 1e-3f : 1e-5f) &&
-              rec.gpp * step * step <= (fast ? 1e-7f : 5e-11f) * fabsf(rec.gp));
+    B.defer_part[c] = fs;
+  }
+}
+
+// The deferred FP64 root steps, one thread per record: g = (the chunks'
+// sums in order) + (FP32 part) + b at x, one Newton step with the reused g'
+// under root_edge's acceptance tests.  Accepted steps write t and the point
+// (x1 + t dir in root_edge's order); the others go to the redo queue.
+template <int D>
+__global__ void __launch_bounds__(256) k_roots_finish(MfFrame F, MfRbfDev R, MfTraceBufs B,
+                                                      uint64_t cap, double tol, int fast) {
+  const unsigned long long nrec = B.cnt->n_defer < cap ? B.cnt->n_defer : cap;
+  const int d = dim_of<D>(F.d);
+  const float tolf = (float)tol;
+  unsigned long long terms = 0, evals = 0;
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i < nrec) {
+    const RootRec rec = reinterpret_cast<const RootRec *>(B.defer_rec)[i];
+    if (rec.e != ~0ull) {
+      const uint64_t e = rec.e;
+      double fs = 0.0;
+      const uint32_t nc = (rec.ns + DEFER_CHUNK - 1) / DEFER_CHUNK;
+      for (uint32_t c = 0; c < nc; c++) fs += B.defer_part[rec.ch + c];
+      terms += rec.ns;
+      evals++;
+      const double t = (double)rec.t;
+      const double f = fs + (double)rec.wf + R.b;
+      double tn = t;
+      bool ok = true;
+      const long long fb = __double_as_longlong(f);
+      if ((fb << 1) != 0) {  // f = +-0 keeps t
+        const bool s1 = B.edge_f[2 * e] >= 0.0;
+        double lo = 0.0, hi = 1.0;
+        if ((fb >= 0) == s1) lo = t; else hi = t;
+        tn = fma(-f, (double)(1.0f / rec.gp), t);
+        ok = tn > lo && tn < hi;
+        if (ok) {
+          const float step = fabsf((float)(tn - t));
+          ok = step <= tolf || step <= 1e-7f || hi - lo <= 9.094947017729282e-13 ||
+               (step <= (fast ? 1e-3f : 1e-5f) &&
+                rec.gpp * step * step <= (fast ? 1e-7f : 5e-11f) * fabsf(rec.gp));
+        }
       }
-    }
-    if (ok) {
-      B.edge_t[e] = tn;
+      if (ok) {
+        long long sy = 0;
+        int32_t y[D];
 #pragma unroll
-      for (int k = 0; k < D; k++)
-        if (k < d) B.edge_pt[e * d + k] = __dadd_rn(x1[k], __dmul_rn(tn, dir[k]));
-    } else {
-      const unsigned long long q = atomicAdd(&B.cnt->n_redo, 1ull);
-      if (q < cap) B.redo[q] = e;
+        for (int k = 0; k < D; k++) {
+          y[k] = k < d ? B.edge_y[e * d + k] : 0;
+          sy += y[k];
+        }
+        const uint32_t mask = B.edge_mask[e] & ((1u << d) - 1u);
+        const double cs1 = __dmul_rn(F.c, (double)sy);
+        const double cs2 = __dmul_rn(F.c, (double)(sy + __popc(mask)));
+        B.edge_t[e] = tn;
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+          if (k < d) {
+            double x1, dir;
+            root_ends64(F, cs1, cs2, y[k], (mask >> k) & 1u, k, x1, dir);
+            B.edge_pt[e * d + k] = __dadd_rn(x1, __dmul_rn(tn, dir));
+          }
+        }
+      } else {
+        const unsigned long long q = atomicAdd(&B.cnt->n_redo, 1ull);
+        if (q < cap) B.redo[q] = e;
+      }
     }
   }
   // warp totals of the counters
@@ -1697,7 +1861,8 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, 2) k_b_roots(const MfSlot *sl
       for (int q = 0; q < ng; q++)
         root_edge<D>(S.F, S.R, S.B, e0 + q, S.root_tol, gn >= 0 ? sgrp : nullptr, gn, snear[w],
                      smid[w], sq[w][0], sq[w][1], &sws[w], evals, terms,
-                     S.precision != MF_FP64 && !(S.flags & MF_ROOTS_FP64_EXACT), false);
+                     S.precision != MF_FP64 && !(S.flags & MF_ROOTS_FP64_EXACT), false, nullptr,
+                     nullptr, 0);
       root_flush(S.B, evals, terms);
       i = end;
     }
@@ -1795,10 +1960,14 @@ static void launch_roots_d(const MfFrame &F, const MfRbfDev &R, const MfTraceBuf
   const size_t span = offsetof(MfCounters, n_redo) + sizeof(unsigned long long) - off_defer;
   for (uint64_t e0 = 0; e0 < n_edges; e0 += B.defer_cap) {
     const uint64_t n = n_edges - e0 < B.defer_cap ? n_edges - e0 : B.defer_cap;
+    const unsigned nb = (unsigned)((n + 255) / 256);
     cudaMemsetAsync((char *)B.cnt + off_defer, 0, span, st);
+    k_roots_prep<DD><<<nb, 256, 0, st>>>(F, B, e0, n);
     k_roots_f64<DD, MINB><<<grid, ROOT_WARPS * 32, dyn, st>>>(F, R, B, e0, n, tol, group, fast, 1,
                                                              nullptr, nullptr);
-    k_roots_defer<DD><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(F, R, B, B.defer_cap, tol, fast);
+    k_roots_x<DD><<<nb, 256, 0, st>>>(F, B, B.defer_cap);
+    k_roots_terms<DD><<<sms * 16, 256, 0, st>>>(R, B, B.defer_cap);
+    k_roots_finish<DD><<<nb, 256, 0, st>>>(F, R, B, B.defer_cap, tol, fast);
     k_roots_f64<DD, MINB><<<sms * 4, ROOT_WARPS * 32, 0, st>>>(F, R, B, 0, B.defer_cap, tol, 1,
                                                               fast, 0, B.redo, &B.cnt->n_redo);
   }

@@ -109,13 +109,21 @@ struct MfTraceBufs {
   float list_r2;
   // Deferred FP64 root steps of one chunk of edges (NULL: none): records of
   // the edges whose single FP64 Newton step runs lane per edge, their
-  // strong-term lists, and the queue of edges to solve again in full.
+  // strong-term lists in 8-entry chunks (-1 pads a list), the queue of edges
+  // to solve again in full, the chunk's end points in FP32 for the warp
+  // kernel, and the steps' evaluation points and chunk sums.
   void *defer_rec;          // [defer_cap] records (32 bytes each)
   int32_t *defer_list;      // [defer_list_cap] support-vector indices
   uint64_t *redo;           // [defer_cap] edge indices
+  float *ep32;              // [defer_cap][MF_EP_ROW(d)]: x1 hi, x1 lo, dir, f(x1), f(x2),
+                            // [f(x1) >= 0], base vertex's list length and offset (bits)
+  double *defer_x;          // [defer_cap][2d] FP64 x1, dir; then [defer_cap][d] step points
+  double *defer_part;       // [defer_list_cap / 8] FP64 sum of each chunk
+  uint32_t *defer_chunk;    // [defer_list_cap / 8] record of each chunk (~0: none)
   uint64_t defer_cap, defer_list_cap;
 };
 #define MF_NO_LIST 0xFFFFFFFFu
+#define MF_EP_ROW(d) (3 * (d) + 6)
 
 // Prepared RBF: structure-of-arrays copies for coalesced streaming.
 struct MfRbfDev {

@@ -285,18 +285,32 @@ __global__ void __launch_bounds__(EXPAND_WARPS * 32) k_expand_edges(MfFrame F, M
 }
 
 // ---------------------------------------------------------------------------
-// Cells (Sec. IV-C): the |p1|!|p2|! n-simplex cofaces of every traced edge.
-// Coface j orders p1's elements by the Lehmer code j mod |p1|! and p2's by
-// j / |p1|!; the walk is then rotated so that d comes last: vertex
-// z = y + sum_{i<pos(d)} e_sigma_i - 1, permutation pi.
+// Cells (Sec. IV-C): the n-simplex cofaces of every traced edge (y, y+e(S)).
+// A coface is an ordering sigma of p1 = S followed by an ordering of
+// p2 = T u {d} (|p1|!|p2|! of them); the walk is then rotated so that d comes
+// last: vertex z = y + sum_{i<pos(d)} e_sigma_i - 1, permutation pi.  In
+// the cell's vertex order, position a = d - pos(d) holds y and a + |p1|
+// holds y + e(S); positions a + m (0 < m < |p1|) hold y + e(sigma_0..m-1)
+// and positions i < a hold y - e(sigma_{pos(d)+i+1..d}).
 //
 // A cell has several traced edges (every pair of in-domain vertices of
 // opposite sign: they are connected through crossing triangles whose
 // vertices are in the domain, which the search follows).  It is emitted once,
 // by its canonical pair: the first such pair (i, j), i < j, in the order of
-// its vertices z, z + e(pi_0), ...  The vertex signs come from the edge's
-// link table, so the cell needs no hash table, and its sign mask and CSR
-// row length are known when it is written.
+// its vertices z, z + e(pi_0), ...  That pair is (y, y + e(S)) exactly when
+//   A: every vertex at a position i < a is outside the domain, and
+//   B: every vertex at a + m, 0 < m < |p1|, is outside the domain or has y's
+//      sign
+// (an in-domain vertex before y would pair with y or y + e(S); one between
+// them of the other sign would pair with y first).  A constrains only the
+// elements after d (each suffix set of them, compressed to T, must index an
+// out-of-domain c-vertex), B only the ordering of S (each proper prefix set).
+// So the canonical cofaces are (orderings of S passing B) x (suffix
+// sequences Q passing A) x (orderings of the rest of T before d), counted by
+// chain counts over subsets and unranked directly: the edge enumerates only
+// the cells it writes.  The vertex signs come from the edge's link table, so
+// the cell needs no hash table, and its sign mask and CSR row length are
+// known when it is written.
 // ---------------------------------------------------------------------------
 __constant__ uint32_t c_fact[13] = {1u, 1u, 2u, 6u, 24u, 120u, 720u, 5040u, 40320u, 362880u,
                                     3628800u, 39916800u, 479001600u};
@@ -308,6 +322,9 @@ __constant__ uint32_t c_fact[13] = {1u, 1u, 2u, 6u, 24u, 120u, 720u, 5040u, 4032
 #define LINK_MAX (1 << MF_MAXD)
 struct CellLink {
   uint8_t a[LINK_MAX], b[LINK_MAX], c[LINK_MAX];
+  uint16_t cnt[LINK_MAX];      // chains of p1 prefixes (subsets of S)
+  uint16_t cc[LINK_MAX / 2];   // chains of suffix sets after d (subsets of T)
+  uint32_t cum[LINK_MAX / 2 + 1];  // prefix sums of the p2 orderings per suffix set
 };
 #define CELL_WARPS 8
 
@@ -360,33 +377,123 @@ __device__ __forceinline__ void cells_enum_edge(const MfFrame &F, const MfTraceB
     *dst = code;
   }
   __syncwarp();
-  uint64_t ls = 0, lt = 0;  // the elements of p1 and of p2 (with d), ascending
+  uint64_t ls = 0, lt = 0;  // the elements of S and of T, ascending
   {
     int c1 = 0, c2 = 0;
-    for (int i = 0; i <= d; i++) {
-      if (i < d && ((S >> i) & 1u)) ls |= (uint64_t)i << (4 * c1++);
+    for (int i = 0; i < d; i++) {
+      if ((S >> i) & 1u) ls |= (uint64_t)i << (4 * c1++);
       else lt |= (uint64_t)i << (4 * c2++);
     }
   }
-  const uint32_t f1 = c_fact[n1], total = f1 * c_fact[n2];
-  for (uint32_t j = lane; j < total; j += 32) {
-    // Lehmer decode of each part: sigma_i at nibble i; p = position of d
-    uint64_t sig = 0;
-    int at = 0, p = 0;
-    uint32_t rr[2] = {j % f1, j / f1};
+  const int nt = n2 - 1, nc = 1 << nt;
+  // chain counts by subset size: cnt[U] = orderings of U whose nonempty
+  // prefix sets all pass B (U = S itself always passes); cc[W] = orderings
+  // of W, built from its last element, whose suffix sets all pass A
+  const uint32_t ys = (L.a[0] >> 1) & 1u;
+  for (int lev = 0; lev <= n1 || lev <= nt; lev++) {
+    for (int u = lane; u < na; u += 32) {
+      if (__popc(u) != lev) continue;
+      uint32_t v = 1;
+      if (u) {
+        const uint32_t code = L.a[u];
+        v = 0;
+        if (u == na - 1 || !(code & 1u) || ((code >> 1) & 1u) == ys)
+          for (uint32_t m = (uint32_t)u; m; m &= m - 1) v += L.cnt[u & ~(m & (0u - m))];
+      }
+      L.cnt[u] = (uint16_t)v;
+    }
+    for (int w = lane; w < nc; w += 32) {
+      if (__popc(w) != lev) continue;
+      uint32_t v = 1;
+      if (w) {
+        v = 0;
+        if (!(L.c[w] & 1u))
+          for (uint32_t m = (uint32_t)w; m; m &= m - 1) v += L.cc[w & ~(m & (0u - m))];
+      }
+      L.cc[w] = (uint16_t)v;
+    }
+    __syncwarp();
+  }
+  // cum[w]: p2 orderings whose suffix set (compressed) is below w: each set
+  // W contributes cc[W] (|T| - |W|)! (the rest of T in any order before d)
+  uint32_t run = 0;
+  for (int base = 0; base < nc; base += 32) {
+    const int w = base + lane;
+    uint32_t inc = w < nc ? (uint32_t)L.cc[w] * c_fact[nt - __popc(w)] : 0u;
 #pragma unroll
-    for (int part = 0; part < 2; part++) {
-      uint64_t pool = part ? lt : ls;
-      const int np = part ? n2 : n1;
-      uint32_t r = rr[part];
-      for (int i = 0; i < np; i++) {
-        const uint32_t f = c_fact[np - 1 - i], q = r / f;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    if (w < nc) L.cum[w + 1] = run + inc;
+    run += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  if (lane == 0) L.cum[0] = 0;
+  __syncwarp();
+  const uint32_t c1 = L.cnt[na - 1], total = c1 * run;
+  if (total == 0) return;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(&B.cnt->n_cells, (unsigned long long)total);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  for (uint32_t k = lane; k < total; k += 32) {
+    const unsigned long long idx = base + k;
+    if (idx >= B.max_cells) { atomicOr(&B.cnt->err_overflow, 1u); continue; }
+    // unrank: k = k1 + c1 k2; the ordering of S from its last element back
+    uint32_t k1 = k % c1, k2 = k / c1;
+    uint64_t sig = 0;
+    {
+      uint32_t u = (uint32_t)(na - 1);
+      for (int pos = n1 - 1; pos >= 0; pos--) {
+        for (uint32_t m = u; m; m &= m - 1) {
+          const uint32_t bit = m & (0u - m), c = L.cnt[u & ~bit];
+          if (k1 < c) {
+            sig |= ((ls >> (4 * (__ffs(bit) - 1))) & 15ull) << (4 * pos);
+            u &= ~bit;
+            break;
+          }
+          k1 -= c;
+        }
+      }
+    }
+    // the suffix set W: the first w with cum[w + 1] > k2
+    int lo = 0, hi = nc - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (L.cum[mid + 1] > k2) hi = mid; else lo = mid + 1;
+    }
+    const uint32_t w = (uint32_t)lo, cw = L.cc[w];
+    const uint32_t r2 = k2 - L.cum[w], kp = r2 / cw;
+    uint32_t kq = r2 - kp * cw;
+    const int nw = __popc(w), nP = nt - nw, p = n1 + nP;
+    // the rest of T before d, ordering kp (Lehmer code)
+    {
+      uint64_t pool = 0;
+      int np = 0;
+      for (int b = 0; b < nt; b++)
+        if (!((w >> b) & 1u)) pool |= ((lt >> (4 * b)) & 15ull) << (4 * np++);
+      uint32_t r = kp;
+      for (int i = 0; i < nP; i++) {
+        const uint32_t f = c_fact[nP - 1 - i], q = r / f;
         r -= q * f;
-        const uint64_t v = (pool >> (4 * q)) & 15ull;
-        if (v == (uint64_t)d) p = at;
-        sig |= v << (4 * at++);
+        sig |= ((pool >> (4 * q)) & 15ull) << (4 * (n1 + i));
         const uint64_t low = q ? (pool & ((1ull << (4 * q)) - 1ull)) : 0ull;
         pool = low | ((pool >> (4 * (q + 1))) << (4 * q));
+      }
+    }
+    sig |= (uint64_t)d << (4 * p);
+    // Q after d: walking W back to the empty set gives q_1, q_2, ...
+    {
+      uint32_t ww = w;
+      for (int pos = p + 1; pos <= d; pos++) {
+        for (uint32_t m = ww; m; m &= m - 1) {
+          const uint32_t bit = m & (0u - m), c = L.cc[ww & ~bit];
+          if (kq < c) {
+            sig |= ((lt >> (4 * (__ffs(bit) - 1))) & 15ull) << (4 * pos);
+            ww &= ~bit;
+            break;
+          }
+          kq -= c;
+        }
       }
     }
     // vertex signs in the cell's order: y sits at position a = d - p and
@@ -411,36 +518,29 @@ __device__ __forceinline__ void cells_enum_edge(const MfFrame &F, const MfTraceB
       inm |= (code & 1u) << i;
       posm |= ((code >> 1) & 1u) << i;
     }
-    // canonical pair: the first position i with an in-domain vertex of the
-    // other sign after it (a positive vertex below the highest negative one,
-    // or the reverse), and the first such vertex j after it
+    // the canonical pair, checked: the first position i with an in-domain
+    // vertex of the other sign after it (a positive vertex below the highest
+    // negative one, or the reverse), and the first such vertex after it,
+    // must be a and a + n1
     const uint32_t P = inm & posm, N = inm & ~posm;
     const uint32_t belowN = N ? (1u << (31 - __clz(N))) - 1u : 0u;  // positions below N's top
     const uint32_t belowP = P ? (1u << (31 - __clz(P))) - 1u : 0u;
     const uint32_t cand = (P & belowN) | (N & belowP);
     const int ci = cand ? __ffs(cand) - 1 : -1;
-    bool take = false;
+    bool canon = false;
     if (ci == a) {
       const uint32_t other = (((P >> ci) & 1u) ? N : P) >> (ci + 1);
-      take = ci + __ffs(other) == a + n1;
+      canon = ci + __ffs(other) == a + n1;
     }
-    // one trace per warp here: a ballot-based allocation suffices
-    const unsigned act = __activemask(), m = __ballot_sync(act, take);
-    unsigned long long base = 0;
-    const int leader = m ? __ffs(m) - 1 : lane;
-    if (m && lane == leader) base = atomicAdd(&B.cnt->n_cells, (unsigned long long)__popc(m));
-    base = __shfl_sync(act, base, leader);
-    const unsigned long long idx = base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
-    if (!take) continue;
-    if (idx >= B.max_cells) { atomicOr(&B.cnt->err_overflow, 1u); continue; }
+    if (!canon) atomicOr(&B.cnt->err_missing, 4u);
     // z = y + e(sigma_0..sigma_{p-1}) - 1; pi = sigma_{p+1..d}, sigma_{0..p-1}
     uint32_t inc = 0;
     for (int i = 0; i < p; i++) inc |= 1u << ((sig >> (4 * i)) & 15ull);
-    const uint64_t hi = sig >> (4 * (p + 1)), lo = p ? (sig & ((1ull << (4 * p)) - 1ull)) : 0ull;
-    const uint64_t pi = hi | (lo << (4 * (d - p)));
-    for (int k = 0; k < d; k++) {
-      B.cell_y[idx * d + k] = y[k] + (int32_t)((inc >> k) & 1u) - 1;
-      B.cell_perm[idx * d + k] = (uint8_t)((pi >> (4 * k)) & 15ull);
+    const uint64_t hi4 = sig >> (4 * (p + 1)), lo4 = p ? (sig & ((1ull << (4 * p)) - 1ull)) : 0ull;
+    const uint64_t pi = hi4 | (lo4 << (4 * (d - p)));
+    for (int k2i = 0; k2i < d; k2i++) {
+      B.cell_y[idx * d + k2i] = y[k2i] + (int32_t)((inc >> k2i) & 1u) - 1;
+      B.cell_perm[idx * d + k2i] = (uint8_t)((pi >> (4 * k2i)) & 15ull);
     }
     // sign mask and CSR row length (paths without these arrays count later)
     if (B.cell_sgn) B.cell_sgn[idx] = inm | (posm << 16);
@@ -1062,6 +1162,8 @@ static int read_counters(mf_ctx *ctx, const MfTraceBufs &B, cudaStream_t st) {
   const MfCounters &h = *ctx->h_counters;
   if (h.err_table_full)
     return mf_set_error(ctx, MF_ERR_DEVICE, "a resident hash table is full");
+  if (h.err_missing & 4u)
+    return mf_set_error(ctx, MF_ERR_DEVICE, "an enumerated cell failed its canonical-pair check");
   if (h.err_missing)
     return mf_set_error(ctx, MF_ERR_DEVICE, "vertex missing from the vertex table");
   if (h.err_timeout)
@@ -1122,13 +1224,18 @@ static int setup_buffers(mf_ctx *ctx, int d, uint64_t ME, uint64_t MV, uint64_t 
   // warp-per-edge kernel)
   {
     const uint64_t dc = std::min<uint64_t>(ME, 1ull << 22), dl = dc * 48;
-    const size_t db = al(dc * 32) + al(dc * 8) + al(dl * 4);
+    const size_t db = al(dc * 32) + al(dc * 8) + al(dl * 4) + al(dc * MF_EP_ROW(d) * 4) +
+                      al(dc * 3 * d * 8) + al(dl) + al(dl / 2);
     std::string keep = ctx->err;
     char *q = (char *)mf_ctx_buffer(ctx, MF_SLOT_DEFER, db);
     if (q) {
       B->defer_rec = q; q += al(dc * 32);
       B->redo = (uint64_t *)q; q += al(dc * 8);
-      B->defer_list = (int32_t *)q;
+      B->defer_list = (int32_t *)q; q += al(dl * 4);
+      B->ep32 = (float *)q; q += al(dc * MF_EP_ROW(d) * 4);
+      B->defer_x = (double *)q; q += al(dc * 3 * d * 8);
+      B->defer_part = (double *)q; q += al(dl);  // dl / 8 doubles
+      B->defer_chunk = (uint32_t *)q;            // dl / 8 uint32
       B->defer_cap = dc;
       B->defer_list_cap = dl;
     } else {
