@@ -390,6 +390,34 @@ __device__ __forceinline__ void cells_enum_edge(const MfFrame &F, const MfTraceB
   // prefix sets all pass B (U = S itself always passes); cc[W] = orderings
   // of W, built from its last element, whose suffix sets all pass A
   const uint32_t ys = (L.a[0] >> 1) & 1u;
+  if (na <= 32 && nc <= 32) {
+    // lane u holds cnt[u] and cc[u]; each level sums the lanes one bit below
+    const uint32_t u = (uint32_t)lane;
+    const uint32_t ca = u < (uint32_t)na ? L.a[u] : 0u;
+    const bool oka = u < (uint32_t)na && (u == (uint32_t)(na - 1) || !(ca & 1u) || ((ca >> 1) & 1u) == ys);
+    const bool okc = u < (uint32_t)nc && !(L.c[u] & 1u);
+    uint32_t cv = u == 0 ? 1u : 0u, qv = u == 0 ? 1u : 0u;
+    const int levels = n1 > nt ? n1 : nt;
+    for (int lev = 1; lev <= levels; lev++) {
+      uint32_t sa = 0, sc = 0;
+#pragma unroll
+      for (int b = 0; b < 5; b++) {
+        const uint32_t va = __shfl_xor_sync(0xffffffffu, cv, 1 << b);
+        const uint32_t vc = __shfl_xor_sync(0xffffffffu, qv, 1 << b);
+        if ((u >> b) & 1u) {
+          sa += va;
+          sc += vc;
+        }
+      }
+      if (__popc(u) == lev) {
+        cv = oka ? sa : 0u;
+        qv = okc ? sc : 0u;
+      }
+    }
+    if (u < (uint32_t)na) L.cnt[u] = (uint16_t)cv;
+    if (u < (uint32_t)nc) L.cc[u] = (uint16_t)qv;
+    __syncwarp();
+  } else
   for (int lev = 0; lev <= n1 || lev <= nt; lev++) {
     for (int u = lane; u < na; u += 32) {
       if (__popc(u) != lev) continue;
