@@ -57,9 +57,15 @@ struct MfRbfStats {
 __global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alpha, const int32_t *perm,
                               float *sv32, float *svlo32, double *sv64, double *alpha64,
                               float *alpha32, float *strong32, double *exp_tab, double *sv64r,
-                              float *svhl, MfRbfStats *st) {
+                              float *svhl, float *sv3, float *alpha_lo32, float2 *exp_df,
+                              MfRbfStats *st) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < 64) exp_tab[j] = exp2((double)j / 64.0);
+  for (int t = j; exp_df && t < 1024; t += gridDim.x * blockDim.x) {
+    const double v = exp2(-(double)t / 1024.0);
+    const float hi = (float)v;
+    exp_df[t] = make_float2(hi, (float)(v - (double)hi));
+  }
   double a = 0.0;
   float m = 0.f;
   int bad = 0;
@@ -76,17 +82,28 @@ __global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alph
       sv64r[(int64_t)j * 8 + k] = s;
       svhl[(int64_t)j * 16 + 2 * k] = hi;
       svhl[(int64_t)j * 16 + 2 * k + 1] = lo;
+      // s = s1 + s2 + s3 exactly (53 bits in three 24-bit pieces)
+      if (sv3) {
+        const double r1 = s - (double)hi;
+        sv3[(int64_t)j * 24 + 3 * k] = hi;
+        sv3[(int64_t)j * 24 + 3 * k + 1] = lo;
+        sv3[(int64_t)j * 24 + 3 * k + 2] = (float)(r1 - (double)lo);
+      }
       m = fmaxf(m, fabsf(hi));
     }
     for (int k = d; k < 8; k++) {
       sv64r[(int64_t)j * 8 + k] = 0.0;
       svhl[(int64_t)j * 16 + 2 * k] = 0.f;
       svhl[(int64_t)j * 16 + 2 * k + 1] = 0.f;
+      if (sv3)
+        sv3[(int64_t)j * 24 + 3 * k] = sv3[(int64_t)j * 24 + 3 * k + 1] =
+            sv3[(int64_t)j * 24 + 3 * k + 2] = 0.f;
     }
     double al = alpha[src];
     if (!isfinite(al)) bad = 1;
     alpha64[j] = al;
     alpha32[j] = (float)al;
+    if (alpha_lo32) alpha_lo32[j] = isfinite(al) ? (float)(al - (double)(float)al) : 0.f;
     a = fabs(al);
     // strong iff gamma r^2 < ln(|alpha| / tau)
     strong32[j] = a > STRONG_TAU ? (float)log(a / STRONG_TAU) : -1.0f;
@@ -128,7 +145,7 @@ size_t mf_rbf_prep_bytes(int d, int64_t n) {
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t nb = (size_t)n, nblk = (nb + 31) / 32;
   return 256 + al(nb * d * 8) + 2 * al(nb * d * 4) + 2 * al(nb * 4) + al(64 * 8) + 2 * al(nb * 64) +
-         al(nb * 8) + al(nb * 4) + 2 * al(nblk * d * 4);
+         al(nb * 8) + al(nb * 4) + 2 * al(nblk * d * 4) + al(nb * 96) + al(nb * 4) + al(1024 * 8);
 }
 
 // Orders the vectors along a Morton (Z-order) curve of their coordinates:
@@ -193,7 +210,10 @@ int mf_prepare_rbf_at(mf_ctx *ctx, const mf_rbf *rbf, char *base, MfRbfDev *out,
   int32_t *perm = (int32_t *)p; p += al(nb * 4);
   const int nblk = (n + 31) / 32;
   float *blo = (float *)p; p += al((size_t)nblk * d * 4);
-  float *bhi = (float *)p;
+  float *bhi = (float *)p; p += al((size_t)nblk * d * 4);
+  float *sv3 = (float *)p; p += al(nb * 96);
+  float *alpha_lo32 = (float *)p; p += al(nb * 4);
+  float2 *exp_df = (float2 *)p;
   // Morton order of the vectors (host): spatially compact 32-vector blocks
   {
     std::vector<double> hsv((size_t)n * d);
@@ -211,7 +231,7 @@ int mf_prepare_rbf_at(mf_ctx *ctx, const mf_rbf *rbf, char *base, MfRbfDev *out,
   cudaMemsetAsync(dst, 0, sizeof(MfRbfStats), st);
   k_prepare_rbf<<<(n + 255) / 256, 256, 0, st>>>(d, n, rbf->sv, rbf->alpha, perm, sv32, svlo32, sv64,
                                                   alpha64, alpha32, strong32, exp_tab, sv64r, svhl,
-                                                  dst);
+                                                  sv3, alpha_lo32, exp_df, dst);
   k_rbf_blocks<<<(nblk + 7) / 8, 256, 0, st>>>(d, n, nblk, sv32, blo, bhi);
   MfRbfStats h;
   int rc = mf_cuda_check(ctx, cudaMemcpyAsync(&h, dst, sizeof(h), cudaMemcpyDeviceToHost, st),
@@ -231,6 +251,9 @@ int mf_prepare_rbf_at(mf_ctx *ctx, const mf_rbf *rbf, char *base, MfRbfDev *out,
   out->exp_tab = exp_tab;
   out->sv64r = sv64r;
   out->svhl = svhl;
+  out->sv3 = sv3;
+  out->alpha_lo32 = alpha_lo32;
+  out->exp_df = exp_df;
   out->blk_lo = blo;
   out->blk_hi = bhi;
   out->nblk = nblk;
@@ -1553,8 +1576,9 @@ __global__ void __launch_bounds__(256) k_roots_prep(MfFrame F, MfTraceBufs B, ui
 }
 
 // The evaluation point x = x1 + t (x2 - x1) of each deferred step (thread
-// per record), in root_edge's operation order, into B.defer_x after the end
-// points' rows: record i at [2 d cap + i d].
+// per record), in root_edge's operation order, split into three floats per
+// coordinate (x = x1 + x2 + x3 exactly) for the double-float terms: record
+// i at B.defer_x3[3 d i].
 template <int D>
 __global__ void __launch_bounds__(256) k_roots_x(MfFrame F, MfTraceBufs B, uint64_t cap) {
   const unsigned long long nrec = B.cnt->n_defer < cap ? B.cnt->n_defer : cap;
@@ -1574,59 +1598,127 @@ __global__ void __launch_bounds__(256) k_roots_x(MfFrame F, MfTraceBufs B, uint6
   const double cs1 = __dmul_rn(F.c, (double)sy);
   const double cs2 = __dmul_rn(F.c, (double)(sy + __popc(mask)));
   const double t = (double)rec.t;
-  double *xp = B.defer_x + (cap * 2 * (uint64_t)d) + i * (uint64_t)d;
+  float *xp = B.defer_x3 + i * 3 * (uint64_t)d;
 #pragma unroll
   for (int k = 0; k < D; k++) {
     if (k < d) {
       double x1, dir;
       root_ends64(F, cs1, cs2, y[k], (mask >> k) & 1u, k, x1, dir);
-      xp[k] = __dadd_rn(x1, __dmul_rn(t, dir));
+      const double x = __dadd_rn(x1, __dmul_rn(t, dir));
+      const float h = (float)x;
+      const double r = x - (double)h;
+      const float m = (float)r;
+      xp[3 * k] = h;
+      xp[3 * k + 1] = m;
+      xp[3 * k + 2] = (float)(r - (double)m);
     }
   }
 }
 
-// FP64 sum of the strong terms of each 8-entry chunk (thread per chunk, so
-// lanes differ by at most the padding of a list's last chunk): alpha_j
-// exp(-gamma |x - s_j|^2) in list order, at the chunk's record's point.
+// Sum of the strong terms of each 8-entry chunk (thread per chunk, so lanes
+// differ by at most the padding of a list's last chunk): alpha_j
+// exp(-gamma |x - s_j|^2) in list order, at the chunk's record's point, in
+// double-float arithmetic on the FP32 pipe:
+//  - u = x - s from the exact three-float forms of x and s (TwoSums), so u
+//    is good to 2^-47 |u| whatever the cancellation;
+//  - r2 = sum u_k^2 and z = gamma r2 in double-float;
+//  - exp(-z) = 2^(-k/1024) exp(-r), k = round(1024 z / ln 2), |r| <=
+//    ln 2 / 2048, ln 2 / 1024 in three pieces (k times the first exact by
+//    FMA); exp(-r) = 1 - r + r^2 (1/2 - r/6 + r^2/24), the bracket in FP32
+//    (its error is below 2^-46 of the result for |r| <= 3.4e-4, and
+//    r^5 / 120 < 4e-20); 2^(-j/1024) from a double-float table;
+//  - alpha e in double-float, summed in double-float.
+// Each term's relative error stays below (1 + z) 2^-44 (the exponent's
+// error grows with z; the rest is a few double-float roundings), so the
+// chunk also records w = sum |term| (1 + z): the step's error from these
+// sums is below 2^-43 w summed over the chunks (checked in
+// k_roots_finish, with a factor 2 to spare).
+// ln 2 / 1024 = A + B + C to about 4e-24 relative (each the float nearest
+// the remainder)
+#define DF_LN2_1024_A 0x1.62e43p-11f
+#define DF_LN2_1024_B -0x1.05c61p-39f
+#define DF_LN2_1024_C -0x1.950d88p-64f
 template <int D>
 __global__ void __launch_bounds__(256) k_roots_terms(MfRbfDev R, MfTraceBufs B, uint64_t cap) {
+  __shared__ float2 stab[1024];
+  for (int i = threadIdx.x; i < 1024; i += blockDim.x) stab[i] = R.exp_df[i];
+  __syncthreads();
   const unsigned long long nrec = B.cnt->n_defer < cap ? B.cnt->n_defer : cap;
   const unsigned long long nl = B.cnt->n_defer_list;
   const uint64_t nch = (nl < B.defer_list_cap ? nl : B.defer_list_cap) / DEFER_CHUNK;
   const int d = dim_of<D>(R.d);
+  const float g1 = (float)R.gamma;
+  const MfDf gam = {g1, (float)(R.gamma - (double)g1)};
   for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < nch;
        c += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t r = B.defer_chunk[c];
     if (r >= nrec) continue;
-    const double *xp = B.defer_x + (cap * 2 * (uint64_t)d) + r * (uint64_t)d;
-    double x[D];
+    const float *xp = B.defer_x3 + r * 3 * (uint64_t)d;
+    float xa[D], xb[D], xc[D];
 #pragma unroll
-    for (int k = 0; k < D; k++) x[k] = k < d ? xp[k] : 0.0;
+    for (int k = 0; k < D; k++) {
+      xa[k] = k < d ? xp[3 * k] : 0.f;
+      xb[k] = k < d ? xp[3 * k + 1] : 0.f;
+      xc[k] = k < d ? xp[3 * k + 2] : 0.f;
+    }
     const int4 *pl = reinterpret_cast<const int4 *>(B.defer_list + c * DEFER_CHUNK);
     const int4 q0 = pl[0], q1 = pl[1];
     const int js[DEFER_CHUNK] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-    double fs = 0.0;
+    MfDf fs = {0.f, 0.f};
+    float w = 0.f;
 #pragma unroll
     for (int q = 0; q < DEFER_CHUNK; q++) {
       const int j = js[q];
       if (j < 0 || j >= R.n) continue;
-      double r2 = 0.0;
-      const double2 *row = reinterpret_cast<const double2 *>(R.sv64r + (int64_t)j * 8);
+      const float4 *row = reinterpret_cast<const float4 *>(R.sv3 + (int64_t)j * 24);
+      float sr[((3 * D + 3) / 4) * 4];
 #pragma unroll
-      for (int k2 = 0; k2 < (D + 1) / 2; k2++) {
-        const double2 sv = __ldg(row + k2);
+      for (int v = 0; v < (3 * D + 3) / 4; v++) {
+        const float4 t4 = __ldg(row + v);
+        sr[4 * v] = t4.x;
+        sr[4 * v + 1] = t4.y;
+        sr[4 * v + 2] = t4.z;
+        sr[4 * v + 3] = t4.w;
+      }
+      MfDf r2 = {0.f, 0.f};
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-          const int k = 2 * k2 + h;
-          if (k < D && k < d) {
-            const double u = x[k] - (h ? sv.y : sv.x);
-            r2 = fma(u, u, r2);
-          }
+      for (int k = 0; k < D; k++) {
+        if (k < d) {
+          // u = (xa - s1) + (xb - s2) + (xc - s3), the first two exactly
+          const MfDf a = mf_two_sum(xa[k], -sr[3 * k]);
+          const MfDf b = mf_two_sum(xb[k], -sr[3 * k + 1]);
+          const MfDf m = mf_two_sum(a.lo, b.hi);
+          const float lo = m.lo + (b.lo + (xc[k] - sr[3 * k + 2]));
+          const MfDf h = mf_two_sum(a.hi, m.hi);
+          const MfDf u = mf_fast_two_sum(h.hi, h.lo + lo);
+          // u^2 (the lo^2 term is below 2^-48 u^2)
+          const MfDf p = mf_two_prod(u.hi, u.hi);
+          r2 = mf_df_add(r2, mf_fast_two_sum(p.hi, fmaf(2.f * u.hi, u.lo, p.lo)));
         }
       }
-      fs += __ldg(R.alpha + j) * mf_exp_neg(-R.gamma * r2, R.exp_tab);
+      const MfDf z = mf_df_mul(gam, r2);
+      // k = round(z 1024 / ln 2); r = z - k ln2/1024 in double-float
+      const float kf = rintf(z.hi * 1477.3197218702985f);
+      const MfDf ka = mf_two_prod(kf, DF_LN2_1024_A);
+      MfDf rr = mf_two_sum(z.hi, -ka.hi);
+      rr = mf_fast_two_sum(rr.hi, rr.lo + (z.lo - ka.lo) - fmaf(kf, DF_LN2_1024_B, kf * DF_LN2_1024_C));
+      // exp(-r) = 1 - r + r^2 (1/2 - r/6 + r^2/24)
+      const float rh = rr.hi;
+      const float br = fmaf(rh, fmaf(rh, 1.f / 24.f, -1.f / 6.f), 0.5f);
+      const MfDf one_r = mf_two_sum(1.f, -rh);
+      const MfDf er = mf_fast_two_sum(one_r.hi, one_r.lo + fmaf(rh * rh, br, -rr.lo));
+      const int ki = (int)kf;
+      const float2 tt = stab[ki & 1023];
+      MfDf e = mf_df_mul({tt.x, tt.y}, er);
+      const int sh = ki >> 10;  // 2^-sh (z <= ~750, so sh stays far from the float exponent limit)
+      e.hi = ldexpf(e.hi, -sh);
+      e.lo = ldexpf(e.lo, -sh);
+      const MfDf t = mf_df_mul({__ldg(R.alpha32 + j), __ldg(R.alpha_lo32 + j)}, e);
+      fs = mf_df_add(fs, t);
+      w = fmaf(fabsf(t.hi), 1.f + z.hi, w);
     }
-    B.defer_part[c] = fs;
+    B.defer_part[c] = (double)fs.hi + (double)fs.lo;
+    B.defer_bnd[c] = w;
   }
 }
 
@@ -1647,16 +1739,22 @@ __global__ void __launch_bounds__(256) k_roots_finish(MfFrame F, MfRbfDev R, MfT
     if (rec.e != ~0ull) {
       const uint64_t e = rec.e;
       double fs = 0.0;
+      float w = 0.f;
       const uint32_t nc = (rec.ns + DEFER_CHUNK - 1) / DEFER_CHUNK;
-      for (uint32_t c = 0; c < nc; c++) fs += B.defer_part[rec.ch + c];
+      for (uint32_t c = 0; c < nc; c++) {
+        fs += B.defer_part[rec.ch + c];
+        w += B.defer_bnd[rec.ch + c];
+      }
       terms += rec.ns;
       evals++;
       const double t = (double)rec.t;
       const double f = fs + (double)rec.wf + R.b;
       double tn = t;
-      bool ok = true;
+      // the double-float sums' error (2^-43 w, doubled) may move t by at
+      // most 2e-10 (1e-7 in the fast mode), beside the FP32 part's 1e-10
+      bool ok = 2.f * 0x1p-43f * w <= (fast ? 0.99e-7f : 2e-10f) * fabsf(rec.gp);
       const long long fb = __double_as_longlong(f);
-      if ((fb << 1) != 0) {  // f = +-0 keeps t
+      if (ok && (fb << 1) != 0) {  // f = +-0 keeps t
         const bool s1 = B.edge_f[2 * e] >= 0.0;
         double lo = 0.0, hi = 1.0;
         if ((fb >= 0) == s1) lo = t; else hi = t;

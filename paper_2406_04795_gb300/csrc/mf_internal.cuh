@@ -117,7 +117,9 @@ struct MfTraceBufs {
   uint64_t *redo;           // [defer_cap] edge indices
   float *ep32;              // [defer_cap][MF_EP_ROW(d)]: x1 hi, x1 lo, dir, f(x1), f(x2),
                             // [f(x1) >= 0], base vertex's list length and offset (bits)
-  double *defer_x;          // [defer_cap][2d] FP64 x1, dir; then [defer_cap][d] step points
+  double *defer_x;          // [defer_cap][2d] FP64 x1, dir
+  float *defer_x3;          // [defer_cap][3d] step points, each coordinate as three floats
+  float *defer_bnd;         // [defer_list_cap / 8] error weight of each chunk (see k_roots_terms)
   double *defer_part;       // [defer_list_cap / 8] FP64 sum of each chunk
   uint32_t *defer_chunk;    // [defer_list_cap / 8] record of each chunk (~0: none)
   uint64_t defer_cap, defer_list_cap;
@@ -139,6 +141,10 @@ struct MfRbfDev {
   // row-major copies for gathers (one support vector per 64-byte row):
   const double *sv64r;   // [n][8] coordinates, zero-padded
   const float *svhl;     // [n][16] (hi, lo) FP32 pairs of the coordinates
+  // double-float (FP32 pair) forms for the root step's strong terms:
+  const float *sv3;        // [n][24] each coordinate as three floats s1 + s2 + s3 (exact)
+  const float *alpha_lo32; // [n] alpha - (double)alpha32
+  const float2 *exp_df;    // [1024] 2^(-j/1024) as (hi, lo)
   // blocks of 32 consecutive vectors (the preparation orders the vectors
   // along a Morton curve, so a block is spatially compact): FP32 box of sv32
   const float *blk_lo, *blk_hi;  // [d][nblk]
@@ -614,3 +620,40 @@ enum {
   MF_SLOT_DEFER = 16,
   MF_NUM_SLOTS = 17
 };
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic (a value as an unevaluated sum hi + lo of two
+// floats; Dekker 1971, Knuth TAOCP vol. 2 4.2.2): the error-free transforms
+// TwoSum and TwoProduct (by FMA) and the usual add / multiply built on them.
+// They run on the FP32 pipe; on GB300 it issues about 70 times as many
+// operations per clock as the FP64 pipe.
+// ---------------------------------------------------------------------------
+struct MfDf {
+  float hi, lo;
+};
+// s + e == a + b exactly (any magnitudes)
+__device__ __forceinline__ MfDf mf_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+// s + e == a + b exactly when |a| >= |b| or a == 0
+__device__ __forceinline__ MfDf mf_fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+// p + e == a b exactly (barring underflow)
+__device__ __forceinline__ MfDf mf_two_prod(float a, float b) {
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+// x + y, relative error below 2^-47 (|x| + |y|)
+__device__ __forceinline__ MfDf mf_df_add(MfDf x, MfDf y) {
+  const MfDf s = mf_two_sum(x.hi, y.hi);
+  return mf_fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+// x y, relative error below 2^-46
+__device__ __forceinline__ MfDf mf_df_mul(MfDf x, MfDf y) {
+  const MfDf p = mf_two_prod(x.hi, y.hi);
+  return mf_fast_two_sum(p.hi, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo)));
+}
+

@@ -40,7 +40,8 @@ struct MfRbfStats {
 __global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alpha, const int32_t *perm,
                               float *sv32, float *svlo32, double *sv64, double *alpha64,
                               float *alpha32, float *strong32, double *exp_tab, double *sv64r,
-                              float *svhl, MfRbfStats *st);
+                              float *svhl, float *sv3, float *alpha_lo32, float2 *exp_df,
+                              MfRbfStats *st);
 __global__ void k_rbf_blocks(int d, int n, int nblk, const float *sv32, float *blo, float *bhi);
 __global__ void k_seed_vertices(MfFrame F, MfTraceBufs B, const double *seeds, int64_t n);
 __global__ void k_seed_edges(MfFrame F, MfTraceBufs B, const double *seeds, int64_t n);
@@ -240,14 +241,14 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   // holds, it just skips fewer blocks
   k_prepare_rbf<<<(n + 255) / 256, 256, 0, st>>>(d, n, rbf->sv, rbf->alpha, nullptr, sv32, svlo32,
                                                   sv64, alpha64, alpha32, strong32, exp_tab, sv64r,
-                                                  svhl, stats);
+                                                  svhl, nullptr, nullptr, nullptr, stats);
   k_rbf_blocks<<<(nblk + 7) / 8, 256, 0, st>>>(d, n, nblk, sv32, blo, bhi);
   MfRbfStats hs;
   if (cudaMemcpyAsync(&hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return MF_ERR_CUDA;
   if (hs.bad) return MF_ERR_INVALID;
-  MfRbfDev R;
+  MfRbfDev R = {};
   R.d = d;
   R.n = n;
   R.sv32 = sv32;

@@ -1253,7 +1253,7 @@ static int setup_buffers(mf_ctx *ctx, int d, uint64_t ME, uint64_t MV, uint64_t 
   {
     const uint64_t dc = std::min<uint64_t>(ME, 1ull << 22), dl = dc * 48;
     const size_t db = al(dc * 32) + al(dc * 8) + al(dl * 4) + al(dc * MF_EP_ROW(d) * 4) +
-                      al(dc * 3 * d * 8) + al(dl) + al(dl / 2);
+                      al(dc * 2 * d * 8) + al(dc * 3 * d * 4) + al(dl) + al(dl / 2) + al(dl / 2);
     std::string keep = ctx->err;
     char *q = (char *)mf_ctx_buffer(ctx, MF_SLOT_DEFER, db);
     if (q) {
@@ -1261,9 +1261,11 @@ static int setup_buffers(mf_ctx *ctx, int d, uint64_t ME, uint64_t MV, uint64_t 
       B->redo = (uint64_t *)q; q += al(dc * 8);
       B->defer_list = (int32_t *)q; q += al(dl * 4);
       B->ep32 = (float *)q; q += al(dc * MF_EP_ROW(d) * 4);
-      B->defer_x = (double *)q; q += al(dc * 3 * d * 8);
+      B->defer_x = (double *)q; q += al(dc * 2 * d * 8);
+      B->defer_x3 = (float *)q; q += al(dc * 3 * d * 4);
       B->defer_part = (double *)q; q += al(dl);  // dl / 8 doubles
-      B->defer_chunk = (uint32_t *)q;            // dl / 8 uint32
+      B->defer_bnd = (float *)q; q += al(dl / 2);  // dl / 8 floats
+      B->defer_chunk = (uint32_t *)q;              // dl / 8 uint32
       B->defer_cap = dc;
       B->defer_list_cap = dl;
     } else {
