@@ -36,9 +36,29 @@ from paper_2406_04795_gb300 import workloads as W  # noqa: E402
 # r^2 (1 mul), degree-5 polynomial (4 FMA), table product (1 FMA), 2^m (1 mul);
 # an FMA counts 2 flops
 FP64_EXP_FLOPS = 19
-# DRAM bytes per traced edge of k_roots_f64 from its ncu capture (per-edge
-# dram__bytes_read.sum + dram__bytes_write.sum on the lambda = 0.15 case of
-# the d=5 workload); None once the kernel has changed since the capture
+
+
+# FP32-pipe operations of one double-float strong term of the root step
+# (k_roots_terms): per coordinate 3 TwoSums, 3 adds and a fast TwoSum for
+# u = x - s, a TwoProduct, an FMA and a fast TwoSum for u^2, a double-float
+# add into r2 (47); then z = gamma r2, the reduction, the polynomial, the
+# table product, the scaling, alpha e and the sum (68)
+def df_term_ops(d):
+    return 47 * d + 68
+
+
+# FP32-pipe operations of one FP32 term (Halley step or weak term): per
+# coordinate a hi and a lo difference, their sum, r2 and the projection
+# FMAs (5); then the exponent, ex2, alpha e and the accumulations (8)
+def f32_term_ops(d):
+    return 5 * d + 8
+
+
+# DRAM bytes per traced edge of the root phase's kernels from their ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum of k_roots_prep,
+# k_roots_f64 (warp and redo launches), k_roots_x, k_roots_terms and
+# k_roots_finish on the lambda = 0.15 case of the d=5 workload, divided by
+# its 880,448 edges); None once a kernel has changed since the capture
 ROOTS_DRAM_BYTES_PER_EDGE = None
 
 
@@ -111,27 +131,33 @@ def measured_peaks():
 
 def roofline(stats, w, rates, E, ms_proof, n_proofs):
     """Roofline of the dominant phase against the measured peaks: the FP64
-    pipe (mf_probe_rates FP64 FMA probe) for the RBF phases, the MUFU ex2
-    probe for the tensor-core evaluation, the STREAM copy for the table
-    phases.  Work is counted in kept terms: the screened sum evaluates in FP64
-    only the terms that can exceed 3e-10 (1e-8 in the root step), so the dense
-    N x (vertices + root evaluations) count of an unscreened sum does not
-    apply.  Also the whole proof's per-edge time against its bound
-    max(FP64 flops / FP64 peak, ex2 / ex2 rate, bytes / HBM)."""
+    pipe (mf_probe_rates FP64 FMA probe) for the FP64 vertex evaluation and
+    certification, the FP32 pipe (FP32 FMA probe, one operation per
+    instruction) for the root solve, whose strong terms are double-float
+    and whose Halley steps and weak terms are FP32, the MUFU ex2 probe for
+    the tensor-core evaluation, the STREAM copy for the table phases.  Work
+    is counted in kept terms: the screened sum keeps only the terms that can
+    exceed 3e-10 (1e-8 in the root step), so the dense N x (vertices + root
+    evaluations) count of an unscreened sum does not apply.  Also the whole
+    proof's per-edge time against its bound max(FP64 flops / FP64 peak,
+    FP32 operations / FP32 rate, ex2 / ex2 rate, bytes / HBM)."""
     peaks, src = measured_peaks()
     dom = max(stats, key=lambda k: stats[k]["ms"])
     s = stats[dom]
     ms_per_launch = s["ms"] / max(s["launches"], 1)
     d = w.d
     fp64_peak = 2.0 * rates["fp64_fma_per_s"] / 1e12  # TFLOP/s, measured
+    f32_peak = rates["fp32_fma_per_s"] / 1e12         # T FP32 instructions/s, measured
     ex2_peak = rates["ex2_per_s"] / 1e12             # T ex2/s, measured
     phase_ms = {k: round(v["ms"], 3) for k, v in stats.items() if v["ms"] > 0}
-    per_root = 5 * d + 5 + FP64_EXP_FLOPS
     per_eval = 3 * d + 3 + FP64_EXP_FLOPS
-    # proof level (per traced edge): FP64 flops of all kept FP64 terms,
-    # ex2 of all FP32 terms (weak terms; every term of a tensor-core tile),
-    # and the algorithmic bytes of the table phases
-    f64 = stats["roots"]["terms"] * per_root + stats["eval"]["terms"] * per_eval
+    # proof level (per traced edge): FP64 flops of the vertex evaluation's
+    # strong terms, FP32 operations of the root solve (double-float strong
+    # terms; FP32 Halley and weak terms) and of the evaluation's weak terms,
+    # ex2 of all FP32 terms, and the algorithmic bytes of the table phases
+    f64 = stats["eval"]["terms"] * per_eval
+    f32 = (stats["roots"]["terms"] * df_term_ops(d) +
+           (stats["roots"]["terms_weak"] + stats["eval"]["terms_weak"]) * f32_term_ops(d))
     ex2 = stats["roots"]["terms_weak"] + stats["eval"]["terms_weak"]
     k = d // 2
     by = (stats["expand_vertices"]["units"] * ((4 * d + 4) + 32 * 2 ** d) +
@@ -141,13 +167,15 @@ def roofline(stats, w, rates, E, ms_proof, n_proofs):
           stats["csr"]["units"] * ((5 * d) + (32 + 8) * (d + 1)))
     steps = max(n_proofs, 1)
     t_f64 = f64 / steps / (fp64_peak * 1e12)
+    t_f32 = f32 / steps / (f32_peak * 1e12)
     t_ex2 = ex2 / steps / (ex2_peak * 1e12)
     t_hbm = by / steps / (peaks["hbm_gbs"] * 1e9)
-    t_bound = max(t_f64, t_ex2, t_hbm)
+    t_bound = max(t_f64, t_f32, t_ex2, t_hbm)
     proof = {"ns_per_edge": ms_proof * 1e6 / max(E, 1), "bound_ns_per_edge": t_bound * 1e9 / max(E, 1),
-             "frac": t_bound / (ms_proof * 1e-3), "bound_by": ["fp64", "ex2", "hbm"][
-                 [t_f64, t_ex2, t_hbm].index(t_bound)],
-             "fp64_ms": t_f64 * 1e3, "ex2_ms": t_ex2 * 1e3, "hbm_ms": t_hbm * 1e3}
+             "frac": t_bound / (ms_proof * 1e-3), "bound_by": ["fp64", "fp32", "ex2", "hbm"][
+                 [t_f64, t_f32, t_ex2, t_hbm].index(t_bound)],
+             "fp64_ms": t_f64 * 1e3, "fp32_ms": t_f32 * 1e3, "ex2_ms": t_ex2 * 1e3,
+             "hbm_ms": t_hbm * 1e3}
     base = {"phase_ms": phase_ms, "proof": proof,
             "measured_rates": {k: v for k, v in rates.items()}}
     if dom == "eval" and w.precision not in ("fp64", "mixed_fp32"):
@@ -159,20 +187,32 @@ def roofline(stats, w, rates, E, ms_proof, n_proofs):
                     unit="T ex2/s", frac=ach / ex2_peak, traffic=None,
                     peak_source="measured: mf_probe_rates ex2.approx probe",
                     work="%d RBF terms (vertex x support vector), one ex2 each" % s["terms_weak"])
-    if dom in ("roots", "eval"):
-        per = per_root if dom == "roots" else per_eval
-        flops = s["terms"] * per / max(s["launches"], 1)
-        ach = flops / (ms_per_launch * 1e-3) / 1e12
-        # DRAM bytes per edge from the ncu capture of k_roots_f64 (profiles/),
-        # scaled by the edges one launch processes
+    if dom == "roots":
+        # the root phase's arithmetic runs on the FP32 pipe: double-float
+        # strong terms (k_roots_terms) and FP32 Halley / weak terms (the warp
+        # kernel); the few full FP64 re-evaluations are counted as strong terms
+        ops = (s["terms"] * df_term_ops(d) + s["terms_weak"] * f32_term_ops(d)) / max(s["launches"], 1)
+        ach = ops / (ms_per_launch * 1e-3) / 1e12
+        # DRAM bytes per edge from the ncu capture of the root kernels
+        # (profiles/), scaled by the edges one launch processes
         traffic = ROOTS_DRAM_BYTES_PER_EDGE * s["units"] / max(s["launches"], 1) \
-            if dom == "roots" and ROOTS_DRAM_BYTES_PER_EDGE else None
-        return dict(base, kernel="k_roots_f64" if dom == "roots" else "k_eval_vertices_f64",
-                    bound="alu", achieved=ach, peak=fp64_peak, unit="TFLOP/s", frac=ach / fp64_peak,
-                    traffic=traffic,
+            if ROOTS_DRAM_BYTES_PER_EDGE else None
+        return dict(base, kernel="roots phase: k_roots_prep, k_roots_f64 (warp screen and FP32 "
+                    "Halley steps), k_roots_x, k_roots_terms (double-float sums), k_roots_finish",
+                    bound="alu", achieved=ach, peak=f32_peak, unit="T FP32 ops/s",
+                    frac=ach / f32_peak, traffic=traffic,
+                    peak_source="measured: mf_probe_rates FP32 FMA probe (one operation per "
+                    "instruction)",
+                    work="%d strong terms x %d FP32 ops (double-float) + %d FP32 terms x %d ops" % (
+                        s["terms"], df_term_ops(d), s["terms_weak"], f32_term_ops(d)))
+    if dom == "eval":
+        flops = s["terms"] * per_eval / max(s["launches"], 1)
+        ach = flops / (ms_per_launch * 1e-3) / 1e12
+        return dict(base, kernel="k_eval_vertices_f64", bound="alu", achieved=ach, peak=fp64_peak,
+                    unit="TFLOP/s", frac=ach / fp64_peak, traffic=None,
                     peak_source="measured: mf_probe_rates FP64 FMA probe (2 flops per FMA)",
                     work="%d kept FP64 terms x %d flops (and %d FP32 weak terms, not counted)" % (
-                        s["terms"], per, s["terms_weak"]))
+                        s["terms"], per_eval, s["terms_weak"]))
     if dom == "certify_points":
         n_obs = int(w.obs_type.shape[0])
         flops = s["units"] * d * (60 + n_obs * 150) / max(s["launches"], 1)

@@ -406,8 +406,11 @@ typedef struct {
   double ms[MF_PHASES];        /* device time summed over the phase's launches */
   int64_t launches[MF_PHASES]; /* kernel launches of the phase */
   int64_t units[MF_PHASES];    /* work items: seeds, frontier edges, edges solved, points ... */
-  int64_t terms[MF_PHASES];    /* RBF terms with the FP64 exp (eval / roots phases) */
-  int64_t terms_weak[MF_PHASES]; /* RBF terms with the reduced-cost exp (|term| <= 1e-9) */
+  int64_t terms[MF_PHASES];    /* strong RBF terms: FP64 exp (eval phase; the root
+                                  step's full FP64 re-evaluations) or double-float
+                                  (the root step's lane-per-chunk sums) */
+  int64_t terms_weak[MF_PHASES]; /* RBF terms in FP32 with ex2: weak terms, the tensor-
+                                    core tiles' terms, the root solve's FP32 Halley steps */
 } mf_stats;
 
 /* Enables (1) or disables (0) profiling on the context; enabling clears the stats. */

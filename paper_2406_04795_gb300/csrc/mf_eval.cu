@@ -1263,6 +1263,7 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
     float lo = 0.f, hi = 1.f;
     for (int it = 0; it < 12; it++) {
       const Root32 r = root_eval32<D>(R, near, ns, midl, nm, x1hi, x1lo, dir32, dd32, b32, t32);
+      terms[1] += ns + nm;  // FP32 terms of this Halley evaluation
       gpp = r.gpp;
       gp32 = r.gp;
       t_eval = t32;
@@ -1393,10 +1394,10 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
 
 __device__ __forceinline__ void root_flush(const MfTraceBufs &B, unsigned long long evals,
                                            const unsigned long long *terms) {
-  if ((threadIdx.x & 31) == 0 && evals) {
-    atomicAdd(&B.cnt->root_evals, evals);
-    atomicAdd(&B.cnt->root_terms, terms[0]);
-    atomicAdd(&B.cnt->root_terms_weak, terms[1]);
+  if ((threadIdx.x & 31) == 0 && (evals || terms[0] || terms[1])) {
+    if (evals) atomicAdd(&B.cnt->root_evals, evals);
+    if (terms[0]) atomicAdd(&B.cnt->root_terms, terms[0]);
+    if (terms[1]) atomicAdd(&B.cnt->root_terms_weak, terms[1]);
   }
 }
 
