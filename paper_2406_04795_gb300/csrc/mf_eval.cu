@@ -920,42 +920,77 @@ struct Root32 {
   float g, gp, gpp, gpa;  // gpa: the sum of |g'| terms (cancellation measure)
 };
 
-// FP32 evaluation of g, g', g'' at t over the strong entries of the near
-// list (all lanes).  The weak entries are below tau e^(1/2) = 5e-10 each, so
-// even a few hundred of them shift g by less than its FP32 rounding (~1e-7
-// of sum |terms|); the FP32 stage leaves them to the FP64 step, which sums
-// every kept term.
+// The FP32 stage's per-term data, cached by the segment screen for the first
+// HC_STRONG strong and HC_MID mid entries of each edge (per warp, in shared
+// memory): with u = x1 - s (FP32 hi/lo differences) and dir = x2 - x1,
+// A = |u|^2 and Bp = u . dir, so that at x(t) = x1 + t dir
+//   proj(t) = (x(t) - s) . dir = Bp + t |dir|^2,
+//   r2(t) = |x(t) - s|^2 = A + t (Bp + proj(t)),
+// and an evaluation reads three floats per term instead of gathering the
+// vector's coordinates again.  r2's absolute error stays below ~(d+3) 2^-24
+// (|u| + |dir|)^2, i.e. a relative term error of a few 1e-6 on the kept
+// range gamma r2 <= T + 1/2 (the stage only steers and feeds the reused g').
+#define HC_STRONG 192
+#define HC_MID 64
+#define HC_ALL (HC_STRONG + HC_MID)
+
+// A and Bp of support vector j against x1 (hi/lo) along dir32, from its
+// hi/lo coordinate row.
 template <int D>
-__device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const int *near, int ns,
-                                              const int *midl, int nm, const float *x1hi,
+__device__ __forceinline__ void term_ab(const MfRbfDev &R, int j, const float *x1hi,
+                                        const float *x1lo, const float *dir32, float &A,
+                                        float &Bp) {
+  const int d = dim_of<D>(R.d);
+  const float4 *row = reinterpret_cast<const float4 *>(R.svhl + (int64_t)j * 16);
+  A = 0.f;
+  Bp = 0.f;
+#pragma unroll
+  for (int k2 = 0; k2 < (D + 1) / 2; k2++) {
+    const float4 s = __ldg(row + k2);
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int k = 2 * k2 + h;
+      if (k < D && k < d) {
+        const float u = (x1hi[k] - (h ? s.z : s.x)) + (x1lo[k] - (h ? s.w : s.y));
+        A = fmaf(u, u, A);
+        Bp = fmaf(u, dir32[k], Bp);
+      }
+    }
+  }
+}
+
+// FP32 evaluation of g, g', g'' at t over the strong entries of the near
+// list and the mid list (all lanes), from the screen's cache (hc: A, Bp,
+// alpha, HC_ALL floats each) where it holds the entry.  The weak entries are
+// below tau e^(1/2) = 5e-10 each, so even a few hundred of them shift g by
+// less than its FP32 rounding (~1e-7 of sum |terms|); the FP32 stage leaves
+// them to the FP64 step, which sums every kept term.
+template <int D>
+__device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const float *hc, const int *near,
+                                              int ns, const int *midl, int nm, const float *x1hi,
                                               const float *x1lo, const float *dir32, float dd32,
                                               float b32, float t) {
   const int lane = threadIdx.x & 31;
-  const int d = dim_of<D>(R.d);
   const float g2 = (float)(R.gamma * 1.4426950408889634);
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s1a = 0.f;
   const int total = ns + nm;
 #pragma unroll 2
   for (int i = lane; i < total; i += 32) {
-    const int j = i < ns ? near[i] : midl[i - ns];
-    float r2 = 0.f, proj = 0.f;
-    const float4 *row = reinterpret_cast<const float4 *>(R.svhl + (int64_t)j * 16);
-#pragma unroll
-    for (int k2 = 0; k2 < (D + 1) / 2; k2++) {
-      const float4 s = __ldg(row + k2);
-#pragma unroll
-      for (int h = 0; h < 2; h++) {
-        const int k = 2 * k2 + h;
-        if (k < D && k < d) {
-          const float a = x1hi[k] - (h ? s.z : s.x);
-          const float b = fmaf(t, dir32[k], x1lo[k] - (h ? s.w : s.y));
-          const float df = a + b;
-          r2 = fmaf(df, df, r2);
-          proj = fmaf(df, dir32[k], proj);
-        }
-      }
+    const bool strong = i < ns;
+    const int c = strong ? i : HC_STRONG + (i - ns);
+    float A, Bp, al;
+    if (strong ? i < HC_STRONG : i - ns < HC_MID) {
+      A = hc[c];
+      Bp = hc[HC_ALL + c];
+      al = hc[2 * HC_ALL + c];
+    } else {
+      const int j = strong ? near[i] : midl[i - ns];
+      term_ab<D>(R, j, x1hi, x1lo, dir32, A, Bp);
+      al = R.alpha32[j];
     }
-    const float e = R.alpha32[j] * ex2_approx(-g2 * r2);
+    const float proj = fmaf(t, dd32, Bp);
+    const float r2 = fmaf(t, proj + Bp, A);
+    const float e = al * ex2_approx(-g2 * r2);
     s0 += e;
     s1 = fmaf(e, proj, s1);
     s1a = fmaf(fabsf(e), fabsf(proj), s1a);
@@ -1063,8 +1098,8 @@ struct RootWarpState {
 // e - ep0), or NULL (every lane k < d then computes axis k here in FP64).
 template <int D>
 __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs &B, uint64_t e,
-                          double tol, const int *src, int srcn, int *near, int *midl, int *qs,
-                          int *qw,
+                          double tol, const int *src, int srcn, int *near, int *midl, float *hc,
+                          int *qs, int *qw,
                           RootWarpState *ws, unsigned long long &evals, unsigned long long *terms,
                           bool fast, bool defer, const float *ep32, const double *ep64,
                           uint64_t ep0) {
@@ -1138,15 +1173,20 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
   // coalesced coordinate arrays) and the survivors are compacted
   auto screen_round = [&](bool valid, int j, bool gathered) {
     bool keep = false, strong = false, strong64 = false;
+    float cA = 0.f, cB = 0.f;
     if (valid) {
-      float p[D], pd = 0.f;
+      float p[D], sl[D], pd = 0.f;
       if (gathered) {
         const float4 *row = reinterpret_cast<const float4 *>(R.svhl + (int64_t)j * 16);
 #pragma unroll
         for (int k2 = 0; k2 < (D + 1) / 2; k2++) {
           const float4 v = __ldg(row + k2);
           p[2 * k2] = 2 * k2 < d ? v.x - x1hi[2 * k2] : 0.f;
-          if (2 * k2 + 1 < D) p[2 * k2 + 1] = 2 * k2 + 1 < d ? v.z - x1hi[2 * k2 + 1] : 0.f;
+          sl[2 * k2] = v.y;
+          if (2 * k2 + 1 < D) {
+            p[2 * k2 + 1] = 2 * k2 + 1 < d ? v.z - x1hi[2 * k2 + 1] : 0.f;
+            sl[2 * k2 + 1] = v.w;
+          }
         }
       } else {
 #pragma unroll
@@ -1172,6 +1212,19 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
         const float s32 = R.strong32[j];
         strong = g32 * r2 < s32 + 0.5f;
         strong64 = g32 * r2 < s32 + shift64;
+        if (keep && strong) {
+          // the FP32 stage's A and Bp (term_ab's operations: x1hi - s_hi is
+          // -p exactly)
+#pragma unroll
+          for (int k = 0; k < D; k++) {
+            if (k < d) {
+              const float lo = gathered ? sl[k] : R.svlo32[(int64_t)k * R.n + j];
+              const float u = -p[k] + (x1lo[k] - lo);
+              cA = fmaf(u, u, cA);
+              cB = fmaf(u, dir32[k], cB);
+            }
+          }
+        }
       }
     }
     // strong64 entries fill near from the front, weak ones from the back,
@@ -1182,6 +1235,12 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
     const int cs = ns + __popc(ms & lt), cm = nm + __popc(mm & lt), cw = nw + __popc(mw & lt);
     if (keep && strong64 && cs + nw < NEAR_CAP) near[cs] = j;
     if (keep && strong && !strong64 && cm < MID_CAP) midl[cm] = j;
+    if (keep && strong && (strong64 ? cs < HC_STRONG : cm < HC_MID)) {
+      const int c = strong64 ? cs : HC_STRONG + cm;
+      hc[c] = cA;
+      hc[HC_ALL + c] = cB;
+      hc[2 * HC_ALL + c] = R.alpha32[j];
+    }
     if (keep && !strong && ns + cw < NEAR_CAP) near[NEAR_CAP - 1 - cw] = j;
     ns += __popc(ms);
     nm += __popc(mm);
@@ -1262,7 +1321,7 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
     const float b32 = (float)R.b;
     float lo = 0.f, hi = 1.f;
     for (int it = 0; it < 12; it++) {
-      const Root32 r = root_eval32<D>(R, near, ns, midl, nm, x1hi, x1lo, dir32, dd32, b32, t32);
+      const Root32 r = root_eval32<D>(R, hc, near, ns, midl, nm, x1hi, x1lo, dir32, dd32, b32, t32);
       terms[1] += ns + nm;  // FP32 terms of this Halley evaluation
       gpp = r.gpp;
       gp32 = r.gp;
@@ -1487,6 +1546,7 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(
   const double *ep64 = defer ? B.defer_x : nullptr;
   __shared__ int snear[ROOT_WARPS][NEAR_CAP];
   __shared__ int smid[ROOT_WARPS][MID_CAP];
+  __shared__ float shc[ROOT_WARPS][3 * HC_ALL];
   __shared__ int sq[ROOT_WARPS][2][64];
   __shared__ RootWarpState sws[ROOT_WARPS];
   extern __shared__ int sgrp_all[];  // [ROOT_WARPS][GROUP_CAP] when group > 1
@@ -1498,11 +1558,11 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(
   if (list) {
     const uint64_t nl = *n_list < n_edges ? *n_list : n_edges;
     for (uint64_t i = (uint64_t)blockIdx.x * ROOT_WARPS + w; i < nl; i += nwarps)
-      root_edge<D>(F, R, B, list[i], tol, nullptr, 0, snear[w], smid[w], sq[w][0], sq[w][1],
+      root_edge<D>(F, R, B, list[i], tol, nullptr, 0, snear[w], smid[w], shc[w], sq[w][0], sq[w][1],
                    &sws[w], evals, terms, fast != 0, false, nullptr, nullptr, 0);
   } else if (group <= 1) {
     for (uint64_t i = (uint64_t)blockIdx.x * ROOT_WARPS + w; i < n_edges; i += nwarps)
-      root_edge<D>(F, R, B, e0 + i, tol, nullptr, 0, snear[w], smid[w], sq[w][0], sq[w][1],
+      root_edge<D>(F, R, B, e0 + i, tol, nullptr, 0, snear[w], smid[w], shc[w], sq[w][0], sq[w][1],
                    &sws[w], evals, terms, fast != 0, defer != 0, ep32, ep64, e0);
   } else {
     const uint64_t G = (uint64_t)group;
@@ -1511,7 +1571,7 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, MINB) k_roots_f64(
       const int gn = group_screen<D>(F, R, B, e0 + g0, ng, rs, sgrp);
       for (int q = 0; q < ng; q++)
         root_edge<D>(F, R, B, e0 + g0 + q, tol, gn >= 0 ? sgrp : nullptr, gn, snear[w], smid[w],
-                     sq[w][0], sq[w][1], &sws[w], evals, terms, fast != 0, defer != 0, ep32, ep64,
+                     shc[w], sq[w][0], sq[w][1], &sws[w], evals, terms, fast != 0, defer != 0, ep32, ep64,
                      e0);
     }
   }
@@ -1581,31 +1641,21 @@ __global__ void __launch_bounds__(256) k_roots_prep(MfFrame F, MfTraceBufs B, ui
 // coordinate (x = x1 + x2 + x3 exactly) for the double-float terms: record
 // i at B.defer_x3[3 d i].
 template <int D>
-__global__ void __launch_bounds__(256) k_roots_x(MfFrame F, MfTraceBufs B, uint64_t cap) {
+__global__ void __launch_bounds__(256) k_roots_x(MfFrame F, MfTraceBufs B, uint64_t cap, uint64_t e0) {
   const unsigned long long nrec = B.cnt->n_defer < cap ? B.cnt->n_defer : cap;
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i >= nrec) return;
   const int d = dim_of<D>(F.d);
   const RootRec rec = reinterpret_cast<const RootRec *>(B.defer_rec)[i];
   if (rec.e == ~0ull) return;
-  long long sy = 0;
-  int32_t y[D];
-#pragma unroll
-  for (int k = 0; k < D; k++) {
-    y[k] = k < d ? B.edge_y[rec.e * d + k] : 0;
-    sy += y[k];
-  }
-  const uint32_t mask = B.edge_mask[rec.e] & ((1u << d) - 1u);
-  const double cs1 = __dmul_rn(F.c, (double)sy);
-  const double cs2 = __dmul_rn(F.c, (double)(sy + __popc(mask)));
+  // x1 and dir as k_roots_prep computed them (row rec.e - e0)
+  const double *row64 = B.defer_x + (rec.e - e0) * 2 * (uint64_t)d;
   const double t = (double)rec.t;
   float *xp = B.defer_x3 + i * 3 * (uint64_t)d;
 #pragma unroll
   for (int k = 0; k < D; k++) {
     if (k < d) {
-      double x1, dir;
-      root_ends64(F, cs1, cs2, y[k], (mask >> k) & 1u, k, x1, dir);
-      const double x = __dadd_rn(x1, __dmul_rn(t, dir));
+      const double x = __dadd_rn(row64[k], __dmul_rn(t, row64[d + k]));
       const float h = (float)x;
       const double r = x - (double)h;
       const float m = (float)r;
@@ -1729,7 +1779,8 @@ __global__ void __launch_bounds__(256) k_roots_terms(MfRbfDev R, MfTraceBufs B, 
 // (x1 + t dir in root_edge's order); the others go to the redo queue.
 template <int D>
 __global__ void __launch_bounds__(256) k_roots_finish(MfFrame F, MfRbfDev R, MfTraceBufs B,
-                                                      uint64_t cap, double tol, int fast) {
+                                                      uint64_t cap, double tol, int fast,
+                                                      uint64_t e0) {
   const unsigned long long nrec = B.cnt->n_defer < cap ? B.cnt->n_defer : cap;
   const int d = dim_of<D>(F.d);
   const float tolf = (float)tol;
@@ -1769,25 +1820,12 @@ __global__ void __launch_bounds__(256) k_roots_finish(MfFrame F, MfRbfDev R, MfT
         }
       }
       if (ok) {
-        long long sy = 0;
-        int32_t y[D];
-#pragma unroll
-        for (int k = 0; k < D; k++) {
-          y[k] = k < d ? B.edge_y[e * d + k] : 0;
-          sy += y[k];
-        }
-        const uint32_t mask = B.edge_mask[e] & ((1u << d) - 1u);
-        const double cs1 = __dmul_rn(F.c, (double)sy);
-        const double cs2 = __dmul_rn(F.c, (double)(sy + __popc(mask)));
+        // x1 and dir as k_roots_prep computed them (row e - e0)
+        const double *row64 = B.defer_x + (e - e0) * 2 * (uint64_t)d;
         B.edge_t[e] = tn;
 #pragma unroll
-        for (int k = 0; k < D; k++) {
-          if (k < d) {
-            double x1, dir;
-            root_ends64(F, cs1, cs2, y[k], (mask >> k) & 1u, k, x1, dir);
-            B.edge_pt[e * d + k] = __dadd_rn(x1, __dmul_rn(tn, dir));
-          }
-        }
+        for (int k = 0; k < D; k++)
+          if (k < d) B.edge_pt[e * d + k] = __dadd_rn(row64[k], __dmul_rn(tn, row64[d + k]));
       } else {
         const unsigned long long q = atomicAdd(&B.cnt->n_redo, 1ull);
         if (q < cap) B.redo[q] = e;
@@ -1938,6 +1976,7 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, 2) k_b_roots(const MfSlot *sl
                                                                 int group) {
   __shared__ int snear[ROOT_WARPS][NEAR_CAP];
   __shared__ int smid[ROOT_WARPS][MID_CAP];
+  __shared__ float shc[ROOT_WARPS][3 * HC_ALL];
   __shared__ int sq[ROOT_WARPS][2][64];
   __shared__ RootWarpState sws[ROOT_WARPS];
   extern __shared__ int sgrp_all[];  // [ROOT_WARPS][GROUP_CAP] when group > 1
@@ -1959,7 +1998,7 @@ __global__ void __launch_bounds__(ROOT_WARPS * 32, 2) k_b_roots(const MfSlot *sl
       unsigned long long evals = 0, terms[2] = {0, 0};
       for (int q = 0; q < ng; q++)
         root_edge<D>(S.F, S.R, S.B, e0 + q, S.root_tol, gn >= 0 ? sgrp : nullptr, gn, snear[w],
-                     smid[w], sq[w][0], sq[w][1], &sws[w], evals, terms,
+                     smid[w], shc[w], sq[w][0], sq[w][1], &sws[w], evals, terms,
                      S.precision != MF_FP64 && !(S.flags & MF_ROOTS_FP64_EXACT), false, nullptr,
                      nullptr, 0);
       root_flush(S.B, evals, terms);
@@ -2064,9 +2103,9 @@ static void launch_roots_d(const MfFrame &F, const MfRbfDev &R, const MfTraceBuf
     k_roots_prep<DD><<<nb, 256, 0, st>>>(F, B, e0, n);
     k_roots_f64<DD, MINB><<<grid, ROOT_WARPS * 32, dyn, st>>>(F, R, B, e0, n, tol, group, fast, 1,
                                                              nullptr, nullptr);
-    k_roots_x<DD><<<nb, 256, 0, st>>>(F, B, B.defer_cap);
+    k_roots_x<DD><<<nb, 256, 0, st>>>(F, B, B.defer_cap, e0);
     k_roots_terms<DD><<<sms * 16, 256, 0, st>>>(R, B, B.defer_cap);
-    k_roots_finish<DD><<<nb, 256, 0, st>>>(F, R, B, B.defer_cap, tol, fast);
+    k_roots_finish<DD><<<nb, 256, 0, st>>>(F, R, B, B.defer_cap, tol, fast, e0);
     k_roots_f64<DD, MINB><<<sms * 4, ROOT_WARPS * 32, 0, st>>>(F, R, B, 0, B.defer_cap, tol, 1,
                                                               fast, 0, B.redo, &B.cnt->n_redo);
   }
