@@ -107,6 +107,12 @@ __global__ void k_prepare_rbf(int d, int n, const double *sv, const double *alph
     a = fabs(al);
     // strong iff gamma r^2 < ln(|alpha| / tau)
     strong32[j] = a > STRONG_TAU ? (float)log(a / STRONG_TAU) : -1.0f;
+    // below 8 coordinates the row's padding also carries alpha and the
+    // strong threshold, so that one gather of the row serves the root screen
+    if (d < 8) {
+      svhl[(int64_t)j * 16 + 2 * d] = alpha32[j];
+      svhl[(int64_t)j * 16 + 2 * d + 1] = strong32[j];
+    }
   }
   a = mf_warp_sum_d(a);
 #pragma unroll
@@ -285,6 +291,7 @@ struct F64Acc {
   double f, g;  // f (with b) and, with GRAD, grad f . dir
   float weak;   // sum of |term| over weak terms (error bound input)
   float wf, wg; // FP32 partial sums of the weak terms
+  float weakc;  // sum of |term| over the weak terms taken from the root screen's cache
 };
 
 // x split as x_hi + x_lo (both FP32) so that FP32 differences to a support
@@ -401,6 +408,33 @@ __device__ __forceinline__ void f64_term(const MfRbfDev &R, const double *x, con
   if (GRAD) acc.g = fma(e, proj, acc.g);
 }
 
+// Support vector j's row for the root path, in one gather: the hi/lo
+// coordinate pairs c[2k], c[2k + 1] (k < D) and, below 8 coordinates, alpha
+// and the strong threshold from the row's padding (else from their arrays).
+template <int D>
+__device__ __forceinline__ void sv_row(const MfRbfDev &R, int j, float *c, float &al, float &s32) {
+  constexpr int Q = D < 8 ? (2 * D + 2 + 3) / 4 : 4;
+  const float4 *row = reinterpret_cast<const float4 *>(R.svhl + (int64_t)j * 16);
+  float v[4 * Q];
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    const float4 t = __ldg(row + q);
+    v[4 * q] = t.x;
+    v[4 * q + 1] = t.y;
+    v[4 * q + 2] = t.z;
+    v[4 * q + 3] = t.w;
+  }
+#pragma unroll
+  for (int k = 0; k < 2 * D && k < 4 * Q; k++) c[k] = v[k];
+  if (D < 8) {
+    al = v[D < 8 ? 2 * D : 0];
+    s32 = v[D < 8 ? 2 * D + 1 : 0];
+  } else {
+    al = R.alpha32[j];
+    s32 = R.strong32[j];
+  }
+}
+
 // Weak term (|alpha| e <= tau): FP32 throughout with hi/lo-split coordinates.
 // Its relative error is at most (d+2) u gamma r^2 (differences, squares and
 // the exponent's rounding, u = 2^-24) + 2^-20 (ex2) + 2u (alpha, product); on
@@ -411,22 +445,17 @@ __device__ __forceinline__ void f32_weak_term(const MfRbfDev &R, const Split32<D
   if (j < 0) return;
   const int d = dim_of<D>(R.d);
   const float g2 = (float)(R.gamma * 1.4426950408889634);
-  float r2 = 0.f, proj = 0.f;
-  const float4 *row = reinterpret_cast<const float4 *>(R.svhl + (int64_t)j * 16);
+  float r2 = 0.f, proj = 0.f, c[2 * D], al, s32;
+  sv_row<D>(R, j, c, al, s32);
 #pragma unroll
-  for (int k2 = 0; k2 < (D + 1) / 2; k2++) {
-    const float4 s = __ldg(row + k2);
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-      const int k = 2 * k2 + h;
-      if (k < D && k < d) {
-        const float t = (x.hi[k] - (h ? s.z : s.x)) + (x.lo[k] - (h ? s.w : s.y));
-        r2 = fmaf(t, t, r2);
-        if (GRAD) proj = fmaf(t, x.dir[k], proj);
-      }
+  for (int k = 0; k < D; k++) {
+    if (k < d) {
+      const float t = (x.hi[k] - c[2 * k]) + (x.lo[k] - c[2 * k + 1]);
+      r2 = fmaf(t, t, r2);
+      if (GRAD) proj = fmaf(t, x.dir[k], proj);
     }
   }
-  const float e = R.alpha32[j] * ex2_approx(-g2 * r2);
+  const float e = al * ex2_approx(-g2 * r2);
   acc.wf += e;
   acc.weak += fabsf(e);
   if (GRAD) acc.wg = fmaf(e, proj, acc.wg);
@@ -456,7 +485,7 @@ __device__ F64Acc warp_f64_pass(const MfRbfDev &R, const double *x, const double
   const int lane = threadIdx.x & 31;
   const int d = dim_of<D>(R.d);
   const float g32 = (float)R.gamma;
-  F64Acc acc = {0.0, 0.0, 0.f, 0.f, 0.f};
+  F64Acc acc = {0.0, 0.0, 0.f, 0.f, 0.f, 0.f};
   const Split32<D> xs = split32<D>(d, x, dir);
   int ns = 0, nw = 0;
   const unsigned lt = (1u << lane) - 1u;
@@ -920,41 +949,45 @@ struct Root32 {
   float g, gp, gpp, gpa;  // gpa: the sum of |g'| terms (cancellation measure)
 };
 
-// The FP32 stage's per-term data, cached by the segment screen for the first
-// HC_STRONG strong and HC_MID mid entries of each edge (per warp, in shared
-// memory): with u = x1 - s (FP32 hi/lo differences) and dir = x2 - x1,
+// The per-term data of the root path, cached by the segment screen for the
+// first HC_STRONG strong, HC_MID mid and HC_WEAK weak entries of each edge
+// (per warp, in shared memory): with u = x1 - s (FP32 hi/lo differences)
+// and dir = x2 - x1,
 // A = |u|^2 and Bp = u . dir, so that at x(t) = x1 + t dir
 //   proj(t) = (x(t) - s) . dir = Bp + t |dir|^2,
 //   r2(t) = |x(t) - s|^2 = A + t (Bp + proj(t)),
 // and an evaluation reads three floats per term instead of gathering the
-// vector's coordinates again.  r2's absolute error stays below ~(d+3) 2^-24
-// (|u| + |dir|)^2, i.e. a relative term error of a few 1e-6 on the kept
-// range gamma r2 <= T + 1/2 (the stage only steers and feeds the reused g').
+// vector's coordinates again.  With the support vector at distance r from
+// x(t), |u| + t |dir| <= r + 2 |dir|, and the roundings of u (2 per
+// coordinate), A (d FMAs), Bp, |dir|^2, proj and r2 leave
+//   |r2~ - r2| <= 2^-24 (r2 + (d + 4.5) (r + 2 |dir|)^2);
+// with the rounding of gamma log2(e) and of the exponent's product the
+// term's relative error from its exponent is below
+//   (d + 8) 2^-24 gamma (r + 2 |dir|)^2,
+// plus ex2's 2^-20 and 2^-23 for alpha and the product (root_rel_cached).
+// The FP32 stage only steers and feeds the reused g' (per-term errors of a
+// few 1e-6 there); the weak terms of the deferred FP64 step use the bound.
 #define HC_STRONG 192
 #define HC_MID 64
-#define HC_ALL (HC_STRONG + HC_MID)
+#define HC_WEAK 192
+#define HC_ALL (HC_STRONG + HC_MID + HC_WEAK)
 
-// A and Bp of support vector j against x1 (hi/lo) along dir32, from its
-// hi/lo coordinate row.
+// A, Bp and alpha of support vector j against x1 (hi/lo) along dir32.
 template <int D>
 __device__ __forceinline__ void term_ab(const MfRbfDev &R, int j, const float *x1hi,
                                         const float *x1lo, const float *dir32, float &A,
-                                        float &Bp) {
+                                        float &Bp, float &al) {
   const int d = dim_of<D>(R.d);
-  const float4 *row = reinterpret_cast<const float4 *>(R.svhl + (int64_t)j * 16);
+  float c[2 * D], s32;
+  sv_row<D>(R, j, c, al, s32);
   A = 0.f;
   Bp = 0.f;
 #pragma unroll
-  for (int k2 = 0; k2 < (D + 1) / 2; k2++) {
-    const float4 s = __ldg(row + k2);
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-      const int k = 2 * k2 + h;
-      if (k < D && k < d) {
-        const float u = (x1hi[k] - (h ? s.z : s.x)) + (x1lo[k] - (h ? s.w : s.y));
-        A = fmaf(u, u, A);
-        Bp = fmaf(u, dir32[k], Bp);
-      }
+  for (int k = 0; k < D; k++) {
+    if (k < d) {
+      const float u = (x1hi[k] - c[2 * k]) + (x1lo[k] - c[2 * k + 1]);
+      A = fmaf(u, u, A);
+      Bp = fmaf(u, dir32[k], Bp);
     }
   }
 }
@@ -985,8 +1018,7 @@ __device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const float *hc
       al = hc[2 * HC_ALL + c];
     } else {
       const int j = strong ? near[i] : midl[i - ns];
-      term_ab<D>(R, j, x1hi, x1lo, dir32, A, Bp);
-      al = R.alpha32[j];
+      term_ab<D>(R, j, x1hi, x1lo, dir32, A, Bp, al);
     }
     const float proj = fmaf(t, dd32, Bp);
     const float r2 = fmaf(t, proj + Bp, A);
@@ -1008,16 +1040,43 @@ __device__ __forceinline__ Root32 root_eval32(const MfRbfDev &R, const float *hc
 
 // The FP32 part of a root evaluation at xs: the mid entries, then the weak
 // ones, as one lane-strided list (accumulated into acc.wf / wg / weak).
+// With hc (the deferred step, whose point is x1 + tc dir with tc the FP32
+// stage's t, exactly), the weak entries that the screen cached are
+// evaluated from A, Bp and alpha (r2 = A + tc (Bp + proj)); their |terms|
+// go to acc.weakc, bounded by root_rel_cached instead of R.weak_rel.
 template <bool GRAD, int D>
 __device__ __forceinline__ void root_fp32_part(const MfRbfDev &R, const int *near, int nw,
                                                const int *midl, int nm, const Split32<D> &xs,
-                                               F64Acc &acc) {
+                                               F64Acc &acc, const float *hc = nullptr,
+                                               float tc = 0.f, float dd32 = 0.f) {
   const int lane = threadIdx.x & 31;
   const int nr = nm + nw;
+  const float g2 = (float)(R.gamma * 1.4426950408889634);
   for (int i = lane; i < nr; i += 32) {
-    const int j = i < nm ? midl[i] : near[NEAR_CAP - 1 - (i - nm)];
-    f32_weak_term<GRAD, D>(R, xs, j, acc);
+    const int w = i - nm;
+    if (hc && w >= 0 && w < HC_WEAK) {
+      const int c = HC_STRONG + HC_MID + w;
+      const float A = hc[c], Bp = hc[HC_ALL + c], al = hc[2 * HC_ALL + c];
+      const float proj = fmaf(tc, dd32, Bp);
+      const float r2 = fmaf(tc, proj + Bp, A);
+      const float e = al * ex2_approx(-g2 * r2);
+      acc.wf += e;
+      acc.weakc += fabsf(e);
+      if (GRAD) acc.wg = fmaf(e, proj, acc.wg);
+    } else {
+      const int j = i < nm ? midl[i] : near[NEAR_CAP - 1 - w];
+      f32_weak_term<GRAD, D>(R, xs, j, acc);
+    }
   }
+}
+
+// Relative error bound of a cached weak term on an edge with |dir|^2 = dd32
+// (every kept vector lies within the screen radius of the segment; 1.1
+// covers this bound's own FP32 rounding).
+__device__ __forceinline__ float root_rel_cached(const MfRbfDev &R, int d, float dd32) {
+  const float q = sqrtf(R.screen_r2) + 2.f * sqrtf(dd32);
+  return 1.1f * ((float)d + 8.f) * 5.9604644775390625e-08f * (float)R.gamma * q * q +
+         9.5367431640625e-07f + 2.f * 5.9604644775390625e-08f;
 }
 
 // FP64 evaluation of g and g' at x over the near list (all lanes); xs is x
@@ -1028,7 +1087,7 @@ __device__ __forceinline__ F64Acc root_eval64(const MfRbfDev &R, const int *near
                                               const double *dir, const Split32<D> &xs,
                                               unsigned long long *terms) {
   const int lane = threadIdx.x & 31;
-  F64Acc acc = {0.0, 0.0, 0.f, 0.f, 0.f};
+  F64Acc acc = {0.0, 0.0, 0.f, 0.f, 0.f, 0.f};
   for (int i = lane; i < ns; i += 32) f64_term<GRAD, D>(R, x, dir, near[i], acc);
   // mid entries, then weak ones, as one list
   const int nr = nm + nw;
@@ -1173,20 +1232,16 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
   // coalesced coordinate arrays) and the survivors are compacted
   auto screen_round = [&](bool valid, int j, bool gathered) {
     bool keep = false, strong = false, strong64 = false;
-    float cA = 0.f, cB = 0.f;
+    float cA = 0.f, cB = 0.f, al = 0.f, s32 = 0.f;
     if (valid) {
       float p[D], sl[D], pd = 0.f;
       if (gathered) {
-        const float4 *row = reinterpret_cast<const float4 *>(R.svhl + (int64_t)j * 16);
+        float c[2 * D];
+        sv_row<D>(R, j, c, al, s32);
 #pragma unroll
-        for (int k2 = 0; k2 < (D + 1) / 2; k2++) {
-          const float4 v = __ldg(row + k2);
-          p[2 * k2] = 2 * k2 < d ? v.x - x1hi[2 * k2] : 0.f;
-          sl[2 * k2] = v.y;
-          if (2 * k2 + 1 < D) {
-            p[2 * k2 + 1] = 2 * k2 + 1 < d ? v.z - x1hi[2 * k2 + 1] : 0.f;
-            sl[2 * k2 + 1] = v.w;
-          }
+        for (int k = 0; k < D; k++) {
+          p[k] = k < d ? c[2 * k] - x1hi[k] : 0.f;
+          sl[k] = c[2 * k + 1];
         }
       } else {
 #pragma unroll
@@ -1209,12 +1264,12 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
           r2 = fmaf(q, q, r2);
         }
         keep = r2 <= R.screen_r2;
-        const float s32 = R.strong32[j];
+        if (!gathered) s32 = R.strong32[j];
         strong = g32 * r2 < s32 + 0.5f;
         strong64 = g32 * r2 < s32 + shift64;
-        if (keep && strong) {
-          // the FP32 stage's A and Bp (term_ab's operations: x1hi - s_hi is
-          // -p exactly)
+        if (keep) {
+          // the cached A and Bp (term_ab's operations: x1hi - s_hi is -p
+          // exactly)
 #pragma unroll
           for (int k = 0; k < D; k++) {
             if (k < d) {
@@ -1239,7 +1294,13 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
       const int c = strong64 ? cs : HC_STRONG + cm;
       hc[c] = cA;
       hc[HC_ALL + c] = cB;
-      hc[2 * HC_ALL + c] = R.alpha32[j];
+      hc[2 * HC_ALL + c] = gathered ? al : R.alpha32[j];
+    }
+    if (keep && !strong && cw < HC_WEAK) {
+      const int c = HC_STRONG + HC_MID + cw;
+      hc[c] = cA;
+      hc[HC_ALL + c] = cB;
+      hc[2 * HC_ALL + c] = gathered ? al : R.alpha32[j];
     }
     if (keep && !strong && ns + cw < NEAR_CAP) near[NEAR_CAP - 1 - cw] = j;
     ns += __popc(ms);
@@ -1375,10 +1436,14 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
       // step's FP32 part and hands over the strong entries (unless the
       // part's error bound is too coarse or the pools are full; the step
       // then runs here)
-      F64Acc part = {0.0, 0.0, 0.f, 0.f, 0.f};
-      root_fp32_part<false, D>(R, near, nw, midl, nm, xs, part);
+      F64Acc part = {0.0, 0.0, 0.f, 0.f, 0.f, 0.f};
+      root_fp32_part<false, D>(R, near, nw, midl, nm, xs, part, hc, t32, dd32);
       const float wf = mf_warp_sum_f(part.wf), weak = mf_warp_sum_f(part.weak);
-      if (!root_fp32_part_too_coarse(R, weak, gpf, fast)) {
+      const float weakc = mf_warp_sum_f(part.weakc);
+      // the cached weak terms count with their own bound, as a multiple of
+      // R.weak_rel's
+      const float kc = fmaxf(root_rel_cached(R, d, dd32) / R.weak_rel32, 1.f);
+      if (!root_fp32_part_too_coarse(R, fmaf(weakc, kc, weak), gpf, fast)) {
         const int nch = (ns + DEFER_CHUNK - 1) / DEFER_CHUNK;
         unsigned long long at = 0, lat = 0;
         if (lane == 0) {

@@ -140,7 +140,8 @@ struct MfRbfDev {
   const double *exp_tab; // [64] 2^(j/64), the table of mf_exp_neg
   // row-major copies for gathers (one support vector per 64-byte row):
   const double *sv64r;   // [n][8] coordinates, zero-padded
-  const float *svhl;     // [n][16] (hi, lo) FP32 pairs of the coordinates
+  const float *svhl;     // [n][16] (hi, lo) FP32 pairs of the coordinates; for d < 8
+                         // the pair after them holds (alpha, strong32)
   // double-float (FP32 pair) forms for the root step's strong terms:
   const float *sv3;        // [n][24] each coordinate as three floats s1 + s2 + s3 (exact)
   const float *alpha_lo32; // [n] alpha - (double)alpha32
