@@ -368,9 +368,7 @@ def config_lines(ctx, d6_lam=0.15):
                       "edges_per_proof": r["n_edges"], "cells_per_proof": r["n_cells"],
                       "cells_points_in_collision": int(p.last[3].sum().item()),
                       "cells_whole_certified": int(p.whole.sum().item())}
-    keep["d3"] = dict(w=w3, points=r["points"].cpu().numpy(), off=r["cell_off"].cpu().numpy(),
-                      idx=r["cell_idx"].cpu().numpy(), cv=p.last[3].cpu().numpy(),
-                      whole=p.whole.cpu().numpy())
+    keep["d3"] = sample_cells(w3, r, p.last[3], p.whole)
     del p, r
     w6 = W.config_d6(lam=d6_lam)
     ms, p, r = _proof_ms(ctx, w6)
@@ -392,10 +390,31 @@ def config_lines(ctx, d6_lam=0.15):
     return out, keep
 
 
+def sample_cells(w, r, cv, whole, n_cells=300, seed=7):
+    """Up to n_cells random cells of a proof whose points are all in
+    collision, with their points and whole-cell verdicts (host copies), for
+    the dense-sampling check of the CPU-baseline leg."""
+    import torch
+    cells = torch.nonzero(cv).flatten()
+    if cells.numel() == 0:
+        return dict(w=w, cells=[], whole=np.zeros(0, bool))
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    pick = cells[torch.randperm(cells.numel(), generator=g)[:n_cells].to(cells.device)]
+    lo = r["cell_off"][pick].cpu().tolist()
+    hi = r["cell_off"][pick + 1].cpu().tolist()
+    out = []
+    for a, b in zip(lo, hi):
+        idx = r["cell_idx"][a:b]
+        out.append(r["points"][idx].cpu().numpy())
+    wh = whole[pick].cpu().numpy().astype(bool) if whole is not None else np.zeros(len(out), bool)
+    return dict(w=w, cells=out, whole=wh)
+
+
 def oracle_checks(keep):
     """CPU-baseline leg: the FP64 oracle on the samples the GPU lines kept:
     the d=6 mixed proof's sampled roots and end values (error vs the oracle),
-    and the d=3 proof's cells: the point-only verdict's false-certify rate
+    and cells whose points are all in collision (from the main proof, and the
+    d=3 proof's when it has any): the point-only verdict's false-certify rate
     against dense sampling of each cell's piece (convex combinations of its
     points), and that no whole-cell certified cell has a free sample."""
     import oracle
@@ -412,24 +431,25 @@ def oracle_checks(keep):
             "max_dpoint": float(np.abs(k["pt"] - pt)[ok].max()),
             "max_df_edge_ends": float(np.abs(k["f"] - f2).max()),
             "sign_mismatches": int(np.sum((f2 >= 0) != (k["f"] >= 0)))}
-    if "d3" in keep:
-        k = keep["d3"]
+    for name in ("main", "d3"):
+        if name not in keep:
+            continue
+        k = keep[name]
         w = k["w"]
         rng = np.random.default_rng(7)
-        cells = np.flatnonzero(k["cv"])
-        pick = rng.choice(cells, min(len(cells), 300), replace=False)
         false_pt = false_whole = 0
-        for c in pick:
-            P = k["points"][k["idx"][k["off"][c]:k["off"][c + 1]]]
+        for P, wh in zip(k["cells"], k["whole"]):
             S = rng.dirichlet(np.ones(P.shape[0]), size=200) @ P
             v, _, _ = oracle.certify(w.dh, w.radius, w.obs_type, w.obs_pose, w.obs_dims, S)
             free = not v.all()
             false_pt += free
-            false_whole += free and bool(k["whole"][c])
-        out["d3_cells_dense_sampling"] = {
-            "cells_sampled": int(len(pick)), "samples_per_cell": 200,
+            false_whole += free and bool(wh)
+        n = len(k["cells"])
+        out["%s_cells_dense_sampling" % name] = {
+            "workload": w.name, "cells_sampled": n, "samples_per_cell": 200,
+            "cells_whole_certified": int(np.sum(k["whole"])),
             "point_only_false_certify": int(false_pt),
-            "point_only_false_certify_rate": float(false_pt) / max(len(pick), 1),
+            "point_only_false_certify_rate": float(false_pt) / max(n, 1),
             "whole_certified_with_free_sample": int(false_whole)}
     return out
 
@@ -640,11 +660,13 @@ def run_gb300(args):
             # the server gets a context of its own: the proofs' resident tables
             # and outputs are released first, so that its arena can hold many
             # requests
+            keep_main = sample_cells(w, r, cv, proof.whole)
             del proof, r, v, m, cv
             ctx.close()
             torch.cuda.empty_cache()
             ctx = Context(local, 0)
             line["configs"], keep = config_lines(ctx)
+            keep["main"] = keep_main
             if "cpu_baseline" in line:
                 line["cpu_baseline"].update(oracle_checks(keep))
             ctx.close()

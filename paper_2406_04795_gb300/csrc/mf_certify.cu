@@ -242,12 +242,14 @@ __device__ __forceinline__ bool point_deep_inside32(const CertObsT<float> &o, co
 // distance is then exactly 0); tested only when the bound is 0.  Its
 // candidates: the middle of the segment's slab-clipped interval in the
 // shrunk box (boxes), the final t and the projection of the centre
-// (cylinders), the closest point (spheres).  Not inlined: the kernel calls
+// (cylinders), the closest point (spheres).  *ubd: an upper bound on the
+// same distance, from the squared distance at the final t plus eta (the
+// distance from one point of the segment).  Not inlined: the kernel calls
 // it from three places, and one copy keeps the code in the instruction
 // cache.
 __device__ __noinline__ float seg_obstacle_lb32(const CertObsT<float> &o, const float *pa,
                                                 const float *pb, float eta, float dlt, float *tmin,
-                                                bool *deep) {
+                                                bool *deep, float *ubd) {
   const float wa[3] = {pa[0] - o.t[0], pa[1] - o.t[1], pa[2] - o.t[2]};
   const float wb[3] = {pb[0] - o.t[0], pb[1] - o.t[1], pb[2] - o.t[2]};
   float a[3], dl[3];
@@ -270,6 +272,7 @@ __device__ __noinline__ float seg_obstacle_lb32(const CertObsT<float> &o, const 
       if (it < 3 && H > 0.f) t = fminf(fmaxf(t - G / H, 0.f), 1.f);
     }
     *tmin = t;
+    *ubd = sqrtf(F + eta) * 1.000001f;
     const float lbF = F - 2.f * fabsf(G) * (G > 0.f ? t : 1.f - t) - eta;
     *deep = !(lbF > 0.f) &&
             (point_deep_inside32(o, a, dl, tc, dlt) || point_deep_inside32(o, a, dl, t, dlt));
@@ -278,7 +281,9 @@ __device__ __noinline__ float seg_obstacle_lb32(const CertObsT<float> &o, const 
   if (o.type != MF_BOX) {
     *tmin = t;
     const float c0 = fmaf(t, dl[0], a[0]), c1 = fmaf(t, dl[1], a[1]), c2 = fmaf(t, dl[2], a[2]);
-    const float lb = fmaxf(sqrtf(c0 * c0 + c1 * c1 + c2 * c2) - o.h[0], 0.f);
+    const float c2s = c0 * c0 + c1 * c1 + c2 * c2;
+    const float lb = fmaxf(sqrtf(c2s) - o.h[0], 0.f);
+    *ubd = fmaxf(sqrtf(c2s + eta) * 1.000001f - o.h[0], 0.f) * 1.000001f;
     *deep = !(lb > 0.f) && point_deep_inside32(o, a, dl, t, dlt);
     return lb;
   }
@@ -301,6 +306,7 @@ __device__ __noinline__ float seg_obstacle_lb32(const CertObsT<float> &o, const 
     if (it < 3 && H > 0.f) t = fminf(fmaxf(t - G / H, 0.f), 1.f);
   }
   *tmin = t;
+  *ubd = sqrtf(F + eta) * 1.000001f;
   const float lbF = F - 2.f * fabsf(G) * (G > 0.f ? t : 1.f - t) - eta;
   *deep = false;
   if (!(lbF > 0.f)) {
@@ -354,21 +360,46 @@ __host__ __device__ __forceinline__ int cert_rec_stride(int d) { return (d + 2 +
 // cache (measured: 45 no-instruction stall cycles per issue).
 // Elements: link capsules e < NC (NC = NL with capsules, 0 without), then
 // spheres e - NC on their links.
-__global__ void __launch_bounds__(CERT_THREADS) k_certify_points(
-    int NL, const double *dh, const double *radius, int NS, const int32_t *sph_link,
-    const double *sph_c, const double *sph_r, int nobs, const int32_t *type, const double *pose,
-    const double *dims, const double *pts, int64_t n, int d, const double2 *sctab, uint8_t *verdict,
-    double *margin, int16_t *element, float *rec32) {
-  __shared__ CertObs so[CERT_MAX_OBS];
-  __shared__ CertObsT<float> sof[CERT_MAX_OBS];  // FP32 copy for the lower bounds
-  __shared__ double sdh[MF_MAXD * 4], srad[MF_MAXD], ssa[MF_MAXD], sca[MF_MAXD];
-  // FP32 copies, so that the FP32 passes convert nothing on the FP64 pipe
-  __shared__ float sdh32[MF_MAXD * 4], srad32[MF_MAXD], ssa32[MF_MAXD], sca32[MF_MAXD];
-  __shared__ double2 ssc[128];
-  __shared__ int ssl[MF_MAX_SPHERES];
-  __shared__ double ssc64[MF_MAX_SPHERES * 3], ssr64[MF_MAX_SPHERES];
-  __shared__ float ssc32[MF_MAX_SPHERES * 3], ssr32[MF_MAX_SPHERES];
-  for (int i = threadIdx.x; i < 128; i += blockDim.x) ssc[i] = sctab[i];
+
+// T <- T A with the standard DH link transform A = Rz(theta) Tz(d) Tx(a)
+// Rx(alpha),
+//   A = [ct, -st ca, st sa, a ct; st, ct ca, -ct sa, a st; 0, sa, ca, d],
+// row by row from c0 = T[r][0:2] . (ct, st) and v = T[r][0:2] . (-st, ct)
+// (30 FP64 operations instead of the 36 of the full product).
+__device__ __forceinline__ void cert_dh_step(double *T, double ct, double st, double ca, double sa,
+                                             double aa, double dd) {
+#pragma unroll
+  for (int r = 0; r < 3; r++) {
+    const double t0 = T[4 * r], t1 = T[4 * r + 1], t2 = T[4 * r + 2], t3 = T[4 * r + 3];
+    const double c0 = fma(t0, ct, t1 * st);
+    const double v = fma(t1, ct, -(t0 * st));
+    T[4 * r] = c0;
+    T[4 * r + 1] = fma(v, ca, t2 * sa);
+    T[4 * r + 2] = fma(t2, ca, -(v * sa));
+    T[4 * r + 3] = fma(aa, c0, fma(dd, t2, t3));
+  }
+}
+
+// The robot, the obstacles and the sin/cos table, per block in shared memory
+// (FP32 copies, so that the FP32 passes convert nothing on the FP64 pipe).
+struct CertShared {
+  CertObs so[CERT_MAX_OBS];
+  CertObsT<float> sof[CERT_MAX_OBS];
+  double sdh[MF_MAXD * 4], srad[MF_MAXD], ssa[MF_MAXD], sca[MF_MAXD];
+  float sdh32[MF_MAXD * 4], srad32[MF_MAXD], ssa32[MF_MAXD], sca32[MF_MAXD];
+  double2 ssc[128];
+  int ssl[MF_MAX_SPHERES];
+  double ssc64[MF_MAX_SPHERES * 3], ssr64[MF_MAX_SPHERES];
+  float ssc32[MF_MAX_SPHERES * 3], ssr32[MF_MAX_SPHERES];
+};
+
+__device__ __forceinline__ void cert_load_shared(CertShared &sh, int NL, const double *dh,
+                                                 const double *radius, int NS,
+                                                 const int32_t *sph_link, const double *sph_c,
+                                                 const double *sph_r, int nobs,
+                                                 const int32_t *type, const double *pose,
+                                                 const double *dims, const double2 *sctab) {
+  for (int i = threadIdx.x; i < 128; i += blockDim.x) sh.ssc[i] = sctab[i];
   for (int i = threadIdx.x; i < nobs; i += blockDim.x) {
     CertObs o;
     CertObsT<float> of;
@@ -380,29 +411,57 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(
       if (o.type == MF_BOX || (o.type == MF_CYLINDER && k == 1)) h *= 0.5;
       of.h[k] = (float)(o.h[k] = h);
     }
-    so[i] = o;
-    sof[i] = of;
+    sh.so[i] = o;
+    sh.sof[i] = of;
   }
   for (int i = threadIdx.x; i < NL * 4; i += blockDim.x) {
-    sdh[i] = dh[i];
-    sdh32[i] = (float)dh[i];
+    sh.sdh[i] = dh[i];
+    sh.sdh32[i] = (float)dh[i];
   }
   for (int i = threadIdx.x; i < NL; i += blockDim.x) {
-    srad[i] = radius ? radius[i] : 0.0;
-    srad32[i] = (float)srad[i];
-    sincos(dh[4 * i + 3], &ssa[i], &sca[i]);
-    ssa32[i] = (float)ssa[i];
-    sca32[i] = (float)sca[i];
+    sh.srad[i] = radius ? radius[i] : 0.0;
+    sh.srad32[i] = (float)sh.srad[i];
+    sincos(dh[4 * i + 3], &sh.ssa[i], &sh.sca[i]);
+    sh.ssa32[i] = (float)sh.ssa[i];
+    sh.sca32[i] = (float)sh.sca[i];
   }
   for (int i = threadIdx.x; i < NS; i += blockDim.x) {
-    ssl[i] = sph_link[i];
-    ssr64[i] = sph_r[i];
-    ssr32[i] = (float)sph_r[i];
-    for (int k = 0; k < 3; k++) ssc32[3 * i + k] = (float)(ssc64[3 * i + k] = sph_c[3 * i + k]);
+    sh.ssl[i] = sph_link[i];
+    sh.ssr64[i] = sph_r[i];
+    sh.ssr32[i] = (float)sph_r[i];
+    for (int k = 0; k < 3; k++) sh.ssc32[3 * i + k] = (float)(sh.ssc64[3 * i + k] = sph_c[3 * i + k]);
   }
-  __syncthreads();
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p >= n) return;
+}
+
+// A point that at most two exact evaluations settle: its elements with a
+// pair inside an obstacle (bit masks over elements 0..63, 64..) and the
+// pairs (element, obstacle, FP32 start t) to evaluate (0xff: none).
+struct CertRec {
+  uint64_t deep_lo, deep_hi;
+  float t1, t2;
+  uint8_t e1, k1, e2, k2;
+  int32_t loc;  // the point's thread in the block
+};
+
+// Point p: margin = max over (element, obstacle) of radius - distance, its
+// verdict, deciding element and FP32 record.  FAST: after the FP32 bounds,
+// a point that at most two exact pair evaluations settle returns true with
+// its record in *simple for cert_simple_eval; every other point is appended
+// to queue and left to a FAST = false pass.
+template <bool FAST>
+__device__ __noinline__ bool cert_point(const CertShared &sh, int NL, const double *radius, int NS,
+                                        int nobs, const double *pts, int64_t p, int d,
+                                        uint8_t *verdict, double *margin, int16_t *element,
+                                        float *rec32, CertRec *simple, uint32_t *queue,
+                                        unsigned long long *nq) {
+  const CertObs *so = sh.so;
+  const CertObsT<float> *sof = sh.sof;
+  const double *sdh = sh.sdh, *srad = sh.srad, *ssa = sh.ssa, *sca = sh.sca;
+  const float *sdh32 = sh.sdh32, *srad32 = sh.srad32, *ssa32 = sh.ssa32, *sca32 = sh.sca32;
+  const double2 *ssc = sh.ssc;
+  const int *ssl = sh.ssl;
+  const double *ssc64 = sh.ssc64, *ssr64 = sh.ssr64;
+  const float *ssc32 = sh.ssc32, *ssr32 = sh.ssr32;
   const int NC = radius ? NL : 0, NE = NC + NS;
   // Forward kinematics, T = T * A_i with the standard DH link transform,
   // keeping every frame origin (link i runs from origin i to origin i+1) and,
@@ -452,24 +511,9 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(
   int done = 0;  // FP64 origins known: 0 .. done
   auto fk64 = [&](int upto) {
     for (int i = done; i < upto; i++) {
-      const double th = pts[p * d + i] + sdh[4 * i], dd = sdh[4 * i + 1], aa = sdh[4 * i + 2];
       double st, ct;
-      cert_sincos(th, ssc, &st, &ct);
-      const double sa = ssa[i], ca = sca[i];
-      const double A[12] = {ct, -st * ca, st * sa, aa * ct, st, ct * ca, -ct * sa, aa * st,
-                            0.0, sa, ca, dd};
-      double N[12];
-#pragma unroll
-      for (int r = 0; r < 3; r++) {
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-          double v = T[4 * r + 0] * A[c] + T[4 * r + 1] * A[4 + c] + T[4 * r + 2] * A[8 + c];
-          if (c == 3) v += T[4 * r + 3];
-          N[4 * r + c] = v;
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 12; k++) T[k] = N[k];
+      cert_sincos(pts[p * d + i] + sdh[4 * i], ssc, &st, &ct);
+      cert_dh_step(T, ct, st, sca[i], ssa[i], sdh[4 * i + 2], sdh[4 * i + 1]);
       org[3 * (i + 1) + 0] = T[3];
       org[3 * (i + 1) + 1] = T[7];
       org[3 * (i + 1) + 2] = T[11];
@@ -537,7 +581,7 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(
   // inside it shrunk by the same 1e-4 (1 + scale), which covers the FP32
   // chain's error in every coordinate) is at distance exactly 0: its margin
   // is the element's radius, with no FP64 work (*deep).
-  auto upper = [&](int e, int k, float *tmin, bool *deep) -> float {
+  auto upper = [&](int e, int k, float *tmin, bool *deep, float *lower = nullptr) -> float {
     float a[3], b[3];
     const float rad = elem32(e, a, b);
     float scale = 1.f;
@@ -548,14 +592,20 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(
     // squared distance stays far below 4e-5 (1 + scale)^2
     const float eta = 4e-5f * (1.f + scale) * (1.f + scale);
     const float sl = 1e-4f * (1.f + scale);
-    return rad - (seg_obstacle_lb32(sof[k], a, b, eta, sl, tmin, deep) - sl);
+    float ubd;
+    const float lbd = seg_obstacle_lb32(sof[k], a, b, eta, sl, tmin, deep, &ubd);
+    if (lower) *lower = rad - (ubd + sl);
+    return rad - (lbd - sl);
   };
   auto rad64 = [&](int e) -> double { return e < NC ? srad[e] : ssr64[e - NC]; };
   // first pass: the deep pairs fix a margin without FP64 (best_in, reached
   // first by element ein); the other pairs give bounds ub (largest ub1 at
   // (bi, bk), second ub2; per element the largest, ube, and whether it has
   // a deep pair)
-  float ub1 = -INFINITY, ub2 = -INFINITY, tb = 0.f;
+  float ub1 = -INFINITY, ub2 = -INFINITY, tb = 0.f, lb1 = -INFINITY;
+  // FAST: the pair with the second-largest bound (ub2) and the third bound
+  float ub3 = -INFINITY, tb2 = 0.f, lb2 = -INFINITY;
+  int bi2 = -1, bk2 = -1;
   int bi = -1, bk = -1, ein = -1;
   double best_in = -INFINITY;
   float ube[CERT_MAX_ELEM];
@@ -566,9 +616,9 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(
   for (int e = 0; e < NE; e++) {
     float um = -INFINITY;
     for (int k = 0; k < nobs; k++) {
-      float tk;
+      float tk, lbk;
       bool deep;
-      const float ub = upper(e, k, &tk, &deep);
+      const float ub = upper(e, k, &tk, &deep, &lbk);
       if (deep) {
         if (e < 64) deep_lo |= 1ull << e;
         else deep_hi |= 1ull << (e - 64);
@@ -580,16 +630,68 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(
       }
       um = fmaxf(um, ub);
       if (ub > ub1) {
+        if (FAST) {
+          ub3 = ub2;
+          bi2 = bi;
+          bk2 = bk;
+          tb2 = tb;
+          lb2 = lb1;
+        }
         ub2 = ub1;
         ub1 = ub;
         bi = e;
         bk = k;
         tb = tk;
+        lb1 = lbk;
       } else if (ub > ub2) {
+        if (FAST) {
+          ub3 = ub2;
+          bi2 = e;
+          bk2 = k;
+          tb2 = tk;
+          lb2 = lbk;
+        }
         ub2 = ub;
+      } else if (FAST && ub > ub3) {
+        ub3 = ub;
       }
     }
     ube[e] = um;
+  }
+  if (FAST) {
+    // L = max(best_in, lb1, lb2) is a lower bound on the point's margin
+    // (lb: the pair's margin bound from the upper distance bound of the FP32
+    // chain plus the same slack).  When the third-largest bound lies below
+    // L by more than the gap, only the two pairs with the largest bounds
+    // (those of them whose bound reaches L - gap) can hold the maximum or tie
+    // with it, besides the elements inside an obstacle (margin = radius):
+    // their exact evaluations settle the point (cert_simple_eval).  The gap
+    // covers the FP32 rounding of the bounds, the FP64 distance's 2e-12 and
+    // the 1e-9 tie.
+    const double L = fmax(best_in, (double)fmaxf(lb1, lb2));
+    const double thr = L - 4e-6 * (1.0 + fabs(L));
+    if (bi < 0 || (double)ub3 < thr) {
+      CertRec r;
+      r.deep_lo = deep_lo;
+      r.deep_hi = deep_hi;
+      r.e1 = r.k1 = r.e2 = r.k2 = 0xff;
+      r.t1 = tb;
+      r.t2 = tb2;
+      r.loc = 0;
+      if (bi >= 0 && (double)ub1 >= thr) {
+        r.e1 = (uint8_t)bi;
+        r.k1 = (uint8_t)bk;
+      }
+      if (bi2 >= 0 && (double)ub2 >= thr) {
+        r.e2 = (uint8_t)bi2;
+        r.k2 = (uint8_t)bk2;
+      }
+      *simple = r;
+      return true;
+    }
+    const unsigned long long q = atomicAdd(nq, 1ull);
+    queue[q] = (uint32_t)p;
+    return false;
   }
   // exact margins of the other pairs: first the one with the largest bound
   // (if it can exceed best_in), then (if the second-largest bound exceeds
@@ -655,6 +757,180 @@ __global__ void __launch_bounds__(CERT_THREADS) k_certify_points(
     rec32[p * rs + d] = (float)best;
     rec32[p * rs + d + 1] = __int_as_float(be);
   }
+  return false;
+}
+
+// A settled point (CertRec): the FP64 chain to the deeper of the pairs'
+// links, their FP64 distances from the FP32 bounds' t (the operations of
+// cert_point's exact evaluation), the maximum margin with the elements
+// inside an obstacle (margin = radius), the deciding element (the lowest
+// index within CERT_ELEM_TIE of the maximum) and the outputs.
+__device__ __forceinline__ void cert_simple_eval(const CertShared &sh, int NL, const double *radius,
+                                                 const double *pts, int64_t p, int d,
+                                                 const CertRec &r, uint8_t *verdict,
+                                                 double *margin, int16_t *element, float *rec32) {
+  const int NC = radius ? NL : 0;
+  const int ec[2] = {r.e1 == 0xff ? -1 : (int)r.e1, r.e2 == 0xff ? -1 : (int)r.e2};
+  const int kc[2] = {(int)r.k1, (int)r.k2};
+  const double tc[2] = {(double)r.t1, (double)r.t2};
+  double m[2] = {-INFINITY, -INFINITY};
+  int fc[2] = {0, 0};
+#pragma unroll
+  for (int c = 0; c < 2; c++)
+    if (ec[c] >= 0) fc[c] = ec[c] < NC ? ec[c] + 1 : sh.ssl[ec[c] - NC] + 1;
+  const int fdeep = fc[0] > fc[1] ? fc[0] : fc[1];
+  if (fdeep > 0) {
+    double T[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+    double a[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}}, b[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    for (int i = 0; i < fdeep; i++) {
+#pragma unroll
+      for (int c = 0; c < 2; c++)
+        if (ec[c] == i && i < NC) {
+          a[c][0] = T[3];
+          a[c][1] = T[7];
+          a[c][2] = T[11];
+        }
+      double st, ct;
+      cert_sincos(pts[p * d + i] + sh.sdh[4 * i], sh.ssc, &st, &ct);
+      cert_dh_step(T, ct, st, sh.sca[i], sh.ssa[i], sh.sdh[4 * i + 2], sh.sdh[4 * i + 1]);
+#pragma unroll
+      for (int c = 0; c < 2; c++) {
+        if (ec[c] < 0 || fc[c] != i + 1) continue;
+        if (ec[c] < NC) {
+          b[c][0] = T[3];
+          b[c][1] = T[7];
+          b[c][2] = T[11];
+        } else {
+          const int s = ec[c] - NC;
+#pragma unroll
+          for (int q = 0; q < 3; q++)
+            a[c][q] = b[c][q] = T[4 * q] * sh.ssc64[3 * s] + T[4 * q + 1] * sh.ssc64[3 * s + 1] +
+                                T[4 * q + 2] * sh.ssc64[3 * s + 2] + T[4 * q + 3];
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 2; c++)
+      if (ec[c] >= 0) {
+        const double rad = ec[c] < NC ? sh.srad[ec[c]] : sh.ssr64[ec[c] - NC];
+        m[c] = rad - seg_obstacle_dist(sh.so[kc[c]], a[c], b[c], tc[c]);
+      }
+  }
+  auto rad64 = [&](int e) -> double { return e < NC ? sh.srad[e] : sh.ssr64[e - NC]; };
+  double best = -INFINITY;
+  for (uint64_t w = r.deep_lo; w; w &= w - 1) best = fmax(best, rad64(__ffsll((long long)w) - 1));
+  for (uint64_t w = r.deep_hi; w; w &= w - 1)
+    best = fmax(best, rad64(64 + __ffsll((long long)w) - 1));
+  best = fmax(best, fmax(m[0], m[1]));
+  int be = -1;
+  if (best > -INFINITY) {
+    const int none = 1 << 30;
+    be = none;
+    for (uint64_t w = r.deep_lo; w && be == none; w &= w - 1) {
+      const int e = __ffsll((long long)w) - 1;
+      if (rad64(e) >= best - CERT_ELEM_TIE) be = e;
+    }
+    for (uint64_t w = r.deep_hi; w && be == none; w &= w - 1) {
+      const int e = 64 + __ffsll((long long)w) - 1;
+      if (rad64(e) >= best - CERT_ELEM_TIE) be = e;
+    }
+#pragma unroll
+    for (int c = 0; c < 2; c++)
+      if (ec[c] >= 0 && ec[c] < be && m[c] >= best - CERT_ELEM_TIE) be = ec[c];
+  }
+  margin[p] = best;
+  verdict[p] = best >= 0.0 ? 1 : 0;
+  if (element) element[p] = (int16_t)be;
+  if (rec32) {
+    const int rs = cert_rec_stride(d);
+    for (int q = 0; q < d; q++) rec32[p * rs + q] = (float)pts[p * d + q];
+    rec32[p * rs + d] = (float)best;
+    rec32[p * rs + d + 1] = __int_as_float(be);
+  }
+}
+
+// Certification of points, first pass (thread per point): the FP32 chain and
+// pair bounds of every point; the points that one exact evaluation settles
+// are sorted within the block by (link depth, obstacle type) of that pair,
+// so that the warps run the FP64 chain and distance with their lanes
+// together, and evaluated; the others are queued for k_certify_points_rest.
+#define CERT_KEYS 64
+__global__ void __launch_bounds__(CERT_THREADS) k_certify_points(
+    int NL, const double *dh, const double *radius, int NS, const int32_t *sph_link,
+    const double *sph_c, const double *sph_r, int nobs, const int32_t *type, const double *pose,
+    const double *dims, const double *pts, int64_t n, int d, const double2 *sctab, uint8_t *verdict,
+    double *margin, int16_t *element, float *rec32, uint32_t *queue, unsigned long long *nq) {
+  __shared__ CertShared sh;
+  __shared__ int s_cnt[CERT_KEYS], s_start[CERT_KEYS];
+  __shared__ CertRec s_rec[CERT_THREADS];
+  __shared__ int s_n;
+  cert_load_shared(sh, NL, dh, radius, NS, sph_link, sph_c, sph_r, nobs, type, pose, dims, sctab);
+  for (int i = threadIdx.x; i < CERT_KEYS; i += blockDim.x) s_cnt[i] = 0;
+  __syncthreads();
+  const int64_t p0 = blockIdx.x * (int64_t)blockDim.x;
+  const int64_t p = p0 + threadIdx.x;
+  CertRec rec;
+  bool simple = false;
+  if (p < n)
+    simple = cert_point<true>(sh, NL, radius, NS, nobs, pts, p, d, verdict, margin, element, rec32,
+                              &rec, queue, nq);
+  // counting sort of the settled points by (chain depth, obstacle type) of
+  // their deeper pair within the block (key 0: no exact evaluation)
+  int key = 0, pos = 0;
+  if (simple) {
+    const int NC = radius ? NL : 0;
+    const int e1 = rec.e1 == 0xff ? -1 : rec.e1, e2 = rec.e2 == 0xff ? -1 : rec.e2;
+    const int f1 = e1 < 0 ? 0 : (e1 < NC ? e1 + 1 : sh.ssl[e1 - NC] + 1);
+    const int f2 = e2 < 0 ? 0 : (e2 < NC ? e2 + 1 : sh.ssl[e2 - NC] + 1);
+    const int kk = f1 >= f2 ? rec.k1 : rec.k2;
+    key = (f1 > f2 ? f1 : f2) * 4 + (f1 || f2 ? sh.so[kk].type + 1 : 0);
+    key = key < CERT_KEYS ? key : CERT_KEYS - 1;
+    pos = atomicAdd(&s_cnt[key], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    // exclusive scan of the CERT_KEYS (= 64) counts: two per lane
+    const int lane = threadIdx.x;
+    const int c0 = s_cnt[2 * lane], c1 = s_cnt[2 * lane + 1];
+    int inc = c0 + c1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    s_start[2 * lane] = inc - c0 - c1;
+    s_start[2 * lane + 1] = inc - c1;
+    if (lane == 31) s_n = inc;
+  }
+  __syncthreads();
+  if (simple) {
+    rec.loc = (int32_t)threadIdx.x;
+    s_rec[s_start[key] + pos] = rec;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < s_n) {
+    const CertRec r = s_rec[threadIdx.x];
+    cert_simple_eval(sh, NL, radius, pts, p0 + r.loc, d, r, verdict, margin, element, rec32);
+  }
+}
+
+// Certification of points, second pass: the queued points, with the full
+// search (exact evaluations of every pair whose bound can reach the maximum,
+// and the deciding element's tie search).
+__global__ void __launch_bounds__(CERT_THREADS) k_certify_points_rest(
+    int NL, const double *dh, const double *radius, int NS, const int32_t *sph_link,
+    const double *sph_c, const double *sph_r, int nobs, const int32_t *type, const double *pose,
+    const double *dims, const double *pts, int d, const double2 *sctab, uint8_t *verdict,
+    double *margin, int16_t *element, float *rec32, const uint32_t *queue,
+    const unsigned long long *nq) {
+  __shared__ CertShared sh;
+  cert_load_shared(sh, NL, dh, radius, NS, sph_link, sph_c, sph_r, nobs, type, pose, dims, sctab);
+  __syncthreads();
+  const unsigned long long m = *nq;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    cert_point<false>(sh, NL, radius, NS, nobs, pts, (int64_t)queue[i], d, verdict, margin,
+                      element, rec32, nullptr, nullptr, nullptr);
 }
 
 // Whole-cell certificate (one thread per cell): with lo_k / hi_k the range of
@@ -930,7 +1206,7 @@ extern "C" int mf_certify_ex(mf_ctx *ctx, const mf_robot *robot, const mf_scene 
       (!robot->radius && robot->n_spheres == 0) ||
       (scene->n > 0 && (!scene->type || !scene->pose || !scene->dims)) ||
       (n_points > 0 && (!points || !out->point_verdict || !out->margin)) ||
-      (n_cells > 0 && want_cells && (!cell_off || !cell_idx)))
+      (n_cells > 0 && want_cells && (!cell_off || !cell_idx)) || n_points > 0xffffffffll)
     return mf_set_error(ctx, MF_ERR_INVALID, "mf_certify: bad arguments");
   cudaSetDevice(ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -948,8 +1224,10 @@ extern "C" int mf_certify_ex(mf_ctx *ctx, const mf_robot *robot, const mf_scene 
   const size_t o_el = o_L32 + al((size_t)NE * NL * 4 + 8);
   const size_t need_el = whole && !out->element ? al((size_t)n_points * 2 + 8) : 0;
   const size_t o_rec = o_el + need_el;
-  const size_t need_rec = fast ? (size_t)n_points * cert_rec_stride(d) * 4 : 0;
-  char *scr = (char *)mf_ctx_buffer(ctx, MF_SLOT_CERT, o_rec + need_rec + 256);
+  const size_t need_rec = fast ? al((size_t)n_points * cert_rec_stride(d) * 4) : 0;
+  // the queue of points left to the full search (and its length)
+  const size_t o_q = o_rec + need_rec, o_nq = o_q + al((size_t)n_points * 4 + 8);
+  char *scr = (char *)mf_ctx_buffer(ctx, MF_SLOT_CERT, o_nq + 256);
   if (!scr) return MF_ERR_OOM;
   unsigned *bad = (unsigned *)scr;
   const double2 *sctab = (const double2 *)(scr + o_tab);
@@ -957,7 +1235,10 @@ extern "C" int mf_certify_ex(mf_ctx *ctx, const mf_robot *robot, const mf_scene 
   float *dL32 = (float *)(scr + o_L32);
   float *rec32 = fast ? (float *)(scr + o_rec) : nullptr;
   int16_t *elem = out->element ? out->element : (need_el ? (int16_t *)(scr + o_el) : nullptr);
+  uint32_t *queue = (uint32_t *)(scr + o_q);
+  unsigned long long *nq = (unsigned long long *)(scr + o_nq);
   cudaMemsetAsync(bad, 0, sizeof(unsigned), st);
+  cudaMemsetAsync(nq, 0, sizeof(unsigned long long), st);
   {
     // (sin, cos)(j pi / 64), rounded from extended precision
     static const std::vector<double> tab = [] {
@@ -1012,7 +1293,13 @@ extern "C" int mf_certify_ex(mf_ctx *ctx, const mf_robot *robot, const mf_scene 
     k_certify_points<<<g, CERT_THREADS, 0, st>>>(
         NL, robot->dh, robot->radius, NS, robot->sphere_link, robot->sphere_center,
         robot->sphere_radius, scene->n, scene->type, scene->pose, scene->dims, points, n_points,
-        d, sctab, out->point_verdict, out->margin, elem, rec32);
+        d, sctab, out->point_verdict, out->margin, elem, rec32, queue, nq);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    k_certify_points_rest<<<(unsigned)(sms > 0 ? sms * 8 : 1024), CERT_THREADS, 0, st>>>(
+        NL, robot->dh, robot->radius, NS, robot->sphere_link, robot->sphere_center,
+        robot->sphere_radius, scene->n, scene->type, scene->pose, scene->dims, points, d, sctab,
+        out->point_verdict, out->margin, elem, rec32, queue, nq);
   }
   if (n_cells > 0 && out->cell_verdict) {
     MfProfScope ps(ctx, MF_PH_CERT_CELLS, st, 1, n_cells);
