@@ -58,9 +58,8 @@ def f32_term_ops(d):
 # capture (dram__bytes_read.sum + dram__bytes_write.sum of k_roots_prep,
 # k_roots_f64 (warp and redo launches), k_roots_x, k_roots_terms and
 # k_roots_finish on the lambda = 0.15 case of the d=5 workload, divided by
-# its 880,448 edges: 1230.5 MB); None once a kernel has changed since the
-# capture
-ROOTS_DRAM_BYTES_PER_EDGE = 1397.6
+# its 880,448 edges); None once a kernel has changed since the capture
+ROOTS_DRAM_BYTES_PER_EDGE = None
 
 
 def make_workload(cfg: str, rank: int, lam=None):
@@ -130,7 +129,7 @@ def measured_peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
-def roofline(stats, w, rates, E, ms_proof, n_proofs):
+def roofline(stats, w, rates, E, ms_proof, n_proofs, root_traffic=True):
     """Roofline of the dominant phase against the measured peaks: the FP64
     pipe (mf_probe_rates FP64 FMA probe) for the FP64 vertex evaluation and
     certification, the FP32 pipe (FP32 FMA probe, one operation per
@@ -196,8 +195,9 @@ def roofline(stats, w, rates, E, ms_proof, n_proofs):
         ach = ops / (ms_per_launch * 1e-3) / 1e12
         # DRAM bytes per edge from the ncu capture of the root kernels
         # (profiles/), scaled by the edges one launch processes
+        # (taken on the FP64 path: none for the other precision)
         traffic = ROOTS_DRAM_BYTES_PER_EDGE * s["units"] / max(s["launches"], 1) \
-            if ROOTS_DRAM_BYTES_PER_EDGE else None
+            if ROOTS_DRAM_BYTES_PER_EDGE and root_traffic else None
         return dict(base, kernel="roots phase: k_roots_prep, k_roots_f64 (warp screen and FP32 "
                     "Halley steps), k_roots_x, k_roots_terms (double-float sums), k_roots_finish",
                     bound="alu", achieved=ach, peak=f32_peak, unit="T FP32 ops/s",
@@ -339,13 +339,18 @@ def served_lines(ctx, n_requests, rate_hz, seed=1005):
     return out
 
 
-def _proof_ms(ctx, w, reps=2):
-    """Device-timed ms per proof of workload w (after one untimed proof)."""
+def _proof_ms(ctx, w, reps=2, stats=None):
+    """Device-timed ms per proof of workload w (after one untimed proof);
+    with a dict in stats, the library's per-phase counters of the timed
+    proofs are put there (profiling on, as in the main line)."""
     import torch
+    from paper_2406_04795_gb300 import mf
     from paper_2406_04795_gb300.pipeline import Proof
     p = Proof(ctx, w)
     p.step()
     torch.cuda.synchronize()
+    if stats is not None:
+        mf.mf_ctx_set_profiling(ctx.h, True)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -353,7 +358,25 @@ def _proof_ms(ctx, w, reps=2):
         r, v, m, cv = p.step()
     e1.record(stream)
     torch.cuda.synchronize()
+    if stats is not None:
+        stats.update(mf.mf_ctx_get_stats(ctx.h))
+        mf.mf_ctx_set_profiling(ctx.h, False)
     return e0.elapsed_time(e1) / reps, p, r
+
+
+def eval_tc_roofline(stats, rates):
+    """The tensor-core evaluation of a mixed proof against the MUFU ex2
+    roofline: every RBF term (vertex x support vector) takes one ex2 after
+    its distance comes out of the BF16 MMA."""
+    s = stats["eval"]
+    ex2_peak = rates["ex2_per_s"] / 1e12
+    ms = s["ms"] / max(s["launches"], 1)
+    ex = s["terms_weak"] / max(s["launches"], 1)
+    ach = ex / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+    return {"kernel": "k_eval_tc (+ FP64 recheck)", "bound": "alu", "achieved": ach,
+            "peak": ex2_peak, "unit": "T ex2/s", "frac": ach / ex2_peak,
+            "peak_source": "measured: mf_probe_rates ex2.approx probe",
+            "phase_ms": s["ms"], "terms": s["terms_weak"]}
 
 
 def config_lines(ctx, d6_lam=0.15):
@@ -652,11 +675,16 @@ def run_gb300(args):
             # the tensor cores, FP64 recheck, roots to 1e-6)
             wm = make_workload(args.config, rank, args.lam)
             wm.precision = "mixed" if w.precision == "fp64" else "fp64"
-            msm, pm, rm = _proof_ms(ctx, wm)
+            st_m = {}
+            msm, pm, rm = _proof_ms(ctx, wm, stats=st_m)
             line["other_precision"] = {"precision": wm.precision, "ms_per_proof": msm,
                                        "value": rm["n_edges"] / (msm * 1e-3),
                                        "edges_per_proof": rm["n_edges"],
-                                       "rechecked_vertices": rm["n_recheck"]}
+                                       "rechecked_vertices": rm["n_recheck"],
+                                       "roofline": roofline(st_m, wm, rates, rm["n_edges"], msm, 2,
+                                                            root_traffic=False)}
+            if wm.precision == "mixed":
+                line["other_precision"]["eval_roofline"] = eval_tc_roofline(st_m, rates)
             del pm, rm
             # the server gets a context of its own: the proofs' resident tables
             # and outputs are released first, so that its arena can hold many

@@ -1220,13 +1220,11 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
     dir32[k] = k < d ? __shfl_sync(FULL, d32o, k) : 0.f;
     dd32 = fmaf(dir32[k], dir32[k], dd32);
   }
-  // 1. segment screen.  Every segment point lies within |dir|/2 of the
-  //    midpoint, so a vector farther than r_s + |dir|/2 from it (with a
-  //    rounding margin) cannot pass; only the others get the exact
-  //    point-to-segment test.
+  // 1. segment screen: with u = x1 - s (hi/lo differences), A = |u|^2 and
+  //    Bp = u . dir (the cached terms), the squared distance from s to the
+  //    segment is A + t (2 Bp + t |dir|^2) at t = clamp(-Bp / |dir|^2, 0, 1).
   int ns = 0, nm = 0, nw = 0;
   const float inv_dd = 1.f / dd32;
-  const float pre = (sqrtf(R.screen_r2) + 0.5f * sqrtf(dd32)) * 1.0001f + 1e-5f, pre2 = pre * pre;
   const float shift64 = 0.5f - (fast ? ROOT_TAU_SHIFT_FAST : ROOT_TAU_SHIFT);
   // one round: lane tests vector j (gathered row for a group list, or the
   // coalesced coordinate arrays) and the survivors are compacted
@@ -1234,53 +1232,32 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
     bool keep = false, strong = false, strong64 = false;
     float cA = 0.f, cB = 0.f, al = 0.f, s32 = 0.f;
     if (valid) {
-      float p[D], sl[D], pd = 0.f;
+      float c[2 * D];
       if (gathered) {
-        float c[2 * D];
         sv_row<D>(R, j, c, al, s32);
-#pragma unroll
-        for (int k = 0; k < D; k++) {
-          p[k] = k < d ? c[2 * k] - x1hi[k] : 0.f;
-          sl[k] = c[2 * k + 1];
-        }
       } else {
 #pragma unroll
-        for (int k = 0; k < D; k++) p[k] = k < d ? (R.sv32[(int64_t)k * R.n + j] - x1hi[k]) : 0.f;
+        for (int k = 0; k < D; k++) {
+          c[2 * k] = k < d ? R.sv32[(int64_t)k * R.n + j] : 0.f;
+          c[2 * k + 1] = k < d ? R.svlo32[(int64_t)k * R.n + j] : 0.f;
+        }
+        al = R.alpha32[j];
+        s32 = R.strong32[j];
       }
-      float dm2 = 0.f;
+      // term_ab's operations
 #pragma unroll
       for (int k = 0; k < D; k++) {
-        const float u = fmaf(-0.5f, dir32[k], p[k]);
-        dm2 = fmaf(u, u, dm2);
-      }
-      if (dm2 <= pre2) {
-#pragma unroll
-        for (int k = 0; k < D; k++) pd = fmaf(p[k], dir32[k], pd);
-        const float tt = fminf(fmaxf(pd * inv_dd, 0.f), 1.f);
-        float r2 = 0.f;
-#pragma unroll
-        for (int k = 0; k < D; k++) {
-          const float q = fmaf(-tt, dir32[k], p[k]);
-          r2 = fmaf(q, q, r2);
-        }
-        keep = r2 <= R.screen_r2;
-        if (!gathered) s32 = R.strong32[j];
-        strong = g32 * r2 < s32 + 0.5f;
-        strong64 = g32 * r2 < s32 + shift64;
-        if (keep) {
-          // the cached A and Bp (term_ab's operations: x1hi - s_hi is -p
-          // exactly)
-#pragma unroll
-          for (int k = 0; k < D; k++) {
-            if (k < d) {
-              const float lo = gathered ? sl[k] : R.svlo32[(int64_t)k * R.n + j];
-              const float u = -p[k] + (x1lo[k] - lo);
-              cA = fmaf(u, u, cA);
-              cB = fmaf(u, dir32[k], cB);
-            }
-          }
+        if (k < d) {
+          const float u = (x1hi[k] - c[2 * k]) + (x1lo[k] - c[2 * k + 1]);
+          cA = fmaf(u, u, cA);
+          cB = fmaf(u, dir32[k], cB);
         }
       }
+      const float tt = fminf(fmaxf(-cB * inv_dd, 0.f), 1.f);
+      const float r2 = fmaf(tt, fmaf(tt, dd32, 2.f * cB), cA);
+      keep = r2 <= R.screen_r2;
+      strong = g32 * r2 < s32 + 0.5f;
+      strong64 = g32 * r2 < s32 + shift64;
     }
     // strong64 entries fill near from the front, weak ones from the back,
     // mid ones (strong, not strong64) fill midl
@@ -1294,13 +1271,13 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
       const int c = strong64 ? cs : HC_STRONG + cm;
       hc[c] = cA;
       hc[HC_ALL + c] = cB;
-      hc[2 * HC_ALL + c] = gathered ? al : R.alpha32[j];
+      hc[2 * HC_ALL + c] = al;
     }
     if (keep && !strong && cw < HC_WEAK) {
       const int c = HC_STRONG + HC_MID + cw;
       hc[c] = cA;
       hc[HC_ALL + c] = cB;
-      hc[2 * HC_ALL + c] = gathered ? al : R.alpha32[j];
+      hc[2 * HC_ALL + c] = al;
     }
     if (keep && !strong && ns + cw < NEAR_CAP) near[NEAR_CAP - 1 - cw] = j;
     ns += __popc(ms);
@@ -1344,7 +1321,11 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
   } else {
     // whole blocks of 32 vectors whose box lies beyond the prefilter ball
     // (looser by 1e-3 for the rounding of the two paths) are skipped
-    const float box2 = pre2 * 1.001f + 1e-5f;
+    // (every segment point lies within |dir|/2 of the midpoint, so a vector
+    // farther than r_s + |dir|/2 from it, with a rounding margin, cannot
+    // pass)
+    const float pre = (sqrtf(R.screen_r2) + 0.5f * sqrtf(dd32)) * 1.0001f + 1e-5f;
+    const float box2 = pre * pre * 1.001f + 1e-5f;
     for (int bb0 = 0; bb0 < R.nblk; bb0 += 32) {
       bool bkeep = false;
       if (bb0 + lane < R.nblk) {
