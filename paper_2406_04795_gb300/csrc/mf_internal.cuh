@@ -59,6 +59,7 @@ struct MfCounters {
   unsigned long long n_defer;      // root steps handed to the lane-per-edge FP64 kernel
   unsigned long long n_defer_list; // their strong-term list entries
   unsigned long long n_redo;       // deferred steps not accepted (solved again in full)
+  unsigned long long n_items;      // expand items of the current chunk given a vertex slot
   unsigned int err_table_full;     // a hash probe ran past the table
   unsigned int err_overflow;       // a list ran past its capacity
   unsigned int err_missing;        // a vertex expected in the table was absent
@@ -123,6 +124,14 @@ struct MfTraceBufs {
   double *defer_part;       // [defer_list_cap / 8] FP64 sum of each chunk
   uint32_t *defer_chunk;    // [defer_list_cap / 8] record of each chunk (~0: none)
   uint64_t defer_cap, defer_list_cap;
+  // vertex slots of one chunk's expand items: k_expand_vertices records the
+  // slot of item j of warp w at item_slot[warp_base[w] + j] (~0u: outside
+  // the domain), k_expand_edges reads it instead of looking the vertex up
+  // (warp_base[w] = ~0: the warp's items did not fit, look them up); absent
+  // when null
+  uint32_t *item_slot;
+  unsigned long long *warp_base;
+  uint64_t item_cap;
 };
 #define MF_NO_LIST 0xFFFFFFFFu
 #define MF_EP_ROW(d) (3 * (d) + 6)
@@ -477,20 +486,23 @@ __device__ __forceinline__ unsigned long long mf_warp_alloc(unsigned long long *
 // kernels share them).
 // ------------------------------------------------------------------------
 // Inserts an in-domain vertex into the vertex table; first inserter appends it.
-__device__ __forceinline__ void mf_visit_vertex(const MfFrame &F, const MfTraceBufs &B, const int32_t *w) {
+// Inserts vertex w if new (appending it to the vertex list); returns its
+// table slot (~0: the table is full).
+__device__ __forceinline__ uint64_t mf_visit_vertex(const MfFrame &F, const MfTraceBufs &B, const int32_t *w) {
   const unsigned long long key = mf_vertex_key(F, w);
   bool won;
   const uint64_t slot = mf_table_insert<2>(B.vtab_key, B.vtab_mask, key, &won);
   if (slot == ~0ull) atomicOr(&B.cnt->err_table_full, 1u);
   const bool take = slot != ~0ull && won;
   const unsigned long long idx = mf_warp_alloc(&B.cnt->n_vertices, take);
-  if (!take) return;
-  if (idx >= B.max_vertices) { atomicOr(&B.cnt->err_overflow, 1u); return; }
+  if (!take) return slot;
+  if (idx >= B.max_vertices) { atomicOr(&B.cnt->err_overflow, 1u); return slot; }
 #pragma unroll
   for (int k = 0; k < MF_MAXD; k++)
     if (k < F.d) B.vert_y[idx * F.d + k] = w[k];
   B.vert_slot[idx] = (uint32_t)slot;
   if (B.vtab_idx) B.vtab_idx[slot] = (uint32_t)idx;
+  return slot;
 }
 
 __device__ __forceinline__ double mf_lookup_f(const MfFrame &F, const MfTraceBufs &B, const int32_t *w) {
@@ -619,7 +631,8 @@ enum {
   MF_SLOT_SUBDIV = 14,
   MF_SLOT_SORT = 15,
   MF_SLOT_DEFER = 16,
-  MF_NUM_SLOTS = 17
+  MF_SLOT_ITEMS = 17,
+  MF_NUM_SLOTS = 18
 };
 
 // ---------------------------------------------------------------------------

@@ -166,9 +166,10 @@ __device__ __forceinline__ uint32_t expand_item_decode(uint32_t S, int d, uint32
 }
 
 // Visits the new vertex of one item; returns 1 if it lies outside the box.
+// *slot: its table slot (~0u outside the box or with a full table).
 __device__ __forceinline__ unsigned expand_vertices_item(const MfFrame &F, const MfTraceBufs &B,
                                                          uint64_t e, uint32_t S, int kind,
-                                                         uint32_t M) {
+                                                         uint32_t M, uint32_t *slot = nullptr) {
   const int d = F.d;
   int32_t w[MF_MAXD];
   load_y(B.edge_y + e * d, d, w);
@@ -176,17 +177,23 @@ __device__ __forceinline__ unsigned expand_vertices_item(const MfFrame &F, const
   else if (kind == 1) mf_add_mask(d, w, S | M, 1);
   else mf_add_mask(d, w, M, -1);
   if (vertex_in(F, w)) {
-    mf_visit_vertex(F, B, w);
+    const uint64_t sl = mf_visit_vertex(F, B, w);
+    if (slot) *slot = sl == ~0ull ? ~0u : (uint32_t)sl;
     return 0;
   }
+  if (slot) *slot = ~0u;
   return 1;
 }
 
 // Under the sign rule s = [f >= 0] a crossing triangle has exactly two
 // crossing edges (Sec. IV-A): the parent and the one joining the new vertex w
 // to the parent end whose sign differs from s(w).
+// slot: the new vertex's table slot recorded by k_expand_vertices (~0u:
+// outside the box), or MF_SLOT_UNKNOWN to look it up.
+#define MF_SLOT_UNKNOWN 0xfffffffeu
 __device__ __forceinline__ void expand_edges_item(const MfFrame &F, const MfTraceBufs &B,
-                                                  uint64_t e, uint32_t S, int kind, uint32_t M) {
+                                                  uint64_t e, uint32_t S, int kind, uint32_t M,
+                                                  uint32_t slot = MF_SLOT_UNKNOWN) {
   const int d = F.d;
   int32_t y[MF_MAXD], w[MF_MAXD];
   load_y(B.edge_y + e * d, d, y);
@@ -194,9 +201,15 @@ __device__ __forceinline__ void expand_edges_item(const MfFrame &F, const MfTrac
   if (kind == 0) mf_add_mask(d, w, M, 1);
   else if (kind == 1) mf_add_mask(d, w, S | M, 1);
   else mf_add_mask(d, w, M, -1);
-  if (!vertex_in(F, w)) return;
+  double fw;
+  if (slot == MF_SLOT_UNKNOWN) {
+    if (!vertex_in(F, w)) return;
+    fw = mf_lookup_f(F, B, w);
+  } else {
+    if (slot == ~0u) return;
+    fw = mf_vtab_f(B, slot);
+  }
   const double f0 = B.edge_f[2 * e], f1 = B.edge_f[2 * e + 1];
-  const double fw = mf_lookup_f(F, B, w);
   const bool cross0 = (fw >= 0.0) != (f0 >= 0.0);
   if (kind == 0) {
     if (cross0) mf_emit_edge(F, B, y, M, f0, fw);
@@ -258,6 +271,21 @@ __device__ __forceinline__ void expand_warp(const MfFrame &F, const MfTraceBufs 
   }
   s_S[wi][lane] = S;
   const uint32_t total = expand_warp_scan(c, s_end[wi]);
+  // the warp's items in the chunk's slot record (see MfTraceBufs.item_slot)
+  const uint64_t wg = blockIdx.x * (uint64_t)EXPAND_WARPS + wi;
+  unsigned long long ib = ~0ull;
+  if (B.item_slot) {
+    if (EDGES) {
+      ib = B.warp_base[wg];
+    } else {
+      if (lane == 0) {
+        ib = atomicAdd(&B.cnt->n_items, (unsigned long long)total);
+        if (ib + total > B.item_cap) ib = ~0ull;
+        B.warp_base[wg] = ib;
+      }
+      ib = __shfl_sync(0xffffffffu, ib, 0);
+    }
+  }
   unsigned nb = 0;
   for (uint32_t j = lane; j < total; j += 32) {
     uint32_t r;
@@ -265,8 +293,14 @@ __device__ __forceinline__ void expand_warp(const MfFrame &F, const MfTraceBufs 
     const uint32_t So = s_S[wi][o];
     int kind;
     const uint32_t M = expand_item_decode(So, d, r, &kind);
-    if (EDGES) expand_edges_item(F, B, e0 + first + o, So, kind, M);
-    else nb += expand_vertices_item(F, B, e0 + first + o, So, kind, M);
+    if (EDGES) {
+      expand_edges_item(F, B, e0 + first + o, So, kind, M,
+                        ib != ~0ull ? B.item_slot[ib + j] : MF_SLOT_UNKNOWN);
+    } else {
+      uint32_t sl;
+      nb += expand_vertices_item(F, B, e0 + first + o, So, kind, M, &sl);
+      if (ib != ~0ull) B.item_slot[ib + j] = sl;
+    }
   }
   if (!EDGES) {
     nb = __reduce_add_sync(0xffffffffu, nb);
@@ -1400,6 +1434,23 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
   if (B.vlist) B.list_r2 = mf_list_r2(F, R);
   uint64_t cap = opts->batch_cap_edges > 0 ? (uint64_t)opts->batch_cap_edges : (1ull << 24);
   if (ctx->tune.frontier_chunk > 0 && ctx->tune.frontier_chunk < cap) cap = ctx->tune.frontier_chunk;
+  // the expand items' vertex slots for one chunk (2^d - 2 items per edge at
+  // most, up to 2^29 items), when the budget allows
+  {
+    const uint64_t ce = std::min<uint64_t>(cap, ME);
+    const uint64_t ic = std::min<uint64_t>(ce * ((1ull << d) - 2), 1ull << 29);
+    const uint64_t nw = (ce + 255) / 256 * EXPAND_WARPS + EXPAND_WARPS;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    std::string keep = ctx->err;
+    char *q = (char *)mf_ctx_buffer(ctx, MF_SLOT_ITEMS, al(ic * 4) + al(nw * 8));
+    if (q) {
+      B.item_slot = (uint32_t *)q;
+      B.warp_base = (unsigned long long *)(q + al(ic * 4));
+      B.item_cap = ic;
+    } else {
+      ctx->err = keep;
+    }
+  }
   const double band = opts->recheck_band > 0 ? opts->recheck_band : 1e-3;
   const double tol = opts->root_tol > 0 ? opts->root_tol : 1e-12;
   const int sms = ctx->sms;
@@ -1435,6 +1486,8 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
       const unsigned g = (unsigned)((n + EXPAND_WARPS * 32 - 1) / (EXPAND_WARPS * 32));
       {
         MfProfScope ps(ctx, MF_PH_EXPAND_V, st, 1, (int64_t)n);
+        if (B.item_slot)
+          cudaMemsetAsync(&B.cnt->n_items, 0, sizeof(unsigned long long), st);
         k_expand_vertices<<<g, EXPAND_WARPS * 32, 0, st>>>(F, B, a, n);
       }
       {
