@@ -124,13 +124,16 @@ struct MfTraceBufs {
   double *defer_part;       // [defer_list_cap / 8] FP64 sum of each chunk
   uint32_t *defer_chunk;    // [defer_list_cap / 8] record of each chunk (~0: none)
   uint64_t defer_cap, defer_list_cap;
-  // vertex slots of one chunk's expand items: k_expand_vertices records the
-  // slot of item j of warp w at item_slot[warp_base[w] + j] (~0u: outside
-  // the domain), k_expand_edges reads it instead of looking the vertex up
-  // (warp_base[w] = ~0: the warp's items did not fit, look them up); absent
-  // when null
+  // vertex slots of the expand items of the whole search: k_expand_vertices
+  // records the slot of item j of warp w of a chunk at
+  // item_slot[warp_base[w] + j] (~0u: outside the domain) and the first item
+  // of each edge in edge_item_off (~0: not recorded); k_expand_edges and the
+  // cell enumeration's link tables read them instead of looking the
+  // vertices up (warp_base[w] = ~0: the warp's items did not fit, look them
+  // up); absent when null
   uint32_t *item_slot;
   unsigned long long *warp_base;
+  unsigned long long *edge_item_off;
   uint64_t item_cap;
 };
 #define MF_NO_LIST 0xFFFFFFFFu

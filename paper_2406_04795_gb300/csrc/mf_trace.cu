@@ -284,6 +284,10 @@ __device__ __forceinline__ void expand_warp(const MfFrame &F, const MfTraceBufs 
         B.warp_base[wg] = ib;
       }
       ib = __shfl_sync(0xffffffffu, ib, 0);
+      // each lane's edge: the first of its items
+      if (B.edge_item_off && first + lane < n)
+        B.edge_item_off[e0 + first + lane] =
+            ib == ~0ull ? ~0ull : ib + (lane ? s_end[wi][lane - 1] : 0u);
     }
   }
   unsigned nb = 0;
@@ -386,27 +390,52 @@ __device__ __forceinline__ void cells_enum_edge(const MfFrame &F, const MfTraceB
   const int n1 = __popc(S), n2 = d + 1 - n1;
   // the link table, one vertex lookup per entry
   const int na = 1 << n1, nb = 1 << (n2 - 1);
+  // the edge's expand items and end values: the link table's vertices are
+  // the edge's ends (a[0] = c[0] = y, a[na - 1] = b[0] = y + e(S)) and its
+  // coface items (a[q]: item q - 1; b[r], c[r]: items na - 2 + 2 (r - 1)
+  // and the one after), whose vertex slots the expansion recorded
+  const unsigned long long ioff = B.edge_item_off ? B.edge_item_off[e] : ~0ull;
+  const uint8_t c_y = B.edge_f[2 * e] >= 0.0 ? 3 : 1, c_ys = B.edge_f[2 * e + 1] >= 0.0 ? 3 : 1;
   __syncwarp();  // the previous edge's cofaces have read the table
   for (int q = lane; q < na + 2 * nb; q += 32) {
-    int32_t w[MF_MAXD];
-    load_y(y, d, w);
     uint8_t *dst;
+    uint32_t M;
+    int sgn = 1;
+    long long ri;  // the item, -1: an end of the edge
+    uint8_t code = 0;
     if (q < na) {
-      mf_add_mask(d, w, deposit_bits((uint32_t)q, S), 1);
+      M = deposit_bits((uint32_t)q, S);
       dst = &L.a[q];
+      ri = (q == 0 || q == na - 1) ? -1 : q - 1;
+      if (q == 0) code = c_y;
+      else if (q == na - 1) code = c_ys;
     } else if (q < na + nb) {
       const uint32_t r = (uint32_t)(q - na);
-      mf_add_mask(d, w, S | deposit_bits(r, T), 1);
+      M = S | deposit_bits(r, T);
       dst = &L.b[r];
+      ri = r == 0 ? -1 : (long long)(na - 2) + 2 * ((long long)r - 1);
+      if (r == 0) code = c_ys;
     } else {
       const uint32_t r = (uint32_t)(q - na - nb);
-      mf_add_mask(d, w, deposit_bits(r, T), -1);
+      M = deposit_bits(r, T);
+      sgn = -1;
       dst = &L.c[r];
+      ri = r == 0 ? -1 : (long long)(na - 2) + 2 * ((long long)r - 1) + 1;
+      if (r == 0) code = c_y;
     }
-    uint8_t code = 0;
-    if (vertex_in(F, w)) {
-      const uint64_t slot = mf_table_find<2>(B.vtab_key, B.vtab_mask, mf_vertex_key(F, w));
-      if (slot != ~0ull) code = mf_vtab_f(B, slot) >= 0.0 ? 3 : 1;
+    if (ri >= 0) {
+      if (ioff != ~0ull) {
+        const uint32_t slot = B.item_slot[ioff + (unsigned long long)ri];
+        code = slot == ~0u ? 0 : (mf_vtab_f(B, slot) >= 0.0 ? 3 : 1);
+      } else {
+        int32_t w[MF_MAXD];
+        load_y(y, d, w);
+        mf_add_mask(d, w, M, sgn);
+        if (vertex_in(F, w)) {
+          const uint64_t slot = mf_table_find<2>(B.vtab_key, B.vtab_mask, mf_vertex_key(F, w));
+          if (slot != ~0ull) code = mf_vtab_f(B, slot) >= 0.0 ? 3 : 1;
+        }
+      }
     }
     *dst = code;
   }
@@ -1434,22 +1463,26 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
   if (B.vlist) B.list_r2 = mf_list_r2(F, R);
   uint64_t cap = opts->batch_cap_edges > 0 ? (uint64_t)opts->batch_cap_edges : (1ull << 24);
   if (ctx->tune.frontier_chunk > 0 && ctx->tune.frontier_chunk < cap) cap = ctx->tune.frontier_chunk;
-  // the expand items' vertex slots for one chunk (2^d - 2 items per edge at
-  // most, up to 2^29 items), when the budget allows
+  // the expand items' vertex slots of the whole search: up to (2^d - 2)
+  // items per edge (at most 2^31, halved while the budget refuses), the
+  // first item of each edge and the bases of one chunk's warps
   {
     const uint64_t ce = std::min<uint64_t>(cap, ME);
-    const uint64_t ic = std::min<uint64_t>(ce * ((1ull << d) - 2), 1ull << 29);
     const uint64_t nw = (ce + 255) / 256 * EXPAND_WARPS + EXPAND_WARPS;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     std::string keep = ctx->err;
-    char *q = (char *)mf_ctx_buffer(ctx, MF_SLOT_ITEMS, al(ic * 4) + al(nw * 8));
-    if (q) {
-      B.item_slot = (uint32_t *)q;
-      B.warp_base = (unsigned long long *)(q + al(ic * 4));
-      B.item_cap = ic;
-    } else {
-      ctx->err = keep;
+    for (uint64_t ic = std::min<uint64_t>(ME * ((1ull << d) - 2), 1ull << 31); ic >= (1ull << 20);
+         ic >>= 1) {
+      char *q = (char *)mf_ctx_buffer(ctx, MF_SLOT_ITEMS, al(ic * 4) + al(nw * 8) + al(ME * 8));
+      if (q) {
+        B.item_slot = (uint32_t *)q;
+        B.warp_base = (unsigned long long *)(q + al(ic * 4));
+        B.edge_item_off = (unsigned long long *)(q + al(ic * 4) + al(nw * 8));
+        B.item_cap = ic;
+        break;
+      }
     }
+    ctx->err = keep;
   }
   const double band = opts->recheck_band > 0 ? opts->recheck_band : 1e-3;
   const double tol = opts->root_tol > 0 ? opts->root_tol : 1e-12;
@@ -1486,8 +1519,6 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
       const unsigned g = (unsigned)((n + EXPAND_WARPS * 32 - 1) / (EXPAND_WARPS * 32));
       {
         MfProfScope ps(ctx, MF_PH_EXPAND_V, st, 1, (int64_t)n);
-        if (B.item_slot)
-          cudaMemsetAsync(&B.cnt->n_items, 0, sizeof(unsigned long long), st);
         k_expand_vertices<<<g, EXPAND_WARPS * 32, 0, st>>>(F, B, a, n);
       }
       {
