@@ -1100,11 +1100,14 @@ template <int NV4>
 __global__ void __launch_bounds__(256) k_certify_cells_whole32(
     const int64_t *off, const int64_t *idx, int64_t n_cells, const float *rec32, const double *pts,
     int d, const double *margin, const int16_t *element, const float *L32, const double *L, int NE,
-    int64_t n_points, uint8_t *whole, unsigned *bad) {
+    int64_t n_points, uint8_t *whole, unsigned *bad, const uint8_t *verdict,
+    uint8_t *cell_verdict) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= n_cells) return;
   const int64_t j0 = off[c], j1 = off[c + 1];
   const int64_t nr = j1 - j0;
+  // with cell_verdict: also the AND of the points' verdicts (k_certify_cells)
+  uint32_t all = 1;
   const float4 *R4 = reinterpret_cast<const float4 *>(rec32);
   float lo[MF_MAXD], hi[MF_MAXD];
 #pragma unroll
@@ -1119,7 +1122,11 @@ __global__ void __launch_bounds__(256) k_certify_cells_whole32(
   for (int r = 0; r < CERT_ROW_CACHE; r++) {
     const int64_t i = r < nr ? idx[j0 + r] : -1;
     const bool in = i >= 0 && i < n_points;
-    if (r < nr && !in) atomicOr(bad, 1u);
+    if (r < nr && !in) {
+      atomicOr(bad, 1u);
+      all = 0;
+    }
+    if (cell_verdict && in) all &= verdict[i];
 #pragma unroll
     for (int q = 0; q < NV4; q++)
       cache[r][q] = in ? __ldg(R4 + i * NV4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1132,13 +1139,16 @@ __global__ void __launch_bounds__(256) k_certify_cells_whole32(
     const int64_t i = idx[j];
     if (i < 0 || i >= n_points) {
       atomicOr(bad, 1u);
+      all = 0;
       continue;
     }
+    if (cell_verdict) all &= verdict[i];
     float4 v[NV4];
 #pragma unroll
     for (int q = 0; q < NV4; q++) v[q] = __ldg(R4 + i * NV4 + q);
     cert_rec_extend<NV4>(v, d, lo, hi, P);
   }
+  if (cell_verdict) cell_verdict[c] = (uint8_t)all;
   bool yes = false, undecided = false;
 #pragma unroll
   for (int r = 0; r < CERT_ROW_CACHE; r++)
@@ -1301,7 +1311,10 @@ extern "C" int mf_certify_ex(mf_ctx *ctx, const mf_robot *robot, const mf_scene 
         robot->sphere_radius, scene->n, scene->type, scene->pose, scene->dims, points, d, sctab,
         out->point_verdict, out->margin, elem, rec32, queue, nq);
   }
-  if (n_cells > 0 && out->cell_verdict) {
+  // the FP32 whole-cell pass also forms the cell verdicts (one read of
+  // each row)
+  const bool fused = fast && cert_rec_stride(d) / 4 <= 3;
+  if (n_cells > 0 && out->cell_verdict && !fused) {
     MfProfScope ps(ctx, MF_PH_CERT_CELLS, st, 1, n_cells);
     k_certify_cells<<<(unsigned)((n_cells + 255) / 256), 256, 0, st>>>(
         cell_off, cell_idx, n_cells, out->point_verdict, n_points, out->cell_verdict, bad);
@@ -1313,15 +1326,18 @@ extern "C" int mf_certify_ex(mf_ctx *ctx, const mf_robot *robot, const mf_scene 
     if (fast && nv4 == 1)
       k_certify_cells_whole32<1><<<gc, 256, 0, st>>>(cell_off, cell_idx, n_cells, rec32, points, d,
                                                       out->margin, elem, dL32, dL, NE, n_points,
-                                                      out->cell_whole, bad);
+                                                      out->cell_whole, bad, out->point_verdict,
+                                                      out->cell_verdict);
     else if (fast && nv4 == 2)
       k_certify_cells_whole32<2><<<gc, 256, 0, st>>>(cell_off, cell_idx, n_cells, rec32, points, d,
                                                       out->margin, elem, dL32, dL, NE, n_points,
-                                                      out->cell_whole, bad);
+                                                      out->cell_whole, bad, out->point_verdict,
+                                                      out->cell_verdict);
     else if (fast)
       k_certify_cells_whole32<3><<<gc, 256, 0, st>>>(cell_off, cell_idx, n_cells, rec32, points, d,
                                                       out->margin, elem, dL32, dL, NE, n_points,
-                                                      out->cell_whole, bad);
+                                                      out->cell_whole, bad, out->point_verdict,
+                                                      out->cell_verdict);
     else
       k_certify_cells_whole<<<(unsigned)((n_cells + 255) / 256), 256, 0, st>>>(
           cell_off, cell_idx, n_cells, points, d, out->margin, elem, dL, NE, n_points,
