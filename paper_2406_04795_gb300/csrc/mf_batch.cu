@@ -192,7 +192,7 @@ int mf_setup_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_trace_opts *o, char 
     B.vlist_n = (uint32_t *)(base + l->vlist_n);
     B.vlist = (int32_t *)(base + l->vlist);
     B.vlist_cap = l->VL;
-    B.list_r2 = mf_list_r2(S->F, S->R);
+    B.list_r2 = mf_list_r2(S->F, S->R, o->precision != MF_FP64 && !(o->flags & MF_ROOTS_FP64_EXACT));
   } else {  // no per-vertex lists: the root screen scans the blocks
     B.vtab_idx = nullptr;
     B.vlist = nullptr;

@@ -281,6 +281,14 @@ int mf_prepare_rbf_at(mf_ctx *ctx, const mf_rbf *rbf, char *base, MfRbfDev *out,
   out->drop_bound32 = (float)out->drop_bound;
   out->weak_rel32 = (float)out->weak_rel;
   out->smax = h.max_abs_s;
+  // the mixed paths' root screen: sum|alpha| e^-T <= 1e-12
+  {
+    double Tf = std::log(sa / 1e-12);
+    if (Tf < 30.0) Tf = 30.0;
+    if (Tf > T) Tf = T;
+    out->screen_r2_fast = (float)((Tf + 0.5) / rbf->gamma);
+    out->drop_bound32_fast = (float)(sa * std::exp(-Tf));
+  }
   return MF_OK;
 }
 
@@ -1071,10 +1079,10 @@ __device__ __forceinline__ void root_fp32_part(const MfRbfDev &R, const int *nea
 }
 
 // Relative error bound of a cached weak term on an edge with |dir|^2 = dd32
-// (every kept vector lies within the screen radius of the segment; 1.1
-// covers this bound's own FP32 rounding).
-__device__ __forceinline__ float root_rel_cached(const MfRbfDev &R, int d, float dd32) {
-  const float q = sqrtf(R.screen_r2) + 2.f * sqrtf(dd32);
+// (every kept vector lies within the screen radius sqrt(rs2) of the segment;
+// 1.1 covers this bound's own FP32 rounding).
+__device__ __forceinline__ float root_rel_cached(const MfRbfDev &R, int d, float dd32, float rs2) {
+  const float q = sqrtf(rs2) + 2.f * sqrtf(dd32);
   return 1.1f * ((float)d + 8.f) * 5.9604644775390625e-08f * (float)R.gamma * q * q +
          9.5367431640625e-07f + 2.f * 5.9604644775390625e-08f;
 }
@@ -1121,7 +1129,8 @@ __device__ __forceinline__ F64Acc root_eval64(const MfRbfDev &R, const int *near
 // (The check runs in FP32: the 1.01 factor covers its roundings.)
 __device__ __forceinline__ bool root_fp32_part_too_coarse(const MfRbfDev &R, float weak, float gp,
                                                           bool fast) {
-  const float lim = fmaxf(R.weak_limit32, (fast ? 0.99e-7f : 0.99e-10f) * fabsf(gp) - R.drop_bound32);
+  const float lim = fmaxf(R.weak_limit32, (fast ? 0.99e-7f : 0.99e-10f) * fabsf(gp) -
+                                              (fast ? R.drop_bound32_fast : R.drop_bound32));
   return weak * (1.01f * R.weak_rel32) > lim;
 }
 
@@ -1226,6 +1235,8 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
   int ns = 0, nm = 0, nw = 0;
   const float inv_dd = 1.f / dd32;
   const float shift64 = 0.5f - (fast ? ROOT_TAU_SHIFT_FAST : ROOT_TAU_SHIFT);
+  // the mixed paths (fast) drop at most 1e-12 instead of 1e-13
+  const float rs2 = fast ? R.screen_r2_fast : R.screen_r2;
   // one round: lane tests vector j (gathered row for a group list, or the
   // coalesced coordinate arrays) and the survivors are compacted
   auto screen_round = [&](bool valid, int j, bool gathered) {
@@ -1255,7 +1266,7 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
       }
       const float tt = fminf(fmaxf(-cB * inv_dd, 0.f), 1.f);
       const float r2 = fmaf(tt, fmaf(tt, dd32, 2.f * cB), cA);
-      keep = r2 <= R.screen_r2;
+      keep = r2 <= rs2;
       strong = g32 * r2 < s32 + 0.5f;
       strong64 = g32 * r2 < s32 + shift64;
     }
@@ -1324,7 +1335,7 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
     // (every segment point lies within |dir|/2 of the midpoint, so a vector
     // farther than r_s + |dir|/2 from it, with a rounding margin, cannot
     // pass)
-    const float pre = (sqrtf(R.screen_r2) + 0.5f * sqrtf(dd32)) * 1.0001f + 1e-5f;
+    const float pre = (sqrtf(rs2) + 0.5f * sqrtf(dd32)) * 1.0001f + 1e-5f;
     const float box2 = pre * pre * 1.001f + 1e-5f;
     for (int bb0 = 0; bb0 < R.nblk; bb0 += 32) {
       bool bkeep = false;
@@ -1423,7 +1434,7 @@ __device__ void root_edge(const MfFrame &F, const MfRbfDev &R, const MfTraceBufs
       const float weakc = mf_warp_sum_f(part.weakc);
       // the cached weak terms count with their own bound, as a multiple of
       // R.weak_rel's
-      const float kc = fmaxf(root_rel_cached(R, d, dd32) / R.weak_rel32, 1.f);
+      const float kc = fmaxf(root_rel_cached(R, d, dd32, rs2) / R.weak_rel32, 1.f);
       if (!root_fp32_part_too_coarse(R, fmaf(weakc, kc, weak), gpf, fast)) {
         const int nch = (ns + DEFER_CHUNK - 1) / DEFER_CHUNK;
         unsigned long long at = 0, lat = 0;

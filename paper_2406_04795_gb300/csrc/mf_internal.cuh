@@ -170,6 +170,9 @@ struct MfRbfDev {
   double weak_rel;     // relative error bound of one FP32 weak term
   float weak_limit32, drop_bound32, weak_rel32;  // FP32 copies for the FP32 checks
   float smax;          // max |s_ik| over all support-vector coordinates
+  // the mixed paths' root solve (|dt| <= 1e-6): its screen keeps the terms
+  // with r^2 <= screen_r2_fast, dropping at most drop_bound32_fast (1e-12)
+  float screen_r2_fast, drop_bound32_fast;
 };
 
 // ------------------------------------------------------------------------
@@ -569,13 +572,15 @@ int mf_prepare_rbf_at(mf_ctx *ctx, const mf_rbf *rbf, char *base, MfRbfDev *out,
 // any point of an edge leaving the vertex.  The longest edge is lam |L e(M)|
 // with |L e(M)|^2 = k (1 - 2ck + c^2 k d) for |M| = k; the margins cover the
 // FP32 distances of both screens.
-static inline float mf_list_r2(const MfFrame &F, const MfRbfDev &R) {
+// fast: for the mixed paths' root solve (screen_r2_fast).
+static inline float mf_list_r2(const MfFrame &F, const MfRbfDev &R, bool fast = false) {
   double m2 = 0.0;
   for (int k = 1; k <= F.d; k++) {
     const double v = k * (1.0 - 2.0 * F.c * k + F.c * F.c * k * F.d);
     if (v > m2) m2 = v;
   }
-  const double rl = std::sqrt((double)R.screen_r2) * 1.0001 + F.lam * std::sqrt(m2) + 1e-4;
+  const double rs2 = fast ? (double)R.screen_r2_fast : (double)R.screen_r2;
+  const double rl = std::sqrt(rs2) * 1.0001 + F.lam * std::sqrt(m2) + 1e-4;
   return (float)(rl * rl);
 }
 // Trace host helpers (mf_trace.cu).

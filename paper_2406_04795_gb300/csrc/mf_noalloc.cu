@@ -278,6 +278,15 @@ extern "C" int mf_trace_noalloc(const mf_rbf *rbf, const mf_domain *dom, const m
   R.drop_bound32 = (float)R.drop_bound;
   R.weak_rel32 = (float)R.weak_rel;
   R.smax = hs.max_abs_s;
+  // the mixed paths' root screen: sum|alpha| e^-T <= 1e-12
+  {
+    double Tf = std::log(sa / 1e-12);
+    if (Tf < 30.0) Tf = 30.0;
+    if (Tf > T) Tf = T;
+    R.screen_r2_fast = (float)((Tf + 0.5) / rbf->gamma);
+    R.drop_bound32_fast = (float)(sa * std::exp(-Tf));
+  }
+
 
   // Everything that must start empty.
   cudaMemsetAsync(cnt, 0, sizeof(MfCounters), st);

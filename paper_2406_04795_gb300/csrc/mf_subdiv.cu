@@ -250,7 +250,7 @@ extern "C" int mf_subdiv_next(mf_ctx *ctx, mf_trace_out *out, int64_t *cells_lef
   MfTraceBufs B;
   int rc = mf_setup_buffers(ctx, d, S.ME, S.MV, 1, mixed, S.R.n, &B);
   if (rc) return rc;
-  if (B.vlist) B.list_r2 = mf_list_r2(F, S.R);
+  if (B.vlist) B.list_r2 = mf_list_r2(F, S.R, mixed && !(S.flags & MF_ROOTS_FP64_EXACT));
   B.max_cells = 0;
   cudaMemsetAsync(B.cnt, 0, sizeof(MfCounters), st);
   cudaMemsetAsync(B.etab_key, 0xFF, (B.etab_mask + 1) * 16, st);

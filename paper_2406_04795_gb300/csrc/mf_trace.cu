@@ -1460,7 +1460,9 @@ extern "C" int mf_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom,
   MfTraceBufs B;
   rc = setup_buffers(ctx, d, ME, MV, MC, mixed, (int)rbf->n_sv, &B);
   if (rc) return rc;
-  if (B.vlist) B.list_r2 = mf_list_r2(F, R);
+  // the root screen's lists: the mixed paths' radius when their roots are fast
+  if (B.vlist)
+    B.list_r2 = mf_list_r2(F, R, mixed && !(opts->flags & MF_ROOTS_FP64_EXACT));
   uint64_t cap = opts->batch_cap_edges > 0 ? (uint64_t)opts->batch_cap_edges : (1ull << 24);
   if (ctx->tune.frontier_chunk > 0 && ctx->tune.frontier_chunk < cap) cap = ctx->tune.frontier_chunk;
   // the expand items' vertex slots of the whole search: up to (2^d - 2)
