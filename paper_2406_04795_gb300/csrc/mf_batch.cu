@@ -34,6 +34,8 @@ struct TraceLayout {
   size_t rbf, dom, cnt, etab_key, vtab_key;
   size_t edge_y, edge_mask, edge_f, edge_t, edge_pt, vert_y, vert_slot, recheck;
   size_t cell_y, cell_perm, cell_sgn, cell_off, scan;
+  size_t items, item_off;
+  uint64_t IC;
   size_t vtab_idx, vlist_off, vlist_n, vlist;  // root-screen lists (0 bytes: none)
   uint64_t ME, MV, MC, TE, TV, VL;
   std::vector<int2> tab;
@@ -133,6 +135,11 @@ int mf_layout_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_domain *dom, const 
   l->edge_f = bump->take(l->ME * 16);
   l->edge_t = bump->take(l->ME * 8);
   l->edge_pt = bump->take(l->ME * d * 8);
+  // the expansion's vertex slots (16 items per edge on average; an edge
+  // whose items do not fit looks its vertices up) and each edge's first item
+  l->IC = l->ME * 16;
+  l->items = bump->take(l->IC * 4 + 8);
+  l->item_off = bump->take(l->ME * 8 + 8);
   l->vert_y = bump->take(l->MV * d * 4);
   l->vert_slot = bump->take(l->MV * 4);
   l->recheck = bump->take(l->MV * 4);
@@ -177,6 +184,9 @@ int mf_setup_trace(mf_ctx *ctx, const mf_rbf *rbf, const mf_trace_opts *o, char 
   B.edge_t = (double *)(base + l->edge_t);
   B.edge_pt = (double *)(base + l->edge_pt);
   B.max_edges = l->ME;
+  B.item_slot = (uint32_t *)(base + l->items);
+  B.edge_item_off = (unsigned long long *)(base + l->item_off);
+  B.item_cap = l->IC;
   B.vert_y = (int32_t *)(base + l->vert_y);
   B.vert_slot = (uint32_t *)(base + l->vert_slot);
   B.recheck = (uint32_t *)(base + l->recheck);

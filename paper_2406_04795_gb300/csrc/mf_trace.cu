@@ -780,7 +780,7 @@ __global__ void __launch_bounds__(EXPAND_WARPS * 32) k_b_expand(const MfSlot *sl
                                                                 const MfBatchPlan *P, int n) {
   __shared__ uint32_t s_end[EXPAND_WARPS][32], s_S[EXPAND_WARPS][32];
   __shared__ int s_t[EXPAND_WARPS][32];
-  __shared__ unsigned long long s_e[EXPAND_WARPS][32];
+  __shared__ unsigned long long s_e[EXPAND_WARPS][32], s_io[EXPAND_WARPS][32];
   const unsigned long long total = P->px[n];
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const unsigned long long nwarps = (unsigned long long)gridDim.x * EXPAND_WARPS;
@@ -799,18 +799,38 @@ __global__ void __launch_bounds__(EXPAND_WARPS * 32) k_b_expand(const MfSlot *sl
     s_S[wi][lane] = S;
     s_t[wi][lane] = t;
     s_e[wi][lane] = e;
+    // the edge's first item in its trace's slot record (see
+    // MfTraceBufs.item_slot; per edge, as the warp's edges may belong to
+    // several traces): taken by the vertices pass, read by the edges pass
+    unsigned long long io = ~0ull;
+    if (item < total && slots[t].B.item_slot) {
+      const MfTraceBufs &TB = slots[t].B;
+      if (EDGES) {
+        io = TB.edge_item_off[e];
+      } else {
+        io = atomicAdd(&TB.cnt->n_items, (unsigned long long)c);
+        if (io + c > TB.item_cap) io = ~0ull;
+        TB.edge_item_off[e] = io;
+      }
+    }
+    s_io[wi][lane] = io;
     const uint32_t nit = expand_warp_scan(c, s_end[wi]);
     for (uint32_t j = lane; j < nit; j += 32) {
       uint32_t r;
       const int o = expand_owner(s_end[wi], j, &r);
       const MfSlot &SL = slots[s_t[wi][o]];
       const uint32_t So = s_S[wi][o];
+      const unsigned long long oo = s_io[wi][o];
       int kind;
       const uint32_t M = expand_item_decode(So, SL.F.d, r, &kind);
       if (EDGES) {
-        expand_edges_item(SL.F, SL.B, s_e[wi][o], So, kind, M);
-      } else if (expand_vertices_item(SL.F, SL.B, s_e[wi][o], So, kind, M)) {
-        atomicAdd(&SL.B.cnt->n_boundary, 1ull);
+        expand_edges_item(SL.F, SL.B, s_e[wi][o], So, kind, M,
+                          oo != ~0ull ? SL.B.item_slot[oo + r] : MF_SLOT_UNKNOWN);
+      } else {
+        uint32_t sl;
+        if (expand_vertices_item(SL.F, SL.B, s_e[wi][o], So, kind, M, &sl))
+          atomicAdd(&SL.B.cnt->n_boundary, 1ull);
+        if (oo != ~0ull) SL.B.item_slot[oo + r] = sl;
       }
     }
     __syncwarp();  // the next group overwrites this warp's shared entries
@@ -997,8 +1017,9 @@ void mf_b_launch_cells(const MfSlot *slots, MfBatchPlan *P, int n, const int32_t
 void mf_b_launch_cell_edges(const MfSlot *slots, MfBatchPlan *P, int n, bool fill,
                             const int32_t *only, int sms, cudaStream_t s) {
   if (!fill) {
+    // the cells' plan; their sign masks and row lengths were written by the
+    // enumeration (cells_enum_edge), so no counting pass is needed
     k_b_plan_edges<<<1, MF_MAX_SLOTS, 0, s>>>(slots, P, n, 1, only, 0);
-    k_b_cell_edges<false><<<sms * 8, 256, 0, s>>>(slots, P, n);
   } else {
     k_b_cell_edges<true><<<sms * 8, 256, 0, s>>>(slots, P, n);
   }
