@@ -58,8 +58,9 @@ def f32_term_ops(d):
 # capture (dram__bytes_read.sum + dram__bytes_write.sum of k_roots_prep,
 # k_roots_f64 (warp and redo launches), k_roots_x, k_roots_terms and
 # k_roots_finish on the lambda = 0.15 case of the d=5 workload, divided by
-# its 880,448 edges); None once a kernel has changed since the capture
-ROOTS_DRAM_BYTES_PER_EDGE = None
+# its 880,448 edges: 1229.8 MB); None once a kernel has changed since the
+# capture
+ROOTS_DRAM_BYTES_PER_EDGE = 1396.8
 
 
 def make_workload(cfg: str, rank: int, lam=None):
