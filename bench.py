@@ -439,8 +439,16 @@ def sample_cells(w, r, cv, whole, n_cells=300, seed=7):
     cells = torch.nonzero(cv).flatten()
     if cells.numel() == 0:
         return dict(w=w, cells=[], whole=np.zeros(0, bool))
-    g = torch.Generator(device="cpu").manual_seed(seed)
-    pick = cells[torch.randperm(cells.numel(), generator=g)[:n_cells].to(cells.device)]
+    # distinct random positions (drawn on the host, few of them)
+    rng = np.random.default_rng(seed)
+    k = min(n_cells, cells.numel())
+    if cells.numel() <= 4 * k:
+        pos = rng.choice(cells.numel(), size=k, replace=False)
+    else:
+        pos = np.unique(rng.integers(0, cells.numel(), size=2 * k))
+        rng.shuffle(pos)
+        pos = pos[:k]
+    pick = cells[torch.as_tensor(pos, dtype=torch.int64, device=cells.device)]
     lo = r["cell_off"][pick].cpu().tolist()
     hi = r["cell_off"][pick + 1].cpu().tolist()
     out = []
@@ -513,16 +521,21 @@ def batched_line(ctx, n_traces=64, seed=1003):
         E_tot += r["n_edges"]
         del r
     torch.cuda.empty_cache()
-    tune_on(ctx, ws, caps)
-    out = {"traces": n_traces, "edges": E_tot,
+    tuned = tune_on(ctx, ws, caps)
+    out = {"traces": n_traces, "edges": E_tot, "autotune": tuned,
            "workload": "d in {4,5,6}, 256-8192 SVs log-uniform, lambda in [0.03, 0.1], 1-64 seeds"}
     for name, prec in (("mixed_bf16", mf.MF_MIXED_BF16), ("fp64", mf.MF_FP64)):
         ctx.trace_batch(ws, precisions=[prec] * n_traces, capacities=caps)  # untimed
         torch.cuda.synchronize()
+        mf.mf_ctx_set_profiling(ctx.h, True)  # per-phase CUDA events of the batch
         t0 = time.perf_counter()
         got = ctx.trace_batch(ws, precisions=[prec] * n_traces, capacities=caps)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        # (the batch records its whole search graph under expand_vertices)
+        phases = {("bfs_graph" if k == "expand_vertices" else k): round(v["ms"], 3)
+                  for k, v in mf.mf_ctx_get_stats(ctx.h).items() if v["ms"] > 0}
+        mf.mf_ctx_set_profiling(ctx.h, False)
         E = sum(g["n_edges"] for g in got)
         del got
         t0 = time.perf_counter()
@@ -533,7 +546,8 @@ def batched_line(ctx, n_traces=64, seed=1003):
         torch.cuda.synchronize()
         dt1 = time.perf_counter() - t0
         out[name] = {"simplices_per_s": E / dt, "ms": dt * 1e3,
-                     "one_at_a_time_simplices_per_s": E / dt1, "one_at_a_time_ms": dt1 * 1e3}
+                     "one_at_a_time_simplices_per_s": E / dt1, "one_at_a_time_ms": dt1 * 1e3,
+                     "phase_ms": phases}
     out["tune"] = mf.mf_ctx_get_tune(ctx.h).as_dict()
     torch.cuda.empty_cache()
     return out
