@@ -9,8 +9,10 @@ in [0, 1]: min F >= F(t) - |F'(t)| (t or 1 - t).  The kernel uses this twice:
     slack);
   - in FP64, as the certificate that accepts a Newton minimiser as exact to
     2e-12 in the distance.
-This test restates both steps in numpy (float32 / float64) and checks them
-against the oracle on random segments and boxes."""
+It also takes the squared distance at the FP32 Newton point, plus eta, as an
+upper bound (the first certification pass's lower bound on a pair's
+margin).  This test restates these steps in numpy (float32 / float64) and
+checks them against the oracle on random segments and boxes."""
 import math
 
 import numpy as np
@@ -64,6 +66,35 @@ def test_fp32_tangent_bound_is_a_lower_bound():
         assert lb - 1e-4 * (1 + scale) <= exact
         gaps.append(exact - lb)
     assert np.median(gaps) < 1e-3  # tight enough to prune
+
+
+def test_fp32_upper_bound_is_an_upper_bound():
+    """The first certification pass also bounds each pair's distance from
+    above: the squared distance at the FP32 Newton point plus the rounding
+    allowance eta, then the same 1e-4 (1 + scale) slack.  radius minus that
+    is the lower bound on the pair's margin that lets one or two exact
+    evaluations settle a point; it must never exceed the exact margin."""
+    rng = np.random.default_rng(14)
+    gaps = []
+    for _ in range(3000):
+        R, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        tt = rng.uniform(-1, 1, 3)
+        h = rng.uniform(0.02, 0.4, 3)
+        pa = rng.uniform(-1.5, 1.5, 3)
+        pb = pa + rng.normal(scale=0.4, size=3)
+        exact = oracle.segment_obstacle_dist(pa, pb, 0, np.concatenate([R.reshape(-1), tt]), 2 * h)
+        a, b = _local(pa.astype(np.float32), pb.astype(np.float32), R.astype(np.float32),
+                      tt.astype(np.float32))
+        dl = b - a
+        dd = float(dl @ dl)
+        t0 = min(max(-float(a @ dl) / dd, 0.0), 1.0) if dd > 0 else 0.0
+        _, F, _ = _newton_tangent(a, dl, h, t0, 3, np.float32)
+        scale = max(1.0, np.abs(pa).max(), np.abs(pb).max(), (np.abs(tt) + h).max())
+        eta = 4e-5 * (1 + scale) ** 2
+        ub = float(np.float32(math.sqrt(float(F) + eta)) * np.float32(1.000001))
+        assert ub + 1e-4 * (1 + scale) >= exact
+        gaps.append(ub - exact)
+    assert np.median(gaps) < 1e-3  # tight enough to settle most points
 
 
 def test_fp64_certificate_accepts_only_exact_minima():
