@@ -1097,7 +1097,7 @@ __device__ __forceinline__ void cert_rec_test(const float4 (&v)[NV4], int d, int
 }
 
 template <int NV4>
-__global__ void __launch_bounds__(256) k_certify_cells_whole32(
+__global__ void __launch_bounds__(256, 3) k_certify_cells_whole32(
     const int64_t *off, const int64_t *idx, int64_t n_cells, const float *rec32, const double *pts,
     int d, const double *margin, const int16_t *element, const float *L32, const double *L, int NE,
     int64_t n_points, uint8_t *whole, unsigned *bad, const uint8_t *verdict,

@@ -665,16 +665,21 @@ __device__ __forceinline__ void cell_edges_item(const MfFrame &F, const MfTraceB
   // the d+1 vertex signs, and the fill pass looks up only those pairs.
   const int d = F.d;
   int32_t vi[MF_MAXD];
-  int pi[MF_MAXD];
   load_y(B.cell_y + c * d, d, vi);
-  for (int k = 0; k < d; k++) pi[k] = B.cell_perm[c * d + k];
+  // the permutation as 4-bit nibbles (no indexed local array)
+  uint64_t pw = 0;
+  for (int k = 0; k < d; k++) pw |= (uint64_t)B.cell_perm[c * d + k] << (4 * k);
   uint32_t sg;
   if (!FILL) {
     uint32_t in = 0, pos = 0;
     int32_t w[MF_MAXD];
     load_y(vi, d, w);
     for (int i = 0; i <= d; i++) {
-      if (i > 0) w[pi[i - 1]] += 1;
+      if (i > 0) {
+        const int p = (int)((pw >> (4 * (i - 1))) & 15ull);
+#pragma unroll
+        for (int k = 0; k < MF_MAXD; k++) w[k] += k == p ? 1 : 0;
+      }
       const uint64_t slot = mf_table_find<2>(B.vtab_key, B.vtab_mask, mf_vertex_key(F, w));
       if (slot == ~0ull) continue;
       in |= 1u << i;
@@ -691,7 +696,7 @@ __device__ __forceinline__ void cell_edges_item(const MfFrame &F, const MfTraceB
   for (int i = 0; i < d; i++) {
     uint32_t mask = 0;
     for (int j = i + 1; j <= d; j++) {
-      mask |= 1u << pi[j - 1];
+      mask |= 1u << (uint32_t)((pw >> (4 * (j - 1))) & 15ull);
       if (!((in >> i) & (in >> j) & 1u) || ((pos >> i) & 1u) == ((pos >> j) & 1u)) continue;
       const uint64_t slot = mf_table_find<2>(B.etab_key, B.etab_mask, mf_edge_key(F, vi, mask));
       if (slot == ~0ull) {
@@ -701,7 +706,9 @@ __device__ __forceinline__ void cell_edges_item(const MfFrame &F, const MfTraceB
       }
       B.cell_idx[at++] = (int64_t)mf_etab_val(B, slot);
     }
-    vi[pi[i]] += 1;
+    const int p = (int)((pw >> (4 * i)) & 15ull);
+#pragma unroll
+    for (int k = 0; k < MF_MAXD; k++) vi[k] += k == p ? 1 : 0;
   }
 }
 
