@@ -397,7 +397,7 @@ def eval_tc_roofline(stats, rates):
 
 
 def config_lines(ctx, d6_lam=0.15):
-    """The other BASELINE configurations, each one line (untimed by the main
+    """The other workload configurations, each one line (untimed by the main
     metric): d=3 FP64; d=6 mixed BF16 at the finest lambda traced here.  The
     proofs' sampled edges are kept for the oracle comparison of the CPU
     baseline leg."""
