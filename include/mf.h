@@ -316,7 +316,9 @@ int mf_server_wait(mf_server *s, int64_t id, double timeout_ms, void *stream, in
  * the point is in C_obs, iff margin >= 0), and per cell the AND of the
  * verdicts of its points.  points: device [n_points][d]; cell CSR: device
  * (n_cells may be 0 and the CSR pointers NULL); outputs: device
- * point_verdict [n_points], margin [n_points], cell_verdict [n_cells]. */
+ * point_verdict [n_points], margin [n_points], cell_verdict [n_cells].
+ * n_points must be below 2^32 (MF_ERR_INVALID otherwise); the context's
+ * scratch holds 4 bytes per point for the points left to the full search. */
 int mf_certify(mf_ctx *ctx, const mf_robot *robot, const mf_scene *scene, const double *points,
                int64_t n_points, int32_t d, const int64_t *cell_edge_off,
                const int64_t *cell_edge_idx, int64_t n_cells, uint8_t *point_verdict,
