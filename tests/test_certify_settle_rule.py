@@ -14,6 +14,7 @@ the oracle's exact margins widened by random amounts up to the slack the
 kernel allows, and every settled point must reproduce the oracle's margin
 and deciding element."""
 import numpy as np
+import pytest
 
 import oracle
 from paper_2406_04795_gb300 import workloads as W
@@ -21,9 +22,28 @@ from paper_2406_04795_gb300 import workloads as W
 TIE = 1e-9
 
 
-def test_settled_points_match_the_full_search():
+def _mixed_scene(w, rng):
+    """The workload's boxes, every third turned into a sphere and every
+    third (offset by one) into a cylinder (App. A's obstacle types)."""
+    types = np.array(w.obs_type, dtype=np.int32).copy()
+    dims = np.array(w.obs_dims, dtype=np.float64).copy()
+    for k in range(len(types)):
+        if k % 3 == 0:
+            types[k] = 1  # sphere: radius in dims[0]
+            dims[k] = [dims[k].min() / 2, 0.0, 0.0]
+        elif k % 3 == 1:
+            types[k] = 2  # cylinder: radius, height
+            dims[k] = [dims[k][0] / 2, dims[k][2], 0.0]
+    return types, dims
+
+
+@pytest.mark.parametrize("scene", ["boxes", "boxes_spheres_cylinders"])
+def test_settled_points_match_the_full_search(scene):
     w = W.config_d5(lam=0.6)
     rng = np.random.default_rng(21)
+    if scene != "boxes":
+        types, dims = _mixed_scene(w, rng)
+        w.obs_type, w.obs_dims = types, dims
     NL = w.dh.shape[0]
     pts = rng.uniform(-np.pi, np.pi, size=(300, NL))
     o = oracle.certify_ex(w.dh, w.radius, w.obs_type, w.obs_pose, w.obs_dims, pts)
